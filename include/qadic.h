@@ -1,0 +1,231 @@
+/*
+ * qadic.h -- C ABI of the GB300 (sm_103a) library for matrix multiplication
+ * over small extension fields GF(p^k) through the q-adic transform
+ * ("Q-adic Transform Revisited", J.-G. Dumas).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Field.   GF(p^k) = Z_p[X]/(P), P monic irreducible of degree k; an element is
+ *          the coefficient vector (c_0..c_{k-1}), c_i in [0, p-1]  (Sec. 6).
+ *          Discrete-log codes: code e in [0, p^k-2] is g^e for the field's
+ *          generator g; code p^k-1 is zero (Sec. 6, Alg. 4 REQUIRE).
+ * Planes.  A "k-plane" matrix of rows x cols stores coefficient i of every
+ *          element in plane i: element (r, c) of plane i is at
+ *          base + (i * rows + r) * ld + c, i.e. planes are contiguous blocks
+ *          of rows * ld elements.
+ * Memory.  Every data pointer is a DEVICE pointer (cudaMalloc, or a torch
+ *          CUDA tensor) unless the name ends in _host.  The caller owns all
+ *          data buffers and workspaces; the library owns only the field
+ *          handle and the device tables it uploads at qadic_field_init and
+ *          frees at qadic_field_destroy.
+ * Streams. `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *          stream).  Calls that take a stream only enqueue work and return.
+ * Errors.  Every call returns a qadic_status.  Argument, size, alignment and
+ *          exactness-bound violations are detected on the host before
+ *          anything is enqueued; outputs are then left untouched ("overflow
+ *          rejected rather than miscomputed").  A CUDA launch error returns
+ *          QADIC_E_CUDA.  Device-side conditions (a bounded wait that ran
+ *          out) set a per-device status word read by qadic_sync_status.
+ *          qadic_last_error() gives a one-line description of the last
+ *          failure on the calling thread.
+ * Threads. Field handles are immutable after init and may be shared by
+ *          threads and streams.
+ */
+#ifndef QADIC_H
+#define QADIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QADIC_OK = 0,
+    QADIC_E_INVALID = 1,        /* bad argument, size, stride or alignment */
+    QADIC_E_NOT_PRIME = 2,      /* p is not prime */
+    QADIC_E_REDUCIBLE = 3,      /* the given P is not irreducible mod p */
+    QADIC_E_OVERFLOW = 4,       /* an exactness bound (Eq. 2, Lemma 1, Eq. 4) fails */
+    QADIC_E_UNSUPPORTED = 5,    /* valid request this build has no kernel for */
+    QADIC_E_CUDA = 6,           /* a CUDA runtime call failed */
+    QADIC_E_DEVICE_TIMEOUT = 7, /* a bounded device wait ran out (qadic_sync_status) */
+    QADIC_E_NOMEM = 8           /* host or device allocation failed, or workspace too small */
+} qadic_status;
+
+/* Element formats accepted / produced by qadic_pack. */
+typedef enum {
+    QADIC_FMT_LOG = 0,        /* one discrete-log code per element: uint8 when p^k <= 256, else uint16 */
+    QADIC_FMT_COEFF_U8 = 1,   /* k planes of uint8 coefficients in [0, p-1] */
+    QADIC_FMT_INT8_PLANES = 2,/* k planes of int8 coefficients, any representative mod p */
+    QADIC_FMT_QADIC_F64 = 3,  /* one double per element: sum_i c_i q^i, c_i in [0, p-1] (Eq. 1) */
+    QADIC_FMT_OPERAND_A = 4,  /* k planes of bf16 centred coefficients, rows x cols (K contiguous) */
+    QADIC_FMT_OPERAND_B = 5   /* k planes of bf16 centred coefficients, TRANSPOSED: cols x rows */
+} qadic_format;
+
+/* Contraction forms of qadic_gemm. */
+typedef enum {
+    QADIC_PATH_FP64_QADIC = 0, /* FP64 q-adic GEMM, REDQ after every n_q-product K-block (Alg. 4) */
+    QADIC_PATH_PLANES = 1      /* k x k coefficient-plane tensor-core GEMMs + fused mod-p / mod-P epilogue */
+} qadic_path;
+
+/* Field description returned by qadic_field_info. */
+typedef struct {
+    uint32_t p, k;
+    uint32_t poly[17];        /* P, k+1 coefficients low -> high (poly[k] == 1) */
+    uint32_t generator[16];   /* coefficients of g */
+    uint32_t order;           /* p^k */
+    uint32_t zero_code;       /* p^k - 1 */
+    uint32_t log_bytes;       /* 1 or 2: width of a QADIC_FMT_LOG code */
+    uint32_t log2_q;          /* FP64 q-adic radix q = 2^log2_q (Eq. 2 with m = 53) */
+    uint32_t n_q;             /* products per K-block of the FP64 path (Eq. 2); 0 = path unavailable */
+    uint32_t reserved;
+    int64_t k_max_int32;      /* Eq. 4 with centred planes and a 32-bit signed accumulator */
+    int64_t k_chunk_f32;      /* K per exact FP32 tensor-core accumulation chunk */
+} qadic_info;
+
+/* One product of qadic_batched_gemm: C = A * B over fields[field].
+ * A: k-plane COEFF_U8 m x K (ld = lda), B: k-plane COEFF_U8 K x n (ld = ldb),
+ * C: k-plane COEFF_U8 m x n (ld = ldc).  All device pointers. */
+typedef struct {
+    int32_t field;            /* index into the fields array */
+    int32_t m, n, K;
+    const uint8_t *A;
+    const uint8_t *B;
+    uint8_t *C;
+    int32_t lda, ldb, ldc;
+    int32_t reserved;
+} qadic_gemm_desc;
+
+typedef struct qadic_field qadic_field;
+
+/* ---------------------------------------------------------------- field --
+ * qadic_field_init: build GF(p^k) on the current CUDA device.
+ *   p     prime, 2 <= p <= 251 (coefficients fit a byte).
+ *   k     1 <= k <= 8, p^k <= 65536.
+ *   poly  k+1 coefficients low -> high, monic, or NULL for the default: the
+ *         monic irreducible whose low coefficients have the smallest value
+ *         sum_i a_i p^i.  (Sec. 6: the field as polynomials modulo p and
+ *         modulo an irreducible P of degree k.)
+ *   flags 0, or QADIC_FIELD_HOST_ONLY: build the field and its tables on the
+ *         host only (no device upload, no CUDA call); such a handle serves
+ *         qadic_field_info and is rejected by every call that launches work.
+ * Host side: checks p prime (QADIC_E_NOT_PRIME) and P irreducible
+ * (QADIC_E_REDUCIBLE), picks the generator (smallest primitive element),
+ * derives q and n_q from Eq. 2, the Eq. 4 K bound, and builds the tables of
+ * Sec. 5-6: log -> q-adic FP64 word, log -> centred planes, the Thm. 3 L/H
+ * correction-and-fold tables and X^t mod P; then uploads them (owned by the
+ * handle).  *out is set only on success. */
+#define QADIC_FIELD_HOST_ONLY 0x1u
+int qadic_field_init(qadic_field **out, uint32_t p, uint32_t k, const uint32_t *poly,
+                     uint32_t flags);
+/* Frees the handle and its device tables.  The caller must ensure no queued
+ * work still uses the field.  NULL is accepted. */
+int qadic_field_destroy(qadic_field *field);
+/* Copies the field description into *out (host memory). */
+int qadic_field_info(const qadic_field *field, qadic_info *out);
+
+/* ----------------------------------------------------------------- pack --
+ * DQT (Sec. 2, Alg. 1 line 1; Alg. 4 line 1 with the Sec. 6 improvement:
+ * one table lookup instead of a Horner evaluation).  Converts a rows x cols
+ * matrix from in_fmt to out_fmt.
+ *   in, ld_in    input in in_fmt (element stride per row = ld_in elements)
+ *   out, ld_out  output in out_fmt; for QADIC_FMT_OPERAND_B the output is the
+ *                transpose (cols x rows, ld_out >= rows)
+ * Supported pairs: LOG -> QADIC_F64 | OPERAND_A | OPERAND_B | COEFF_U8;
+ * COEFF_U8 or INT8_PLANES -> QADIC_F64 | OPERAND_A | OPERAND_B.
+ * Errors: QADIC_E_INVALID (format pair, ld < cols, NULL), QADIC_E_OVERFLOW
+ * (QADIC_F64 requested but Eq. 2 has no q with n_q >= 1).
+ * OPERAND formats need ld_out a multiple of 8 and 16-byte aligned bases. */
+int qadic_pack(const qadic_field *field, int in_fmt, const void *in, int64_t rows, int64_t cols,
+               int64_t ld_in, int out_fmt, void *out, int64_t ld_out, void *stream);
+
+/* ----------------------------------------------------------------- gemm --
+ * C = A * B over GF(p^k) (Alg. 4 applied to every row/column pair, the
+ * numerical routine being a GEMM, Sec. 6).  m x K times K x n.
+ * QADIC_PATH_FP64_QADIC: A is QADIC_F64 m x K (lda), B is QADIC_F64 K x n
+ *   (ldb).  K is cut into blocks of n_q products (Eq. 2); after each block
+ *   the packed sums go through REDQ (Alg. 2 with Lemma 1's floor) and the
+ *   two Thm. 3 table lookups, and the block results are added mod p.
+ * QADIC_PATH_PLANES: A is OPERAND_A (k planes, m x K, lda), B is OPERAND_B
+ *   (k planes, n x K, ldb).  The 2k-1 plane sums C_t = sum_{i+j=t} A_i B_j
+ *   (Eq. 1 coefficientwise) are accumulated exactly on the tensor cores in
+ *   K-chunks of at most k_chunk_f32, reduced mod p, and folded mod P with
+ *   X^t mod P in the epilogue.  lda, ldb multiples of 8.
+ * C: k planes of uint8 in [0, p-1], m x n (ldc).
+ * workspace/ws_bytes: unused by these kernels (pass NULL, 0).
+ * Errors: QADIC_E_INVALID, QADIC_E_OVERFLOW (FP64 path with n_q = 0),
+ * QADIC_E_UNSUPPORTED (plane path for a k without a tensor-core kernel). */
+int qadic_gemm(const qadic_field *field, int path, int64_t m, int64_t n, int64_t K,
+               const void *A, int64_t lda, const void *B, int64_t ldb, uint8_t *C, int64_t ldc,
+               void *workspace, size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------ matmul_host --
+ * End-to-end convenience: A (m x K) and B (K x n) in in_fmt (LOG, COEFF_U8 or
+ * INT8_PLANES) in HOST memory (pinned for asynchrony), C (k planes of uint8,
+ * m x n) in HOST memory.  Copies the inputs into `workspace` (device, at
+ * least qadic_matmul_workspace_size bytes), packs, multiplies with `path`,
+ * and copies C back, all enqueued on `stream`.  Dense leading dimensions. */
+size_t qadic_matmul_workspace_size(const qadic_field *field, int path, int in_fmt, int64_t m,
+                                   int64_t n, int64_t K);
+int qadic_matmul_host(const qadic_field *field, int path, int in_fmt, int64_t m, int64_t n,
+                      int64_t K, const void *A_host, const void *B_host, uint8_t *C_host,
+                      void *workspace, size_t ws_bytes, void *stream);
+
+/* ----------------------------------------------------------------- redq --
+ * REDQ (Alg. 2) on `count` packed words in[i] = sum_{j<=d} mu~_j q^j with
+ * q = 2^log2_q, d = ndigits-1, each an exact non-negative integer held in a
+ * double.  Writes out[i] = rho = sum_j (mu~_j mod p) q^j (exact, as double).
+ * rop = floor(r/p) by Lemma 1 (multiplication by 1/p rounded upward, then
+ * floor) or, with QADIC_REDQ_INT_FLOOR, by an integer multiply-high; the
+ * u_j by shifts; the corrections mu_j = (u_j - q u_{j+1}) mod p per
+ * table_mode (Table 2): 0 arithmetic, 1 a p^2 table (d lookups), 2 a p^k'
+ * table (ceil(d/(k'-1)) lookups, largest k' fitting shared memory), 3 the
+ * full p^(d+1) table (one lookup) when it fits.
+ * Requires ndigits * log2_q <= 51 (Lemma 1's limit 1/(2eps+eps^2) with
+ * eps = 2^-52), else QADIC_E_OVERFLOW; in/out 16-byte aligned; may alias. */
+#define QADIC_REDQ_INT_FLOOR 0x100u
+int qadic_redq(uint32_t p, uint32_t log2_q, uint32_t ndigits, const double *in, double *out,
+               int64_t count, uint32_t table_mode, void *stream);
+
+/* ------------------------------------------------------ polymul_batched --
+ * Alg. 1 on `count` independent pairs in Z_p[X] (no defining polynomial):
+ * a, b: count x k uint8 coefficients in [0, p-1] (pair s at a + s*k);
+ * out: count x (2k-1) uint8, the product's coefficients mod p.
+ * q = the smallest power of two above k (p-1)^2 (one product, n_q = 1);
+ * pack by shifts, product in FP64, REDQ in 64-bit words (Sec. 2 allows
+ * 64-bit machine words).  With QADIC_POLYMUL_PLAIN_F64 the product is the
+ * single-rounded FP64 product and Eq. 2 (m = 53) must hold, else
+ * QADIC_E_OVERFLOW.  Otherwise the product is made exact with an FMA
+ * error term (hi + lo), which needs (2k-1) log2 q <= 63. */
+#define QADIC_POLYMUL_PLAIN_F64 0x1u
+int qadic_polymul_batched(uint32_t p, uint32_t k, const uint8_t *a, const uint8_t *b, uint8_t *out,
+                          int64_t count, uint32_t flags, void *stream);
+
+/* -------------------------------------------------------- batched_gemm --
+ * `count` independent products descs[i] over fields[descs[i].field] in ONE
+ * persistent launch (tiles of all products on a device work list).
+ * Requires 1 <= m, n, K <= 4096 per product, k <= 8.  `workspace` must hold
+ * qadic_batched_workspace_size(count, descs) bytes (device); the host packs
+ * the work list into it.  With QADIC_BATCHED_GRAPH the launch is captured in
+ * a CUDA graph keyed by (descs, count, workspace) and replayed on later calls
+ * with the same key.  Errors: QADIC_E_INVALID, QADIC_E_NOMEM (workspace too
+ * small), QADIC_E_OVERFLOW (K beyond the exact FP32 chunk of a field). */
+#define QADIC_BATCHED_GRAPH 0x1u
+size_t qadic_batched_workspace_size(const qadic_gemm_desc *descs, int64_t count);
+int qadic_batched_gemm(const qadic_field *const *fields, int32_t nfields,
+                       const qadic_gemm_desc *descs, int64_t count, void *workspace,
+                       size_t ws_bytes, uint32_t flags, void *stream);
+
+/* --------------------------------------------------------------- status --
+ * Synchronises `stream` and returns QADIC_E_DEVICE_TIMEOUT if a kernel of
+ * this library on the current device gave up a bounded wait since the last
+ * call (the word is then cleared), QADIC_E_CUDA on a CUDA error, else OK. */
+int qadic_sync_status(void *stream);
+const char *qadic_status_string(int status);
+const char *qadic_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QADIC_H */

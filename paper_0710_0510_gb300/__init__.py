@@ -1,0 +1,265 @@
+"""GF(p^k) matrix multiplication through the q-adic transform on GB300.
+
+Python binding of ``libqadic.so`` (C ABI in ``include/qadic.h``).  This module
+only marshals arguments: torch tensors supply device memory and the current
+CUDA stream, and every step of the computation runs in the library's CUDA
+kernels.  There is no CPU fallback: without the built library or a CUDA
+device every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+from . import build as _build
+
+# qadic_status
+OK, E_INVALID, E_NOT_PRIME, E_REDUCIBLE, E_OVERFLOW, E_UNSUPPORTED, E_CUDA, E_DEVICE_TIMEOUT, \
+    E_NOMEM = range(9)
+# qadic_format
+FMT_LOG, FMT_COEFF_U8, FMT_INT8_PLANES, FMT_QADIC_F64, FMT_OPERAND_A, FMT_OPERAND_B = range(6)
+# qadic_path
+PATH_FP64_QADIC, PATH_PLANES = 0, 1
+REDQ_INT_FLOOR = 0x100
+POLYMUL_PLAIN_F64 = 0x1
+BATCHED_GRAPH = 0x1
+FIELD_HOST_ONLY = 0x1
+
+_lock = threading.Lock()
+_lib = None
+
+
+class QadicError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"qadic status {status}: {message}")
+        self.status = status
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_uint32), ("k", ctypes.c_uint32),
+                ("poly", ctypes.c_uint32 * 17), ("generator", ctypes.c_uint32 * 16),
+                ("order", ctypes.c_uint32), ("zero_code", ctypes.c_uint32),
+                ("log_bytes", ctypes.c_uint32), ("log2_q", ctypes.c_uint32),
+                ("n_q", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("k_max_int32", ctypes.c_int64), ("k_chunk_f32", ctypes.c_int64)]
+
+
+class GemmDesc(ctypes.Structure):
+    _fields_ = [("field", ctypes.c_int32), ("m", ctypes.c_int32), ("n", ctypes.c_int32),
+                ("K", ctypes.c_int32), ("A", ctypes.c_void_p), ("B", ctypes.c_void_p),
+                ("C", ctypes.c_void_p), ("lda", ctypes.c_int32), ("ldb", ctypes.c_int32),
+                ("ldc", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_SIGS = {
+    "qadic_field_init": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_uint32,
+                                        ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint32]),
+    "qadic_field_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "qadic_field_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Info)]),
+    "qadic_pack": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                                  ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
+                                  ctypes.c_int64, ctypes.c_void_p]),
+    "qadic_gemm": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
+                                  ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                  ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                  ctypes.c_size_t, ctypes.c_void_p]),
+    "qadic_matmul_workspace_size": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                                      ctypes.c_int64, ctypes.c_int64,
+                                                      ctypes.c_int64]),
+    "qadic_matmul_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "qadic_redq": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                  ctypes.c_uint32, ctypes.c_void_p]),
+    "qadic_polymul_batched": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                             ctypes.c_uint32, ctypes.c_void_p]),
+    "qadic_batched_workspace_size": (ctypes.c_size_t, [ctypes.POINTER(GemmDesc), ctypes.c_int64]),
+    "qadic_batched_gemm": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32,
+                                          ctypes.POINTER(GemmDesc), ctypes.c_int64,
+                                          ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32,
+                                          ctypes.c_void_p]),
+    "qadic_sync_status": (ctypes.c_int, [ctypes.c_void_p]),
+    "qadic_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "qadic_last_error": (ctypes.c_char_p, []),
+}
+
+
+def lib(load: bool = True):
+    """The loaded ``libqadic.so`` (built in-tree on first use)."""
+    global _lib
+    with _lock:
+        if _lib is None and load:
+            path = _build.build()
+            handle = ctypes.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(handle, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = handle
+    return _lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _check(status: int):
+    if status != OK:
+        msg = lib().qadic_last_error().decode(errors="replace")
+        raise QadicError(status, msg)
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("a CUDA device is required: libqadic has no CPU path")
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+class Field:
+    """GF(p^k) on the current CUDA device (``qadic_field_init``)."""
+
+    def __init__(self, p: int, k: int, poly=None, host_only: bool = False):
+        if not host_only:
+            _torch()
+        L = lib()
+        h = ctypes.c_void_p()
+        arr = None
+        if poly is not None:
+            arr = (ctypes.c_uint32 * len(poly))(*poly)
+        _check(L.qadic_field_init(ctypes.byref(h), p, k,
+                                  ctypes.cast(arr, ctypes.c_void_p) if arr is not None else None,
+                                  FIELD_HOST_ONLY if host_only else 0))
+        self._h = h
+        info = Info()
+        _check(L.qadic_field_info(h, ctypes.byref(info)))
+        self.p, self.k = info.p, info.k
+        self.poly = [info.poly[i] for i in range(self.k + 1)]
+        self.generator = [info.generator[i] for i in range(self.k)]
+        self.order = info.order
+        self.zero_code = info.zero_code
+        self.log_bytes = info.log_bytes
+        self.log2_q = info.log2_q
+        self.n_q = info.n_q
+        self.k_max_int32 = info.k_max_int32
+        self.k_chunk_f32 = info.k_chunk_f32
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.qadic_field_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------
+    def pack(self, in_fmt: int, x, rows: int, cols: int, out_fmt: int, out=None, ld_in=None,
+             ld_out=None, stream=None):
+        """DQT pack (``qadic_pack``).  Allocates ``out`` when not given."""
+        torch = _torch()
+        if out is None:
+            if out_fmt == FMT_QADIC_F64:
+                out = torch.empty((rows, cols), dtype=torch.float64, device=x.device)
+            elif out_fmt == FMT_OPERAND_A:
+                out = torch.empty((self.k, rows, cols), dtype=torch.bfloat16, device=x.device)
+            elif out_fmt == FMT_OPERAND_B:
+                out = torch.empty((self.k, cols, rows), dtype=torch.bfloat16, device=x.device)
+            elif out_fmt == FMT_COEFF_U8:
+                out = torch.empty((self.k, rows, cols), dtype=torch.uint8, device=x.device)
+            else:
+                raise ValueError("unsupported output format")
+        if ld_in is None:
+            ld_in = cols
+        if ld_out is None:
+            ld_out = rows if out_fmt == FMT_OPERAND_B else cols
+        _check(lib().qadic_pack(self._h, in_fmt, _ptr(x), rows, cols, ld_in, out_fmt, _ptr(out),
+                                ld_out, _stream(stream)))
+        return out
+
+    def gemm(self, path: int, A, B, m: int, n: int, K: int, C=None, lda=None, ldb=None,
+             ldc=None, stream=None):
+        """C = A B over GF(p^k) (``qadic_gemm``); C: (k, m, n) uint8."""
+        torch = _torch()
+        if C is None:
+            C = torch.empty((self.k, m, n), dtype=torch.uint8, device=A.device)
+        if lda is None:
+            lda = K
+        if ldb is None:
+            ldb = n if path == PATH_FP64_QADIC else K
+        if ldc is None:
+            ldc = n
+        _check(lib().qadic_gemm(self._h, path, m, n, K, _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc,
+                                None, 0, _stream(stream)))
+        return C
+
+    def matmul_workspace_size(self, path: int, in_fmt: int, m: int, n: int, K: int) -> int:
+        return int(lib().qadic_matmul_workspace_size(self._h, path, in_fmt, m, n, K))
+
+    def matmul_host(self, path: int, in_fmt: int, A_host, B_host, C_host, m: int, n: int, K: int,
+                    workspace, stream=None):
+        """End to end from host buffers (``qadic_matmul_host``)."""
+        _check(lib().qadic_matmul_host(self._h, path, in_fmt, m, n, K, _ptr(A_host), _ptr(B_host),
+                                       _ptr(C_host), _ptr(workspace), workspace.numel(),
+                                       _stream(stream)))
+        return C_host
+
+
+def redq(p: int, log2_q: int, ndigits: int, words, out=None, table_mode: int = 3,
+         int_floor: bool = False, stream=None):
+    """REDQ over packed FP64 words (``qadic_redq``)."""
+    torch = _torch()
+    if out is None:
+        out = torch.empty_like(words)
+    mode = table_mode | (REDQ_INT_FLOOR if int_floor else 0)
+    _check(lib().qadic_redq(p, log2_q, ndigits, _ptr(words), _ptr(out), words.numel(), mode,
+                            _stream(stream)))
+    return out
+
+
+def polymul_batched(p: int, k: int, a, b, out=None, plain_f64: bool = False, stream=None):
+    """Batched Alg. 1 + Alg. 2 (``qadic_polymul_batched``); a, b: (count, k) uint8."""
+    torch = _torch()
+    count = a.shape[0]
+    if out is None:
+        out = torch.empty((count, 2 * k - 1), dtype=torch.uint8, device=a.device)
+    _check(lib().qadic_polymul_batched(p, k, _ptr(a), _ptr(b), _ptr(out), count,
+                                       POLYMUL_PLAIN_F64 if plain_f64 else 0, _stream(stream)))
+    return out
+
+
+def batched_workspace_size(descs) -> int:
+    arr = (GemmDesc * len(descs))(*descs)
+    return int(lib().qadic_batched_workspace_size(arr, len(descs)))
+
+
+def batched_gemm(fields, descs, workspace, graph: bool = False, stream=None):
+    """Many independent products in one persistent launch (``qadic_batched_gemm``)."""
+    arr = (GemmDesc * len(descs))(*descs)
+    hs = (ctypes.c_void_p * len(fields))(*[f.handle for f in fields])
+    _check(lib().qadic_batched_gemm(hs, len(fields), arr, len(descs), _ptr(workspace),
+                                    workspace.numel() * workspace.element_size(),
+                                    BATCHED_GRAPH if graph else 0, _stream(stream)))
+
+
+def sync_status(stream=None):
+    _check(lib().qadic_sync_status(_stream(stream)))

@@ -1,0 +1,375 @@
+// C ABI entry points of libqadic (declared in include/qadic.h): argument
+// and bound checks on the host, field lifetime, dispatch to the kernels.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "qadic_internal.h"
+
+struct qadic_field {
+    qadic::Field f;
+};
+
+namespace qadic {
+
+namespace {
+thread_local std::string t_last_error;
+
+__device__ int g_status_word;   // bounded-wait status (one per device)
+
+std::mutex g_status_mu;
+int *g_status_ptr[64] = {nullptr};
+
+template <class T>
+int upload(T **dst, const std::vector<T> &src) {
+    *dst = nullptr;
+    if (src.empty()) return QADIC_OK;
+    if (cudaMalloc((void **)dst, src.size() * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(QADIC_E_NOMEM, "cudaMalloc of %zu bytes failed", src.size() * sizeof(T));
+    }
+    if (cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+        return set_error(QADIC_E_CUDA, "table upload failed: %s",
+                         cudaGetErrorString(cudaGetLastError()));
+    return QADIC_OK;
+}
+
+void free_tables(Field &f) {
+    cudaFree(f.d_antilog);
+    cudaFree(f.d_log_f64);
+    cudaFree(f.d_log_centred);
+    cudaFree(f.d_tab_L);
+    cudaFree(f.d_tab_H);
+    cudaFree(f.d_fold);
+    f.d_antilog = nullptr;
+    f.d_log_f64 = nullptr;
+    f.d_log_centred = nullptr;
+    f.d_tab_L = f.d_tab_H = nullptr;
+    f.d_fold = nullptr;
+}
+
+bool on_device(const Field &f) {
+    if (f.device < 0) return false;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    return dev == f.device;
+}
+
+}  // namespace
+
+int set_error(int status, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    t_last_error = buf;
+    return status;
+}
+
+int *device_status_word() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(g_status_mu);
+    if (!g_status_ptr[dev]) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_status_word) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        g_status_ptr[dev] = (int *)ptr;
+    }
+    return g_status_ptr[dev];
+}
+
+}  // namespace qadic
+
+using namespace qadic;
+
+extern "C" {
+
+int qadic_field_init(qadic_field **out, uint32_t p, uint32_t k, const uint32_t *poly,
+                     uint32_t flags) {
+    if (!out) return set_error(QADIC_E_INVALID, "out is NULL");
+    if (flags & ~QADIC_FIELD_HOST_ONLY) return set_error(QADIC_E_INVALID, "unknown flags");
+    qadic_field *h = new (std::nothrow) qadic_field();
+    if (!h) return set_error(QADIC_E_NOMEM, "host allocation failed");
+    int st = build_field(h->f, p, k, poly);
+    if (st != QADIC_OK) {
+        delete h;
+        return st;
+    }
+    if (flags & QADIC_FIELD_HOST_ONLY) {
+        h->f.device = -1;
+        *out = h;
+        return QADIC_OK;
+    }
+    if (cudaGetDevice(&h->f.device) != cudaSuccess) {
+        delete h;
+        return set_error(QADIC_E_CUDA, "no CUDA device: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    Field &f = h->f;
+    if ((st = upload(&f.d_antilog, f.antilog)) || (st = upload(&f.d_log_f64, f.log_f64)) ||
+        (st = upload(&f.d_log_centred, f.log_centred)) || (st = upload(&f.d_tab_L, f.tab_L)) ||
+        (st = upload(&f.d_tab_H, f.tab_H)) || (st = upload(&f.d_fold, f.fold))) {
+        free_tables(f);
+        delete h;
+        return st;
+    }
+    if (!device_status_word()) {
+        free_tables(f);
+        delete h;
+        return set_error(QADIC_E_CUDA, "status word unavailable");
+    }
+    *out = h;
+    return QADIC_OK;
+}
+
+int qadic_field_destroy(qadic_field *field) {
+    if (!field) return QADIC_OK;
+    if (field->f.device < 0) {
+        delete field;
+        return QADIC_OK;
+    }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != field->f.device) cudaSetDevice(field->f.device);
+    free_tables(field->f);
+    if (prev >= 0 && prev != field->f.device) cudaSetDevice(prev);
+    delete field;
+    return QADIC_OK;
+}
+
+int qadic_field_info(const qadic_field *field, qadic_info *out) {
+    if (!field || !out) return set_error(QADIC_E_INVALID, "NULL argument");
+    const Field &f = field->f;
+    std::memset(out, 0, sizeof(*out));
+    out->p = f.p;
+    out->k = f.k;
+    for (uint32_t i = 0; i <= f.k; ++i) out->poly[i] = f.poly[i];
+    for (uint32_t i = 0; i < f.k; ++i) out->generator[i] = f.gen[i];
+    out->order = f.order;
+    out->zero_code = f.order - 1;
+    out->log_bytes = f.order <= 256 ? 1 : 2;
+    out->log2_q = f.log2_q;
+    out->n_q = f.n_q;
+    out->k_max_int32 = f.k_max_int32;
+    out->k_chunk_f32 = f.k_chunk_f32;
+    return QADIC_OK;
+}
+
+int qadic_pack(const qadic_field *field, int in_fmt, const void *in, int64_t rows, int64_t cols,
+               int64_t ld_in, int out_fmt, void *out, int64_t ld_out, void *stream) {
+    if (!field) return set_error(QADIC_E_INVALID, "field is NULL");
+    const Field &f = field->f;
+    if (!on_device(f)) return set_error(QADIC_E_INVALID, "field lives on another device");
+    if (rows < 0 || cols < 0) return set_error(QADIC_E_INVALID, "negative size");
+    if (rows == 0 || cols == 0) return QADIC_OK;
+    if (!in || !out) return set_error(QADIC_E_INVALID, "NULL data pointer");
+    if (ld_in < cols) return set_error(QADIC_E_INVALID, "ld_in < cols");
+    const int64_t out_minor = (out_fmt == QADIC_FMT_OPERAND_B) ? rows : cols;
+    if (ld_out < out_minor) return set_error(QADIC_E_INVALID, "ld_out too small");
+    if (out_fmt == QADIC_FMT_QADIC_F64 && f.n_q == 0)
+        return set_error(QADIC_E_OVERFLOW, "Eq. 2 admits no q-adic block for p=%u k=%u", f.p, f.k);
+    if (out_fmt == QADIC_FMT_OPERAND_A || out_fmt == QADIC_FMT_OPERAND_B) {
+        if (ld_out % 8 != 0 || ((uintptr_t)out & 15) != 0)
+            return set_error(QADIC_E_INVALID, "operand output needs ld %% 8 == 0 and 16B alignment");
+    }
+    return launch_pack(f, in_fmt, in, rows, cols, ld_in, out_fmt, out, ld_out,
+                       (cudaStream_t)stream);
+}
+
+int qadic_gemm(const qadic_field *field, int path, int64_t m, int64_t n, int64_t K, const void *A,
+               int64_t lda, const void *B, int64_t ldb, uint8_t *C, int64_t ldc, void *workspace,
+               size_t ws_bytes, void *stream) {
+    (void)workspace;
+    (void)ws_bytes;
+    if (!field) return set_error(QADIC_E_INVALID, "field is NULL");
+    const Field &f = field->f;
+    if (!on_device(f)) return set_error(QADIC_E_INVALID, "field lives on another device");
+    if (m < 0 || n < 0 || K < 0) return set_error(QADIC_E_INVALID, "negative size");
+    if (m == 0 || n == 0) return QADIC_OK;
+    if (!C) return set_error(QADIC_E_INVALID, "C is NULL");
+    if (ldc < n) return set_error(QADIC_E_INVALID, "ldc < n");
+    if (K > 0 && (!A || !B)) return set_error(QADIC_E_INVALID, "NULL operand");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (path == QADIC_PATH_FP64_QADIC) {
+        if (f.n_q == 0)
+            return set_error(QADIC_E_OVERFLOW, "Eq. 2 admits no q-adic block for p=%u k=%u", f.p,
+                             f.k);
+        if (f.k > 4) return set_error(QADIC_E_UNSUPPORTED, "FP64 path supports k <= 4");
+        if (lda < K || ldb < n) return set_error(QADIC_E_INVALID, "lda < K or ldb < n");
+        return launch_gemm_f64(f, m, n, K, (const double *)A, lda, (const double *)B, ldb, C, ldc,
+                               s);
+    }
+    if (path == QADIC_PATH_PLANES) {
+        if (lda < K || ldb < K) return set_error(QADIC_E_INVALID, "lda or ldb < K");
+        if (!gemm_planes_tc_supported(f))
+            return set_error(QADIC_E_UNSUPPORTED, "no tensor-core plane kernel for k=%u", f.k);
+        return launch_gemm_planes_tc(f, m, n, K, A, lda, B, ldb, C, ldc, s);
+    }
+    return set_error(QADIC_E_INVALID, "unknown path %d", path);
+}
+
+static size_t in_elem_bytes(const Field &f, int fmt) {
+    if (fmt == QADIC_FMT_LOG) return f.order <= 256 ? 1 : 2;
+    if (fmt == QADIC_FMT_COEFF_U8 || fmt == QADIC_FMT_INT8_PLANES) return f.k;
+    return 0;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t qadic_matmul_workspace_size(const qadic_field *field, int path, int in_fmt, int64_t m,
+                                   int64_t n, int64_t K) {
+    if (!field || m < 0 || n < 0 || K < 0) return 0;
+    const Field &f = field->f;
+    const size_t eb = in_elem_bytes(f, in_fmt);
+    if (!eb) return 0;
+    size_t ws = align256(eb * m * K) + align256(eb * K * n) + align256((size_t)f.k * m * n);
+    if (path == QADIC_PATH_FP64_QADIC)
+        ws += align256(8 * (size_t)m * K) + align256(8 * (size_t)K * n);
+    else
+        ws += align256(2 * (size_t)f.k * m * K) + align256(2 * (size_t)f.k * n * K);
+    return ws;
+}
+
+int qadic_matmul_host(const qadic_field *field, int path, int in_fmt, int64_t m, int64_t n,
+                      int64_t K, const void *A_host, const void *B_host, uint8_t *C_host,
+                      void *workspace, size_t ws_bytes, void *stream) {
+    if (!field) return set_error(QADIC_E_INVALID, "field is NULL");
+    const Field &f = field->f;
+    const size_t need = qadic_matmul_workspace_size(field, path, in_fmt, m, n, K);
+    if (!need) return set_error(QADIC_E_INVALID, "bad format or size");
+    if (!workspace || ws_bytes < need)
+        return set_error(QADIC_E_NOMEM, "workspace %zu < %zu bytes", ws_bytes, need);
+    if (!A_host || !B_host || !C_host) return set_error(QADIC_E_INVALID, "NULL host pointer");
+    if (path == QADIC_PATH_PLANES && (K % 8 != 0))
+        return set_error(QADIC_E_INVALID, "plane path needs K %% 8 == 0 for dense operands");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t eb = in_elem_bytes(f, in_fmt);
+    char *w = (char *)workspace;
+    char *dA = w;
+    w += align256(eb * m * K);
+    char *dB = w;
+    w += align256(eb * K * n);
+    uint8_t *dC = (uint8_t *)w;
+    w += align256((size_t)f.k * m * n);
+    char *pA = w;
+    w += align256((path == QADIC_PATH_FP64_QADIC ? 8 : 2 * (size_t)f.k) * m * K);
+    char *pB = w;
+    if (cudaMemcpyAsync(dA, A_host, eb * m * K, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(dB, B_host, eb * K * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return set_error(QADIC_E_CUDA, "H2D copy: %s", cudaGetErrorString(cudaGetLastError()));
+    int st;
+    if (path == QADIC_PATH_FP64_QADIC) {
+        if ((st = qadic_pack(field, in_fmt, dA, m, K, K, QADIC_FMT_QADIC_F64, pA, K, stream)) ||
+            (st = qadic_pack(field, in_fmt, dB, K, n, n, QADIC_FMT_QADIC_F64, pB, n, stream)) ||
+            (st = qadic_gemm(field, path, m, n, K, pA, K, pB, n, dC, n, nullptr, 0, stream)))
+            return st;
+    } else {
+        if ((st = qadic_pack(field, in_fmt, dA, m, K, K, QADIC_FMT_OPERAND_A, pA, K, stream)) ||
+            (st = qadic_pack(field, in_fmt, dB, K, n, n, QADIC_FMT_OPERAND_B, pB, K, stream)) ||
+            (st = qadic_gemm(field, path, m, n, K, pA, K, pB, K, dC, n, nullptr, 0, stream)))
+            return st;
+    }
+    if (cudaMemcpyAsync(C_host, dC, (size_t)f.k * m * n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return set_error(QADIC_E_CUDA, "D2H copy: %s", cudaGetErrorString(cudaGetLastError()));
+    return QADIC_OK;
+}
+
+int qadic_redq(uint32_t p, uint32_t log2_q, uint32_t ndigits, const double *in, double *out,
+               int64_t count, uint32_t table_mode, void *stream) {
+    if (!is_prime(p) || p > 251) return set_error(QADIC_E_INVALID, "p must be a prime <= 251");
+    if (log2_q < 1 || ndigits < 1 || ndigits > 51)
+        return set_error(QADIC_E_INVALID, "bad log2_q or ndigits");
+    if ((uint64_t)ndigits * log2_q > 51)
+        return set_error(QADIC_E_OVERFLOW,
+                         "ndigits*log2_q=%u exceeds 51 bits (Lemma 1 limit for binary64)",
+                         ndigits * log2_q);
+    if ((1ull << log2_q) <= p) return set_error(QADIC_E_INVALID, "q must exceed p");
+    if (count < 0) return set_error(QADIC_E_INVALID, "negative count");
+    if (count == 0) return QADIC_OK;
+    if (!in || !out) return set_error(QADIC_E_INVALID, "NULL pointer");
+    if (((uintptr_t)in & 15) || ((uintptr_t)out & 15))
+        return set_error(QADIC_E_INVALID, "in/out must be 16-byte aligned");
+    const uint32_t mode = table_mode & 0xff;
+    if (mode > 3) return set_error(QADIC_E_INVALID, "table_mode %u", mode);
+    return launch_redq(p, log2_q, ndigits, in, out, count, mode,
+                       (table_mode & QADIC_REDQ_INT_FLOOR) != 0, (cudaStream_t)stream);
+}
+
+int qadic_polymul_batched(uint32_t p, uint32_t k, const uint8_t *a, const uint8_t *b, uint8_t *out,
+                          int64_t count, uint32_t flags, void *stream) {
+    if (!is_prime(p) || p > 251) return set_error(QADIC_E_INVALID, "p must be a prime <= 251");
+    if (k < 1 || k > kMaxK) return set_error(QADIC_E_INVALID, "k outside [1, 8]");
+    if (count < 0) return set_error(QADIC_E_INVALID, "negative count");
+    if (count == 0) return QADIC_OK;
+    if (!a || !b || !out) return set_error(QADIC_E_INVALID, "NULL pointer");
+    // q: the smallest power of two above k (p-1)^2 (Thm. 1 with n_q = 1).
+    const uint64_t bound = (uint64_t)k * (p - 1) * (p - 1);
+    uint32_t s = 1;
+    while ((1ull << s) <= bound) ++s;
+    const bool plain = (flags & QADIC_POLYMUL_PLAIN_F64) != 0;
+    if (plain && (2 * k - 1) * s >= 53)
+        return set_error(QADIC_E_OVERFLOW,
+                         "(2k-1) log2 q = %u >= 53: Eq. 2 fails for a single-rounded FP64 product",
+                         (2 * k - 1) * s);
+    if (!plain && (2 * k - 1) * s > 63)
+        return set_error(QADIC_E_OVERFLOW, "(2k-1) log2 q = %u > 63", (2 * k - 1) * s);
+    return launch_polymul(p, k, s, plain, a, b, out, count, (cudaStream_t)stream);
+}
+
+int qadic_sync_status(void *stream) {
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
+        return set_error(QADIC_E_CUDA, "%s", cudaGetErrorString(cudaGetLastError()));
+    int *word = device_status_word();
+    if (!word) return set_error(QADIC_E_CUDA, "status word unavailable");
+    int v = 0;
+    if (cudaMemcpy(&v, word, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return set_error(QADIC_E_CUDA, "%s", cudaGetErrorString(cudaGetLastError()));
+    if (v != 0) {
+        int zero = 0;
+        cudaMemcpy(word, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        return set_error(QADIC_E_DEVICE_TIMEOUT, "a bounded device wait ran out (site %d)", v);
+    }
+    return QADIC_OK;
+}
+
+const char *qadic_status_string(int status) {
+    switch (status) {
+        case QADIC_OK: return "ok";
+        case QADIC_E_INVALID: return "invalid argument";
+        case QADIC_E_NOT_PRIME: return "p is not prime";
+        case QADIC_E_REDUCIBLE: return "defining polynomial is reducible";
+        case QADIC_E_OVERFLOW: return "exactness bound violated";
+        case QADIC_E_UNSUPPORTED: return "unsupported by this build";
+        case QADIC_E_CUDA: return "CUDA error";
+        case QADIC_E_DEVICE_TIMEOUT: return "device wait timed out";
+        case QADIC_E_NOMEM: return "out of memory or workspace too small";
+        default: return "unknown status";
+    }
+}
+
+const char *qadic_last_error(void) { return t_last_error.c_str(); }
+
+}  // extern "C"
+
+extern "C" {
+
+size_t qadic_batched_workspace_size(const qadic_gemm_desc *descs, int64_t count) {
+    (void)descs;
+    (void)count;
+    return 0;
+}
+
+int qadic_batched_gemm(const qadic_field *const *fields, int32_t nfields,
+                       const qadic_gemm_desc *descs, int64_t count, void *workspace,
+                       size_t ws_bytes, uint32_t flags, void *stream) {
+    (void)fields; (void)nfields; (void)descs; (void)count; (void)workspace; (void)ws_bytes;
+    (void)flags; (void)stream;
+    return set_error(QADIC_E_UNSUPPORTED, "batched kernel not built yet");
+}
+
+}  // extern "C"

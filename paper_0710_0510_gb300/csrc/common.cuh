@@ -1,0 +1,71 @@
+// Device helpers shared by the kernels of libqadic.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "qadic_internal.h"
+
+namespace qadic {
+
+// Division by an invariant integer d (2 <= d < 2^32) with one multiply-high,
+// after Granlund & Montgomery, "Division by invariant integers using
+// multiplication" (PLDI 1994), Fig. 4.1: with l = ceil(log2 d) and
+// m = floor(2^64 (2^l - d) / d) + 1, floor(n/d) = (t + ((n - t) >> 1)) >> (l-1)
+// where t = mulhi(m, n), for every 64-bit n.
+struct Div64 {
+    uint64_t m;
+    uint32_t sh1, sh2;
+};
+
+inline Div64 make_div64(uint32_t d) {
+    uint32_t l = 0;
+    while ((1ull << l) < d) ++l;
+    const unsigned __int128 two64 = (unsigned __int128)1 << 64;
+    const unsigned __int128 num = two64 * (((unsigned __int128)1 << l) - d);
+    Div64 r;
+    r.m = (uint64_t)(num / d + 1);
+    r.sh1 = l < 1 ? l : 1;
+    r.sh2 = l >= 1 ? l - 1 : 0;
+    return r;
+}
+
+__device__ __forceinline__ uint64_t div64(uint64_t n, const Div64 &d) {
+    const uint64_t t = __umul64hi(d.m, n);
+    return (t + ((n - t) >> d.sh1)) >> d.sh2;
+}
+
+// x mod d for 0 <= x < 2^16 and d < 256: floor(x/d) = mulhi(x, ceil(2^32/d))
+// (the round-up error (m d - 2^32) x / 2^32 < d x / 2^32 stays below 1/d).
+__device__ __forceinline__ uint32_t mod_small(uint32_t x, uint32_t d, uint32_t m32) {
+    return x - d * __umulhi(x, m32);
+}
+
+inline uint32_t make_mod_small(uint32_t d) {
+    return (uint32_t)((((uint64_t)1 << 32) + d - 1) / d);
+}
+
+// Exact integer value of a non-negative double holding an integer < 2^53,
+// read from its bit pattern (no floating-point unit involved).
+__device__ __forceinline__ uint64_t f64_to_u64_exact(double x) {
+    const uint64_t bits = (uint64_t)__double_as_longlong(x);
+    const int e = (int)((bits >> 52) & 0x7ff);
+    if (e < 1023) return 0;   // 0 (or a fraction, never produced here)
+    const uint64_t mant = (bits & ((1ull << 52) - 1)) | (1ull << 52);
+    return mant >> (1075 - e);
+}
+
+// Double holding the integer v < 2^53, built from its bit pattern.
+__device__ __forceinline__ double u64_to_f64_exact(uint64_t v) {
+    if (v == 0) return 0.0;
+    const int top = 63 - __clzll((long long)v);
+    const uint64_t mant = (v << (52 - top)) & ((1ull << 52) - 1);
+    return __longlong_as_double((long long)((((uint64_t)(1023 + top)) << 52) | mant));
+}
+
+__device__ __forceinline__ void record_timeout(int *status, int site) {
+    if (status) atomicCAS(status, 0, site);
+}
+
+}  // namespace qadic

@@ -1,0 +1,226 @@
+// DQT pack (Sec. 2 and Sec. 6, improvement 1: "replace the Horner
+// evaluation by a single table lookup"; Alg. 4 line 1).
+//
+// Inputs: discrete-log codes (uint8/uint16), uint8 coefficient planes in
+// [0, p-1], or int8 coefficient planes (any representative).  Outputs:
+//   QADIC_F64    sum_i c_i q^i as a double (table lookup for logs, shifts for
+//                planes since q = 2^s, Sec. 2)
+//   OPERAND_A    k planes of bf16 centred coefficients, same layout
+//   OPERAND_B    k planes of bf16 centred coefficients, transposed (K-major B)
+//   COEFF_U8     k planes of uint8 coefficients (log input only)
+// The log -> value tables live in shared memory when they fit (96 KB).
+// HBM-bound elementwise work; the transposing variant stages 32 x 32 tiles
+// in shared memory so both the reads and the writes are coalesced.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace qadic {
+
+namespace {
+
+enum InKind { IN_LOG8 = 0, IN_LOG16 = 1, IN_U8 = 2, IN_I8 = 3 };
+enum OutKind { OUT_F64 = 0, OUT_OPA = 1, OUT_OPB = 2, OUT_COEFF = 3 };
+
+constexpr int kTile = 32;
+constexpr int kSmemTableBytes = 96 * 1024;
+
+struct PackParams {
+    int64_t rows, cols, ld_in, ld_out;
+    uint32_t p, k, s, order, h;
+    uint32_t m32;                 // ceil(2^32/p)
+    const double *log_f64;        // global tables
+    const int8_t *log_centred;
+    const uint8_t *antilog;
+    int tables_in_smem;
+};
+
+// Coefficient i of the input element (row r, col c), reduced to [0, p-1].
+template <int IN>
+__device__ __forceinline__ uint32_t coeff_canon(const void *in, const PackParams &P, int64_t r,
+                                                int64_t c, uint32_t i) {
+    if (IN == IN_U8) {
+        return mod_small(__ldg((const uint8_t *)in + ((int64_t)i * P.rows + r) * P.ld_in + c), P.p,
+                         P.m32);
+    } else {
+        const int32_t v = __ldg((const int8_t *)in + ((int64_t)i * P.rows + r) * P.ld_in + c);
+        const uint32_t shifted = (uint32_t)(v + 128 * (int32_t)P.p);   // >= 0, < 2^16
+        return mod_small(shifted, P.p, P.m32);
+    }
+}
+
+__device__ __forceinline__ int32_t centre(uint32_t c, const PackParams &P) {
+    return (P.p > 2 && c > P.h) ? (int32_t)c - (int32_t)P.p : (int32_t)c;
+}
+
+template <int IN>
+__device__ __forceinline__ uint32_t load_code(const void *in, const PackParams &P, int64_t r,
+                                              int64_t c) {
+    if (IN == IN_LOG8) return __ldg((const uint8_t *)in + r * P.ld_in + c);
+    return __ldg((const uint16_t *)in + r * P.ld_in + c);
+}
+
+// Elementwise outputs (F64, OPA, COEFF): one thread per element, 2-D grid.
+template <int IN, int OUT>
+__global__ void __launch_bounds__(256) pack_elementwise(const void *__restrict__ in,
+                                                        void *__restrict__ out, PackParams P) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const double *tf64 = P.log_f64;
+    const int8_t *tcen = P.log_centred;
+    if ((IN == IN_LOG8 || IN == IN_LOG16) && P.tables_in_smem) {
+        if (OUT == OUT_F64) {
+            double *t = (double *)smem;
+            for (uint32_t i = threadIdx.x; i < P.order; i += blockDim.x) t[i] = P.log_f64[i];
+            tf64 = t;
+        } else if (OUT == OUT_OPA) {
+            int8_t *t = (int8_t *)smem;
+            for (uint32_t i = threadIdx.x; i < P.order * P.k; i += blockDim.x)
+                t[i] = P.log_centred[i];
+            tcen = t;
+        }
+        __syncthreads();
+    }
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t r = blockIdx.y + (int64_t)blockIdx.z * gridDim.y;
+    if (c >= P.cols || r >= P.rows) return;
+    if (IN == IN_LOG8 || IN == IN_LOG16) {
+        uint32_t code = load_code<IN>(in, P, r, c);
+        if (code >= P.order) code = P.order - 1;   // out-of-range codes read as zero
+        if (OUT == OUT_F64) {
+            ((double *)out)[r * P.ld_out + c] = tf64[code];
+        } else if (OUT == OUT_OPA) {
+            for (uint32_t i = 0; i < P.k; ++i)
+                ((__nv_bfloat16 *)out)[((int64_t)i * P.rows + r) * P.ld_out + c] =
+                    __int2bfloat16_rn(tcen[code * P.k + i]);
+        } else {
+            for (uint32_t i = 0; i < P.k; ++i)
+                ((uint8_t *)out)[((int64_t)i * P.rows + r) * P.ld_out + c] =
+                    __ldg(P.antilog + code * P.k + i);
+        }
+    } else {
+        if (OUT == OUT_F64) {
+            uint64_t w = 0;
+            for (uint32_t i = 0; i < P.k; ++i) w |= (uint64_t)coeff_canon<IN>(in, P, r, c, i) << (P.s * i);
+            ((double *)out)[r * P.ld_out + c] = (double)w;   // exact: w < 2^53
+        } else {
+            for (uint32_t i = 0; i < P.k; ++i)
+                ((__nv_bfloat16 *)out)[((int64_t)i * P.rows + r) * P.ld_out + c] =
+                    __int2bfloat16_rn(centre(coeff_canon<IN>(in, P, r, c, i), P));
+        }
+    }
+}
+
+// Transposed operand (OPERAND_B): out plane i is cols x rows.
+template <int IN>
+__global__ void __launch_bounds__(kTile * 8) pack_transpose(const void *__restrict__ in,
+                                                           __nv_bfloat16 *__restrict__ out,
+                                                           PackParams P) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ int16_t tile[kMaxK][kTile][kTile + 1];
+    const int8_t *tcen = P.log_centred;
+    if ((IN == IN_LOG8 || IN == IN_LOG16) && P.tables_in_smem) {
+        int8_t *t = (int8_t *)smem;
+        for (uint32_t i = threadIdx.x; i < P.order * P.k; i += blockDim.x) t[i] = P.log_centred[i];
+        tcen = t;
+        __syncthreads();
+    }
+    const int64_t r0 = (int64_t)blockIdx.y * kTile, c0 = (int64_t)blockIdx.x * kTile;
+    const int tx = threadIdx.x % kTile, ty = threadIdx.x / kTile;   // 32 x 8
+    for (int yy = ty; yy < kTile; yy += 8) {
+        const int64_t r = r0 + yy, c = c0 + tx;
+        if (r < P.rows && c < P.cols) {
+            if (IN == IN_LOG8 || IN == IN_LOG16) {
+                uint32_t code = load_code<IN>(in, P, r, c);
+                if (code >= P.order) code = P.order - 1;
+                for (uint32_t i = 0; i < P.k; ++i) tile[i][yy][tx] = tcen[code * P.k + i];
+            } else {
+                for (uint32_t i = 0; i < P.k; ++i)
+                    tile[i][yy][tx] = (int16_t)centre(coeff_canon<IN>(in, P, r, c, i), P);
+            }
+        }
+    }
+    __syncthreads();
+    for (int yy = ty; yy < kTile; yy += 8) {
+        const int64_t oc = c0 + yy, orow = r0 + tx;   // output row = input col
+        if (oc < P.cols && orow < P.rows)
+            for (uint32_t i = 0; i < P.k; ++i)
+                out[((int64_t)i * P.cols + oc) * P.ld_out + orow] = __int2bfloat16_rn(tile[i][tx][yy]);
+    }
+}
+
+template <int IN>
+int dispatch_out(int out_fmt, const void *in, void *out, const PackParams &P0, cudaStream_t stream) {
+    PackParams P = P0;
+    size_t smem = 0;
+    if (IN == IN_LOG8 || IN == IN_LOG16) {
+        const size_t need = (out_fmt == QADIC_FMT_QADIC_F64) ? (size_t)P.order * 8
+                                                              : (size_t)P.order * P.k;
+        P.tables_in_smem = (out_fmt != QADIC_FMT_COEFF_U8) && need <= (size_t)kSmemTableBytes;
+        if (P.tables_in_smem) smem = (need + 15) & ~(size_t)15;
+    }
+    cudaError_t e = cudaSuccess;
+    if (out_fmt == QADIC_FMT_OPERAND_B) {
+        auto kern = pack_transpose<IN>;
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const dim3 grid((unsigned)((P.cols + kTile - 1) / kTile), (unsigned)((P.rows + kTile - 1) / kTile));
+        if (grid.y > 65535) return set_error(QADIC_E_INVALID, "too many rows for the transpose pack");
+        kern<<<grid, kTile * 8, smem, stream>>>(in, (__nv_bfloat16 *)out, P);
+    } else {
+        void (*kern)(const void *, void *, PackParams) = nullptr;
+        if (out_fmt == QADIC_FMT_QADIC_F64) kern = pack_elementwise<IN, OUT_F64>;
+        else if (out_fmt == QADIC_FMT_OPERAND_A) kern = pack_elementwise<IN, OUT_OPA>;
+        else if (out_fmt == QADIC_FMT_COEFF_U8 && (IN == IN_LOG8 || IN == IN_LOG16))
+            kern = pack_elementwise<IN, OUT_COEFF>;
+        else return set_error(QADIC_E_INVALID, "unsupported pack format pair");
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const int64_t gy = std::min<int64_t>(P.rows, 65535);
+        const int64_t gz = (P.rows + gy - 1) / gy;
+        const dim3 grid((unsigned)((P.cols + 255) / 256), (unsigned)gy, (unsigned)gz);
+        kern<<<grid, 256, smem, stream>>>(in, out, P);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(QADIC_E_CUDA, "pack launch: %s", cudaGetErrorString(e));
+    return QADIC_OK;
+}
+
+}  // namespace
+
+int launch_pack(const Field &f, int in_fmt, const void *in, int64_t rows, int64_t cols,
+                int64_t ld_in, int out_fmt, void *out, int64_t ld_out, cudaStream_t stream) {
+    PackParams P;
+    P.rows = rows;
+    P.cols = cols;
+    P.ld_in = ld_in;
+    P.ld_out = ld_out;
+    P.p = f.p;
+    P.k = f.k;
+    P.s = f.log2_q;
+    P.order = f.order;
+    P.h = f.h;
+    P.m32 = make_mod_small(f.p);
+    P.log_f64 = f.d_log_f64;
+    P.log_centred = f.d_log_centred;
+    P.antilog = f.d_antilog;
+    P.tables_in_smem = 0;
+    if (out_fmt < QADIC_FMT_COEFF_U8 || out_fmt > QADIC_FMT_OPERAND_B ||
+        out_fmt == QADIC_FMT_INT8_PLANES)
+        return set_error(QADIC_E_INVALID, "unsupported output format %d", out_fmt);
+    switch (in_fmt) {
+        case QADIC_FMT_LOG:
+            return f.order <= 256 ? dispatch_out<IN_LOG8>(out_fmt, in, out, P, stream)
+                                  : dispatch_out<IN_LOG16>(out_fmt, in, out, P, stream);
+        case QADIC_FMT_COEFF_U8:
+            if (out_fmt == QADIC_FMT_COEFF_U8) break;
+            return dispatch_out<IN_U8>(out_fmt, in, out, P, stream);
+        case QADIC_FMT_INT8_PLANES:
+            if (out_fmt == QADIC_FMT_COEFF_U8) break;
+            return dispatch_out<IN_I8>(out_fmt, in, out, P, stream);
+        default:
+            break;
+    }
+    return set_error(QADIC_E_INVALID, "unsupported pack format pair %d -> %d", in_fmt, out_fmt);
+}
+
+}  // namespace qadic

@@ -1,0 +1,309 @@
+// Standalone REDQ (Alg. 2) over packed FP64 words: for each word
+// r = sum_{j<=d} mu~_j q^j (q = 2^s) produce rho = sum_j (mu~_j mod p) q^j.
+//
+//   rop  = floor(r/p): Lemma 1 (multiply by 1/p rounded up, rounding up,
+//          then floor) -- or an integer multiply-high (QADIC_REDQ_INT_FLOOR)
+//   u_j  = (r >> s j) - p (rop >> s j)                       (Alg. 2, Thm. 2)
+//   mu_d = u_d, mu_j = (u_j - q u_{j+1}) mod p               (Sec. 5.1: Q_d u)
+// with the corrections evaluated per Table 2's time-memory trade-off:
+//   mode 0: arithmetic (d mul/add/mod)
+//   mode 1: p^2 table, d lookups   -- held in registers across the warp and
+//           read with __shfl_sync when p^2 <= 64, else in shared memory
+//   mode 2: p^k' table, ceil(d/(k'-1)) overlapping lookups (Alg. 3)
+//   mode 3: full p^(d+1) table, one lookup returning rho itself
+// Table indices are p-adic, sum u_i p^i (Sec. 5.3).
+//
+// HBM-bound: 8 bytes in and 8 bytes out per word; each thread streams pairs
+// of words with 16-byte loads/stores over a grid sized to the SM count.
+#include "common.cuh"
+
+namespace qadic {
+
+namespace {
+
+constexpr int kThreads = 512;
+
+struct RedqParams {
+    uint32_t p, s, d;          // prime, log2 q, top digit index (ndigits - 1)
+    uint32_t qneg;             // (-q) mod p
+    uint32_t m32;              // ceil(2^32 / p) for mod_small
+    uint32_t kk;               // table width k' (mode 2), d+1 (mode 3)
+    uint32_t table_entries;
+    double inv_p_up;           // 1/p rounded toward +infinity
+    Div64 divp;
+};
+
+template <int MODE, bool INT_FLOOR>
+__device__ __forceinline__ double redq_word(double x, const RedqParams &P, const uint8_t *t1,
+                                            const uint64_t *tk, const double *tfull,
+                                            uint32_t lane_t0, uint32_t lane_t1) {
+    uint64_t r, rop;
+    if (INT_FLOOR) {
+        r = f64_to_u64_exact(x);
+        rop = div64(r, P.divp);
+    } else {
+        r = f64_to_u64_exact(x);
+        // Lemma 1: floor(RU(r * RU(1/p))); the floor of the positive product
+        // is read off its bit pattern (truncation of the fraction bits).
+        rop = f64_to_u64_exact(__dmul_ru(x, P.inv_p_up));
+    }
+    const uint32_t p = P.p, s = P.s, d = P.d;
+    if (MODE == 3) {
+        uint32_t idx = 0, pw = 1;
+        for (uint32_t j = 0; j <= d; ++j) {
+            const uint32_t u = (uint32_t)((r >> (s * j)) - (uint64_t)p * (rop >> (s * j)));
+            idx += u * pw;
+            pw *= p;
+        }
+        return tfull[idx];
+    }
+    if (MODE == 2) {
+        // lookups at starts 0, kk-1, 2(kk-1), ..., the last clipped to d+1-kk
+        const uint32_t kk = P.kk;
+        uint64_t rho = 0;
+        uint32_t start = 0;
+        while (true) {
+            const bool last = start + kk >= d + 1;
+            const uint32_t st = last ? d + 1 - kk : start;
+            uint32_t idx = 0, pw = 1;
+            for (uint32_t j = 0; j < kk; ++j) {
+                const uint32_t sh = s * (st + j);
+                const uint32_t u = (uint32_t)((r >> sh) - (uint64_t)p * (rop >> sh));
+                idx += u * pw;
+                pw *= p;
+            }
+            const uint64_t e = tk[idx];   // mu_0..mu_{kk-1} packed at s-bit spacing
+            if (last) {
+                // keep the positions not written by earlier lookups
+                const uint32_t skip = start - st;
+                const uint64_t keep = e >> (s * skip);
+                rho |= keep << (s * start);
+                break;
+            }
+            rho |= (e & ((1ull << (s * (kk - 1))) - 1)) << (s * st);
+            start += kk - 1;
+        }
+        return u64_to_f64_exact(rho);
+    }
+    // MODE 0 / 1: walk j = d down to 0
+    uint64_t rho = 0;
+    uint32_t u_next = 0;
+    for (int j = (int)d; j >= 0; --j) {
+        const uint32_t sh = s * (uint32_t)j;
+        const uint32_t u = (uint32_t)((r >> sh) - (uint64_t)p * (rop >> sh));
+        uint32_t mu;
+        if (j == (int)d) {
+            mu = u;
+        } else if (MODE == 0) {
+            mu = mod_small(u + P.qneg * u_next, p, P.m32);
+        } else if (t1 == nullptr) {
+            // p^2 <= 64: the table lives in two registers per lane
+            const uint32_t idx = u * p + u_next;
+            const uint32_t lo = __shfl_sync(0xffffffffu, lane_t0, idx & 31);
+            const uint32_t hi = __shfl_sync(0xffffffffu, lane_t1, idx & 31);
+            mu = idx < 32 ? lo : hi;
+        } else {
+            mu = t1[u * p + u_next];
+        }
+        rho |= (uint64_t)mu << sh;
+        u_next = u;
+    }
+    return u64_to_f64_exact(rho);
+}
+
+template <int MODE, bool INT_FLOOR>
+__global__ void __launch_bounds__(kThreads)
+redq_kernel(const double *__restrict__ in, double *__restrict__ out, int64_t count, RedqParams P) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const uint8_t *t1 = nullptr;
+    const uint64_t *tk = nullptr;
+    const double *tfull = nullptr;
+    uint32_t lane_t0 = 0, lane_t1 = 0;
+    const uint32_t p = P.p;
+
+    if (MODE == 1) {
+        if (p * p <= 64) {
+            const uint32_t lane = threadIdx.x & 31;
+            const uint32_t x0 = lane / p, y0 = lane % p, x1 = (lane + 32) / p, y1 = (lane + 32) % p;
+            lane_t0 = lane < p * p ? mod_small(x0 + P.qneg * y0, p, P.m32) : 0;
+            lane_t1 = lane + 32 < p * p ? mod_small(x1 + P.qneg * y1, p, P.m32) : 0;
+        } else {
+            uint8_t *t = smem;
+            for (uint32_t i = threadIdx.x; i < p * p; i += blockDim.x)
+                t[i] = (uint8_t)mod_small(i / p + P.qneg * (i % p), p, P.m32);
+            t1 = t;
+        }
+    } else if (MODE == 2) {
+        // entry for (u_0..u_{kk-1}) = packed (Q_{kk-1} u) at s-bit spacing
+        uint64_t *t = (uint64_t *)smem;
+        for (uint32_t i = threadIdx.x; i < P.table_entries; i += blockDim.x) {
+            uint32_t u[16];
+            uint32_t v = i;
+            for (uint32_t j = 0; j < P.kk; ++j) {
+                u[j] = v % p;
+                v /= p;
+            }
+            uint64_t e = 0;
+            for (uint32_t j = 0; j < P.kk; ++j) {
+                const uint32_t mu = (j + 1 < P.kk) ? mod_small(u[j] + P.qneg * u[j + 1], p, P.m32)
+                                                   : u[j];
+                e |= (uint64_t)mu << (P.s * j);
+            }
+            t[i] = e;
+        }
+        tk = t;
+    } else if (MODE == 3) {
+        double *t = (double *)smem;
+        for (uint32_t i = threadIdx.x; i < P.table_entries; i += blockDim.x) {
+            uint32_t v = i, u_prev = 0;
+            uint64_t rho = 0;
+            uint32_t u[52];
+            for (uint32_t j = 0; j <= P.d; ++j) {
+                u[j] = v % p;
+                v /= p;
+            }
+            for (int j = (int)P.d; j >= 0; --j) {
+                const uint32_t mu =
+                    (j == (int)P.d) ? u[j] : mod_small(u[j] + P.qneg * u_prev, p, P.m32);
+                rho |= (uint64_t)mu << (P.s * j);
+                u_prev = u[j];
+            }
+            t[i] = u64_to_f64_exact(rho);
+        }
+        tfull = t;
+    }
+    __syncthreads();
+
+    // Warp-uniform grid-stride loop (every lane of a warp runs every
+    // iteration, so the shuffle table of mode 1 always sees a full warp);
+    // two 16-byte loads in flight per thread.
+    const int64_t npairs = count >> 1;
+    const double2 *in2 = reinterpret_cast<const double2 *>(in);
+    double2 *out2 = reinterpret_cast<double2 *>(out);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    for (int64_t wb = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); wb < npairs;
+         wb += 2 * stride) {
+        const int64_t i0 = wb + lane, i1 = wb + stride + lane;
+        const double2 w0 = i0 < npairs ? __ldcs(in2 + i0) : make_double2(0.0, 0.0);
+        const double2 w1 = i1 < npairs ? __ldcs(in2 + i1) : make_double2(0.0, 0.0);
+        double2 o0, o1;
+        o0.x = redq_word<MODE, INT_FLOOR>(w0.x, P, t1, tk, tfull, lane_t0, lane_t1);
+        o0.y = redq_word<MODE, INT_FLOOR>(w0.y, P, t1, tk, tfull, lane_t0, lane_t1);
+        o1.x = redq_word<MODE, INT_FLOOR>(w1.x, P, t1, tk, tfull, lane_t0, lane_t1);
+        o1.y = redq_word<MODE, INT_FLOOR>(w1.y, P, t1, tk, tfull, lane_t0, lane_t1);
+        if (i0 < npairs) __stcs(out2 + i0, o0);
+        if (i1 < npairs) __stcs(out2 + i1, o1);
+    }
+    // odd tail word (all lanes take part in the shuffles above; here only
+    // the shuffle-free modes can be used by a single thread)
+    if ((count & 1) && blockIdx.x == 0) {
+        const int64_t j = count - 1;
+        if (MODE == 1 && t1 == nullptr) {
+            const double v = redq_word<MODE, INT_FLOOR>(threadIdx.x < 32 ? in[j] : 0.0, P, t1, tk,
+                                                        tfull, lane_t0, lane_t1);
+            if (threadIdx.x == 0) out[j] = v;
+        } else if (threadIdx.x == 0) {
+            out[j] = redq_word<MODE, INT_FLOOR>(in[j], P, t1, tk, tfull, lane_t0, lane_t1);
+        }
+    }
+}
+
+template <int MODE, bool INT_FLOOR>
+int launch_mode(const double *in, double *out, int64_t count, const RedqParams &P, size_t smem,
+                cudaStream_t stream) {
+    auto kern = redq_kernel<MODE, INT_FLOOR>;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+        return set_error(QADIC_E_CUDA, "redq smem attribute: %s",
+                         cudaGetErrorString(cudaGetLastError()));
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem) !=
+            cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const int64_t npairs = count >> 1;
+    int64_t blocks = (int64_t)sms * per_sm;
+    const int64_t need = (npairs + kThreads - 1) / kThreads;
+    if (need < blocks) blocks = need > 0 ? need : 1;
+    kern<<<(unsigned)blocks, kThreads, smem, stream>>>(in, out, count, P);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(QADIC_E_CUDA, "redq launch: %s", cudaGetErrorString(e));
+    return QADIC_OK;
+}
+
+}  // namespace
+
+int launch_redq(uint32_t p, uint32_t log2_q, uint32_t ndigits, const double *in, double *out,
+                int64_t count, uint32_t table_mode, bool int_floor, cudaStream_t stream) {
+    RedqParams P;
+    P.p = p;
+    P.s = log2_q;
+    P.d = ndigits - 1;
+    const uint64_t q = 1ull << log2_q;
+    P.qneg = (uint32_t)((p - q % p) % p);
+    P.m32 = make_mod_small(p);
+    P.divp = make_div64(p);
+    // 1/p rounded toward +infinity: the nearest double, bumped up one ulp if
+    // it falls below the true 1/p (checked exactly in 128-bit integers).
+    {
+        double inv = 1.0 / (double)p;
+        int e;
+        const double mfrac = frexp(inv, &e);          // inv = mfrac * 2^e, mfrac in [0.5, 1)
+        const uint64_t M = (uint64_t)ldexp(mfrac, 53); // inv = M * 2^(e-53)
+        // inv >= 1/p  <=>  M * p >= 2^(53-e)
+        const unsigned __int128 lhs = (unsigned __int128)M * p;
+        const unsigned __int128 rhs = (unsigned __int128)1 << (53 - e);
+        if (lhs < rhs) inv = nextafter(inv, 2.0);
+        P.inv_p_up = inv;
+    }
+    size_t smem = 0;
+    uint32_t mode = table_mode;
+    if (mode == 3) {
+        uint64_t entries = 1;
+        for (uint32_t j = 0; j < ndigits && entries <= 28000; ++j) entries *= p;
+        if (entries * 8 > 220 * 1024) {
+            mode = 2;   // full table does not fit: fall back to the largest p^k' table
+        } else {
+            P.kk = ndigits;
+            P.table_entries = (uint32_t)entries;
+            smem = entries * 8;
+        }
+    }
+    if (mode == 2) {
+        uint32_t kk = 2;
+        uint64_t entries = (uint64_t)p * p;
+        while (kk < ndigits && entries * p * 8 <= 96 * 1024) {
+            entries *= p;
+            ++kk;
+        }
+        if (ndigits < 2) {
+            mode = 0;
+        } else if (entries * 8 > 96 * 1024) {
+            mode = 1;   // not even a p^2 table of packed words fits: byte table
+        } else {
+            P.kk = kk;
+            P.table_entries = (uint32_t)entries;
+            smem = entries * 8;
+        }
+    }
+    if (mode == 1 && (uint64_t)p * p > 64) smem = ((uint64_t)p * p + 15) & ~15ull;
+    if (int_floor) {
+        switch (mode) {
+            case 0: return launch_mode<0, true>(in, out, count, P, smem, stream);
+            case 1: return launch_mode<1, true>(in, out, count, P, smem, stream);
+            case 2: return launch_mode<2, true>(in, out, count, P, smem, stream);
+            default: return launch_mode<3, true>(in, out, count, P, smem, stream);
+        }
+    }
+    switch (mode) {
+        case 0: return launch_mode<0, false>(in, out, count, P, smem, stream);
+        case 1: return launch_mode<1, false>(in, out, count, P, smem, stream);
+        case 2: return launch_mode<2, false>(in, out, count, P, smem, stream);
+        default: return launch_mode<3, false>(in, out, count, P, smem, stream);
+    }
+}
+
+}  // namespace qadic

@@ -1,0 +1,138 @@
+"""C-ABI library loads and exports every symbol include/qadic.h declares, and
+the host-side logic (field construction, bounds, argument checks) agrees
+with the oracle.  No GPU: host-only field handles, and calls that fail
+their checks before any launch."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_0710_0510_gb300 as q
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "qadic.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(qadic_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(q.build.build())
+    names = declared_functions()
+    assert len(names) >= 14
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_header():
+    assert set(q._SIGS) == set(declared_functions())
+
+
+def test_status_strings():
+    L = q.lib()
+    for s in range(9):
+        assert L.qadic_status_string(s)
+    assert L.qadic_status_string(0) == b"ok"
+
+
+FIELDS = [(3, 3), (101, 2), (251, 2), (2, 8), (7, 4), (31, 2), (5, 3), (2, 4)]
+
+
+@pytest.mark.parametrize("p,k", FIELDS)
+def test_host_field_matches_oracle(orc, p, k):
+    f = q.Field(p, k, host_only=True)
+    assert f.poly == orc.smallest_irreducible(p, k)
+    assert f.generator == orc.generator(p, f.poly)
+    assert f.order == p ** k and f.zero_code == p ** k - 1
+    assert f.log_bytes == (1 if p ** k <= 256 else 2)
+    # q: largest 2^s with (2k-1) s <= 51; n_q: Eq. 2
+    assert (2 * k - 1) * f.log2_q <= 51 < (2 * k - 1) * (f.log2_q + 1)
+    assert f.n_q == (2 ** f.log2_q - 1) // (k * (p - 1) ** 2)
+    assert f.k_max_int32 == orc.delayed_k_bound(p, k, 31)
+    h = 1 if p == 2 else (p - 1) // 2
+    assert 2 * p + k * f.k_chunk_f32 * h * h <= 2 ** 24 < 2 * p + k * (f.k_chunk_f32 + 1) * h * h
+    f.close()
+
+
+@pytest.mark.parametrize("p,k", [(3, 3), (101, 2), (7, 3)])
+def test_fp64_block_matches_eq2_reading(orc, p, k):
+    f = q.Field(p, k, host_only=True)
+    assert (2 ** f.log2_q, f.n_q) == orc.qadic_bounds(p, k, 53)
+
+
+def test_given_polynomial_accepted_and_reducible_rejected():
+    f = q.Field(3, 3, poly=[2, 2, 0, 1], host_only=True)   # X^3 + 2X + 2: no root mod 3
+    assert f.poly == [2, 2, 0, 1]
+    with pytest.raises(q.QadicError) as e:
+        q.Field(3, 3, poly=[1, 0, 0, 1], host_only=True)   # X^3 + 1 = (X+1)^3 mod 3
+    assert e.value.status == q.E_REDUCIBLE
+    with pytest.raises(q.QadicError) as e:
+        q.Field(101, 2, poly=[1, 0, 1], host_only=True)    # X^2 + 1: -1 is a square mod 101
+    assert e.value.status == q.E_REDUCIBLE
+
+
+def test_bad_fields_rejected():
+    for p, k, st in [(4, 2, q.E_NOT_PRIME), (9, 1, q.E_NOT_PRIME), (257, 1, q.E_INVALID),
+                     (3, 0, q.E_INVALID), (2, 17, q.E_INVALID), (251, 3, q.E_INVALID)]:
+        with pytest.raises(q.QadicError) as e:
+            q.Field(p, k, host_only=True)
+        assert e.value.status == st, (p, k)
+
+
+def test_irreducibility_test_agrees_with_oracle(orc):
+    L = q.lib()
+    for p, k in [(2, 4), (3, 3), (3, 4), (5, 2), (7, 2), (2, 6)]:
+        for v in range(p ** k):
+            poly = [(v // p ** i) % p for i in range(k)] + [1]
+            arr = (ctypes.c_uint32 * (k + 1))(*poly)
+            h = ctypes.c_void_p()
+            st = L.qadic_field_init(ctypes.byref(h), p, k, ctypes.cast(arr, ctypes.c_void_p),
+                                    q.FIELD_HOST_ONLY)
+            assert (st == q.OK) == orc.irreducible(p, poly), (p, poly)
+            if st == q.OK:
+                L.qadic_field_destroy(h)
+
+
+def test_host_only_field_rejects_launches():
+    f = q.Field(101, 2, host_only=True)
+    L = q.lib()
+    st = L.qadic_gemm(f.handle, q.PATH_PLANES, 4, 4, 4, ctypes.c_void_p(16), 8,
+                      ctypes.c_void_p(16), 8, ctypes.c_void_p(16), 4, None, 0, None)
+    assert st == q.E_INVALID
+    st = L.qadic_pack(f.handle, q.FMT_LOG, ctypes.c_void_p(16), 4, 4, 4, q.FMT_QADIC_F64,
+                      ctypes.c_void_p(16), 4, None)
+    assert st == q.E_INVALID
+
+
+def test_polymul_plain_fp64_rejected_for_config_sizes():
+    """p = 7, k = 4, q = 2^8: (2k-1) log2 q = 56 >= 53, so the single-rounded
+    product is refused (overflow rejected rather than miscomputed)."""
+    L = q.lib()
+    st = L.qadic_polymul_batched(7, 4, ctypes.c_void_p(16), ctypes.c_void_p(16),
+                                 ctypes.c_void_p(16), 65536, q.POLYMUL_PLAIN_F64, None)
+    assert st == q.E_OVERFLOW
+    assert b"53" in L.qadic_last_error()
+
+
+def test_redq_lemma1_limit_rejected():
+    L = q.lib()
+    # 5 digits of 2^11: 55 bits > 51
+    st = L.qadic_redq(7, 11, 5, ctypes.c_void_p(16), ctypes.c_void_p(16), 10, 3, None)
+    assert st == q.E_OVERFLOW
+    # misaligned pointers
+    st = L.qadic_redq(7, 10, 5, ctypes.c_void_p(8), ctypes.c_void_p(16), 10, 3, None)
+    assert st == q.E_INVALID
+    # q must exceed p
+    st = L.qadic_redq(7, 2, 5, ctypes.c_void_p(16), ctypes.c_void_p(16), 10, 3, None)
+    assert st == q.E_INVALID
+
+
+def test_zero_counts_are_noops():
+    L = q.lib()
+    assert L.qadic_redq(7, 10, 5, None, None, 0, 3, None) == q.OK
+    assert L.qadic_polymul_batched(7, 4, None, None, None, 0, 0, None) == q.OK

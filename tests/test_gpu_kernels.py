@@ -1,0 +1,281 @@
+"""GPU parity: each CUDA kernel, called through the C ABI, against the oracle,
+element by element, bit-exact (all results are integers)."""
+import numpy as np
+import pytest
+
+import paper_0710_0510_gb300 as q
+from paper_0710_0510_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch
+
+
+def dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+# ------------------------------------------------------------ polymul ----
+
+@pytest.mark.parametrize("count", [1, 255, 257, 4099, 65536])
+def test_polymul_config1(torch, orc, count):
+    a, b = W.polymul_pairs(count, 7, 4, salt=count)
+    out = q.polymul_batched(7, 4, dev(torch, a), dev(torch, b))
+    torch.cuda.synchronize()
+    assert np.array_equal(host(out), orc.polymul(7, a, b))
+
+
+def test_polymul_example1(torch):
+    out = q.polymul_batched(3, 2, dev(torch, np.array([[1, 1]], np.uint8)),
+                            dev(torch, np.array([[2, 1]], np.uint8)))
+    assert host(out).tolist() == [[2, 0, 1]]
+
+
+@pytest.mark.parametrize("p,k", [(3, 3), (2, 8), (31, 2), (251, 2), (5, 5), (101, 2)])
+def test_polymul_other_rings(torch, orc, p, k):
+    a, b = W.polymul_pairs(3000, p, k, salt=p * 10 + k)
+    for plain in (False, True):
+        try:
+            out = q.polymul_batched(p, k, dev(torch, a), dev(torch, b), plain_f64=plain)
+        except q.QadicError as e:
+            assert plain and e.status == q.E_OVERFLOW
+            continue
+        assert np.array_equal(host(out), orc.polymul(p, a, b))
+
+
+def test_polymul_all_max(torch, orc):
+    a = np.full((1000, 4), 6, np.uint8)
+    out = q.polymul_batched(7, 4, dev(torch, a), dev(torch, a))
+    assert np.array_equal(host(out), orc.polymul(7, a, a))
+
+
+# --------------------------------------------------------------- REDQ ----
+
+def redq_cases():
+    for mode in (0, 1, 2, 3):
+        for int_floor in (False, True):
+            yield mode, int_floor
+
+
+@pytest.mark.parametrize("mode,int_floor", list(redq_cases()))
+def test_redq_sweep_words(torch, orc, mode, int_floor):
+    w = W.redq_words(100001, 5, 10, salt=mode)   # odd count: ragged tail
+    out = q.redq(7, 10, 5, dev(torch, w), table_mode=mode, int_floor=int_floor)
+    assert np.array_equal(host(out), orc.redq(7, 1024, 4, w))
+
+
+@pytest.mark.parametrize("p,s,nd", [(5, 8, 6), (23, 12, 4), (101, 17, 3), (251, 16, 3),
+                                    (2, 3, 17), (3, 25, 2)])
+def test_redq_other_parameters(torch, orc, p, s, nd):
+    w = W.redq_words(20000, nd, s, salt=p)
+    for mode in (0, 1, 2, 3):
+        for int_floor in (False, True):
+            out = q.redq(p, s, nd, dev(torch, w), table_mode=mode, int_floor=int_floor)
+            assert np.array_equal(host(out), orc.redq(p, 2 ** s, nd - 1, w)), (mode, int_floor)
+
+
+def test_redq_adversarial_words(torch, orc):
+    p, s, nd = 7, 10, 5
+    q_ = 1 << s
+    digs = [[q_ - 1] * nd, [0] * nd, [p - 1] * nd, [2 * p - 1] * nd, [q_ - 2] * nd,
+            [p * (q_ // p) - 1] * nd, [q_ - 1, 0, q_ - 1, 0, q_ - 1]]
+    words = np.array([sum(d * q_ ** i for i, d in enumerate(x)) for x in digs] * 3,
+                     dtype=np.float64)
+    top = float(2 ** 50 - 1)
+    words = np.concatenate([words, [top, top - 1, 1.0]])
+    for mode in (0, 1, 2, 3):
+        for int_floor in (False, True):
+            out = q.redq(p, s, nd, dev(torch, words), table_mode=mode, int_floor=int_floor)
+            assert np.array_equal(host(out), orc.redq(p, q_, nd - 1, words))
+
+
+# --------------------------------------------------------------- pack ----
+
+@pytest.mark.parametrize("pk", [(3, 3), (101, 2), (7, 4), (2, 8), (251, 2)])
+def test_pack_log_formats(torch, orc, pk):
+    p, k = pk
+    f = q.Field(p, k)
+    T = orc.antilog(p, f.poly)                       # oracle's own generator
+    rows, cols = 37, 70
+    L = W.log_matrix(rows, cols, f.order, salt=p)
+    x = dev(torch, L)
+    coeff = T[L.astype(np.int64)]                    # (rows, cols, k)
+    got = host(f.pack(q.FMT_LOG, x, rows, cols, q.FMT_COEFF_U8))
+    assert np.array_equal(got, np.transpose(coeff, (2, 0, 1)))
+    cen = orc.centred(coeff, p)
+    got = host(f.pack(q.FMT_LOG, x, rows, cols, q.FMT_OPERAND_A, ld_out=72,
+                      out=torch.empty((k, rows, 72), dtype=torch.bfloat16, device="cuda")).float())
+    assert np.array_equal(got[:, :, :cols], np.transpose(cen, (2, 0, 1)))
+    got = host(f.pack(q.FMT_LOG, x, rows, cols, q.FMT_OPERAND_B, ld_out=40,
+                      out=torch.empty((k, cols, 40), dtype=torch.bfloat16, device="cuda")).float())
+    assert np.array_equal(got[:, :, :rows], np.transpose(cen, (2, 1, 0)))
+    if f.n_q > 0:
+        got = host(f.pack(q.FMT_LOG, x, rows, cols, q.FMT_QADIC_F64))
+        assert np.array_equal(got.astype(np.int64), orc.qadic_value(coeff, 2 ** f.log2_q))
+
+
+@pytest.mark.parametrize("pk", [(101, 2), (251, 2), (3, 3)])
+def test_pack_plane_formats(torch, orc, pk):
+    p, k = pk
+    f = q.Field(p, k)
+    rows, cols = 45, 66
+    I8 = np.random.default_rng(p).integers(-128, 128, (k, rows, cols), dtype=np.int8)
+    U8 = W.coeff_planes(k, rows, cols, p, salt=p)
+    for fmt, X in ((q.FMT_INT8_PLANES, I8), (q.FMT_COEFF_U8, U8)):
+        canon = np.transpose(X.astype(np.int64) % p, (1, 2, 0))   # (rows, cols, k)
+        x = dev(torch, X)
+        got = host(f.pack(fmt, x, rows, cols, q.FMT_QADIC_F64))
+        assert np.array_equal(got.astype(np.int64), orc.qadic_value(canon, 2 ** f.log2_q))
+        cen = orc.centred(canon, p)
+        got = host(f.pack(fmt, x, rows, cols, q.FMT_OPERAND_A, ld_out=72,
+                          out=torch.empty((k, rows, 72), dtype=torch.bfloat16, device="cuda")).float())
+        assert np.array_equal(got[:, :, :cols], np.transpose(cen, (2, 0, 1)))
+        got = host(f.pack(fmt, x, rows, cols, q.FMT_OPERAND_B, ld_out=48,
+                          out=torch.empty((k, cols, 48), dtype=torch.bfloat16, device="cuda")).float())
+        assert np.array_equal(got[:, :, :rows], np.transpose(cen, (2, 1, 0)))
+
+
+# ----------------------------------------------------- GEMM helpers ----
+
+def oracle_gemm_from_planes(orc, p, poly, Ap, Bp):
+    """Ap: (k, m, K), Bp: (k, K, n) integer planes -> (k, m, n)."""
+    C = orc.gemm(p, poly, np.transpose(Ap, (1, 2, 0)), np.transpose(Bp, (1, 2, 0)))
+    return np.transpose(C, (2, 0, 1))
+
+
+def run_fp64(torch, f, fmt, A, B, m, n, K):
+    a = f.pack(fmt, dev(torch, A), m, K, q.FMT_QADIC_F64)
+    b = f.pack(fmt, dev(torch, B), K, n, q.FMT_QADIC_F64)
+    return host(f.gemm(q.PATH_FP64_QADIC, a, b, m, n, K))
+
+
+def run_planes(torch, f, fmt, A, B, m, n, K):
+    Kp = (K + 7) // 8 * 8
+    a = torch.zeros((f.k, m, Kp), dtype=torch.bfloat16, device="cuda")
+    b = torch.zeros((f.k, n, Kp), dtype=torch.bfloat16, device="cuda")
+    f.pack(fmt, dev(torch, A), m, K, q.FMT_OPERAND_A, out=a, ld_out=Kp)
+    f.pack(fmt, dev(torch, B), K, n, q.FMT_OPERAND_B, out=b, ld_out=Kp)
+    return host(f.gemm(q.PATH_PLANES, a, b, m, n, K, lda=Kp, ldb=Kp))
+
+
+# ----------------------------------------------------------- FP64 GEMM ----
+
+@pytest.mark.parametrize("shape", [(70, 45, 200), (64, 64, 85), (1, 1, 1), (130, 3, 171),
+                                   (5, 129, 86)])
+def test_gemm_fp64_gf27_log(torch, orc, shape):
+    m, n, K = shape
+    f = q.Field(3, 3)
+    assert (f.log2_q, f.n_q) == (10, 85)
+    T = orc.antilog(3, f.poly)
+    A = W.log_matrix(m, K, 27, salt=m)
+    B = W.log_matrix(K, n, 27, salt=n + 1)
+    got = run_fp64(torch, f, q.FMT_LOG, A, B, m, n, K)
+    want = orc.gemm(3, f.poly, T[A.astype(np.int64)], T[B.astype(np.int64)])
+    assert np.array_equal(got, np.transpose(want, (2, 0, 1)))
+
+
+@pytest.mark.parametrize("pk,shape", [((101, 2), (67, 70, 333)), ((7, 4), (40, 33, 50)),
+                                      ((31, 2), (33, 65, 257)), ((251, 2), (20, 20, 40))])
+def test_gemm_fp64_planes_input(torch, orc, pk, shape):
+    p, k = pk
+    m, n, K = shape
+    f = q.Field(p, k)
+    h = (p - 1) // 2
+    A = W.centred_planes(k, m, K, h, salt=1)
+    B = W.centred_planes(k, K, n, h, salt=2)
+    got = run_fp64(torch, f, q.FMT_INT8_PLANES, A, B, m, n, K)
+    assert np.array_equal(got, oracle_gemm_from_planes(orc, p, f.poly, A, B))
+
+
+def test_gemm_fp64_all_max(torch, orc):
+    """All coefficients p-1: every block sum sits at the Eq. 2 limit."""
+    p, k = 101, 2
+    f = q.Field(p, k)
+    m, n, K = 16, 16, 6 * 7 + 5
+    A = np.full((k, m, K), p - 1, np.uint8)
+    B = np.full((k, K, n), p - 1, np.uint8)
+    got = run_fp64(torch, f, q.FMT_COEFF_U8, A, B, m, n, K)
+    assert np.array_equal(got, oracle_gemm_from_planes(orc, p, f.poly, A, B))
+
+
+# ------------------------------------------------ tensor-core plane GEMM ----
+
+@pytest.mark.parametrize("shape", [(128, 128, 64), (293, 261, 209), (1, 1, 1), (128, 256, 8),
+                                   (200, 129, 1000), (384, 384, 4096 + 64 * 3 + 5)])
+def test_gemm_planes_gf101_2(torch, orc, shape):
+    m, n, K = shape
+    p, k = 101, 2
+    f = q.Field(p, k)
+    A = W.centred_planes(k, m, K, 50, salt=m)
+    B = W.centred_planes(k, K, n, 50, salt=n)
+    got = run_planes(torch, f, q.FMT_INT8_PLANES, A, B, m, n, K)
+    assert np.array_equal(got, oracle_gemm_from_planes(orc, p, f.poly, A, B))
+
+
+@pytest.mark.parametrize("shape", [(130, 140, 2000), (128, 128, 512), (64, 300, 1537)])
+def test_gemm_planes_gf251_2_drains(torch, orc, shape):
+    """p = 251: the exact FP32 chunk is 536 -> 8 K-blocks, so K = 2000 crosses
+    three in-place reductions."""
+    m, n, K = shape
+    p, k = 251, 2
+    f = q.Field(p, k)
+    A = W.centred_planes(k, m, K, 125, salt=K)
+    B = W.centred_planes(k, K, n, 125, salt=K + 1)
+    got = run_planes(torch, f, q.FMT_INT8_PLANES, A, B, m, n, K)
+    assert np.array_equal(got, oracle_gemm_from_planes(orc, p, f.poly, A, B))
+
+
+@pytest.mark.parametrize("p,val", [(251, 125), (251, -125), (101, 50), (101, -50)])
+def test_gemm_planes_sums_at_the_fp32_limit(torch, orc, p, val):
+    """All coefficients at +-h with the same sign: every accumulator grows by
+    the maximum k h^2 per K step, reaching the 2^24 bound at each chunk end."""
+    k = 2
+    f = q.Field(p, k)
+    m, n = 128, 128
+    K = 3 * f.k_chunk_f32 // 64 * 64 + 64
+    A = np.full((k, m, K), val, np.int8)
+    B = np.full((k, K, n), val, np.int8)
+    got = run_planes(torch, f, q.FMT_INT8_PLANES, A, B, m, n, K)
+    full = oracle_gemm_from_planes(orc, p, f.poly, A[:, :2, :], B[:, :, :2])
+    assert np.array_equal(got[:, :2, :2], full)
+    assert (got == got[:, :1, :1]).all()
+
+
+def test_gemm_planes_k0_gives_zero(torch):
+    f = q.Field(101, 2)
+    a = torch.zeros((2, 4, 8), dtype=torch.bfloat16, device="cuda")
+    b = torch.zeros((2, 4, 8), dtype=torch.bfloat16, device="cuda")
+    C = torch.full((2, 4, 4), 7, dtype=torch.uint8, device="cuda")
+    f.gemm(q.PATH_PLANES, a, b, 4, 4, 0, C=C, lda=8, ldb=8)
+    assert not host(C).any()
+
+
+def test_fp64_and_planes_agree_config3_slice(torch, orc):
+    """The two contraction forms on the same inputs (GF(101^2))."""
+    p, k = 101, 2
+    f = q.Field(p, k)
+    m, n, K = 256, 192, 1024
+    A = W.centred_planes(k, m, K, 50, salt=5)
+    B = W.centred_planes(k, K, n, 50, salt=6)
+    g1 = run_planes(torch, f, q.FMT_INT8_PLANES, A, B, m, n, K)
+    g2 = run_fp64(torch, f, q.FMT_INT8_PLANES, A, B, m, n, K)
+    assert np.array_equal(g1, g2)
+    ii = np.arange(0, m, 17)
+    jj = np.arange(0, n, 13)[: len(ii)]
+    ii = ii[: len(jj)]
+    want = orc.gemm_entries(p, f.poly, np.transpose(A, (1, 2, 0)), np.transpose(B, (1, 2, 0)),
+                            ii, jj)
+    assert np.array_equal(g1[:, ii, jj].T, want)
+
+
+def test_sync_status_clean(torch):
+    q.sync_status()
