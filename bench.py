@@ -1,0 +1,469 @@
+"""Benchmark: GF(p^k) matmul field Gop/s (coefficient-plane tensor-core form
+vs FP64 q-adic form) and REDQ residues/s, on one GB300 (or N replicas).
+
+One step = one pass of the whole hot path over one batch of synthetic input:
+  plane   GF(101^2), n = 4096: DQT pack of A and B (int8 centred planes ->
+          bf16 operand planes) + tensor-core plane GEMM with the fused
+          mod-p / mod-P epilogue.                           [headline]
+Measured beside it (each a full path of its own, reported as extra keys):
+  fp64    the FP64 q-adic form on the same inputs (pack -> FP64 GEMM with
+          REDQ after every n_q = 6 products)
+  redq    standalone REDQ over 2^28 packed words (p = 7, q = 2^10, 5 digits)
+  polymul 65,536 degree-3 products over Z/7 (Alg. 1 + Alg. 2)
+  large   GF(251^2), n = 16384 plane form
+  batched 4096 uneven products over GF(2^8), GF(7^4), GF(31^2), one launch
+
+`--workload NAME` runs NAME alone as the headline (same JSON contract).
+`--impl reference` times the oracle (plain CPU schoolbook arithmetic) on a
+bounded sample of the same workload.
+Inputs are seeded synthetic data shaped like the paper's workloads.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FLUSH_NOTE = "inputs larger than L2 (129 MB)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="plane",
+                    choices=["plane", "fp64", "redq", "polymul", "large", "batched"])
+    ap.add_argument("--n", type=int, default=None, help="override the matrix size")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------ distributed --
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, None
+    import torch
+    import torch.distributed as dist
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if torch.cuda.is_available():
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dist.init_process_group(backend)
+    return dist.get_rank(), dist.get_world_size(), dist
+
+
+def reduce_max(x: float, dist) -> float:
+    if dist is None:
+        return x
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- clocks --
+
+class Clocks:
+    """nvidia-smi sampled every 200 ms during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        sms, maxs, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                maxs.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sms:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxs),
+                "reasons": sorted(reasons), "samples": len(sms)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return {"hbm_gbs": d["hbm_gbs"], "bf16": d["bf16_tflops"],
+                "bf16_sustained": d.get("bf16_tflops_sustained", d["bf16_tflops"]),
+                "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16": 1900.0, "bf16_sustained": 1700.0, "source": "fallback"}
+
+
+# -------------------------------------------------------------- timing --
+
+def time_steps(torch, step, steps, warmup, dist, kernel_events=None):
+    """Run `warmup` untimed steps then `steps` timed steps bracketed by a
+    barrier and a synchronize; returns (total ms max over ranks, kernel ms
+    per launch or None)."""
+    for _ in range(warmup):
+        step(None)
+    torch.cuda.synchronize()
+    barrier(dist)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    kev = [] if kernel_events else None
+    start.record(stream)
+    for _ in range(steps):
+        step(kev)
+    end.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    total = reduce_max(start.elapsed_time(end), dist)
+    kms = None
+    if kev:
+        kms = sum(a.elapsed_time(b) for a, b in kev) / len(kev)
+    return total, kms
+
+
+def ev_pair(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+# ------------------------------------------------------------ workloads --
+
+def make_plane_workload(torch, q, W, p, n, salt=0):
+    k = 2
+    h = (p - 1) // 2
+    f = q.Field(p, k)
+    A = W.centred_planes(k, n, n, h, index=2, salt=salt)
+    B = W.centred_planes(k, n, n, h, index=2, salt=salt + 1)
+    dA = torch.from_numpy(A).cuda()
+    dB = torch.from_numpy(B).cuda()
+    opA = torch.empty((k, n, n), dtype=torch.bfloat16, device="cuda")
+    opB = torch.empty((k, n, n), dtype=torch.bfloat16, device="cuda")
+    C = torch.empty((k, n, n), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(kev):
+        f.pack(q.FMT_INT8_PLANES, dA, n, n, q.FMT_OPERAND_A, out=opA)
+        f.pack(q.FMT_INT8_PLANES, dB, n, n, q.FMT_OPERAND_B, out=opB)
+        if kev is not None:
+            a, b = ev_pair(torch)
+            a.record(stream)
+        f.gemm(q.PATH_PLANES, opA, opB, n, n, n, C=C)
+        if kev is not None:
+            b.record(stream)
+            kev.append((a, b))
+
+    return f, A, B, C, step
+
+
+def bench_plane(args, torch, q, W, dist, p=101, n=4096, name="plane"):
+    if args.n:
+        n = args.n
+    f, A, B, C, step = make_plane_workload(torch, q, W, p, n)
+    total, kms = time_steps(torch, step, args.steps, args.warmup, dist, kernel_events=True)
+    ms = total / args.steps
+    field_ops = 2.0 * n ** 3
+    flops = 4 * 2.0 * n ** 3          # k^2 plane products
+    pk = peaks()
+    achieved = flops / (kms * 1e-3) / 1e12
+    res = {
+        "ms_per_step": ms, "value": field_ops / (ms * 1e-3) / 1e9, "n": n, "p": p,
+        "kernel_ms": kms,
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": pk["bf16_sustained"],
+                     "unit": "TFLOP/s", "frac": achieved / pk["bf16_sustained"],
+                     "traffic": None, "kernel": "gemm_planes_tc_kernel<2,128>",
+                     "peak_source": pk["source"] + " bf16 sustained (cuBLAS)"},
+        "gpu_launches": 3 * args.steps,
+    }
+    return f, A, B, C, res
+
+
+def bench_fp64(args, torch, q, W, f, A, B, n, reps=2):
+    """FP64 q-adic form on the same inputs (pack + FP64 GEMM with REDQ)."""
+    k = f.k
+    dA = torch.from_numpy(A).cuda()
+    dB = torch.from_numpy(B).cuda()
+    a64 = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    b64 = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    C = torch.empty((k, n, n), dtype=torch.uint8, device="cuda")
+
+    def step(kev):
+        f.pack(q.FMT_INT8_PLANES, dA, n, n, q.FMT_QADIC_F64, out=a64)
+        f.pack(q.FMT_INT8_PLANES, dB, n, n, q.FMT_QADIC_F64, out=b64)
+        f.gemm(q.PATH_FP64_QADIC, a64, b64, n, n, n, C=C)
+
+    total, _ = time_steps(torch, step, reps, 1, None)
+    ms = total / reps
+    fl = 2.0 * n ** 3
+    return C, {"value": fl / (ms * 1e-3) / 1e9, "unit": "field Gop/s", "ms_per_step": ms,
+               "fp64_tflops": fl / (ms * 1e-3) / 1e12, "n_q": f.n_q, "log2_q": f.log2_q}
+
+
+def bench_redq(args, torch, q, W, count=1 << 28, steps=10):
+    w = W.redq_words(count, 5, 10)
+    d = torch.from_numpy(w).cuda()
+    out = torch.empty_like(d)
+    res = {}
+    best = None
+    for mode in (3, 1, 0, 2):
+        for int_floor in (False, True):
+            def step(kev):
+                q.redq(7, 10, 5, d, out=out, table_mode=mode, int_floor=int_floor)
+            total, _ = time_steps(torch, step, steps, 3, None)
+            ms = total / steps
+            gbs = 16.0 * count / (ms * 1e-3) / 1e9
+            key = f"mode{mode}{'_int' if int_floor else '_lemma1'}"
+            res[key] = {"ms": ms, "GB/s": gbs}
+            if best is None or ms < best[1]:
+                best = (key, ms)
+    key, ms = best
+    pk = peaks()
+    gbs = 16.0 * count / (ms * 1e-3) / 1e9
+    return d, out, {"value": 5.0 * count / (ms * 1e-3), "unit": "residues/s", "best": key,
+                    "ms": ms, "words": count,
+                    "roofline": {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"],
+                                 "unit": "GB/s", "frac": gbs / pk["hbm_gbs"], "traffic": None},
+                    "variants": res}
+
+
+def bench_polymul(args, torch, q, W, count=65536, steps=50):
+    a, b = W.polymul_pairs(count, 7, 4)
+    da = torch.from_numpy(a).cuda()
+    db = torch.from_numpy(b).cuda()
+    out = torch.empty((count, 7), dtype=torch.uint8, device="cuda")
+
+    def step(kev):
+        q.polymul_batched(7, 4, da, db, out=out)
+
+    total, _ = time_steps(torch, step, steps, 3, None)
+    ms = total / steps
+    return a, b, out, {"value": count / (ms * 1e-3), "unit": "products/s", "us_per_batch": ms * 1e3,
+                       "residues_per_s": 7 * count / (ms * 1e-3)}
+
+
+def e2e_plane(args, torch, q, W, f, A, B, n):
+    """Same metric through qadic_matmul_host: pinned host inputs, H2D copies,
+    pack, GEMM, D2H of C, all inside the timed region."""
+    k = f.k
+    hA = torch.from_numpy(A).pin_memory()
+    hB = torch.from_numpy(B).pin_memory()
+    hC = torch.empty((k, n, n), dtype=torch.uint8).pin_memory()
+    ws = torch.empty(f.matmul_workspace_size(q.PATH_PLANES, q.FMT_INT8_PLANES, n, n, n),
+                     dtype=torch.uint8, device="cuda")
+
+    def step(kev):
+        f.matmul_host(q.PATH_PLANES, q.FMT_INT8_PLANES, hA, hB, hC, n, n, n, ws)
+
+    total, _ = time_steps(torch, step, max(3, args.steps // 2), 2, None)
+    ms = total / max(3, args.steps // 2)
+    return hC, {"value": 2.0 * n ** 3 / (ms * 1e-3) / 1e9, "unit": "field Gop/s",
+                "h2d_bytes_per_step": int(A.nbytes + B.nbytes), "d2h_bytes_per_step": int(hC.numel()),
+                "ms_per_step": ms}
+
+
+def sampled_parity(orc, f, A, B, C_dev, samples=512, seed=1):
+    import numpy as np
+    n = A.shape[1]
+    rng = np.random.default_rng(seed)
+    ii = rng.integers(0, n, samples)
+    jj = rng.integers(0, A.shape[2] if B is None else B.shape[2], samples)
+    C = C_dev.cpu().numpy()
+    want = orc.gemm_entries(f.p, f.poly, np.transpose(A, (1, 2, 0)), np.transpose(B, (1, 2, 0)),
+                            ii, jj)
+    return bool(np.array_equal(C[:, ii, jj].T, want))
+
+
+# ------------------------------------------------------------ CPU oracle --
+
+def cpu_baseline_plane(p, n, target_s=12.0):
+    """Oracle (plain C schoolbook, OpenMP) on a bounded sample of the n x n
+    workload: whole output rows, field Gop/s scaled by the ops done."""
+    import numpy as np
+    import oracle
+    from paper_0710_0510_gb300 import workloads as W
+    oracle.build()
+    k = 2
+    h = (p - 1) // 2
+    poly = oracle.smallest_irreducible(p, k)
+    B = W.centred_planes(k, n, n, h, index=2, salt=1)
+    Bt = np.ascontiguousarray(np.transpose(B, (1, 2, 0)))          # (K, n, k)
+    rows = 2
+    spent = 0.0
+    done = 0
+    while True:
+        A = W.centred_planes(k, rows, n, h, index=2, salt=0)        # rows of the same law
+        Ar = np.ascontiguousarray(np.transpose(A, (1, 2, 0)))
+        t0 = time.perf_counter()
+        oracle.gemm(p, poly, Ar, Bt)
+        dt = time.perf_counter() - t0
+        spent, done = dt, rows
+        if dt > target_s / 4 or rows >= n:
+            break
+        rows = min(n, max(rows * 2, int(rows * target_s / 4 / max(dt, 1e-3))))
+    ops = 2.0 * done * n * n
+    return {"value": ops / spent / 1e9, "unit": "field Gop/s", "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": f"{done} of {n} output rows of the n={n} GF({p}^2) product "
+                                        f"({spent:.1f} s)"}
+
+
+def run_reference(args):
+    rank, world, dist = 0, 1, None
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        rank = int(os.environ.get("RANK", "0"))
+        if rank != 0:
+            return 0
+    p, n = (101, args.n or 4096)
+    vals = []
+    cb = None
+    for _ in range(args.warmup):
+        cpu_baseline_plane(p, n, target_s=2.0)
+    for _ in range(args.steps):
+        cb = cpu_baseline_plane(p, n, target_s=5.0)
+        vals.append(cb["value"])
+    value = statistics.median(vals)
+    cb["value"] = value
+    line = {"impl": "reference", "metric": "GF(p^k) matmul field Gop/s (GF(101^2), n=4096)",
+            "value": value, "unit": "field Gop/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": f"GF(101^2) n={n} schoolbook oracle (CPU)", "p": 101, "k": 2,
+                       "n": n},
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": "field Gop/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ main --
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, world, dist = dist_setup()
+    import torch
+    import paper_0710_0510_gb300 as q
+    from paper_0710_0510_gb300 import workloads as W
+    assert torch.cuda.is_available(), "bench.py needs a CUDA device"
+    dev_index = torch.cuda.current_device()
+    uuid = getattr(torch.cuda.get_device_properties(dev_index), "uuid", None)
+    smi_id = f"GPU-{uuid}" if uuid else str(dev_index)
+    q.lib()
+    import oracle   # sampled parity check and the CPU-baseline leg only
+    oracle.build()
+
+    line = {"metric": "GF(p^k) matmul field Gop/s, INT8-plane vs FP64 q-adic; REDQ residues/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "data": "synthetic (seeded, shaped like the paper's workloads)"}
+    extras = {}
+    with Clocks(smi_id) as clk:
+        if args.workload == "plane":
+            f, A, B, C, res = bench_plane(args, torch, q, W, dist)
+            n = res["n"]
+            line.update({"value": res["value"] * world, "unit": "field Gop/s",
+                         "ms_per_step": res["ms_per_step"], "dtype": "bf16 (exact small integers), "
+                         "f32 accumulate", "roofline": res["roofline"],
+                         "gpu_launches": res["gpu_launches"]})
+            line["config"] = {"workload": f"GF(101^2) n={n}: pack A,B (int8 centred planes -> bf16 "
+                              f"operands) + tcgen05 plane GEMM + fused mod-p/mod-P epilogue",
+                              "p": 101, "k": 2, "n": n, "l2": FLUSH_NOTE}
+            extras["parity_sampled"] = sampled_parity(oracle, f, A, B, C)
+            if rank == 0:
+                C64, fp = bench_fp64(args, torch, q, W, f, A, B, n)
+                fp["bitexact_vs_plane"] = bool(torch.equal(C64, C))
+                extras["fp64_qadic"] = fp
+                extras["plane_over_fp64"] = res["value"] / fp["value"]
+                hC, e2e = e2e_plane(args, torch, q, W, f, A, B, n)
+                e2e["bitexact"] = bool(torch.equal(hC, C.cpu()))
+                line["e2e"] = e2e
+        elif args.workload == "redq":
+            d, out, r = bench_redq(args, torch, q, W)
+            line.update({"value": r["value"] * world, "unit": "residues/s", "ms_per_step": r["ms"],
+                         "dtype": "f64 words, integer REDQ", "roofline": r["roofline"],
+                         "gpu_launches": args.steps})
+            line["config"] = {"workload": "REDQ sweep: 2^28 FP64 words, 5 digits, p=7, q=2^10",
+                              "l2": FLUSH_NOTE}
+            extras["redq_variants"] = r["variants"]
+        elif args.workload == "polymul":
+            a, b, out, r = bench_polymul(args, torch, q, W)
+            line.update({"value": r["value"] * world, "unit": "products/s",
+                         "ms_per_step": r["us_per_batch"] / 1e3, "dtype": "f64 product, u64 REDQ",
+                         "gpu_launches": 50})
+            line["config"] = {"workload": "65,536 pairs of degree-3 polynomials over Z/7, q=2^8"}
+            extras["parity"] = bool((out.cpu().numpy() == oracle.polymul(7, a, b)).all())
+        elif args.workload == "large":
+            f, A, B, C, res = bench_plane(args, torch, q, W, dist, p=251, n=args.n or 16384)
+            line.update({"value": res["value"] * world, "unit": "field Gop/s",
+                         "ms_per_step": res["ms_per_step"], "dtype": "bf16 exact, f32 accumulate",
+                         "roofline": res["roofline"], "gpu_launches": res["gpu_launches"]})
+            line["config"] = {"workload": f"GF(251^2) n={res['n']} plane form", "p": 251, "k": 2,
+                              "n": res["n"], "l2": FLUSH_NOTE}
+            extras["parity_sampled"] = sampled_parity(oracle, f, A, B, C, samples=256)
+        else:
+            raise SystemExit(f"workload {args.workload} not available")
+    line["clocks"] = clk.summary()
+    if args.workload == "plane" and rank == 0:
+        r2 = bench_redq(args, torch, q, W)[2]
+        extras["redq"] = {k: r2[k] for k in ("value", "unit", "best", "ms", "roofline")}
+        pm = bench_polymul(args, torch, q, W)
+        extras["polymul"] = pm[3]
+        extras["polymul"]["parity"] = bool((pm[2].cpu().numpy() == oracle.polymul(7, pm[0], pm[1])).all())
+    if rank == 0:
+        if args.workload == "plane":
+            line["cpu_baseline"] = cpu_baseline_plane(101, line["config"]["n"])
+        line.update(extras)
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

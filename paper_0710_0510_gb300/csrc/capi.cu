@@ -359,17 +359,24 @@ const char *qadic_last_error(void) { return t_last_error.c_str(); }
 extern "C" {
 
 size_t qadic_batched_workspace_size(const qadic_gemm_desc *descs, int64_t count) {
-    (void)descs;
-    (void)count;
-    return 0;
+    return batched_workspace_size(descs, count);
 }
 
 int qadic_batched_gemm(const qadic_field *const *fields, int32_t nfields,
                        const qadic_gemm_desc *descs, int64_t count, void *workspace,
                        size_t ws_bytes, uint32_t flags, void *stream) {
-    (void)fields; (void)nfields; (void)descs; (void)count; (void)workspace; (void)ws_bytes;
-    (void)flags; (void)stream;
-    return set_error(QADIC_E_UNSUPPORTED, "batched kernel not built yet");
+    if (count < 0) return set_error(QADIC_E_INVALID, "negative count");
+    if (count == 0) return QADIC_OK;
+    if (!fields || !descs) return set_error(QADIC_E_INVALID, "NULL fields or descs");
+    if (flags & ~QADIC_BATCHED_GRAPH) return set_error(QADIC_E_INVALID, "unknown flags");
+    if (nfields < 1 || nfields > 64) return set_error(QADIC_E_INVALID, "nfields outside [1, 64]");
+    const Field *fs[64];
+    for (int32_t i = 0; i < nfields; ++i) {
+        if (!fields[i]) return set_error(QADIC_E_INVALID, "field %d is NULL", i);
+        fs[i] = &fields[i]->f;
+    }
+    return launch_batched(fs, nfields, descs, count, workspace, ws_bytes,
+                          (flags & QADIC_BATCHED_GRAPH) != 0, (cudaStream_t)stream);
 }
 
 }  // extern "C"

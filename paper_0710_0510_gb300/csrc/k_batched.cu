@@ -1,0 +1,467 @@
+// Many independent GF(p^k) products in one persistent launch.
+//
+// Each product C = A B is the coefficient-plane form of Eq. 1: 2k-1 plane
+// sums C_t = sum_{i+j=t} A_i B_j, reduced mod p and folded mod P with
+// X^t mod P.  The host lays a work list into the caller's workspace: field
+// parameters, product descriptors and one entry per output tile, sorted by
+// decreasing work.  A grid of (SMs x resident blocks) CTAs pulls tiles with
+// one atomicAdd each (no waits of any kind), so thousands of uneven products
+// (m, n, K in [16, 256], three different fields) share one launch.
+//
+// Per tile: uint8 coefficient tiles are staged in shared memory as centred
+// bf16 (exact small integers), multiplied with warp-level mma.sync
+// (m16n8k16, bf16 -> f32; the tiles are too small for 128-row tcgen05
+// MMAs), accumulated exactly in FP32 registers (every partial sum stays
+// within 2^24; at each exact chunk the accumulators are reduced mod p in
+// place), then reduced mod p, folded and written as uint8 planes.  The
+// tile shape follows k so that the 2k-1 accumulator sets fit in registers.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+
+namespace qadic {
+
+namespace {
+
+constexpr int kThreads = 128;
+constexpr int BK = 32;
+constexpr int kMaxFields = 64;
+
+struct BFieldParams {
+    uint32_t p, k, h, m32;
+    float pf, inv_pf;
+    int32_t chunk_blocks;          // BK-blocks per exact FP32 chunk
+    int32_t pad;
+    uint8_t fold[kMaxK * kMaxK];   // X^(k+t) mod P, row t (k coefficients)
+};
+
+struct BProd {
+    const uint8_t *A;
+    const uint8_t *B;
+    uint8_t *C;
+    int32_t m, n, K, lda, ldb, ldc;
+    int32_t field, pad;
+};
+
+struct BTile {
+    int32_t prod;
+    int16_t tm, tn;
+};
+
+struct BHeader {
+    uint32_t counter;
+    int32_t ntiles;
+    int32_t nprod;
+    int32_t nfields;
+    uint32_t fields_off, prods_off, tiles_off, pad;
+};
+
+constexpr size_t kHeaderBytes = 256;
+
+template <int KP>
+struct TileCfg {
+    static constexpr int BM = KP <= 2 ? 64 : KP <= 4 ? 64 : 32;
+    static constexpr int BN = KP <= 2 ? 64 : KP <= 4 ? 32 : 16;
+    static constexpr int WM = BM / 2, WN = BN / 2;   // 2 x 2 warps
+    static constexpr int MT = WM / 16, NT = WN / 8;
+    static constexpr int NACC = 2 * KP - 1;
+    static constexpr int LDA = BK + 8;               // bf16 elements per A_s row
+    static constexpr int LDB = BN + 8;               // bf16 elements per B_s row
+    static constexpr int SMEM = (KP * BM * LDA + KP * BK * LDB) * 2;
+};
+
+__host__ __device__ constexpr int max_i(int a, int b) { return a > b ? a : b; }
+
+constexpr int kSmemBytes =
+    max_i(max_i(TileCfg<2>::SMEM, TileCfg<4>::SMEM), max_i(TileCfg<8>::SMEM, TileCfg<1>::SMEM));
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2,
+                                        uint32_t &r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void ldsm_x2_trans(uint32_t addr, uint32_t &r0, uint32_t &r1) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];"
+                 : "=r"(r0), "=r"(r1)
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4],
+                                               const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ __nv_bfloat16 centred_bf16(uint32_t c, const BFieldParams &F) {
+    const uint32_t r = mod_small(c, F.p, F.m32);
+    const int v = (F.p > 2 && r > F.h) ? (int)r - (int)F.p : (int)r;
+    return __int2bfloat16_rn(v);
+}
+
+template <int KP>
+__device__ void run_tile(const BProd &P, const BFieldParams &F, int tm, int tn, uint8_t *smem) {
+    using T = TileCfg<KP>;
+    __nv_bfloat16 *As = reinterpret_cast<__nv_bfloat16 *>(smem);   // [KP][BM][LDA]
+    __nv_bfloat16 *Bs = As + KP * T::BM * T::LDA;                   // [KP][BK][LDB]
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int wm = warp / 2, wn = warp % 2;
+    const int row0 = tm * T::BM, col0 = tn * T::BN;
+
+    float acc[T::NACC][T::MT][T::NT][4];
+#pragma unroll
+    for (int t = 0; t < T::NACC; ++t)
+#pragma unroll
+        for (int a = 0; a < T::MT; ++a)
+#pragma unroll
+            for (int b = 0; b < T::NT; ++b)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[t][a][b][e] = 0.f;
+
+    const int nkb = (P.K + BK - 1) / BK;
+    for (int kb = 0; kb < nkb; ++kb) {
+        const int k0 = kb * BK;
+        __syncthreads();   // previous tile/step finished reading shared memory
+#pragma unroll 4
+        for (int e = threadIdx.x; e < KP * T::BM * BK; e += kThreads) {
+            const int c = e % BK, r = (e / BK) % T::BM, i = e / (BK * T::BM);
+            const int gr = row0 + r, gk = k0 + c;
+            uint32_t v = 0;
+            if (gr < P.m && gk < P.K) v = __ldg(P.A + ((int64_t)i * P.m + gr) * P.lda + gk);
+            As[(i * T::BM + r) * T::LDA + c] = centred_bf16(v, F);
+        }
+#pragma unroll 4
+        for (int e = threadIdx.x; e < KP * BK * T::BN; e += kThreads) {
+            const int c = e % T::BN, r = (e / T::BN) % BK, j = e / (T::BN * BK);
+            const int gk = k0 + r, gc = col0 + c;
+            uint32_t v = 0;
+            if (gk < P.K && gc < P.n) v = __ldg(P.B + ((int64_t)j * P.K + gk) * P.ldb + gc);
+            Bs[(j * BK + r) * T::LDB + c] = centred_bf16(v, F);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < BK / 16; ++ks) {
+            uint32_t bfr[KP][T::NT][2];
+#pragma unroll
+            for (int j = 0; j < KP; ++j)
+#pragma unroll
+                for (int nt = 0; nt < T::NT; ++nt) {
+                    const __nv_bfloat16 *src =
+                        Bs + (j * BK + ks * 16 + (lane % 16)) * T::LDB + wn * T::WN + nt * 8;
+                    ldsm_x2_trans((uint32_t)__cvta_generic_to_shared(src), bfr[j][nt][0],
+                                  bfr[j][nt][1]);
+                }
+#pragma unroll
+            for (int i = 0; i < KP; ++i) {
+                uint32_t afr[T::MT][4];
+#pragma unroll
+                for (int mt = 0; mt < T::MT; ++mt) {
+                    const __nv_bfloat16 *src = As + (i * T::BM + wm * T::WM + mt * 16 + (lane % 16)) *
+                                                        T::LDA + ks * 16 + (lane / 16) * 8;
+                    ldsm_x4((uint32_t)__cvta_generic_to_shared(src), afr[mt][0], afr[mt][1],
+                            afr[mt][2], afr[mt][3]);
+                }
+#pragma unroll
+                for (int j = 0; j < KP; ++j)
+#pragma unroll
+                    for (int mt = 0; mt < T::MT; ++mt)
+#pragma unroll
+                        for (int nt = 0; nt < T::NT; ++nt)
+                            mma_bf16_16816(acc[i + j][mt][nt], afr[mt], bfr[j][nt]);
+            }
+        }
+        if ((kb + 1) % F.chunk_blocks == 0 && kb + 1 < nkb) {
+            // exact-chunk boundary: bring every accumulator back to |x| <= 1.5 p
+#pragma unroll
+            for (int t = 0; t < T::NACC; ++t)
+#pragma unroll
+                for (int a = 0; a < T::MT; ++a)
+#pragma unroll
+                    for (int b = 0; b < T::NT; ++b)
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const float x = acc[t][a][b][e];
+                            acc[t][a][b][e] = fmaf(-F.pf, rintf(x * F.inv_pf), x);
+                        }
+        }
+    }
+
+    // epilogue: exact mod p, fold mod P, uint8 planes
+#pragma unroll
+    for (int mt = 0; mt < T::MT; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < T::NT; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int row = row0 + wm * T::WM + mt * 16 + (lane / 4) + (e >= 2 ? 8 : 0);
+                const int col = col0 + wn * T::WN + nt * 8 + 2 * (lane % 4) + (e & 1);
+                uint32_t mu[T::NACC];
+#pragma unroll
+                for (int t = 0; t < T::NACC; ++t) {
+                    const float x = acc[t][mt][nt][e];
+                    float r = fmaf(-F.pf, floorf(x * F.inv_pf), x);
+                    if (r < 0.f) r += F.pf;
+                    if (r >= F.pf) r -= F.pf;
+                    mu[t] = (uint32_t)r;
+                }
+                if (row < P.m && col < P.n) {
+#pragma unroll
+                    for (int i = 0; i < KP; ++i) {
+                        uint32_t o = mu[i];
+#pragma unroll
+                        for (int t = KP; t < T::NACC; ++t)
+                            o = mod_small(o + mu[t] * F.fold[(t - KP) * KP + i], F.p, F.m32);
+                        P.C[((int64_t)i * P.m + row) * P.ldc + col] = (uint8_t)o;
+                    }
+                }
+            }
+}
+
+__global__ void __launch_bounds__(kThreads, 2) batched_kernel(uint8_t *ws) {
+    __shared__ __align__(16) uint8_t smem[kSmemBytes];
+    __shared__ int s_tile;
+    BHeader *hdr = reinterpret_cast<BHeader *>(ws);
+    const BFieldParams *fields = reinterpret_cast<const BFieldParams *>(ws + hdr->fields_off);
+    const BProd *prods = reinterpret_cast<const BProd *>(ws + hdr->prods_off);
+    const BTile *tiles = reinterpret_cast<const BTile *>(ws + hdr->tiles_off);
+    const int ntiles = hdr->ntiles;
+    while (true) {
+        if (threadIdx.x == 0) s_tile = (int)atomicAdd(&hdr->counter, 1u);
+        __syncthreads();
+        const int t = s_tile;
+        __syncthreads();
+        if (t >= ntiles) break;
+        const BTile tile = tiles[t];
+        const BProd P = prods[tile.prod];
+        const BFieldParams F = fields[P.field];
+        switch (F.k) {
+            case 1: run_tile<1>(P, F, tile.tm, tile.tn, smem); break;
+            case 2: run_tile<2>(P, F, tile.tm, tile.tn, smem); break;
+            case 3: run_tile<3>(P, F, tile.tm, tile.tn, smem); break;
+            case 4: run_tile<4>(P, F, tile.tm, tile.tn, smem); break;
+            case 5: run_tile<5>(P, F, tile.tm, tile.tn, smem); break;
+            case 6: run_tile<6>(P, F, tile.tm, tile.tn, smem); break;
+            case 7: run_tile<7>(P, F, tile.tm, tile.tn, smem); break;
+            default: run_tile<8>(P, F, tile.tm, tile.tn, smem); break;
+        }
+    }
+}
+
+void tile_shape(uint32_t k, int &bm, int &bn) {
+    bm = k <= 4 ? 64 : 32;
+    bn = k <= 2 ? 64 : k <= 4 ? 32 : 16;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Layout {
+    size_t fields_off, prods_off, tiles_off, total;
+};
+
+Layout layout_for(int64_t count, int64_t ntiles) {
+    Layout L;
+    L.fields_off = kHeaderBytes;
+    L.prods_off = align_up(L.fields_off + kMaxFields * sizeof(BFieldParams), 256);
+    L.tiles_off = align_up(L.prods_off + count * sizeof(BProd), 256);
+    L.total = align_up(L.tiles_off + ntiles * sizeof(BTile), 256);
+    return L;
+}
+
+int64_t max_tiles(const qadic_gemm_desc *descs, int64_t count) {
+    int64_t t = 0;
+    for (int64_t i = 0; i < count; ++i)
+        t += (int64_t)((descs[i].m + 31) / 32) * ((descs[i].n + 15) / 16);   // smallest tile 32 x 16
+    return t;
+}
+
+// Cached CUDA graphs of {counter reset, persistent kernel}, keyed by the
+// call's exact arguments (descriptors, fields, workspace, stream).
+struct GraphEntry {
+    std::vector<uint8_t> key;
+    cudaGraphExec_t exec;
+};
+std::mutex g_graph_mu;
+std::vector<GraphEntry> g_graphs;
+constexpr size_t kMaxGraphs = 32;
+
+}  // namespace
+
+size_t batched_workspace_size(const qadic_gemm_desc *descs, int64_t count) {
+    if (!descs || count <= 0) return 0;
+    return layout_for(count, max_tiles(descs, count)).total;
+}
+
+int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm_desc *descs,
+                   int64_t count, void *workspace, size_t ws_bytes, bool use_graph,
+                   cudaStream_t stream) {
+    if (nfields < 1 || nfields > kMaxFields)
+        return set_error(QADIC_E_INVALID, "nfields must be in [1, %d]", kMaxFields);
+    if (count > (1 << 24)) return set_error(QADIC_E_INVALID, "too many products");
+    int dev = -1;
+    cudaGetDevice(&dev);
+    for (int32_t i = 0; i < nfields; ++i) {
+        if (!fields[i]) return set_error(QADIC_E_INVALID, "field %d is NULL", i);
+        if (fields[i]->device != dev)
+            return set_error(QADIC_E_INVALID, "field %d lives on another device", i);
+    }
+    for (int64_t i = 0; i < count; ++i) {
+        const qadic_gemm_desc &d = descs[i];
+        if (d.field < 0 || d.field >= nfields)
+            return set_error(QADIC_E_INVALID, "desc %lld: field index out of range", (long long)i);
+        if (d.m < 1 || d.n < 1 || d.K < 1 || d.m > 4096 || d.n > 4096 || d.K > 4096)
+            return set_error(QADIC_E_INVALID, "desc %lld: sizes must be in [1, 4096]", (long long)i);
+        if (!d.A || !d.B || !d.C) return set_error(QADIC_E_INVALID, "desc %lld: NULL", (long long)i);
+        if (d.lda < d.K || d.ldb < d.n || d.ldc < d.n)
+            return set_error(QADIC_E_INVALID, "desc %lld: leading dimension too small",
+                             (long long)i);
+        const Field &f = *fields[d.field];
+        if (f.k_chunk_f32 < BK)
+            return set_error(QADIC_E_OVERFLOW, "exact FP32 chunk below one K-block (p=%u k=%u)",
+                             f.p, f.k);
+    }
+    const int64_t tile_bound = max_tiles(descs, count);
+    const Layout L = layout_for(count, tile_bound);
+    if (!workspace || ws_bytes < L.total)
+        return set_error(QADIC_E_NOMEM, "workspace %zu < %zu bytes", ws_bytes, L.total);
+    if (((uintptr_t)workspace) & 255) return set_error(QADIC_E_INVALID, "workspace must be 256-byte aligned");
+
+    // graph cache lookup
+    std::vector<uint8_t> key;
+    if (use_graph) {
+        key.resize(sizeof(int64_t) + count * sizeof(qadic_gemm_desc) + nfields * sizeof(void *) +
+                   2 * sizeof(void *));
+        uint8_t *kp = key.data();
+        std::memcpy(kp, &count, sizeof(int64_t));
+        kp += sizeof(int64_t);
+        std::memcpy(kp, descs, count * sizeof(qadic_gemm_desc));
+        kp += count * sizeof(qadic_gemm_desc);
+        std::memcpy(kp, fields, nfields * sizeof(void *));
+        kp += nfields * sizeof(void *);
+        std::memcpy(kp, &workspace, sizeof(void *));
+        kp += sizeof(void *);
+        std::memcpy(kp, &stream, sizeof(void *));
+        std::lock_guard<std::mutex> lock(g_graph_mu);
+        for (auto &g : g_graphs)
+            if (g.key == key) {
+                if (cudaGraphLaunch(g.exec, stream) != cudaSuccess)
+                    return set_error(QADIC_E_CUDA, "graph launch: %s",
+                                     cudaGetErrorString(cudaGetLastError()));
+                return QADIC_OK;
+            }
+    }
+
+    // host-built work list
+    std::vector<uint8_t> host(L.total, 0);
+    std::vector<BTile> tiles;
+    std::vector<uint64_t> cost;
+    tiles.reserve(tile_bound);
+    BFieldParams *fp = reinterpret_cast<BFieldParams *>(host.data() + L.fields_off);
+    for (int32_t i = 0; i < nfields; ++i) {
+        const Field &f = *fields[i];
+        BFieldParams &F = fp[i];
+        F.p = f.p;
+        F.k = f.k;
+        F.h = f.h;
+        F.m32 = make_mod_small(f.p);
+        F.pf = (float)f.p;
+        F.inv_pf = 1.0f / (float)f.p;
+        F.chunk_blocks = (int32_t)std::min<int64_t>(f.k_chunk_f32 / BK, 1 << 20);
+        for (uint32_t t = 0; t + 1 < f.k; ++t)
+            for (uint32_t c = 0; c < f.k; ++c) F.fold[t * f.k + c] = f.fold[t * f.k + c];
+    }
+    BProd *pp = reinterpret_cast<BProd *>(host.data() + L.prods_off);
+    for (int64_t i = 0; i < count; ++i) {
+        const qadic_gemm_desc &d = descs[i];
+        BProd &P = pp[i];
+        P.A = d.A;
+        P.B = d.B;
+        P.C = d.C;
+        P.m = d.m;
+        P.n = d.n;
+        P.K = d.K;
+        P.lda = d.lda;
+        P.ldb = d.ldb;
+        P.ldc = d.ldc;
+        P.field = d.field;
+        int bm, bn;
+        const uint32_t k = fields[d.field]->k;
+        tile_shape(k, bm, bn);
+        for (int tm = 0; tm * bm < d.m; ++tm)
+            for (int tn = 0; tn * bn < d.n; ++tn) {
+                tiles.push_back(BTile{(int32_t)i, (int16_t)tm, (int16_t)tn});
+                cost.push_back((uint64_t)bm * bn * (uint64_t)((d.K + BK - 1) / BK) * k * k);
+            }
+    }
+    std::vector<int64_t> order(tiles.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int64_t)i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int64_t a, int64_t b) { return cost[a] > cost[b]; });
+    BTile *tp = reinterpret_cast<BTile *>(host.data() + L.tiles_off);
+    for (size_t i = 0; i < order.size(); ++i) tp[i] = tiles[order[i]];
+    BHeader *hdr = reinterpret_cast<BHeader *>(host.data());
+    hdr->counter = 0;
+    hdr->ntiles = (int32_t)tiles.size();
+    hdr->nprod = (int32_t)count;
+    hdr->nfields = nfields;
+    hdr->fields_off = (uint32_t)L.fields_off;
+    hdr->prods_off = (uint32_t)L.prods_off;
+    hdr->tiles_off = (uint32_t)L.tiles_off;
+    const size_t used = L.tiles_off + tiles.size() * sizeof(BTile);
+    if (cudaMemcpyAsync(workspace, host.data(), used, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+        return set_error(QADIC_E_CUDA, "work list upload: %s", cudaGetErrorString(cudaGetLastError()));
+
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel, kThreads, 0) !=
+            cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    int64_t grid = (int64_t)sms * per_sm;
+    if ((int64_t)tiles.size() < grid) grid = std::max<int64_t>(1, (int64_t)tiles.size());
+
+    if (!use_graph) {
+        batched_kernel<<<(unsigned)grid, kThreads, 0, stream>>>((uint8_t *)workspace);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return set_error(QADIC_E_CUDA, "batched launch: %s", cudaGetErrorString(e));
+        return QADIC_OK;
+    }
+    // capture {counter reset, kernel}; the work list above stays in the
+    // workspace for every replay
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return set_error(QADIC_E_CUDA, "begin capture: %s", cudaGetErrorString(cudaGetLastError()));
+    cudaMemsetAsync(workspace, 0, sizeof(uint32_t), stream);
+    batched_kernel<<<(unsigned)grid, kThreads, 0, stream>>>((uint8_t *)workspace);
+    const cudaError_t le = cudaGetLastError();
+    const cudaError_t ce = cudaStreamEndCapture(stream, &graph);
+    if (le != cudaSuccess || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return set_error(QADIC_E_CUDA, "capture: %s", cudaGetErrorString(le != cudaSuccess ? le : ce));
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return set_error(QADIC_E_CUDA, "instantiate: %s", cudaGetErrorString(ie));
+    if (cudaGraphLaunch(exec, stream) != cudaSuccess) {
+        cudaGraphExecDestroy(exec);
+        return set_error(QADIC_E_CUDA, "graph launch: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    if (g_graphs.size() >= kMaxGraphs) {
+        cudaGraphExecDestroy(g_graphs.front().exec);
+        g_graphs.erase(g_graphs.begin());
+    }
+    g_graphs.push_back(GraphEntry{std::move(key), exec});
+    return QADIC_OK;
+}
+
+}  // namespace qadic

@@ -75,4 +75,10 @@ int launch_gemm_planes_tc(const Field &f, int64_t m, int64_t n, int64_t K, const
 
 bool gemm_planes_tc_supported(const Field &f);
 
+size_t batched_workspace_size(const qadic_gemm_desc *descs, int64_t count);
+
+int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm_desc *descs,
+                   int64_t count, void *workspace, size_t ws_bytes, bool use_graph,
+                   cudaStream_t stream);
+
 }  // namespace qadic

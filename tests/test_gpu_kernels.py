@@ -183,7 +183,18 @@ def test_gemm_fp64_gf27_log(torch, orc, shape):
     assert np.array_equal(got, np.transpose(want, (2, 0, 1)))
 
 
-@pytest.mark.parametrize("pk,shape", [((101, 2), (67, 70, 333)), ((7, 4), (40, 33, 50)),
+def test_gemm_fp64_rejects_field_without_block(torch):
+    """GF(7^4): the largest q with 7 log2 q <= 51 is 2^7 = 128 < k (p-1)^2 =
+    144, so Eq. 2 admits no block: the FP64 form is refused, not run."""
+    f = q.Field(7, 4)
+    assert f.n_q == 0
+    x = torch.zeros((4, 8, 8), dtype=torch.uint8, device="cuda")
+    with pytest.raises(q.QadicError) as e:
+        f.pack(q.FMT_COEFF_U8, x, 8, 8, q.FMT_QADIC_F64)
+    assert e.value.status == q.E_OVERFLOW
+
+
+@pytest.mark.parametrize("pk,shape", [((101, 2), (67, 70, 333)), ((5, 3), (40, 33, 50)),
                                       ((31, 2), (33, 65, 257)), ((251, 2), (20, 20, 40))])
 def test_gemm_fp64_planes_input(torch, orc, pk, shape):
     p, k = pk
