@@ -286,6 +286,119 @@ def bench_polymul(args, torch, q, W, count=65536, steps=50):
                        "residues_per_s": 7 * count / (ms * 1e-3)}
 
 
+def make_batched(torch, q, W, count=4096, salt=0):
+    """4096 products, m, n, K log-uniform in [16, 256], fields GF(2^8),
+    GF(7^4), GF(31^2), coefficients uniform per field."""
+    import numpy as np
+    fields = [q.Field(2, 8), q.Field(7, 4), q.Field(31, 2)]
+    dims, fidx = W.batched_shapes(count, index=3, salt=salt)
+    g = W.rng(3, salt + 17)
+    sa = sb = sc = 0
+    offs = []
+    for (m, n, K), fi in zip(dims, fidx):
+        m, n, K, k = int(m), int(n), int(K), fields[fi].k
+        offs.append((sa, sb, sc))
+        sa += k * m * K
+        sb += k * K * n
+        sc += k * m * n
+    hA = np.empty(sa, np.uint8)
+    hB = np.empty(sb, np.uint8)
+    for (m, n, K), fi, (a, b, c) in zip(dims, fidx, offs):
+        f = fields[fi]
+        hA[a:a + f.k * m * K] = g.integers(0, f.p, f.k * m * K, dtype=np.uint8)
+        hB[b:b + f.k * K * n] = g.integers(0, f.p, f.k * K * n, dtype=np.uint8)
+    dA = torch.from_numpy(hA).cuda()
+    dB = torch.from_numpy(hB).cuda()
+    dC = torch.zeros(sc, dtype=torch.uint8, device="cuda")
+    descs = []
+    for (m, n, K), fi, (a, b, c) in zip(dims, fidx, offs):
+        descs.append(q.GemmDesc(int(fi), int(m), int(n), int(K), dA.data_ptr() + a,
+                                dB.data_ptr() + b, dC.data_ptr() + c, int(K), int(n), int(n), 0))
+    ws = torch.empty(q.batched_workspace_size(descs), dtype=torch.uint8, device="cuda")
+    return fields, dims, fidx, offs, hA, hB, dC, descs, ws
+
+
+def bench_batched(args, torch, q, W, orc):
+    import numpy as np
+    fields, dims, fidx, offs, hA, hB, dC, descs, ws = make_batched(torch, q, W)
+
+    def step(kev):
+        q.batched_gemm(fields, descs, ws, graph=True)
+
+    total, _ = time_steps(torch, step, args.steps, args.warmup, None)
+    ms = total / args.steps
+    ops = float(sum(2 * int(m) * int(n) * int(K) for m, n, K in dims))
+    flops = float(sum(2 * fields[fi].k ** 2 * int(m) * int(n) * int(K)
+                      for (m, n, K), fi in zip(dims, fidx)))
+    # one launch per product through the same entry point (no graph)
+    single_ws = torch.empty(q.batched_workspace_size([max(descs, key=lambda d: d.m * d.n)]) * 2,
+                            dtype=torch.uint8, device="cuda")
+
+    def step_each(kev):
+        for d in descs:
+            q.batched_gemm(fields, [d], single_ws)
+
+    tot1, _ = time_steps(torch, step_each, 2, 1, None)
+    ms1 = tot1 / 2
+    # parity on a sample of products
+    C = dC.cpu().numpy()
+    ok = True
+    for i in np.random.default_rng(5).integers(0, len(descs), 12):
+        m, n, K = (int(x) for x in dims[i])
+        f = fields[fidx[i]]
+        a, b, c = offs[i]
+        A = hA[a:a + f.k * m * K].reshape(f.k, m, K)
+        B = hB[b:b + f.k * K * n].reshape(f.k, K, n)
+        want = np.transpose(orc.gemm(f.p, f.poly, np.transpose(A, (1, 2, 0)),
+                                     np.transpose(B, (1, 2, 0))), (2, 0, 1))
+        ok = ok and bool(np.array_equal(C[c:c + f.k * m * n].reshape(f.k, m, n), want))
+    pk = peaks()
+    achieved = flops / (ms * 1e-3) / 1e12
+    return {"value": ops / (ms * 1e-3) / 1e9, "unit": "field Gop/s", "ms_per_step": ms,
+            "products": len(descs), "field_ops": ops, "plane_flops": flops,
+            "one_launch_per_product": {"value": ops / (ms1 * 1e-3) / 1e9, "ms": ms1},
+            "speedup_vs_per_product": ms1 / ms, "parity_sampled": ok,
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": pk["bf16_sustained"],
+                         "unit": "TFLOP/s", "frac": achieved / pk["bf16_sustained"],
+                         "traffic": None, "kernel": "batched_kernel (mma.sync bf16)",
+                         "note": "legacy mma.sync bf16 measured at 606 TFLOP/s on this GPU"}}
+
+
+def bench_fp64_gf27(args, torch, q, W, orc, n=1024):
+    """GF(3^3), n = 1024, log-coded inputs: pack (log -> q-adic FP64 word by
+    table lookup) + FP64 q-adic GEMM with REDQ every n_q = 85 products."""
+    import numpy as np
+    f = q.Field(3, 3)
+    A = W.log_matrix(n, n, 27, index=1, salt=0)
+    B = W.log_matrix(n, n, 27, index=1, salt=1)
+    dA = torch.from_numpy(A).cuda()
+    dB = torch.from_numpy(B).cuda()
+    a64 = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    b64 = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    C = torch.empty((3, n, n), dtype=torch.uint8, device="cuda")
+
+    def step(kev):
+        f.pack(q.FMT_LOG, dA, n, n, q.FMT_QADIC_F64, out=a64)
+        f.pack(q.FMT_LOG, dB, n, n, q.FMT_QADIC_F64, out=b64)
+        f.gemm(q.PATH_FP64_QADIC, a64, b64, n, n, n, C=C)
+
+    total, _ = time_steps(torch, step, args.steps, args.warmup, None)
+    ms = total / args.steps
+    T = orc.antilog(3, f.poly)
+    rng = np.random.default_rng(3)
+    ii, jj = rng.integers(0, n, 256), rng.integers(0, n, 256)
+    want = orc.gemm_entries(3, f.poly, T[A.astype(np.int64)], T[B.astype(np.int64)], ii, jj)
+    ok = bool(np.array_equal(C.cpu().numpy()[:, ii, jj].T, want))
+    fl = 2.0 * n ** 3
+    return {"value": fl / (ms * 1e-3) / 1e9, "unit": "field Gop/s", "ms_per_step": ms,
+            "parity_sampled": ok, "n_q": f.n_q, "log2_q": f.log2_q,
+            "roofline": {"bound": "alu", "achieved": fl / (ms * 1e-3) / 1e12, "peak": 1.05,
+                         "unit": "TFLOP/s", "frac": fl / (ms * 1e-3) / 1e12 / 1.05,
+                         "traffic": None, "kernel": "gemm_f64_kernel<3>",
+                         "peak_source": "FP64 FMA rate measured on this GPU (DMMA 1.05, DFMA 1.01, "
+                                        "cuBLAS 1.10 TFLOP/s)"}}
+
+
 def e2e_plane(args, torch, q, W, f, A, B, n):
     """Same metric through qadic_matmul_host: pinned host inputs, H2D copies,
     pack, GEMM, D2H of C, all inside the timed region."""
@@ -446,6 +559,23 @@ def main():
             line["config"] = {"workload": f"GF(251^2) n={res['n']} plane form", "p": 251, "k": 2,
                               "n": res["n"], "l2": FLUSH_NOTE}
             extras["parity_sampled"] = sampled_parity(oracle, f, A, B, C, samples=256)
+        elif args.workload == "batched":
+            r = bench_batched(args, torch, q, W, oracle)
+            line.update({"value": r["value"] * world, "unit": "field Gop/s",
+                         "ms_per_step": r["ms_per_step"], "dtype": "bf16 exact, f32 accumulate",
+                         "roofline": r["roofline"], "gpu_launches": args.steps})
+            line["config"] = {"workload": "4096 products, m,n,K log-uniform in [16,256], fields "
+                              "GF(2^8), GF(7^4), GF(31^2); one persistent graph-replayed launch"}
+            extras.update({k: r[k] for k in ("one_launch_per_product", "speedup_vs_per_product",
+                                             "parity_sampled", "products")})
+        elif args.workload == "fp64":
+            r = bench_fp64_gf27(args, torch, q, W, oracle)
+            line.update({"value": r["value"] * world, "unit": "field Gop/s",
+                         "ms_per_step": r["ms_per_step"], "dtype": "f64",
+                         "roofline": r["roofline"], "gpu_launches": 3 * args.steps})
+            line["config"] = {"workload": "GF(3^3) n=1024 log-coded: pack (log->q-adic table) + "
+                              "FP64 q-adic GEMM, REDQ every n_q=85 products"}
+            extras["parity_sampled"] = r["parity_sampled"]
         else:
             raise SystemExit(f"workload {args.workload} not available")
     line["clocks"] = clk.summary()
@@ -455,6 +585,21 @@ def main():
         pm = bench_polymul(args, torch, q, W)
         extras["polymul"] = pm[3]
         extras["polymul"]["parity"] = bool((pm[2].cpu().numpy() == oracle.polymul(7, pm[0], pm[1])).all())
+        bb = bench_batched(args, torch, q, W, oracle)
+        extras["batched"] = {k: bb[k] for k in ("value", "unit", "ms_per_step", "one_launch_per_product",
+                                                "speedup_vs_per_product", "parity_sampled", "roofline")}
+        g27 = bench_fp64_gf27(args, torch, q, W, oracle)
+        extras["fp64_gf27_n1024"] = g27
+        del pm, bb
+        torch.cuda.empty_cache()
+        lf, lA, lB, lC, lres = bench_plane(argparse.Namespace(n=None, steps=5, warmup=2), torch, q,
+                                           W, None, p=251, n=16384)
+        extras["large_gf251_2_n16384"] = {
+            "value": lres["value"], "unit": "field Gop/s", "ms_per_step": lres["ms_per_step"],
+            "kernel_ms": lres["kernel_ms"], "roofline": lres["roofline"],
+            "parity_sampled": sampled_parity(oracle, lf, lA, lB, lC, samples=256)}
+        del lA, lB, lC
+        torch.cuda.empty_cache()
     if rank == 0:
         if args.workload == "plane":
             line["cpu_baseline"] = cpu_baseline_plane(101, line["config"]["n"])

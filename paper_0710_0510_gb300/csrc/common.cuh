@@ -48,12 +48,14 @@ inline uint32_t make_mod_small(uint32_t d) {
 
 // Exact integer value of a non-negative double holding an integer < 2^53,
 // read from its bit pattern (no floating-point unit involved).
+// For a non-negative x < 2^53 this is floor(x) (a truncation of the fraction
+// bits); other bit patterns give some value without faulting.
 __device__ __forceinline__ uint64_t f64_to_u64_exact(double x) {
     const uint64_t bits = (uint64_t)__double_as_longlong(x);
-    const int e = (int)((bits >> 52) & 0x7ff);
-    if (e < 1023) return 0;   // 0 (or a fraction, never produced here)
+    const uint32_t e = (uint32_t)(bits >> 52);
     const uint64_t mant = (bits & ((1ull << 52) - 1)) | (1ull << 52);
-    return mant >> (1075 - e);
+    const uint32_t sh = min(1075u - e, 63u);   // e < 1023 (x < 1): shift >= 53 -> 0
+    return mant >> sh;
 }
 
 // Double holding the integer v < 2^53, built from its bit pattern.

@@ -294,6 +294,19 @@ std::mutex g_graph_mu;
 std::vector<GraphEntry> g_graphs;
 constexpr size_t kMaxGraphs = 32;
 
+// One non-blocking stream per device, used only to capture graphs.
+cudaStream_t capture_stream(int dev) {
+    static std::mutex mu;
+    static cudaStream_t streams[64] = {nullptr};
+    if (dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        streams[dev] = nullptr;
+    }
+    return streams[dev];
+}
+
 }  // namespace
 
 size_t batched_workspace_size(const qadic_gemm_desc *descs, int64_t count) {
@@ -434,16 +447,20 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
         if (e != cudaSuccess) return set_error(QADIC_E_CUDA, "batched launch: %s", cudaGetErrorString(e));
         return QADIC_OK;
     }
-    // capture {counter reset, kernel}; the work list above stays in the
-    // workspace for every replay
+    // Capture {counter reset, kernel} on a private stream (the caller's may
+    // be the legacy default stream, which cannot be captured; capturing runs
+    // nothing), then launch the graph on the caller's stream.  The work list
+    // uploaded above stays in the workspace for every replay.
+    cudaStream_t cap = capture_stream(dev);
+    if (!cap) return set_error(QADIC_E_CUDA, "no capture stream");
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return set_error(QADIC_E_CUDA, "begin capture: %s", cudaGetErrorString(cudaGetLastError()));
-    cudaMemsetAsync(workspace, 0, sizeof(uint32_t), stream);
-    batched_kernel<<<(unsigned)grid, kThreads, 0, stream>>>((uint8_t *)workspace);
+    cudaMemsetAsync(workspace, 0, sizeof(uint32_t), cap);
+    batched_kernel<<<(unsigned)grid, kThreads, 0, cap>>>((uint8_t *)workspace);
     const cudaError_t le = cudaGetLastError();
-    const cudaError_t ce = cudaStreamEndCapture(stream, &graph);
+    const cudaError_t ce = cudaStreamEndCapture(cap, &graph);
     if (le != cudaSuccess || ce != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
         return set_error(QADIC_E_CUDA, "capture: %s", cudaGetErrorString(le != cudaSuccess ? le : ce));

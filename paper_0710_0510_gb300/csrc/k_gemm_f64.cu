@@ -100,7 +100,9 @@ gemm_f64_kernel(const double *__restrict__ A, const double *__restrict__ B, uint
                     idxH += u * pw;
                     pw *= p;
                 }
-                const uint32_t L = tL[idxL], H = tH[idxH];
+                // in range for every input that respects Eq. 2 (Thm. 2: 0 <= u < p);
+                // clamped so that malformed words cannot read past the tables
+                const uint32_t L = tL[min(idxL, P.order - 1)], H = tH[min(idxH, P.order - 1)];
 #pragma unroll
                 for (int c = 0; c < KK; ++c)
                     sum[i][j][c] += (int32_t)((L >> (8 * c)) & 0xff) + (int32_t)((H >> (8 * c)) & 0xff);

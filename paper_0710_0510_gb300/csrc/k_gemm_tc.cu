@@ -33,6 +33,7 @@ namespace qadic {
 namespace {
 
 constexpr int BM = 128, BK = 64, UMMA_K = 16;
+constexpr int kGroupM = 16;
 constexpr int kThreads = 192;
 constexpr int kSmemBudget = 227 * 1024;
 
@@ -48,12 +49,15 @@ struct Cfg {
     static constexpr int TMEM_COLS = ACC_COLS <= 32 ? 32 : ACC_COLS <= 64 ? 64
                                    : ACC_COLS <= 128 ? 128 : ACC_COLS <= 256 ? 256 : 512;
     static constexpr int SMEM = 1024 + STAGES * STAGE + 256;
+    static constexpr int EC = KP <= 2 ? 32 : 16;   // epilogue columns per pass
     static_assert(ACC_COLS <= 512, "accumulators exceed tensor memory");
+    static_assert(KP * BN <= 256 && (KP * BN) % 16 == 0, "combined MMA N must be <= 256");
     static_assert(STAGES >= 2, "not enough shared memory for two stages");
 };
 
 struct TcParams {
     int64_t m, n, ldc;
+    int32_t tiles_m, tiles_n;   // output tiles; CTAs walk them in groups of kGroupM tile rows
     int32_t nkb;          // K-blocks of 64
     int32_t chunk_kb;     // K-blocks per exact FP32 chunk
     uint32_t p, m32;
@@ -87,7 +91,19 @@ gemm_planes_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int tile_n = blockIdx.x, tile_m = blockIdx.y;
+    // Grouped raster: consecutive CTAs cover kGroupM tile rows before moving
+    // to the next tile column, so the A and B panels of the CTAs resident at
+    // one time overlap and stay in L2.
+    int tile_m, tile_n;
+    {
+        const int pid = blockIdx.x;
+        const int per_group = kGroupM * P.tiles_n;
+        const int first_m = (pid / per_group) * kGroupM;
+        const int gm = min(P.tiles_m - first_m, kGroupM);
+        const int r = pid % per_group;
+        tile_m = first_m + r % gm;
+        tile_n = r / gm;
+    }
     const int nkb = P.nkb;
 
     if (threadIdx.x == 0) {
@@ -146,8 +162,12 @@ gemm_planes_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
-            const uint32_t idesc = ptx::idesc_bf16_f32(BM, BN);
-            uint32_t init = 0;   // accumulators written at least once
+            // The KP B-plane tiles are adjacent in shared memory, so together
+            // they form one K-major operand of N = KP*BN rows.  With C_t at
+            // TMEM column t*BN, one MMA of A_i against [B_0; ...; B_{KP-1}]
+            // at column i*BN adds A_i B_j into C_{i+j} for every j.
+            const uint32_t idesc_all = ptx::idesc_bf16_f32(BM, KP * BN);
+            const uint32_t idesc_one = ptx::idesc_bf16_f32(BM, BN);
             int drain = 0;
             bool ok = true;
             for (int kb = 0; kb < nkb && ok; ++kb) {
@@ -157,17 +177,24 @@ gemm_planes_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                     break;
                 }
                 ptx::tc_fence_after();
+                const uint64_t bd0 = ptx::smem_desc_sw128(b_tile(stage, 0));
 #pragma unroll
                 for (int kk = 0; kk < BK / UMMA_K; ++kk) {
 #pragma unroll
                     for (int i = 0; i < KP; ++i) {
                         const uint64_t ad = ptx::smem_desc_sw128(a_tile(stage, i)) + 2 * kk;
+                        if (kb == 0 && kk == 0 && i > 0) {
+                            // first K step: C_0..C_{i+KP-2} already hold data,
+                            // C_{i+KP-1} is written for the first time
 #pragma unroll
-                        for (int j = 0; j < KP; ++j) {
-                            const int t = i + j;
-                            const uint64_t bd = ptx::smem_desc_sw128(b_tile(stage, j)) + 2 * kk;
-                            ptx::mma_bf16(tmem_base + t * BN, ad, bd, idesc, (init >> t) & 1);
-                            init |= 1u << t;
+                            for (int j = 0; j < KP; ++j) {
+                                const uint64_t bd = ptx::smem_desc_sw128(b_tile(stage, j));
+                                ptx::mma_bf16(tmem_base + (i + j) * BN, ad, bd, idesc_one,
+                                              j < KP - 1 ? 1u : 0u);
+                            }
+                        } else {
+                            ptx::mma_bf16(tmem_base + i * BN, ad, bd0 + 2 * kk, idesc_all,
+                                          (kb == 0 && kk == 0) ? 0u : 1u);
                         }
                     }
                 }
@@ -226,25 +253,26 @@ gemm_planes_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
         } else {
             ptx::tc_fence_after();
             const int64_t row = (int64_t)tile_m * BM + wq * 32 + lane;
+            constexpr int EC = CF::EC;   // columns per pass (bounds registers)
 #pragma unroll 1
-            for (int c0 = 0; c0 < BN; c0 += 32) {
-                uint32_t mu[CF::NACC][32];
+            for (int c0 = 0; c0 < BN; c0 += EC) {
+                uint32_t mu[CF::NACC][EC];
 #pragma unroll
-                for (int t = 0; t < CF::NACC; ++t) ptx::tmem_ld32(tbase + t * BN + c0, mu[t]);
+                for (int t = 0; t < CF::NACC; ++t) ptx::tmem_ld<EC>(tbase + t * BN + c0, mu[t]);
                 ptx::tmem_wait_ld();
 #pragma unroll
                 for (int t = 0; t < CF::NACC; ++t)
 #pragma unroll
-                    for (int e = 0; e < 32; ++e) mu[t][e] = mod_exact_f32(mu[t][e], P.pf, P.inv_pf);
+                    for (int e = 0; e < EC; ++e) mu[t][e] = mod_exact_f32(mu[t][e], P.pf, P.inv_pf);
                 const int64_t col = (int64_t)tile_n * BN + c0;
                 if (row < P.m && col < P.n) {
 #pragma unroll
                     for (int i = 0; i < KP; ++i) {
-                        uint32_t packed[8];
+                        uint32_t packed[EC / 4];
 #pragma unroll
-                        for (int w = 0; w < 8; ++w) packed[w] = 0;
+                        for (int w = 0; w < EC / 4; ++w) packed[w] = 0;
 #pragma unroll
-                        for (int e = 0; e < 32; ++e) {
+                        for (int e = 0; e < EC; ++e) {
                             uint32_t o = mu[i][e];
 #pragma unroll
                             for (int t = KP; t < 2 * KP - 1; ++t)
@@ -252,14 +280,15 @@ gemm_planes_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                             packed[e / 4] |= o << (8 * (e % 4));
                         }
                         uint8_t *dst = C + ((int64_t)i * P.m + row) * P.ldc + col;
-                        if (col + 32 <= P.n && (((uintptr_t)dst) & 15) == 0) {
-                            reinterpret_cast<uint4 *>(dst)[0] =
-                                make_uint4(packed[0], packed[1], packed[2], packed[3]);
-                            reinterpret_cast<uint4 *>(dst)[1] =
-                                make_uint4(packed[4], packed[5], packed[6], packed[7]);
+                        if (col + EC <= P.n && (((uintptr_t)dst) & 15) == 0) {
+#pragma unroll
+                            for (int w = 0; w < EC / 16; ++w)
+                                reinterpret_cast<uint4 *>(dst)[w] =
+                                    make_uint4(packed[4 * w], packed[4 * w + 1], packed[4 * w + 2],
+                                               packed[4 * w + 3]);
                         } else {
                             const int64_t nrem = P.n - col;
-                            const int lim = nrem < 32 ? (int)nrem : 32;
+                            const int lim = nrem < EC ? (int)nrem : EC;
                             for (int e = 0; e < lim; ++e)
                                 dst[e] = (uint8_t)(packed[e / 4] >> (8 * (e % 4)));
                         }
@@ -342,9 +371,11 @@ int launch_tc(const Field &f, int64_t m, int64_t n, int64_t K, const void *A, in
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM) !=
         cudaSuccess)
         return set_error(QADIC_E_CUDA, "tc smem attribute: %s", cudaGetErrorString(cudaGetLastError()));
-    const dim3 grid((unsigned)((n + BN - 1) / BN), (unsigned)((m + BM - 1) / BM));
-    if (grid.y > 65535) return set_error(QADIC_E_INVALID, "m too large");
-    kern<<<grid, kThreads, CF::SMEM, stream>>>(tmA, tmB, C, P);
+    const int64_t tiles_m = (m + BM - 1) / BM, tiles_n = (n + BN - 1) / BN;
+    if (tiles_m * tiles_n > 0x7fffffff) return set_error(QADIC_E_INVALID, "too many tiles");
+    P.tiles_m = (int32_t)tiles_m;
+    P.tiles_n = (int32_t)tiles_n;
+    kern<<<(unsigned)(tiles_m * tiles_n), kThreads, CF::SMEM, stream>>>(tmA, tmB, C, P);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(QADIC_E_CUDA, "tc launch: %s", cudaGetErrorString(e));
     return QADIC_OK;
@@ -352,7 +383,7 @@ int launch_tc(const Field &f, int64_t m, int64_t n, int64_t K, const void *A, in
 
 }  // namespace
 
-bool gemm_planes_tc_supported(const Field &f) { return f.k == 2; }
+bool gemm_planes_tc_supported(const Field &f) { return f.k >= 2 && f.k <= 4; }
 
 int launch_gemm_planes_tc(const Field &f, int64_t m, int64_t n, int64_t K, const void *A,
                           int64_t lda, const void *B, int64_t ldb, uint8_t *C, int64_t ldc,
@@ -367,6 +398,8 @@ int launch_gemm_planes_tc(const Field &f, int64_t m, int64_t n, int64_t K, const
         return QADIC_OK;
     }
     if (f.k == 2) return launch_tc<2, 128>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
+    if (f.k == 3) return launch_tc<3, 64>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
+    if (f.k == 4) return launch_tc<4, 64>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
     return set_error(QADIC_E_UNSUPPORTED, "no tensor-core plane kernel for k=%u", f.k);
 }
 

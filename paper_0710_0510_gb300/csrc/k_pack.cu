@@ -148,6 +148,95 @@ __global__ void __launch_bounds__(kTile * 8) pack_transpose(const void *__restri
     }
 }
 
+// Fast paths for coefficient planes (int8 / uint8) -> bf16 operands when
+// every row starts on a 16-byte boundary and cols % 16 == 0: each thread
+// turns 16 coefficients (one 16-byte load) into 16 bf16 (two 16-byte
+// stores).
+template <int IN>
+__device__ __forceinline__ uint32_t centre_pair(uint32_t b0, uint32_t b1, const PackParams &P) {
+    const int32_t v0 = (IN == IN_I8) ? (int32_t)(int8_t)b0 : (int32_t)b0;
+    const int32_t v1 = (IN == IN_I8) ? (int32_t)(int8_t)b1 : (int32_t)b1;
+    const uint32_t c0 = mod_small((uint32_t)(v0 + 128 * (int32_t)P.p), P.p, P.m32);
+    const uint32_t c1 = mod_small((uint32_t)(v1 + 128 * (int32_t)P.p), P.p, P.m32);
+    const __nv_bfloat16 h0 = __int2bfloat16_rn(centre(c0, P));
+    const __nv_bfloat16 h1 = __int2bfloat16_rn(centre(c1, P));
+    return (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+}
+
+template <int IN>
+__global__ void __launch_bounds__(256) pack_vec_a(const uint8_t *__restrict__ in,
+                                                  __nv_bfloat16 *__restrict__ out, PackParams P) {
+    const int64_t per_row = P.cols / 16;
+    const int64_t units = (int64_t)P.k * P.rows * per_row;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < units;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c16 = u % per_row, pr = u / per_row;   // pr = plane * rows + row
+        const uint4 w = __ldcs(reinterpret_cast<const uint4 *>(in + pr * P.ld_in + c16 * 16));
+        const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+        uint32_t o[8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            o[2 * q] = centre_pair<IN>(words[q] & 0xff, (words[q] >> 8) & 0xff, P);
+            o[2 * q + 1] = centre_pair<IN>((words[q] >> 16) & 0xff, words[q] >> 24, P);
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(out + pr * P.ld_out + c16 * 16);
+        dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
+        dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
+    }
+}
+
+// Transposed operand: a 64 x 64 input tile per block and plane; 16-byte
+// loads along the input rows, 16-byte stores along the output rows.
+template <int IN>
+__global__ void __launch_bounds__(256) pack_vec_b(const uint8_t *__restrict__ in,
+                                                  __nv_bfloat16 *__restrict__ out, PackParams P) {
+    __shared__ uint16_t tile[64][64 + 2];
+    const int64_t r0 = (int64_t)blockIdx.y * 64, c0 = (int64_t)blockIdx.x * 64;
+    const int plane = blockIdx.z;
+    {   // load: 64 rows x 4 chunks of 16 bytes, one chunk per thread
+        const int rr = threadIdx.x / 4, cc = (threadIdx.x % 4) * 16;
+        const int64_t r = r0 + rr;
+        uint32_t words[4] = {0, 0, 0, 0};
+        if (r < P.rows) {
+            const uint4 w = __ldcs(reinterpret_cast<const uint4 *>(
+                in + ((int64_t)plane * P.rows + r) * P.ld_in + c0 + cc));
+            words[0] = w.x;
+            words[1] = w.y;
+            words[2] = w.z;
+            words[3] = w.w;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t lo = centre_pair<IN>(words[q] & 0xff, (words[q] >> 8) & 0xff, P);
+            const uint32_t hi = centre_pair<IN>((words[q] >> 16) & 0xff, words[q] >> 24, P);
+            tile[rr][cc + 4 * q] = (uint16_t)lo;
+            tile[rr][cc + 4 * q + 1] = (uint16_t)(lo >> 16);
+            tile[rr][cc + 4 * q + 2] = (uint16_t)hi;
+            tile[rr][cc + 4 * q + 3] = (uint16_t)(hi >> 16);
+        }
+    }
+    __syncthreads();
+    // store: output row (input column) oc, 8 consecutive input rows per chunk
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const int idx = threadIdx.x + 256 * s;        // 64 output rows x 8 chunks
+        const int oc = idx / 8, ch = (idx % 8) * 8;
+        uint32_t v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            v[q] = (uint32_t)tile[ch + 2 * q][oc] | ((uint32_t)tile[ch + 2 * q + 1][oc] << 16);
+        const int64_t orow = c0 + oc, ocol = r0 + ch;
+        if (ocol + 8 <= P.rows) {
+            *reinterpret_cast<uint4 *>(out + ((int64_t)plane * P.cols + orow) * P.ld_out + ocol) =
+                make_uint4(v[0], v[1], v[2], v[3]);
+        } else {
+            for (int e = 0; e < 8 && ocol + e < P.rows; ++e)
+                out[((int64_t)plane * P.cols + orow) * P.ld_out + ocol + e] =
+                    __ushort_as_bfloat16((uint16_t)(v[e / 2] >> (16 * (e % 2))));
+        }
+    }
+}
+
 template <int IN>
 int dispatch_out(int out_fmt, const void *in, void *out, const PackParams &P0, cudaStream_t stream) {
     PackParams P = P0;
@@ -159,7 +248,23 @@ int dispatch_out(int out_fmt, const void *in, void *out, const PackParams &P0, c
         if (P.tables_in_smem) smem = (need + 15) & ~(size_t)15;
     }
     cudaError_t e = cudaSuccess;
-    if (out_fmt == QADIC_FMT_OPERAND_B) {
+    const bool planes_in = (IN == IN_U8 || IN == IN_I8);
+    const bool aligned16 = P.cols % 16 == 0 && P.ld_in % 16 == 0 && ((uintptr_t)in & 15) == 0 &&
+                           P.ld_out % 8 == 0 && ((uintptr_t)out & 15) == 0;
+    if (planes_in && aligned16 && out_fmt == QADIC_FMT_OPERAND_A) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int64_t units = (int64_t)P.k * P.rows * (P.cols / 16);
+        int64_t blocks = (units + 255) / 256;
+        if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
+        pack_vec_a<IN><<<(unsigned)blocks, 256, 0, stream>>>((const uint8_t *)in,
+                                                             (__nv_bfloat16 *)out, P);
+    } else if (planes_in && aligned16 && out_fmt == QADIC_FMT_OPERAND_B && P.cols % 64 == 0 &&
+               (P.rows + 63) / 64 <= 65535) {
+        const dim3 grid((unsigned)(P.cols / 64), (unsigned)((P.rows + 63) / 64), P.k);
+        pack_vec_b<IN><<<grid, 256, 0, stream>>>((const uint8_t *)in, (__nv_bfloat16 *)out, P);
+    } else if (out_fmt == QADIC_FMT_OPERAND_B) {
         auto kern = pack_transpose<IN>;
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -36,9 +36,9 @@ polymul_kernel(const uint8_t *__restrict__ a, const uint8_t *__restrict__ b,
     const int64_t idx = base + threadIdx.x;
     if (idx < count) {
         uint64_t aw = 0, bw = 0;
-        for (uint32_t i = 0; i < k; ++i) {
-            aw |= (uint64_t)__ldg(a + idx * k + i) << (s * i);
-            bw |= (uint64_t)__ldg(b + idx * k + i) << (s * i);
+        for (uint32_t i = 0; i < k; ++i) {   // coefficients taken mod p
+            aw |= (uint64_t)mod_small(__ldg(a + idx * k + i), p, m32) << (s * i);
+            bw |= (uint64_t)mod_small(__ldg(b + idx * k + i), p, m32) << (s * i);
         }
         const double ad = (double)aw, bd = (double)bw;   // exact: < 2^53
         uint64_t r;

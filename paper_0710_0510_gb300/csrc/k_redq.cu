@@ -21,7 +21,8 @@ namespace qadic {
 
 namespace {
 
-constexpr int kThreads = 512;
+constexpr int kThreads = 1024;
+constexpr int kUnroll = 4;
 
 struct RedqParams {
     uint32_t p, s, d;          // prime, log2 q, top digit index (ndigits - 1)
@@ -48,14 +49,16 @@ __device__ __forceinline__ double redq_word(double x, const RedqParams &P, const
         rop = f64_to_u64_exact(__dmul_ru(x, P.inv_p_up));
     }
     const uint32_t p = P.p, s = P.s, d = P.d;
+    // u_j = floor(r/q^j) - p floor(rop/q^j) lies in [0, p) (Thm. 2), so it is
+    // computed exactly from the low 32 bits of both shifted words.
+    auto digit = [&](uint32_t j) -> uint32_t {
+        const uint32_t sh = s * j;
+        return (uint32_t)(r >> sh) - p * (uint32_t)(rop >> sh);
+    };
     if (MODE == 3) {
-        uint32_t idx = 0, pw = 1;
-        for (uint32_t j = 0; j <= d; ++j) {
-            const uint32_t u = (uint32_t)((r >> (s * j)) - (uint64_t)p * (rop >> (s * j)));
-            idx += u * pw;
-            pw *= p;
-        }
-        return tfull[idx];
+        uint32_t idx = digit(d);   // sum_j u_j p^j by Horner from the top digit
+        for (int j = (int)d - 1; j >= 0; --j) idx = idx * p + digit((uint32_t)j);
+        return tfull[min(idx, P.table_entries - 1)];
     }
     if (MODE == 2) {
         // lookups at starts 0, kk-1, 2(kk-1), ..., the last clipped to d+1-kk
@@ -65,14 +68,9 @@ __device__ __forceinline__ double redq_word(double x, const RedqParams &P, const
         while (true) {
             const bool last = start + kk >= d + 1;
             const uint32_t st = last ? d + 1 - kk : start;
-            uint32_t idx = 0, pw = 1;
-            for (uint32_t j = 0; j < kk; ++j) {
-                const uint32_t sh = s * (st + j);
-                const uint32_t u = (uint32_t)((r >> sh) - (uint64_t)p * (rop >> sh));
-                idx += u * pw;
-                pw *= p;
-            }
-            const uint64_t e = tk[idx];   // mu_0..mu_{kk-1} packed at s-bit spacing
+            uint32_t idx = digit(st + kk - 1);
+            for (int j = (int)kk - 2; j >= 0; --j) idx = idx * p + digit(st + (uint32_t)j);
+            const uint64_t e = tk[min(idx, P.table_entries - 1)];   // mu packed at s-bit spacing
             if (last) {
                 // keep the positions not written by earlier lookups
                 const uint32_t skip = start - st;
@@ -90,7 +88,7 @@ __device__ __forceinline__ double redq_word(double x, const RedqParams &P, const
     uint32_t u_next = 0;
     for (int j = (int)d; j >= 0; --j) {
         const uint32_t sh = s * (uint32_t)j;
-        const uint32_t u = (uint32_t)((r >> sh) - (uint64_t)p * (rop >> sh));
+        const uint32_t u = digit((uint32_t)j);
         uint32_t mu;
         if (j == (int)d) {
             mu = u;
@@ -103,7 +101,7 @@ __device__ __forceinline__ double redq_word(double x, const RedqParams &P, const
             const uint32_t hi = __shfl_sync(0xffffffffu, lane_t1, idx & 31);
             mu = idx < 32 ? lo : hi;
         } else {
-            mu = t1[u * p + u_next];
+            mu = t1[min(u * p + u_next, p * p - 1)];
         }
         rho |= (uint64_t)mu << sh;
         u_next = u;
@@ -176,24 +174,28 @@ redq_kernel(const double *__restrict__ in, double *__restrict__ out, int64_t cou
 
     // Warp-uniform grid-stride loop (every lane of a warp runs every
     // iteration, so the shuffle table of mode 1 always sees a full warp);
-    // two 16-byte loads in flight per thread.
+    // kUnroll 16-byte loads in flight per thread.
     const int64_t npairs = count >> 1;
     const double2 *in2 = reinterpret_cast<const double2 *>(in);
     double2 *out2 = reinterpret_cast<double2 *>(out);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
     for (int64_t wb = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); wb < npairs;
-         wb += 2 * stride) {
-        const int64_t i0 = wb + lane, i1 = wb + stride + lane;
-        const double2 w0 = i0 < npairs ? __ldcs(in2 + i0) : make_double2(0.0, 0.0);
-        const double2 w1 = i1 < npairs ? __ldcs(in2 + i1) : make_double2(0.0, 0.0);
-        double2 o0, o1;
-        o0.x = redq_word<MODE, INT_FLOOR>(w0.x, P, t1, tk, tfull, lane_t0, lane_t1);
-        o0.y = redq_word<MODE, INT_FLOOR>(w0.y, P, t1, tk, tfull, lane_t0, lane_t1);
-        o1.x = redq_word<MODE, INT_FLOOR>(w1.x, P, t1, tk, tfull, lane_t0, lane_t1);
-        o1.y = redq_word<MODE, INT_FLOOR>(w1.y, P, t1, tk, tfull, lane_t0, lane_t1);
-        if (i0 < npairs) __stcs(out2 + i0, o0);
-        if (i1 < npairs) __stcs(out2 + i1, o1);
+         wb += kUnroll * stride) {
+        double2 w[kUnroll];
+#pragma unroll
+        for (int s = 0; s < kUnroll; ++s) {
+            const int64_t i = wb + s * stride + lane;
+            w[s] = i < npairs ? __ldcs(in2 + i) : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int s = 0; s < kUnroll; ++s) {
+            const int64_t i = wb + s * stride + lane;
+            double2 o;
+            o.x = redq_word<MODE, INT_FLOOR>(w[s].x, P, t1, tk, tfull, lane_t0, lane_t1);
+            o.y = redq_word<MODE, INT_FLOOR>(w[s].y, P, t1, tk, tfull, lane_t0, lane_t1);
+            if (i < npairs) __stcs(out2 + i, o);
+        }
     }
     // odd tail word (all lanes take part in the shuffles above; here only
     // the shuffle-free modes can be used by a single thread)

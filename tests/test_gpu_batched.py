@@ -1,0 +1,156 @@
+"""GPU parity of the batched persistent kernel (qadic_batched_gemm) against
+the oracle, product by product, bit-exact."""
+import numpy as np
+import pytest
+
+import paper_0710_0510_gb300 as q
+from paper_0710_0510_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    assert torch.cuda.is_available()
+    return torch
+
+
+class Batch:
+    """Products laid out in three flat device buffers (A, B, C)."""
+
+    def __init__(self, torch, fields, shapes, fidx, seed):
+        rng = np.random.default_rng(seed)
+        self.fields, self.shapes, self.fidx = fields, shapes, fidx
+        self.A, self.B, offs = [], [], []
+        oa = ob = oc = 0
+        for (m, n, K), fi in zip(shapes, fidx):
+            f = fields[fi]
+            self.A.append(rng.integers(0, f.p, (f.k, m, K), dtype=np.uint8))
+            self.B.append(rng.integers(0, f.p, (f.k, K, n), dtype=np.uint8))
+            offs.append((oa, ob, oc))
+            oa += f.k * m * K
+            ob += f.k * K * n
+            oc += f.k * m * n
+        self.dA = torch.from_numpy(np.concatenate([a.ravel() for a in self.A])).cuda()
+        self.dB = torch.from_numpy(np.concatenate([b.ravel() for b in self.B])).cuda()
+        self.dC = torch.zeros(oc, dtype=torch.uint8, device="cuda")
+        self.offs = offs
+        self.descs = []
+        for i, ((m, n, K), fi) in enumerate(zip(shapes, fidx)):
+            a, b, c = offs[i]
+            self.descs.append(q.GemmDesc(fi, m, n, K, self.dA.data_ptr() + a,
+                                         self.dB.data_ptr() + b, self.dC.data_ptr() + c,
+                                         K, n, n, 0))
+        ws = q.batched_workspace_size(self.descs)
+        self.ws = torch.empty(ws, dtype=torch.uint8, device="cuda")
+
+    def run(self, graph=False):
+        q.batched_gemm(self.fields, self.descs, self.ws, graph=graph)
+
+    def result(self, i):
+        m, n, K = self.shapes[i]
+        f = self.fields[self.fidx[i]]
+        c = self.offs[i][2]
+        return self.dC[c:c + f.k * m * n].cpu().numpy().reshape(f.k, m, n)
+
+    def expected(self, orc, i):
+        f = self.fields[self.fidx[i]]
+        C = orc.gemm(f.p, f.poly, np.transpose(self.A[i], (1, 2, 0)),
+                     np.transpose(self.B[i], (1, 2, 0)))
+        return np.transpose(C, (2, 0, 1))
+
+
+def mixed_fields():
+    return [q.Field(2, 8), q.Field(7, 4), q.Field(31, 2)]
+
+
+def test_batched_mixed_fields(torch, orc):
+    fields = mixed_fields()
+    dims, fidx = W.batched_shapes(60, salt=1)
+    shapes = [tuple(int(x) for x in d) for d in dims]
+    shapes[:5] = [(1, 1, 1), (16, 16, 16), (256, 256, 256), (65, 17, 33), (3, 200, 7)]
+    bt = Batch(torch, fields, shapes, [int(x) for x in fidx], seed=5)
+    bt.run()
+    q.sync_status()
+    for i in range(len(shapes)):
+        assert np.array_equal(bt.result(i), bt.expected(orc, i)), (i, shapes[i], fidx[i])
+
+
+@pytest.mark.parametrize("pk", [(3, 3), (5, 5), (2, 6), (101, 2), (3, 7), (13, 3), (2, 1)])
+def test_batched_other_fields(torch, orc, pk):
+    fields = [q.Field(*pk)]
+    shapes = [(33, 47, 95), (64, 64, 64), (100, 3, 250), (1, 70, 129)]
+    bt = Batch(torch, fields, shapes, [0] * len(shapes), seed=pk[0])
+    bt.run()
+    for i in range(len(shapes)):
+        assert np.array_equal(bt.result(i), bt.expected(orc, i)), (pk, shapes[i])
+
+
+def test_batched_exact_chunks_p251(torch, orc):
+    """GF(251^2): the exact FP32 chunk is 536 -> 16 K-blocks of 32, so
+    K = 2000 crosses three in-register reductions; all-max inputs push every
+    chunk to the bound."""
+    f = q.Field(251, 2)
+    shapes = [(64, 64, 2000), (50, 70, 1100)]
+    bt = Batch(torch, [f], shapes, [0, 0], seed=2)
+    bt.A[0][:] = 126                      # centred -125 for every coefficient
+    bt.B[0][:] = 126
+    bt.dA[: bt.A[0].size] = torch.from_numpy(bt.A[0].ravel()).cuda()
+    bt.dB[: bt.B[0].size] = torch.from_numpy(bt.B[0].ravel()).cuda()
+    bt.run()
+    for i in range(len(shapes)):
+        assert np.array_equal(bt.result(i), bt.expected(orc, i))
+
+
+def test_batched_graph_replay(torch, orc):
+    fields = mixed_fields()
+    dims, fidx = W.batched_shapes(40, salt=2)
+    shapes = [tuple(int(x) for x in d) for d in dims]
+    bt = Batch(torch, fields, shapes, [int(x) for x in fidx], seed=9)
+    bt.run(graph=True)
+    first = [bt.result(i) for i in range(len(shapes))]
+    bt.dC.zero_()
+    bt.run(graph=True)                     # replay of the cached graph
+    for i in range(len(shapes)):
+        assert np.array_equal(bt.result(i), first[i])
+        assert np.array_equal(first[i], bt.expected(orc, i))
+    # new input data behind the same pointers is picked up by the replay
+    new = np.random.default_rng(3).integers(0, fields[bt.fidx[0]].p, bt.A[0].shape,
+                                            dtype=np.uint8)
+    bt.A[0] = new
+    bt.dA[: new.size] = torch.from_numpy(new.ravel()).cuda()
+    bt.run(graph=True)
+    assert np.array_equal(bt.result(0), bt.expected(orc, 0))
+
+
+def test_batched_matches_plane_gemm(torch, orc):
+    """One GF(101^2) product through both the batched kernel and the
+    tensor-core plane GEMM."""
+    f = q.Field(101, 2)
+    m, n, K = 192, 160, 300
+    bt = Batch(torch, [f], [(m, n, K)], [0], seed=4)
+    bt.run()
+    a = f.pack(q.FMT_COEFF_U8, torch.from_numpy(bt.A[0]).cuda(), m, K, q.FMT_OPERAND_A,
+               out=torch.zeros((2, m, 304), dtype=torch.bfloat16, device="cuda"), ld_out=304)
+    b = f.pack(q.FMT_COEFF_U8, torch.from_numpy(bt.B[0]).cuda(), K, n, q.FMT_OPERAND_B,
+               out=torch.zeros((2, n, 304), dtype=torch.bfloat16, device="cuda"), ld_out=304)
+    C = f.gemm(q.PATH_PLANES, a, b, m, n, K, lda=304, ldb=304).cpu().numpy()
+    assert np.array_equal(bt.result(0), C)
+
+
+def test_batched_rejects_bad_descriptors(torch):
+    f = q.Field(31, 2)
+    x = torch.zeros(1024, dtype=torch.uint8, device="cuda")
+    ws = torch.zeros(1 << 16, dtype=torch.uint8, device="cuda")
+    good = q.GemmDesc(0, 4, 4, 4, x.data_ptr(), x.data_ptr(), x.data_ptr(), 4, 4, 4, 0)
+    for bad in (q.GemmDesc(1, 4, 4, 4, x.data_ptr(), x.data_ptr(), x.data_ptr(), 4, 4, 4, 0),
+                q.GemmDesc(0, 0, 4, 4, x.data_ptr(), x.data_ptr(), x.data_ptr(), 4, 4, 4, 0),
+                q.GemmDesc(0, 4, 4, 4, x.data_ptr(), x.data_ptr(), x.data_ptr(), 3, 4, 4, 0),
+                q.GemmDesc(0, 4, 4, 4, 0, x.data_ptr(), x.data_ptr(), 4, 4, 4, 0)):
+        with pytest.raises(q.QadicError) as e:
+            q.batched_gemm([f], [good, bad], ws)
+        assert e.value.status == q.E_INVALID
+    with pytest.raises(q.QadicError) as e:
+        q.batched_gemm([f], [good], ws[:64])
+    assert e.value.status == q.E_NOMEM

@@ -261,6 +261,42 @@ def test_gemm_planes_sums_at_the_fp32_limit(torch, orc, p, val):
     assert (got == got[:, :1, :1]).all()
 
 
+@pytest.mark.parametrize("pk,shape", [((3, 3), (200, 130, 300)), ((7, 4), (129, 64, 256)),
+                                      ((13, 3), (128, 192, 1000)), ((5, 4), (77, 65, 90)),
+                                      ((31, 3), (128, 64, 64 * 390 + 20))])
+def test_gemm_planes_k3_k4(torch, orc, pk, shape):
+    """k = 3, 4: one MMA of N = k*64 per A plane into 2k-1 accumulators;
+    GF(31^3) with K = 24980 crosses the exact FP32 chunk (24855)."""
+    p, k = pk
+    m, n, K = shape
+    f = q.Field(p, k)
+    h = (p - 1) // 2
+    A = W.centred_planes(k, m, K, h, salt=m + 1)
+    B = W.centred_planes(k, K, n, h, salt=n + 2)
+    got = run_planes(torch, f, q.FMT_INT8_PLANES, A, B, m, n, K)
+    assert np.array_equal(got, oracle_gemm_from_planes(orc, p, f.poly, A, B))
+
+
+@pytest.mark.parametrize("rows,cols", [(64, 128), (45, 128), (128, 64), (7, 192)])
+def test_pack_aligned_fast_paths(torch, orc, rows, cols):
+    for p in (101, 251, 3):
+        k = 2 if p > 3 else 3
+        f = q.Field(p, k)
+        I8 = np.random.default_rng(rows + p).integers(-128, 128, (k, rows, cols), dtype=np.int8)
+        U8 = np.random.default_rng(cols + p).integers(0, 256, (k, rows, cols), dtype=np.uint8)
+        for fmt, X in ((q.FMT_INT8_PLANES, I8), (q.FMT_COEFF_U8, U8)):
+            cen = orc.centred(np.transpose(X.astype(np.int64) % p, (1, 2, 0)), p)
+            x = dev(torch, X)
+            ldb = (rows + 7) // 8 * 8
+            a = host(f.pack(fmt, x, rows, cols, q.FMT_OPERAND_A).float())
+            assert np.array_equal(a, np.transpose(cen, (2, 0, 1)))
+            b = host(f.pack(fmt, x, rows, cols, q.FMT_OPERAND_B, ld_out=ldb,
+                            out=torch.zeros((k, cols, ldb), dtype=torch.bfloat16,
+                                            device="cuda")).float())
+            assert np.array_equal(b[:, :, :rows], np.transpose(cen, (2, 1, 0)))
+            assert not b[:, :, rows:].any()
+
+
 def test_gemm_planes_k0_gives_zero(torch):
     f = q.Field(101, 2)
     a = torch.zeros((2, 4, 8), dtype=torch.bfloat16, device="cuda")
