@@ -217,6 +217,27 @@ int qadic_batched_gemm(const qadic_field *const *fields, int32_t nfields,
                        const qadic_gemm_desc *descs, int64_t count, void *workspace,
                        size_t ws_bytes, uint32_t flags, void *stream);
 
+/* ------------------------------------------------ batched_gemm_noalloc --
+ * The same products as qadic_batched_gemm (same descriptors, same results),
+ * for callers that must not allocate memory during the call: code running
+ * under a framework whose allocator owns all device memory, latency-bound
+ * loops where cudaMalloc/cudaFree would synchronise the device, or plugins
+ * that are handed only their input and output buffers and no workspace.
+ * The paper has no counterpart; this is a property of the library only.
+ *   The work list is kept in a fixed 8 MiB device array inside the library
+ *   (built on the host in a fixed host array of the same size); no device or
+ *   host memory is allocated and no allocating routine is called.  Every
+ *   device that loads the library holds that array until the process exits.
+ *   The first call on a device looks up the array's device address; make
+ *   that first call before capturing a stream into a CUDA graph.
+ *   All calls share the one array and each call rewrites it from the start
+ *   (the tile counter included), so calls whose kernels overlap on the GPU
+ *   race: order them on one stream, or synchronise in between.
+ *   QADIC_E_INVALID when the work list would exceed the array (about
+ *   8 MiB / 8 bytes per 32 x 16 output tile); use qadic_batched_gemm then. */
+int qadic_batched_gemm_noalloc(const qadic_field *const *fields, int32_t nfields,
+                               const qadic_gemm_desc *descs, int64_t count, void *stream);
+
 /* --------------------------------------------------------------- status --
  * Synchronises `stream` and returns QADIC_E_DEVICE_TIMEOUT if a kernel of
  * this library on the current device gave up a bounded wait since the last

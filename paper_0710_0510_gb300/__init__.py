@@ -81,6 +81,9 @@ _SIGS = {
                                           ctypes.POINTER(GemmDesc), ctypes.c_int64,
                                           ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32,
                                           ctypes.c_void_p]),
+    "qadic_batched_gemm_noalloc": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32,
+                                                  ctypes.POINTER(GemmDesc), ctypes.c_int64,
+                                                  ctypes.c_void_p]),
     "qadic_sync_status": (ctypes.c_int, [ctypes.c_void_p]),
     "qadic_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "qadic_last_error": (ctypes.c_char_p, []),
@@ -259,6 +262,15 @@ def batched_gemm(fields, descs, workspace, graph: bool = False, stream=None):
     _check(lib().qadic_batched_gemm(hs, len(fields), arr, len(descs), _ptr(workspace),
                                     workspace.numel() * workspace.element_size(),
                                     BATCHED_GRAPH if graph else 0, _stream(stream)))
+
+
+def batched_gemm_noalloc(fields, descs, stream=None):
+    """Same products as batched_gemm without any allocation
+    (``qadic_batched_gemm_noalloc``: fixed library-owned scratch, calls that
+    overlap on the GPU race)."""
+    arr = (GemmDesc * len(descs))(*descs)
+    hs = (ctypes.c_void_p * len(fields))(*[f.handle for f in fields])
+    _check(lib().qadic_batched_gemm_noalloc(hs, len(fields), arr, len(descs), _stream(stream)))
 
 
 def sync_status(stream=None):

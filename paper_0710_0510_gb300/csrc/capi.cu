@@ -59,6 +59,8 @@ bool on_device(const Field &f) {
 
 }  // namespace
 
+const Field *field_of(const qadic_field *handle) { return handle ? &handle->f : nullptr; }
+
 int set_error(int status, const char *fmt, ...) {
     char buf[512];
     va_list ap;

@@ -79,7 +79,8 @@ struct TileCfg {
 __host__ __device__ constexpr int max_i(int a, int b) { return a > b ? a : b; }
 
 constexpr int kSmemBytes =
-    max_i(max_i(TileCfg<2>::SMEM, TileCfg<4>::SMEM), max_i(TileCfg<8>::SMEM, TileCfg<1>::SMEM));
+    max_i(max_i(max_i(TileCfg<1>::SMEM, TileCfg<2>::SMEM), max_i(TileCfg<3>::SMEM, TileCfg<4>::SMEM)),
+          max_i(max_i(TileCfg<5>::SMEM, TileCfg<6>::SMEM), max_i(TileCfg<7>::SMEM, TileCfg<8>::SMEM)));
 
 __device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2,
                                         uint32_t &r3) {
@@ -482,3 +483,174 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
 }
 
 }  // namespace qadic
+
+// ------------------------------------------------------------------------
+// Allocation-free variant of qadic_batched_gemm.
+//
+// The work list lives in a fixed device array that belongs to this library
+// instead of in a caller-provided workspace, and the host side builds it in
+// a fixed host array, so a call allocates no memory of any kind.  Every
+// device that loads the library keeps the array until the process exits.
+// All calls share it: the header (tile counter included) is rewritten by
+// every call, and two calls whose kernels overlap on the GPU race on it.
+namespace qadic {
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 8u << 20;   // 8 MiB
+
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mu;
+alignas(256) uint8_t g_noalloc_host[kNoAllocScratchBytes];
+void *g_noalloc_dev[64] = {nullptr};
+
+// Device address of the array on the current device, looked up once per
+// device (the symbol's name is only a host-side stand-in).
+int noalloc_device_ptr(int dev, void **out) {
+    if (dev < 0 || dev >= 64) return set_error(QADIC_E_INVALID, "device index %d", dev);
+    if (!g_noalloc_dev[dev]) {
+        void *ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr)
+            return set_error(QADIC_E_CUDA, "scratch address: %s", cudaGetErrorString(e));
+        g_noalloc_dev[dev] = ptr;
+    }
+    *out = g_noalloc_dev[dev];
+    return QADIC_OK;
+}
+
+}  // namespace
+
+int launch_batched_noalloc(const Field *const *fields, int32_t nfields,
+                           const qadic_gemm_desc *descs, int64_t count, cudaStream_t stream) {
+    if (nfields < 1 || nfields > kMaxFields)
+        return set_error(QADIC_E_INVALID, "nfields must be in [1, %d]", kMaxFields);
+    if (count > (1 << 24)) return set_error(QADIC_E_INVALID, "too many products");
+    int dev = -1;
+    cudaGetDevice(&dev);
+    for (int32_t i = 0; i < nfields; ++i) {
+        if (!fields[i]) return set_error(QADIC_E_INVALID, "field %d is NULL", i);
+        if (fields[i]->device != dev)
+            return set_error(QADIC_E_INVALID, "field %d lives on another device", i);
+    }
+    for (int64_t i = 0; i < count; ++i) {
+        const qadic_gemm_desc &d = descs[i];
+        if (d.field < 0 || d.field >= nfields)
+            return set_error(QADIC_E_INVALID, "desc %lld: field index out of range", (long long)i);
+        if (d.m < 1 || d.n < 1 || d.K < 1 || d.m > 4096 || d.n > 4096 || d.K > 4096)
+            return set_error(QADIC_E_INVALID, "desc %lld: sizes must be in [1, 4096]", (long long)i);
+        if (!d.A || !d.B || !d.C) return set_error(QADIC_E_INVALID, "desc %lld: NULL", (long long)i);
+        if (d.lda < d.K || d.ldb < d.n || d.ldc < d.n)
+            return set_error(QADIC_E_INVALID, "desc %lld: leading dimension too small",
+                             (long long)i);
+        if (fields[d.field]->k_chunk_f32 < BK)
+            return set_error(QADIC_E_OVERFLOW, "exact FP32 chunk below one K-block");
+    }
+    const Layout L = layout_for(count, max_tiles(descs, count));
+    if (L.total > kNoAllocScratchBytes)
+        return set_error(QADIC_E_INVALID,
+                         "work list of %zu bytes exceeds the %zu-byte fixed scratch of the "
+                         "allocation-free entry point; use qadic_batched_gemm with a workspace",
+                         L.total, kNoAllocScratchBytes);
+
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    void *dptr = nullptr;
+    int st = noalloc_device_ptr(dev, &dptr);
+    if (st != QADIC_OK) return st;
+
+    uint8_t *host = g_noalloc_host;
+    std::memset(host, 0, L.tiles_off);
+    BFieldParams *fp = reinterpret_cast<BFieldParams *>(host + L.fields_off);
+    for (int32_t i = 0; i < nfields; ++i) {
+        const Field &f = *fields[i];
+        BFieldParams &F = fp[i];
+        F.p = f.p;
+        F.k = f.k;
+        F.h = f.h;
+        F.m32 = make_mod_small(f.p);
+        F.pf = (float)f.p;
+        F.inv_pf = 1.0f / (float)f.p;
+        F.chunk_blocks = (int32_t)std::min<int64_t>(f.k_chunk_f32 / BK, 1 << 20);
+        for (uint32_t t = 0; t + 1 < f.k; ++t)
+            for (uint32_t c = 0; c < f.k; ++c) F.fold[t * f.k + c] = f.fold[t * f.k + c];
+    }
+    BProd *pp = reinterpret_cast<BProd *>(host + L.prods_off);
+    BTile *tp = reinterpret_cast<BTile *>(host + L.tiles_off);
+    int64_t nt = 0;
+    for (int64_t i = 0; i < count; ++i) {
+        const qadic_gemm_desc &d = descs[i];
+        BProd &P = pp[i];
+        P.A = d.A;
+        P.B = d.B;
+        P.C = d.C;
+        P.m = d.m;
+        P.n = d.n;
+        P.K = d.K;
+        P.lda = d.lda;
+        P.ldb = d.ldb;
+        P.ldc = d.ldc;
+        P.field = d.field;
+        int bm, bn;
+        tile_shape(fields[d.field]->k, bm, bn);
+        for (int tm = 0; tm * bm < d.m; ++tm)
+            for (int tn = 0; tn * bn < d.n; ++tn) tp[nt++] = BTile{(int32_t)i, (int16_t)tm, (int16_t)tn};
+    }
+    // largest tiles first; std::sort works in place
+    auto cost = [&](const BTile &t) {
+        const qadic_gemm_desc &d = descs[t.prod];
+        const uint64_t k = fields[d.field]->k;
+        int bm, bn;
+        tile_shape((uint32_t)k, bm, bn);
+        return (uint64_t)bm * bn * (uint64_t)((d.K + BK - 1) / BK) * k * k;
+    };
+    std::sort(tp, tp + nt, [&](const BTile &a, const BTile &b) {
+        const uint64_t ca = cost(a), cb = cost(b);
+        if (ca != cb) return ca > cb;
+        if (a.prod != b.prod) return a.prod < b.prod;
+        return a.tm != b.tm ? a.tm < b.tm : a.tn < b.tn;
+    });
+    BHeader *hdr = reinterpret_cast<BHeader *>(host);
+    hdr->counter = 0;   // every call starts the tile counter from zero
+    hdr->ntiles = (int32_t)nt;
+    hdr->nprod = (int32_t)count;
+    hdr->nfields = nfields;
+    hdr->fields_off = (uint32_t)L.fields_off;
+    hdr->prods_off = (uint32_t)L.prods_off;
+    hdr->tiles_off = (uint32_t)L.tiles_off;
+    const size_t used = L.tiles_off + (size_t)nt * sizeof(BTile);
+    // A copy from pageable host memory returns once the data has been staged,
+    // so the host array may be rewritten by the next call.
+    if (cudaMemcpyAsync(dptr, host, used, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+        return set_error(QADIC_E_CUDA, "work list upload: %s", cudaGetErrorString(cudaGetLastError()));
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel, kThreads, 0) !=
+            cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    int64_t grid = (int64_t)sms * per_sm;
+    if (nt < grid) grid = std::max<int64_t>(1, nt);
+    batched_kernel<<<(unsigned)grid, kThreads, 0, stream>>>((uint8_t *)dptr);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(QADIC_E_CUDA, "batched launch: %s", cudaGetErrorString(e));
+    return QADIC_OK;
+}
+
+}  // namespace qadic
+
+using namespace qadic;
+
+extern "C" int qadic_batched_gemm_noalloc(const qadic_field *const *fields, int32_t nfields,
+                                          const qadic_gemm_desc *descs, int64_t count,
+                                          void *stream) {
+    if (count < 0) return set_error(QADIC_E_INVALID, "negative count");
+    if (count == 0) return QADIC_OK;
+    if (!fields || !descs) return set_error(QADIC_E_INVALID, "NULL fields or descs");
+    if (nfields < 1 || nfields > 64) return set_error(QADIC_E_INVALID, "nfields outside [1, 64]");
+    const Field *fs[64];
+    for (int32_t i = 0; i < nfields; ++i) {
+        if (!fields[i]) return set_error(QADIC_E_INVALID, "field %d is NULL", i);
+        fs[i] = field_of(fields[i]);
+    }
+    return launch_batched_noalloc(fs, nfields, descs, count, (cudaStream_t)stream);
+}

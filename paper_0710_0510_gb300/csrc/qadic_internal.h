@@ -41,6 +41,9 @@ struct Field {
     uint8_t *d_fold = nullptr;
 };
 
+// The library-side field behind an opaque handle (capi.cu).
+const Field *field_of(const qadic_field *handle);
+
 // Field construction (field.cpp).
 bool is_prime(uint32_t p);
 bool poly_irreducible(uint32_t p, uint32_t k, const uint32_t *P);
