@@ -66,8 +66,8 @@ constexpr size_t kHeaderBytes = 256;
 
 template <int KP>
 struct TileCfg {
-    static constexpr int BM = KP <= 2 ? 64 : KP <= 4 ? 64 : 32;
-    static constexpr int BN = KP <= 2 ? 64 : KP <= 4 ? 32 : 16;
+    static constexpr int BM = KP <= 2 ? 64 : 32;
+    static constexpr int BN = KP <= 2 ? 32 : KP <= 4 ? 32 : 16;
     static constexpr int WM = BM / 2, WN = BN / 2;   // 2 x 2 warps
     static constexpr int MT = WM / 16, NT = WN / 8;
     static constexpr int NACC = 2 * KP - 1;
@@ -110,8 +110,100 @@ __device__ __forceinline__ __nv_bfloat16 centred_bf16(uint32_t c, const BFieldPa
     return __int2bfloat16_rn(v);
 }
 
+// 16 consecutive bytes of a row starting at `src` (any alignment); only the
+// first `valid` (<= 16) are read, the others are zero.  In the full case the
+// bytes come from aligned 32-bit loads joined by funnel shifts; every word
+// loaded holds at least one of the 16 bytes, so no load leaves the buffer.
+__device__ __forceinline__ void load16(const uint8_t *src, int valid, uint32_t (&w)[4]) {
+    if (valid >= 16) {
+        const uint32_t a = (uint32_t)((uintptr_t)src & 3);
+        const uint32_t *base = reinterpret_cast<const uint32_t *>(src - a);
+        if (a == 0) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) w[i] = __ldg(base + i);
+        } else {
+            uint32_t x[5];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) x[i] = __ldg(base + i);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) w[i] = __funnelshift_r(x[i], x[i + 1], 8 * a);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) w[i] = 0;
+        for (int b = 0; b < valid; ++b) w[b >> 2] |= (uint32_t)__ldg(src + b) << (8 * (b & 3));
+    }
+}
+
+// Tile staging: chunks of 16 coefficients (one row segment of one plane).
 template <int KP>
-__device__ void run_tile(const BProd &P, const BFieldParams &F, int tm, int tn, uint8_t *smem) {
+struct Stager {
+    using T = TileCfg<KP>;
+    static constexpr int A_CH = KP * T::BM * (BK / 16);
+    static constexpr int B_CH = KP * BK * (T::BN / 16);
+    static constexpr int PER_THREAD = (A_CH + B_CH + kThreads - 1) / kThreads;
+
+    uint32_t raw[PER_THREAD][4];
+
+    __device__ __forceinline__ void load(const BProd &P, int row0, int col0, int k0) {
+#pragma unroll
+        for (int s = 0; s < PER_THREAD; ++s) {
+            const int c = threadIdx.x + s * kThreads;
+            if (c < A_CH) {
+                const int part = c % (BK / 16), r = (c / (BK / 16)) % T::BM,
+                          i = c / ((BK / 16) * T::BM);
+                const int gr = row0 + r, gk = k0 + part * 16;
+                const int valid = gr < P.m ? min(16, max(0, P.K - gk)) : 0;
+                load16(P.A + ((int64_t)i * P.m + gr) * P.lda + gk, valid, raw[s]);
+            } else if (c < A_CH + B_CH) {
+                const int cb = c - A_CH;
+                const int part = cb % (T::BN / 16), r = (cb / (T::BN / 16)) % BK,
+                          j = cb / ((T::BN / 16) * BK);
+                const int gk = k0 + r, gc = col0 + part * 16;
+                const int valid = gk < P.K ? min(16, max(0, P.n - gc)) : 0;
+                load16(P.B + ((int64_t)j * P.K + gk) * P.ldb + gc, valid, raw[s]);
+            }
+        }
+    }
+
+    // bytes -> centred bf16 through the 256-entry table, 32-byte stores
+    __device__ __forceinline__ void store(__nv_bfloat16 *As, __nv_bfloat16 *Bs,
+                                          const uint16_t *tab) const {
+#pragma unroll
+        for (int s = 0; s < PER_THREAD; ++s) {
+            const int c = threadIdx.x + s * kThreads;
+            uint32_t o[8];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t w = raw[s][q];
+                o[2 * q] = (uint32_t)tab[w & 0xff] | ((uint32_t)tab[(w >> 8) & 0xff] << 16);
+                o[2 * q + 1] = (uint32_t)tab[(w >> 16) & 0xff] | ((uint32_t)tab[w >> 24] << 16);
+            }
+            __nv_bfloat16 *dst = nullptr;
+            if (c < A_CH) {
+                const int part = c % (BK / 16), r = (c / (BK / 16)) % T::BM,
+                          i = c / ((BK / 16) * T::BM);
+                dst = As + (i * T::BM + r) * T::LDA + part * 16;
+            } else if (c < A_CH + B_CH) {
+                const int cb = c - A_CH;
+                const int part = cb % (T::BN / 16), r = (cb / (T::BN / 16)) % BK,
+                          j = cb / ((T::BN / 16) * BK);
+                dst = Bs + (j * BK + r) * T::LDB + part * 16;
+            }
+            if (dst) {
+                uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+                d4[0] = make_uint4(o[0], o[1], o[2], o[3]);
+                d4[1] = make_uint4(o[4], o[5], o[6], o[7]);
+            }
+        }
+    }
+};
+
+// Not inlined: each k variant is register-allocated on its own instead of
+// inside one kernel body holding all eight.
+template <int KP>
+__device__ __noinline__ void run_tile(const BProd &P, const BFieldParams &F, int tm, int tn,
+                                      uint8_t *smem, const uint16_t *tab) {
     using T = TileCfg<KP>;
     __nv_bfloat16 *As = reinterpret_cast<__nv_bfloat16 *>(smem);   // [KP][BM][LDA]
     __nv_bfloat16 *Bs = As + KP * T::BM * T::LDA;                   // [KP][BK][LDB]
@@ -130,27 +222,14 @@ __device__ void run_tile(const BProd &P, const BFieldParams &F, int tm, int tn, 
                 for (int e = 0; e < 4; ++e) acc[t][a][b][e] = 0.f;
 
     const int nkb = (P.K + BK - 1) / BK;
+    Stager<KP> stage;
+    stage.load(P, row0, col0, 0);
     for (int kb = 0; kb < nkb; ++kb) {
-        const int k0 = kb * BK;
         __syncthreads();   // previous tile/step finished reading shared memory
-#pragma unroll 4
-        for (int e = threadIdx.x; e < KP * T::BM * BK; e += kThreads) {
-            const int c = e % BK, r = (e / BK) % T::BM, i = e / (BK * T::BM);
-            const int gr = row0 + r, gk = k0 + c;
-            uint32_t v = 0;
-            if (gr < P.m && gk < P.K) v = __ldg(P.A + ((int64_t)i * P.m + gr) * P.lda + gk);
-            As[(i * T::BM + r) * T::LDA + c] = centred_bf16(v, F);
-        }
-#pragma unroll 4
-        for (int e = threadIdx.x; e < KP * BK * T::BN; e += kThreads) {
-            const int c = e % T::BN, r = (e / T::BN) % BK, j = e / (T::BN * BK);
-            const int gk = k0 + r, gc = col0 + c;
-            uint32_t v = 0;
-            if (gk < P.K && gc < P.n) v = __ldg(P.B + ((int64_t)j * P.K + gk) * P.ldb + gc);
-            Bs[(j * BK + r) * T::LDB + c] = centred_bf16(v, F);
-        }
+        stage.store(As, Bs, tab);
         __syncthreads();
-#pragma unroll
+        if (kb + 1 < nkb) stage.load(P, row0, col0, (kb + 1) * BK);   // in flight during the MMAs
+#pragma unroll 1
         for (int ks = 0; ks < BK / 16; ++ks) {
             uint32_t bfr[KP][T::NT][2];
 #pragma unroll
@@ -228,39 +307,51 @@ __device__ void run_tile(const BProd &P, const BFieldParams &F, int tm, int tn, 
             }
 }
 
-__global__ void __launch_bounds__(kThreads, 2) batched_kernel(uint8_t *ws) {
+__global__ void __launch_bounds__(kThreads, 3) batched_kernel(uint8_t *ws) {
     __shared__ __align__(16) uint8_t smem[kSmemBytes];
-    __shared__ int s_tile;
+    __shared__ uint16_t tab[256];   // input byte -> centred bf16 bits, for field s_field
+    __shared__ int s_tile, s_field;
     BHeader *hdr = reinterpret_cast<BHeader *>(ws);
     const BFieldParams *fields = reinterpret_cast<const BFieldParams *>(ws + hdr->fields_off);
     const BProd *prods = reinterpret_cast<const BProd *>(ws + hdr->prods_off);
     const BTile *tiles = reinterpret_cast<const BTile *>(ws + hdr->tiles_off);
     const int ntiles = hdr->ntiles;
+    if (threadIdx.x == 0) s_field = -1;
     while (true) {
         if (threadIdx.x == 0) s_tile = (int)atomicAdd(&hdr->counter, 1u);
         __syncthreads();
         const int t = s_tile;
+        const int cur_field = s_field;
         __syncthreads();
         if (t >= ntiles) break;
         const BTile tile = tiles[t];
-        const BProd P = prods[tile.prod];
-        const BFieldParams F = fields[P.field];
+        // descriptors stay in global memory (read-only, L1-cached) and are
+        // read where used instead of being copied into registers
+        const BProd &P = prods[tile.prod];
+        const BFieldParams &F = fields[P.field];
+        if (P.field != cur_field) {   // block-uniform
+            for (int b = threadIdx.x; b < 256; b += kThreads)
+                tab[b] = __bfloat16_as_ushort(centred_bf16((uint32_t)b, F));
+            if (threadIdx.x == 0) s_field = P.field;
+            // run_tile's first __syncthreads orders these writes before any use
+        }
         switch (F.k) {
-            case 1: run_tile<1>(P, F, tile.tm, tile.tn, smem); break;
-            case 2: run_tile<2>(P, F, tile.tm, tile.tn, smem); break;
-            case 3: run_tile<3>(P, F, tile.tm, tile.tn, smem); break;
-            case 4: run_tile<4>(P, F, tile.tm, tile.tn, smem); break;
-            case 5: run_tile<5>(P, F, tile.tm, tile.tn, smem); break;
-            case 6: run_tile<6>(P, F, tile.tm, tile.tn, smem); break;
-            case 7: run_tile<7>(P, F, tile.tm, tile.tn, smem); break;
-            default: run_tile<8>(P, F, tile.tm, tile.tn, smem); break;
+            case 1: run_tile<1>(P, F, tile.tm, tile.tn, smem, tab); break;
+            case 2: run_tile<2>(P, F, tile.tm, tile.tn, smem, tab); break;
+            case 3: run_tile<3>(P, F, tile.tm, tile.tn, smem, tab); break;
+            case 4: run_tile<4>(P, F, tile.tm, tile.tn, smem, tab); break;
+            case 5: run_tile<5>(P, F, tile.tm, tile.tn, smem, tab); break;
+            case 6: run_tile<6>(P, F, tile.tm, tile.tn, smem, tab); break;
+            case 7: run_tile<7>(P, F, tile.tm, tile.tn, smem, tab); break;
+            default: run_tile<8>(P, F, tile.tm, tile.tn, smem, tab); break;
         }
     }
 }
 
+// Must match TileCfg<k>::BM / BN.
 void tile_shape(uint32_t k, int &bm, int &bn) {
-    bm = k <= 4 ? 64 : 32;
-    bn = k <= 2 ? 64 : k <= 4 ? 32 : 16;
+    bm = k <= 2 ? 64 : 32;
+    bn = k <= 4 ? 32 : 16;
 }
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }

@@ -15,14 +15,21 @@
 // each chunk boundary the epilogue warps reduce the accumulators in place
 // (tcgen05.ld, x - p*rint(x/p), tcgen05.st) before the MMAs continue.
 //
-// One CTA per 128 x BN output tile, 6 warps:
-//   warp 0      TMA producer: per 64-wide K-block, the k A-plane tiles and the
-//               k B-plane tiles (128-byte swizzle) into a STAGES-deep ring
+// The k B-plane tiles of a stage sit next to each other in shared memory and
+// form one K-major operand of N = k*BN rows; with C_t at tensor-memory
+// column t*BN, one MMA of A_i against [B_0; ...; B_{k-1}] at column i*BN
+// adds A_i B_j into C_{i+j} for every j (k MMAs per 16-wide K step).
+//
+// Persistent: one CTA per SM walks output tiles (grouped raster) with
+//   warp 0      TMA producer, streaming K-blocks of consecutive tiles into a
+//               STAGES-deep ring without a break between tiles
 //   warp 1      allocates tensor memory; one thread issues tcgen05.mma
-//               (M=128, N=BN, K=16) into the 2k-1 accumulators
-//   warps 2-5   epilogue: drains, then exact mod p, fold, uint8 planes out
+//   warps 2-5   epilogue, one warp per 32-lane quarter: in-place drains; at
+//               the end of a tile they read the accumulators, reduce mod p
+//               into packed bytes, release tensor memory to the next tile's
+//               MMAs, then fold and store while those MMAs run.
 // All waits are bounded (kSpinLimit); on expiry the kernel records
-// QADIC_E_DEVICE_TIMEOUT, drains what it issued and frees tensor memory.
+// QADIC_E_DEVICE_TIMEOUT, lets its copies land and frees tensor memory.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -32,9 +39,24 @@ namespace qadic {
 
 namespace {
 
+// K-block of 64 bf16 = 128-byte rows (128-byte swizzle), 64 KB stages for
+// k = 2.  32-wide K-blocks with 64-byte swizzle fit seven stages instead of
+// three but measured 30% slower on GB300.
 constexpr int BM = 128, BK = 64, UMMA_K = 16;
+constexpr int kRowBytes = BK * 2;
+static_assert(kRowBytes == 64 || kRowBytes == 128, "supported swizzle widths");
+
+__device__ __forceinline__ uint64_t operand_desc(const void *tile) {
+    if constexpr (kRowBytes == 128) return ptx::smem_desc_sw128(tile);
+    else return ptx::smem_desc_sw64(tile);
+}
 constexpr int kGroupM = 16;
-constexpr int kThreads = 192;
+// Four epilogue warps, one per 32-lane quarter of tensor memory.  (Warps are
+// spread over the SM's four sub-partitions, each with its own register
+// file: more epilogue warps would add no issue slots and would cap the
+// registers per thread.)
+constexpr int kEpiWarps = 4;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kSmemBudget = 227 * 1024;
 
 template <int KP, int BN>
@@ -44,21 +66,25 @@ struct Cfg {
     static constexpr int B_TILE = BN * BK * 2;
     static constexpr int STAGE = KP * (A_TILE + B_TILE);
     static constexpr int STAGES_RAW = (kSmemBudget - 2048) / STAGE;
-    static constexpr int STAGES = STAGES_RAW > 6 ? 6 : STAGES_RAW;
+    static constexpr int STAGES = STAGES_RAW > 8 ? 8 : STAGES_RAW;
     static constexpr int ACC_COLS = NACC * BN;
     static constexpr int TMEM_COLS = ACC_COLS <= 32 ? 32 : ACC_COLS <= 64 ? 64
                                    : ACC_COLS <= 128 ? 128 : ACC_COLS <= 256 ? 256 : 512;
+    static constexpr int HALF = BN * 4 / kEpiWarps;   // columns per epilogue warp
+    static constexpr int CH = HALF / 32;         // 32-column chunks per epilogue warp
     static constexpr int SMEM = 1024 + STAGES * STAGE + 256;
-    static constexpr int EC = KP <= 2 ? 32 : 16;   // epilogue columns per pass
     static_assert(ACC_COLS <= 512, "accumulators exceed tensor memory");
     static_assert(KP * BN <= 256 && (KP * BN) % 16 == 0, "combined MMA N must be <= 256");
+    static_assert(HALF % 32 == 0, "epilogue works on 32-column chunks");
     static_assert(STAGES >= 2, "not enough shared memory for two stages");
 };
 
 struct TcParams {
     int64_t m, n, ldc;
-    int32_t tiles_m, tiles_n;   // output tiles; CTAs walk them in groups of kGroupM tile rows
-    int32_t nkb;          // K-blocks of 64
+    // Work units are CM tile rows tall (CM = CTAs per cluster along M):
+    // units_m = ceil(tiles_m / CM), nunits = units_m * tiles_n.
+    int32_t tiles_m, tiles_n, units_m, nunits;
+    int32_t nkb;          // K-blocks of BK
     int32_t chunk_kb;     // K-blocks per exact FP32 chunk
     uint32_t p, m32;
     float pf, inv_pf;
@@ -75,44 +101,53 @@ __device__ __forceinline__ uint32_t mod_exact_f32(uint32_t bits, float pf, float
     return (uint32_t)r;
 }
 
-template <int KP, int BN>
+// Grouped raster: consecutive unit indices cover kGroupM unit rows before the
+// next tile column, so the A and B panels in use at one time stay in L2.
+__device__ __forceinline__ void unit_coords(int unit, const TcParams &P, int &um, int &tn) {
+    const int per_group = kGroupM * P.tiles_n;
+    const int first_m = (unit / per_group) * kGroupM;
+    const int gm = min(P.units_m - first_m, kGroupM);
+    const int r = unit % per_group;
+    um = first_m + r % gm;
+    tn = r / gm;
+}
+
+// CM = 1: one CTA per tile.  CM = 2: clusters of two CTAs on vertically
+// adjacent tiles that share their B tiles: each CTA loads half of every B
+// tile and multicasts it to both, so each SM reads 3/4 of the operand bytes
+// per K-block.  A stage is refilled only when both CTAs have consumed it
+// (their MMA completions arrive on both CTAs' "empty" barriers).
+template <int KP, int BN, int CM>
 __global__ void __launch_bounds__(kThreads, 1)
 gemm_planes_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       uint8_t *__restrict__ C, const TcParams P) {
     using CF = Cfg<KP, BN>;
+    static_assert(CM == 1 || CM == 2, "cluster size along M");
+    constexpr uint16_t kAllCtas = (uint16_t)((1u << CM) - 1);
+    const int rank = CM > 1 ? (int)ptx::cluster_ctarank() : 0;
+    const int unit0 = blockIdx.x / CM, unit_step = gridDim.x / CM;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = (uint64_t *)(smem + CF::STAGES * CF::STAGE);
     uint64_t *empty = full + CF::STAGES;
-    uint64_t *acc_full = empty + CF::STAGES;
-    uint64_t *acc_empty = acc_full + 1;
-    uint64_t *mma_done = acc_empty + 1;
+    uint64_t *acc_full = empty + CF::STAGES;   // MMAs of a chunk / a tile completed
+    uint64_t *acc_empty = acc_full + 1;        // a drain finished
+    uint64_t *tmem_free = acc_empty + 1;       // a tile's accumulators were read out
+    uint64_t *mma_done = tmem_free + 1;
     uint32_t *tmem_slot = (uint32_t *)(mma_done + 1);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    // Grouped raster: consecutive CTAs cover kGroupM tile rows before moving
-    // to the next tile column, so the A and B panels of the CTAs resident at
-    // one time overlap and stay in L2.
-    int tile_m, tile_n;
-    {
-        const int pid = blockIdx.x;
-        const int per_group = kGroupM * P.tiles_n;
-        const int first_m = (pid / per_group) * kGroupM;
-        const int gm = min(P.tiles_m - first_m, kGroupM);
-        const int r = pid % per_group;
-        tile_m = first_m + r % gm;
-        tile_n = r / gm;
-    }
     const int nkb = P.nkb;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < CF::STAGES; ++s) {
             ptx::mbar_init(&full[s], 1);
-            ptx::mbar_init(&empty[s], 1);
+            ptx::mbar_init(&empty[s], CM);   // one MMA completion from each CTA
         }
         ptx::mbar_init(acc_full, 1);
-        ptx::mbar_init(acc_empty, 128);
+        ptx::mbar_init(acc_empty, 32 * kEpiWarps);
+        ptx::mbar_init(tmem_free, 32 * kEpiWarps);
         ptx::mbar_init(mma_done, 1);
         *abort_flag = 0;
         ptx::fence_mbar_init();
@@ -123,6 +158,7 @@ gemm_planes_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
     }
     ptx::tc_fence_before();
     __syncthreads();
+    if (CM > 1) ptx::cluster_sync();   // peers' barriers exist before any multicast
     ptx::tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
@@ -136,81 +172,108 @@ gemm_planes_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
             // ---------------- TMA producer ----------------
             ptx::prefetch_tmap(&tmA);
             ptx::prefetch_tmap(&tmB);
-            int issued = 0;
-            for (int kb = 0; kb < nkb; ++kb) {
-                const int stage = kb % CF::STAGES;
-                if (kb >= CF::STAGES) {
-                    if (*abort_flag ||
-                        !ptx::mbar_wait(&empty[stage], ((kb / CF::STAGES) - 1) & 1)) {
-                        *abort_flag = 1;
-                        break;
+            int64_t it = 0;   // K-blocks issued so far, over all tiles
+            bool ok = true;
+            for (int unit = unit0; unit < P.nunits && ok; unit += unit_step) {
+                int um, tn;
+                unit_coords(unit, P, um, tn);
+                const int tm = um * CM + rank;
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int stage = (int)(it % CF::STAGES);
+                    if (it >= CF::STAGES) {
+                        // with CM > 1 this completes once every CTA has freed the stage
+                        if (*abort_flag ||
+                            !ptx::mbar_wait(&empty[stage], (uint32_t)((it / CF::STAGES) - 1) & 1)) {
+                            ok = false;
+                            break;
+                        }
+                    }
+                    // own A tiles + all of the B tiles (half from each CTA when CM = 2)
+                    ptx::mbar_arrive_expect_tx(&full[stage], CF::STAGE);
+                    for (int i = 0; i < KP; ++i)
+                        ptx::tma_load_3d(a_tile(stage, i), &tmA, &full[stage], kb * BK, tm * BM, i);
+                    for (int j = 0; j < KP; ++j) {
+                        if (CM == 1) {
+                            ptx::tma_load_3d(b_tile(stage, j), &tmB, &full[stage], kb * BK, tn * BN, j);
+                        } else {
+                            constexpr int ROWS = BN / CM;   // rows of the B tile this CTA fetches
+                            ptx::tma_load_3d_multicast(b_tile(stage, j) + rank * ROWS * kRowBytes, &tmB,
+                                                       &full[stage], kb * BK, tn * BN + rank * ROWS,
+                                                       j, kAllCtas);
+                        }
                     }
                 }
-                ptx::mbar_arrive_expect_tx(&full[stage], CF::STAGE);
-                for (int i = 0; i < KP; ++i)
-                    ptx::tma_load_3d(a_tile(stage, i), &tmA, &full[stage], kb * BK, tile_m * BM, i);
-                for (int j = 0; j < KP; ++j)
-                    ptx::tma_load_3d(b_tile(stage, j), &tmB, &full[stage], kb * BK, tile_n * BN, j);
-                issued = kb + 1;
             }
-            if (*abort_flag) {
+            if (!ok) {
+                *abort_flag = 1;
                 // let the copies this thread started land before the CTA exits
-                for (int kb = (issued > CF::STAGES ? issued - CF::STAGES : 0); kb < issued; ++kb)
-                    ptx::mbar_wait(&full[kb % CF::STAGES], (kb / CF::STAGES) & 1);
+                for (int64_t j = (it > CF::STAGES ? it - CF::STAGES : 0); j < it; ++j)
+                    ptx::mbar_wait(&full[j % CF::STAGES], (uint32_t)(j / CF::STAGES) & 1);
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
-            // The KP B-plane tiles are adjacent in shared memory, so together
-            // they form one K-major operand of N = KP*BN rows.  With C_t at
-            // TMEM column t*BN, one MMA of A_i against [B_0; ...; B_{KP-1}]
-            // at column i*BN adds A_i B_j into C_{i+j} for every j.
             const uint32_t idesc_all = ptx::idesc_bf16_f32(BM, KP * BN);
             const uint32_t idesc_one = ptx::idesc_bf16_f32(BM, BN);
-            int drain = 0;
+            int64_t it = 0;
+            int drain = 0, tcount = 0;
             bool ok = true;
-            for (int kb = 0; kb < nkb && ok; ++kb) {
-                const int stage = kb % CF::STAGES;
-                if (*abort_flag || !ptx::mbar_wait(&full[stage], (kb / CF::STAGES) & 1)) {
-                    ok = false;
-                    break;
-                }
-                ptx::tc_fence_after();
-                const uint64_t bd0 = ptx::smem_desc_sw128(b_tile(stage, 0));
-#pragma unroll
-                for (int kk = 0; kk < BK / UMMA_K; ++kk) {
-#pragma unroll
-                    for (int i = 0; i < KP; ++i) {
-                        const uint64_t ad = ptx::smem_desc_sw128(a_tile(stage, i)) + 2 * kk;
-                        if (kb == 0 && kk == 0 && i > 0) {
-                            // first K step: C_0..C_{i+KP-2} already hold data,
-                            // C_{i+KP-1} is written for the first time
-#pragma unroll
-                            for (int j = 0; j < KP; ++j) {
-                                const uint64_t bd = ptx::smem_desc_sw128(b_tile(stage, j));
-                                ptx::mma_bf16(tmem_base + (i + j) * BN, ad, bd, idesc_one,
-                                              j < KP - 1 ? 1u : 0u);
-                            }
-                        } else {
-                            ptx::mma_bf16(tmem_base + i * BN, ad, bd0 + 2 * kk, idesc_all,
-                                          (kb == 0 && kk == 0) ? 0u : 1u);
-                        }
-                    }
-                }
-                ptx::mma_commit(&empty[stage]);
-                if ((kb + 1) % P.chunk_kb == 0 && kb + 1 < nkb) {
-                    ptx::mma_commit(acc_full);
-                    if (!ptx::mbar_wait(acc_empty, drain & 1)) {
+            for (int unit = unit0; unit < P.nunits && ok; unit += unit_step, ++tcount) {
+                if (tcount > 0) {   // the previous tile's accumulators must have been read
+                    if (*abort_flag || !ptx::mbar_wait(tmem_free, (uint32_t)(tcount - 1) & 1)) {
                         ok = false;
                         break;
                     }
                     ptx::tc_fence_after();
-                    ++drain;
                 }
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int stage = (int)(it % CF::STAGES);
+                    if (*abort_flag ||
+                        !ptx::mbar_wait(&full[stage], (uint32_t)(it / CF::STAGES) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    ptx::tc_fence_after();
+                    const uint64_t bd0 = operand_desc(b_tile(stage, 0));
+#pragma unroll
+                    for (int kk = 0; kk < BK / UMMA_K; ++kk) {
+#pragma unroll
+                        for (int i = 0; i < KP; ++i) {
+                            const uint64_t ad = operand_desc(a_tile(stage, i)) + 2 * kk;
+                            if (kb == 0 && kk == 0 && i > 0) {
+                                // first K step of a tile: C_0..C_{i+KP-2} hold data,
+                                // C_{i+KP-1} is written for the first time
+#pragma unroll
+                                for (int j = 0; j < KP; ++j) {
+                                    const uint64_t bd = operand_desc(b_tile(stage, j));
+                                    ptx::mma_bf16(tmem_base + (i + j) * BN, ad, bd, idesc_one,
+                                                  j < KP - 1 ? 1u : 0u);
+                                }
+                            } else {
+                                ptx::mma_bf16(tmem_base + i * BN, ad, bd0 + 2 * kk, idesc_all,
+                                              (kb == 0 && kk == 0) ? 0u : 1u);
+                            }
+                        }
+                    }
+                    if (CM == 1) ptx::mma_commit(&empty[stage]);
+                    else ptx::mma_commit_multicast(&empty[stage], kAllCtas);
+                    if ((kb + 1) % P.chunk_kb == 0 && kb + 1 < nkb) {
+                        ptx::mma_commit(acc_full);
+                        if (!ptx::mbar_wait(acc_empty, (uint32_t)drain & 1)) {
+                            ok = false;
+                            break;
+                        }
+                        ptx::tc_fence_after();
+                        ++drain;
+                    }
+                }
+                if (ok) ptx::mma_commit(acc_full);   // tile complete
             }
-            if (!ok) *abort_flag = 1;
-            ptx::mma_commit(acc_full);   // final (or abort) completion
+            if (!ok) {
+                *abort_flag = 1;
+                ptx::mma_commit(acc_full);   // wake the epilogue
+            }
             // every MMA of this CTA has completed once mma_done flips: only
             // then may tensor memory be released
             ptx::mma_commit(mma_done);
@@ -218,88 +281,119 @@ gemm_planes_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
         }
     } else {
         // ---------------- epilogue (warps 2..5) ----------------
-        const int wq = warp & 3;
-        const uint32_t tbase = tmem_base + ((uint32_t)(wq * 32) << 16);
+        const int ew = warp - 2;
+        const int quarter = warp & 3;           // TMEM lanes 32*quarter.. (warp % 4 rule)
+        const int col_base = (ew / 4) * CF::HALF;   // 0 with four epilogue warps
+        const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + col_base;
         const int ndrain = nkb > 0 ? (nkb - 1) / P.chunk_kb : 0;
-        bool ok = true;
+        float foldf[(KP - 1) * KP + 1];
+#pragma unroll
+        for (int x = 0; x < (KP - 1) * KP; ++x) foldf[x] = (float)P.fold[x];
         int phase = 0;
-        for (int d = 0; d < ndrain; ++d, ++phase) {
-            if (!ptx::mbar_wait(acc_full, phase & 1) || *abort_flag) {
+        bool ok = true;
+        for (int unit = unit0; unit < P.nunits && ok; unit += unit_step) {
+            int um, tn;
+            unit_coords(unit, P, um, tn);
+            const int tm = um * CM + rank;
+            for (int d = 0; d < ndrain; ++d, ++phase) {
+                if (!ptx::mbar_wait(acc_full, (uint32_t)phase & 1) || *abort_flag) {
+                    ok = false;
+                    break;
+                }
+                ptx::tc_fence_after();
+#pragma unroll 1
+                for (int t = 0; t < CF::NACC; ++t)
+#pragma unroll 1
+                    for (int c = 0; c < CF::HALF; c += 32) {
+                        uint32_t v[32];
+                        ptx::tmem_ld32(tbase + t * BN + c, v);
+                        ptx::tmem_wait_ld();
+#pragma unroll
+                        for (int e = 0; e < 32; ++e) {
+                            const float x = __uint_as_float(v[e]);
+                            const float nq = rintf(x * P.inv_pf);
+                            v[e] = __float_as_uint(fmaf(-P.pf, nq, x));   // |.| <= 1.5 p, exact
+                        }
+                        ptx::tmem_st32(tbase + t * BN + c, v);
+                    }
+                ptx::tmem_wait_st();
+                ptx::tc_fence_before();
+                ptx::mbar_arrive(acc_empty);
+            }
+            if (!ok) break;
+            if (!ptx::mbar_wait(acc_full, (uint32_t)phase & 1) || *abort_flag) {
                 ok = false;
                 break;
             }
+            ++phase;
             ptx::tc_fence_after();
+            // Each plane sum is brought to |r| <= 1.5 p by one rint step, the
+            // fold out_i = r_i + sum_t r_t (X^t mod P)_i runs in FP32 FMAs
+            // (every value stays below 2^19, so they are exact), and only the
+            // k outputs take the exact reduction to [0, p).  Chunks of 16
+            // columns are stored as soon as they are computed; tensor memory is
+            // released once the last chunk has been read.
+            const int64_t row = (int64_t)tm * BM + quarter * 32 + lane;
 #pragma unroll 1
-            for (int c = 0; c < CF::ACC_COLS; c += 32) {
-                uint32_t v[32];
-                ptx::tmem_ld32(tbase + c, v);
-                ptx::tmem_wait_ld();
+            for (int c = 0; c < CF::HALF; c += 16) {
+                float r[CF::NACC][16];
+                {
+                    uint32_t v[CF::NACC][16];
 #pragma unroll
-                for (int e = 0; e < 32; ++e) {
-                    const float x = __uint_as_float(v[e]);
-                    const float nq = rintf(x * P.inv_pf);
-                    v[e] = __float_as_uint(fmaf(-P.pf, nq, x));   // |.| <= 1.5 p, exact
+                    for (int t = 0; t < CF::NACC; ++t) ptx::tmem_ld16(tbase + t * BN + c, v[t]);
+                    ptx::tmem_wait_ld();
+                    if (c + 16 >= CF::HALF) {
+                        // tensor memory may now take the next tile's MMAs
+                        ptx::tc_fence_before();
+                        ptx::mbar_arrive(tmem_free);
+                    }
+#pragma unroll
+                    for (int t = 0; t < CF::NACC; ++t)
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) {
+                            const float x = __uint_as_float(v[t][e]);
+                            r[t][e] = fmaf(-P.pf, rintf(x * P.inv_pf), x);
+                        }
                 }
-                ptx::tmem_st32(tbase + c, v);
-            }
-            ptx::tmem_wait_st();
-            ptx::tc_fence_before();
-            ptx::mbar_arrive(acc_empty);
-        }
-        if (ok) ok = ptx::mbar_wait(acc_full, phase & 1);
-        if (*abort_flag) ok = false;
-        if (!ok) {
-            *abort_flag = 1;
-        } else {
-            ptx::tc_fence_after();
-            const int64_t row = (int64_t)tile_m * BM + wq * 32 + lane;
-            constexpr int EC = CF::EC;   // columns per pass (bounds registers)
-#pragma unroll 1
-            for (int c0 = 0; c0 < BN; c0 += EC) {
-                uint32_t mu[CF::NACC][EC];
+                const int64_t col = (int64_t)tn * BN + col_base + c;
 #pragma unroll
-                for (int t = 0; t < CF::NACC; ++t) ptx::tmem_ld<EC>(tbase + t * BN + c0, mu[t]);
-                ptx::tmem_wait_ld();
+                for (int i = 0; i < KP; ++i) {
+                    uint32_t word[4];
 #pragma unroll
-                for (int t = 0; t < CF::NACC; ++t)
+                    for (int w = 0; w < 4; ++w) {
+                        word[w] = 0;
 #pragma unroll
-                    for (int e = 0; e < EC; ++e) mu[t][e] = mod_exact_f32(mu[t][e], P.pf, P.inv_pf);
-                const int64_t col = (int64_t)tile_n * BN + c0;
-                if (row < P.m && col < P.n) {
-#pragma unroll
-                    for (int i = 0; i < KP; ++i) {
-                        uint32_t packed[EC / 4];
-#pragma unroll
-                        for (int w = 0; w < EC / 4; ++w) packed[w] = 0;
-#pragma unroll
-                        for (int e = 0; e < EC; ++e) {
-                            uint32_t o = mu[i][e];
+                        for (int b = 0; b < 4; ++b) {
+                            const int e = 4 * w + b;
+                            float o = r[i][e];
 #pragma unroll
                             for (int t = KP; t < 2 * KP - 1; ++t)
-                                o = mod_small(o + mu[t][e] * P.fold[(t - KP) * KP + i], P.p, P.m32);
-                            packed[e / 4] |= o << (8 * (e % 4));
+                                o = fmaf(r[t][e], foldf[(t - KP) * KP + i], o);
+                            word[w] |= mod_exact_f32(__float_as_uint(o), P.pf, P.inv_pf) << (8 * b);
                         }
+                    }
+                    if (row < P.m && col < P.n) {
                         uint8_t *dst = C + ((int64_t)i * P.m + row) * P.ldc + col;
-                        if (col + EC <= P.n && (((uintptr_t)dst) & 15) == 0) {
-#pragma unroll
-                            for (int w = 0; w < EC / 16; ++w)
-                                reinterpret_cast<uint4 *>(dst)[w] =
-                                    make_uint4(packed[4 * w], packed[4 * w + 1], packed[4 * w + 2],
-                                               packed[4 * w + 3]);
+                        if (col + 16 <= P.n && (((uintptr_t)dst) & 15) == 0) {
+                            *reinterpret_cast<uint4 *>(dst) = make_uint4(word[0], word[1], word[2], word[3]);
                         } else {
                             const int64_t nrem = P.n - col;
-                            const int lim = nrem < EC ? (int)nrem : EC;
-                            for (int e = 0; e < lim; ++e)
-                                dst[e] = (uint8_t)(packed[e / 4] >> (8 * (e % 4)));
+                            const int lim = nrem < 16 ? (int)nrem : 16;
+                            for (int e = 0; e < lim; ++e) dst[e] = (uint8_t)(word[e / 4] >> (8 * (e % 4)));
                         }
                     }
                 }
             }
         }
+        if (!ok) *abort_flag = 1;
     }
 
     ptx::tc_fence_before();
     __syncthreads();
+    // no peer may still multicast into this CTA's shared memory or arrive on
+    // its barriers once it exits: every CTA has waited for its own MMAs
+    // (mma_done) and its loads (full barriers) before this point
+    if (CM > 1) ptx::cluster_sync();
     if (threadIdx.x == 0 && *abort_flag) record_timeout(P.status, 3);
     if (warp == 1) {
         ptx::tc_fence_after();
@@ -338,20 +432,21 @@ int make_plane_map(CUtensorMap *map, const void *base, int64_t K, int64_t rows, 
     const cuuint32_t estr[3] = {1, 1, 1};
     const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims,
                            strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           kRowBytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(QADIC_E_INVALID, "tensor map encode failed (%d)", (int)r);
     return QADIC_OK;
 }
 
-template <int KP, int BN>
+template <int KP, int BN, int CM>
 int launch_tc(const Field &f, int64_t m, int64_t n, int64_t K, const void *A, int64_t lda,
               const void *B, int64_t ldb, uint8_t *C, int64_t ldc, cudaStream_t stream) {
     using CF = Cfg<KP, BN>;
     CUtensorMap tmA, tmB;
     int st;
     if ((st = make_plane_map(&tmA, A, K, m, lda, KP, BM))) return st;
-    if ((st = make_plane_map(&tmB, B, K, n, ldb, KP, BN))) return st;
+    if ((st = make_plane_map(&tmB, B, K, n, ldb, KP, BN / CM))) return st;
     TcParams P;
     P.m = m;
     P.n = n;
@@ -367,17 +462,47 @@ int launch_tc(const Field &f, int64_t m, int64_t n, int64_t K, const void *A, in
     for (uint32_t t = 0; t + 1 < f.k; ++t)
         for (uint32_t i = 0; i < f.k; ++i) P.fold[t * KP + i] = f.fold[t * f.k + i];
     P.status = device_status_word();
-    auto kern = gemm_planes_tc_kernel<KP, BN>;
+    auto kern = gemm_planes_tc_kernel<KP, BN, CM>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM) !=
         cudaSuccess)
         return set_error(QADIC_E_CUDA, "tc smem attribute: %s", cudaGetErrorString(cudaGetLastError()));
     const int64_t tiles_m = (m + BM - 1) / BM, tiles_n = (n + BN - 1) / BN;
-    if (tiles_m * tiles_n > 0x7fffffff) return set_error(QADIC_E_INVALID, "too many tiles");
+    const int64_t units_m = (tiles_m + CM - 1) / CM;
+    if (units_m * tiles_n > 0x7fffffff) return set_error(QADIC_E_INVALID, "too many tiles");
     P.tiles_m = (int32_t)tiles_m;
     P.tiles_n = (int32_t)tiles_n;
-    kern<<<(unsigned)(tiles_m * tiles_n), kThreads, CF::SMEM, stream>>>(tmA, tmB, C, P);
-    const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return set_error(QADIC_E_CUDA, "tc launch: %s", cudaGetErrorString(e));
+    P.units_m = (int32_t)units_m;
+    P.nunits = (int32_t)(units_m * tiles_n);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = CF::SMEM;
+    cfg.stream = stream;
+    int max_units = sms > 0 ? sms / CM : 1;
+    if (CM > 1) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = CM;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cfg.gridDim = dim3((unsigned)(max_units * CM));
+        int clusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) == cudaSuccess && clusters > 0)
+            max_units = std::min(max_units, clusters);
+        else
+            cudaGetLastError();
+    }
+    const int units = (int)std::min<int64_t>(P.nunits, std::max(max_units, 1));
+    cfg.gridDim = dim3((unsigned)(units * CM));
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, tmA, tmB, C, P);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(QADIC_E_CUDA, "tc launch: %s", cudaGetErrorString(e));
+    }
     return QADIC_OK;
 }
 
@@ -397,9 +522,9 @@ int launch_gemm_planes_tc(const Field &f, int64_t m, int64_t n, int64_t K, const
                 return set_error(QADIC_E_CUDA, "memset: %s", cudaGetErrorString(cudaGetLastError()));
         return QADIC_OK;
     }
-    if (f.k == 2) return launch_tc<2, 128>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
-    if (f.k == 3) return launch_tc<3, 64>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
-    if (f.k == 4) return launch_tc<4, 64>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
+    if (f.k == 2) return launch_tc<2, 128, 2>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
+    if (f.k == 3) return launch_tc<3, 64, 2>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
+    if (f.k == 4) return launch_tc<4, 64, 2>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
     return set_error(QADIC_E_UNSUPPORTED, "no tensor-core plane kernel for k=%u", f.k);
 }
 

@@ -168,20 +168,34 @@ __global__ void __launch_bounds__(256) pack_vec_a(const uint8_t *__restrict__ in
                                                   __nv_bfloat16 *__restrict__ out, PackParams P) {
     const int64_t per_row = P.cols / 16;
     const int64_t units = (int64_t)P.k * P.rows * per_row;
-    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < units;
-         u += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t c16 = u % per_row, pr = u / per_row;   // pr = plane * rows + row
-        const uint4 w = __ldcs(reinterpret_cast<const uint4 *>(in + pr * P.ld_in + c16 * 16));
-        const uint32_t words[4] = {w.x, w.y, w.z, w.w};
-        uint32_t o[8];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // two independent 16-byte loads in flight per thread
+    for (int64_t u0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u0 < units; u0 += 2 * stride) {
+        uint4 w[2];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            o[2 * q] = centre_pair<IN>(words[q] & 0xff, (words[q] >> 8) & 0xff, P);
-            o[2 * q + 1] = centre_pair<IN>((words[q] >> 16) & 0xff, words[q] >> 24, P);
+        for (int s = 0; s < 2; ++s) {
+            const int64_t u = u0 + s * stride;
+            if (u < units) {
+                const int64_t c16 = u % per_row, pr = u / per_row;   // pr = plane * rows + row
+                w[s] = __ldcs(reinterpret_cast<const uint4 *>(in + pr * P.ld_in + c16 * 16));
+            }
         }
-        uint4 *dst = reinterpret_cast<uint4 *>(out + pr * P.ld_out + c16 * 16);
-        dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
-        dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const int64_t u = u0 + s * stride;
+            if (u >= units) break;
+            const int64_t c16 = u % per_row, pr = u / per_row;
+            const uint32_t words[4] = {w[s].x, w[s].y, w[s].z, w[s].w};
+            uint32_t o[8];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                o[2 * q] = centre_pair<IN>(words[q] & 0xff, (words[q] >> 8) & 0xff, P);
+                o[2 * q + 1] = centre_pair<IN>((words[q] >> 16) & 0xff, words[q] >> 24, P);
+            }
+            uint4 *dst = reinterpret_cast<uint4 *>(out + pr * P.ld_out + c16 * 16);
+            __stcs(dst, make_uint4(o[0], o[1], o[2], o[3]));
+            __stcs(dst + 1, make_uint4(o[4], o[5], o[6], o[7]));
+        }
     }
 }
 
