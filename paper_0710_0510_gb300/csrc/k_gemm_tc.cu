@@ -59,15 +59,28 @@ constexpr int kEpiWarps = 4;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kSmemBudget = 227 * 1024;
 
+// Accumulator layouts in tensor memory (C_t = sum_{i+j=t} A_i B_j):
+//   shared (SPLIT = false): C_t at column t*BN, 2k-1 accumulators; the MMA of
+//     A_i against [B_0; ...; B_{k-1}] starts at column i*BN, so products of
+//     different A planes meet in the same accumulator;
+//   split (SPLIT = true, k = 2): the MMA of A_i starts at column i*k*BN, so
+//     every accumulator receives one product per K step: [C_0 | C_1a | C_1b |
+//     C_2], C_1 = C_1a + C_1b in the epilogue.  One product per K step
+//     doubles the exact FP32 chunk (k h^2 -> h^2 per K step).
 template <int KP, int BN>
 struct Cfg {
-    static constexpr int NACC = 2 * KP - 1;
+    static constexpr bool SPLIT = KP == 2;
+    static constexpr int NACC = SPLIT ? KP * KP : 2 * KP - 1;   // tensor-memory accumulators
     static constexpr int A_TILE = BM * BK * 2;
     static constexpr int B_TILE = BN * BK * 2;
     static constexpr int STAGE = KP * (A_TILE + B_TILE);
     static constexpr int STAGES_RAW = (kSmemBudget - 2048) / STAGE;
     static constexpr int STAGES = STAGES_RAW > 8 ? 8 : STAGES_RAW;
     static constexpr int ACC_COLS = NACC * BN;
+    // column of the MMA for A plane i
+    static constexpr int a_col(int i) { return SPLIT ? i * KP * BN : i * BN; }
+    // plane sum t collected by accumulator a
+    static constexpr int sum_of(int a) { return SPLIT ? (a / KP) + (a % KP) : a; }
     static constexpr int TMEM_COLS = ACC_COLS <= 32 ? 32 : ACC_COLS <= 64 ? 64
                                    : ACC_COLS <= 128 ? 128 : ACC_COLS <= 256 ? 256 : 512;
     static constexpr int HALF = BN * 4 / kEpiWarps;   // columns per epilogue warp
@@ -241,7 +254,7 @@ gemm_planes_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
 #pragma unroll
                         for (int i = 0; i < KP; ++i) {
                             const uint64_t ad = operand_desc(a_tile(stage, i)) + 2 * kk;
-                            if (kb == 0 && kk == 0 && i > 0) {
+                            if (!CF::SPLIT && kb == 0 && kk == 0 && i > 0) {
                                 // first K step of a tile: C_0..C_{i+KP-2} hold data,
                                 // C_{i+KP-1} is written for the first time
 #pragma unroll
@@ -251,7 +264,7 @@ gemm_planes_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                                                   j < KP - 1 ? 1u : 0u);
                                 }
                             } else {
-                                ptx::mma_bf16(tmem_base + i * BN, ad, bd0 + 2 * kk, idesc_all,
+                                ptx::mma_bf16(tmem_base + CF::a_col(i), ad, bd0 + 2 * kk, idesc_all,
                                               (kb == 0 && kk == 0) ? 0u : 1u);
                             }
                         }
@@ -355,6 +368,16 @@ gemm_planes_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                             r[t][e] = fmaf(-P.pf, rintf(x * P.inv_pf), x);
                         }
                 }
+                // plane sums C_t from the accumulators (exact: small integers)
+                float s[2 * KP - 1][16];
+#pragma unroll
+                for (int t = 0; t < 2 * KP - 1; ++t)
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) s[t][e] = 0.f;
+#pragma unroll
+                for (int a = 0; a < CF::NACC; ++a)
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) s[CF::sum_of(a)][e] += r[a][e];
                 const int64_t col = (int64_t)tn * BN + col_base + c;
 #pragma unroll
                 for (int i = 0; i < KP; ++i) {
@@ -365,10 +388,10 @@ gemm_planes_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
 #pragma unroll
                         for (int b = 0; b < 4; ++b) {
                             const int e = 4 * w + b;
-                            float o = r[i][e];
+                            float o = s[i][e];
 #pragma unroll
                             for (int t = KP; t < 2 * KP - 1; ++t)
-                                o = fmaf(r[t][e], foldf[(t - KP) * KP + i], o);
+                                o = fmaf(s[t][e], foldf[(t - KP) * KP + i], o);
                             word[w] |= mod_exact_f32(__float_as_uint(o), P.pf, P.inv_pf) << (8 * b);
                         }
                     }
@@ -452,7 +475,12 @@ int launch_tc(const Field &f, int64_t m, int64_t n, int64_t K, const void *A, in
     P.n = n;
     P.ldc = ldc;
     P.nkb = (int32_t)((K + BK - 1) / BK);
-    P.chunk_kb = (int32_t)(f.k_chunk_f32 / BK);
+    // exact FP32 chunk: a drained residue (|.| <= 1.5p < 2p) plus the growth
+    // per K step (k h^2 with shared accumulators, h^2 with split ones) must
+    // stay within 2^24
+    const int64_t hh = (int64_t)f.h * f.h;
+    const int64_t chunk = CF::SPLIT ? ((1ll << 24) - 2 * (int64_t)f.p) / hh : f.k_chunk_f32;
+    P.chunk_kb = (int32_t)std::min<int64_t>(chunk / BK, 1 << 30);
     if (P.chunk_kb < 1) return set_error(QADIC_E_OVERFLOW, "exact FP32 chunk below one K-block");
     P.p = f.p;
     P.m32 = make_mod_small(f.p);

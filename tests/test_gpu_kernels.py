@@ -245,6 +245,18 @@ def test_gemm_planes_gf251_2_drains(torch, orc, shape):
     assert np.array_equal(got, oracle_gemm_from_planes(orc, p, f.poly, A, B))
 
 
+def test_gemm_planes_gf101_2_two_split_chunks(torch, orc):
+    """k = 2 keeps one product per accumulator per K step, so the exact chunk
+    for p = 101 is 6656; K = 13412 crosses two in-place reductions."""
+    p, k = 101, 2
+    f = q.Field(p, k)
+    m, n, K = 128, 130, 2 * 6656 + 100
+    A = W.centred_planes(k, m, K, 50, salt=77)
+    B = W.centred_planes(k, K, n, 50, salt=78)
+    got = run_planes(torch, f, q.FMT_INT8_PLANES, A, B, m, n, K)
+    assert np.array_equal(got, oracle_gemm_from_planes(orc, p, f.poly, A, B))
+
+
 @pytest.mark.parametrize("p,val", [(251, 125), (251, -125), (101, 50), (101, -50)])
 def test_gemm_planes_sums_at_the_fp32_limit(torch, orc, p, val):
     """All coefficients at +-h with the same sign: every accumulator grows by
