@@ -50,6 +50,19 @@ void free_tables(Field &f) {
     f.d_fold = nullptr;
 }
 
+// One non-blocking stream per device for the host copies of qadic_matmul_host.
+cudaStream_t side_stream(int dev) {
+    static std::mutex mu;
+    static cudaStream_t streams[64] = {nullptr};
+    if (dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        streams[dev] = nullptr;
+    }
+    return streams[dev];
+}
+
 bool on_device(const Field &f) {
     if (f.device < 0) return false;
     int dev = -1;
@@ -261,24 +274,82 @@ int qadic_matmul_host(const qadic_field *field, int path, int in_fmt, int64_t m,
     char *pA = w;
     w += align256((path == QADIC_PATH_FP64_QADIC ? 8 : 2 * (size_t)f.k) * m * K);
     char *pB = w;
-    if (cudaMemcpyAsync(dA, A_host, eb * m * K, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(dB, B_host, eb * K * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return set_error(QADIC_E_CUDA, "H2D copy: %s", cudaGetErrorString(cudaGetLastError()));
+    if (path != QADIC_PATH_FP64_QADIC && path != QADIC_PATH_PLANES)
+        return set_error(QADIC_E_INVALID, "unknown path %d", path);
+    if (path == QADIC_PATH_PLANES && !gemm_planes_tc_supported(f))
+        return set_error(QADIC_E_UNSUPPORTED, "no tensor-core plane kernel for k=%u", f.k);
+
+    // Overlap: the inputs are copied on a side stream (A, then B), so A is
+    // packed while B is still on its way; the plane GEMM runs as two row
+    // halves and the top half of C is copied back while the bottom half is
+    // computed.  Everything is joined back into `stream` before returning.
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaStream_t side = side_stream(dev);
+    if (!side) return set_error(QADIC_E_CUDA, "no side stream");
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    for (auto &e : ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            for (auto &x : ev)
+                if (x) cudaEventDestroy(x);
+            return set_error(QADIC_E_CUDA, "event: %s", cudaGetErrorString(cudaGetLastError()));
+        }
+    auto cleanup = [&](int status) {
+        for (auto &x : ev) cudaEventDestroy(x);   // released once their work completes
+        return status;
+    };
+    auto cuda_fail = [&](const char *what) {
+        return cleanup(set_error(QADIC_E_CUDA, "%s: %s", what, cudaGetErrorString(cudaGetLastError())));
+    };
+    const size_t c_plane = (size_t)m * n;
+    // side stream starts after everything already queued on `stream`
+    if (cudaEventRecord(ev[0], s) || cudaStreamWaitEvent(side, ev[0], 0) ||
+        cudaMemcpyAsync(dA, A_host, eb * m * K, cudaMemcpyHostToDevice, side) ||
+        cudaEventRecord(ev[1], side) ||
+        cudaMemcpyAsync(dB, B_host, eb * K * n, cudaMemcpyHostToDevice, side) ||
+        cudaEventRecord(ev[2], side) || cudaStreamWaitEvent(s, ev[1], 0))
+        return cuda_fail("H2D copy");
     int st;
+    const int opA = path == QADIC_PATH_FP64_QADIC ? QADIC_FMT_QADIC_F64 : QADIC_FMT_OPERAND_A;
+    const int opB = path == QADIC_PATH_FP64_QADIC ? QADIC_FMT_QADIC_F64 : QADIC_FMT_OPERAND_B;
+    if ((st = qadic_pack(field, in_fmt, dA, m, K, K, opA, pA, K, stream))) return cleanup(st);
+    if (cudaStreamWaitEvent(s, ev[2], 0)) return cuda_fail("wait");
+    if ((st = qadic_pack(field, in_fmt, dB, K, n, n, opB, pB, path == QADIC_PATH_FP64_QADIC ? n : K,
+                         stream)))
+        return cleanup(st);
+    const int64_t mh = (path == QADIC_PATH_PLANES && m >= 512) ? (m / 2 + 127) / 128 * 128 : m;
     if (path == QADIC_PATH_FP64_QADIC) {
-        if ((st = qadic_pack(field, in_fmt, dA, m, K, K, QADIC_FMT_QADIC_F64, pA, K, stream)) ||
-            (st = qadic_pack(field, in_fmt, dB, K, n, n, QADIC_FMT_QADIC_F64, pB, n, stream)) ||
-            (st = qadic_gemm(field, path, m, n, K, pA, K, pB, n, dC, n, nullptr, 0, stream)))
-            return st;
+        if ((st = qadic_gemm(field, path, m, n, K, pA, K, pB, n, dC, n, nullptr, 0, stream)))
+            return cleanup(st);
     } else {
-        if ((st = qadic_pack(field, in_fmt, dA, m, K, K, QADIC_FMT_OPERAND_A, pA, K, stream)) ||
-            (st = qadic_pack(field, in_fmt, dB, K, n, n, QADIC_FMT_OPERAND_B, pB, K, stream)) ||
-            (st = qadic_gemm(field, path, m, n, K, pA, K, pB, K, dC, n, nullptr, 0, stream)))
-            return st;
+        const uint16_t *a16 = (const uint16_t *)pA;
+        if ((st = launch_gemm_planes_tc_strided(f, mh, n, K, a16, K, (int64_t)m * K, pB, K,
+                                                (int64_t)n * K, dC, n, (int64_t)c_plane, s)))
+            return cleanup(st);
+        if (mh < m) {
+            if (cudaEventRecord(ev[3], s) || cudaStreamWaitEvent(side, ev[3], 0))
+                return cuda_fail("event");
+            for (uint32_t i = 0; i < f.k; ++i)
+                if (cudaMemcpyAsync(C_host + i * c_plane, dC + i * c_plane, (size_t)mh * n,
+                                    cudaMemcpyDeviceToHost, side))
+                    return cuda_fail("D2H copy");
+            if ((st = launch_gemm_planes_tc_strided(f, m - mh, n, K, a16 + mh * K, K,
+                                                    (int64_t)m * K, pB, K, (int64_t)n * K,
+                                                    dC + mh * n, n, (int64_t)c_plane, s)))
+                return cleanup(st);
+        }
     }
-    if (cudaMemcpyAsync(C_host, dC, (size_t)f.k * m * n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        return set_error(QADIC_E_CUDA, "D2H copy: %s", cudaGetErrorString(cudaGetLastError()));
-    return QADIC_OK;
+    if (mh < m) {   // bottom half of every plane
+        for (uint32_t i = 0; i < f.k; ++i)
+            if (cudaMemcpyAsync(C_host + i * c_plane + mh * n, dC + i * c_plane + mh * n,
+                                (size_t)(m - mh) * n, cudaMemcpyDeviceToHost, s))
+                return cuda_fail("D2H copy");
+    } else if (cudaMemcpyAsync(C_host, dC, (size_t)f.k * m * n, cudaMemcpyDeviceToHost, s)) {
+        return cuda_fail("D2H copy");
+    }
+    // join: `stream` also waits for the side stream's copies
+    if (cudaEventRecord(ev[4], side) || cudaStreamWaitEvent(s, ev[4], 0)) return cuda_fail("join");
+    return cleanup(QADIC_OK);
 }
 
 int qadic_redq(uint32_t p, uint32_t log2_q, uint32_t ndigits, const double *in, double *out,

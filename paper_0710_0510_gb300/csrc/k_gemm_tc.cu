@@ -18,16 +18,23 @@
 // The k B-plane tiles of a stage sit next to each other in shared memory and
 // form one K-major operand of N = k*BN rows; with C_t at tensor-memory
 // column t*BN, one MMA of A_i against [B_0; ...; B_{k-1}] at column i*BN
-// adds A_i B_j into C_{i+j} for every j (k MMAs per 16-wide K step).
+// adds A_i B_j into C_{i+j} for every j (k MMAs per 16-wide K step).  For
+// k = 2 the middle sum is split instead (A_0 B_1 and A_1 B_0 land in two
+// accumulators, four in all), so each FP32 accumulator gathers one plane
+// product only and the exact chunk grows by a factor k: at K = 4096 a tile
+// needs no drain at all.
 //
-// Persistent: one CTA per SM walks output tiles (grouped raster) with
+// Persistent, in clusters of two CTAs on vertically adjacent output tiles
+// (one unit) that share their B tiles: each CTA loads half of the B tile and
+// multicasts it to both.  One CTA per SM walks units (grouped raster) with
 //   warp 0      TMA producer, streaming K-blocks of consecutive tiles into a
 //               STAGES-deep ring without a break between tiles
 //   warp 1      allocates tensor memory; one thread issues tcgen05.mma
 //   warps 2-5   epilogue, one warp per 32-lane quarter: in-place drains; at
-//               the end of a tile they read the accumulators, reduce mod p
-//               into packed bytes, release tensor memory to the next tile's
-//               MMAs, then fold and store while those MMAs run.
+//               the end of a tile they read the accumulators 16 columns at
+//               a time, release tensor memory to the next tile's MMAs after
+//               the last read, and reduce mod p, fold mod P and store while
+//               those MMAs run.
 // All waits are bounded (kSpinLimit); on expiry the kernel records
 // QADIC_E_DEVICE_TIMEOUT, lets its copies land and frees tensor memory.
 #include <cuda_bf16.h>
@@ -94,6 +101,7 @@ struct Cfg {
 
 struct TcParams {
     int64_t m, n, ldc;
+    int64_t c_plane;      // elements between output planes
     // Work units are CM tile rows tall (CM = CTAs per cluster along M):
     // units_m = ceil(tiles_m / CM), nunits = units_m * tiles_n.
     int32_t tiles_m, tiles_n, units_m, nunits;
@@ -396,7 +404,7 @@ gemm_planes_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                         }
                     }
                     if (row < P.m && col < P.n) {
-                        uint8_t *dst = C + ((int64_t)i * P.m + row) * P.ldc + col;
+                        uint8_t *dst = C + (int64_t)i * P.c_plane + row * P.ldc + col;
                         if (col + 16 <= P.n && (((uintptr_t)dst) & 15) == 0) {
                             *reinterpret_cast<uint4 *>(dst) = make_uint4(word[0], word[1], word[2], word[3]);
                         } else {
@@ -446,11 +454,11 @@ EncodeTiledFn get_encode_fn() {
 
 // 3-D map over (K, rows, planes) of a k-plane bf16 operand, box (64, box_rows, 1).
 int make_plane_map(CUtensorMap *map, const void *base, int64_t K, int64_t rows, int64_t ld,
-                   uint32_t planes, uint32_t box_rows) {
+                   int64_t plane_stride, uint32_t planes, uint32_t box_rows) {
     EncodeTiledFn enc = get_encode_fn();
     if (!enc) return set_error(QADIC_E_CUDA, "cuTensorMapEncodeTiled unavailable");
     const cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)planes};
-    const cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)(rows * ld * 2)};
+    const cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)(plane_stride * 2)};
     const cuuint32_t box[3] = {(cuuint32_t)BK, box_rows, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims,
@@ -464,16 +472,18 @@ int make_plane_map(CUtensorMap *map, const void *base, int64_t K, int64_t rows, 
 
 template <int KP, int BN, int CM>
 int launch_tc(const Field &f, int64_t m, int64_t n, int64_t K, const void *A, int64_t lda,
-              const void *B, int64_t ldb, uint8_t *C, int64_t ldc, cudaStream_t stream) {
+              int64_t a_plane, const void *B, int64_t ldb, int64_t b_plane, uint8_t *C,
+              int64_t ldc, int64_t c_plane, cudaStream_t stream) {
     using CF = Cfg<KP, BN>;
     CUtensorMap tmA, tmB;
     int st;
-    if ((st = make_plane_map(&tmA, A, K, m, lda, KP, BM))) return st;
-    if ((st = make_plane_map(&tmB, B, K, n, ldb, KP, BN / CM))) return st;
+    if ((st = make_plane_map(&tmA, A, K, m, lda, a_plane, KP, BM))) return st;
+    if ((st = make_plane_map(&tmB, B, K, n, ldb, b_plane, KP, BN / CM))) return st;
     TcParams P;
     P.m = m;
     P.n = n;
     P.ldc = ldc;
+    P.c_plane = c_plane;
     P.nkb = (int32_t)((K + BK - 1) / BK);
     // exact FP32 chunk: a drained residue (|.| <= 1.5p < 2p) plus the growth
     // per K step (k h^2 with shared accumulators, h^2 with split ones) must
@@ -538,22 +548,34 @@ int launch_tc(const Field &f, int64_t m, int64_t n, int64_t K, const void *A, in
 
 bool gemm_planes_tc_supported(const Field &f) { return f.k >= 2 && f.k <= 4; }
 
-int launch_gemm_planes_tc(const Field &f, int64_t m, int64_t n, int64_t K, const void *A,
-                          int64_t lda, const void *B, int64_t ldb, uint8_t *C, int64_t ldc,
-                          cudaStream_t stream) {
-    if (lda % 8 || ldb % 8 || ((uintptr_t)A & 15) || ((uintptr_t)B & 15))
+int launch_gemm_planes_tc_strided(const Field &f, int64_t m, int64_t n, int64_t K,
+                                  const void *A, int64_t lda, int64_t a_plane, const void *B,
+                                  int64_t ldb, int64_t b_plane, uint8_t *C, int64_t ldc,
+                                  int64_t c_plane, cudaStream_t stream) {
+    if (lda % 8 || ldb % 8 || a_plane % 8 || b_plane % 8 || ((uintptr_t)A & 15) ||
+        ((uintptr_t)B & 15))
         return set_error(QADIC_E_INVALID, "plane operands need ld %% 8 == 0 and 16-byte alignment");
     if (K == 0) {
         for (uint32_t i = 0; i < f.k; ++i)
-            if (cudaMemset2DAsync(C + (size_t)i * m * ldc, (size_t)ldc, 0, (size_t)n, (size_t)m,
+            if (cudaMemset2DAsync(C + (size_t)i * c_plane, (size_t)ldc, 0, (size_t)n, (size_t)m,
                                   stream) != cudaSuccess)
                 return set_error(QADIC_E_CUDA, "memset: %s", cudaGetErrorString(cudaGetLastError()));
         return QADIC_OK;
     }
-    if (f.k == 2) return launch_tc<2, 128, 2>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
-    if (f.k == 3) return launch_tc<3, 64, 2>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
-    if (f.k == 4) return launch_tc<4, 64, 2>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
+    if (f.k == 2)
+        return launch_tc<2, 128, 2>(f, m, n, K, A, lda, a_plane, B, ldb, b_plane, C, ldc, c_plane, stream);
+    if (f.k == 3)
+        return launch_tc<3, 64, 2>(f, m, n, K, A, lda, a_plane, B, ldb, b_plane, C, ldc, c_plane, stream);
+    if (f.k == 4)
+        return launch_tc<4, 64, 2>(f, m, n, K, A, lda, a_plane, B, ldb, b_plane, C, ldc, c_plane, stream);
     return set_error(QADIC_E_UNSUPPORTED, "no tensor-core plane kernel for k=%u", f.k);
+}
+
+int launch_gemm_planes_tc(const Field &f, int64_t m, int64_t n, int64_t K, const void *A,
+                          int64_t lda, const void *B, int64_t ldb, uint8_t *C, int64_t ldc,
+                          cudaStream_t stream) {
+    return launch_gemm_planes_tc_strided(f, m, n, K, A, lda, m * lda, B, ldb, n * ldb, C, ldc,
+                                         m * ldc, stream);
 }
 
 }  // namespace qadic

@@ -336,5 +336,28 @@ def test_fp64_and_planes_agree_config3_slice(torch, orc):
     assert np.array_equal(g1[:, ii, jj].T, want)
 
 
+@pytest.mark.parametrize("path,shape", [(q.PATH_PLANES, (640, 200, 136)),
+                                        (q.PATH_PLANES, (300, 96, 64)),
+                                        (q.PATH_FP64_QADIC, (130, 70, 45))])
+def test_matmul_host_end_to_end(torch, orc, path, shape):
+    """qadic_matmul_host from pinned host buffers (copies overlapped with the
+    pack, the plane GEMM in two row halves when m >= 512) against the oracle."""
+    m, n, K = shape
+    p, k = 101, 2
+    f = q.Field(p, k)
+    A = W.centred_planes(k, m, K, 50, salt=31)
+    B = W.centred_planes(k, K, n, 50, salt=32)
+    hA = torch.from_numpy(A).pin_memory()
+    hB = torch.from_numpy(B).pin_memory()
+    hC = torch.full((k, m, n), 255, dtype=torch.uint8).pin_memory()
+    ws = torch.empty(f.matmul_workspace_size(path, q.FMT_INT8_PLANES, m, n, K), dtype=torch.uint8,
+                     device="cuda")
+    for _ in range(2):
+        hC.fill_(255)
+        f.matmul_host(path, q.FMT_INT8_PLANES, hA, hB, hC, m, n, K, ws)
+        torch.cuda.synchronize()
+        assert np.array_equal(hC.numpy(), oracle_gemm_from_planes(orc, p, f.poly, A, B))
+
+
 def test_sync_status_clean(torch):
     q.sync_status()
