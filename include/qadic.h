@@ -188,6 +188,57 @@ int qadic_matmul_host(const qadic_field *field, int path, int in_fmt, int64_t m,
 int qadic_redq(uint32_t p, uint32_t log2_q, uint32_t ndigits, const double *in, double *out,
                int64_t count, uint32_t table_mode, void *stream);
 
+/* -------------------------------------------------------------- redq_pq --
+ * REDQ (Alg. 2) for q a multiple of p, the other choice of q that the
+ * paper's conclusion leaves to compare (q = 10^4, p = 5 in Ex. 3).  Since
+ * -q = 0 mod p the corrections of Alg. 2 vanish and mu_j = u_j (Thm. 2): no
+ * table.  Each division by q^j (no longer a shift) is a Lemma 1 floor by
+ * 1/q^j rounded upward, or with QADIC_REDQ_INT_FLOOR an integer
+ * multiply-high, and floor(rop/q^j) = floor(r/(p q^j)).
+ * in[i] = sum_{j<=d} mu~_j q^j with 0 <= mu~_j < q, d = ndigits-1, an exact
+ * integer held in a double; out[i] = rho = sum_j (mu~_j mod p) q^j (exact).
+ * Requires p prime <= 251, q >= p with p | q, q^ndigits <= 2^51 (else
+ * QADIC_E_OVERFLOW: Lemma 1's limit), flags 0 or QADIC_REDQ_INT_FLOOR,
+ * in/out 16-byte aligned device pointers (may alias).  Words at or above
+ * q^ndigits give unspecified values without faulting. */
+int qadic_redq_pq(uint32_t p, uint64_t q, uint32_t ndigits, const double *in, double *out,
+                  int64_t count, uint32_t flags, void *stream);
+
+/* ---------------------------------------------------------- polymul_fqt --
+ * Products of long polynomials in Z_p[X] by the d-FQT (Sec. 7, Table 1).
+ * a, b: count polynomials of degree N, N+1 uint8 coefficients each (lowest
+ * first; values are reduced mod p).  out: count x (2N+1) uint8 coefficients
+ * in [0, p-1].  Device pointers, owned by the caller.
+ * Each polynomial is cut into D_q+1 blocks of d+1 coefficients packed into
+ * one word each (Y = X^(d+1), q = 2^log2_q); the word convolution is summed
+ * exactly and reduced by REDQ_{2d+1} (Alg. 2) after at most n_q products,
+ * the reduced word being fed back into the sum; overlapping block digits
+ * are added mod p.  d = 0 is the classical algorithm with delayed
+ * reduction.  Words (flags):
+ *   0                    binary64, the paper's choice: (2d+1) log2_q <= 51
+ *                        (Lemma 1's limit), floor(r/p) by Lemma 1;
+ *   QADIC_FQT_INT_WORDS  64-bit integers with 32-bit operands (Sec. 2 allows
+ *                        m = 64): (d+1) log2_q <= 32, (2d+1) log2_q <= 64,
+ *                        floor(r/p) by an integer multiply-high.
+ * n_q is the largest integer with q > n_q (d+1)(p-1)^2 + (p-1) (Eq. 2 with
+ * k = d+1, plus room for the fed-back word).  Errors: QADIC_E_INVALID (p not
+ * a prime <= 251, d > 24, bad flags, NULL with count > 0), QADIC_E_OVERFLOW
+ * (n_q = 0 for this d), QADIC_E_UNSUPPORTED (N too large for one CTA's
+ * shared memory: about 200 KB for the words and residue sums). */
+#define QADIC_FQT_INT_WORDS 0x1u
+typedef struct qadic_fqt_info {
+    uint32_t log2_q;           /* q = 2^log2_q */
+    uint32_t n_q;              /* products summed between reductions (capped at 2^32-1) */
+    uint32_t D_q;              /* blocks per polynomial, minus one: ceil((N+1)/(d+1)) - 1 */
+    uint32_t word_bits;        /* 53 (binary64) or 64 */
+    uint64_t word_products;    /* (D_q+1)^2 word multiply-adds per polynomial product */
+} qadic_fqt_info;
+/* Host only: the parameters qadic_polymul_fqt would use (same errors). */
+int qadic_polymul_fqt_info(uint32_t p, uint32_t N, uint32_t d, uint32_t flags,
+                           qadic_fqt_info *out);
+int qadic_polymul_fqt(uint32_t p, uint32_t N, uint32_t d, const uint8_t *a, const uint8_t *b,
+                      uint8_t *out, int64_t count, uint32_t flags, void *stream);
+
 /* ------------------------------------------------------ polymul_batched --
  * Alg. 1 on `count` independent pairs in Z_p[X] (no defining polynomial):
  * a, b: count x k uint8 coefficients in [0, p-1] (pair s at a + s*k);

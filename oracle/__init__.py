@@ -64,6 +64,7 @@ def _c():
                 "or_gemm": (None, [u32, u32, u32p, i64, i64, i64, i32p, i32p, u32p]),
                 "or_dot_batch": (None, [u32, u32, u32p, i64, i64, i32p, i32p, u32p]),
                 "or_polymul": (None, [u32, u32, i64, i32p, i32p, u32p]),
+                "or_polymul_long": (None, [u32, i64, i64, i32p, i32p, u32p]),
                 "or_redq": (None, [u32, u64, u32, i64, f64p, f64p]),
                 "or_redq_digits_u128": (None, [u32, u64, u32, u64, u64, u32p]),
                 "or_redq_alg2_u128": (None, [u32, u64, u32, u64, u64, u64p, i64p, u32p]),
@@ -210,6 +211,19 @@ def polymul(p: int, a, b) -> np.ndarray:
     out = np.zeros((count, 2 * k - 1), dtype=np.uint32)
     _c().or_polymul(p, k, count, _ptr(A, ctypes.c_int32), _ptr(B, ctypes.c_int32),
                     _ptr(out, ctypes.c_uint32))
+    return out
+
+
+def polymul_long(p: int, a, b) -> np.ndarray:
+    """Products of degree-N polynomials in Z_p[X] (Sec. 7's workload): a, b
+    (count, N+1), lowest coefficient first.  Returns (count, 2N+1) in
+    [0, p-1]: the schoolbook convolution, accumulated in int64, mod p."""
+    A, B = _i32(a), _i32(b)
+    count, n1 = A.shape
+    assert B.shape == A.shape and n1 >= 1
+    out = np.zeros((count, 2 * n1 - 1), dtype=np.uint32)
+    _c().or_polymul_long(p, n1 - 1, count, _ptr(A, ctypes.c_int32), _ptr(B, ctypes.c_int32),
+                         _ptr(out, ctypes.c_uint32))
     return out
 
 

@@ -240,6 +240,24 @@ void or_polymul(uint32_t p, uint32_t k, int64_t count, const int32_t *a, const i
     }
 }
 
+/* Long polynomial products in Z_p[X] (Sec. 7's workload, the plain
+ * definition behind both the classical method and the d-FQT): a and b are
+ * count polynomials of degree N (N+1 coefficients each, lowest first);
+ * out[s*(2N+1) + t] = (sum_{i+j=t} a_i b_j) mod p, accumulated in int64. */
+void or_polymul_long(uint32_t p, int64_t N, int64_t count, const int32_t *a, const int32_t *b,
+                     uint32_t *out) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t s = 0; s < count; ++s) {
+        const int32_t *x = a + s * (N + 1), *y = b + s * (N + 1);
+        for (int64_t t = 0; t <= 2 * N; ++t) {
+            int64_t acc = 0;
+            const int64_t lo = t > N ? t - N : 0, hi = t < N ? t : N;
+            for (int64_t i = lo; i <= hi; ++i) acc += (int64_t)x[i] * (int64_t)y[t - i];
+            out[s * (2 * N + 1) + t] = (uint32_t)(((acc % (int64_t)p) + p) % p);
+        }
+    }
+}
+
 /* Plain REDQ specification (Alg. 2 ENSURE): for each word r = sum_{i<=d}
  * mu~_i q^i (an exact non-negative integer held in a double, < 2^53), write
  * rho = sum_i (mu~_i mod p) q^i.  Digits by repeated integer division. */

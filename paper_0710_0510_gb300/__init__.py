@@ -24,6 +24,7 @@ REDQ_INT_FLOOR = 0x100
 POLYMUL_PLAIN_F64 = 0x1
 BATCHED_GRAPH = 0x1
 FIELD_HOST_ONLY = 0x1
+FQT_INT_WORDS = 0x1
 
 _lock = threading.Lock()
 _lib = None
@@ -51,6 +52,11 @@ class GemmDesc(ctypes.Structure):
                 ("ldc", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class FqtInfo(ctypes.Structure):
+    _fields_ = [("log2_q", ctypes.c_uint32), ("n_q", ctypes.c_uint32), ("D_q", ctypes.c_uint32),
+                ("word_bits", ctypes.c_uint32), ("word_products", ctypes.c_uint64)]
+
+
 _SIGS = {
     "qadic_field_init": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_uint32,
                                         ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint32]),
@@ -73,6 +79,14 @@ _SIGS = {
     "qadic_redq": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                   ctypes.c_uint32, ctypes.c_void_p]),
+    "qadic_redq_pq": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                     ctypes.c_uint32, ctypes.c_void_p]),
+    "qadic_polymul_fqt_info": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                              ctypes.c_uint32, ctypes.POINTER(FqtInfo)]),
+    "qadic_polymul_fqt": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_int64, ctypes.c_uint32, ctypes.c_void_p]),
     "qadic_polymul_batched": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                              ctypes.c_uint32, ctypes.c_void_p]),
@@ -236,6 +250,37 @@ def redq(p: int, log2_q: int, ndigits: int, words, out=None, table_mode: int = 3
     mode = table_mode | (REDQ_INT_FLOOR if int_floor else 0)
     _check(lib().qadic_redq(p, log2_q, ndigits, _ptr(words), _ptr(out), words.numel(), mode,
                             _stream(stream)))
+    return out
+
+
+def redq_pq(p: int, q: int, ndigits: int, words, out=None, int_floor: bool = False,
+            stream=None):
+    """REDQ for q a multiple of p, no correction step (``qadic_redq_pq``)."""
+    torch = _torch()
+    if out is None:
+        out = torch.empty_like(words)
+    _check(lib().qadic_redq_pq(p, q, ndigits, _ptr(words), _ptr(out), words.numel(),
+                               REDQ_INT_FLOOR if int_floor else 0, _stream(stream)))
+    return out
+
+
+def polymul_fqt_info(p: int, N: int, d: int, int_words: bool = False) -> FqtInfo:
+    """Parameters of the d-FQT product (``qadic_polymul_fqt_info``, host only)."""
+    info = FqtInfo()
+    _check(lib().qadic_polymul_fqt_info(p, N, d, FQT_INT_WORDS if int_words else 0,
+                                        ctypes.byref(info)))
+    return info
+
+
+def polymul_fqt(p: int, d: int, a, b, out=None, int_words: bool = False, stream=None):
+    """Long polynomial products by the d-FQT (``qadic_polymul_fqt``);
+    a, b: (count, N+1) uint8, returns (count, 2N+1) uint8."""
+    torch = _torch()
+    count, n1 = a.shape
+    if out is None:
+        out = torch.empty((count, 2 * n1 - 1), dtype=torch.uint8, device=a.device)
+    _check(lib().qadic_polymul_fqt(p, n1 - 1, d, _ptr(a), _ptr(b), _ptr(out), count,
+                                   FQT_INT_WORDS if int_words else 0, _stream(stream)))
     return out
 
 

@@ -373,6 +373,46 @@ int qadic_redq(uint32_t p, uint32_t log2_q, uint32_t ndigits, const double *in, 
                        (table_mode & QADIC_REDQ_INT_FLOOR) != 0, (cudaStream_t)stream);
 }
 
+int qadic_redq_pq(uint32_t p, uint64_t q, uint32_t ndigits, const double *in, double *out,
+                  int64_t count, uint32_t flags, void *stream) {
+    if (!is_prime(p) || p > 251) return set_error(QADIC_E_INVALID, "p must be a prime <= 251");
+    if (q < p || q % p != 0) return set_error(QADIC_E_INVALID, "q must be a multiple of p");
+    if (ndigits < 1 || ndigits > 51) return set_error(QADIC_E_INVALID, "bad ndigits");
+    unsigned __int128 qd = 1;
+    for (uint32_t j = 0; j < ndigits && qd <= ((unsigned __int128)1 << 51); ++j) qd *= q;
+    if (qd > ((unsigned __int128)1 << 51))
+        return set_error(QADIC_E_OVERFLOW,
+                         "q^ndigits exceeds 2^51 (Lemma 1 limit for binary64)");
+    if (flags & ~QADIC_REDQ_INT_FLOOR) return set_error(QADIC_E_INVALID, "flags 0x%x", flags);
+    if (count < 0) return set_error(QADIC_E_INVALID, "negative count");
+    if (count == 0) return QADIC_OK;
+    if (!in || !out) return set_error(QADIC_E_INVALID, "NULL pointer");
+    if (((uintptr_t)in & 15) || ((uintptr_t)out & 15))
+        return set_error(QADIC_E_INVALID, "in/out must be 16-byte aligned");
+    return launch_redq_pq(p, q, ndigits, in, out, count, (flags & QADIC_REDQ_INT_FLOOR) != 0,
+                          (cudaStream_t)stream);
+}
+
+int qadic_polymul_fqt_info(uint32_t p, uint32_t N, uint32_t d, uint32_t flags,
+                           qadic_fqt_info *out) {
+    if (!out) return set_error(QADIC_E_INVALID, "NULL info");
+    if (flags & ~QADIC_FQT_INT_WORDS) return set_error(QADIC_E_INVALID, "flags 0x%x", flags);
+    return fqt_parameters(p, N, d, (flags & QADIC_FQT_INT_WORDS) != 0, out);
+}
+
+int qadic_polymul_fqt(uint32_t p, uint32_t N, uint32_t d, const uint8_t *a, const uint8_t *b,
+                      uint8_t *out, int64_t count, uint32_t flags, void *stream) {
+    if (flags & ~QADIC_FQT_INT_WORDS) return set_error(QADIC_E_INVALID, "flags 0x%x", flags);
+    qadic_fqt_info info;
+    const int st = fqt_parameters(p, N, d, (flags & QADIC_FQT_INT_WORDS) != 0, &info);
+    if (st != QADIC_OK) return st;
+    if (count < 0) return set_error(QADIC_E_INVALID, "negative count");
+    if (count == 0) return QADIC_OK;
+    if (!a || !b || !out) return set_error(QADIC_E_INVALID, "NULL pointer");
+    return launch_polymul_fqt(p, N, d, (flags & QADIC_FQT_INT_WORDS) != 0, a, b, out, count,
+                              (cudaStream_t)stream);
+}
+
 int qadic_polymul_batched(uint32_t p, uint32_t k, const uint8_t *a, const uint8_t *b, uint8_t *out,
                           int64_t count, uint32_t flags, void *stream) {
     if (!is_prime(p) || p > 251) return set_error(QADIC_E_INVALID, "p must be a prime <= 251");

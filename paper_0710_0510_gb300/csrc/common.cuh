@@ -9,7 +9,7 @@
 
 namespace qadic {
 
-// Division by an invariant integer d (2 <= d < 2^32) with one multiply-high,
+// Division by an invariant integer d (1 <= d < 2^63) with one multiply-high,
 // after Granlund & Montgomery, "Division by invariant integers using
 // multiplication" (PLDI 1994), Fig. 4.1: with l = ceil(log2 d) and
 // m = floor(2^64 (2^l - d) / d) + 1, floor(n/d) = (t + ((n - t) >> 1)) >> (l-1)
@@ -19,7 +19,7 @@ struct Div64 {
     uint32_t sh1, sh2;
 };
 
-inline Div64 make_div64(uint32_t d) {
+inline Div64 make_div64(uint64_t d) {
     uint32_t l = 0;
     while ((1ull << l) < d) ++l;
     const unsigned __int128 two64 = (unsigned __int128)1 << 64;

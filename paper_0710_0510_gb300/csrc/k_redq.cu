@@ -13,6 +13,10 @@
 //   mode 3: full p^(d+1) table, one lookup returning rho itself
 // Table indices are p-adic, sum u_i p^i (Sec. 5.3).
 //
+// A second kernel handles q a multiple of p (no corrections, divisions by
+// q^j instead of shifts), the alternative choice of q left open in the
+// paper's conclusion.
+//
 // HBM-bound: 8 bytes in and 8 bytes out per word; each thread streams pairs
 // of words with 16-byte loads/stores over a grid sized to the SM count.
 #include "common.cuh"
@@ -211,14 +215,82 @@ redq_kernel(const double *__restrict__ in, double *__restrict__ out, int64_t cou
     }
 }
 
-template <int MODE, bool INT_FLOOR>
-int launch_mode(const double *in, double *out, int64_t count, const RedqParams &P, size_t smem,
-                cudaStream_t stream) {
-    auto kern = redq_kernel<MODE, INT_FLOOR>;
+
+// ---------------------------------------------------------------------------
+// REDQ with q a multiple of p.  Then -q = 0 mod p, so Alg. 2's corrections
+// vanish (mu_j = u_j, Thm. 2) and no table is needed; the price is that the
+// divisions by q^j are no longer shifts.  Each is a Lemma 1 floor by a
+// precomputed 1/q^j rounded up (or an integer multiply-high), and
+// floor(rop/q^j) = floor(r/(p q^j)) (nested floors, as in the proof of
+// Thm. 2) makes every digit independent of the others:
+//   u_j = floor(r/q^j) - p floor(r/(p q^j)),   rho = sum_j u_j q^j.
+constexpr int kMaxPqDigits = 51;
+
+struct RedqPqParams {
+    uint32_t p, d;
+    uint64_t qpow[kMaxPqDigits];       // q^j
+    double inv_q_up[kMaxPqDigits];     // 1/q^j rounded toward +infinity
+    double inv_pq_up[kMaxPqDigits];    // 1/(p q^j) rounded toward +infinity
+    Div64 div_q[kMaxPqDigits], div_pq[kMaxPqDigits];
+};
+
+template <bool INT_FLOOR>
+__device__ __forceinline__ double redq_pq_word(double x, const RedqPqParams &P) {
+    const uint64_t r = f64_to_u64_exact(x);
+    uint64_t rho = 0;
+    for (uint32_t j = 0; j <= P.d; ++j) {
+        uint64_t a, b;   // floor(r / q^j), floor(r / (p q^j))
+        if (INT_FLOOR) {
+            a = j == 0 ? r : div64(r, P.div_q[j]);
+            b = div64(r, P.div_pq[j]);
+        } else {
+            a = j == 0 ? r : f64_to_u64_exact(__dmul_ru(x, P.inv_q_up[j]));
+            b = f64_to_u64_exact(__dmul_ru(x, P.inv_pq_up[j]));
+        }
+        const uint32_t u = (uint32_t)a - P.p * (uint32_t)b;
+        rho += (uint64_t)u * P.qpow[j];
+    }
+    return u64_to_f64_exact(rho);
+}
+
+template <bool INT_FLOOR>
+__global__ void __launch_bounds__(kThreads)
+redq_pq_kernel(const double *__restrict__ in, double *__restrict__ out, int64_t count,
+               const __grid_constant__ RedqPqParams P) {
+    const int64_t npairs = count >> 1;
+    const double2 *in2 = reinterpret_cast<const double2 *>(in);
+    double2 *out2 = reinterpret_cast<double2 *>(out);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < npairs;
+         b += kUnroll * stride) {
+        double2 w[kUnroll];
+#pragma unroll
+        for (int s = 0; s < kUnroll; ++s) {
+            const int64_t i = b + s * stride;
+            w[s] = i < npairs ? __ldcs(in2 + i) : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int s = 0; s < kUnroll; ++s) {
+            const int64_t i = b + s * stride;
+            if (i < npairs) {
+                double2 o;
+                o.x = redq_pq_word<INT_FLOOR>(w[s].x, P);
+                o.y = redq_pq_word<INT_FLOOR>(w[s].y, P);
+                __stcs(out2 + i, o);
+            }
+        }
+    }
+    if ((count & 1) && blockIdx.x == 0 && threadIdx.x == 0)
+        out[count - 1] = redq_pq_word<INT_FLOOR>(in[count - 1], P);
+}
+
+template <typename Kern, typename Params>
+int launch_stream(Kern kern, const double *in, double *out, int64_t count, const Params &P,
+                  size_t smem, cudaStream_t stream, const char *what) {
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
-        return set_error(QADIC_E_CUDA, "redq smem attribute: %s",
+        return set_error(QADIC_E_CUDA, "%s smem attribute: %s", what,
                          cudaGetErrorString(cudaGetLastError()));
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
@@ -232,11 +304,31 @@ int launch_mode(const double *in, double *out, int64_t count, const RedqParams &
     if (need < blocks) blocks = need > 0 ? need : 1;
     kern<<<(unsigned)blocks, kThreads, smem, stream>>>(in, out, count, P);
     const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return set_error(QADIC_E_CUDA, "redq launch: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) return set_error(QADIC_E_CUDA, "%s launch: %s", what, cudaGetErrorString(e));
     return QADIC_OK;
 }
 
+template <int MODE, bool INT_FLOOR>
+int launch_mode(const double *in, double *out, int64_t count, const RedqParams &P, size_t smem,
+                cudaStream_t stream) {
+    return launch_stream(redq_kernel<MODE, INT_FLOOR>, in, out, count, P, smem, stream, "redq");
+}
+
 }  // namespace
+
+// 1/d rounded toward +infinity (d < 2^52): the nearest double, bumped up one
+// ulp if it falls below the true 1/d (checked exactly in 128-bit integers).
+double inv_up(uint64_t d) {
+    double inv = 1.0 / (double)d;
+    int e;
+    const double mfrac = frexp(inv, &e);            // inv = mfrac * 2^e, mfrac in [0.5, 1)
+    const uint64_t M = (uint64_t)ldexp(mfrac, 53);  // inv = M * 2^(e-53)
+    // inv >= 1/d  <=>  M * d >= 2^(53-e)
+    const unsigned __int128 lhs = (unsigned __int128)M * d;
+    const unsigned __int128 rhs = (unsigned __int128)1 << (53 - e);
+    if (lhs < rhs) inv = nextafter(inv, 2.0);
+    return inv;
+}
 
 int launch_redq(uint32_t p, uint32_t log2_q, uint32_t ndigits, const double *in, double *out,
                 int64_t count, uint32_t table_mode, bool int_floor, cudaStream_t stream) {
@@ -248,19 +340,7 @@ int launch_redq(uint32_t p, uint32_t log2_q, uint32_t ndigits, const double *in,
     P.qneg = (uint32_t)((p - q % p) % p);
     P.m32 = make_mod_small(p);
     P.divp = make_div64(p);
-    // 1/p rounded toward +infinity: the nearest double, bumped up one ulp if
-    // it falls below the true 1/p (checked exactly in 128-bit integers).
-    {
-        double inv = 1.0 / (double)p;
-        int e;
-        const double mfrac = frexp(inv, &e);          // inv = mfrac * 2^e, mfrac in [0.5, 1)
-        const uint64_t M = (uint64_t)ldexp(mfrac, 53); // inv = M * 2^(e-53)
-        // inv >= 1/p  <=>  M * p >= 2^(53-e)
-        const unsigned __int128 lhs = (unsigned __int128)M * p;
-        const unsigned __int128 rhs = (unsigned __int128)1 << (53 - e);
-        if (lhs < rhs) inv = nextafter(inv, 2.0);
-        P.inv_p_up = inv;
-    }
+    P.inv_p_up = inv_up(p);
     size_t smem = 0;
     uint32_t mode = table_mode;
     if (mode == 3) {
@@ -306,6 +386,26 @@ int launch_redq(uint32_t p, uint32_t log2_q, uint32_t ndigits, const double *in,
         case 2: return launch_mode<2, false>(in, out, count, P, smem, stream);
         default: return launch_mode<3, false>(in, out, count, P, smem, stream);
     }
+}
+
+int launch_redq_pq(uint32_t p, uint64_t q, uint32_t ndigits, const double *in, double *out,
+                   int64_t count, bool int_floor, cudaStream_t stream) {
+    if (ndigits < 1 || ndigits > (uint32_t)kMaxPqDigits)
+        return set_error(QADIC_E_INVALID, "ndigits outside [1, %d]", kMaxPqDigits);
+    RedqPqParams P{};
+    P.p = p;
+    P.d = ndigits - 1;
+    uint64_t qj = 1;
+    for (uint32_t j = 0; j < ndigits; ++j) {
+        P.qpow[j] = qj;
+        P.inv_q_up[j] = inv_up(qj);
+        P.inv_pq_up[j] = inv_up(qj * p);
+        P.div_q[j] = make_div64(qj);
+        P.div_pq[j] = make_div64(qj * p);
+        qj *= q;
+    }
+    if (int_floor) return launch_stream(redq_pq_kernel<true>, in, out, count, P, 0, stream, "redq_pq");
+    return launch_stream(redq_pq_kernel<false>, in, out, count, P, 0, stream, "redq_pq");
 }
 
 }  // namespace qadic

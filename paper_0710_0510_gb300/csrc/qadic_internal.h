@@ -66,6 +66,18 @@ int launch_polymul(uint32_t p, uint32_t k, uint32_t log2_q, bool plain_f64, cons
 int launch_redq(uint32_t p, uint32_t log2_q, uint32_t ndigits, const double *in, double *out,
                 int64_t count, uint32_t table_mode, bool int_floor, cudaStream_t stream);
 
+// 1/d rounded toward +infinity (d < 2^52), checked exactly (k_redq.cu).
+double inv_up(uint64_t d);
+
+// d-FQT long polynomial products (k_polyfqt.cu).
+int fqt_parameters(uint32_t p, uint32_t N, uint32_t d, bool int_words, qadic_fqt_info *info);
+int launch_polymul_fqt(uint32_t p, uint32_t N, uint32_t d, bool int_words, const uint8_t *a,
+                       const uint8_t *b, uint8_t *out, int64_t count, cudaStream_t stream);
+
+// REDQ with q a multiple of p (q^ndigits <= 2^51): no correction step.
+int launch_redq_pq(uint32_t p, uint64_t q, uint32_t ndigits, const double *in, double *out,
+                   int64_t count, bool int_floor, cudaStream_t stream);
+
 int launch_pack(const Field &f, int in_fmt, const void *in, int64_t rows, int64_t cols,
                 int64_t ld_in, int out_fmt, void *out, int64_t ld_out, cudaStream_t stream);
 

@@ -23,6 +23,16 @@ def polymul_pairs(count: int, p: int, k: int, index: int = 0, salt: int = 0):
     return a, b
 
 
+def polylong_pairs(count: int, N: int, p: int, index: int = 5, salt: int = 0):
+    """count pairs of degree-N polynomials over Z_p (Sec. 7's workload; the
+    paper's example is p = 3, N = 500): coefficients uniform in [0, p-1],
+    uint8 arrays of shape (count, N+1)."""
+    g = rng(index, salt)
+    a = g.integers(0, p, (count, N + 1), dtype=np.uint8)
+    b = g.integers(0, p, (count, N + 1), dtype=np.uint8)
+    return a, b
+
+
 def log_matrix(rows: int, cols: int, order: int, index: int = 1, salt: int = 0):
     """Discrete-log codes uniform over all `order` field elements (code
     order-1 is zero): uint8 when order <= 256, else uint16."""
@@ -48,6 +58,15 @@ def redq_words(count: int, ndigits: int, log2_q: int, index: int = 4, salt: int 
     [0, 2^log2_q - 1]: a uniform integer below 2^(ndigits*log2_q), as float64."""
     g = rng(index, salt)
     return g.integers(0, 1 << (ndigits * log2_q), count, dtype=np.int64).astype(np.float64)
+
+
+def redq_words_q(count: int, ndigits: int, q: int, index: int = 4, salt: int = 0):
+    """Packed words sum_j mu~_j q^j with the digits independent and uniform
+    in [0, q-1] -- the same law as a uniform integer below q^ndigits (the
+    base-q digits are a bijection) -- for any q with q^ndigits <= 2^53, as
+    float64."""
+    g = rng(index, salt)
+    return g.integers(0, q ** ndigits, count, dtype=np.int64).astype(np.float64)
 
 
 def batched_shapes(count: int, lo: int = 16, hi: int = 256, index: int = 3, salt: int = 0):

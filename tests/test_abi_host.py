@@ -132,6 +132,79 @@ def test_redq_lemma1_limit_rejected():
     assert st == q.E_INVALID
 
 
+def test_redq_pq_rejections():
+    L = q.lib()
+    a, b = ctypes.c_void_p(16), ctypes.c_void_p(32)
+    # q not a multiple of p
+    assert L.qadic_redq_pq(7, 1024, 5, a, b, 10, 0, None) == q.E_INVALID
+    # q below p
+    assert L.qadic_redq_pq(7, 0, 5, a, b, 10, 0, None) == q.E_INVALID
+    # 1183^5 > 2^51 (Lemma 1 limit); 1176^5 is just below it
+    assert L.qadic_redq_pq(7, 1183, 5, a, b, 10, 0, None) == q.E_OVERFLOW
+    assert b"2^51" in L.qadic_last_error()
+    # q^ndigits overflowing 64 bits is rejected, not wrapped
+    assert L.qadic_redq_pq(7, 7 * 2 ** 40, 30, a, b, 10, 0, None) == q.E_OVERFLOW
+    # unknown flags, misaligned pointers, non-prime p
+    assert L.qadic_redq_pq(7, 1176, 5, a, b, 10, 0x1, None) == q.E_INVALID
+    assert L.qadic_redq_pq(7, 1176, 5, ctypes.c_void_p(8), b, 10, 0, None) == q.E_INVALID
+    assert L.qadic_redq_pq(9, 18, 5, a, b, 10, 0, None) == q.E_INVALID
+    assert L.qadic_redq_pq(7, 1176, 5, None, None, 0, 0, None) == q.OK
+
+
+@pytest.mark.parametrize("p", [2, 3, 7, 31, 101, 251])
+@pytest.mark.parametrize("int_words", [False, True])
+def test_fqt_parameters_satisfy_eq2(p, int_words):
+    """q = 2^s as large as the word allows, n_q the largest count with
+    q > n_q (d+1)(p-1)^2 + (p-1), D_q = ceil((N+1)/(d+1)) - 1 (Sec. 7)."""
+    for d in range(0, 8):
+        D = 2 * d + 1
+        s = min(64 // D, 32 // (d + 1)) if int_words else 51 // D
+        q_ = 2 ** s
+        unit = (d + 1) * (p - 1) ** 2
+        try:
+            info = q.polymul_fqt_info(p, 500, d, int_words)
+        except q.QadicError as e:
+            assert e.status == q.E_OVERFLOW
+            assert unit + (p - 1) >= q_          # not even one product fits
+            continue
+        assert info.log2_q == s
+        assert (2 * d + 1) * s <= (64 if int_words else 51)
+        if int_words:
+            assert (d + 1) * s <= 32
+        n_q = info.n_q
+        assert n_q >= 1 and n_q * unit + (p - 1) < q_
+        if n_q < 2 ** 32 - 1:
+            assert (n_q + 1) * unit + (p - 1) >= q_
+        assert info.D_q == -(-501 // (d + 1)) - 1
+        assert info.word_products == (info.D_q + 1) ** 2
+        assert info.word_bits == (64 if int_words else 53)
+
+
+def test_fqt_paper_example_parameters():
+    """p = 3, N = 500 with binary64 words: d = 2 packs 3 coefficients into
+    q = 2^10 with 85 products between reductions, D_q = 166 (Sec. 7 uses
+    this N and p)."""
+    info = q.polymul_fqt_info(3, 500, 2)
+    assert (info.log2_q, info.n_q, info.D_q) == (10, 85, 166)
+    info = q.polymul_fqt_info(3, 500, 0)
+    assert info.D_q == 500 and info.word_products == 501 ** 2
+
+
+def test_polymul_fqt_rejections():
+    L = q.lib()
+    a = ctypes.c_void_p(16)
+    info = q.FqtInfo()
+    assert L.qadic_polymul_fqt_info(4, 10, 1, 0, ctypes.byref(info)) == q.E_INVALID
+    assert L.qadic_polymul_fqt_info(3, 10, 25, 0, ctypes.byref(info)) == q.E_INVALID
+    assert L.qadic_polymul_fqt_info(3, 10, 1, 2, ctypes.byref(info)) == q.E_INVALID
+    assert L.qadic_polymul_fqt_info(3, 10, 5, 0, ctypes.byref(info)) == q.E_OVERFLOW
+    assert L.qadic_polymul_fqt(3, 10, 1, None, a, a, 4, 0, None) == q.E_INVALID
+    assert L.qadic_polymul_fqt(3, 10, 1, a, a, a, -1, 0, None) == q.E_INVALID
+    assert L.qadic_polymul_fqt(3, 10, 1, None, None, None, 0, 0, None) == q.OK
+    # too long for one CTA's shared memory: refused before any launch
+    assert L.qadic_polymul_fqt(3, 1 << 20, 0, a, a, a, 4, 0, None) == q.E_UNSUPPORTED
+
+
 def test_zero_counts_are_noops():
     L = q.lib()
     assert L.qadic_redq(7, 10, 5, None, None, 0, 3, None) == q.OK

@@ -1,0 +1,155 @@
+"""GPU parity at the benchmark's full sizes, in the launch configuration that
+bench.py times (its own workload builders): outputs against the oracle,
+entry by entry where the oracle can compute them in seconds, and otherwise
+sampled entries plus Freivalds checks (C x = A (B x) for random field
+vectors x), which hold at any size."""
+import numpy as np
+import pytest
+
+import bench
+import paper_0710_0510_gb300 as q
+from paper_0710_0510_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch
+
+
+def planes_to_mkk(X):
+    """(k, rows, cols) planes -> (rows, cols, k) coefficient vectors."""
+    return np.ascontiguousarray(np.transpose(X, (1, 2, 0)))
+
+
+def sampled_entries_agree(orc, f, A, B, C, ii, jj):
+    want = orc.gemm_entries(f.p, f.poly, planes_to_mkk(A), planes_to_mkk(B), ii, jj)
+    return np.array_equal(C[:, ii, jj].T, want)
+
+
+def freivalds(orc, f, A, B, C, vectors=2, seed=0):
+    """C x == A (B x) over GF(p^k) for random x (all as (rows, cols, k))."""
+    rng = np.random.default_rng(seed)
+    n = B.shape[1]
+    for _ in range(vectors):
+        x = rng.integers(0, f.p, (n, 1, f.k))
+        Bx = orc.gemm(f.p, f.poly, B, x)
+        ABx = orc.gemm(f.p, f.poly, A, Bx)
+        Cx = orc.gemm(f.p, f.poly, C, x)
+        if not np.array_equal(ABx, Cx):
+            return False
+    return True
+
+
+def test_plane_gf101_2_n4096_and_fp64_form(torch, orc):
+    """Headline workload: pack + tcgen05 plane GEMM at n = 4096, and the FP64
+    q-adic form on the same inputs."""
+    n = 4096
+    f, A, B, C, step = bench.make_plane_workload(torch, q, W, 101, n)
+    step(None)
+    torch.cuda.synchronize()
+    Ch = C.cpu().numpy()
+    rng = np.random.default_rng(11)
+    ii = np.concatenate([rng.integers(0, n, 512), np.full(n, 17), np.arange(n)])
+    jj = np.concatenate([rng.integers(0, n, 512), np.arange(n), np.full(n, n - 1)])
+    assert sampled_entries_agree(orc, f, A, B, Ch, ii, jj)
+    assert freivalds(orc, f, planes_to_mkk(A), planes_to_mkk(B), planes_to_mkk(Ch))
+    C64, _ = bench.bench_fp64(None, torch, q, W, f, A, B, n, reps=1)
+    assert torch.equal(C64, C)
+    # end to end from pinned host buffers, as timed
+    hA = torch.from_numpy(A).pin_memory()
+    hB = torch.from_numpy(B).pin_memory()
+    hC = torch.empty((2, n, n), dtype=torch.uint8).pin_memory()
+    ws = torch.empty(f.matmul_workspace_size(q.PATH_PLANES, q.FMT_INT8_PLANES, n, n, n),
+                     dtype=torch.uint8, device="cuda")
+    for _ in range(2):
+        hC.zero_()
+        f.matmul_host(q.PATH_PLANES, q.FMT_INT8_PLANES, hA, hB, hC, n, n, n, ws)
+        torch.cuda.synchronize()
+        assert np.array_equal(hC.numpy(), Ch)
+    del C64, ws
+    torch.cuda.empty_cache()
+
+
+def test_plane_gf251_2_n16384(torch, orc):
+    """The n = 16384 GF(251^2) product: 256 sampled entries, one full row and
+    two Freivalds vectors."""
+    n = 16384
+    f, A, B, C, step = bench.make_plane_workload(torch, q, W, 251, n)
+    step(None)
+    torch.cuda.synchronize()
+    Ch = C.cpu().numpy()
+    del C
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(12)
+    ii = np.concatenate([rng.integers(0, n, 256), np.full(n, n - 1)])
+    jj = np.concatenate([rng.integers(0, n, 256), np.arange(n)])
+    assert sampled_entries_agree(orc, f, A, B, Ch, ii, jj)
+    assert freivalds(orc, f, planes_to_mkk(A), planes_to_mkk(B), planes_to_mkk(Ch))
+
+
+def test_fp64_gf27_n1024_full(torch, orc):
+    """GF(3^3), n = 1024 from log codes: every entry against the oracle, the
+    logs converted through the oracle's own generator."""
+    f, A, B, C, step = bench.make_fp64_gf27(torch, q, W)
+    step(None)
+    torch.cuda.synchronize()
+    T = orc.antilog(3, f.poly)
+    want = orc.gemm(3, f.poly, T[A.astype(np.int64)], T[B.astype(np.int64)])
+    assert np.array_equal(planes_to_mkk(C.cpu().numpy()), want)
+
+
+def test_redq_sweep_2_28_words(torch, orc):
+    """The 2^28-word sweep (p = 7, q = 2^10, 5 digits) in every table mode
+    and floor, and the q = 1176 (7 | q) variant, all words compared."""
+    count = 1 << 28
+    w = W.redq_words(count, 5, 10)
+    want = torch.from_numpy(orc.redq(7, 1024, 4, w)).cuda()
+    d = torch.from_numpy(w).cuda()
+    del w
+    out = torch.empty_like(d)
+    for mode in (0, 1, 2, 3):
+        for int_floor in (False, True):
+            out.zero_()
+            q.redq(7, 10, 5, d, out=out, table_mode=mode, int_floor=int_floor)
+            assert torch.equal(out, want), (mode, int_floor)
+    del d, want
+    wq = W.redq_words_q(count, 5, bench.PQ_Q)
+    want = torch.from_numpy(orc.redq(7, bench.PQ_Q, 4, wq)).cuda()
+    d = torch.from_numpy(wq).cuda()
+    del wq
+    for int_floor in (False, True):
+        out.zero_()
+        q.redq_pq(7, bench.PQ_Q, 5, d, out=out, int_floor=int_floor)
+        assert torch.equal(out, want), int_floor
+    del d, want, out
+    torch.cuda.empty_cache()
+
+
+def test_batched_4096_products(torch, orc):
+    """4096 uneven products over GF(2^8), GF(7^4), GF(31^2) in one
+    graph-replayed launch: 48 products in full, every product by a
+    Freivalds vector."""
+    fields, dims, fidx, offs, hA, hB, dC, descs, ws = bench.make_batched(torch, q, W)
+    q.batched_gemm(fields, descs, ws, graph=True)
+    torch.cuda.synchronize()
+    Ch = dC.cpu().numpy()
+
+    def operands(i):
+        m, n, K = (int(x) for x in dims[i])
+        f = fields[fidx[i]]
+        a, b, c = offs[i]
+        A = planes_to_mkk(hA[a:a + f.k * m * K].reshape(f.k, m, K))
+        B = planes_to_mkk(hB[b:b + f.k * K * n].reshape(f.k, K, n))
+        C = planes_to_mkk(Ch[c:c + f.k * m * n].reshape(f.k, m, n))
+        return f, A, B, C
+
+    for i in np.random.default_rng(5).choice(len(descs), 48, replace=False):
+        f, A, B, C = operands(i)
+        assert np.array_equal(C, orc.gemm(f.p, f.poly, A, B)), i
+    for i in range(len(descs)):
+        f, A, B, C = operands(i)
+        assert freivalds(orc, f, A, B, C, vectors=1, seed=i), i

@@ -98,6 +98,49 @@ def test_redq_adversarial_words(torch, orc):
             assert np.array_equal(host(out), orc.redq(p, q_, nd - 1, words))
 
 
+# ------------------------------------------------- REDQ, p divides q ----
+
+@pytest.mark.parametrize("p,q_,nd", [(7, 1176, 5), (5, 10 ** 4, 3), (5, 10, 15), (2, 6, 19),
+                                     (251, 251, 6), (2, 1024, 5), (3, 3 * 2 ** 14, 3),
+                                     (101, 101 * 64, 3), (13, 13, 1)])
+def test_redq_pq_parameters(torch, orc, p, q_, nd):
+    w = W.redq_words_q(30001, nd, q_, salt=p)   # odd count: ragged tail
+    want = orc.redq(p, q_, nd - 1, w)
+    for int_floor in (False, True):
+        out = q.redq_pq(p, q_, nd, dev(torch, w), int_floor=int_floor)
+        assert np.array_equal(host(out), want), int_floor
+
+
+def test_redq_pq_adversarial_words(torch, orc):
+    p, q_, nd = 7, 1176, 5
+    digs = [[q_ - 1] * nd, [0] * nd, [p - 1] * nd, [p] * nd, [2 * p - 1] * nd,
+            [q_ - p] * nd, [q_ - p - 1] * nd, [q_ - 1, 0, q_ - 1, 0, q_ - 1],
+            [0, 0, 0, 0, q_ - 1], [q_ - 1, 0, 0, 0, 0]]
+    words = np.array([sum(d * q_ ** i for i, d in enumerate(x)) for x in digs] * 3 + [1.0],
+                     dtype=np.float64)
+    assert words.max() == q_ ** nd - 1
+    for int_floor in (False, True):
+        out = q.redq_pq(p, q_, nd, dev(torch, words), int_floor=int_floor)
+        assert np.array_equal(host(out), orc.redq(p, q_, nd - 1, words))
+        one = q.redq_pq(p, q_, nd, dev(torch, words[:1]), int_floor=int_floor)
+        assert np.array_equal(host(one), orc.redq(p, q_, nd - 1, words[:1]))
+
+
+def test_redq_pq_in_place(torch, orc):
+    w = W.redq_words_q(4096, 5, 1176, salt=9)
+    x = dev(torch, w)
+    q.redq_pq(7, 1176, 5, x, out=x)
+    assert np.array_equal(host(x), orc.redq(7, 1176, 4, w))
+
+
+def test_redq_pq_agrees_with_power_of_two_path(torch):
+    """q = 2^10 is a multiple of p = 2: both REDQ entry points apply."""
+    w = dev(torch, W.redq_words(10000, 5, 10, salt=2))
+    a = q.redq_pq(2, 1024, 5, w)
+    for mode in (0, 3):
+        assert torch.equal(a, q.redq(2, 10, 5, w, table_mode=mode))
+
+
 # --------------------------------------------------------------- pack ----
 
 @pytest.mark.parametrize("pk", [(3, 3), (101, 2), (7, 4), (2, 8), (251, 2)])

@@ -102,6 +102,71 @@ def test_redq_large_words_vs_u128(orc):
         assert int(o) == sum(m * q ** i for i, m in enumerate(mu))
 
 
+# ------------------------------------------ q a multiple of p (Sec. 4) ----
+
+def test_example3_result_at_a_smaller_multiple_of_p(orc):
+    """Ex. 3's product, packed with q = 100 (also a multiple of p = 5, and
+    large enough for its coefficients) so that the word is an exact double:
+    the oracle's word-level REDQ returns the example's residues."""
+    ex = EX["example3"]
+    p, q = ex["p"], 100
+    r = int(orc.qadic_value(ex["a"], q)) * int(orc.qadic_value(ex["b"], q))
+    assert r < 2 ** 53
+    rho = int(orc.redq(p, q, 4, np.array([float(r)]))[0])
+    assert [(rho // q ** i) % q for i in range(5)] == ex["result"]
+
+
+@pytest.mark.parametrize("p,q,d", [(3, 6, 2), (5, 10, 3), (2, 4, 4), (7, 7, 2)])
+def test_redq_p_divides_q_shortcut(orc, p, q, d):
+    """With p | q the whole reduction is one subtraction (Ex. 3):
+    rho = r - p * sum_i floor(mu~_i / p) q^i, over every word with d+1
+    base-q digits."""
+    words = np.arange(q ** (d + 1), dtype=np.int64)
+    out = orc.redq(p, q, d, words.astype(np.float64)).astype(np.int64)
+    for w, o in zip(words.tolist(), out.tolist()):
+        quot = sum((((w // q ** i) % q) // p) * q ** i for i in range(d + 1))
+        assert o == w - p * quot
+
+
+def test_redq_p_divides_q_sweep_vs_u128(orc):
+    p, q, d = 7, 1176, 4
+    assert q % p == 0 and q ** (d + 1) <= 2 ** 51
+    rng = np.random.default_rng(3)
+    digits = rng.integers(0, q, (3000, d + 1))
+    words = (digits * np.array([q ** i for i in range(d + 1)])).sum(axis=1)
+    out = orc.redq(p, q, d, words.astype(np.float64)).astype(np.int64)
+    assert np.array_equal(out, ((digits % p) * np.array([q ** i for i in range(d + 1)])).sum(axis=1))
+    for x, o in zip(words[:200].tolist(), out[:200].tolist()):
+        mu = orc.redq_digits_u128(p, q, d, int(x))
+        assert o == sum(m * q ** i for i, m in enumerate(mu))
+
+
+@pytest.mark.parametrize("D", [1176, 1176 ** 2, 7 * 1176 ** 3, 1176 ** 4, 7 * 1176 ** 4,
+                               10 ** 4, 5 * 10 ** 12])
+def test_lemma1_composite_divisors(orc, D):
+    """Lemma 1 holds for any positive integer divisor, not only primes: the
+    floors by q^j and p q^j near the 2^51 limit."""
+    limit = 2 ** 51
+    rng = np.random.default_rng(D % 1000003)
+    us = [int(x) for x in rng.integers(0, limit // D, 300)] + [limit // D - 1, 0, 1]
+    for u in us:
+        for i in (0, 1, D - 1):
+            r = u * D + i
+            if r < limit:
+                assert orc.lemma1_floor(float(r), float(D)) == r // D
+
+
+def test_nested_floor_identity():
+    """floor(floor(r/p)/q^j) = floor(r/(p q^j)) (used in the proof of Thm. 2),
+    the identity that lets each digit's second floor divide r directly."""
+    rng = np.random.default_rng(5)
+    for p, q in [(7, 1176), (5, 10), (3, 8), (251, 251)]:
+        for _ in range(2000):
+            r = int(rng.integers(0, 2 ** 51))
+            for j in range(4):
+                assert (r // p) // q ** j == r // (p * q ** j)
+
+
 # ------------------------------------------------ Sec. 5: Q_d matrices ----
 
 def qd_matrix(d, q, p):
