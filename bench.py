@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--workload", default="plane",
                     choices=["plane", "fp64", "redq", "polymul", "large", "batched", "fqt"])
     ap.add_argument("--n", type=int, default=None, help="override the matrix size")
+    ap.add_argument("--words", type=int, default=1 << 28, help="REDQ sweep size (words)")
+    ap.add_argument("--extras", default="all", choices=["all", "none"],
+                    help="none: only the selected workload's timed step (for profiling)")
     return ap.parse_args()
 
 
@@ -248,7 +251,8 @@ def bench_fp64(args, torch, q, W, f, A, B, n, reps=2):
                "fp64_tflops": fl / (ms * 1e-3) / 1e12, "n_q": f.n_q, "log2_q": f.log2_q}
 
 
-def bench_redq(args, torch, q, W, count=1 << 28, steps=10):
+def bench_redq(args, torch, q, W, count=None, steps=10):
+    count = count or args.words
     w = W.redq_words(count, 5, 10)
     d = torch.from_numpy(w).cuda()
     out = torch.empty_like(d)
@@ -392,6 +396,13 @@ def bench_batched(args, torch, q, W):
     def step(kev):
         q.batched_gemm(fields, descs, ws, graph=True)
 
+    # default tiles, then the autotuner's choice on this batch (tuning is
+    # setup, outside the timed region)
+    for k in range(1, 9):
+        q.batched_select_tiles(k, -1)
+    total0, _ = time_steps(torch, step, args.steps, args.warmup, None)
+    ms_default = total0 / args.steps
+    chosen = q.batched_autotune(fields, descs, ws, reps=3)
     total, _ = time_steps(torch, step, args.steps, args.warmup, None)
     ms = total / args.steps
     ops = float(sum(2 * int(m) * int(n) * int(K) for m, n, K in dims))
@@ -413,6 +424,10 @@ def bench_batched(args, torch, q, W):
             "products": len(descs), "field_ops": ops, "plane_flops": flops,
             "one_launch_per_product": {"value": ops / (ms1 * 1e-3) / 1e9, "ms": ms1},
             "speedup_vs_per_product": ms1 / ms,
+            "autotuned_tiles": {str(k): dict(zip(("bm", "bn", "bk"),
+                                                 q.batched_tile_configs(k)[c][:3]))
+                                for k, c in chosen.items()},
+            "ms_default_tiles": ms_default,
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": pk["bf16_sustained"],
                          "unit": "TFLOP/s", "frac": achieved / pk["bf16_sustained"],
                          "traffic": None, "kernel": "batched_kernel (mma.sync bf16)",
@@ -567,7 +582,7 @@ def main():
             line["config"] = {"workload": f"GF(101^2) n={n}: pack A,B (int8 centred planes -> bf16 "
                               f"operands) + tcgen05 plane GEMM + fused mod-p/mod-P epilogue",
                               "p": 101, "k": 2, "n": n, "l2": FLUSH_NOTE}
-            if rank == 0:
+            if rank == 0 and args.extras == "all":
                 C64, fp = bench_fp64(args, torch, q, W, f, A, B, n)
                 fp["bitexact_vs_plane"] = bool(torch.equal(C64, C))
                 extras["fp64_qadic"] = fp
@@ -580,8 +595,8 @@ def main():
             line.update({"value": r["value"] * world, "unit": "residues/s", "ms_per_step": r["ms"],
                          "dtype": "f64 words, integer REDQ", "roofline": r["roofline"],
                          "gpu_launches": args.steps})
-            line["config"] = {"workload": "REDQ sweep: 2^28 FP64 words, 5 digits, p=7, q=2^10",
-                              "l2": FLUSH_NOTE}
+            line["config"] = {"workload": f"REDQ sweep: {args.words} FP64 words, 5 digits, p=7, "
+                              "q=2^10", "l2": FLUSH_NOTE}
             extras["redq_variants"] = r["variants"]
             extras["q_multiple_of_p"] = r["q_multiple_of_p"]
         elif args.workload == "polymul":
@@ -614,7 +629,7 @@ def main():
             line["config"] = {"workload": "4096 products, m,n,K log-uniform in [16,256], fields "
                               "GF(2^8), GF(7^4), GF(31^2); one persistent graph-replayed launch"}
             extras.update({k: r[k] for k in ("one_launch_per_product", "speedup_vs_per_product",
-                                             "products")})
+                                             "products", "autotuned_tiles", "ms_default_tiles")})
         elif args.workload == "fp64":
             r = bench_fp64_gf27(args, torch, q, W)
             line.update({"value": r["value"] * world, "unit": "field Gop/s",
@@ -625,7 +640,7 @@ def main():
         else:
             raise SystemExit(f"workload {args.workload} not available")
     line["clocks"] = clk.summary()
-    if args.workload == "plane" and rank == 0:
+    if args.workload == "plane" and rank == 0 and args.extras == "all":
         r2 = bench_redq(args, torch, q, W)[2]
         extras["redq"] = {k: r2[k] for k in ("value", "unit", "best", "ms", "roofline",
                                              "q_multiple_of_p")}
@@ -633,7 +648,8 @@ def main():
         extras["polymul"] = pm[3]
         bb = bench_batched(args, torch, q, W)
         extras["batched"] = {k: bb[k] for k in ("value", "unit", "ms_per_step", "one_launch_per_product",
-                                                "speedup_vs_per_product", "roofline")}
+                                                "speedup_vs_per_product", "roofline",
+                                                "autotuned_tiles", "ms_default_tiles")}
         g27 = bench_fp64_gf27(args, torch, q, W)
         extras["polymul_fqt_p3_n500"] = bench_fqt(args, torch, q, W)
         extras["fp64_gf27_n1024"] = g27
@@ -647,7 +663,7 @@ def main():
         del lA, lB, lC
         torch.cuda.empty_cache()
     if rank == 0:
-        if args.workload == "plane":
+        if args.workload == "plane" and args.extras == "all":
             line["cpu_baseline"] = cpu_baseline_plane(101, line["config"]["n"])
         line.update(extras)
         print(json.dumps(line))

@@ -260,13 +260,47 @@ int qadic_polymul_batched(uint32_t p, uint32_t k, const uint8_t *a, const uint8_
  * qadic_batched_workspace_size(count, descs) bytes (device); the host packs
  * the work list into it.  With QADIC_BATCHED_GRAPH the launch is captured in
  * a CUDA graph keyed by (descs, count, workspace) and replayed on later calls
- * with the same key.  Errors: QADIC_E_INVALID, QADIC_E_NOMEM (workspace too
- * small), QADIC_E_OVERFLOW (K beyond the exact FP32 chunk of a field). */
+ * with the same key (and the same tile configurations); a replay first
+ * re-uploads its own work list if another call wrote a different one into
+ * the same workspace.  Tiles: for each field the configuration selected for
+ * its k (qadic_batched_select_tiles / qadic_batched_autotune below), or
+ * configuration 0.  Errors: QADIC_E_INVALID, QADIC_E_NOMEM (workspace too
+ * small), QADIC_E_OVERFLOW (exact FP32 chunk of a field below 32). */
 #define QADIC_BATCHED_GRAPH 0x1u
 size_t qadic_batched_workspace_size(const qadic_gemm_desc *descs, int64_t count);
 int qadic_batched_gemm(const qadic_field *const *fields, int32_t nfields,
                        const qadic_gemm_desc *descs, int64_t count, void *workspace,
                        size_t ws_bytes, uint32_t flags, void *stream);
+
+/* ----------------------------------------------- batched tile autotuning --
+ * The batched kernel can run each product with one of a few tile
+ * configurations per field degree k (the shapes whose 2k-1 accumulator sets
+ * fit in registers): output tile bm x bn, K-block bk, and the shared memory
+ * it needs.  Configuration 0 is the default.  No counterpart in the paper
+ * (it concerns the GPU schedule, not the arithmetic).
+ * qadic_batched_tile_configs: writes min(capacity, n) entries of the table
+ *   for k and sets *count = n.
+ * qadic_batched_select_tiles: process-wide choice for fields with k
+ *   coefficients (index -1 restores the default).  A field whose exact FP32
+ *   chunk is shorter than the chosen bk runs configuration 0.
+ * qadic_batched_autotune: for each k present in `descs` (largest total work
+ *   first), runs the whole batch with every configuration -- a graph
+ *   capture as warm-up, then `reps` graph replays timed with CUDA events on
+ *   `stream` -- selects the fastest and writes it to chosen[k] (chosen has
+ *   9 entries; -1 for an absent k).  It synchronizes `stream`, and the
+ *   outputs hold the products (every configuration computes them exactly).
+ *   Arguments as for qadic_batched_gemm; reps in [1, 1000]. */
+typedef struct qadic_tile_config {
+    int32_t bm, bn, bk;
+    int32_t smem_bytes;
+} qadic_tile_config;
+int qadic_batched_tile_configs(uint32_t k, qadic_tile_config *out, int32_t capacity,
+                               int32_t *count);
+int qadic_batched_select_tiles(uint32_t k, int32_t index);
+int qadic_batched_selected_tiles(uint32_t k, int32_t *index);
+int qadic_batched_autotune(const qadic_field *const *fields, int32_t nfields,
+                           const qadic_gemm_desc *descs, int64_t count, void *workspace,
+                           size_t ws_bytes, int32_t reps, int32_t *chosen, void *stream);
 
 /* ------------------------------------------------ batched_gemm_noalloc --
  * The same products as qadic_batched_gemm (same descriptors, same results),

@@ -52,6 +52,11 @@ class GemmDesc(ctypes.Structure):
                 ("ldc", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class TileConfig(ctypes.Structure):
+    _fields_ = [("bm", ctypes.c_int32), ("bn", ctypes.c_int32), ("bk", ctypes.c_int32),
+                ("smem_bytes", ctypes.c_int32)]
+
+
 class FqtInfo(ctypes.Structure):
     _fields_ = [("log2_q", ctypes.c_uint32), ("n_q", ctypes.c_uint32), ("D_q", ctypes.c_uint32),
                 ("word_bits", ctypes.c_uint32), ("word_products", ctypes.c_uint64)]
@@ -87,6 +92,15 @@ _SIGS = {
     "qadic_polymul_fqt": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_int64, ctypes.c_uint32, ctypes.c_void_p]),
+    "qadic_batched_tile_configs": (ctypes.c_int, [ctypes.c_uint32, ctypes.POINTER(TileConfig),
+                                                  ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    "qadic_batched_select_tiles": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_int32]),
+    "qadic_batched_selected_tiles": (ctypes.c_int, [ctypes.c_uint32,
+                                                    ctypes.POINTER(ctypes.c_int32)]),
+    "qadic_batched_autotune": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32,
+                                              ctypes.POINTER(GemmDesc), ctypes.c_int64,
+                                              ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32,
+                                              ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p]),
     "qadic_polymul_batched": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                              ctypes.c_uint32, ctypes.c_void_p]),
@@ -307,6 +321,37 @@ def batched_gemm(fields, descs, workspace, graph: bool = False, stream=None):
     _check(lib().qadic_batched_gemm(hs, len(fields), arr, len(descs), _ptr(workspace),
                                     workspace.numel() * workspace.element_size(),
                                     BATCHED_GRAPH if graph else 0, _stream(stream)))
+
+
+def batched_tile_configs(k: int):
+    """The batched kernel's tile configurations for degree k
+    (``qadic_batched_tile_configs``): list of (bm, bn, bk, smem_bytes)."""
+    n = ctypes.c_int32()
+    arr = (TileConfig * 8)()
+    _check(lib().qadic_batched_tile_configs(k, arr, 8, ctypes.byref(n)))
+    return [(c.bm, c.bn, c.bk, c.smem_bytes) for c in arr[:n.value]]
+
+
+def batched_select_tiles(k: int, index: int):
+    _check(lib().qadic_batched_select_tiles(k, index))
+
+
+def batched_selected_tiles(k: int) -> int:
+    i = ctypes.c_int32()
+    _check(lib().qadic_batched_selected_tiles(k, ctypes.byref(i)))
+    return i.value
+
+
+def batched_autotune(fields, descs, workspace, reps: int = 3, stream=None):
+    """Time every tile configuration on this batch and keep the fastest per k
+    (``qadic_batched_autotune``); returns {k: chosen index}."""
+    arr = (GemmDesc * len(descs))(*descs)
+    hs = (ctypes.c_void_p * len(fields))(*[f.handle for f in fields])
+    chosen = (ctypes.c_int32 * 9)()
+    _check(lib().qadic_batched_autotune(hs, len(fields), arr, len(descs), _ptr(workspace),
+                                        workspace.numel() * workspace.element_size(), reps,
+                                        chosen, _stream(stream)))
+    return {k: chosen[k] for k in range(9) if chosen[k] >= 0}
 
 
 def batched_gemm_noalloc(fields, descs, stream=None):

@@ -13,8 +13,12 @@
 // (m16n8k16, bf16 -> f32; the tiles are too small for 128-row tcgen05
 // MMAs), accumulated exactly in FP32 registers (every partial sum stays
 // within 2^24; at each exact chunk the accumulators are reduced mod p in
-// place), then reduced mod p, folded and written as uint8 planes.  The
-// tile shape follows k so that the 2k-1 accumulator sets fit in registers.
+// place), then reduced mod p, folded and written as uint8 planes.
+//
+// Tile shape (BM x BN) and K-block size BK are picked per k from a short
+// list of candidates whose 2k-1 accumulator sets fit in registers: index 0
+// by default, or whichever qadic_batched_autotune measured fastest on the
+// caller's own batch (qadic_batched_select_tiles sets one by hand).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -30,13 +34,13 @@ namespace qadic {
 namespace {
 
 constexpr int kThreads = 128;
-constexpr int BK = 32;
+constexpr int kMinBK = 32;        // smallest K-block of any candidate
 constexpr int kMaxFields = 64;
 
 struct BFieldParams {
     uint32_t p, k, h, m32;
     float pf, inv_pf;
-    int32_t chunk_blocks;          // BK-blocks per exact FP32 chunk
+    int32_t chunk_k;               // K elements per exact FP32 chunk (capped)
     int32_t pad;
     uint8_t fold[kMaxK * kMaxK];   // X^(k+t) mod P, row t (k coefficients)
 };
@@ -46,7 +50,7 @@ struct BProd {
     const uint8_t *B;
     uint8_t *C;
     int32_t m, n, K, lda, ldb, ldc;
-    int32_t field, pad;
+    int32_t field, cfg;            // field index, tile configuration index
 };
 
 struct BTile {
@@ -64,23 +68,39 @@ struct BHeader {
 
 constexpr size_t kHeaderBytes = 256;
 
-template <int KP>
+template <int KP, int BM_, int BN_, int BK_>
 struct TileCfg {
-    static constexpr int BM = KP <= 2 ? 64 : 32;
-    static constexpr int BN = KP <= 2 ? 32 : KP <= 4 ? 32 : 16;
+    static constexpr int BM = BM_, BN = BN_, BK = BK_;
     static constexpr int WM = BM / 2, WN = BN / 2;   // 2 x 2 warps
     static constexpr int MT = WM / 16, NT = WN / 8;
     static constexpr int NACC = 2 * KP - 1;
     static constexpr int LDA = BK + 8;               // bf16 elements per A_s row
     static constexpr int LDB = BN + 8;               // bf16 elements per B_s row
     static constexpr int SMEM = (KP * BM * LDA + KP * BK * LDB) * 2;
+    static_assert(MT >= 1 && NT >= 1 && BK % 16 == 0, "tile shape");
 };
 
-__host__ __device__ constexpr int max_i(int a, int b) { return a > b ? a : b; }
+// Candidate (BM, BN, BK) per k; index 0 is the default.  Every candidate is
+// at least 32 x 16 (the work-list bound) and at least kMinBK deep.
+struct TileShape {
+    int bm, bn, bk;
+};
+constexpr int kMaxCfg = 4;
+constexpr TileShape kShapesK2[kMaxCfg] = {{64, 32, 32}, {64, 64, 32}, {32, 32, 32}, {64, 32, 64}};
+constexpr TileShape kShapesK4[kMaxCfg] = {{32, 32, 32}, {64, 32, 32}, {32, 16, 32}, {32, 32, 64}};
+constexpr TileShape kShapesK8[kMaxCfg] = {{32, 16, 32}, {32, 32, 32}, {32, 16, 64}, {32, 16, 32}};
 
-constexpr int kSmemBytes =
-    max_i(max_i(max_i(TileCfg<1>::SMEM, TileCfg<2>::SMEM), max_i(TileCfg<3>::SMEM, TileCfg<4>::SMEM)),
-          max_i(max_i(TileCfg<5>::SMEM, TileCfg<6>::SMEM), max_i(TileCfg<7>::SMEM, TileCfg<8>::SMEM)));
+__host__ __device__ constexpr int num_cfgs(uint32_t k) { return k <= 4 ? 4 : 3; }
+
+inline TileShape tile_shape_of(uint32_t k, int cfg) {
+    if (cfg < 0 || cfg >= num_cfgs(k)) cfg = 0;
+    return k <= 2 ? kShapesK2[cfg] : k <= 4 ? kShapesK4[cfg] : kShapesK8[cfg];
+}
+
+inline size_t tile_smem_bytes(uint32_t k, int cfg) {
+    const TileShape t = tile_shape_of(k, cfg);
+    return (size_t)(k * t.bm * (t.bk + 8) + k * t.bk * (t.bn + 8)) * 2;
+}
 
 __device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2,
                                         uint32_t &r3) {
@@ -136,9 +156,9 @@ __device__ __forceinline__ void load16(const uint8_t *src, int valid, uint32_t (
 }
 
 // Tile staging: chunks of 16 coefficients (one row segment of one plane).
-template <int KP>
+template <int KP, typename T>
 struct Stager {
-    using T = TileCfg<KP>;
+    static constexpr int BK = T::BK;
     static constexpr int A_CH = KP * T::BM * (BK / 16);
     static constexpr int B_CH = KP * BK * (T::BN / 16);
     static constexpr int PER_THREAD = (A_CH + B_CH + kThreads - 1) / kThreads;
@@ -199,12 +219,10 @@ struct Stager {
     }
 };
 
-// Not inlined: each k variant is register-allocated on its own instead of
-// inside one kernel body holding all eight.
-template <int KP>
-__device__ __noinline__ void run_tile(const BProd &P, const BFieldParams &F, int tm, int tn,
+template <int KP, int BM, int BN, int BK>
+__device__ __forceinline__ void run_tile(const BProd &P, const BFieldParams &F, int tm, int tn,
                                       uint8_t *smem, const uint16_t *tab) {
-    using T = TileCfg<KP>;
+    using T = TileCfg<KP, BM, BN, BK>;
     __nv_bfloat16 *As = reinterpret_cast<__nv_bfloat16 *>(smem);   // [KP][BM][LDA]
     __nv_bfloat16 *Bs = As + KP * T::BM * T::LDA;                   // [KP][BK][LDB]
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -222,7 +240,8 @@ __device__ __noinline__ void run_tile(const BProd &P, const BFieldParams &F, int
                 for (int e = 0; e < 4; ++e) acc[t][a][b][e] = 0.f;
 
     const int nkb = (P.K + BK - 1) / BK;
-    Stager<KP> stage;
+    const int chunk_blocks = max(1, F.chunk_k / BK);
+    Stager<KP, T> stage;
     stage.load(P, row0, col0, 0);
     for (int kb = 0; kb < nkb; ++kb) {
         __syncthreads();   // previous tile/step finished reading shared memory
@@ -260,7 +279,7 @@ __device__ __noinline__ void run_tile(const BProd &P, const BFieldParams &F, int
                             mma_bf16_16816(acc[i + j][mt][nt], afr[mt], bfr[j][nt]);
             }
         }
-        if ((kb + 1) % F.chunk_blocks == 0 && kb + 1 < nkb) {
+        if ((kb + 1) % chunk_blocks == 0 && kb + 1 < nkb) {
             // exact-chunk boundary: bring every accumulator back to |x| <= 1.5 p
 #pragma unroll
             for (int t = 0; t < T::NACC; ++t)
@@ -307,8 +326,32 @@ __device__ __noinline__ void run_tile(const BProd &P, const BFieldParams &F, int
             }
 }
 
+// Not inlined: each k is register-allocated on its own (its configurations
+// are branches of one function) instead of inside one kernel body holding
+// all eight.
+template <int KP>
+__device__ __noinline__ void run_tile_cfg(int cfg, const BProd &P, const BFieldParams &F, int tm,
+                                             int tn, uint8_t *smem, const uint16_t *tab) {
+    constexpr bool kSmall = KP <= 2, kMid = KP > 2 && KP <= 4;
+    constexpr TileShape c0 = kSmall ? kShapesK2[0] : kMid ? kShapesK4[0] : kShapesK8[0];
+    constexpr TileShape c1 = kSmall ? kShapesK2[1] : kMid ? kShapesK4[1] : kShapesK8[1];
+    constexpr TileShape c2 = kSmall ? kShapesK2[2] : kMid ? kShapesK4[2] : kShapesK8[2];
+    constexpr TileShape c3 = kSmall ? kShapesK2[3] : kMid ? kShapesK4[3] : kShapesK8[3];
+    switch (cfg) {
+        case 1: run_tile<KP, c1.bm, c1.bn, c1.bk>(P, F, tm, tn, smem, tab); break;
+        case 2: run_tile<KP, c2.bm, c2.bn, c2.bk>(P, F, tm, tn, smem, tab); break;
+        case 3:
+            if constexpr (num_cfgs(KP) > 3) {
+                run_tile<KP, c3.bm, c3.bn, c3.bk>(P, F, tm, tn, smem, tab);
+                break;
+            }
+            [[fallthrough]];
+        default: run_tile<KP, c0.bm, c0.bn, c0.bk>(P, F, tm, tn, smem, tab); break;
+    }
+}
+
 __global__ void __launch_bounds__(kThreads, 3) batched_kernel(uint8_t *ws) {
-    __shared__ __align__(16) uint8_t smem[kSmemBytes];
+    extern __shared__ __align__(16) uint8_t smem[];   // sized for the largest tile in the list
     __shared__ uint16_t tab[256];   // input byte -> centred bf16 bits, for field s_field
     __shared__ int s_tile, s_field;
     BHeader *hdr = reinterpret_cast<BHeader *>(ws);
@@ -336,22 +379,77 @@ __global__ void __launch_bounds__(kThreads, 3) batched_kernel(uint8_t *ws) {
             // run_tile's first __syncthreads orders these writes before any use
         }
         switch (F.k) {
-            case 1: run_tile<1>(P, F, tile.tm, tile.tn, smem, tab); break;
-            case 2: run_tile<2>(P, F, tile.tm, tile.tn, smem, tab); break;
-            case 3: run_tile<3>(P, F, tile.tm, tile.tn, smem, tab); break;
-            case 4: run_tile<4>(P, F, tile.tm, tile.tn, smem, tab); break;
-            case 5: run_tile<5>(P, F, tile.tm, tile.tn, smem, tab); break;
-            case 6: run_tile<6>(P, F, tile.tm, tile.tn, smem, tab); break;
-            case 7: run_tile<7>(P, F, tile.tm, tile.tn, smem, tab); break;
-            default: run_tile<8>(P, F, tile.tm, tile.tn, smem, tab); break;
+            case 1: run_tile_cfg<1>(P.cfg, P, F, tile.tm, tile.tn, smem, tab); break;
+            case 2: run_tile_cfg<2>(P.cfg, P, F, tile.tm, tile.tn, smem, tab); break;
+            case 3: run_tile_cfg<3>(P.cfg, P, F, tile.tm, tile.tn, smem, tab); break;
+            case 4: run_tile_cfg<4>(P.cfg, P, F, tile.tm, tile.tn, smem, tab); break;
+            case 5: run_tile_cfg<5>(P.cfg, P, F, tile.tm, tile.tn, smem, tab); break;
+            case 6: run_tile_cfg<6>(P.cfg, P, F, tile.tm, tile.tn, smem, tab); break;
+            case 7: run_tile_cfg<7>(P.cfg, P, F, tile.tm, tile.tn, smem, tab); break;
+            default: run_tile_cfg<8>(P.cfg, P, F, tile.tm, tile.tn, smem, tab); break;
         }
     }
 }
 
-// Must match TileCfg<k>::BM / BN.
-void tile_shape(uint32_t k, int &bm, int &bn) {
-    bm = k <= 2 ? 64 : 32;
-    bn = k <= 4 ? 32 : 16;
+// Selected configuration per k (process-wide: every device runs the same
+// kernel), -1 = default.
+std::mutex g_tiles_mu;
+int g_tile_choice[kMaxK + 1] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
+
+int tile_choice(uint32_t k) {
+    std::lock_guard<std::mutex> lock(g_tiles_mu);
+    const int c = (k <= kMaxK) ? g_tile_choice[k] : -1;
+    return c < 0 ? 0 : c;
+}
+
+void field_params(const Field &f, BFieldParams &F) {
+    F.p = f.p;
+    F.k = f.k;
+    F.h = f.h;
+    F.m32 = make_mod_small(f.p);
+    F.pf = (float)f.p;
+    F.inv_pf = 1.0f / (float)f.p;
+    F.chunk_k = (int32_t)std::min<int64_t>(f.k_chunk_f32, 1 << 30);
+    for (uint32_t t = 0; t + 1 < f.k; ++t)
+        for (uint32_t c = 0; c < f.k; ++c) F.fold[t * f.k + c] = f.fold[t * f.k + c];
+}
+
+int field_cfg(const Field &f) {
+    const int c = tile_choice(f.k);
+    return f.k_chunk_f32 >= tile_shape_of(f.k, c).bk ? c : 0;
+}
+
+uint64_t tile_cost(const qadic_gemm_desc &d, uint32_t k, int cfg) {
+    const TileShape t = tile_shape_of(k, cfg);
+    return (uint64_t)t.bm * t.bn * (uint64_t)(((d.K + t.bk - 1) / t.bk) * t.bk) * k * k;
+}
+
+// Opt the kernel in to the largest dynamic shared memory any candidate needs.
+int prepare_kernel(size_t smem) {
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] {
+        size_t most = 0;
+        for (uint32_t k = 1; k <= kMaxK; ++k)
+            for (int c = 0; c < num_cfgs(k); ++c) most = std::max(most, tile_smem_bytes(k, c));
+        err = cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)most);
+    });
+    (void)smem;
+    if (err != cudaSuccess)
+        return set_error(QADIC_E_CUDA, "batched smem attribute: %s", cudaGetErrorString(err));
+    return QADIC_OK;
+}
+
+int64_t grid_for(int dev, size_t smem, int64_t ntiles) {
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel, kThreads, smem) !=
+            cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    int64_t grid = (int64_t)sms * per_sm;
+    if (ntiles < grid) grid = std::max<int64_t>(1, ntiles);
+    return grid;
 }
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -377,14 +475,21 @@ int64_t max_tiles(const qadic_gemm_desc *descs, int64_t count) {
 }
 
 // Cached CUDA graphs of {counter reset, persistent kernel}, keyed by the
-// call's exact arguments (descriptors, fields, workspace, stream).
+// call's exact arguments (descriptors, fields, workspace, stream, tile
+// configurations).  A graph replays whatever work list its workspace holds,
+// so each entry keeps the list it was built with, and a hit re-uploads it
+// when another list was written to the same workspace in between.
 struct GraphEntry {
     std::vector<uint8_t> key;
     cudaGraphExec_t exec;
+    std::vector<uint8_t> list;   // the uploaded bytes of the work list
+    uint64_t id;
 };
 std::mutex g_graph_mu;
 std::vector<GraphEntry> g_graphs;
 constexpr size_t kMaxGraphs = 32;
+uint64_t g_next_list_id = 1;
+std::map<void *, uint64_t> g_ws_list;   // workspace -> id of the list it holds
 
 // One non-blocking stream per device, used only to capture graphs.
 cudaStream_t capture_stream(int dev) {
@@ -430,10 +535,18 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
             return set_error(QADIC_E_INVALID, "desc %lld: leading dimension too small",
                              (long long)i);
         const Field &f = *fields[d.field];
-        if (f.k_chunk_f32 < BK)
+        if (f.k_chunk_f32 < kMinBK)
             return set_error(QADIC_E_OVERFLOW, "exact FP32 chunk below one K-block (p=%u k=%u)",
                              f.p, f.k);
     }
+    int cfgs[kMaxFields];
+    size_t smem = 0;
+    for (int32_t i = 0; i < nfields; ++i) {
+        cfgs[i] = field_cfg(*fields[i]);
+        smem = std::max(smem, tile_smem_bytes(fields[i]->k, cfgs[i]));
+    }
+    int st = prepare_kernel(smem);
+    if (st != QADIC_OK) return st;
     const int64_t tile_bound = max_tiles(descs, count);
     const Layout L = layout_for(count, tile_bound);
     if (!workspace || ws_bytes < L.total)
@@ -444,7 +557,7 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
     std::vector<uint8_t> key;
     if (use_graph) {
         key.resize(sizeof(int64_t) + count * sizeof(qadic_gemm_desc) + nfields * sizeof(void *) +
-                   2 * sizeof(void *));
+                   2 * sizeof(void *) + nfields * sizeof(int));
         uint8_t *kp = key.data();
         std::memcpy(kp, &count, sizeof(int64_t));
         kp += sizeof(int64_t);
@@ -455,9 +568,19 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
         std::memcpy(kp, &workspace, sizeof(void *));
         kp += sizeof(void *);
         std::memcpy(kp, &stream, sizeof(void *));
+        kp += sizeof(void *);
+        std::memcpy(kp, cfgs, nfields * sizeof(int));   // the tile configurations in use
         std::lock_guard<std::mutex> lock(g_graph_mu);
         for (auto &g : g_graphs)
             if (g.key == key) {
+                auto it = g_ws_list.find(workspace);
+                if (it == g_ws_list.end() || it->second != g.id) {
+                    if (cudaMemcpyAsync(workspace, g.list.data(), g.list.size(),
+                                        cudaMemcpyHostToDevice, stream) != cudaSuccess)
+                        return set_error(QADIC_E_CUDA, "work list upload: %s",
+                                         cudaGetErrorString(cudaGetLastError()));
+                    g_ws_list[workspace] = g.id;
+                }
                 if (cudaGraphLaunch(g.exec, stream) != cudaSuccess)
                     return set_error(QADIC_E_CUDA, "graph launch: %s",
                                      cudaGetErrorString(cudaGetLastError()));
@@ -471,19 +594,7 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
     std::vector<uint64_t> cost;
     tiles.reserve(tile_bound);
     BFieldParams *fp = reinterpret_cast<BFieldParams *>(host.data() + L.fields_off);
-    for (int32_t i = 0; i < nfields; ++i) {
-        const Field &f = *fields[i];
-        BFieldParams &F = fp[i];
-        F.p = f.p;
-        F.k = f.k;
-        F.h = f.h;
-        F.m32 = make_mod_small(f.p);
-        F.pf = (float)f.p;
-        F.inv_pf = 1.0f / (float)f.p;
-        F.chunk_blocks = (int32_t)std::min<int64_t>(f.k_chunk_f32 / BK, 1 << 20);
-        for (uint32_t t = 0; t + 1 < f.k; ++t)
-            for (uint32_t c = 0; c < f.k; ++c) F.fold[t * f.k + c] = f.fold[t * f.k + c];
-    }
+    for (int32_t i = 0; i < nfields; ++i) field_params(*fields[i], fp[i]);
     BProd *pp = reinterpret_cast<BProd *>(host.data() + L.prods_off);
     for (int64_t i = 0; i < count; ++i) {
         const qadic_gemm_desc &d = descs[i];
@@ -498,13 +609,14 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
         P.ldb = d.ldb;
         P.ldc = d.ldc;
         P.field = d.field;
-        int bm, bn;
+        P.cfg = cfgs[d.field];
         const uint32_t k = fields[d.field]->k;
-        tile_shape(k, bm, bn);
-        for (int tm = 0; tm * bm < d.m; ++tm)
-            for (int tn = 0; tn * bn < d.n; ++tn) {
+        const TileShape ts = tile_shape_of(k, P.cfg);
+        const uint64_t c = tile_cost(d, k, P.cfg);
+        for (int tm = 0; tm * ts.bm < d.m; ++tm)
+            for (int tn = 0; tn * ts.bn < d.n; ++tn) {
                 tiles.push_back(BTile{(int32_t)i, (int16_t)tm, (int16_t)tn});
-                cost.push_back((uint64_t)bm * bn * (uint64_t)((d.K + BK - 1) / BK) * k * k);
+                cost.push_back(c);
             }
     }
     std::vector<int64_t> order(tiles.size());
@@ -524,17 +636,15 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
     const size_t used = L.tiles_off + tiles.size() * sizeof(BTile);
     if (cudaMemcpyAsync(workspace, host.data(), used, cudaMemcpyHostToDevice, stream) != cudaSuccess)
         return set_error(QADIC_E_CUDA, "work list upload: %s", cudaGetErrorString(cudaGetLastError()));
+    {
+        std::lock_guard<std::mutex> lock(g_graph_mu);
+        g_ws_list[workspace] = 0;   // an uncached list: no cached graph owns this workspace
+    }
 
-    int sms = 0, per_sm = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel, kThreads, 0) !=
-            cudaSuccess || per_sm < 1)
-        per_sm = 1;
-    int64_t grid = (int64_t)sms * per_sm;
-    if ((int64_t)tiles.size() < grid) grid = std::max<int64_t>(1, (int64_t)tiles.size());
+    const int64_t grid = grid_for(dev, smem, (int64_t)tiles.size());
 
     if (!use_graph) {
-        batched_kernel<<<(unsigned)grid, kThreads, 0, stream>>>((uint8_t *)workspace);
+        batched_kernel<<<(unsigned)grid, kThreads, smem, stream>>>((uint8_t *)workspace);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return set_error(QADIC_E_CUDA, "batched launch: %s", cudaGetErrorString(e));
         return QADIC_OK;
@@ -550,7 +660,7 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
     if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return set_error(QADIC_E_CUDA, "begin capture: %s", cudaGetErrorString(cudaGetLastError()));
     cudaMemsetAsync(workspace, 0, sizeof(uint32_t), cap);
-    batched_kernel<<<(unsigned)grid, kThreads, 0, cap>>>((uint8_t *)workspace);
+    batched_kernel<<<(unsigned)grid, kThreads, smem, cap>>>((uint8_t *)workspace);
     const cudaError_t le = cudaGetLastError();
     const cudaError_t ce = cudaStreamEndCapture(cap, &graph);
     if (le != cudaSuccess || ce != cudaSuccess) {
@@ -569,8 +679,107 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
         cudaGraphExecDestroy(g_graphs.front().exec);
         g_graphs.erase(g_graphs.begin());
     }
-    g_graphs.push_back(GraphEntry{std::move(key), exec});
+    const uint64_t id = g_next_list_id++;
+    host.resize(used);
+    g_graphs.push_back(GraphEntry{std::move(key), exec, std::move(host), id});
+    g_ws_list[workspace] = id;
     return QADIC_OK;
+}
+
+int batched_tile_configs(uint32_t k, qadic_tile_config *out, int32_t capacity, int32_t *n) {
+    if (k < 1 || k > kMaxK) return set_error(QADIC_E_INVALID, "k outside [1, %u]", kMaxK);
+    if (!n || (capacity > 0 && !out)) return set_error(QADIC_E_INVALID, "NULL output");
+    *n = num_cfgs(k);
+    for (int32_t c = 0; c < std::min<int32_t>(capacity, *n); ++c) {
+        const TileShape t = tile_shape_of(k, c);
+        out[c].bm = t.bm;
+        out[c].bn = t.bn;
+        out[c].bk = t.bk;
+        out[c].smem_bytes = (int32_t)tile_smem_bytes(k, c);
+    }
+    return QADIC_OK;
+}
+
+int batched_select_tiles(uint32_t k, int32_t index) {
+    if (k < 1 || k > kMaxK) return set_error(QADIC_E_INVALID, "k outside [1, %u]", kMaxK);
+    if (index < -1 || index >= num_cfgs(k))
+        return set_error(QADIC_E_INVALID, "configuration %d outside [-1, %d)", index, num_cfgs(k));
+    std::lock_guard<std::mutex> lock(g_tiles_mu);
+    g_tile_choice[k] = index;
+    return QADIC_OK;
+}
+
+int batched_selected_tiles(uint32_t k, int32_t *index) {
+    if (k < 1 || k > kMaxK) return set_error(QADIC_E_INVALID, "k outside [1, %u]", kMaxK);
+    if (!index) return set_error(QADIC_E_INVALID, "NULL output");
+    *index = tile_choice(k);
+    return QADIC_OK;
+}
+
+// For each k present (largest total work first), time every candidate on
+// this batch -- one graph capture as warm-up, then `reps` graph replays
+// between CUDA events -- and keep the fastest before tuning the next k.
+int autotune_batched(const Field *const *fields, int32_t nfields, const qadic_gemm_desc *descs,
+                     int64_t count, void *workspace, size_t ws_bytes, int32_t reps,
+                     int32_t *chosen, cudaStream_t stream) {
+    if (reps < 1 || reps > 1000) return set_error(QADIC_E_INVALID, "reps outside [1, 1000]");
+    if (nfields < 1 || nfields > kMaxFields)
+        return set_error(QADIC_E_INVALID, "nfields must be in [1, %d]", kMaxFields);
+    double work[kMaxK + 1] = {0};
+    for (int64_t i = 0; i < count; ++i) {
+        const qadic_gemm_desc &d = descs[i];
+        if (d.field < 0 || d.field >= nfields || !fields[d.field])
+            return set_error(QADIC_E_INVALID, "desc %lld: field index out of range", (long long)i);
+        const double k = fields[d.field]->k;
+        work[(int)k] += k * k * (double)d.m * d.n * d.K;
+    }
+    std::vector<uint32_t> ks;
+    for (uint32_t k = 1; k <= kMaxK; ++k)
+        if (work[k] > 0) ks.push_back(k);
+    std::stable_sort(ks.begin(), ks.end(), [&](uint32_t a, uint32_t b) { return work[a] > work[b]; });
+    for (uint32_t k = 0; k <= kMaxK; ++k) chosen[k] = -1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return set_error(QADIC_E_CUDA, "event: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    int st = QADIC_OK;
+    for (uint32_t k : ks) {
+        int best = 0;
+        float best_ms = 0.f;
+        bool have = false;
+        for (int c = 0; c < num_cfgs(k) && st == QADIC_OK; ++c) {
+            // a candidate deeper than some field's exact chunk would fall back to 0
+            bool fits = true;
+            for (int32_t i = 0; i < nfields; ++i)
+                if (fields[i]->k == k && fields[i]->k_chunk_f32 < tile_shape_of(k, c).bk) fits = false;
+            if (!fits) continue;
+            batched_select_tiles(k, c);
+            st = launch_batched(fields, nfields, descs, count, workspace, ws_bytes, true, stream);
+            if (st != QADIC_OK) break;
+            cudaEventRecord(e0, stream);
+            for (int32_t r = 0; r < reps && st == QADIC_OK; ++r)
+                st = launch_batched(fields, nfields, descs, count, workspace, ws_bytes, true, stream);
+            cudaEventRecord(e1, stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                st = set_error(QADIC_E_CUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (!have || ms < best_ms) {
+                best = c;
+                best_ms = ms;
+                have = true;
+            }
+        }
+        batched_select_tiles(k, best);
+        chosen[k] = best;
+        if (st != QADIC_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
 }
 
 }  // namespace qadic
@@ -635,9 +844,17 @@ int launch_batched_noalloc(const Field *const *fields, int32_t nfields,
         if (d.lda < d.K || d.ldb < d.n || d.ldc < d.n)
             return set_error(QADIC_E_INVALID, "desc %lld: leading dimension too small",
                              (long long)i);
-        if (fields[d.field]->k_chunk_f32 < BK)
+        if (fields[d.field]->k_chunk_f32 < kMinBK)
             return set_error(QADIC_E_OVERFLOW, "exact FP32 chunk below one K-block");
     }
+    int cfgs[kMaxFields];
+    size_t smem = 0;
+    for (int32_t i = 0; i < nfields; ++i) {
+        cfgs[i] = field_cfg(*fields[i]);
+        smem = std::max(smem, tile_smem_bytes(fields[i]->k, cfgs[i]));
+    }
+    int st0 = prepare_kernel(smem);
+    if (st0 != QADIC_OK) return st0;
     const Layout L = layout_for(count, max_tiles(descs, count));
     if (L.total > kNoAllocScratchBytes)
         return set_error(QADIC_E_INVALID,
@@ -653,19 +870,7 @@ int launch_batched_noalloc(const Field *const *fields, int32_t nfields,
     uint8_t *host = g_noalloc_host;
     std::memset(host, 0, L.tiles_off);
     BFieldParams *fp = reinterpret_cast<BFieldParams *>(host + L.fields_off);
-    for (int32_t i = 0; i < nfields; ++i) {
-        const Field &f = *fields[i];
-        BFieldParams &F = fp[i];
-        F.p = f.p;
-        F.k = f.k;
-        F.h = f.h;
-        F.m32 = make_mod_small(f.p);
-        F.pf = (float)f.p;
-        F.inv_pf = 1.0f / (float)f.p;
-        F.chunk_blocks = (int32_t)std::min<int64_t>(f.k_chunk_f32 / BK, 1 << 20);
-        for (uint32_t t = 0; t + 1 < f.k; ++t)
-            for (uint32_t c = 0; c < f.k; ++c) F.fold[t * f.k + c] = f.fold[t * f.k + c];
-    }
+    for (int32_t i = 0; i < nfields; ++i) field_params(*fields[i], fp[i]);
     BProd *pp = reinterpret_cast<BProd *>(host + L.prods_off);
     BTile *tp = reinterpret_cast<BTile *>(host + L.tiles_off);
     int64_t nt = 0;
@@ -682,18 +887,15 @@ int launch_batched_noalloc(const Field *const *fields, int32_t nfields,
         P.ldb = d.ldb;
         P.ldc = d.ldc;
         P.field = d.field;
-        int bm, bn;
-        tile_shape(fields[d.field]->k, bm, bn);
-        for (int tm = 0; tm * bm < d.m; ++tm)
-            for (int tn = 0; tn * bn < d.n; ++tn) tp[nt++] = BTile{(int32_t)i, (int16_t)tm, (int16_t)tn};
+        P.cfg = cfgs[d.field];
+        const TileShape ts = tile_shape_of(fields[d.field]->k, P.cfg);
+        for (int tm = 0; tm * ts.bm < d.m; ++tm)
+            for (int tn = 0; tn * ts.bn < d.n; ++tn) tp[nt++] = BTile{(int32_t)i, (int16_t)tm, (int16_t)tn};
     }
     // largest tiles first; std::sort works in place
     auto cost = [&](const BTile &t) {
         const qadic_gemm_desc &d = descs[t.prod];
-        const uint64_t k = fields[d.field]->k;
-        int bm, bn;
-        tile_shape((uint32_t)k, bm, bn);
-        return (uint64_t)bm * bn * (uint64_t)((d.K + BK - 1) / BK) * k * k;
+        return tile_cost(d, fields[d.field]->k, cfgs[d.field]);
     };
     std::sort(tp, tp + nt, [&](const BTile &a, const BTile &b) {
         const uint64_t ca = cost(a), cb = cost(b);
@@ -714,14 +916,8 @@ int launch_batched_noalloc(const Field *const *fields, int32_t nfields,
     // so the host array may be rewritten by the next call.
     if (cudaMemcpyAsync(dptr, host, used, cudaMemcpyHostToDevice, stream) != cudaSuccess)
         return set_error(QADIC_E_CUDA, "work list upload: %s", cudaGetErrorString(cudaGetLastError()));
-    int sms = 0, per_sm = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel, kThreads, 0) !=
-            cudaSuccess || per_sm < 1)
-        per_sm = 1;
-    int64_t grid = (int64_t)sms * per_sm;
-    if (nt < grid) grid = std::max<int64_t>(1, nt);
-    batched_kernel<<<(unsigned)grid, kThreads, 0, stream>>>((uint8_t *)dptr);
+    const int64_t grid = grid_for(dev, smem, nt);
+    batched_kernel<<<(unsigned)grid, kThreads, smem, stream>>>((uint8_t *)dptr);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(QADIC_E_CUDA, "batched launch: %s", cudaGetErrorString(e));
     return QADIC_OK;
@@ -744,4 +940,33 @@ extern "C" int qadic_batched_gemm_noalloc(const qadic_field *const *fields, int3
         fs[i] = field_of(fields[i]);
     }
     return launch_batched_noalloc(fs, nfields, descs, count, (cudaStream_t)stream);
+}
+
+extern "C" int qadic_batched_tile_configs(uint32_t k, qadic_tile_config *out, int32_t capacity,
+                                          int32_t *count) {
+    return batched_tile_configs(k, out, capacity, count);
+}
+
+extern "C" int qadic_batched_select_tiles(uint32_t k, int32_t index) {
+    return batched_select_tiles(k, index);
+}
+
+extern "C" int qadic_batched_selected_tiles(uint32_t k, int32_t *index) {
+    return batched_selected_tiles(k, index);
+}
+
+extern "C" int qadic_batched_autotune(const qadic_field *const *fields, int32_t nfields,
+                                      const qadic_gemm_desc *descs, int64_t count, void *workspace,
+                                      size_t ws_bytes, int32_t reps, int32_t *chosen,
+                                      void *stream) {
+    if (count < 1) return set_error(QADIC_E_INVALID, "nothing to tune");
+    if (!fields || !descs || !chosen) return set_error(QADIC_E_INVALID, "NULL argument");
+    if (nfields < 1 || nfields > 64) return set_error(QADIC_E_INVALID, "nfields outside [1, 64]");
+    const Field *fs[64];
+    for (int32_t i = 0; i < nfields; ++i) {
+        if (!fields[i]) return set_error(QADIC_E_INVALID, "field %d is NULL", i);
+        fs[i] = field_of(fields[i]);
+    }
+    return autotune_batched(fs, nfields, descs, count, workspace, ws_bytes, reps, chosen,
+                            (cudaStream_t)stream);
 }

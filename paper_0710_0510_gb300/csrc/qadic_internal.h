@@ -103,4 +103,11 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
                    int64_t count, void *workspace, size_t ws_bytes, bool use_graph,
                    cudaStream_t stream);
 
+int batched_tile_configs(uint32_t k, qadic_tile_config *out, int32_t capacity, int32_t *n);
+int batched_select_tiles(uint32_t k, int32_t index);
+int batched_selected_tiles(uint32_t k, int32_t *index);
+int autotune_batched(const Field *const *fields, int32_t nfields, const qadic_gemm_desc *descs,
+                     int64_t count, void *workspace, size_t ws_bytes, int32_t reps,
+                     int32_t *chosen, cudaStream_t stream);
+
 }  // namespace qadic

@@ -205,6 +205,27 @@ def test_polymul_fqt_rejections():
     assert L.qadic_polymul_fqt(3, 1 << 20, 0, a, a, a, 4, 0, None) == q.E_UNSUPPORTED
 
 
+def test_batched_tile_table_and_selection():
+    for k in range(1, 9):
+        cfgs = q.batched_tile_configs(k)
+        assert len(cfgs) >= 3 and q.batched_selected_tiles(k) == 0
+        for bm, bn, bk, smem in cfgs:
+            assert bm % 32 == 0 and bn % 16 == 0 and bk % 32 == 0
+            assert smem == (k * bm * (bk + 8) + k * bk * (bn + 8)) * 2
+            assert smem <= 227 * 1024 // 3           # three CTAs per SM
+        assert len(set(cfgs)) == len(cfgs)          # no duplicate candidates
+    L = q.lib()
+    assert L.qadic_batched_select_tiles(0, 0) == q.E_INVALID
+    assert L.qadic_batched_select_tiles(9, 0) == q.E_INVALID
+    assert L.qadic_batched_select_tiles(2, 4) == q.E_INVALID
+    assert L.qadic_batched_select_tiles(5, 3) == q.E_INVALID
+    assert L.qadic_batched_select_tiles(2, -2) == q.E_INVALID
+    q.batched_select_tiles(2, 3)
+    assert q.batched_selected_tiles(2) == 3
+    q.batched_select_tiles(2, -1)
+    assert q.batched_selected_tiles(2) == 0
+
+
 def test_zero_counts_are_noops():
     L = q.lib()
     assert L.qadic_redq(7, 10, 5, None, None, 0, 3, None) == q.OK

@@ -154,3 +154,79 @@ def test_batched_rejects_bad_descriptors(torch):
     with pytest.raises(q.QadicError) as e:
         q.batched_gemm([f], [good], ws[:64])
     assert e.value.status == q.E_NOMEM
+
+
+# ------------------------------------------------- tile configurations ----
+
+@pytest.fixture
+def restore_tiles():
+    yield
+    for k in range(1, 9):
+        q.batched_select_tiles(k, -1)
+
+
+@pytest.mark.parametrize("pk", [(101, 1), (31, 2), (3, 3), (7, 4), (5, 5), (2, 6), (2, 8)])
+def test_batched_every_tile_configuration(torch, orc, restore_tiles, pk):
+    """Each (BM, BN, BK) candidate of the autotuner computes the same exact
+    products: ragged shapes, K across exact-chunk boundaries."""
+    f = q.Field(*pk)
+    shapes = [(1, 1, 1), (33, 47, 95), (64, 64, 64), (100, 3, 250), (1, 70, 129), (77, 65, 640)]
+    for c in range(len(q.batched_tile_configs(f.k))):
+        q.batched_select_tiles(f.k, c)
+        bt = Batch(torch, [f], shapes, [0] * len(shapes), seed=pk[0] + c)
+        bt.run(graph=bool(c % 2))
+        for i in range(len(shapes)):
+            assert np.array_equal(bt.result(i), bt.expected(orc, i)), (pk, c, shapes[i])
+
+
+def test_batched_p251_chunks_every_configuration(torch, orc, restore_tiles):
+    """GF(251^2) (exact chunk 536 = 16 blocks of 32 or 8 of 64), all-max
+    inputs, K = 2000, under every configuration for k = 2."""
+    f = q.Field(251, 2)
+    for c in range(len(q.batched_tile_configs(2))):
+        q.batched_select_tiles(2, c)
+        bt = Batch(torch, [f], [(64, 64, 2000), (50, 70, 1100)], [0, 0], seed=2)
+        bt.A[0][:] = 126
+        bt.B[0][:] = 126
+        bt.dA[: bt.A[0].size] = torch.from_numpy(bt.A[0].ravel()).cuda()
+        bt.dB[: bt.B[0].size] = torch.from_numpy(bt.B[0].ravel()).cuda()
+        bt.run()
+        for i in range(2):
+            assert np.array_equal(bt.result(i), bt.expected(orc, i)), c
+
+
+def test_graph_replay_after_another_list_in_the_same_workspace(torch, orc):
+    """graph(X), graph(Y), graph(X) on one workspace: the third call replays
+    X's cached graph and must first restore X's work list."""
+    fields = mixed_fields()
+    dims, fidx = W.batched_shapes(30, salt=4)
+    shapes = [tuple(int(x) for x in d) for d in dims]
+    x = Batch(torch, fields, shapes, [int(v) for v in fidx], seed=11)
+    y = Batch(torch, fields, shapes[::-1], [int(v) for v in fidx][::-1], seed=12)
+    ws = torch.empty(max(x.ws.numel(), y.ws.numel()), dtype=torch.uint8, device="cuda")
+    x.ws = y.ws = ws
+    x.run(graph=True)
+    y.run(graph=True)
+    x.dC.zero_()
+    x.run(graph=True)
+    for i in range(len(shapes)):
+        assert np.array_equal(x.result(i), x.expected(orc, i)), i
+        assert np.array_equal(y.result(i), y.expected(orc, i)), i
+
+
+def test_autotune_selects_measured_configurations(torch, orc, restore_tiles):
+    fields = mixed_fields()
+    dims, fidx = W.batched_shapes(200, salt=6)
+    shapes = [tuple(int(v) for v in d) for d in dims]
+    bt = Batch(torch, fields, shapes, [int(v) for v in fidx], seed=13)
+    chosen = q.batched_autotune(fields, bt.descs, bt.ws, reps=2)
+    assert set(chosen) == {f.k for f in fields}
+    for k, c in chosen.items():
+        assert 0 <= c < len(q.batched_tile_configs(k))
+        assert q.batched_selected_tiles(k) == c
+    for i in range(len(shapes)):
+        assert np.array_equal(bt.result(i), bt.expected(orc, i)), i
+    bt.dC.zero_()
+    bt.run(graph=True)
+    for i in range(0, len(shapes), 7):
+        assert np.array_equal(bt.result(i), bt.expected(orc, i)), i
