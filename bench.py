@@ -230,6 +230,74 @@ def bench_plane(args, torch, q, W, dist, p=101, n=4096, name="plane"):
     return f, A, B, C, res
 
 
+def bench_fold(args, torch, q, W, f, A, B, n, C_plane, steps=20):
+    """Fold-before form on the same inputs: pack A (OPERAND_A) and B into its
+    multiplication matrices (OPERAND_B_FOLD), one prime-field tensor-core
+    GEMM over k K with k accumulators; bit-exact against the plane form."""
+    k = f.k
+    dA = torch.from_numpy(A).cuda()
+    dB = torch.from_numpy(B).cuda()
+    opA = torch.empty((k, n, n), dtype=torch.bfloat16, device="cuda")
+    opB = torch.empty((k, k * q.fold_n_pad(n), n), dtype=torch.bfloat16, device="cuda")
+    C = torch.empty((k, n, n), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(kev):
+        f.pack(q.FMT_INT8_PLANES, dA, n, n, q.FMT_OPERAND_A, out=opA)
+        f.pack(q.FMT_INT8_PLANES, dB, n, n, q.FMT_OPERAND_B_FOLD, out=opB, ld_out=n)
+        if kev is not None:
+            a, b = ev_pair(torch)
+            a.record(stream)
+        f.gemm(q.PATH_FOLD, opA, opB, n, n, n, C=C, ldb=n)
+        if kev is not None:
+            b.record(stream)
+            kev.append((a, b))
+
+    total, kms = time_steps(torch, step, steps, 3, None, kernel_events=True)
+    ms = total / steps
+    pk = peaks()
+    achieved = 2.0 * k * k * n ** 3 / (kms * 1e-3) / 1e12
+    return {"value": 2.0 * n ** 3 / (ms * 1e-3) / 1e9, "unit": "field Gop/s", "ms_per_step": ms,
+            "kernel_ms": kms, "bitexact_vs_plane": bool(torch.equal(C, C_plane)),
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": pk["bf16_sustained"],
+                         "unit": "TFLOP/s", "frac": achieved / pk["bf16_sustained"],
+                         "traffic": None, "kernel": "gemm_fold_tc_kernel<2,256,2>"}}
+
+
+def bench_karatsuba(args, torch, q, W, f, A, B, n, C_plane, steps=20):
+    """Karatsuba form (k = 2) on the same inputs: three bf16 planes per
+    operand (c_0, c_1, c_0 + c_1), three plane products on the tensor cores;
+    bit-exact against the plane form."""
+    dA = torch.from_numpy(A).cuda()
+    dB = torch.from_numpy(B).cuda()
+    opA = torch.empty((3, n, n), dtype=torch.bfloat16, device="cuda")
+    opB = torch.empty((3, n, n), dtype=torch.bfloat16, device="cuda")
+    C = torch.empty((2, n, n), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(kev):
+        f.pack(q.FMT_INT8_PLANES, dA, n, n, q.FMT_OPERAND_A_KARA, out=opA)
+        f.pack(q.FMT_INT8_PLANES, dB, n, n, q.FMT_OPERAND_B_KARA, out=opB)
+        if kev is not None:
+            a, b = ev_pair(torch)
+            a.record(stream)
+        f.gemm(q.PATH_KARATSUBA, opA, opB, n, n, n, C=C)
+        if kev is not None:
+            b.record(stream)
+            kev.append((a, b))
+
+    total, kms = time_steps(torch, step, steps, 3, None, kernel_events=True)
+    ms = total / steps
+    pk = peaks()
+    achieved = 2.0 * 3 * n ** 3 / (kms * 1e-3) / 1e12   # three plane products
+    return {"value": 2.0 * n ** 3 / (ms * 1e-3) / 1e9, "unit": "field Gop/s", "ms_per_step": ms,
+            "kernel_ms": kms, "bitexact_vs_plane": bool(torch.equal(C, C_plane)),
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": pk["bf16_sustained"],
+                         "unit": "TFLOP/s", "frac": achieved / pk["bf16_sustained"],
+                         "traffic": None, "kernel": "gemm_fold_tc_kernel<3,128,2,karatsuba>",
+                         "flop_count": "3 plane products (2 * 3 * n^3)"}}
+
+
 def bench_fp64(args, torch, q, W, f, A, B, n, reps=2):
     """FP64 q-adic form on the same inputs (pack + FP64 GEMM with REDQ)."""
     k = f.k
@@ -307,8 +375,36 @@ def bench_polymul(args, torch, q, W, count=65536, steps=50):
 
     total, _ = time_steps(torch, step, steps, 3, None)
     ms = total / steps
+    # labelled scaling run: 2^24 pairs (252 MB moved) for the HBM fraction
+    big = 1 << 24
+    ba, bb = W.polymul_pairs(big, 7, 4, salt=1)
+    dba, dbb = torch.from_numpy(ba).cuda(), torch.from_numpy(bb).cuda()
+    bout = torch.empty((big, 7), dtype=torch.uint8, device="cuda")
+
+    def step_big(kev):
+        q.polymul_batched(7, 4, dba, dbb, out=bout)
+
+    tb, _ = time_steps(torch, step_big, 10, 3, None)
+    msb = tb / 10
+    gbs = 15.0 * big / (msb * 1e-3) / 1e9
+    pk = peaks()
+
+    def step_big_int(kev):
+        q.polymul_batched(7, 4, dba, dbb, out=bout, int_words=True)
+
+    ti, _ = time_steps(torch, step_big_int, 10, 3, None)
+    msi = ti / 10
+    gbi = 15.0 * big / (msi * 1e-3) / 1e9
+    del dba, dbb, bout
     return a, b, out, {"value": count / (ms * 1e-3), "unit": "products/s", "us_per_batch": ms * 1e3,
-                       "residues_per_s": 7 * count / (ms * 1e-3)}
+                       "residues_per_s": 7 * count / (ms * 1e-3),
+                       "scaling_2_24_pairs": {
+                           "value": big / (msb * 1e-3), "unit": "products/s", "ms": msb,
+                           "roofline": {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"],
+                                        "unit": "GB/s", "frac": gbs / pk["hbm_gbs"],
+                                        "traffic": None, "bytes_per_pair": 15},
+                           "int64_words": {"value": big / (msi * 1e-3), "ms": msi,
+                                           "GB/s": gbi, "frac": gbi / pk["hbm_gbs"]}}}
 
 
 FQT_P, FQT_N, FQT_COUNT = 3, 500, 16384
@@ -521,6 +617,78 @@ def cpu_baseline_plane(p, n, target_s=12.0):
                                         f"({spent:.1f} s)"}
 
 
+def cpu_baselines_all():
+    """The oracle as it stands, on bounded samples of every workload, on all
+    host cores (and on one core for the polynomial and GF(3^3) workloads).
+    Rates are scaled to each workload's unit by the work the sample did."""
+    import numpy as np
+    import oracle
+    from paper_0710_0510_gb300 import workloads as W
+    oracle.build()
+    cores = oracle.num_threads()
+    out = {"cores": cores, "kind": "oracle"}
+
+    def timed(fn):
+        t0 = time.perf_counter()
+        fn()
+        return time.perf_counter() - t0
+
+    a, b = W.polymul_pairs(65536, 7, 4)
+    for th, tag in ((cores, "all_cores"), (1, "one_core")):
+        oracle.set_threads(th)
+        dt = timed(lambda: oracle.polymul(7, a, b))
+        out[f"polymul_65536_z7_{tag}"] = {"value": 65536 / dt, "unit": "products/s",
+                                          "sample": "all 65,536 pairs", "s": dt}
+    oracle.set_threads(cores)
+    poly27 = oracle.smallest_irreducible(3, 3)
+    T = oracle.antilog(3, poly27)
+    A = T[W.log_matrix(1024, 1024, 27, index=1, salt=0).astype(np.int64)]
+    B = T[W.log_matrix(1024, 1024, 27, index=1, salt=1).astype(np.int64)]
+    for th, tag, rows in ((cores, "all_cores", 1024), (1, "one_core", 64)):
+        oracle.set_threads(th)
+        dt = timed(lambda: oracle.gemm(3, poly27, A[:rows], B))
+        out[f"gf27_n1024_{tag}"] = {"value": 2.0 * rows * 1024 * 1024 / dt / 1e9,
+                                    "unit": "field Gop/s", "s": dt,
+                                    "sample": f"{rows} of 1024 output rows"}
+    oracle.set_threads(cores)
+    # batched: a sample of the 4096 products (same generator as the GPU run)
+    dims, fidx = W.batched_shapes(4096, index=3, salt=0)
+    fields = [(2, oracle.smallest_irreducible(2, 8)), (7, oracle.smallest_irreducible(7, 4)),
+              (31, oracle.smallest_irreducible(31, 2))]
+    rng = np.random.default_rng(1)
+    ops, spent = 0.0, 0.0
+    for i in range(0, 4096, 32):
+        m, n, K = (int(x) for x in dims[i])
+        p, poly = fields[int(fidx[i])]
+        k = len(poly) - 1
+        Ai = rng.integers(0, p, (m, K, k))
+        Bi = rng.integers(0, p, (K, n, k))
+        spent += timed(lambda: oracle.gemm(p, poly, Ai, Bi))
+        ops += 2.0 * m * n * K
+    out["batched_4096"] = {"value": ops / spent / 1e9, "unit": "field Gop/s", "s": spent,
+                           "sample": "128 of the 4096 products (every 32nd)"}
+    # GF(251^2) n = 16384: 8 output rows, extrapolated by the op count
+    h = 125
+    poly251 = oracle.smallest_irreducible(251, 2)
+    B = np.ascontiguousarray(np.transpose(W.centred_planes(2, 16384, 16384, h, index=2, salt=1),
+                                          (1, 2, 0)))
+    A = np.ascontiguousarray(np.transpose(W.centred_planes(2, 8, 16384, h, index=2, salt=0),
+                                          (1, 2, 0)))
+    dt = timed(lambda: oracle.gemm(251, poly251, A, B))
+    out["gf251_2_n16384"] = {"value": 2.0 * 8 * 16384 * 16384 / dt / 1e9, "unit": "field Gop/s",
+                             "s": dt, "sample": "8 of 16384 output rows (extrapolated)"}
+    del A, B
+    w = W.redq_words(1 << 24, 5, 10)
+    dt = timed(lambda: oracle.redq(7, 1024, 4, w))
+    out["redq_2_24_words"] = {"value": 5.0 * (1 << 24) / dt, "unit": "residues/s", "s": dt,
+                              "sample": "2^24 of the 2^28 words"}
+    pa, pb = W.polylong_pairs(1024, FQT_N, FQT_P)
+    dt = timed(lambda: oracle.polymul_long(FQT_P, pa, pb))
+    out["polymul_long_p3_n500"] = {"value": 1024 / dt, "unit": "products/s", "s": dt,
+                                   "sample": "1024 of the 16384 pairs"}
+    return out
+
+
 def run_reference(args):
     rank, world, dist = 0, 1, None
     if int(os.environ.get("WORLD_SIZE", "1")) > 1:
@@ -587,6 +755,8 @@ def main():
                 fp["bitexact_vs_plane"] = bool(torch.equal(C64, C))
                 extras["fp64_qadic"] = fp
                 extras["plane_over_fp64"] = res["value"] / fp["value"]
+                extras["fold_before"] = bench_fold(args, torch, q, W, f, A, B, n, C)
+                extras["karatsuba"] = bench_karatsuba(args, torch, q, W, f, A, B, n, C)
                 hC, e2e = e2e_plane(args, torch, q, W, f, A, B, n)
                 e2e["bitexact"] = bool(torch.equal(hC, C.cpu()))
                 line["e2e"] = e2e
@@ -605,6 +775,7 @@ def main():
                          "ms_per_step": r["us_per_batch"] / 1e3, "dtype": "f64 product, u64 REDQ",
                          "gpu_launches": 50})
             line["config"] = {"workload": "65,536 pairs of degree-3 polynomials over Z/7, q=2^8"}
+            extras["scaling_2_24_pairs"] = r["scaling_2_24_pairs"]
         elif args.workload == "fqt":
             r = bench_fqt(args, torch, q, W)
             line.update({"value": r["value"] * world, "unit": "products/s", "ms_per_step": r["ms"],
@@ -665,6 +836,7 @@ def main():
     if rank == 0:
         if args.workload == "plane" and args.extras == "all":
             line["cpu_baseline"] = cpu_baseline_plane(101, line["config"]["n"])
+            line["cpu_baselines_all"] = cpu_baselines_all()
         line.update(extras)
         print(json.dumps(line))
     if dist is not None:

@@ -60,13 +60,19 @@ typedef enum {
     QADIC_FMT_INT8_PLANES = 2,/* k planes of int8 coefficients, any representative mod p */
     QADIC_FMT_QADIC_F64 = 3,  /* one double per element: sum_i c_i q^i, c_i in [0, p-1] (Eq. 1) */
     QADIC_FMT_OPERAND_A = 4,  /* k planes of bf16 centred coefficients, rows x cols (K contiguous) */
-    QADIC_FMT_OPERAND_B = 5   /* k planes of bf16 centred coefficients, TRANSPOSED: cols x rows */
+    QADIC_FMT_OPERAND_B = 5,  /* k planes of bf16 centred coefficients, TRANSPOSED: cols x rows */
+    QADIC_FMT_OPERAND_B_FOLD = 6,/* k planes i, each k blocks j of n_pad rows: plane j of B X^i mod P,
+                                    TRANSPOSED (K contiguous); n_pad = cols rounded up to 256 */
+    QADIC_FMT_OPERAND_A_KARA = 7,/* k = 2: 3 bf16 planes c_0, c_1, (c_0 + c_1) mod p, centred, rows x cols */
+    QADIC_FMT_OPERAND_B_KARA = 8 /* k = 2: the same 3 planes, TRANSPOSED: cols x rows */
 } qadic_format;
 
 /* Contraction forms of qadic_gemm. */
 typedef enum {
     QADIC_PATH_FP64_QADIC = 0, /* FP64 q-adic GEMM, REDQ after every n_q-product K-block (Alg. 4) */
-    QADIC_PATH_PLANES = 1      /* k x k coefficient-plane tensor-core GEMMs + fused mod-p / mod-P epilogue */
+    QADIC_PATH_PLANES = 1,     /* k x k coefficient-plane tensor-core GEMMs + fused mod-p / mod-P epilogue */
+    QADIC_PATH_FOLD = 2,       /* fold-before: B's multiplication matrices, one prime-field tensor-core GEMM */
+    QADIC_PATH_KARATSUBA = 3   /* k = 2: three plane products (Karatsuba) on the tensor cores */
 } qadic_path;
 
 /* Field description returned by qadic_field_info. */
@@ -131,9 +137,19 @@ int qadic_field_info(const qadic_field *field, qadic_info *out);
  * matrix from in_fmt to out_fmt.
  *   in, ld_in    input in in_fmt (element stride per row = ld_in elements)
  *   out, ld_out  output in out_fmt; for QADIC_FMT_OPERAND_B the output is the
- *                transpose (cols x rows, ld_out >= rows)
- * Supported pairs: LOG -> QADIC_F64 | OPERAND_A | OPERAND_B | COEFF_U8;
- * COEFF_U8 or INT8_PLANES -> QADIC_F64 | OPERAND_A | OPERAND_B.
+ *                transpose (cols x rows, ld_out >= rows); for
+ *                QADIC_FMT_OPERAND_B_FOLD (a K x n matrix B: rows = K,
+ *                cols = n) it is k planes i of k * n_pad rows of ld_out
+ *                elements, n_pad = (n + 255) / 256 * 256: row j * n_pad + c
+ *                of plane i holds coefficient j of B[:, c] * X^i mod P,
+ *                centred, with zero rows for c >= n (the matrix b -> b X^i
+ *                mod P of Thm. 3's fold applied before the product)
+ * QADIC_FMT_OPERAND_A_KARA / _B_KARA (k = 2) write three planes like
+ * OPERAND_A / OPERAND_B: c_0, c_1 and (c_0 + c_1) mod p, centred.
+ * Supported pairs: LOG -> QADIC_F64 | OPERAND_A | OPERAND_B | OPERAND_B_FOLD |
+ * OPERAND_A_KARA | OPERAND_B_KARA | COEFF_U8; COEFF_U8 or INT8_PLANES ->
+ * QADIC_F64 | OPERAND_A | OPERAND_B | OPERAND_B_FOLD | OPERAND_A_KARA |
+ * OPERAND_B_KARA.
  * Errors: QADIC_E_INVALID (format pair, ld < cols, NULL), QADIC_E_OVERFLOW
  * (QADIC_F64 requested but Eq. 2 has no q with n_q >= 1).
  * OPERAND formats need ld_out a multiple of 8 and 16-byte aligned bases. */
@@ -152,6 +168,18 @@ int qadic_pack(const qadic_field *field, int in_fmt, const void *in, int64_t row
  *   (Eq. 1 coefficientwise) are accumulated exactly on the tensor cores in
  *   K-chunks of at most k_chunk_f32, reduced mod p, and folded mod P with
  *   X^t mod P in the epilogue.  lda, ldb multiples of 8.
+ * QADIC_PATH_FOLD: A is OPERAND_A, B is OPERAND_B_FOLD (ldb >= K, multiple
+ *   of 8).  out_j = sum_i A_i M_ij(B) with M_ij(B) plane j of B X^i mod P:
+ *   the reduction mod P happens before the contraction (the same map Thm. 3
+ *   tabulates after it), which is one prime-field GEMM over k K with the k
+ *   output planes side by side; one exact FP32 accumulator per plane i,
+ *   reduced mod p in the epilogue.  Any k from 1 to 8 (k = 1: GF(p)).
+ * QADIC_PATH_KARATSUBA (k = 2): A is OPERAND_A_KARA (lda), B is
+ *   OPERAND_B_KARA (ldb).  Karatsuba's identity on the coefficient planes:
+ *   D_0 = A_0 B_0, D_2 = A_1 B_1, D_m = (A_0 + A_1)(B_0 + B_1), so
+ *   C_1 = D_m - D_0 - D_2 -- three plane products instead of four; each in
+ *   its own exact FP32 accumulator, combined and folded with X^2 mod P in
+ *   the epilogue.
  * C: k planes of uint8 in [0, p-1], m x n (ldc).
  * workspace/ws_bytes: unused by these kernels (pass NULL, 0).
  * Errors: QADIC_E_INVALID, QADIC_E_OVERFLOW (FP64 path with n_q = 0),
@@ -248,8 +276,11 @@ int qadic_polymul_fqt(uint32_t p, uint32_t N, uint32_t d, const uint8_t *a, cons
  * 64-bit machine words).  With QADIC_POLYMUL_PLAIN_F64 the product is the
  * single-rounded FP64 product and Eq. 2 (m = 53) must hold, else
  * QADIC_E_OVERFLOW.  Otherwise the product is made exact with an FMA
- * error term (hi + lo), which needs (2k-1) log2 q <= 63. */
+ * error term (hi + lo), which needs (2k-1) log2 q <= 63 and k log2 q <= 53.
+ * With QADIC_POLYMUL_INT_WORDS the packed words are multiplied as 64-bit
+ * integers instead (exact while (2k-1) log2 q <= 63). */
 #define QADIC_POLYMUL_PLAIN_F64 0x1u
+#define QADIC_POLYMUL_INT_WORDS 0x2u
 int qadic_polymul_batched(uint32_t p, uint32_t k, const uint8_t *a, const uint8_t *b, uint8_t *out,
                           int64_t count, uint32_t flags, void *stream);
 

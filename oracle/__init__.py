@@ -54,6 +54,7 @@ def _c():
             u32, u64, i64 = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64
             sig = {
                 "or_num_threads": (ctypes.c_int, []),
+                "or_set_threads": (None, [ctypes.c_int]),
                 "or_is_prime": (ctypes.c_int, [u32]),
                 "or_irreducible": (ctypes.c_int, [u32, u32, u32p]),
                 "or_smallest_irreducible": (ctypes.c_int, [u32, u32, u32p]),
@@ -92,6 +93,11 @@ def _i32(a) -> np.ndarray:
 
 def num_threads() -> int:
     return int(_c().or_num_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads used by the OpenMP loops from now on (CPU timing runs)."""
+    _c().or_set_threads(int(n))
 
 
 # ---------------------------------------------------------------- field ----

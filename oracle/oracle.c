@@ -54,6 +54,15 @@ int or_num_threads(void) {
 #endif
 }
 
+/* Threads for the OpenMP loops that follow (timing runs only). */
+void or_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* Trial division. */
 int or_is_prime(uint32_t p) {
     if (p < 2) return 0;

@@ -17,17 +17,24 @@ from . import build as _build
 OK, E_INVALID, E_NOT_PRIME, E_REDUCIBLE, E_OVERFLOW, E_UNSUPPORTED, E_CUDA, E_DEVICE_TIMEOUT, \
     E_NOMEM = range(9)
 # qadic_format
-FMT_LOG, FMT_COEFF_U8, FMT_INT8_PLANES, FMT_QADIC_F64, FMT_OPERAND_A, FMT_OPERAND_B = range(6)
+FMT_LOG, FMT_COEFF_U8, FMT_INT8_PLANES, FMT_QADIC_F64, FMT_OPERAND_A, FMT_OPERAND_B, \
+    FMT_OPERAND_B_FOLD, FMT_OPERAND_A_KARA, FMT_OPERAND_B_KARA = range(9)
 # qadic_path
-PATH_FP64_QADIC, PATH_PLANES = 0, 1
+PATH_FP64_QADIC, PATH_PLANES, PATH_FOLD, PATH_KARATSUBA = 0, 1, 2, 3
 REDQ_INT_FLOOR = 0x100
 POLYMUL_PLAIN_F64 = 0x1
+POLYMUL_INT_WORDS = 0x2
 BATCHED_GRAPH = 0x1
 FIELD_HOST_ONLY = 0x1
 FQT_INT_WORDS = 0x1
 
 _lock = threading.Lock()
 _lib = None
+
+
+def fold_n_pad(n: int) -> int:
+    """Rows of one output block in a FMT_OPERAND_B_FOLD plane."""
+    return (n + 255) // 256 * 256
 
 
 class QadicError(RuntimeError):
@@ -217,12 +224,22 @@ class Field:
                 out = torch.empty((self.k, cols, rows), dtype=torch.bfloat16, device=x.device)
             elif out_fmt == FMT_COEFF_U8:
                 out = torch.empty((self.k, rows, cols), dtype=torch.uint8, device=x.device)
+            elif out_fmt == FMT_OPERAND_A_KARA:
+                out = torch.empty((3, rows, cols), dtype=torch.bfloat16, device=x.device)
+            elif out_fmt == FMT_OPERAND_B_KARA:
+                out = torch.empty((3, cols, rows), dtype=torch.bfloat16, device=x.device)
+            elif out_fmt == FMT_OPERAND_B_FOLD:
+                out = torch.empty((self.k, self.k * fold_n_pad(cols), (rows + 7) // 8 * 8),
+                                  dtype=torch.bfloat16, device=x.device)
             else:
                 raise ValueError("unsupported output format")
         if ld_in is None:
             ld_in = cols
         if ld_out is None:
-            ld_out = rows if out_fmt == FMT_OPERAND_B else cols
+            if out_fmt == FMT_OPERAND_B_FOLD:
+                ld_out = out.shape[-1]
+            else:
+                ld_out = rows if out_fmt in (FMT_OPERAND_B, FMT_OPERAND_B_KARA) else cols
         _check(lib().qadic_pack(self._h, in_fmt, _ptr(x), rows, cols, ld_in, out_fmt, _ptr(out),
                                 ld_out, _stream(stream)))
         return out
@@ -236,7 +253,7 @@ class Field:
         if lda is None:
             lda = K
         if ldb is None:
-            ldb = n if path == PATH_FP64_QADIC else K
+            ldb = n if path == PATH_FP64_QADIC else (B.shape[-1] if path == PATH_FOLD else K)
         if ldc is None:
             ldc = n
         _check(lib().qadic_gemm(self._h, path, m, n, K, _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc,
@@ -298,14 +315,16 @@ def polymul_fqt(p: int, d: int, a, b, out=None, int_words: bool = False, stream=
     return out
 
 
-def polymul_batched(p: int, k: int, a, b, out=None, plain_f64: bool = False, stream=None):
+def polymul_batched(p: int, k: int, a, b, out=None, plain_f64: bool = False,
+                    int_words: bool = False, stream=None):
     """Batched Alg. 1 + Alg. 2 (``qadic_polymul_batched``); a, b: (count, k) uint8."""
     torch = _torch()
     count = a.shape[0]
     if out is None:
         out = torch.empty((count, 2 * k - 1), dtype=torch.uint8, device=a.device)
     _check(lib().qadic_polymul_batched(p, k, _ptr(a), _ptr(b), _ptr(out), count,
-                                       POLYMUL_PLAIN_F64 if plain_f64 else 0, _stream(stream)))
+                                       (POLYMUL_PLAIN_F64 if plain_f64 else 0) |
+                                       (POLYMUL_INT_WORDS if int_words else 0), _stream(stream)))
     return out
 
 

@@ -184,11 +184,15 @@ int qadic_pack(const qadic_field *field, int in_fmt, const void *in, int64_t row
     if (rows == 0 || cols == 0) return QADIC_OK;
     if (!in || !out) return set_error(QADIC_E_INVALID, "NULL data pointer");
     if (ld_in < cols) return set_error(QADIC_E_INVALID, "ld_in < cols");
-    const int64_t out_minor = (out_fmt == QADIC_FMT_OPERAND_B) ? rows : cols;
+    const int64_t out_minor =
+        (out_fmt == QADIC_FMT_OPERAND_B || out_fmt == QADIC_FMT_OPERAND_B_FOLD ||
+         out_fmt == QADIC_FMT_OPERAND_B_KARA) ? rows : cols;
     if (ld_out < out_minor) return set_error(QADIC_E_INVALID, "ld_out too small");
     if (out_fmt == QADIC_FMT_QADIC_F64 && f.n_q == 0)
         return set_error(QADIC_E_OVERFLOW, "Eq. 2 admits no q-adic block for p=%u k=%u", f.p, f.k);
-    if (out_fmt == QADIC_FMT_OPERAND_A || out_fmt == QADIC_FMT_OPERAND_B) {
+    if (out_fmt == QADIC_FMT_OPERAND_A || out_fmt == QADIC_FMT_OPERAND_B ||
+        out_fmt == QADIC_FMT_OPERAND_B_FOLD || out_fmt == QADIC_FMT_OPERAND_A_KARA ||
+        out_fmt == QADIC_FMT_OPERAND_B_KARA) {
         if (ld_out % 8 != 0 || ((uintptr_t)out & 15) != 0)
             return set_error(QADIC_E_INVALID, "operand output needs ld %% 8 == 0 and 16B alignment");
     }
@@ -224,6 +228,16 @@ int qadic_gemm(const qadic_field *field, int path, int64_t m, int64_t n, int64_t
         if (!gemm_planes_tc_supported(f))
             return set_error(QADIC_E_UNSUPPORTED, "no tensor-core plane kernel for k=%u", f.k);
         return launch_gemm_planes_tc(f, m, n, K, A, lda, B, ldb, C, ldc, s);
+    }
+    if (path == QADIC_PATH_FOLD) {
+        if (lda < K || ldb < K) return set_error(QADIC_E_INVALID, "lda or ldb < K");
+        if (f.k > 8) return set_error(QADIC_E_UNSUPPORTED, "no fold kernel for k=%u", f.k);
+        return launch_gemm_fold_tc(f, m, n, K, A, lda, B, ldb, C, ldc, s);
+    }
+    if (path == QADIC_PATH_KARATSUBA) {
+        if (lda < K || ldb < K) return set_error(QADIC_E_INVALID, "lda or ldb < K");
+        if (f.k != 2) return set_error(QADIC_E_UNSUPPORTED, "the Karatsuba form is for k = 2");
+        return launch_gemm_karatsuba_tc(f, m, n, K, A, lda, B, ldb, C, ldc, s);
     }
     return set_error(QADIC_E_INVALID, "unknown path %d", path);
 }
@@ -424,14 +438,22 @@ int qadic_polymul_batched(uint32_t p, uint32_t k, const uint8_t *a, const uint8_
     const uint64_t bound = (uint64_t)k * (p - 1) * (p - 1);
     uint32_t s = 1;
     while ((1ull << s) <= bound) ++s;
+    if (flags & ~(QADIC_POLYMUL_PLAIN_F64 | QADIC_POLYMUL_INT_WORDS))
+        return set_error(QADIC_E_INVALID, "flags 0x%x", flags);
     const bool plain = (flags & QADIC_POLYMUL_PLAIN_F64) != 0;
+    const bool ints = (flags & QADIC_POLYMUL_INT_WORDS) != 0;
+    if (plain && ints) return set_error(QADIC_E_INVALID, "PLAIN_F64 and INT_WORDS exclude each other");
     if (plain && (2 * k - 1) * s >= 53)
         return set_error(QADIC_E_OVERFLOW,
                          "(2k-1) log2 q = %u >= 53: Eq. 2 fails for a single-rounded FP64 product",
                          (2 * k - 1) * s);
     if (!plain && (2 * k - 1) * s > 63)
         return set_error(QADIC_E_OVERFLOW, "(2k-1) log2 q = %u > 63", (2 * k - 1) * s);
-    return launch_polymul(p, k, s, plain, a, b, out, count, (cudaStream_t)stream);
+    if (!ints && k * s > 53)
+        return set_error(QADIC_E_OVERFLOW, "k log2 q = %u > 53: a packed operand is not an exact double",
+                         k * s);
+    return launch_polymul(p, k, s, ints ? 2 : plain ? 1 : 0, a, b, out, count,
+                          (cudaStream_t)stream);
 }
 
 int qadic_sync_status(void *stream) {

@@ -124,7 +124,8 @@ __device__ __forceinline__ uint32_t mod_exact_f32(uint32_t bits, float pf, float
 
 // Grouped raster: consecutive unit indices cover kGroupM unit rows before the
 // next tile column, so the A and B panels in use at one time stay in L2.
-__device__ __forceinline__ void unit_coords(int unit, const TcParams &P, int &um, int &tn) {
+template <typename Params>
+__device__ __forceinline__ void unit_coords(int unit, const Params &P, int &um, int &tn) {
     const int per_group = kGroupM * P.tiles_n;
     const int first_m = (unit / per_group) * kGroupM;
     const int gm = min(P.units_m - first_m, kGroupM);
@@ -432,6 +433,344 @@ gemm_planes_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
     }
 }
 
+// ---------------------------------------------------------------------------
+// Fold-before-GEMM form.  out_j = sum_i A_i M_ij(B), where M_ij(B) is plane
+// j of B X^i mod P (the columns of b's multiplication matrix): the
+// reduction mod P moves in front of the contraction, which becomes one
+// prime-field GEMM of m x (k n_pad) over k K, the k output planes side by
+// side.  The pack step writes the operand as k planes (index i), plane i
+// being the k blocks M_i0, ..., M_i,k-1 (n_pad rows each, K-major), so a
+// K-block of plane i of A meets the same K-block of plane i of the operand.
+// The K loop runs over (plane i, K-block) pairs, one tile of each per stage;
+// each plane has its own accumulator (one product per K step, so the exact
+// FP32 chunk is (2^24 - 2p) / h^2), and the epilogue adds the k
+// accumulators and reduces mod p -- no fold, no 2k-1 plane sums.
+//
+// The same streaming serves the Karatsuba form for k = 2 (EPI_KARATSUBA):
+// three operand plane pairs (A_0, B_0), (A_1, B_1), (A_0 + A_1, B_0 + B_1)
+// (sums reduced and centred by the pack step) give D_0 = A_0 B_0,
+// D_2 = A_1 B_1 and D_m, so C_1 = D_m - D_0 - D_2: three plane products
+// instead of four.  The epilogue combines them and folds C_2 with X^2 mod P.
+constexpr int EPI_FOLD = 0, EPI_KARATSUBA = 1;
+
+struct FoldParams {
+    int64_t m, n, n_pad, ldc, c_plane;
+    int32_t tiles_m, tiles_n, units_m, nunits;
+    int32_t nkbp;         // K-blocks per plane
+    int32_t chunk_kb;     // K-blocks per exact FP32 chunk of one accumulator
+    float pf, inv_pf;
+    float x2[2];          // Karatsuba: X^2 mod P
+    int *status;
+};
+
+template <int KP, int BN>
+struct FoldCfg {
+    static constexpr int A_TILE = BM * BK * 2;
+    static constexpr int B_TILE = BN * BK * 2;
+    static constexpr int STAGE = A_TILE + B_TILE;
+    static constexpr int STAGES_RAW = (kSmemBudget - 2048) / STAGE;
+    static constexpr int STAGES = STAGES_RAW > 8 ? 8 : STAGES_RAW;
+    static constexpr int ACC_COLS = KP * BN;
+    static constexpr int TMEM_COLS = ACC_COLS <= 32 ? 32 : ACC_COLS <= 64 ? 64
+                                   : ACC_COLS <= 128 ? 128 : ACC_COLS <= 256 ? 256 : 512;
+    static constexpr int SMEM = 1024 + STAGES * STAGE + 256;
+    static_assert(ACC_COLS <= 512, "accumulators exceed tensor memory");
+    static_assert(BN <= 256 && BN % 16 == 0, "MMA N");
+    static_assert(STAGES >= 2, "not enough shared memory for two stages");
+};
+
+template <int KP, int BN, int CM, int EPI>
+__global__ void __launch_bounds__(kThreads, 1)
+gemm_fold_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                    uint8_t *__restrict__ C, const FoldParams P) {
+    using CF = FoldCfg<KP, BN>;
+    static_assert(CM == 1 || CM == 2, "cluster size along M");
+    constexpr uint16_t kAllCtas = (uint16_t)((1u << CM) - 1);
+    const int rank = CM > 1 ? (int)ptx::cluster_ctarank() : 0;
+    const int unit0 = blockIdx.x / CM, unit_step = gridDim.x / CM;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = (uint64_t *)(smem + CF::STAGES * CF::STAGE);
+    uint64_t *empty = full + CF::STAGES;
+    uint64_t *acc_full = empty + CF::STAGES;
+    uint64_t *acc_empty = acc_full + 1;
+    uint64_t *tmem_free = acc_empty + 1;
+    uint64_t *mma_done = tmem_free + 1;
+    uint32_t *tmem_slot = (uint32_t *)(mma_done + 1);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int nkbp = P.nkbp;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < CF::STAGES; ++s) {
+            ptx::mbar_init(&full[s], 1);
+            ptx::mbar_init(&empty[s], CM);
+        }
+        ptx::mbar_init(acc_full, 1);
+        ptx::mbar_init(acc_empty, 32 * kEpiWarps);
+        ptx::mbar_init(tmem_free, 32 * kEpiWarps);
+        ptx::mbar_init(mma_done, 1);
+        *abort_flag = 0;
+        ptx::fence_mbar_init();
+    }
+    if (warp == 1) {
+        ptx::tmem_alloc(tmem_slot, CF::TMEM_COLS);
+        ptx::tmem_relinquish();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    if (CM > 1) ptx::cluster_sync();
+    ptx::tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    auto a_tile = [&](int stage) { return smem + stage * CF::STAGE; };
+    auto b_tile = [&](int stage) { return smem + stage * CF::STAGE + CF::A_TILE; };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer: (plane, K-block) pairs ----------------
+            ptx::prefetch_tmap(&tmA);
+            ptx::prefetch_tmap(&tmB);
+            int64_t it = 0;
+            bool ok = true;
+            for (int unit = unit0; unit < P.nunits && ok; unit += unit_step) {
+                int um, tn;
+                unit_coords(unit, P, um, tn);
+                const int tm = um * CM + rank;
+                for (int i = 0; i < KP && ok; ++i)
+                    for (int kb = 0; kb < nkbp; ++kb, ++it) {
+                        const int stage = (int)(it % CF::STAGES);
+                        if (it >= CF::STAGES) {
+                            if (*abort_flag ||
+                                !ptx::mbar_wait(&empty[stage], (uint32_t)((it / CF::STAGES) - 1) & 1)) {
+                                ok = false;
+                                break;
+                            }
+                        }
+                        ptx::mbar_arrive_expect_tx(&full[stage], CF::STAGE);
+                        ptx::tma_load_3d(a_tile(stage), &tmA, &full[stage], kb * BK, tm * BM, i);
+                        if (CM == 1) {
+                            ptx::tma_load_3d(b_tile(stage), &tmB, &full[stage], kb * BK, tn * BN, i);
+                        } else {
+                            constexpr int ROWS = BN / CM;
+                            ptx::tma_load_3d_multicast(b_tile(stage) + rank * ROWS * kRowBytes, &tmB,
+                                                       &full[stage], kb * BK, tn * BN + rank * ROWS,
+                                                       i, kAllCtas);
+                        }
+                    }
+            }
+            if (!ok) {
+                *abort_flag = 1;
+                for (int64_t j = (it > CF::STAGES ? it - CF::STAGES : 0); j < it; ++j)
+                    ptx::mbar_wait(&full[j % CF::STAGES], (uint32_t)(j / CF::STAGES) & 1);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            const uint32_t idesc = ptx::idesc_bf16_f32(BM, BN);
+            int64_t it = 0;
+            int drain = 0, tcount = 0;
+            bool ok = true;
+            for (int unit = unit0; unit < P.nunits && ok; unit += unit_step, ++tcount) {
+                if (tcount > 0) {
+                    if (*abort_flag || !ptx::mbar_wait(tmem_free, (uint32_t)(tcount - 1) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    ptx::tc_fence_after();
+                }
+                for (int i = 0; i < KP && ok; ++i)
+                    for (int kb = 0; kb < nkbp; ++kb, ++it) {
+                        const int stage = (int)(it % CF::STAGES);
+                        if (*abort_flag ||
+                            !ptx::mbar_wait(&full[stage], (uint32_t)(it / CF::STAGES) & 1)) {
+                            ok = false;
+                            break;
+                        }
+                        ptx::tc_fence_after();
+                        const uint64_t ad = operand_desc(a_tile(stage));
+                        const uint64_t bd = operand_desc(b_tile(stage));
+#pragma unroll
+                        for (int kk = 0; kk < BK / UMMA_K; ++kk)
+                            ptx::mma_bf16(tmem_base + i * BN, ad + 2 * kk, bd + 2 * kk, idesc,
+                                          (kb == 0 && kk == 0) ? 0u : 1u);
+                        if (CM == 1) ptx::mma_commit(&empty[stage]);
+                        else ptx::mma_commit_multicast(&empty[stage], kAllCtas);
+                        if ((kb + 1) % P.chunk_kb == 0 && kb + 1 < nkbp) {
+                            ptx::mma_commit(acc_full);
+                            if (!ptx::mbar_wait(acc_empty, (uint32_t)drain & 1)) {
+                                ok = false;
+                                break;
+                            }
+                            ptx::tc_fence_after();
+                            ++drain;
+                        }
+                    }
+                if (ok) ptx::mma_commit(acc_full);   // tile complete
+            }
+            if (!ok) {
+                *abort_flag = 1;
+                ptx::mma_commit(acc_full);
+            }
+            ptx::mma_commit(mma_done);
+            if (!ptx::mbar_wait(mma_done, 0)) *abort_flag = 1;
+        }
+    } else {
+        // ---------------- epilogue (warps 2..5) ----------------
+        const int quarter = warp & 3;
+        const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16);
+        const int ndrain = nkbp > 0 ? KP * ((nkbp - 1) / P.chunk_kb) : 0;
+        int phase = 0;
+        bool ok = true;
+        for (int unit = unit0; unit < P.nunits && ok; unit += unit_step) {
+            int um, tn;
+            unit_coords(unit, P, um, tn);
+            const int tm = um * CM + rank;
+            for (int d = 0; d < ndrain; ++d, ++phase) {
+                // in-place reduction of every accumulator (the ones of planes
+                // not started yet hold stale values that the plane's first
+                // MMA overwrites)
+                if (!ptx::mbar_wait(acc_full, (uint32_t)phase & 1) || *abort_flag) {
+                    ok = false;
+                    break;
+                }
+                ptx::tc_fence_after();
+#pragma unroll 1
+                for (int c = 0; c < CF::ACC_COLS; c += 32) {
+                    uint32_t v[32];
+                    ptx::tmem_ld32(tbase + c, v);
+                    ptx::tmem_wait_ld();
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) {
+                        const float x = __uint_as_float(v[e]);
+                        v[e] = __float_as_uint(fmaf(-P.pf, rintf(x * P.inv_pf), x));
+                    }
+                    ptx::tmem_st32(tbase + c, v);
+                }
+                ptx::tmem_wait_st();
+                ptx::tc_fence_before();
+                ptx::mbar_arrive(acc_empty);
+            }
+            if (!ok) break;
+            if (!ptx::mbar_wait(acc_full, (uint32_t)phase & 1) || *abort_flag) {
+                ok = false;
+                break;
+            }
+            ++phase;
+            ptx::tc_fence_after();
+            const int64_t row = (int64_t)tm * BM + quarter * 32 + lane;
+            if constexpr (EPI == EPI_KARATSUBA) {
+#pragma unroll 1
+                for (int c = 0; c < BN; c += 16) {
+                    float r[3][16];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        uint32_t v[16];
+                        ptx::tmem_ld16(tbase + a * BN + c, v);
+                        ptx::tmem_wait_ld();
+                        if (c + 16 >= BN && a == 2) {
+                            ptx::tc_fence_before();
+                            ptx::mbar_arrive(tmem_free);
+                        }
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) {
+                            const float x = __uint_as_float(v[e]);
+                            r[a][e] = fmaf(-P.pf, rintf(x * P.inv_pf), x);   // |.| <= 1.5 p
+                        }
+                    }
+                    // C_0 = D_0, C_2 = D_2, C_1 = D_m - D_0 - D_2; out_i = C_i + C_2 (X^2 mod P)_i
+                    uint32_t word[2][4];
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) {
+                        word[0][w] = word[1][w] = 0;
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            const int e = 4 * w + b;
+                            const float c2 = r[1][e];
+                            const float o0 = fmaf(c2, P.x2[0], r[0][e]);
+                            const float o1 = fmaf(c2, P.x2[1], r[2][e] - r[0][e] - r[1][e]);
+                            word[0][w] |= mod_exact_f32(__float_as_uint(o0), P.pf, P.inv_pf) << (8 * b);
+                            word[1][w] |= mod_exact_f32(__float_as_uint(o1), P.pf, P.inv_pf) << (8 * b);
+                        }
+                    }
+                    const int64_t col = (int64_t)tn * BN + c;
+                    if (row < P.m && col < P.n) {
+#pragma unroll
+                        for (int i = 0; i < 2; ++i) {
+                            uint8_t *dst = C + i * P.c_plane + row * P.ldc + col;
+                            if (col + 16 <= P.n && (((uintptr_t)dst) & 15) == 0) {
+                                *reinterpret_cast<uint4 *>(dst) =
+                                    make_uint4(word[i][0], word[i][1], word[i][2], word[i][3]);
+                            } else {
+                                const int64_t nrem = P.n - col;
+                                const int lim = nrem < 16 ? (int)nrem : 16;
+                                for (int e = 0; e < lim; ++e)
+                                    dst[e] = (uint8_t)(word[i][e / 4] >> (8 * (e % 4)));
+                            }
+                        }
+                    }
+                }
+                continue;
+            }
+#pragma unroll 1
+            for (int c = 0; c < BN; c += 16) {
+                float s[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) s[e] = 0.f;
+#pragma unroll 1
+                for (int a = 0; a < KP; ++a) {
+                    uint32_t v[16];
+                    ptx::tmem_ld16(tbase + a * BN + c, v);
+                    ptx::tmem_wait_ld();
+                    if (c + 16 >= BN && a == KP - 1) {
+                        ptx::tc_fence_before();
+                        ptx::mbar_arrive(tmem_free);
+                    }
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        const float x = __uint_as_float(v[e]);
+                        s[e] += fmaf(-P.pf, rintf(x * P.inv_pf), x);   // |.| <= 1.5 p each
+                    }
+                }
+                uint32_t word[4];
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    word[w] = 0;
+#pragma unroll
+                    for (int b = 0; b < 4; ++b)
+                        word[w] |= mod_exact_f32(__float_as_uint(s[4 * w + b]), P.pf, P.inv_pf)
+                                   << (8 * b);
+                }
+                // output column block j = plane j (n_pad is a multiple of BN)
+                const int64_t colx = (int64_t)tn * BN + c;
+                const int64_t j = colx / P.n_pad, col = colx - j * P.n_pad;
+                if (row < P.m && col < P.n) {
+                    uint8_t *dst = C + j * P.c_plane + row * P.ldc + col;
+                    if (col + 16 <= P.n && (((uintptr_t)dst) & 15) == 0) {
+                        *reinterpret_cast<uint4 *>(dst) = make_uint4(word[0], word[1], word[2], word[3]);
+                    } else {
+                        const int64_t nrem = P.n - col;
+                        const int lim = nrem < 16 ? (int)nrem : 16;
+                        for (int e = 0; e < lim; ++e) dst[e] = (uint8_t)(word[e / 4] >> (8 * (e % 4)));
+                    }
+                }
+            }
+        }
+        if (!ok) *abort_flag = 1;
+    }
+
+    ptx::tc_fence_before();
+    __syncthreads();
+    if (CM > 1) ptx::cluster_sync();
+    if (threadIdx.x == 0 && *abort_flag) record_timeout(P.status, 4);
+    if (warp == 1) {
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc(tmem_base, CF::TMEM_COLS);
+    }
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -544,6 +883,81 @@ int launch_tc(const Field &f, int64_t m, int64_t n, int64_t K, const void *A, in
     return QADIC_OK;
 }
 
+template <int KP, int BN, int CM, int EPI = EPI_FOLD>
+int launch_fold(const Field &f, int64_t m, int64_t n, int64_t K, const void *A, int64_t lda,
+                const void *B, int64_t ldb, uint8_t *C, int64_t ldc, cudaStream_t stream) {
+    using CF = FoldCfg<KP, BN>;
+    // fold: B rows are KP blocks of n_pad; Karatsuba: B rows are the n columns
+    const int64_t n_pad = EPI == EPI_FOLD ? fold_n_pad(n) : n;
+    const int64_t b_rows = EPI == EPI_FOLD ? KP * n_pad : n;
+    CUtensorMap tmA, tmB;
+    int st;
+    if ((st = make_plane_map(&tmA, A, K, m, lda, m * lda, KP, BM))) return st;
+    if ((st = make_plane_map(&tmB, B, K, b_rows, ldb, b_rows * ldb, KP, BN / CM))) return st;
+    FoldParams P;
+    P.m = m;
+    P.n = n;
+    P.n_pad = n_pad;
+    P.ldc = ldc;
+    P.c_plane = m * ldc;
+    P.nkbp = (int32_t)((K + BK - 1) / BK);
+    const int64_t hh = (int64_t)f.h * f.h;
+    const int64_t chunk = ((1ll << 24) - 2 * (int64_t)f.p) / (hh ? hh : 1);
+    P.chunk_kb = (int32_t)std::min<int64_t>(chunk / BK, 1 << 30);
+    if (P.chunk_kb < 1) return set_error(QADIC_E_OVERFLOW, "exact FP32 chunk below one K-block");
+    P.pf = (float)f.p;
+    P.inv_pf = 1.0f / (float)f.p;
+    P.x2[0] = P.x2[1] = 0.f;
+    if (EPI == EPI_KARATSUBA) {
+        P.x2[0] = (float)f.fold[0];
+        P.x2[1] = (float)f.fold[1];
+    }
+    P.status = device_status_word();
+    auto kern = gemm_fold_tc_kernel<KP, BN, CM, EPI>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM) !=
+        cudaSuccess)
+        return set_error(QADIC_E_CUDA, "fold smem attribute: %s", cudaGetErrorString(cudaGetLastError()));
+    const int64_t tiles_m = (m + BM - 1) / BM;
+    const int64_t tiles_n = EPI == EPI_FOLD ? KP * n_pad / BN : (n + BN - 1) / BN;
+    const int64_t units_m = (tiles_m + CM - 1) / CM;
+    if (units_m * tiles_n > 0x7fffffff) return set_error(QADIC_E_INVALID, "too many tiles");
+    P.tiles_m = (int32_t)tiles_m;
+    P.tiles_n = (int32_t)tiles_n;
+    P.units_m = (int32_t)units_m;
+    P.nunits = (int32_t)(units_m * tiles_n);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = CF::SMEM;
+    cfg.stream = stream;
+    int max_units = sms > 0 ? sms / CM : 1;
+    if (CM > 1) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = CM;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cfg.gridDim = dim3((unsigned)(max_units * CM));
+        int clusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) == cudaSuccess && clusters > 0)
+            max_units = std::min(max_units, clusters);
+        else
+            cudaGetLastError();
+    }
+    const int units = (int)std::min<int64_t>(P.nunits, std::max(max_units, 1));
+    cfg.gridDim = dim3((unsigned)(units * CM));
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, tmA, tmB, C, P);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(QADIC_E_CUDA, "fold launch: %s", cudaGetErrorString(e));
+    }
+    return QADIC_OK;
+}
+
 }  // namespace
 
 bool gemm_planes_tc_supported(const Field &f) { return f.k >= 2 && f.k <= 4; }
@@ -576,6 +990,47 @@ int launch_gemm_planes_tc(const Field &f, int64_t m, int64_t n, int64_t K, const
                           cudaStream_t stream) {
     return launch_gemm_planes_tc_strided(f, m, n, K, A, lda, m * lda, B, ldb, n * ldb, C, ldc,
                                          m * ldc, stream);
+}
+
+int launch_gemm_fold_tc(const Field &f, int64_t m, int64_t n, int64_t K, const void *A,
+                        int64_t lda, const void *B, int64_t ldb, uint8_t *C, int64_t ldc,
+                        cudaStream_t stream) {
+    if (lda % 8 || ldb % 8 || ((uintptr_t)A & 15) || ((uintptr_t)B & 15))
+        return set_error(QADIC_E_INVALID, "fold operands need ld %% 8 == 0 and 16-byte alignment");
+    if (K == 0) {
+        for (uint32_t i = 0; i < f.k; ++i)
+            if (cudaMemset2DAsync(C + (size_t)i * m * ldc, (size_t)ldc, 0, (size_t)n, (size_t)m,
+                                  stream) != cudaSuccess)
+                return set_error(QADIC_E_CUDA, "memset: %s", cudaGetErrorString(cudaGetLastError()));
+        return QADIC_OK;
+    }
+    switch (f.k) {
+        case 1: return launch_fold<1, 256, 2>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
+        case 2: return launch_fold<2, 256, 2>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
+        case 3: return launch_fold<3, 128, 2>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
+        case 4: return launch_fold<4, 128, 2>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
+        case 5: return launch_fold<5, 64, 2>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
+        case 6: return launch_fold<6, 64, 2>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
+        case 7: return launch_fold<7, 64, 2>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
+        case 8: return launch_fold<8, 64, 2>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
+        default: return set_error(QADIC_E_UNSUPPORTED, "no fold kernel for k=%u", f.k);
+    }
+}
+
+int launch_gemm_karatsuba_tc(const Field &f, int64_t m, int64_t n, int64_t K, const void *A,
+                             int64_t lda, const void *B, int64_t ldb, uint8_t *C, int64_t ldc,
+                             cudaStream_t stream) {
+    if (f.k != 2) return set_error(QADIC_E_UNSUPPORTED, "the Karatsuba form is for k = 2");
+    if (lda % 8 || ldb % 8 || ((uintptr_t)A & 15) || ((uintptr_t)B & 15))
+        return set_error(QADIC_E_INVALID, "Karatsuba operands need ld %% 8 == 0 and 16-byte alignment");
+    if (K == 0) {
+        for (uint32_t i = 0; i < 2; ++i)
+            if (cudaMemset2DAsync(C + (size_t)i * m * ldc, (size_t)ldc, 0, (size_t)n, (size_t)m,
+                                  stream) != cudaSuccess)
+                return set_error(QADIC_E_CUDA, "memset: %s", cudaGetErrorString(cudaGetLastError()));
+        return QADIC_OK;
+    }
+    return launch_fold<3, 128, 2, EPI_KARATSUBA>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
 }
 
 }  // namespace qadic

@@ -8,6 +8,10 @@
 //   OPERAND_A    k planes of bf16 centred coefficients, same layout
 //   OPERAND_B    k planes of bf16 centred coefficients, transposed (K-major B)
 //   COEFF_U8     k planes of uint8 coefficients (log input only)
+//   OPERAND_B_FOLD  B's multiplication matrices for the fold-before form:
+//                plane i, block j = coefficient j of B X^i mod P, transposed
+//   OPERAND_A_KARA / OPERAND_B_KARA  (k = 2) three bf16 planes c_0, c_1 and
+//                (c_0 + c_1) mod p, centred; B transposed (Karatsuba form)
 // The log -> value tables live in shared memory when they fit (96 KB).
 // HBM-bound elementwise work; the transposing variant stages 32 x 32 tiles
 // in shared memory so both the reads and the writes are coalesced.
@@ -33,6 +37,8 @@ struct PackParams {
     const int8_t *log_centred;
     const uint8_t *antilog;
     int tables_in_smem;
+    int64_t n_pad;                       // OPERAND_B_FOLD: rows per block
+    uint8_t xpow[2 * kMaxK - 1][kMaxK];  // X^t mod P, t < 2k - 1
 };
 
 // Coefficient i of the input element (row r, col c), reduced to [0, p-1].
@@ -145,6 +151,90 @@ __global__ void __launch_bounds__(kTile * 8) pack_transpose(const void *__restri
         if (oc < P.cols && orow < P.rows)
             for (uint32_t i = 0; i < P.k; ++i)
                 out[((int64_t)i * P.cols + oc) * P.ld_out + orow] = __int2bfloat16_rn(tile[i][tx][yy]);
+    }
+}
+
+// Fold-before operand: for each element b of B (K x n) and each i, j < k,
+// coefficient j of b X^i mod P = sum_l b_l (X^(l+i) mod P)_j, centred, at
+// row (i k + j) n_pad + c, column r of the output (K contiguous).  The
+// 32 x 32 input tile is staged as canonical coefficients so both the reads
+// and the writes are coalesced; columns c in [n, n_pad) are written as 0.
+template <int IN>
+__global__ void __launch_bounds__(kTile * 8) pack_fold_b(const void *__restrict__ in,
+                                                        __nv_bfloat16 *__restrict__ out,
+                                                        PackParams P) {
+    __shared__ uint8_t tile[kMaxK][kTile][kTile + 1];
+    const int64_t r0 = (int64_t)blockIdx.y * kTile, c0 = (int64_t)blockIdx.x * kTile;
+    const int tx = threadIdx.x % kTile, ty = threadIdx.x / kTile;   // 32 x 8
+    for (int yy = ty; yy < kTile; yy += 8) {
+        const int64_t r = r0 + yy, c = c0 + tx;
+        const bool valid = r < P.rows && c < P.cols;
+        if (IN == IN_LOG8 || IN == IN_LOG16) {
+            uint32_t code = valid ? load_code<IN>(in, P, r, c) : 0;
+            if (code >= P.order) code = P.order - 1;
+            for (uint32_t i = 0; i < P.k; ++i)
+                tile[i][yy][tx] = valid ? __ldg(P.antilog + (int64_t)code * P.k + i) : 0;
+        } else {
+            for (uint32_t i = 0; i < P.k; ++i)
+                tile[i][yy][tx] = valid ? (uint8_t)coeff_canon<IN>(in, P, r, c, i) : 0;
+        }
+    }
+    __syncthreads();
+    for (int yy = ty; yy < kTile; yy += 8) {
+        const int64_t oc = c0 + yy, orow = r0 + tx;   // output row block index = input col
+        if (oc >= P.n_pad || orow >= P.rows) continue;
+        uint32_t b[kMaxK];
+        for (uint32_t l = 0; l < P.k; ++l) b[l] = tile[l][tx][yy];
+        for (uint32_t i = 0; i < P.k; ++i)
+            for (uint32_t j = 0; j < P.k; ++j) {
+                uint32_t v = 0;
+                for (uint32_t l = 0; l < P.k; ++l)
+                    v += mod_small(b[l] * P.xpow[l + i][j], P.p, P.m32);   // each term < p
+                v = mod_small(v, P.p, P.m32);
+                out[(((int64_t)i * P.k + j) * P.n_pad + oc) * P.ld_out + orow] =
+                    __int2bfloat16_rn(centre(v, P));
+            }
+    }
+}
+
+// Karatsuba operands (k = 2): planes c_0, c_1, (c_0 + c_1) mod p, centred;
+// TRANS writes plane v as cols x rows (B), else rows x cols (A).  32 x 32
+// tiles staged in shared memory keep the transposed writes coalesced.
+template <int IN, bool TRANS>
+__global__ void __launch_bounds__(kTile * 8) pack_kara(const void *__restrict__ in,
+                                                      __nv_bfloat16 *__restrict__ out,
+                                                      PackParams P) {
+    __shared__ uint8_t tile[2][kTile][kTile + 1];
+    const int64_t r0 = (int64_t)blockIdx.y * kTile, c0 = (int64_t)blockIdx.x * kTile;
+    const int tx = threadIdx.x % kTile, ty = threadIdx.x / kTile;
+    for (int yy = ty; yy < kTile; yy += 8) {
+        const int64_t r = r0 + yy, c = c0 + tx;
+        if (r < P.rows && c < P.cols) {
+            if (IN == IN_LOG8 || IN == IN_LOG16) {
+                uint32_t code = load_code<IN>(in, P, r, c);
+                if (code >= P.order) code = P.order - 1;
+                tile[0][yy][tx] = __ldg(P.antilog + (int64_t)code * 2);
+                tile[1][yy][tx] = __ldg(P.antilog + (int64_t)code * 2 + 1);
+            } else {
+                tile[0][yy][tx] = (uint8_t)coeff_canon<IN>(in, P, r, c, 0);
+                tile[1][yy][tx] = (uint8_t)coeff_canon<IN>(in, P, r, c, 1);
+            }
+        }
+    }
+    __syncthreads();
+    for (int yy = ty; yy < kTile; yy += 8) {
+        // A: element (r0 + yy, c0 + tx); B: output row c0 + yy, column r0 + tx
+        const int64_t r = TRANS ? r0 + tx : r0 + yy, c = TRANS ? c0 + yy : c0 + tx;
+        if (r >= P.rows || c >= P.cols) continue;
+        const uint32_t a0 = TRANS ? tile[0][tx][yy] : tile[0][yy][tx];
+        const uint32_t a1 = TRANS ? tile[1][tx][yy] : tile[1][yy][tx];
+        const uint32_t v[3] = {a0, a1, mod_small(a0 + a1, P.p, P.m32)};
+#pragma unroll
+        for (int pl = 0; pl < 3; ++pl) {
+            const int64_t o = TRANS ? ((int64_t)pl * P.cols + c) * P.ld_out + r
+                                    : ((int64_t)pl * P.rows + r) * P.ld_out + c;
+            out[o] = __int2bfloat16_rn(centre(v[pl], P));
+        }
     }
 }
 
@@ -278,6 +368,18 @@ int dispatch_out(int out_fmt, const void *in, void *out, const PackParams &P0, c
                (P.rows + 63) / 64 <= 65535) {
         const dim3 grid((unsigned)(P.cols / 64), (unsigned)((P.rows + 63) / 64), P.k);
         pack_vec_b<IN><<<grid, 256, 0, stream>>>((const uint8_t *)in, (__nv_bfloat16 *)out, P);
+    } else if (out_fmt == QADIC_FMT_OPERAND_A_KARA || out_fmt == QADIC_FMT_OPERAND_B_KARA) {
+        if (P.k != 2) return set_error(QADIC_E_UNSUPPORTED, "Karatsuba operands are for k = 2");
+        const dim3 grid((unsigned)((P.cols + kTile - 1) / kTile), (unsigned)((P.rows + kTile - 1) / kTile));
+        if (grid.y > 65535) return set_error(QADIC_E_INVALID, "too many rows for the Karatsuba pack");
+        if (out_fmt == QADIC_FMT_OPERAND_A_KARA)
+            pack_kara<IN, false><<<grid, kTile * 8, 0, stream>>>(in, (__nv_bfloat16 *)out, P);
+        else
+            pack_kara<IN, true><<<grid, kTile * 8, 0, stream>>>(in, (__nv_bfloat16 *)out, P);
+    } else if (out_fmt == QADIC_FMT_OPERAND_B_FOLD) {
+        const dim3 grid((unsigned)(P.n_pad / kTile), (unsigned)((P.rows + kTile - 1) / kTile));
+        if (grid.y > 65535) return set_error(QADIC_E_INVALID, "too many rows for the fold pack");
+        pack_fold_b<IN><<<grid, kTile * 8, 0, stream>>>(in, (__nv_bfloat16 *)out, P);
     } else if (out_fmt == QADIC_FMT_OPERAND_B) {
         auto kern = pack_transpose<IN>;
         if (smem > 48 * 1024)
@@ -323,7 +425,13 @@ int launch_pack(const Field &f, int in_fmt, const void *in, int64_t rows, int64_
     P.log_centred = f.d_log_centred;
     P.antilog = f.d_antilog;
     P.tables_in_smem = 0;
-    if (out_fmt < QADIC_FMT_COEFF_U8 || out_fmt > QADIC_FMT_OPERAND_B ||
+    P.n_pad = fold_n_pad(cols);
+    for (uint32_t t = 0; t < 2 * kMaxK - 1; ++t)
+        for (uint32_t j = 0; j < kMaxK; ++j) P.xpow[t][j] = 0;
+    for (uint32_t t = 0; t < f.k; ++t) P.xpow[t][t] = 1;
+    for (uint32_t t = 0; t + 1 < f.k; ++t)
+        for (uint32_t j = 0; j < f.k; ++j) P.xpow[f.k + t][j] = f.fold[t * f.k + j];
+    if (out_fmt < QADIC_FMT_COEFF_U8 || out_fmt > QADIC_FMT_OPERAND_B_KARA ||
         out_fmt == QADIC_FMT_INT8_PLANES)
         return set_error(QADIC_E_INVALID, "unsupported output format %d", out_fmt);
     switch (in_fmt) {

@@ -8,6 +8,10 @@
 //            p (rop >> s i), mu_{2k-2} = u_{2k-2}, mu_i = (u_i - q u_{i+1})
 //            mod p through a p^2 table (Table 2, "p^2 extra memory, d
 //            accesses").
+// With QADIC_POLYMUL_INT_WORDS the product is taken in 64-bit integer
+// words instead (Sec. 2 allows m = 64): one integer multiply, exact.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace qadic {
@@ -16,13 +20,26 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// Signed integer value of a double holding an exact integer of magnitude
+// < 2^53, from its bit pattern (integer instructions only).
+__device__ __forceinline__ int64_t f64_to_i64_exact(double x) {
+    const int64_t mag = (int64_t)f64_to_u64_exact(fabs(x));
+    return x < 0.0 ? -mag : mag;
+}
+
+// MODE 0: FP64 product made exact as hi + lo (lo = fma(a, b, -hi));
+// MODE 1: single-rounded FP64 product (Eq. 2 with m = 53 must hold);
+// MODE 2: 64-bit integer words, r = a~ b~ exactly (Sec. 2 allows m = 64).
+// The conversions between the packed integers and doubles are done on the
+// bit patterns, so the FP64 pipe only sees the multiply (and the FMA).
+template <int MODE>
 __global__ void __launch_bounds__(kThreads)
 polymul_kernel(const uint8_t *__restrict__ a, const uint8_t *__restrict__ b,
                uint8_t *__restrict__ out, int64_t count, uint32_t p, uint32_t k, uint32_t s,
-               uint32_t qneg_mod_p, Div64 divp, int plain) {
+               uint32_t qneg_mod_p, Div64 divp) {
     extern __shared__ uint8_t smem[];
     const uint32_t D = 2 * k - 1;
-    uint8_t *corr = smem;                         // p*p entries
+    uint8_t *corr = smem;                           // p*p entries
     uint8_t *stage = smem + ((p * p + 15) & ~15u);  // kThreads * D bytes
 
     const uint32_t m32 = (uint32_t)((((uint64_t)1 << 32) + p - 1) / p);
@@ -32,56 +49,86 @@ polymul_kernel(const uint8_t *__restrict__ a, const uint8_t *__restrict__ b,
     }
     __syncthreads();
 
-    const int64_t base = (int64_t)blockIdx.x * kThreads;
-    const int64_t idx = base + threadIdx.x;
-    if (idx < count) {
-        uint64_t aw = 0, bw = 0;
-        for (uint32_t i = 0; i < k; ++i) {   // coefficients taken mod p
-            aw |= (uint64_t)mod_small(__ldg(a + idx * k + i), p, m32) << (s * i);
-            bw |= (uint64_t)mod_small(__ldg(b + idx * k + i), p, m32) << (s * i);
+    // grid-stride over blocks of kThreads pairs (the table is built once)
+    for (int64_t base = (int64_t)blockIdx.x * kThreads; base < count;
+         base += (int64_t)gridDim.x * kThreads) {
+        const int64_t idx = base + threadIdx.x;
+        if (idx < count) {
+            uint64_t aw = 0, bw = 0;
+            if (k == 4 && ((((uintptr_t)a | (uintptr_t)b) & 3) == 0)) {
+                const uint32_t wa = __ldg(reinterpret_cast<const uint32_t *>(a) + idx);
+                const uint32_t wb = __ldg(reinterpret_cast<const uint32_t *>(b) + idx);
+#pragma unroll
+                for (uint32_t i = 0; i < 4; ++i) {
+                    aw |= (uint64_t)mod_small((wa >> (8 * i)) & 0xff, p, m32) << (s * i);
+                    bw |= (uint64_t)mod_small((wb >> (8 * i)) & 0xff, p, m32) << (s * i);
+                }
+            } else {
+                for (uint32_t i = 0; i < k; ++i) {   // coefficients taken mod p
+                    aw |= (uint64_t)mod_small(__ldg(a + idx * k + i), p, m32) << (s * i);
+                    bw |= (uint64_t)mod_small(__ldg(b + idx * k + i), p, m32) << (s * i);
+                }
+            }
+            uint64_t r;
+            if (MODE == 2) {
+                r = aw * bw;   // < 2^((2k-1) s) <= 2^63: exact in 64 bits
+            } else {
+                const double ad = u64_to_f64_exact(aw), bd = u64_to_f64_exact(bw);   // < 2^53
+                const double hi = ad * bd;
+                if (MODE == 1) {
+                    r = f64_to_u64_exact(hi);
+                } else {
+                    // hi may reach 2^63: read it as mantissa << exponent
+                    const uint64_t bits = (uint64_t)__double_as_longlong(hi);
+                    const uint32_t e = (uint32_t)(bits >> 52);
+                    const uint64_t mant = (bits & ((1ull << 52) - 1)) | (1ull << 52);
+                    const uint64_t hi_u = e >= 1075 ? mant << (e - 1075) : f64_to_u64_exact(hi);
+                    const double lo = fma(ad, bd, -hi);   // exact error term, |lo| < 2^11
+                    r = hi_u + (uint64_t)f64_to_i64_exact(lo);
+                }
+            }
+            const uint64_t rop = div64(r, divp);
+            uint32_t u_next = 0;
+            uint8_t *dst = stage + threadIdx.x * D;
+            for (int i = (int)D - 1; i >= 0; --i) {
+                const uint32_t ui = (uint32_t)((r >> (s * i)) - (uint64_t)p * (rop >> (s * i)));
+                dst[i] = (i == (int)D - 1) ? (uint8_t)ui : corr[ui * p + u_next];
+                u_next = ui;
+            }
         }
-        const double ad = (double)aw, bd = (double)bw;   // exact: < 2^53
-        uint64_t r;
-        const double hi = ad * bd;
-        if (plain) {
-            r = (uint64_t)hi;
-        } else {
-            const double lo = fma(ad, bd, -hi);              // exact error term
-            r = (uint64_t)((int64_t)hi + (int64_t)lo);
-        }
-        const uint64_t rop = div64(r, divp);
-        uint32_t u_next = 0;
-        uint8_t *dst = stage + threadIdx.x * D;
-        for (int i = (int)D - 1; i >= 0; --i) {
-            const uint32_t ui = (uint32_t)((r >> (s * i)) - (uint64_t)p * (rop >> (s * i)));
-            dst[i] = (i == (int)D - 1) ? (uint8_t)ui : corr[ui * p + u_next];
-            u_next = ui;
-        }
+        __syncthreads();
+        // coalesced write-out of the block's contiguous output range
+        const int64_t nvalid = (count - base) < kThreads ? (count - base) : kThreads;
+        uint8_t *gout = out + base * D;
+        for (int64_t i = threadIdx.x; i < nvalid * D; i += blockDim.x) gout[i] = stage[i];
+        __syncthreads();
     }
-    __syncthreads();
-    // Coalesced write-out of the block's contiguous output range.
-    const int64_t nvalid = (count - base) < kThreads ? (count - base) : kThreads;
-    uint8_t *gout = out + base * D;
-    for (int64_t i = threadIdx.x; i < nvalid * D; i += blockDim.x) gout[i] = stage[i];
 }
 
 }  // namespace
 
-int launch_polymul(uint32_t p, uint32_t k, uint32_t log2_q, bool plain_f64, const uint8_t *a,
+int launch_polymul(uint32_t p, uint32_t k, uint32_t log2_q, int mode, const uint8_t *a,
                    const uint8_t *b, uint8_t *out, int64_t count, cudaStream_t stream) {
     const uint64_t q = 1ull << log2_q;
     const uint32_t qneg = (uint32_t)((p - q % p) % p);
     const size_t smem = ((p * p + 15) & ~15u) + (size_t)kThreads * (2 * k - 1);
+    auto kern = mode == 2 ? polymul_kernel<2> : mode == 1 ? polymul_kernel<1> : polymul_kernel<0>;
     if (smem > 48 * 1024) {
-        if (cudaFuncSetAttribute(polymul_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem) != cudaSuccess)
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
             return set_error(QADIC_E_CUDA, "smem attribute: %s",
                              cudaGetErrorString(cudaGetLastError()));
     }
-    const int64_t blocks = (count + kThreads - 1) / kThreads;
-    if (blocks > 0x7fffffff) return set_error(QADIC_E_INVALID, "count too large");
-    polymul_kernel<<<(unsigned)blocks, kThreads, smem, stream>>>(
-        a, b, out, count, p, k, log2_q, qneg, make_div64(p), plain_f64 ? 1 : 0);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem) !=
+            cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    int64_t blocks = (count + kThreads - 1) / kThreads;
+    blocks = std::min<int64_t>(blocks, (int64_t)sms * per_sm);
+    kern<<<(unsigned)blocks, kThreads, smem, stream>>>(a, b, out, count, p, k, log2_q, qneg,
+                                                       make_div64(p));
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(QADIC_E_CUDA, "polymul launch: %s", cudaGetErrorString(e));
     return QADIC_OK;

@@ -60,7 +60,9 @@ constexpr uint32_t kSpinLimit = 1u << 26;
 // ------------------------------------------------------------ launchers --
 // Each returns a qadic_status after enqueueing on `stream`.
 
-int launch_polymul(uint32_t p, uint32_t k, uint32_t log2_q, bool plain_f64, const uint8_t *a,
+// mode 0: exact FP64 product (hi + lo), 1: single-rounded FP64 product,
+// 2: 64-bit integer words.
+int launch_polymul(uint32_t p, uint32_t k, uint32_t log2_q, int mode, const uint8_t *a,
                    const uint8_t *b, uint8_t *out, int64_t count, cudaStream_t stream);
 
 int launch_redq(uint32_t p, uint32_t log2_q, uint32_t ndigits, const double *in, double *out,
@@ -96,6 +98,17 @@ int launch_gemm_planes_tc_strided(const Field &f, int64_t m, int64_t n, int64_t 
                                   int64_t c_plane, cudaStream_t stream);
 
 bool gemm_planes_tc_supported(const Field &f);
+
+// Fold-before form: rows of one output block in an OPERAND_B_FOLD plane.
+inline int64_t fold_n_pad(int64_t n) { return (n + 255) / 256 * 256; }
+
+int launch_gemm_karatsuba_tc(const Field &f, int64_t m, int64_t n, int64_t K, const void *A,
+                             int64_t lda, const void *B, int64_t ldb, uint8_t *C, int64_t ldc,
+                             cudaStream_t stream);
+
+int launch_gemm_fold_tc(const Field &f, int64_t m, int64_t n, int64_t K, const void *A,
+                        int64_t lda, const void *B, int64_t ldb, uint8_t *C, int64_t ldc,
+                        cudaStream_t stream);
 
 size_t batched_workspace_size(const qadic_gemm_desc *descs, int64_t count);
 

@@ -226,6 +226,16 @@ def test_batched_tile_table_and_selection():
     assert q.batched_selected_tiles(2) == 0
 
 
+def test_fold_format_and_path_constants_match_header():
+    h = open(os.path.join(os.path.dirname(__file__), "..", "include", "qadic.h")).read()
+    assert re.search(r"QADIC_FMT_OPERAND_B_FOLD = 6", h) and q.FMT_OPERAND_B_FOLD == 6
+    assert re.search(r"QADIC_PATH_FOLD = 2", h) and q.PATH_FOLD == 2
+    assert q.fold_n_pad(1) == 256 and q.fold_n_pad(256) == 256 and q.fold_n_pad(257) == 512
+    assert re.search(r"QADIC_FMT_OPERAND_A_KARA = 7", h) and q.FMT_OPERAND_A_KARA == 7
+    assert re.search(r"QADIC_FMT_OPERAND_B_KARA = 8", h) and q.FMT_OPERAND_B_KARA == 8
+    assert re.search(r"QADIC_PATH_KARATSUBA = 3", h) and q.PATH_KARATSUBA == 3
+
+
 def test_zero_counts_are_noops():
     L = q.lib()
     assert L.qadic_redq(7, 10, 5, None, None, 0, 3, None) == q.OK

@@ -26,12 +26,26 @@ def host(t):
 
 # ------------------------------------------------------------ polymul ----
 
-@pytest.mark.parametrize("count", [1, 255, 257, 4099, 65536])
-def test_polymul_config1(torch, orc, count):
+@pytest.mark.parametrize("int_words", [False, True])
+@pytest.mark.parametrize("count", [1, 255, 257, 4099, 65536, 1 << 20])
+def test_polymul_config1(torch, orc, count, int_words):
     a, b = W.polymul_pairs(count, 7, 4, salt=count)
-    out = q.polymul_batched(7, 4, dev(torch, a), dev(torch, b))
+    out = q.polymul_batched(7, 4, dev(torch, a), dev(torch, b), int_words=int_words)
     torch.cuda.synchronize()
     assert np.array_equal(host(out), orc.polymul(7, a, b))
+
+
+def test_polymul_unaligned_inputs(torch, orc):
+    """Operands one byte off a 4-byte boundary take the byte-load path."""
+    a, b = W.polymul_pairs(5001, 7, 4, salt=3)
+    da = torch.zeros(a.size + 1, dtype=torch.uint8, device="cuda")
+    db = torch.zeros(b.size + 1, dtype=torch.uint8, device="cuda")
+    da[1:] = dev(torch, a.ravel())
+    db[1:] = dev(torch, b.ravel())
+    for int_words in (False, True):
+        out = q.polymul_batched(7, 4, da[1:].view(5001, 4), db[1:].view(5001, 4),
+                                int_words=int_words)
+        assert np.array_equal(host(out), orc.polymul(7, a, b))
 
 
 def test_polymul_example1(torch):
@@ -43,9 +57,10 @@ def test_polymul_example1(torch):
 @pytest.mark.parametrize("p,k", [(3, 3), (2, 8), (31, 2), (251, 2), (5, 5), (101, 2)])
 def test_polymul_other_rings(torch, orc, p, k):
     a, b = W.polymul_pairs(3000, p, k, salt=p * 10 + k)
-    for plain in (False, True):
+    for plain, ints in ((False, False), (True, False), (False, True)):
         try:
-            out = q.polymul_batched(p, k, dev(torch, a), dev(torch, b), plain_f64=plain)
+            out = q.polymul_batched(p, k, dev(torch, a), dev(torch, b), plain_f64=plain,
+                                    int_words=ints)
         except q.QadicError as e:
             assert plain and e.status == q.E_OVERFLOW
             continue
@@ -54,8 +69,9 @@ def test_polymul_other_rings(torch, orc, p, k):
 
 def test_polymul_all_max(torch, orc):
     a = np.full((1000, 4), 6, np.uint8)
-    out = q.polymul_batched(7, 4, dev(torch, a), dev(torch, a))
-    assert np.array_equal(host(out), orc.polymul(7, a, a))
+    for int_words in (False, True):
+        out = q.polymul_batched(7, 4, dev(torch, a), dev(torch, a), int_words=int_words)
+        assert np.array_equal(host(out), orc.polymul(7, a, a))
 
 
 # --------------------------------------------------------------- REDQ ----
@@ -404,3 +420,155 @@ def test_matmul_host_end_to_end(torch, orc, path, shape):
 
 def test_sync_status_clean(torch):
     q.sync_status()
+
+
+# ------------------------------------------------------- fold-before form ----
+
+def fold_operands(torch, f, A, B, m, n, K):
+    """Coefficient planes (k, m, K) and (k, K, n) -> OPERAND_A, OPERAND_B_FOLD."""
+    lda = (K + 7) // 8 * 8
+    a = f.pack(q.FMT_COEFF_U8, dev(torch, A), m, K, q.FMT_OPERAND_A,
+               out=torch.zeros((f.k, m, lda), dtype=torch.bfloat16, device="cuda"), ld_out=lda)
+    b = f.pack(q.FMT_COEFF_U8, dev(torch, B), K, n, q.FMT_OPERAND_B_FOLD)
+    return a, b, lda
+
+
+@pytest.mark.parametrize("pk", [(101, 1), (31, 2), (101, 2), (3, 3), (7, 4), (5, 5), (2, 6), (3, 7),
+                                (2, 8)])
+@pytest.mark.parametrize("shape", [(130, 70, 45), (300, 257, 200), (128, 512, 64), (1, 1, 1)])
+def test_fold_path_against_oracle(torch, orc, pk, shape):
+    p, k = pk
+    m, n, K = shape
+    f = q.Field(p, k)
+    rng = np.random.default_rng(p * 31 + k + m)
+    A = rng.integers(0, p, (k, m, K), dtype=np.uint8)
+    B = rng.integers(0, p, (k, K, n), dtype=np.uint8)
+    a, b, lda = fold_operands(torch, f, A, B, m, n, K)
+    C = f.gemm(q.PATH_FOLD, a, b, m, n, K, lda=lda).cpu().numpy()
+    want = orc.gemm(p, f.poly, np.transpose(A, (1, 2, 0)), np.transpose(B, (1, 2, 0)))
+    assert np.array_equal(np.transpose(C, (1, 2, 0)), want)
+
+
+def test_fold_operand_is_the_multiplication_matrix(torch, orc):
+    """Plane i, block j of OPERAND_B_FOLD = coefficient j of b X^i mod P
+    (centred), checked element by element with the oracle's field product;
+    padding rows are zero."""
+    for p, k in [(7, 4), (3, 3), (2, 8)]:
+        f = q.Field(p, k)
+        K, n = 19, 37
+        B = np.random.default_rng(p).integers(0, p, (k, K, n), dtype=np.uint8)
+        out = f.pack(q.FMT_COEFF_U8, dev(torch, B), K, n, q.FMT_OPERAND_B_FOLD).float().cpu().numpy()
+        n_pad = q.fold_n_pad(n)
+        assert out.shape == (k, k * n_pad, 24)
+        for i in range(k):
+            xi = [0] * k
+            if i < k:
+                xi[i] = 1
+            for r in range(0, K, 5):
+                for c in range(0, n, 3):
+                    prod = orc.field_mul(p, f.poly, [int(B[l, r, c]) for l in range(k)], xi)
+                    for j in range(k):
+                        assert int(out[i, j * n_pad + c, r]) % p == prod[j], (p, k, i, j, r, c)
+                        assert abs(int(out[i, j * n_pad + c, r])) <= max(1, (p - 1) // 2)
+            assert not out[i, :, :K].reshape(k, n_pad, K)[:, n:, :].any()
+
+
+def test_fold_equals_plane_path(torch):
+    for pk, (m, n, K) in [((101, 2), (640, 384, 512)), ((13, 3), (256, 200, 300)),
+                          ((7, 4), (300, 128, 640))]:
+        f = q.Field(*pk)
+        rng = np.random.default_rng(pk[0])
+        A = rng.integers(0, pk[0], (f.k, m, K), dtype=np.uint8)
+        B = rng.integers(0, pk[0], (f.k, K, n), dtype=np.uint8)
+        a, b, lda = fold_operands(torch, f, A, B, m, n, K)
+        C1 = f.gemm(q.PATH_FOLD, a, b, m, n, K, lda=lda)
+        bp = f.pack(q.FMT_COEFF_U8, dev(torch, B), K, n, q.FMT_OPERAND_B,
+                    out=torch.zeros((f.k, n, lda), dtype=torch.bfloat16, device="cuda"), ld_out=lda)
+        C2 = f.gemm(q.PATH_PLANES, a, bp, m, n, K, lda=lda, ldb=lda)
+        assert torch.equal(C1, C2), pk
+
+
+def test_fold_exact_chunks_p251(torch, orc):
+    """GF(251^2), all coefficients -125, K = 2000: every accumulator crosses
+    one in-place reduction (exact chunk 1073 -> 16 K-blocks)."""
+    f = q.Field(251, 2)
+    m, n, K = 256, 300, 2000
+    A = np.full((2, m, K), 126, np.uint8)
+    B = np.full((2, K, n), 126, np.uint8)
+    B[1, ::3, ::5] = 7
+    a, b, lda = fold_operands(torch, f, A, B, m, n, K)
+    C = f.gemm(q.PATH_FOLD, a, b, m, n, K, lda=lda).cpu().numpy()
+    rows = np.array([0, 1, 100, 255])
+    want = orc.gemm(251, f.poly, np.transpose(A[:, rows], (1, 2, 0)), np.transpose(B, (1, 2, 0)))
+    assert np.array_equal(np.transpose(C[:, rows], (1, 2, 0)), want)
+
+
+# ------------------------------------------------------- Karatsuba (k = 2) ----
+
+def kara_operands(torch, f, A, B, m, n, K):
+    ld = (K + 7) // 8 * 8
+    a = f.pack(q.FMT_COEFF_U8, dev(torch, A), m, K, q.FMT_OPERAND_A_KARA,
+               out=torch.zeros((3, m, ld), dtype=torch.bfloat16, device="cuda"), ld_out=ld)
+    b = f.pack(q.FMT_COEFF_U8, dev(torch, B), K, n, q.FMT_OPERAND_B_KARA,
+               out=torch.zeros((3, n, ld), dtype=torch.bfloat16, device="cuda"), ld_out=ld)
+    return a, b, ld
+
+
+@pytest.mark.parametrize("p", [2, 3, 31, 101, 251])
+@pytest.mark.parametrize("shape", [(130, 70, 45), (300, 257, 200), (128, 512, 64), (1, 1, 1),
+                                   (256, 128, 3000)])
+def test_karatsuba_against_oracle(torch, orc, p, shape):
+    m, n, K = shape
+    f = q.Field(p, 2)
+    rng = np.random.default_rng(p + m + K)
+    A = rng.integers(0, p, (2, m, K), dtype=np.uint8)
+    B = rng.integers(0, p, (2, K, n), dtype=np.uint8)
+    a, b, ld = kara_operands(torch, f, A, B, m, n, K)
+    C = f.gemm(q.PATH_KARATSUBA, a, b, m, n, K, lda=ld, ldb=ld).cpu().numpy()
+    if m * n * K > 4e7:
+        rows = np.arange(0, m, 17)
+        want = orc.gemm(p, f.poly, np.transpose(A[:, rows], (1, 2, 0)), np.transpose(B, (1, 2, 0)))
+        assert np.array_equal(np.transpose(C[:, rows], (1, 2, 0)), want)
+    else:
+        want = orc.gemm(p, f.poly, np.transpose(A, (1, 2, 0)), np.transpose(B, (1, 2, 0)))
+        assert np.array_equal(np.transpose(C, (1, 2, 0)), want)
+
+
+def test_karatsuba_operand_planes(torch, orc):
+    f = q.Field(101, 2)
+    A = np.random.default_rng(1).integers(0, 101, (2, 37, 29), dtype=np.uint8)
+    a = f.pack(q.FMT_COEFF_U8, dev(torch, A), 37, 29, q.FMT_OPERAND_A_KARA,
+               out=torch.zeros((3, 37, 32), dtype=torch.bfloat16, device="cuda"), ld_out=32)
+    b = f.pack(q.FMT_COEFF_U8, dev(torch, A), 37, 29, q.FMT_OPERAND_B_KARA,
+               out=torch.zeros((3, 29, 40), dtype=torch.bfloat16, device="cuda"), ld_out=40)
+    want = np.stack([orc.centred(A[0], 101), orc.centred(A[1], 101),
+                     orc.centred(A[0].astype(int) + A[1], 101)])
+    assert np.array_equal(a.float().cpu().numpy()[:, :, :29], want)
+    assert np.array_equal(b.float().cpu().numpy()[:, :, :37], np.transpose(want, (0, 2, 1)))
+
+
+def test_karatsuba_equals_plane_path_and_worst_case(torch, orc):
+    f = q.Field(251, 2)
+    m, n, K = 384, 256, 2048
+    rng = np.random.default_rng(7)
+    A = rng.choice(np.array([0, 126, 125], np.uint8), (2, m, K))   # centred 0, -125, 125
+    B = rng.choice(np.array([0, 126, 125], np.uint8), (2, K, n))
+    A[:, :64] = 126                      # rows with every D_0, D_2 product at the bound
+    B[:, :, :64] = 126
+    a, b, ld = kara_operands(torch, f, A, B, m, n, K)
+    C1 = f.gemm(q.PATH_KARATSUBA, a, b, m, n, K, lda=ld, ldb=ld)
+    ap = f.pack(q.FMT_COEFF_U8, dev(torch, A), m, K, q.FMT_OPERAND_A)
+    bp = f.pack(q.FMT_COEFF_U8, dev(torch, B), K, n, q.FMT_OPERAND_B)
+    C2 = f.gemm(q.PATH_PLANES, ap, bp, m, n, K)
+    assert torch.equal(C1, C2)
+    rows = np.array([0, 63, 64, 383])
+    want = orc.gemm(251, f.poly, np.transpose(A[:, rows], (1, 2, 0)), np.transpose(B, (1, 2, 0)))
+    assert np.array_equal(np.transpose(C1.cpu().numpy()[:, rows], (1, 2, 0)), want)
+
+
+def test_karatsuba_rejects_other_k(torch):
+    f = q.Field(7, 3)
+    x = torch.zeros((3, 16, 16), dtype=torch.bfloat16, device="cuda")
+    with pytest.raises(q.QadicError) as e:
+        f.gemm(q.PATH_KARATSUBA, x, x, 16, 16, 16)
+    assert e.value.status == q.E_UNSUPPORTED
