@@ -1,7 +1,9 @@
 // C ABI entry points of libqadic (declared in include/qadic.h): argument
 // and bound checks on the host, field lifetime, dispatch to the kernels.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -293,15 +295,35 @@ int qadic_matmul_host(const qadic_field *field, int path, int in_fmt, int64_t m,
     if (path == QADIC_PATH_PLANES && !gemm_planes_tc_supported(f))
         return set_error(QADIC_E_UNSUPPORTED, "no tensor-core plane kernel for k=%u", f.k);
 
-    // Overlap: the inputs are copied on a side stream (A, then B), so A is
-    // packed while B is still on its way; the plane GEMM runs as two row
-    // halves and the top half of C is copied back while the bottom half is
-    // computed.  Everything is joined back into `stream` before returning.
-    int dev = 0;
+    // Overlap.  The inputs go host -> device on a side stream, B first and
+    // then A in two row blocks; the plane GEMM runs per row block as soon as
+    // B and that block of A are packed, and the first block of C goes back
+    // to the host while the second is computed.  The split point keeps the
+    // two GEMMs at the wave count of one GEMM over all rows (one cluster of
+    // two CTAs per two SMs).  Everything is joined into `stream` at the end.
+    int dev = 0, sms = 0;
     cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaStream_t side = side_stream(dev);
     if (!side) return set_error(QADIC_E_CUDA, "no side stream");
-    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    int64_t mh = m;   // rows of the first block
+    if (path == QADIC_PATH_PLANES && m >= 512) {
+        const int64_t unit_rows = 256, um = (m + unit_rows - 1) / unit_rows;
+        const int64_t tn = (n + 127) / 128, cl = std::max(1, sms / 2);
+        int64_t best = -1, best_cost = 0;
+        for (int64_t ur = std::max<int64_t>(1, um / 3); ur <= (2 * um) / 3; ++ur) {
+            const int64_t cost = (ur * tn + cl - 1) / cl + ((um - ur) * tn + cl - 1) / cl;
+            const int64_t dist = std::llabs(20 * ur - 11 * um);   // prefer ~0.55 of the rows
+            if (best < 0 || cost < best_cost ||
+                (cost == best_cost && dist < std::llabs(20 * best - 11 * um))) {
+                best = ur;
+                best_cost = cost;
+            }
+        }
+        if (best > 0) mh = std::min<int64_t>(m, best * unit_rows);
+    }
+    const int64_t mb = m - mh;   // rows of the second block (0: one block)
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     for (auto &e : ev)
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
             for (auto &x : ev)
@@ -316,53 +338,72 @@ int qadic_matmul_host(const qadic_field *field, int path, int in_fmt, int64_t m,
         return cleanup(set_error(QADIC_E_CUDA, "%s: %s", what, cudaGetErrorString(cudaGetLastError())));
     };
     const size_t c_plane = (size_t)m * n;
+    // Host A is `planes` planes of m x K elements of `esz` bytes; the device
+    // copy holds block 1 (rows < mh) then block 2, each as its own planes.
+    const bool planar = in_fmt != QADIC_FMT_LOG;
+    const uint32_t planes = planar ? f.k : 1;
+    const size_t esz = planar ? 1 : eb;
+    char *dA2 = dA + (size_t)planes * mh * K * esz;
+    auto copy_rows = [&](char *dst, int64_t r0, int64_t rows) -> cudaError_t {
+        for (uint32_t i = 0; i < planes; ++i) {
+            const cudaError_t e = cudaMemcpyAsync(
+                dst + (size_t)i * rows * K * esz,
+                (const char *)A_host + ((size_t)i * m + r0) * K * esz, (size_t)rows * K * esz,
+                cudaMemcpyHostToDevice, side);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    };
     // side stream starts after everything already queued on `stream`
     if (cudaEventRecord(ev[0], s) || cudaStreamWaitEvent(side, ev[0], 0) ||
-        cudaMemcpyAsync(dA, A_host, eb * m * K, cudaMemcpyHostToDevice, side) ||
-        cudaEventRecord(ev[1], side) ||
         cudaMemcpyAsync(dB, B_host, eb * K * n, cudaMemcpyHostToDevice, side) ||
-        cudaEventRecord(ev[2], side) || cudaStreamWaitEvent(s, ev[1], 0))
+        cudaEventRecord(ev[1], side) || copy_rows(dA, 0, mh) || cudaEventRecord(ev[2], side) ||
+        (mb > 0 && copy_rows(dA2, mh, mb)) || cudaEventRecord(ev[3], side))
         return cuda_fail("H2D copy");
     int st;
     const int opA = path == QADIC_PATH_FP64_QADIC ? QADIC_FMT_QADIC_F64 : QADIC_FMT_OPERAND_A;
     const int opB = path == QADIC_PATH_FP64_QADIC ? QADIC_FMT_QADIC_F64 : QADIC_FMT_OPERAND_B;
-    if ((st = qadic_pack(field, in_fmt, dA, m, K, K, opA, pA, K, stream))) return cleanup(st);
-    if (cudaStreamWaitEvent(s, ev[2], 0)) return cuda_fail("wait");
+    const size_t pa_elem = path == QADIC_PATH_FP64_QADIC ? 8 : 2 * (size_t)f.k;
+    char *pA2 = pA + pa_elem * mh * K;
+    if (cudaStreamWaitEvent(s, ev[1], 0)) return cuda_fail("wait");
     if ((st = qadic_pack(field, in_fmt, dB, K, n, n, opB, pB, path == QADIC_PATH_FP64_QADIC ? n : K,
                          stream)))
         return cleanup(st);
-    const int64_t mh = (path == QADIC_PATH_PLANES && m >= 512) ? (m / 2 + 127) / 128 * 128 : m;
+    if (cudaStreamWaitEvent(s, ev[2], 0)) return cuda_fail("wait");
+    if ((st = qadic_pack(field, in_fmt, dA, mh, K, K, opA, pA, K, stream))) return cleanup(st);
     if (path == QADIC_PATH_FP64_QADIC) {
         if ((st = qadic_gemm(field, path, m, n, K, pA, K, pB, n, dC, n, nullptr, 0, stream)))
             return cleanup(st);
     } else {
-        const uint16_t *a16 = (const uint16_t *)pA;
-        if ((st = launch_gemm_planes_tc_strided(f, mh, n, K, a16, K, (int64_t)m * K, pB, K,
+        if ((st = launch_gemm_planes_tc_strided(f, mh, n, K, pA, K, (int64_t)mh * K, pB, K,
                                                 (int64_t)n * K, dC, n, (int64_t)c_plane, s)))
             return cleanup(st);
-        if (mh < m) {
-            if (cudaEventRecord(ev[3], s) || cudaStreamWaitEvent(side, ev[3], 0))
+        if (mb > 0) {
+            if (cudaEventRecord(ev[4], s) || cudaStreamWaitEvent(side, ev[4], 0))
                 return cuda_fail("event");
             for (uint32_t i = 0; i < f.k; ++i)
                 if (cudaMemcpyAsync(C_host + i * c_plane, dC + i * c_plane, (size_t)mh * n,
                                     cudaMemcpyDeviceToHost, side))
                     return cuda_fail("D2H copy");
-            if ((st = launch_gemm_planes_tc_strided(f, m - mh, n, K, a16 + mh * K, K,
-                                                    (int64_t)m * K, pB, K, (int64_t)n * K,
-                                                    dC + mh * n, n, (int64_t)c_plane, s)))
+            if (cudaStreamWaitEvent(s, ev[3], 0)) return cuda_fail("wait");
+            if ((st = qadic_pack(field, in_fmt, dA2, mb, K, K, opA, pA2, K, stream)))
+                return cleanup(st);
+            if ((st = launch_gemm_planes_tc_strided(f, mb, n, K, pA2, K, (int64_t)mb * K, pB, K,
+                                                    (int64_t)n * K, dC + mh * n, n,
+                                                    (int64_t)c_plane, s)))
                 return cleanup(st);
         }
     }
-    if (mh < m) {   // bottom half of every plane
+    if (mb > 0) {   // second block of every plane
         for (uint32_t i = 0; i < f.k; ++i)
             if (cudaMemcpyAsync(C_host + i * c_plane + mh * n, dC + i * c_plane + mh * n,
-                                (size_t)(m - mh) * n, cudaMemcpyDeviceToHost, s))
+                                (size_t)mb * n, cudaMemcpyDeviceToHost, s))
                 return cuda_fail("D2H copy");
     } else if (cudaMemcpyAsync(C_host, dC, (size_t)f.k * m * n, cudaMemcpyDeviceToHost, s)) {
         return cuda_fail("D2H copy");
     }
     // join: `stream` also waits for the side stream's copies
-    if (cudaEventRecord(ev[4], side) || cudaStreamWaitEvent(s, ev[4], 0)) return cuda_fail("join");
+    if (cudaEventRecord(ev[5], side) || cudaStreamWaitEvent(s, ev[5], 0)) return cuda_fail("join");
     return cleanup(QADIC_OK);
 }
 

@@ -52,7 +52,8 @@ struct FqtParams {
     uint32_t Dq;            // words per input, minus one
     uint32_t chunk;         // products per accumulator between reductions
     uint32_t piece;         // i-range length of one work item (multiple of chunk)
-    uint32_t pieces;        // pieces per block of output words
+    uint32_t npc;           // pieces of the i range [0, Dq], cut at multiples of piece
+    uint32_t span;          // work items per piece (t-blocks that may meet it)
     uint32_t nblocks;       // blocks of kTB output words
     uint32_t qneg, m32;
     double inv_p_up;
@@ -117,14 +118,21 @@ polymul_fqt_kernel(const uint8_t *__restrict__ a, const uint8_t *__restrict__ b,
         for (uint32_t i = threadIdx.x; i < nR; i += blockDim.x) R[i] = 0;
         __syncthreads();
 
-        const uint32_t slots = P.nblocks * P.pieces;
+        // Work items: (piece pc of the i range, cut at multiples of `piece`,
+        // block of kTB output words meeting it).  Consecutive threads take
+        // consecutive word blocks of one piece, so most lanes of a warp run
+        // exactly `piece` steps; only the blocks at the two edges of a
+        // piece's range (the sides of the triangle i <= t, t - i <= Dq) do
+        // less.
+        const uint32_t slots = P.npc * P.span;
         for (uint32_t it = threadIdx.x; it < slots; it += blockDim.x) {
-            const int t0 = (int)(it / P.pieces) * kTB;
-            const int pc = (int)(it % P.pieces);
-            const int ilo = max(0, t0 - (int)Dq) + pc * (int)P.piece;
-            const int ihi = min(t0 + kTB - 1, (int)Dq);
-            if (ilo > ihi) continue;
-            const int iend = min(ihi, ilo + (int)P.piece - 1);
+            const int pc = (int)(it / P.span);
+            const int tb = max(0, pc * (int)P.piece / kTB - 1) + (int)(it % P.span);
+            if (tb >= (int)P.nblocks) continue;
+            const int t0 = tb * kTB;
+            const int ilo = max(max(0, t0 - (int)Dq), pc * (int)P.piece);
+            const int iend = min(min(t0 + kTB - 1, (int)Dq), (pc + 1) * (int)P.piece - 1);
+            if (ilo > iend) continue;
             // window: qv[tt] = Q_{t0+tt-i}, zero outside [0, Dq]
             Word qv[kTB];
 #pragma unroll
@@ -231,9 +239,10 @@ int launch_polymul_fqt(uint32_t p, uint32_t N, uint32_t d, bool int_words, const
     // reduction it adds is cheap next to the multiply-adds.
     P.chunk = std::min<uint32_t>(I.n_q, 32);
     P.piece = P.chunk * std::max<uint32_t>(1, 32 / P.chunk);
-    const uint32_t span = I.D_q + kTB;   // longest i range of a block
-    P.pieces = (span + P.piece - 1) / P.piece;
     P.nblocks = (2 * I.D_q + 1 + kTB - 1) / kTB;
+    P.npc = (I.D_q + P.piece) / P.piece;   // ceil((D_q + 1) / piece)
+    // blocks meeting piece pc: t0 in [pc piece - (kTB - 1), (pc + 1) piece - 1 + D_q]
+    P.span = (P.piece + I.D_q) / kTB + 3;
     P.qneg = (uint32_t)((p - (uint32_t)((1ull << I.log2_q) % p)) % p);
     P.m32 = make_mod_small(p);
     P.divp = make_div64(p);

@@ -400,7 +400,7 @@ def test_fp64_and_planes_agree_config3_slice(torch, orc):
                                         (q.PATH_FP64_QADIC, (130, 70, 45))])
 def test_matmul_host_end_to_end(torch, orc, path, shape):
     """qadic_matmul_host from pinned host buffers (copies overlapped with the
-    pack, the plane GEMM in two row halves when m >= 512) against the oracle."""
+    pack, the plane GEMM in two row blocks when m >= 512) against the oracle."""
     m, n, K = shape
     p, k = 101, 2
     f = q.Field(p, k)
@@ -416,6 +416,28 @@ def test_matmul_host_end_to_end(torch, orc, path, shape):
         f.matmul_host(path, q.FMT_INT8_PLANES, hA, hB, hC, m, n, K, ws)
         torch.cuda.synchronize()
         assert np.array_equal(hC.numpy(), oracle_gemm_from_planes(orc, p, f.poly, A, B))
+
+
+@pytest.mark.parametrize("pk,shape", [((101, 2), (1100, 130, 72)), ((3, 3), (768, 64, 40)),
+                                      ((7, 4), (520, 33, 16))])
+def test_matmul_host_log_codes_split(torch, orc, pk, shape):
+    """Log-coded host inputs (2-byte codes for GF(101^2), 1-byte otherwise)
+    through the two-block host pipeline: B first, A in two row blocks."""
+    p, k = pk
+    m, n, K = shape
+    f = q.Field(p, k)
+    LA = W.log_matrix(m, K, f.order, salt=41)
+    LB = W.log_matrix(K, n, f.order, salt=42)
+    hA = torch.from_numpy(LA).pin_memory()
+    hB = torch.from_numpy(LB).pin_memory()
+    hC = torch.full((k, m, n), 255, dtype=torch.uint8).pin_memory()
+    ws = torch.empty(f.matmul_workspace_size(q.PATH_PLANES, q.FMT_LOG, m, n, K),
+                     dtype=torch.uint8, device="cuda")
+    f.matmul_host(q.PATH_PLANES, q.FMT_LOG, hA, hB, hC, m, n, K, ws)
+    torch.cuda.synchronize()
+    T = orc.antilog(p, f.poly)
+    want = orc.gemm(p, f.poly, T[LA.astype(np.int64)], T[LB.astype(np.int64)])
+    assert np.array_equal(np.transpose(hC.numpy(), (1, 2, 0)), want)
 
 
 def test_sync_status_clean(torch):
