@@ -188,6 +188,31 @@ int qadic_gemm(const qadic_field *field, int path, int64_t m, int64_t n, int64_t
                const void *A, int64_t lda, const void *B, int64_t ldb, uint8_t *C, int64_t ldc,
                void *workspace, size_t ws_bytes, void *stream);
 
+/* ------------------------------------------------------- pack_operands --
+ * Both operands of the plane path at once: A (m x K) -> OPERAND_A (outA,
+ * lda_out) and B (K x n) -> OPERAND_B (outB, ldb_out), as two qadic_pack
+ * calls would.  Coefficient-plane inputs with K % 16 == 0, n % 64 == 0 and
+ * 16-byte aligned rows are packed by ONE launch; other inputs by two.
+ * lda_out, ldb_out >= K, multiples of 8; 16-byte aligned outputs. */
+int qadic_pack_operands(const qadic_field *field, int in_fmt, const void *A, int64_t m, int64_t K,
+                        int64_t lda_in, void *outA, int64_t lda_out, const void *B, int64_t n,
+                        int64_t ldb_in, void *outB, int64_t ldb_out, void *stream);
+
+/* ----------------------------------------------------------------- matmul --
+ * The whole path on device operands in one call: A (m x K) and B (K x n) in
+ * in_fmt (LOG, COEFF_U8 or INT8_PLANES; lda, ldb element strides per row,
+ * planes of a plane format `rows * ld` elements apart), packed into
+ * `workspace` (device, 256-byte aligned, at least
+ * qadic_matmul_device_workspace_size bytes) and multiplied with `path`
+ * (any of the four); C: k planes of uint8, m x n (ldc).  For the plane path
+ * with plane inputs both operands are packed by one launch.  Errors as for
+ * qadic_pack and qadic_gemm, QADIC_E_NOMEM for a short workspace. */
+size_t qadic_matmul_device_workspace_size(const qadic_field *field, int path, int64_t m,
+                                          int64_t n, int64_t K);
+int qadic_matmul(const qadic_field *field, int path, int in_fmt, int64_t m, int64_t n, int64_t K,
+                 const void *A, int64_t lda, const void *B, int64_t ldb, uint8_t *C, int64_t ldc,
+                 void *workspace, size_t ws_bytes, void *stream);
+
 /* ------------------------------------------------------------ matmul_host --
  * End-to-end convenience: A (m x K) and B (K x n) in in_fmt (LOG, COEFF_U8 or
  * INT8_PLANES) in HOST memory (pinned for asynchrony), C (k planes of uint8,

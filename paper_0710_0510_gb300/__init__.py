@@ -81,6 +81,19 @@ _SIGS = {
                                   ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                   ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                   ctypes.c_size_t, ctypes.c_void_p]),
+    "qadic_pack_operands": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                           ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                           ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                           ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
+                                           ctypes.c_int64, ctypes.c_void_p]),
+    "qadic_matmul_device_workspace_size": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int,
+                                                             ctypes.c_int64, ctypes.c_int64,
+                                                             ctypes.c_int64]),
+    "qadic_matmul": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                                    ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
+                                    ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                    ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                    ctypes.c_size_t, ctypes.c_void_p]),
     "qadic_matmul_workspace_size": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                                       ctypes.c_int64, ctypes.c_int64,
                                                       ctypes.c_int64]),
@@ -258,6 +271,31 @@ class Field:
             ldc = n
         _check(lib().qadic_gemm(self._h, path, m, n, K, _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc,
                                 None, 0, _stream(stream)))
+        return C
+
+    def pack_operands(self, in_fmt: int, A, B, m: int, n: int, K: int, outA, outB,
+                      lda_in=None, ldb_in=None, lda_out=None, ldb_out=None, stream=None):
+        """A -> OPERAND_A and B -> OPERAND_B in one call (``qadic_pack_operands``)."""
+        _check(lib().qadic_pack_operands(
+            self._h, in_fmt, _ptr(A), m, K, K if lda_in is None else lda_in, _ptr(outA),
+            outA.shape[-1] if lda_out is None else lda_out, _ptr(B), n,
+            n if ldb_in is None else ldb_in, _ptr(outB),
+            outB.shape[-1] if ldb_out is None else ldb_out, _stream(stream)))
+        return outA, outB
+
+    def matmul_device_workspace_size(self, path: int, m: int, n: int, K: int) -> int:
+        return int(lib().qadic_matmul_device_workspace_size(self._h, path, m, n, K))
+
+    def matmul(self, path: int, in_fmt: int, A, B, m: int, n: int, K: int, workspace, C=None,
+               lda=None, ldb=None, ldc=None, stream=None):
+        """Pack + GEMM on device operands in one call (``qadic_matmul``)."""
+        torch = _torch()
+        if C is None:
+            C = torch.empty((self.k, m, n), dtype=torch.uint8, device=A.device)
+        _check(lib().qadic_matmul(self._h, path, in_fmt, m, n, K, _ptr(A),
+                                  K if lda is None else lda, _ptr(B), n if ldb is None else ldb,
+                                  _ptr(C), n if ldc is None else ldc, _ptr(workspace),
+                                  workspace.numel() * workspace.element_size(), _stream(stream)))
         return C
 
     def matmul_workspace_size(self, path: int, in_fmt: int, m: int, n: int, K: int) -> int:

@@ -244,6 +244,110 @@ int qadic_gemm(const qadic_field *field, int path, int64_t m, int64_t n, int64_t
     return set_error(QADIC_E_INVALID, "unknown path %d", path);
 }
 
+static size_t align256_(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Bytes of the two packed operands of qadic_matmul (bf16 rows padded to a
+// multiple of 8 elements, so every layout meets the 16-byte TMA rules).
+static size_t packed_bytes(const Field &f, int path, int64_t m, int64_t n, int64_t K,
+                           size_t *a_bytes) {
+    const size_t K8 = (size_t)((K + 7) / 8 * 8);
+    size_t a = 0, b = 0;
+    switch (path) {
+        case QADIC_PATH_FP64_QADIC: a = 8 * (size_t)m * K; b = 8 * (size_t)K * n; break;
+        case QADIC_PATH_PLANES: a = 2 * (size_t)f.k * m * K8; b = 2 * (size_t)f.k * n * K8; break;
+        case QADIC_PATH_FOLD:
+            a = 2 * (size_t)f.k * m * K8;
+            b = 2 * (size_t)f.k * f.k * (size_t)fold_n_pad(n) * K8;
+            break;
+        case QADIC_PATH_KARATSUBA: a = 6 * (size_t)m * K8; b = 6 * (size_t)n * K8; break;
+        default: return 0;
+    }
+    if (a_bytes) *a_bytes = align256_(a);
+    return align256_(a) + align256_(b);
+}
+
+int qadic_pack_operands(const qadic_field *field, int in_fmt, const void *A, int64_t m, int64_t K,
+                        int64_t lda_in, void *outA, int64_t lda_out, const void *B, int64_t n,
+                        int64_t ldb_in, void *outB, int64_t ldb_out, void *stream) {
+    if (!field) return set_error(QADIC_E_INVALID, "field is NULL");
+    const Field &f = field->f;
+    if (!on_device(f)) return set_error(QADIC_E_INVALID, "field lives on another device");
+    if (m < 0 || n < 0 || K < 0) return set_error(QADIC_E_INVALID, "negative size");
+    if (m == 0 || n == 0 || K == 0) return QADIC_OK;
+    if (!A || !B || !outA || !outB) return set_error(QADIC_E_INVALID, "NULL data pointer");
+    if (lda_in < K || ldb_in < n) return set_error(QADIC_E_INVALID, "ld_in too small");
+    if (lda_out < K || ldb_out < K || lda_out % 8 || ldb_out % 8 || ((uintptr_t)outA & 15) ||
+        ((uintptr_t)outB & 15))
+        return set_error(QADIC_E_INVALID, "operand outputs need ld >= K, ld %% 8 == 0, 16B alignment");
+    if (in_fmt == QADIC_FMT_LOG) {
+        int st = qadic_pack(field, in_fmt, A, m, K, lda_in, QADIC_FMT_OPERAND_A, outA, lda_out, stream);
+        if (st != QADIC_OK) return st;
+        return qadic_pack(field, in_fmt, B, K, n, ldb_in, QADIC_FMT_OPERAND_B, outB, ldb_out, stream);
+    }
+    if (in_fmt != QADIC_FMT_COEFF_U8 && in_fmt != QADIC_FMT_INT8_PLANES)
+        return set_error(QADIC_E_INVALID, "input format %d", in_fmt);
+    return launch_pack_pair(f, in_fmt, A, m, K, lda_in, outA, lda_out, B, n, ldb_in, outB, ldb_out,
+                            (cudaStream_t)stream);
+}
+
+size_t qadic_matmul_device_workspace_size(const qadic_field *field, int path, int64_t m, int64_t n,
+                                          int64_t K) {
+    if (!field || m < 0 || n < 0 || K < 0) return 0;
+    return packed_bytes(field->f, path, m, n, K, nullptr);
+}
+
+int qadic_matmul(const qadic_field *field, int path, int in_fmt, int64_t m, int64_t n, int64_t K,
+                 const void *A, int64_t lda, const void *B, int64_t ldb, uint8_t *C, int64_t ldc,
+                 void *workspace, size_t ws_bytes, void *stream) {
+    if (!field) return set_error(QADIC_E_INVALID, "field is NULL");
+    const Field &f = field->f;
+    if (!on_device(f)) return set_error(QADIC_E_INVALID, "field lives on another device");
+    if (m < 0 || n < 0 || K < 0) return set_error(QADIC_E_INVALID, "negative size");
+    if (in_fmt != QADIC_FMT_LOG && in_fmt != QADIC_FMT_COEFF_U8 && in_fmt != QADIC_FMT_INT8_PLANES)
+        return set_error(QADIC_E_INVALID, "input format %d", in_fmt);
+    if (path < QADIC_PATH_FP64_QADIC || path > QADIC_PATH_KARATSUBA)
+        return set_error(QADIC_E_INVALID, "unknown path %d", path);
+    size_t a_bytes = 0;
+    const size_t need = packed_bytes(f, path, m, n, K, &a_bytes);
+    if (m == 0 || n == 0) return QADIC_OK;
+    if (need > 0 && (!workspace || ws_bytes < need))
+        return set_error(QADIC_E_NOMEM, "workspace %zu < %zu bytes", ws_bytes, need);
+    if (((uintptr_t)workspace) & 255) return set_error(QADIC_E_INVALID, "workspace must be 256-byte aligned");
+    char *pA = (char *)workspace, *pB = pA ? pA + a_bytes : nullptr;
+    const int64_t K8 = (K + 7) / 8 * 8;
+    int st;
+    if (!C || ldc < n) return set_error(QADIC_E_INVALID, "C is NULL or ldc < n");
+    if (K == 0) {   // empty sums: C = 0
+        for (uint32_t i = 0; i < f.k; ++i)
+            if (cudaMemset2DAsync(C + (size_t)i * m * ldc, (size_t)ldc, 0, (size_t)n, (size_t)m,
+                                  (cudaStream_t)stream) != cudaSuccess)
+                return set_error(QADIC_E_CUDA, "memset: %s", cudaGetErrorString(cudaGetLastError()));
+        return QADIC_OK;
+    }
+    // (bf16 rows are K8 long; the tensor maps' inner extent is K, so the pad
+    // columns are never read)
+    if (path == QADIC_PATH_PLANES) {
+        if (!gemm_planes_tc_supported(f))
+            return set_error(QADIC_E_UNSUPPORTED, "no tensor-core plane kernel for k=%u", f.k);
+        if (!A || !B) return set_error(QADIC_E_INVALID, "NULL operand");
+        if (lda < K || ldb < n) return set_error(QADIC_E_INVALID, "lda < K or ldb < n");
+        if ((st = qadic_pack_operands(field, in_fmt, A, m, K, lda, pA, K8, B, n, ldb, pB, K8,
+                                      stream)))
+            return st;
+        return qadic_gemm(field, path, m, n, K, pA, K8, pB, K8, C, ldc, nullptr, 0, stream);
+    }
+    int fa, fb;
+    int64_t la, lb;
+    switch (path) {
+        case QADIC_PATH_FP64_QADIC: fa = fb = QADIC_FMT_QADIC_F64; la = K; lb = n; break;
+        case QADIC_PATH_FOLD: fa = QADIC_FMT_OPERAND_A; fb = QADIC_FMT_OPERAND_B_FOLD; la = lb = K8; break;
+        default: fa = QADIC_FMT_OPERAND_A_KARA; fb = QADIC_FMT_OPERAND_B_KARA; la = lb = K8; break;
+    }
+    if ((st = qadic_pack(field, in_fmt, A, m, K, lda, fa, pA, la, stream))) return st;
+    if ((st = qadic_pack(field, in_fmt, B, K, n, ldb, fb, pB, lb, stream))) return st;
+    return qadic_gemm(field, path, m, n, K, pA, la, pB, lb, C, ldc, nullptr, 0, stream);
+}
+
 static size_t in_elem_bytes(const Field &f, int fmt) {
     if (fmt == QADIC_FMT_LOG) return f.order <= 256 ? 1 : 2;
     if (fmt == QADIC_FMT_COEFF_U8 || fmt == QADIC_FMT_INT8_PLANES) return f.k;

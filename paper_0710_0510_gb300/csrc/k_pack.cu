@@ -17,6 +17,8 @@
 // in shared memory so both the reads and the writes are coalesced.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace qadic {
@@ -254,34 +256,57 @@ __device__ __forceinline__ uint32_t centre_pair(uint32_t b0, uint32_t b1, const 
 }
 
 template <int IN>
-__global__ void __launch_bounds__(256) pack_vec_a(const uint8_t *__restrict__ in,
-                                                  __nv_bfloat16 *__restrict__ out, PackParams P) {
+__device__ __forceinline__ void convert16(uint4 w, const PackParams &P, uint32_t (&o)[8]) {
+    const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        o[2 * q] = centre_pair<IN>(words[q] & 0xff, (words[q] >> 8) & 0xff, P);
+        o[2 * q + 1] = centre_pair<IN>((words[q] >> 16) & 0xff, words[q] >> 24, P);
+    }
+}
+
+// Same layout: unit u = 16 consecutive coefficients of one row of one plane.
+// Four independent 16-byte loads in flight per thread; the unit -> (row,
+// chunk) split uses 32-bit division whenever the unit count allows.
+template <int IN>
+__device__ __forceinline__ void vec_a_body(const uint8_t *__restrict__ in,
+                                           __nv_bfloat16 *__restrict__ out, const PackParams &P,
+                                           int64_t block, int64_t nblocks) {
+    constexpr int U = 4;
     const int64_t per_row = P.cols / 16;
     const int64_t units = (int64_t)P.k * P.rows * per_row;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    // two independent 16-byte loads in flight per thread
-    for (int64_t u0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u0 < units; u0 += 2 * stride) {
-        uint4 w[2];
+    const int64_t stride = nblocks * blockDim.x;
+    const bool small = units < (1ll << 31) && per_row < (1ll << 31);
+    const uint32_t pr32 = (uint32_t)per_row;
+    auto split = [&](int64_t u, int64_t &pr, int64_t &c16) {
+        if (small) {
+            const uint32_t uu = (uint32_t)u, q = uu / pr32;
+            pr = q;
+            c16 = uu - q * pr32;
+        } else {
+            pr = u / per_row;
+            c16 = u - pr * per_row;
+        }
+    };
+    for (int64_t u0 = block * blockDim.x + threadIdx.x; u0 < units; u0 += U * stride) {
+        uint4 w[U];
 #pragma unroll
-        for (int s = 0; s < 2; ++s) {
+        for (int s = 0; s < U; ++s) {
             const int64_t u = u0 + s * stride;
             if (u < units) {
-                const int64_t c16 = u % per_row, pr = u / per_row;   // pr = plane * rows + row
+                int64_t pr, c16;   // pr = plane * rows + row
+                split(u, pr, c16);
                 w[s] = __ldcs(reinterpret_cast<const uint4 *>(in + pr * P.ld_in + c16 * 16));
             }
         }
 #pragma unroll
-        for (int s = 0; s < 2; ++s) {
+        for (int s = 0; s < U; ++s) {
             const int64_t u = u0 + s * stride;
             if (u >= units) break;
-            const int64_t c16 = u % per_row, pr = u / per_row;
-            const uint32_t words[4] = {w[s].x, w[s].y, w[s].z, w[s].w};
+            int64_t pr, c16;
+            split(u, pr, c16);
             uint32_t o[8];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                o[2 * q] = centre_pair<IN>(words[q] & 0xff, (words[q] >> 8) & 0xff, P);
-                o[2 * q + 1] = centre_pair<IN>((words[q] >> 16) & 0xff, words[q] >> 24, P);
-            }
+            convert16<IN>(w[s], P, o);
             uint4 *dst = reinterpret_cast<uint4 *>(out + pr * P.ld_out + c16 * 16);
             __stcs(dst, make_uint4(o[0], o[1], o[2], o[3]));
             __stcs(dst + 1, make_uint4(o[4], o[5], o[6], o[7]));
@@ -289,55 +314,93 @@ __global__ void __launch_bounds__(256) pack_vec_a(const uint8_t *__restrict__ in
     }
 }
 
-// Transposed operand: a 64 x 64 input tile per block and plane; 16-byte
-// loads along the input rows, 16-byte stores along the output rows.
+template <int IN>
+__global__ void __launch_bounds__(256) pack_vec_a(const uint8_t *__restrict__ in,
+                                                  __nv_bfloat16 *__restrict__ out, PackParams P) {
+    vec_a_body<IN>(in, out, P, blockIdx.x, gridDim.x);
+}
+
+// Transposed operand: a 64 x 64 input tile per block, every plane of it;
+// the k 16-byte loads of a thread are issued together, then each plane goes
+// through the shared-memory transpose and leaves as 16-byte stores along the
+// output rows.
+template <int IN>
+__device__ __forceinline__ void vec_b_body(const uint8_t *__restrict__ in,
+                                           __nv_bfloat16 *__restrict__ out, const PackParams &P,
+                                           int64_t bx, int64_t by, uint16_t (*tile)[64 + 2]) {
+    const int64_t r0 = by * 64, c0 = bx * 64;
+    const int rr = threadIdx.x / 4, cc = (threadIdx.x % 4) * 16;
+    const int64_t r = r0 + rr;
+    // planes in groups of two: both loads of a group are in flight together
+#pragma unroll 1
+    for (int g = 0; g < (int)P.k; g += 2) {
+        uint4 w[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            w[e] = make_uint4(0, 0, 0, 0);
+            if (g + e < (int)P.k && r < P.rows)
+                w[e] = __ldcs(reinterpret_cast<const uint4 *>(
+                    in + ((int64_t)(g + e) * P.rows + r) * P.ld_in + c0 + cc));
+        }
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int plane = g + e;
+            if (plane >= (int)P.k) break;   // block-uniform
+            uint32_t o[8];
+            convert16<IN>(w[e], P, o);
+#pragma unroll
+            for (int x = 0; x < 8; ++x) {
+                tile[rr][cc + 2 * x] = (uint16_t)o[x];
+                tile[rr][cc + 2 * x + 1] = (uint16_t)(o[x] >> 16);
+            }
+            __syncthreads();
+            // output row (input column) oc, 8 consecutive input rows per chunk
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const int idx = threadIdx.x + 256 * s;        // 64 output rows x 8 chunks
+                const int oc = idx / 8, ch = (idx % 8) * 8;
+                uint32_t v[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    v[q] = (uint32_t)tile[ch + 2 * q][oc] | ((uint32_t)tile[ch + 2 * q + 1][oc] << 16);
+                const int64_t orow = c0 + oc, ocol = r0 + ch;
+                if (ocol + 8 <= P.rows) {
+                    *reinterpret_cast<uint4 *>(out + ((int64_t)plane * P.cols + orow) * P.ld_out +
+                                               ocol) = make_uint4(v[0], v[1], v[2], v[3]);
+                } else {
+                    for (int x = 0; x < 8 && ocol + x < P.rows; ++x)
+                        out[((int64_t)plane * P.cols + orow) * P.ld_out + ocol + x] =
+                            __ushort_as_bfloat16((uint16_t)(v[x / 2] >> (16 * (x % 2))));
+                }
+            }
+            __syncthreads();   // the tile is rewritten by the next plane
+        }
+    }
+}
+
 template <int IN>
 __global__ void __launch_bounds__(256) pack_vec_b(const uint8_t *__restrict__ in,
                                                   __nv_bfloat16 *__restrict__ out, PackParams P) {
     __shared__ uint16_t tile[64][64 + 2];
-    const int64_t r0 = (int64_t)blockIdx.y * 64, c0 = (int64_t)blockIdx.x * 64;
-    const int plane = blockIdx.z;
-    {   // load: 64 rows x 4 chunks of 16 bytes, one chunk per thread
-        const int rr = threadIdx.x / 4, cc = (threadIdx.x % 4) * 16;
-        const int64_t r = r0 + rr;
-        uint32_t words[4] = {0, 0, 0, 0};
-        if (r < P.rows) {
-            const uint4 w = __ldcs(reinterpret_cast<const uint4 *>(
-                in + ((int64_t)plane * P.rows + r) * P.ld_in + c0 + cc));
-            words[0] = w.x;
-            words[1] = w.y;
-            words[2] = w.z;
-            words[3] = w.w;
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const uint32_t lo = centre_pair<IN>(words[q] & 0xff, (words[q] >> 8) & 0xff, P);
-            const uint32_t hi = centre_pair<IN>((words[q] >> 16) & 0xff, words[q] >> 24, P);
-            tile[rr][cc + 4 * q] = (uint16_t)lo;
-            tile[rr][cc + 4 * q + 1] = (uint16_t)(lo >> 16);
-            tile[rr][cc + 4 * q + 2] = (uint16_t)hi;
-            tile[rr][cc + 4 * q + 3] = (uint16_t)(hi >> 16);
-        }
-    }
-    __syncthreads();
-    // store: output row (input column) oc, 8 consecutive input rows per chunk
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-        const int idx = threadIdx.x + 256 * s;        // 64 output rows x 8 chunks
-        const int oc = idx / 8, ch = (idx % 8) * 8;
-        uint32_t v[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            v[q] = (uint32_t)tile[ch + 2 * q][oc] | ((uint32_t)tile[ch + 2 * q + 1][oc] << 16);
-        const int64_t orow = c0 + oc, ocol = r0 + ch;
-        if (ocol + 8 <= P.rows) {
-            *reinterpret_cast<uint4 *>(out + ((int64_t)plane * P.cols + orow) * P.ld_out + ocol) =
-                make_uint4(v[0], v[1], v[2], v[3]);
-        } else {
-            for (int e = 0; e < 8 && ocol + e < P.rows; ++e)
-                out[((int64_t)plane * P.cols + orow) * P.ld_out + ocol + e] =
-                    __ushort_as_bfloat16((uint16_t)(v[e / 2] >> (16 * (e % 2))));
-        }
+    vec_b_body<IN>(in, out, P, blockIdx.x, blockIdx.y, tile);
+}
+
+// Both operands of a plane GEMM in one launch: blocks [0, na) convert A
+// (same layout), the others transpose B in 64 x 64 tiles -- one ramp-up and
+// one tail instead of two for these short HBM-bound passes.
+template <int IN>
+__global__ void __launch_bounds__(256) pack_vec_ab(const uint8_t *__restrict__ a,
+                                                   __nv_bfloat16 *__restrict__ oa, PackParams PA,
+                                                   const uint8_t *__restrict__ b,
+                                                   __nv_bfloat16 *__restrict__ ob, PackParams PB,
+                                                   int64_t na) {
+    __shared__ uint16_t tile[64][64 + 2];
+    if ((int64_t)blockIdx.x < na) {
+        vec_a_body<IN>(a, oa, PA, blockIdx.x, na);
+    } else {
+        const int64_t t = (int64_t)blockIdx.x - na;
+        const int64_t nbx = PB.cols / 64;
+        vec_b_body<IN>(b, ob, PB, t % nbx, t / nbx, tile);
     }
 }
 
@@ -366,7 +429,7 @@ int dispatch_out(int out_fmt, const void *in, void *out, const PackParams &P0, c
                                                              (__nv_bfloat16 *)out, P);
     } else if (planes_in && aligned16 && out_fmt == QADIC_FMT_OPERAND_B && P.cols % 64 == 0 &&
                (P.rows + 63) / 64 <= 65535) {
-        const dim3 grid((unsigned)(P.cols / 64), (unsigned)((P.rows + 63) / 64), P.k);
+        const dim3 grid((unsigned)(P.cols / 64), (unsigned)((P.rows + 63) / 64), 1);
         pack_vec_b<IN><<<grid, 256, 0, stream>>>((const uint8_t *)in, (__nv_bfloat16 *)out, P);
     } else if (out_fmt == QADIC_FMT_OPERAND_A_KARA || out_fmt == QADIC_FMT_OPERAND_B_KARA) {
         if (P.k != 2) return set_error(QADIC_E_UNSUPPORTED, "Karatsuba operands are for k = 2");
@@ -448,6 +511,68 @@ int launch_pack(const Field &f, int in_fmt, const void *in, int64_t rows, int64_
             break;
     }
     return set_error(QADIC_E_INVALID, "unsupported pack format pair %d -> %d", in_fmt, out_fmt);
+}
+
+namespace {
+
+PackParams pack_params(const Field &f, int64_t rows, int64_t cols, int64_t ld_in, int64_t ld_out) {
+    PackParams P{};
+    P.rows = rows;
+    P.cols = cols;
+    P.ld_in = ld_in;
+    P.ld_out = ld_out;
+    P.p = f.p;
+    P.k = f.k;
+    P.s = f.log2_q;
+    P.order = f.order;
+    P.h = f.h;
+    P.m32 = make_mod_small(f.p);
+    P.log_f64 = f.d_log_f64;
+    P.log_centred = f.d_log_centred;
+    P.antilog = f.d_antilog;
+    P.tables_in_smem = 0;
+    P.n_pad = fold_n_pad(cols);
+    return P;
+}
+
+}  // namespace
+
+// A (m x K) -> OPERAND_A and B (K x n) -> OPERAND_B from coefficient planes,
+// in one launch when both fit the vectorised paths, else two.
+int launch_pack_pair(const Field &f, int in_fmt, const void *A, int64_t m, int64_t K,
+                     int64_t lda_in, void *outA, int64_t lda_out, const void *B, int64_t n,
+                     int64_t ldb_in, void *outB, int64_t ldb_out, cudaStream_t stream) {
+    const bool planes_in = in_fmt == QADIC_FMT_INT8_PLANES || in_fmt == QADIC_FMT_COEFF_U8;
+    const bool a_ok = K % 16 == 0 && lda_in % 16 == 0 && ((uintptr_t)A & 15) == 0 &&
+                      lda_out % 8 == 0 && ((uintptr_t)outA & 15) == 0;
+    const bool b_ok = n % 64 == 0 && ldb_in % 16 == 0 && ((uintptr_t)B & 15) == 0 &&
+                      ldb_out % 8 == 0 && ((uintptr_t)outB & 15) == 0 && (K + 63) / 64 <= 65535;
+    if (!planes_in || !a_ok || !b_ok) {
+        int st = launch_pack(f, in_fmt, A, m, K, lda_in, QADIC_FMT_OPERAND_A, outA, lda_out, stream);
+        if (st != QADIC_OK) return st;
+        return launch_pack(f, in_fmt, B, K, n, ldb_in, QADIC_FMT_OPERAND_B, outB, ldb_out, stream);
+    }
+    const PackParams PA = pack_params(f, m, K, lda_in, lda_out);
+    const PackParams PB = pack_params(f, K, n, ldb_in, ldb_out);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t units_a = (int64_t)f.k * m * (K / 16);
+    // A blocks in proportion to A's share of the bytes; B blocks one per tile
+    const int64_t nb = (int64_t)(n / 64) * ((K + 63) / 64);
+    const int64_t na = std::max<int64_t>(1, std::min<int64_t>((units_a + 1023) / 1024, (int64_t)sms * 8));
+    if (na + nb > 0x7fffffff) return set_error(QADIC_E_INVALID, "too many pack blocks");
+    if (in_fmt == QADIC_FMT_INT8_PLANES)
+        pack_vec_ab<IN_I8><<<(unsigned)(na + nb), 256, 0, stream>>>(
+            (const uint8_t *)A, (__nv_bfloat16 *)outA, PA, (const uint8_t *)B,
+            (__nv_bfloat16 *)outB, PB, na);
+    else
+        pack_vec_ab<IN_U8><<<(unsigned)(na + nb), 256, 0, stream>>>(
+            (const uint8_t *)A, (__nv_bfloat16 *)outA, PA, (const uint8_t *)B,
+            (__nv_bfloat16 *)outB, PB, na);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(QADIC_E_CUDA, "pack launch: %s", cudaGetErrorString(e));
+    return QADIC_OK;
 }
 
 }  // namespace qadic

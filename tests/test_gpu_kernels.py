@@ -594,3 +594,64 @@ def test_karatsuba_rejects_other_k(torch):
     with pytest.raises(q.QadicError) as e:
         f.gemm(q.PATH_KARATSUBA, x, x, 16, 16, 16)
     assert e.value.status == q.E_UNSUPPORTED
+
+
+# ------------------------------------------- pack_operands / qadic_matmul ----
+
+@pytest.mark.parametrize("fmt", [q.FMT_INT8_PLANES, q.FMT_COEFF_U8, q.FMT_LOG])
+@pytest.mark.parametrize("shape", [(320, 256, 192), (130, 40, 70), (64, 4096, 128)])
+def test_pack_operands_equals_two_packs(torch, fmt, shape):
+    m, K, n = shape
+    f = q.Field(101, 2)
+    if fmt == q.FMT_LOG:
+        A, B = W.log_matrix(m, K, f.order, salt=51), W.log_matrix(K, n, f.order, salt=52)
+    elif fmt == q.FMT_INT8_PLANES:
+        A, B = W.centred_planes(2, m, K, 50, salt=51), W.centred_planes(2, K, n, 50, salt=52)
+    else:
+        A, B = W.coeff_planes(2, m, K, 101, salt=51), W.coeff_planes(2, K, n, 101, salt=52)
+    ld = (K + 7) // 8 * 8
+    oa = torch.zeros((2, m, ld), dtype=torch.bfloat16, device="cuda")
+    ob = torch.zeros((2, n, ld), dtype=torch.bfloat16, device="cuda")
+    f.pack_operands(fmt, dev(torch, A), dev(torch, B), m, n, K, oa, ob)
+    ra = f.pack(fmt, dev(torch, A), m, K, q.FMT_OPERAND_A,
+                out=torch.zeros((2, m, ld), dtype=torch.bfloat16, device="cuda"), ld_out=ld)
+    rb = f.pack(fmt, dev(torch, B), K, n, q.FMT_OPERAND_B,
+                out=torch.zeros((2, n, ld), dtype=torch.bfloat16, device="cuda"), ld_out=ld)
+    assert torch.equal(oa, ra) and torch.equal(ob, rb)
+
+
+@pytest.mark.parametrize("path", [q.PATH_PLANES, q.PATH_FP64_QADIC, q.PATH_FOLD,
+                                  q.PATH_KARATSUBA])
+@pytest.mark.parametrize("fmt", [q.FMT_INT8_PLANES, q.FMT_LOG])
+@pytest.mark.parametrize("shape", [(200, 130, 72), (256, 192, 64), (33, 65, 7)])
+def test_matmul_device_all_paths(torch, orc, path, fmt, shape):
+    m, n, K = shape
+    p, k = 101, 2
+    f = q.Field(p, k)
+    if fmt == q.FMT_LOG:
+        LA, LB = W.log_matrix(m, K, f.order, salt=61), W.log_matrix(K, n, f.order, salt=62)
+        T = orc.antilog(p, f.poly)
+        want = orc.gemm(p, f.poly, T[LA.astype(np.int64)], T[LB.astype(np.int64)])
+        dA, dB = dev(torch, LA), dev(torch, LB)
+    else:
+        A, B = W.centred_planes(k, m, K, 50, salt=61), W.centred_planes(k, K, n, 50, salt=62)
+        want = orc.gemm(p, f.poly, np.transpose(A, (1, 2, 0)), np.transpose(B, (1, 2, 0)))
+        dA, dB = dev(torch, A), dev(torch, B)
+    ws = torch.empty(f.matmul_device_workspace_size(path, m, n, K) + 256, dtype=torch.uint8,
+                     device="cuda")
+    C = f.matmul(path, fmt, dA, dB, m, n, K, ws)
+    assert np.array_equal(np.transpose(C.cpu().numpy(), (1, 2, 0)), want)
+
+
+def test_matmul_device_empty_k_and_short_workspace(torch):
+    f = q.Field(31, 2)
+    x = torch.zeros(64, dtype=torch.int8, device="cuda")
+    ws = torch.empty(f.matmul_device_workspace_size(q.PATH_PLANES, 4, 4, 0) + 256,
+                     dtype=torch.uint8, device="cuda")
+    C = torch.full((2, 4, 4), 7, dtype=torch.uint8, device="cuda")
+    f.matmul(q.PATH_PLANES, q.FMT_INT8_PLANES, x, x, 4, 4, 0, ws, C=C)
+    assert not C.any()
+    small = torch.empty(16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(q.QadicError) as e:
+        f.matmul(q.PATH_PLANES, q.FMT_INT8_PLANES, x, x, 4, 4, 8, small)
+    assert e.value.status == q.E_NOMEM
