@@ -66,7 +66,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="plane",
-                    choices=["plane", "fp64", "redq", "polymul", "large", "batched", "fqt"])
+                    choices=["plane", "fp64", "redq", "polymul", "large", "batched", "fqt", "fold",
+                             "karatsuba"])
     ap.add_argument("--n", type=int, default=None, help="override the matrix size")
     ap.add_argument("--words", type=int, default=1 << 28, help="REDQ sweep size (words)")
     ap.add_argument("--extras", default="all", choices=["all", "none"],
@@ -801,6 +802,18 @@ def main():
                          "gpu_launches": 50})
             line["config"] = {"workload": "65,536 pairs of degree-3 polynomials over Z/7, q=2^8"}
             extras["scaling_2_24_pairs"] = r["scaling_2_24_pairs"]
+        elif args.workload in ("fold", "karatsuba"):
+            f, A, B, C, step = make_plane_workload(torch, q, W, 101, args.n or 4096)
+            step(None)
+            n = args.n or 4096
+            fn = bench_fold if args.workload == "fold" else bench_karatsuba
+            r = fn(args, torch, q, W, f, A, B, n, C, steps=args.steps)
+            line.update({"value": r["value"] * world, "unit": "field Gop/s",
+                         "ms_per_step": r["ms_per_step"], "dtype": "bf16 exact, f32 accumulate",
+                         "roofline": r["roofline"], "gpu_launches": 3 * args.steps})
+            line["config"] = {"workload": f"GF(101^2) n={n}, {args.workload} form", "p": 101,
+                              "k": 2, "n": n, "l2": FLUSH_NOTE}
+            extras["bitexact_vs_plane"] = r["bitexact_vs_plane"]
         elif args.workload == "fqt":
             r = bench_fqt(args, torch, q, W)
             line.update({"value": r["value"] * world, "unit": "products/s", "ms_per_step": r["ms"],
