@@ -53,16 +53,19 @@ void free_tables(Field &f) {
 }
 
 // One non-blocking stream per device for the host copies of qadic_matmul_host.
-cudaStream_t side_stream(int dev) {
+// Library-owned non-blocking streams per device (index 0: copies, 1: packs
+// of later row blocks in qadic_matmul_host).
+cudaStream_t side_stream(int dev, int which = 0) {
     static std::mutex mu;
-    static cudaStream_t streams[64] = {nullptr};
-    if (dev < 0 || dev >= 64) return nullptr;
+    static cudaStream_t streams[64][2] = {};
+    if (dev < 0 || dev >= 64 || which < 0 || which > 1) return nullptr;
     std::lock_guard<std::mutex> lock(mu);
-    if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess) {
+    cudaStream_t &st = streams[dev][which];
+    if (!st && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
-        streams[dev] = nullptr;
+        st = nullptr;
     }
-    return streams[dev];
+    return st;
 }
 
 bool on_device(const Field &f) {
@@ -400,40 +403,62 @@ int qadic_matmul_host(const qadic_field *field, int path, int in_fmt, int64_t m,
         return set_error(QADIC_E_UNSUPPORTED, "no tensor-core plane kernel for k=%u", f.k);
 
     // Overlap.  The inputs go host -> device on a side stream, B first and
-    // then A in two row blocks; the plane GEMM runs per row block as soon as
-    // B and that block of A are packed, and the first block of C goes back
-    // to the host while the second is computed.  The split point keeps the
-    // two GEMMs at the wave count of one GEMM over all rows (one cluster of
-    // two CTAs per two SMs).  Everything is joined into `stream` at the end.
+    // then A in row blocks; B and the first block are packed on `stream`,
+    // later blocks on a second side stream as soon as they land (a pack
+    // block fits beside the GEMM's CTA on an SM), and the plane GEMM runs
+    // per block.  Each block of C goes back to the host while the next one
+    // is computed.  The split keeps the block GEMMs at the wave count of one
+    // GEMM over all rows (one cluster of two CTAs per two SMs) and makes the
+    // last block small, since its copy back cannot be hidden.
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaStream_t side = side_stream(dev);
-    if (!side) return set_error(QADIC_E_CUDA, "no side stream");
-    int64_t mh = m;   // rows of the first block
+    cudaStream_t side = side_stream(dev, 0), side2 = side_stream(dev, 1);
+    if (!side || !side2) return set_error(QADIC_E_CUDA, "no side stream");
+    constexpr int kMaxBlocks = 3;
+    int64_t rows[kMaxBlocks] = {m, 0, 0};
+    int nblk = 1;
     if (path == QADIC_PATH_PLANES && m >= 512) {
         const int64_t unit_rows = 256, um = (m + unit_rows - 1) / unit_rows;
         const int64_t tn = (n + 127) / 128, cl = std::max(1, sms / 2);
-        int64_t best = -1, best_cost = 0;
-        for (int64_t ur = std::max<int64_t>(1, um / 3); ur <= (2 * um) / 3; ++ur) {
-            const int64_t cost = (ur * tn + cl - 1) / cl + ((um - ur) * tn + cl - 1) / cl;
-            const int64_t dist = std::llabs(20 * ur - 11 * um);   // prefer ~0.55 of the rows
-            if (best < 0 || cost < best_cost ||
-                (cost == best_cost && dist < std::llabs(20 * best - 11 * um))) {
-                best = ur;
-                best_cost = cost;
+        auto rounds = [&](int64_t u) { return (u * tn + cl - 1) / cl; };
+        int64_t best[3] = {0, 0, 0}, best_cost = -1;
+        for (int64_t u1 = 1; u1 < um - 1; ++u1)
+            for (int64_t u3 = 1; u1 + u3 < um; ++u3) {
+                const int64_t u2 = um - u1 - u3;
+                const int64_t cost = rounds(u1) + rounds(u2) + rounds(u3);
+                // fewest rounds, then the smallest last block, then the smallest first
+                const bool better = best_cost < 0 || cost < best_cost ||
+                                    (cost == best_cost && (u3 < best[2] ||
+                                                           (u3 == best[2] && u1 < best[0])));
+                if (better) {
+                    best_cost = cost;
+                    best[0] = u1;
+                    best[1] = u2;
+                    best[2] = u3;
+                }
             }
+        if (best_cost > 0 && best_cost <= rounds(um)) {
+            rows[0] = best[0] * unit_rows;
+            rows[1] = best[1] * unit_rows;
+            rows[2] = m - rows[0] - rows[1];
+            nblk = 3;
+        } else if (m >= 512) {   // two blocks
+            rows[0] = std::min<int64_t>(m, (um / 2 + 1) * unit_rows);
+            rows[1] = m - rows[0];
+            nblk = rows[1] > 0 ? 2 : 1;
         }
-        if (best > 0) mh = std::min<int64_t>(m, best * unit_rows);
     }
-    const int64_t mb = m - mh;   // rows of the second block (0: one block)
-    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    constexpr int kEvents = 2 + 3 * kMaxBlocks + 1;
+    cudaEvent_t ev[kEvents] = {};
     for (auto &e : ev)
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
             for (auto &x : ev)
                 if (x) cudaEventDestroy(x);
             return set_error(QADIC_E_CUDA, "event: %s", cudaGetErrorString(cudaGetLastError()));
         }
+    cudaEvent_t &ev_start = ev[0], &ev_b = ev[1], &ev_join = ev[kEvents - 1];
+    cudaEvent_t *ev_copied = ev + 2, *ev_packed = ev + 2 + kMaxBlocks, *ev_gemm = ev + 2 + 2 * kMaxBlocks;
     auto cleanup = [&](int status) {
         for (auto &x : ev) cudaEventDestroy(x);   // released once their work completes
         return status;
@@ -443,71 +468,80 @@ int qadic_matmul_host(const qadic_field *field, int path, int in_fmt, int64_t m,
     };
     const size_t c_plane = (size_t)m * n;
     // Host A is `planes` planes of m x K elements of `esz` bytes; the device
-    // copy holds block 1 (rows < mh) then block 2, each as its own planes.
+    // copy holds block b's rows as planes of their own, blocks back to back.
     const bool planar = in_fmt != QADIC_FMT_LOG;
     const uint32_t planes = planar ? f.k : 1;
     const size_t esz = planar ? 1 : eb;
-    char *dA2 = dA + (size_t)planes * mh * K * esz;
-    auto copy_rows = [&](char *dst, int64_t r0, int64_t rows) -> cudaError_t {
+    const size_t pa_elem = path == QADIC_PATH_FP64_QADIC ? 8 : 2 * (size_t)f.k;
+    int64_t r0[kMaxBlocks] = {0, rows[0], rows[0] + rows[1]};
+    auto dA_blk = [&](int b) { return dA + (size_t)planes * r0[b] * K * esz; };
+    auto pA_blk = [&](int b) { return pA + pa_elem * r0[b] * K; };
+    auto copy_rows = [&](char *dst, int64_t first, int64_t nrows) -> cudaError_t {
         for (uint32_t i = 0; i < planes; ++i) {
             const cudaError_t e = cudaMemcpyAsync(
-                dst + (size_t)i * rows * K * esz,
-                (const char *)A_host + ((size_t)i * m + r0) * K * esz, (size_t)rows * K * esz,
+                dst + (size_t)i * nrows * K * esz,
+                (const char *)A_host + ((size_t)i * m + first) * K * esz, (size_t)nrows * K * esz,
                 cudaMemcpyHostToDevice, side);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
     };
-    // side stream starts after everything already queued on `stream`
-    if (cudaEventRecord(ev[0], s) || cudaStreamWaitEvent(side, ev[0], 0) ||
-        cudaMemcpyAsync(dB, B_host, eb * K * n, cudaMemcpyHostToDevice, side) ||
-        cudaEventRecord(ev[1], side) || copy_rows(dA, 0, mh) || cudaEventRecord(ev[2], side) ||
-        (mb > 0 && copy_rows(dA2, mh, mb)) || cudaEventRecord(ev[3], side))
-        return cuda_fail("H2D copy");
-    int st;
     const int opA = path == QADIC_PATH_FP64_QADIC ? QADIC_FMT_QADIC_F64 : QADIC_FMT_OPERAND_A;
     const int opB = path == QADIC_PATH_FP64_QADIC ? QADIC_FMT_QADIC_F64 : QADIC_FMT_OPERAND_B;
-    const size_t pa_elem = path == QADIC_PATH_FP64_QADIC ? 8 : 2 * (size_t)f.k;
-    char *pA2 = pA + pa_elem * mh * K;
-    if (cudaStreamWaitEvent(s, ev[1], 0)) return cuda_fail("wait");
+    // copies (side stream starts after everything already queued on `stream`)
+    if (cudaEventRecord(ev_start, s) || cudaStreamWaitEvent(side, ev_start, 0) ||
+        cudaMemcpyAsync(dB, B_host, eb * K * n, cudaMemcpyHostToDevice, side) ||
+        cudaEventRecord(ev_b, side))
+        return cuda_fail("H2D copy");
+    for (int b = 0; b < nblk; ++b)
+        if (copy_rows(dA_blk(b), r0[b], rows[b]) || cudaEventRecord(ev_copied[b], side))
+            return cuda_fail("H2D copy");
+    int st;
+    // packs of the later blocks on the second side stream
+    for (int b = 1; b < nblk; ++b) {
+        if (cudaStreamWaitEvent(side2, ev_copied[b], 0)) return cuda_fail("wait");
+        if ((st = qadic_pack(field, in_fmt, dA_blk(b), rows[b], K, K, opA, pA_blk(b), K, side2)))
+            return cleanup(st);
+        if (cudaEventRecord(ev_packed[b], side2)) return cuda_fail("event");
+    }
+    if (cudaStreamWaitEvent(s, ev_b, 0)) return cuda_fail("wait");
     if ((st = qadic_pack(field, in_fmt, dB, K, n, n, opB, pB, path == QADIC_PATH_FP64_QADIC ? n : K,
                          stream)))
         return cleanup(st);
-    if (cudaStreamWaitEvent(s, ev[2], 0)) return cuda_fail("wait");
-    if ((st = qadic_pack(field, in_fmt, dA, mh, K, K, opA, pA, K, stream))) return cleanup(st);
+    if (cudaStreamWaitEvent(s, ev_copied[0], 0)) return cuda_fail("wait");
+    if ((st = qadic_pack(field, in_fmt, dA_blk(0), rows[0], K, K, opA, pA_blk(0), K, stream)))
+        return cleanup(st);
     if (path == QADIC_PATH_FP64_QADIC) {
         if ((st = qadic_gemm(field, path, m, n, K, pA, K, pB, n, dC, n, nullptr, 0, stream)))
             return cleanup(st);
     } else {
-        if ((st = launch_gemm_planes_tc_strided(f, mh, n, K, pA, K, (int64_t)mh * K, pB, K,
-                                                (int64_t)n * K, dC, n, (int64_t)c_plane, s)))
-            return cleanup(st);
-        if (mb > 0) {
-            if (cudaEventRecord(ev[4], s) || cudaStreamWaitEvent(side, ev[4], 0))
-                return cuda_fail("event");
-            for (uint32_t i = 0; i < f.k; ++i)
-                if (cudaMemcpyAsync(C_host + i * c_plane, dC + i * c_plane, (size_t)mh * n,
-                                    cudaMemcpyDeviceToHost, side))
-                    return cuda_fail("D2H copy");
-            if (cudaStreamWaitEvent(s, ev[3], 0)) return cuda_fail("wait");
-            if ((st = qadic_pack(field, in_fmt, dA2, mb, K, K, opA, pA2, K, stream)))
+        for (int b = 0; b < nblk; ++b) {
+            if (b > 0 && cudaStreamWaitEvent(s, ev_packed[b], 0)) return cuda_fail("wait");
+            if ((st = launch_gemm_planes_tc_strided(f, rows[b], n, K, pA_blk(b), K,
+                                                    (int64_t)rows[b] * K, pB, K, (int64_t)n * K,
+                                                    dC + r0[b] * n, n, (int64_t)c_plane, s)))
                 return cleanup(st);
-            if ((st = launch_gemm_planes_tc_strided(f, mb, n, K, pA2, K, (int64_t)mb * K, pB, K,
-                                                    (int64_t)n * K, dC + mh * n, n,
-                                                    (int64_t)c_plane, s)))
-                return cleanup(st);
+            if (b + 1 < nblk) {   // this block's C goes back while the next one is computed
+                if (cudaEventRecord(ev_gemm[b], s) || cudaStreamWaitEvent(side, ev_gemm[b], 0))
+                    return cuda_fail("event");
+                for (uint32_t i = 0; i < f.k; ++i)
+                    if (cudaMemcpyAsync(C_host + i * c_plane + r0[b] * n, dC + i * c_plane + r0[b] * n,
+                                        (size_t)rows[b] * n, cudaMemcpyDeviceToHost, side))
+                        return cuda_fail("D2H copy");
+            }
         }
     }
-    if (mb > 0) {   // second block of every plane
+    if (nblk > 1) {   // last block of every plane
+        const int b = nblk - 1;
         for (uint32_t i = 0; i < f.k; ++i)
-            if (cudaMemcpyAsync(C_host + i * c_plane + mh * n, dC + i * c_plane + mh * n,
-                                (size_t)mb * n, cudaMemcpyDeviceToHost, s))
+            if (cudaMemcpyAsync(C_host + i * c_plane + r0[b] * n, dC + i * c_plane + r0[b] * n,
+                                (size_t)rows[b] * n, cudaMemcpyDeviceToHost, s))
                 return cuda_fail("D2H copy");
     } else if (cudaMemcpyAsync(C_host, dC, (size_t)f.k * m * n, cudaMemcpyDeviceToHost, s)) {
         return cuda_fail("D2H copy");
     }
-    // join: `stream` also waits for the side stream's copies
-    if (cudaEventRecord(ev[5], side) || cudaStreamWaitEvent(s, ev[5], 0)) return cuda_fail("join");
+    // join: `stream` also waits for the side streams' copies
+    if (cudaEventRecord(ev_join, side) || cudaStreamWaitEvent(s, ev_join, 0)) return cuda_fail("join");
     return cleanup(QADIC_OK);
 }
 

@@ -440,6 +440,30 @@ def test_matmul_host_log_codes_split(torch, orc, pk, shape):
     assert np.array_equal(np.transpose(hC.numpy(), (1, 2, 0)), want)
 
 
+def test_matmul_host_three_blocks(torch, orc):
+    """m = 2048, n = 4096: the host pipeline splits A into three row blocks
+    (512, 1024, 512 rows: the block GEMMs keep the single GEMM's four
+    rounds); rows of every block against the oracle, and the whole result
+    against the device path."""
+    p, k, m, n, K = 101, 2, 2048, 4096, 64
+    f = q.Field(p, k)
+    A = W.centred_planes(k, m, K, 50, salt=71)
+    B = W.centred_planes(k, K, n, 50, salt=72)
+    hA, hB = torch.from_numpy(A).pin_memory(), torch.from_numpy(B).pin_memory()
+    hC = torch.full((k, m, n), 255, dtype=torch.uint8).pin_memory()
+    ws = torch.empty(f.matmul_workspace_size(q.PATH_PLANES, q.FMT_INT8_PLANES, m, n, K),
+                     dtype=torch.uint8, device="cuda")
+    f.matmul_host(q.PATH_PLANES, q.FMT_INT8_PLANES, hA, hB, hC, m, n, K, ws)
+    torch.cuda.synchronize()
+    a = f.pack(q.FMT_INT8_PLANES, dev(torch, A), m, K, q.FMT_OPERAND_A)
+    b = f.pack(q.FMT_INT8_PLANES, dev(torch, B), K, n, q.FMT_OPERAND_B)
+    C = f.gemm(q.PATH_PLANES, a, b, m, n, K).cpu().numpy()
+    assert np.array_equal(hC.numpy(), C)
+    rows = np.array([0, 511, 512, 1535, 1536, 2047])
+    want = orc.gemm(p, f.poly, np.transpose(A[:, rows], (1, 2, 0)), np.transpose(B, (1, 2, 0)))
+    assert np.array_equal(np.transpose(C[:, rows], (1, 2, 0)), want)
+
+
 def test_sync_status_clean(torch):
     q.sync_status()
 
