@@ -3,7 +3,11 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "qadic_internal.h"
 
@@ -64,6 +68,35 @@ __device__ __forceinline__ double u64_to_f64_exact(uint64_t v) {
     const int top = 63 - __clzll((long long)v);
     const uint64_t mant = (v << (52 - top)) & ((1ull << 52) - 1);
     return __longlong_as_double((long long)((((uint64_t)(1023 + top)) << 52) | mant));
+}
+
+// Blocks of `kern` resident on the whole device (SMs x blocks per SM at
+// this block size and shared memory), cached per device and configuration:
+// for the short launches (65,536 polynomial pairs take about 2 us) the
+// occupancy query would otherwise cost more than the kernel.
+template <typename Kern>
+inline int64_t resident_blocks(Kern kern, int threads, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void *, int, size_t>, int64_t> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_tuple(dev, (const void *)kern, threads, smem);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        const auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) !=
+            cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    const int64_t r = (int64_t)std::max(sms, 1) * per_sm;
+    std::lock_guard<std::mutex> lock(mu);
+    cache[key] = r;
+    return r;
 }
 
 __device__ __forceinline__ void record_timeout(int *status, int site) {

@@ -442,12 +442,8 @@ int prepare_kernel(size_t smem) {
 }
 
 int64_t grid_for(int dev, size_t smem, int64_t ntiles) {
-    int sms = 0, per_sm = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel, kThreads, smem) !=
-            cudaSuccess || per_sm < 1)
-        per_sm = 1;
-    int64_t grid = (int64_t)sms * per_sm;
+    (void)dev;
+    int64_t grid = resident_blocks(batched_kernel, kThreads, smem);
     if (ntiles < grid) grid = std::max<int64_t>(1, ntiles);
     return grid;
 }

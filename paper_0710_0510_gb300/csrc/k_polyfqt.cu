@@ -254,13 +254,7 @@ int launch_polymul_fqt(uint32_t p, uint32_t N, uint32_t d, bool int_words, const
             cudaSuccess)
         return set_error(QADIC_E_CUDA, "polymul_fqt smem attribute: %s",
                          cudaGetErrorString(cudaGetLastError()));
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFqtThreads, smem) !=
-            cudaSuccess || per_sm < 1)
-        per_sm = 1;
-    const int64_t blocks = std::min<int64_t>(count, (int64_t)sms * per_sm * 8);
+    const int64_t blocks = std::min<int64_t>(count, resident_blocks(kern, kFqtThreads, smem) * 8);
     kern<<<(unsigned)blocks, kFqtThreads, smem, stream>>>(a, b, out, count, P);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)

@@ -19,6 +19,7 @@ namespace qadic {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kMaxPairs = 4;   // pairs per thread per chunk: 1 for small batches, 4 for large
 
 // Signed integer value of a double holding an exact integer of magnitude
 // < 2^53, from its bit pattern (integer instructions only).
@@ -32,15 +33,16 @@ __device__ __forceinline__ int64_t f64_to_i64_exact(double x) {
 // MODE 2: 64-bit integer words, r = a~ b~ exactly (Sec. 2 allows m = 64).
 // The conversions between the packed integers and doubles are done on the
 // bit patterns, so the FP64 pipe only sees the multiply (and the FMA).
-template <int MODE>
+template <int MODE, int kPairs>
 __global__ void __launch_bounds__(kThreads)
 polymul_kernel(const uint8_t *__restrict__ a, const uint8_t *__restrict__ b,
                uint8_t *__restrict__ out, int64_t count, uint32_t p, uint32_t k, uint32_t s,
                uint32_t qneg_mod_p, Div64 divp) {
-    extern __shared__ uint8_t smem[];
+    extern __shared__ __align__(16) uint8_t smem[];
+    constexpr int kChunk = kThreads * kPairs;
     const uint32_t D = 2 * k - 1;
     uint8_t *corr = smem;                           // p*p entries
-    uint8_t *stage = smem + ((p * p + 15) & ~15u);  // kThreads * D bytes
+    uint8_t *stage = smem + ((p * p + 15) & ~15u);  // kChunk * D bytes (16-byte aligned)
 
     const uint32_t m32 = (uint32_t)((((uint64_t)1 << 32) + p - 1) / p);
     for (uint32_t i = threadIdx.x; i < p * p; i += blockDim.x) {
@@ -49,19 +51,34 @@ polymul_kernel(const uint8_t *__restrict__ a, const uint8_t *__restrict__ b,
     }
     __syncthreads();
 
-    // grid-stride over blocks of kThreads pairs (the table is built once)
-    for (int64_t base = (int64_t)blockIdx.x * kThreads; base < count;
-         base += (int64_t)gridDim.x * kThreads) {
-        const int64_t idx = base + threadIdx.x;
-        if (idx < count) {
+    // Grid-stride over chunks of kPairs * kThreads pairs (the table is built
+    // once).  Each thread issues the operand loads of its kPairs pairs first,
+    // so several loads are in flight, then reduces them; the chunk's output
+    // bytes leave through shared memory as 16-byte stores.
+    const bool vec4 = k == 4 && ((((uintptr_t)a | (uintptr_t)b) & 3) == 0);
+    for (int64_t base = (int64_t)blockIdx.x * kChunk; base < count;
+         base += (int64_t)gridDim.x * kChunk) {
+        uint32_t wa[kPairs] = {}, wb[kPairs] = {};
+        if (vec4) {
+#pragma unroll
+            for (int j = 0; j < kPairs; ++j) {
+                const int64_t idx = base + j * kThreads + threadIdx.x;
+                if (idx < count) {
+                    wa[j] = __ldg(reinterpret_cast<const uint32_t *>(a) + idx);
+                    wb[j] = __ldg(reinterpret_cast<const uint32_t *>(b) + idx);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kPairs; ++j) {
+            const int64_t idx = base + j * kThreads + threadIdx.x;
+            if (idx >= count) break;
             uint64_t aw = 0, bw = 0;
-            if (k == 4 && ((((uintptr_t)a | (uintptr_t)b) & 3) == 0)) {
-                const uint32_t wa = __ldg(reinterpret_cast<const uint32_t *>(a) + idx);
-                const uint32_t wb = __ldg(reinterpret_cast<const uint32_t *>(b) + idx);
+            if (vec4) {
 #pragma unroll
                 for (uint32_t i = 0; i < 4; ++i) {
-                    aw |= (uint64_t)mod_small((wa >> (8 * i)) & 0xff, p, m32) << (s * i);
-                    bw |= (uint64_t)mod_small((wb >> (8 * i)) & 0xff, p, m32) << (s * i);
+                    aw |= (uint64_t)mod_small((wa[j] >> (8 * i)) & 0xff, p, m32) << (s * i);
+                    bw |= (uint64_t)mod_small((wb[j] >> (8 * i)) & 0xff, p, m32) << (s * i);
                 }
             } else {
                 for (uint32_t i = 0; i < k; ++i) {   // coefficients taken mod p
@@ -89,7 +106,7 @@ polymul_kernel(const uint8_t *__restrict__ a, const uint8_t *__restrict__ b,
             }
             const uint64_t rop = div64(r, divp);
             uint32_t u_next = 0;
-            uint8_t *dst = stage + threadIdx.x * D;
+            uint8_t *dst = stage + (j * kThreads + threadIdx.x) * D;
             for (int i = (int)D - 1; i >= 0; --i) {
                 const uint32_t ui = (uint32_t)((r >> (s * i)) - (uint64_t)p * (rop >> (s * i)));
                 dst[i] = (i == (int)D - 1) ? (uint8_t)ui : corr[ui * p + u_next];
@@ -97,10 +114,17 @@ polymul_kernel(const uint8_t *__restrict__ a, const uint8_t *__restrict__ b,
             }
         }
         __syncthreads();
-        // coalesced write-out of the block's contiguous output range
-        const int64_t nvalid = (count - base) < kThreads ? (count - base) : kThreads;
+        // write-out of the chunk's contiguous output range
+        const int64_t nvalid = (count - base) < kChunk ? (count - base) : kChunk;
+        const int64_t nbytes = nvalid * D;
         uint8_t *gout = out + base * D;
-        for (int64_t i = threadIdx.x; i < nvalid * D; i += blockDim.x) gout[i] = stage[i];
+        if (nbytes % 16 == 0 && ((uintptr_t)gout & 15) == 0) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(stage);
+            uint4 *g4 = reinterpret_cast<uint4 *>(gout);
+            for (int64_t i = threadIdx.x; i < nbytes / 16; i += blockDim.x) g4[i] = src[i];
+        } else {
+            for (int64_t i = threadIdx.x; i < nbytes; i += blockDim.x) gout[i] = stage[i];
+        }
         __syncthreads();
     }
 }
@@ -111,22 +135,26 @@ int launch_polymul(uint32_t p, uint32_t k, uint32_t log2_q, int mode, const uint
                    const uint8_t *b, uint8_t *out, int64_t count, cudaStream_t stream) {
     const uint64_t q = 1ull << log2_q;
     const uint32_t qneg = (uint32_t)((p - q % p) % p);
-    const size_t smem = ((p * p + 15) & ~15u) + (size_t)kThreads * (2 * k - 1);
-    auto kern = mode == 2 ? polymul_kernel<2> : mode == 1 ? polymul_kernel<1> : polymul_kernel<0>;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // four pairs per thread once the batch fills every SM twice over with them
+    const int pairs = count >= (int64_t)sms * kThreads * kMaxPairs * 2 ? kMaxPairs : 1;
+    const int64_t chunk = (int64_t)kThreads * pairs;
+    const size_t smem = ((p * p + 15) & ~15u) + (size_t)chunk * (2 * k - 1);
+    auto kern = pairs == kMaxPairs
+                    ? (mode == 2 ? polymul_kernel<2, kMaxPairs>
+                                 : mode == 1 ? polymul_kernel<1, kMaxPairs> : polymul_kernel<0, kMaxPairs>)
+                    : (mode == 2 ? polymul_kernel<2, 1>
+                                 : mode == 1 ? polymul_kernel<1, 1> : polymul_kernel<0, 1>);
     if (smem > 48 * 1024) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
             return set_error(QADIC_E_CUDA, "smem attribute: %s",
                              cudaGetErrorString(cudaGetLastError()));
     }
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem) !=
-            cudaSuccess || per_sm < 1)
-        per_sm = 1;
-    int64_t blocks = (count + kThreads - 1) / kThreads;
-    blocks = std::min<int64_t>(blocks, (int64_t)sms * per_sm);
+    int64_t blocks = (count + chunk - 1) / chunk;
+    blocks = std::min<int64_t>(blocks, resident_blocks(kern, kThreads, smem));
     kern<<<(unsigned)blocks, kThreads, smem, stream>>>(a, b, out, count, p, k, log2_q, qneg,
                                                        make_div64(p));
     const cudaError_t e = cudaGetLastError();

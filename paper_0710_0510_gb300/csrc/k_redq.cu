@@ -292,14 +292,8 @@ int launch_stream(Kern kern, const double *in, double *out, int64_t count, const
             cudaSuccess)
         return set_error(QADIC_E_CUDA, "%s smem attribute: %s", what,
                          cudaGetErrorString(cudaGetLastError()));
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem) !=
-            cudaSuccess || per_sm < 1)
-        per_sm = 1;
     const int64_t npairs = count >> 1;
-    int64_t blocks = (int64_t)sms * per_sm;
+    int64_t blocks = resident_blocks(kern, kThreads, smem);
     const int64_t need = (npairs + kThreads - 1) / kThreads;
     if (need < blocks) blocks = need > 0 ? need : 1;
     kern<<<(unsigned)blocks, kThreads, smem, stream>>>(in, out, count, P);
