@@ -350,7 +350,7 @@ __device__ __noinline__ void run_tile_cfg(int cfg, const BProd &P, const BFieldP
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 3) batched_kernel(uint8_t *ws) {
+__global__ void __launch_bounds__(kThreads, 5) batched_kernel(uint8_t *ws) {
     extern __shared__ __align__(16) uint8_t smem[];   // sized for the largest tile in the list
     __shared__ uint16_t tab[256];   // input byte -> centred bf16 bits, for field s_field
     __shared__ int s_tile, s_field;

@@ -153,3 +153,34 @@ def test_batched_4096_products(torch, orc):
     for i in range(len(descs)):
         f, A, B, C = operands(i)
         assert freivalds(orc, f, A, B, C, vectors=1, seed=i), i
+
+
+def test_fold_and_karatsuba_forms_n4096(torch, orc):
+    """The fold-before and Karatsuba forms as bench.py times them (GF(101^2),
+    n = 4096): equal to the plane product, itself checked against the oracle
+    on sampled entries."""
+    n = 4096
+    f, A, B, C, step = bench.make_plane_workload(torch, q, W, 101, n)
+    step(None)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(21)
+    ii, jj = rng.integers(0, n, 256), rng.integers(0, n, 256)
+    assert sampled_entries_agree(orc, f, A, B, C.cpu().numpy(), ii, jj)
+    for fn in (bench.bench_fold, bench.bench_karatsuba):
+        r = fn(None, torch, q, W, f, A, B, n, C, steps=1)
+        assert r["bitexact_vs_plane"], fn.__name__
+    torch.cuda.empty_cache()
+
+
+def test_polymul_2_24_pairs_sampled(torch, orc):
+    """The labelled 2^24-pair scaling run of the batched polynomial products,
+    both product modes: a sample of pairs, and the last ones."""
+    count = 1 << 24
+    a, b = W.polymul_pairs(count, 7, 4, salt=1)
+    da, db = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    idx = np.concatenate([np.random.default_rng(4).choice(count, 20000, replace=False),
+                          np.arange(count - 1000, count)])
+    want = orc.polymul(7, a[idx], b[idx])
+    for int_words in (False, True):
+        out = q.polymul_batched(7, 4, da, db, int_words=int_words).cpu().numpy()
+        assert np.array_equal(out[idx], want), int_words
