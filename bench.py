@@ -35,6 +35,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FLUSH_NOTE = "inputs larger than L2 (129 MB)"
+METRIC = "GF(p^k) matmul field Gop/s, INT8-plane vs FP64 q-adic; REDQ residues/s"
+
+
+def headline_config(n):
+    """The headline workload's config, shared by both arms."""
+    return {"workload": f"GF(101^2) n={n}: pack A,B in one launch (int8 centred planes -> bf16 "
+                        f"operands) + tcgen05 plane GEMM + fused mod-p/mod-P epilogue",
+            "p": 101, "k": 2, "n": n, "l2": FLUSH_NOTE}
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # headline GEMM from one ncu capture (profiles/gemm_planes_tc_gf101_2_n4096.md),
@@ -745,12 +753,13 @@ def run_reference(args):
         vals.append(cb["value"])
     value = statistics.median(vals)
     cb["value"] = value
-    line = {"impl": "reference", "metric": "GF(p^k) matmul field Gop/s (GF(101^2), n=4096)",
+    line = {"impl": "reference", "metric": METRIC,
             "value": value, "unit": "field Gop/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": f"GF(101^2) n={n} schoolbook oracle (CPU)", "p": 101, "k": 2,
-                       "n": n},
+            "config": headline_config(n),
+            "runs": "the oracle (plain C schoolbook arithmetic, OpenMP) on bounded row samples "
+                    "of the same product",
             "cpu_baseline": cb,
             "e2e": {"value": value, "unit": "field Gop/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -774,7 +783,7 @@ def main():
     smi_id = f"GPU-{uuid}" if uuid else str(dev_index)
     q.lib()
 
-    line = {"metric": "GF(p^k) matmul field Gop/s, INT8-plane vs FP64 q-adic; REDQ residues/s",
+    line = {"metric": METRIC,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "data": "synthetic (seeded, shaped like the paper's workloads)"}
@@ -787,10 +796,7 @@ def main():
                          "ms_per_step": res["ms_per_step"], "dtype": "bf16 (exact small integers), "
                          "f32 accumulate", "roofline": res["roofline"],
                          "gpu_launches": res["gpu_launches"]})
-            line["config"] = {"workload": f"GF(101^2) n={n}: pack A,B in one launch (int8 centred "
-                              f"planes -> bf16 operands) + tcgen05 plane GEMM + fused mod-p/mod-P "
-                              f"epilogue",
-                              "p": 101, "k": 2, "n": n, "l2": FLUSH_NOTE}
+            line["config"] = headline_config(n)
             if rank == 0 and args.extras == "all":
                 C64, fp = bench_fp64(args, torch, q, W, f, A, B, n)
                 fp["bitexact_vs_plane"] = bool(torch.equal(C64, C))

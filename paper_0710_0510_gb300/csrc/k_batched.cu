@@ -34,7 +34,8 @@ namespace qadic {
 namespace {
 
 constexpr int kThreads = 128;
-constexpr int kMinBK = 32;        // smallest K-block of any candidate
+constexpr int kMinBK = 32;        // K-block of every configuration 0 (the fallback): a field's
+                                  // exact FP32 chunk must cover at least this much
 constexpr int kMaxFields = 64;
 
 struct BFieldParams {
@@ -81,16 +82,18 @@ struct TileCfg {
 };
 
 // Candidate (BM, BN, BK) per k; index 0 is the default.  Every candidate is
-// at least 32 x 16 (the work-list bound) and at least kMinBK deep.
+// at least 32 x 16 (the work-list bound); configuration 0 is kMinBK deep.
 struct TileShape {
     int bm, bn, bk;
 };
 constexpr int kMaxCfg = 4;
 constexpr TileShape kShapesK2[kMaxCfg] = {{64, 32, 32}, {64, 64, 32}, {32, 32, 32}, {64, 32, 64}};
 constexpr TileShape kShapesK4[kMaxCfg] = {{32, 32, 32}, {64, 32, 32}, {32, 16, 32}, {32, 32, 64}};
-constexpr TileShape kShapesK8[kMaxCfg] = {{32, 16, 32}, {32, 32, 32}, {32, 16, 64}, {32, 16, 32}};
+// (k >= 5: the 16-deep K-block halves the staged operand registers, which
+// the 15 accumulator sets of k = 8 otherwise push into spills)
+constexpr TileShape kShapesK8[kMaxCfg] = {{32, 16, 32}, {32, 32, 32}, {32, 16, 64}, {32, 16, 16}};
 
-__host__ __device__ constexpr int num_cfgs(uint32_t k) { return k <= 4 ? 4 : 3; }
+__host__ __device__ constexpr int num_cfgs(uint32_t k) { return 4; }
 
 inline TileShape tile_shape_of(uint32_t k, int cfg) {
     if (cfg < 0 || cfg >= num_cfgs(k)) cfg = 0;

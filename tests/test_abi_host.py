@@ -210,7 +210,7 @@ def test_batched_tile_table_and_selection():
         cfgs = q.batched_tile_configs(k)
         assert len(cfgs) >= 3 and q.batched_selected_tiles(k) == 0
         for bm, bn, bk, smem in cfgs:
-            assert bm % 32 == 0 and bn % 16 == 0 and bk % 32 == 0
+            assert bm % 32 == 0 and bn % 16 == 0 and bk % 16 == 0
             assert smem == (k * bm * (bk + 8) + k * bk * (bn + 8)) * 2
             assert smem <= 227 * 1024 // 3           # three CTAs per SM
         assert len(set(cfgs)) == len(cfgs)          # no duplicate candidates
@@ -218,7 +218,7 @@ def test_batched_tile_table_and_selection():
     assert L.qadic_batched_select_tiles(0, 0) == q.E_INVALID
     assert L.qadic_batched_select_tiles(9, 0) == q.E_INVALID
     assert L.qadic_batched_select_tiles(2, 4) == q.E_INVALID
-    assert L.qadic_batched_select_tiles(5, 3) == q.E_INVALID
+    assert L.qadic_batched_select_tiles(5, 4) == q.E_INVALID
     assert L.qadic_batched_select_tiles(2, -2) == q.E_INVALID
     q.batched_select_tiles(2, 3)
     assert q.batched_selected_tiles(2) == 3
