@@ -86,14 +86,17 @@ struct TileCfg {
 struct TileShape {
     int bm, bn, bk;
 };
-constexpr int kMaxCfg = 4;
-constexpr TileShape kShapesK2[kMaxCfg] = {{64, 32, 32}, {64, 64, 32}, {32, 32, 32}, {64, 32, 64}};
-constexpr TileShape kShapesK4[kMaxCfg] = {{32, 32, 32}, {64, 32, 32}, {32, 16, 32}, {32, 32, 64}};
+constexpr int kMaxCfg = 5;
+constexpr TileShape kShapesK2[kMaxCfg] = {{64, 32, 32}, {64, 64, 32}, {32, 32, 32}, {64, 32, 64},
+                                          {32, 32, 16}};
+constexpr TileShape kShapesK4[kMaxCfg] = {{32, 32, 32}, {64, 32, 32}, {32, 16, 32}, {32, 32, 64},
+                                          {32, 16, 16}};
 // (k >= 5: the 16-deep K-block halves the staged operand registers, which
 // the 15 accumulator sets of k = 8 otherwise push into spills)
-constexpr TileShape kShapesK8[kMaxCfg] = {{32, 16, 32}, {32, 32, 32}, {32, 16, 64}, {32, 16, 16}};
+constexpr TileShape kShapesK8[kMaxCfg] = {{32, 16, 32}, {32, 32, 32}, {32, 16, 64}, {32, 16, 16},
+                                          {32, 16, 16}};
 
-__host__ __device__ constexpr int num_cfgs(uint32_t k) { return 4; }
+__host__ __device__ constexpr int num_cfgs(uint32_t k) { return k <= 4 ? 5 : 4; }
 
 inline TileShape tile_shape_of(uint32_t k, int cfg) {
     if (cfg < 0 || cfg >= num_cfgs(k)) cfg = 0;
@@ -340,12 +343,14 @@ __device__ __noinline__ void run_tile_cfg(int cfg, const BProd &P, const BFieldP
     constexpr TileShape c1 = kSmall ? kShapesK2[1] : kMid ? kShapesK4[1] : kShapesK8[1];
     constexpr TileShape c2 = kSmall ? kShapesK2[2] : kMid ? kShapesK4[2] : kShapesK8[2];
     constexpr TileShape c3 = kSmall ? kShapesK2[3] : kMid ? kShapesK4[3] : kShapesK8[3];
+    constexpr TileShape c4 = kSmall ? kShapesK2[4] : kMid ? kShapesK4[4] : kShapesK8[4];
     switch (cfg) {
         case 1: run_tile<KP, c1.bm, c1.bn, c1.bk>(P, F, tm, tn, smem, tab); break;
         case 2: run_tile<KP, c2.bm, c2.bn, c2.bk>(P, F, tm, tn, smem, tab); break;
-        case 3:
-            if constexpr (num_cfgs(KP) > 3) {
-                run_tile<KP, c3.bm, c3.bn, c3.bk>(P, F, tm, tn, smem, tab);
+        case 3: run_tile<KP, c3.bm, c3.bn, c3.bk>(P, F, tm, tn, smem, tab); break;
+        case 4:
+            if constexpr (num_cfgs(KP) > 4) {
+                run_tile<KP, c4.bm, c4.bn, c4.bk>(P, F, tm, tn, smem, tab);
                 break;
             }
             [[fallthrough]];

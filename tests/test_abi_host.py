@@ -217,7 +217,7 @@ def test_batched_tile_table_and_selection():
     L = q.lib()
     assert L.qadic_batched_select_tiles(0, 0) == q.E_INVALID
     assert L.qadic_batched_select_tiles(9, 0) == q.E_INVALID
-    assert L.qadic_batched_select_tiles(2, 4) == q.E_INVALID
+    assert L.qadic_batched_select_tiles(2, 5) == q.E_INVALID
     assert L.qadic_batched_select_tiles(5, 4) == q.E_INVALID
     assert L.qadic_batched_select_tiles(2, -2) == q.E_INVALID
     q.batched_select_tiles(2, 3)
