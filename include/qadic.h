@@ -379,6 +379,15 @@ int qadic_batched_autotune(const qadic_field *const *fields, int32_t nfields,
 int qadic_batched_gemm_noalloc(const qadic_field *const *fields, int32_t nfields,
                                const qadic_gemm_desc *descs, int64_t count, void *stream);
 
+/* ------------------------------------------------------------- selftest --
+ * Diagnostic with no counterpart in the paper.  It exercises the failure
+ * path of the bounded device waits that every kernel here uses: one warp
+ * waits on a fresh mbarrier that nothing arrives on, gives up after `polls`
+ * polls (1 <= polls <= 2^26), records QADIC_E_DEVICE_TIMEOUT in the status
+ * word and returns.  The next qadic_sync_status(stream) reports it and
+ * clears it; the context stays usable.  Nothing faults, traps or hangs. */
+int qadic_selftest_bounded_wait(uint32_t polls, void *stream);
+
 /* --------------------------------------------------------------- status --
  * Synchronises `stream` and returns QADIC_E_DEVICE_TIMEOUT if a kernel of
  * this library on the current device gave up a bounded wait since the last

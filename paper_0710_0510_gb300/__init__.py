@@ -121,6 +121,7 @@ _SIGS = {
                                               ctypes.POINTER(GemmDesc), ctypes.c_int64,
                                               ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32,
                                               ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p]),
+    "qadic_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_void_p]),
     "qadic_polymul_batched": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                              ctypes.c_uint32, ctypes.c_void_p]),
@@ -418,6 +419,12 @@ def batched_gemm_noalloc(fields, descs, stream=None):
     arr = (GemmDesc * len(descs))(*descs)
     hs = (ctypes.c_void_p * len(fields))(*[f.handle for f in fields])
     _check(lib().qadic_batched_gemm_noalloc(hs, len(fields), arr, len(descs), _stream(stream)))
+
+
+def selftest_bounded_wait(polls: int, stream=None):
+    """Let a bounded device wait run out on purpose (``qadic_selftest_bounded_wait``):
+    the next sync_status() raises QadicError with E_DEVICE_TIMEOUT."""
+    _check(lib().qadic_selftest_bounded_wait(polls, _stream(stream)))
 
 
 def sync_status(stream=None):

@@ -236,6 +236,12 @@ def test_fold_format_and_path_constants_match_header():
     assert re.search(r"QADIC_PATH_KARATSUBA = 3", h) and q.PATH_KARATSUBA == 3
 
 
+def test_selftest_rejects_bad_poll_counts():
+    L = q.lib()
+    assert L.qadic_selftest_bounded_wait(0, None) == q.E_INVALID
+    assert L.qadic_selftest_bounded_wait((1 << 26) + 1, None) == q.E_INVALID
+
+
 def test_zero_counts_are_noops():
     L = q.lib()
     assert L.qadic_redq(7, 10, 5, None, None, 0, 3, None) == q.OK

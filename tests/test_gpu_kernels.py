@@ -464,6 +464,23 @@ def test_matmul_host_three_blocks(torch, orc):
     assert np.array_equal(np.transpose(C[:, rows], (1, 2, 0)), want)
 
 
+def test_bounded_wait_timeout_is_reported_and_context_survives(torch, orc):
+    """A bounded wait that runs out (nothing arrives on its barrier) records
+    QADIC_E_DEVICE_TIMEOUT; sync_status reports it once, clears it, and the
+    context keeps computing correctly."""
+    q.sync_status()
+    q.selftest_bounded_wait(4096)
+    with pytest.raises(q.QadicError) as e:
+        q.sync_status()
+    assert e.value.status == q.E_DEVICE_TIMEOUT
+    assert b"site 9" in q.lib().qadic_last_error()
+    q.sync_status()   # cleared
+    a, b = W.polymul_pairs(1000, 7, 4, salt=5)
+    out = q.polymul_batched(7, 4, dev(torch, a), dev(torch, b))
+    assert np.array_equal(host(out), orc.polymul(7, a, b))
+    q.sync_status()
+
+
 def test_sync_status_clean(torch):
     q.sync_status()
 
