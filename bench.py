@@ -12,7 +12,7 @@ Measured beside it (each a full path of its own, reported as extra keys):
   polymul 65,536 degree-3 products over Z/7 (Alg. 1 + Alg. 2)
   large   GF(251^2), n = 16384 plane form
   batched 4096 uneven products over GF(2^8), GF(7^4), GF(31^2), one launch
-  fqt     16,384 degree-500 polynomial products over Z/3 by the d-FQT (Sec. 7),
+  fqt     16,384 degree-500 polynomial products over Z/3 by the d-FQT (Sec. 6),
           every valid d with binary64 and 64-bit integer words (d = 0: the
           classical delayed reduction); REDQ with q = 1176, a multiple of p
 
@@ -46,11 +46,12 @@ def headline_config(n):
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # headline GEMM from one ncu capture (profiles/gemm_planes_tc_gf101_2_n4096.md),
-# valid only while the kernel's source file is byte-for-byte the one captured.
+# valid only while the kernel's source file, "//" comments and blank lines
+# aside, is the one captured.
 MEASURED_TRAFFIC = {
     "gemm_planes_tc_kernel<2,128,2>": {
         "file": "paper_0710_0510_gb300/csrc/k_gemm_tc.cu",
-        "sha256": "4282d22bd3e77c29c3ac0420157722d0d90b6d07b5cbc93d51469cd9dc924904",
+        "code_sha256": "b07c9f266a4f45cdf4b43e31ef0b6010c5541f496fc1cba43cc6c119d9b111c4",
         "bytes": 458539776 + 31869184, "n": 4096},
 }
 
@@ -60,9 +61,14 @@ def measured_traffic(kernel, n):
     rec = MEASURED_TRAFFIC.get(kernel)
     if not rec or rec["bytes"] is None or rec["n"] != n:
         return None
-    with open(os.path.join(ROOT, rec["file"]), "rb") as fh:
-        if hashlib.sha256(fh.read()).hexdigest() != rec["sha256"]:
-            return None
+    code = []
+    with open(os.path.join(ROOT, rec["file"])) as fh:
+        for line in fh:
+            line = line.split("//", 1)[0].rstrip()
+            if line:
+                code.append(line)
+    if hashlib.sha256("\n".join(code).encode()).hexdigest() != rec["code_sha256"]:
+        return None
     return rec["bytes"]
 PQ_Q = 1176
 
@@ -444,7 +450,7 @@ FQT_P, FQT_N, FQT_COUNT = 3, 500, 16384
 
 
 def bench_fqt(args, torch, q, W, steps=20):
-    """Long polynomial products (Sec. 7): 16384 pairs of degree 500 over Z/3
+    """Long polynomial products (Sec. 6): 16384 pairs of degree 500 over Z/3
     (the paper's example p and N), every valid FQT degree d with binary64
     and 64-bit integer words; d = 0 is the classical delayed reduction."""
     a, b = W.polylong_pairs(FQT_COUNT, FQT_N, FQT_P)

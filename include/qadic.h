@@ -6,9 +6,9 @@
  * Conventions shared by every call
  * --------------------------------
  * Field.   GF(p^k) = Z_p[X]/(P), P monic irreducible of degree k; an element is
- *          the coefficient vector (c_0..c_{k-1}), c_i in [0, p-1]  (Sec. 6).
+ *          the coefficient vector (c_0..c_{k-1}), c_i in [0, p-1]  (Sec. 7).
  *          Discrete-log codes: code e in [0, p^k-2] is g^e for the field's
- *          generator g; code p^k-1 is zero (Sec. 6, Alg. 4 REQUIRE).
+ *          generator g; code p^k-1 is zero (Sec. 7, Alg. 4's input requirement).
  * Planes.  A "k-plane" matrix of rows x cols stores coefficient i of every
  *          element in plane i: element (r, c) of plane i is at
  *          base + (i * rows + r) * ld + c, i.e. planes are contiguous blocks
@@ -46,7 +46,7 @@ typedef enum {
     QADIC_E_INVALID = 1,        /* bad argument, size, stride or alignment */
     QADIC_E_NOT_PRIME = 2,      /* p is not prime */
     QADIC_E_REDUCIBLE = 3,      /* the given P is not irreducible mod p */
-    QADIC_E_OVERFLOW = 4,       /* an exactness bound (Eq. 2, Lemma 1, Eq. 4) fails */
+    QADIC_E_OVERFLOW = 4,       /* an exactness bound (Eq. 2, Lemma 1, Eq. 3) fails */
     QADIC_E_UNSUPPORTED = 5,    /* valid request this build has no kernel for */
     QADIC_E_CUDA = 6,           /* a CUDA runtime call failed */
     QADIC_E_DEVICE_TIMEOUT = 7, /* a bounded device wait ran out (qadic_sync_status) */
@@ -86,7 +86,7 @@ typedef struct {
     uint32_t log2_q;          /* FP64 q-adic radix q = 2^log2_q (Eq. 2 with m = 53) */
     uint32_t n_q;             /* products per K-block of the FP64 path (Eq. 2); 0 = path unavailable */
     uint32_t reserved;
-    int64_t k_max_int32;      /* Eq. 4 with centred planes and a 32-bit signed accumulator */
+    int64_t k_max_int32;      /* Eq. 3 with centred planes and a 32-bit signed accumulator */
     int64_t k_chunk_f32;      /* K per exact FP32 tensor-core accumulation chunk */
 } qadic_info;
 
@@ -111,14 +111,14 @@ typedef struct qadic_field qadic_field;
  *   k     1 <= k <= 8, p^k <= 65536.
  *   poly  k+1 coefficients low -> high, monic, or NULL for the default: the
  *         monic irreducible whose low coefficients have the smallest value
- *         sum_i a_i p^i.  (Sec. 6: the field as polynomials modulo p and
+ *         sum_i a_i p^i.  (Sec. 7: the field as polynomials modulo p and
  *         modulo an irreducible P of degree k.)
  *   flags 0, or QADIC_FIELD_HOST_ONLY: build the field and its tables on the
  *         host only (no device upload, no CUDA call); such a handle serves
  *         qadic_field_info and is rejected by every call that launches work.
  * Host side: checks p prime (QADIC_E_NOT_PRIME) and P irreducible
  * (QADIC_E_REDUCIBLE), picks the generator (smallest primitive element),
- * derives q and n_q from Eq. 2, the Eq. 4 K bound, and builds the tables of
+ * derives q and n_q from Eq. 2, the Eq. 3 K bound, and builds the tables of
  * Sec. 5-6: log -> q-adic FP64 word, log -> centred planes, the Thm. 3 L/H
  * correction-and-fold tables and X^t mod P; then uploads them (owned by the
  * handle).  *out is set only on success. */
@@ -132,7 +132,7 @@ int qadic_field_destroy(qadic_field *field);
 int qadic_field_info(const qadic_field *field, qadic_info *out);
 
 /* ----------------------------------------------------------------- pack --
- * DQT (Sec. 2, Alg. 1 line 1; Alg. 4 line 1 with the Sec. 6 improvement:
+ * DQT (Sec. 2, Alg. 1's packing; Alg. 4's pack step with the Sec. 7 improvement:
  * one table lookup instead of a Horner evaluation).  Converts a rows x cols
  * matrix from in_fmt to out_fmt.
  *   in, ld_in    input in in_fmt (element stride per row = ld_in elements)
@@ -158,7 +158,7 @@ int qadic_pack(const qadic_field *field, int in_fmt, const void *in, int64_t row
 
 /* ----------------------------------------------------------------- gemm --
  * C = A * B over GF(p^k) (Alg. 4 applied to every row/column pair, the
- * numerical routine being a GEMM, Sec. 6).  m x K times K x n.
+ * numerical routine being a GEMM, Sec. 7).  m x K times K x n.
  * QADIC_PATH_FP64_QADIC: A is QADIC_F64 m x K (lda), B is QADIC_F64 K x n
  *   (ldb).  K is cut into blocks of n_q products (Eq. 2); after each block
  *   the packed sums go through REDQ (Alg. 2 with Lemma 1's floor) and the
@@ -232,7 +232,7 @@ int qadic_matmul_host(const qadic_field *field, int path, int in_fmt, int64_t m,
  * rop = floor(r/p) by Lemma 1 (multiplication by 1/p rounded upward, then
  * floor) or, with QADIC_REDQ_INT_FLOOR, by an integer multiply-high; the
  * u_j by shifts; the corrections mu_j = (u_j - q u_{j+1}) mod p per
- * table_mode (Table 2): 0 arithmetic, 1 a p^2 table (d lookups), 2 a p^k'
+ * table_mode (Table 1): 0 arithmetic, 1 a p^2 table (d lookups), 2 a p^k'
  * table (ceil(d/(k'-1)) lookups, largest k' fitting shared memory), 3 the
  * full p^(d+1) table (one lookup) when it fits.
  * Requires ndigits * log2_q <= 51 (Lemma 1's limit 1/(2eps+eps^2) with
@@ -243,7 +243,7 @@ int qadic_redq(uint32_t p, uint32_t log2_q, uint32_t ndigits, const double *in, 
 
 /* -------------------------------------------------------------- redq_pq --
  * REDQ (Alg. 2) for q a multiple of p, the other choice of q that the
- * paper's conclusion leaves to compare (q = 10^4, p = 5 in Ex. 3).  Since
+ * paper's conclusion leaves to compare (q = 10^4, p = 5 in Ex. 2).  Since
  * -q = 0 mod p the corrections of Alg. 2 vanish and mu_j = u_j (Thm. 2): no
  * table.  Each division by q^j (no longer a shift) is a Lemma 1 floor by
  * 1/q^j rounded upward, or with QADIC_REDQ_INT_FLOOR an integer
@@ -258,7 +258,7 @@ int qadic_redq_pq(uint32_t p, uint64_t q, uint32_t ndigits, const double *in, do
                   int64_t count, uint32_t flags, void *stream);
 
 /* ---------------------------------------------------------- polymul_fqt --
- * Products of long polynomials in Z_p[X] by the d-FQT (Sec. 7, Table 1).
+ * Products of long polynomials in Z_p[X] by the d-FQT (Sec. 6, Table 2).
  * a, b: count polynomials of degree N, N+1 uint8 coefficients each (lowest
  * first; values are reduced mod p).  out: count x (2N+1) uint8 coefficients
  * in [0, p-1].  Device pointers, owned by the caller.

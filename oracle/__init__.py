@@ -121,7 +121,7 @@ def smallest_irreducible(p: int, k: int) -> list[int]:
 
 
 def field_mul(p: int, poly, a, b) -> list[int]:
-    """a*b in Z_p[X]/(P): schoolbook product, mod p, long division (Sec. 6)."""
+    """a*b in Z_p[X]/(P): schoolbook product, mod p, long division (Sec. 7)."""
     P = _u32(poly)
     k = len(P) - 1
     A, B = _u32(a), _u32(b)
@@ -150,8 +150,8 @@ def generator(p: int, poly) -> list[int]:
 def antilog(p: int, poly, g=None) -> np.ndarray:
     """(p^k, k) table: row e = coefficients of g^e, row p^k-1 = zero.
 
-    Field elements stored as discrete logarithms of a generator (Sec. 6,
-    Alg. 4 REQUIRE)."""
+    Field elements stored as discrete logarithms of a generator (Sec. 7,
+    Alg. 4's input requirement)."""
     P = _u32(poly)
     k = len(P) - 1
     if g is None:
@@ -221,7 +221,7 @@ def polymul(p: int, a, b) -> np.ndarray:
 
 
 def polymul_long(p: int, a, b) -> np.ndarray:
-    """Products of degree-N polynomials in Z_p[X] (Sec. 7's workload): a, b
+    """Products of degree-N polynomials in Z_p[X] (Sec. 6's workload): a, b
     (count, N+1), lowest coefficient first.  Returns (count, 2N+1) in
     [0, p-1]: the schoolbook convolution, accumulated in int64, mod p."""
     A, B = _i32(a), _i32(b)
@@ -278,7 +278,7 @@ def qadic_value(coeffs, q: int) -> np.ndarray:
 
 
 def centred(coeffs, p: int) -> np.ndarray:
-    """Centred representative in [-(p-1)/2, (p-1)/2] (Sec. 6, Eq. 4's centred
+    """Centred representative in [-(p-1)/2, (p-1)/2] (Sec. 6, Eq. 3's centred
     representation); p = 2 keeps {0, 1}."""
     c = np.asarray(coeffs, dtype=np.int64) % p
     if p == 2:
@@ -315,6 +315,6 @@ def delayed_k_bound(p: int, k: int, acc_bits: int = 31) -> int:
     """Largest K such that every plane-sum coefficient of K products of
     centred elements stays in a signed accumulator of acc_bits magnitude
     bits: each output coefficient collects at most k*K products of size
-    h^2 with h = (p-1)/2 (Eq. 4 with the centred representation)."""
+    h^2 with h = (p-1)/2 (Eq. 3 with the centred representation)."""
     h = 1 if p == 2 else (p - 1) // 2
     return (2 ** acc_bits - 1) // (k * h * h)

@@ -10,7 +10,7 @@
  * no packing into machine words:
  *
  *   * GF(p^k) = Z_p[X]/(P) with P monic irreducible of degree k, elements as
- *     coefficient vectors c_0..c_{k-1} in [0, p-1]   (Sec. 6, canonical
+ *     coefficient vectors c_0..c_{k-1} in [0, p-1]   (Sec. 7, canonical
  *     representation of a finite field extension).
  *   * A product a*b is the schoolbook product in Z[X] (Eq. 1 gives its
  *     coefficients sum_{i+j=t} alpha_i beta_j), each coefficient reduced
@@ -23,7 +23,7 @@
  *     for r~ = sum_i mu~_i q^i with 0 <= mu~_i < q; the plain oracle extracts
  *     the base-q digits by repeated integer division.  A second routine walks
  *     Alg. 2's own steps (rop, u_i, mu_i) in 128-bit integers so the worked
- *     Example 4 and Thm. 2's invariants can be checked.
+ *     Example 3 and Thm. 2's invariants can be checked.
  *
  * Conventions where the paper is silent (the readings taken):
  *   * The default defining polynomial is the monic irreducible of degree k
@@ -249,7 +249,7 @@ void or_polymul(uint32_t p, uint32_t k, int64_t count, const int32_t *a, const i
     }
 }
 
-/* Long polynomial products in Z_p[X] (Sec. 7's workload, the plain
+/* Long polynomial products in Z_p[X] (Sec. 6's workload, the plain
  * definition behind both the classical method and the d-FQT): a and b are
  * count polynomials of degree N (N+1 coefficients each, lowest first);
  * out[s*(2N+1) + t] = (sum_{i+j=t} a_i b_j) mod p, accumulated in int64. */

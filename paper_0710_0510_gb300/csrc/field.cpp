@@ -1,9 +1,9 @@
 // Host-side construction of GF(p^k) and of the tables the kernels read.
 //
-// Sec. 6: the field is Z_p[X]/(P) with P irreducible of degree k; elements
+// Sec. 7: the field is Z_p[X]/(P) with P irreducible of degree k; elements
 // are stored as discrete logarithms of a generator and converted with
 // tables.  Sec. 2 / Thm. 1 (Eq. 2) fix the q-adic radix and block size,
-// Eq. 4 the plane-accumulation bound, Thm. 3 the two correction-and-fold
+// Eq. 3 the plane-accumulation bound, Thm. 3 the two correction-and-fold
 // tables that replace the radix conversion and the division by P.
 #include <cstring>
 
@@ -204,7 +204,7 @@ int build_field(Field &f, uint32_t p, uint32_t k, const uint32_t *poly) {
     const uint64_t step = (uint64_t)k * (p - 1) * (p - 1);
     f.n_q = (uint32_t)std::min<uint64_t>((q - 1) / step, 1u << 30);
 
-    // Eq. 4 with the centred representation: k K h^2 <= 2^31 - 1.
+    // Eq. 3 with the centred representation: k K h^2 <= 2^31 - 1.
     const uint64_t hh = (uint64_t)f.h * f.h;
     f.k_max_int32 = (int64_t)(((1ull << 31) - 1) / (k * hh));
     // FP32 accumulation: a drained residue (|.| <= 1.5 p, see the tensor-core

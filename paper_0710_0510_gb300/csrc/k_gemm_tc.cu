@@ -4,14 +4,14 @@
 // coefficients C_t = sum_{i+j=t} A_i B_j.  For matrices the same holds with
 // A_i, B_j the coefficient planes, so C = A*B over GF(p^k) is k^2 plane
 // products accumulated into 2k-1 plane sums, each reduced mod p and then
-// folded mod P with X^t mod P (the role of Alg. 4 lines 8-10 / Thm. 3).
+// folded mod P with X^t mod P (the role of Alg. 4's fold step / Thm. 3).
 //
 // GB300 has no integer tcgen05 MMA (kind::i8 does not exist on sm_103a), so
 // the planes are fed as bf16 holding small integers exactly (|c| <= 127 <
 // 256) and accumulated in FP32 in tensor memory.  FP32 is exact while every
 // partial sum stays within 2^24; the host derives the K-chunk for which that
 // holds (a drained residue of magnitude <= 2p plus k K h^2, h = (p-1)/2,
-// the delayed-reduction argument of Eq. 4 with a 24-bit mantissa), and at
+// the delayed-reduction argument of Eq. 3 with a 24-bit mantissa), and at
 // each chunk boundary the epilogue warps reduce the accumulators in place
 // (tcgen05.ld, x - p*rint(x/p), tcgen05.st) before the MMAs continue.
 //

@@ -1,5 +1,5 @@
-// DQT pack (Sec. 2 and Sec. 6, improvement 1: "replace the Horner
-// evaluation by a single table lookup"; Alg. 4 line 1).
+// DQT pack (Sec. 2 and Sec. 7, improvement 1: "replace the Horner
+// evaluation by a single table lookup"; Alg. 4's pack step).
 //
 // Inputs: discrete-log codes (uint8/uint16), uint8 coefficient planes in
 // [0, p-1], or int8 coefficient planes (any representative).  Outputs:

@@ -1,4 +1,4 @@
-// Long polynomial products over Z_p by the d-FQT (Sec. 7, Table 1).
+// Long polynomial products over Z_p by the d-FQT (Sec. 6, Table 2).
 //
 // A polynomial of degree N is cut into D_q + 1 blocks of d + 1 coefficients
 // (P = sum_i P_i Y^i with Y = X^(d+1)), and each block is packed into one
@@ -12,7 +12,7 @@
 // the sum of at most two residues mod p.
 //
 // d = 0 is the classical algorithm with delayed reduction (one coefficient
-// per word, a plain mod p every n_q products), the other row of Table 1.
+// per word, a plain mod p every n_q products), the other row of Table 2.
 //
 // Two machine words:
 //   binary64 (the paper's choice): exact FMAs on integers < 2^51, floor(r/p)
@@ -30,7 +30,7 @@
 // each step loads one P_i and one Q_j for kTB multiply-adds.  After every
 // `chunk` <= n_q products each accumulator is reduced by REDQ and the
 // reduced word rho (digits < p) is fed back as the start of the next chunk
-// -- the reduction "delayed as long as the bounds hold" of Sec. 7.  The
+// -- the reduction "delayed as long as the bounds hold" of Sec. 6.  The
 // item's final words are unpacked into per-coefficient residue sums in
 // shared memory (atomics: pieces of the same t run on different threads),
 // and a last pass adds the overlapping digits mod p and stores bytes.

@@ -6,7 +6,7 @@
 //            (or the single-rounded product when Eq. 2 holds for m = 53)
 //   REDQ:    rop = floor(r/p) (one multiply-high), u_i = (r >> s i) -
 //            p (rop >> s i), mu_{2k-2} = u_{2k-2}, mu_i = (u_i - q u_{i+1})
-//            mod p through a p^2 table (Table 2, "p^2 extra memory, d
+//            mod p through a p^2 table (Table 1, "p^2 extra memory, d
 //            accesses").
 // With QADIC_POLYMUL_INT_WORDS the product is taken in 64-bit integer
 // words instead (Sec. 2 allows m = 64): one integer multiply, exact.

@@ -5,7 +5,7 @@
 //          then floor) -- or an integer multiply-high (QADIC_REDQ_INT_FLOOR)
 //   u_j  = (r >> s j) - p (rop >> s j)                       (Alg. 2, Thm. 2)
 //   mu_d = u_d, mu_j = (u_j - q u_{j+1}) mod p               (Sec. 5.1: Q_d u)
-// with the corrections evaluated per Table 2's time-memory trade-off:
+// with the corrections evaluated per Table 1's time-memory trade-off:
 //   mode 0: arithmetic (d mul/add/mod)
 //   mode 1: p^2 table, d lookups   -- held in registers across the warp and
 //           read with __shfl_sync when p^2 <= 64, else in shared memory
@@ -221,7 +221,7 @@ redq_kernel(const double *__restrict__ in, double *__restrict__ out, int64_t cou
 // vanish (mu_j = u_j, Thm. 2) and no table is needed; the price is that the
 // divisions by q^j are no longer shifts.  Each is a Lemma 1 floor by a
 // precomputed 1/q^j rounded up (or an integer multiply-high), and
-// floor(rop/q^j) = floor(r/(p q^j)) (nested floors, as in the proof of
+// floor(rop/q^j) = floor(r/(p q^j)) (nested floors, Lemma 2; used in the proof of
 // Thm. 2) makes every digit independent of the others:
 //   u_j = floor(r/q^j) - p floor(r/(p q^j)),   rho = sum_j u_j q^j.
 constexpr int kMaxPqDigits = 51;

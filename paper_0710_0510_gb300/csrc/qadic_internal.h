@@ -14,7 +14,7 @@ namespace qadic {
 
 constexpr uint32_t kMaxK = 8;
 
-// Host + device copy of everything a field needs (Sec. 6: conversion tables
+// Host + device copy of everything a field needs (Sec. 7: conversion tables
 // between the log, polynomial and q-adic representations).
 struct Field {
     uint32_t p = 0, k = 0, order = 0;       // order = p^k
@@ -22,7 +22,7 @@ struct Field {
     uint32_t gen[16] = {0};
     uint32_t log2_q = 0, n_q = 0;           // FP64 q-adic radix and block (Eq. 2)
     uint32_t h = 0;                         // centred bound (p-1)/2, 1 for p = 2
-    int64_t k_max_int32 = 0;                // Eq. 4, 32-bit signed accumulator
+    int64_t k_max_int32 = 0;                // Eq. 3, 32-bit signed accumulator
     int64_t k_chunk_f32 = 0;                // exact FP32 accumulation chunk
     int device = 0;
 

@@ -24,7 +24,7 @@ def polymul_pairs(count: int, p: int, k: int, index: int = 0, salt: int = 0):
 
 
 def polylong_pairs(count: int, N: int, p: int, index: int = 5, salt: int = 0):
-    """count pairs of degree-N polynomials over Z_p (Sec. 7's workload; the
+    """count pairs of degree-N polynomials over Z_p (Sec. 6's workload; the
     paper's example is p = 3, N = 500): coefficients uniform in [0, p-1],
     uint8 arrays of shape (count, N+1)."""
     g = rng(index, salt)

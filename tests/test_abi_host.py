@@ -155,7 +155,7 @@ def test_redq_pq_rejections():
 @pytest.mark.parametrize("int_words", [False, True])
 def test_fqt_parameters_satisfy_eq2(p, int_words):
     """q = 2^s as large as the word allows, n_q the largest count with
-    q > n_q (d+1)(p-1)^2 + (p-1), D_q = ceil((N+1)/(d+1)) - 1 (Sec. 7)."""
+    q > n_q (d+1)(p-1)^2 + (p-1), D_q = ceil((N+1)/(d+1)) - 1 (Sec. 6)."""
     for d in range(0, 8):
         D = 2 * d + 1
         s = min(64 // D, 32 // (d + 1)) if int_words else 51 // D
@@ -182,7 +182,7 @@ def test_fqt_parameters_satisfy_eq2(p, int_words):
 
 def test_fqt_paper_example_parameters():
     """p = 3, N = 500 with binary64 words: d = 2 packs 3 coefficients into
-    q = 2^10 with 85 products between reductions, D_q = 166 (Sec. 7 uses
+    q = 2^10 with 85 products between reductions, D_q = 166 (Sec. 6 uses
     this N and p)."""
     info = q.polymul_fqt_info(3, 500, 2)
     assert (info.log2_q, info.n_q, info.D_q) == (10, 85, 166)

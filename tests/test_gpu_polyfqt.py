@@ -1,4 +1,4 @@
-"""GPU parity of the d-FQT long polynomial product (Sec. 7) against the
+"""GPU parity of the d-FQT long polynomial product (Sec. 6) against the
 oracle's schoolbook product, element by element, bit-exact."""
 import numpy as np
 import pytest

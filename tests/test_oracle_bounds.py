@@ -1,4 +1,4 @@
-"""Pins for the bounds the method relies on (Thm. 1 / Eq. 2, Eq. 4) and for
+"""Pins for the bounds the method relies on (Thm. 1 / Eq. 2, Eq. 3) and for
 the reading that the single-rounded FP64 product of the 65,536-pair
 polynomial workload (p = 7, k = 4, q = 2^8) breaks Eq. 2.  CPU only."""
 import numpy as np
@@ -64,7 +64,7 @@ def test_eq4_int32_plane_bound(orc, p, k, K):
     h = 1 if p == 2 else (p - 1) // 2
     assert orc.delayed_k_bound(p, k, 31) == K
     assert k * K * h * h <= 2 ** 31 - 1 < k * (K + 1) * h * h
-    # Eq. 4 form: n_d (p-1)^2 < 2^(m+1) with m = 31 bits of magnitude
+    # Eq. 3 form: n_d (p-1)^2 < 2^(m+1) with m = 31 bits of magnitude
     if p > 2:
         nd = k * K
         assert nd * (p - 1) ** 2 < 2 ** 33

@@ -1,5 +1,5 @@
 """Pins for the oracle's long polynomial product in Z_p[X] (the workload of
-Sec. 7: degree-N polynomials, Table 1's comparison of the classical method
+Sec. 6: degree-N polynomials, Table 2's comparison of the classical method
 with the d-FQT).  CPU only."""
 import numpy as np
 import pytest

@@ -12,8 +12,8 @@ GOLD = os.path.join(os.path.dirname(__file__), "golden")
 EX = json.load(open(os.path.join(GOLD, "paper_examples.json")))
 
 
-def test_example3_p_divides_q(orc):
-    ex = EX["example3"]
+def test_example2_p_divides_q(orc):
+    ex = EX["example2"]
     p, q = ex["p"], ex["q"]
     r = int(orc.qadic_value(ex["a"], q)) * int(orc.qadic_value(ex["b"], q))
     assert r == ex["product"]
@@ -27,8 +27,8 @@ def test_example3_p_divides_q(orc):
     assert r - p * quot == ex["rho"]
 
 
-def test_example4_full_redq(orc):
-    ex = EX["example4"]
+def test_example3_full_redq(orc):
+    ex = EX["example3"]
     p, q, r = ex["p"], ex["q"], ex["r"]
     assert int(sum(c * q ** i for i, c in enumerate(ex["coefficients"]))) == r
     rop, u, mu = orc.redq_alg2_u128(p, q, 3, r)
@@ -104,11 +104,11 @@ def test_redq_large_words_vs_u128(orc):
 
 # ------------------------------------------ q a multiple of p (Sec. 4) ----
 
-def test_example3_result_at_a_smaller_multiple_of_p(orc):
-    """Ex. 3's product, packed with q = 100 (also a multiple of p = 5, and
+def test_example2_result_at_a_smaller_multiple_of_p(orc):
+    """Ex. 2's product, packed with q = 100 (also a multiple of p = 5, and
     large enough for its coefficients) so that the word is an exact double:
     the oracle's word-level REDQ returns the example's residues."""
-    ex = EX["example3"]
+    ex = EX["example2"]
     p, q = ex["p"], 100
     r = int(orc.qadic_value(ex["a"], q)) * int(orc.qadic_value(ex["b"], q))
     assert r < 2 ** 53
@@ -118,7 +118,7 @@ def test_example3_result_at_a_smaller_multiple_of_p(orc):
 
 @pytest.mark.parametrize("p,q,d", [(3, 6, 2), (5, 10, 3), (2, 4, 4), (7, 7, 2)])
 def test_redq_p_divides_q_shortcut(orc, p, q, d):
-    """With p | q the whole reduction is one subtraction (Ex. 3):
+    """With p | q the whole reduction is one subtraction (Ex. 2):
     rho = r - p * sum_i floor(mu~_i / p) q^i, over every word with d+1
     base-q digits."""
     words = np.arange(q ** (d + 1), dtype=np.int64)
@@ -157,7 +157,7 @@ def test_lemma1_composite_divisors(orc, D):
 
 
 def test_nested_floor_identity():
-    """floor(floor(r/p)/q^j) = floor(r/(p q^j)) (used in the proof of Thm. 2),
+    """floor(floor(r/p)/q^j) = floor(r/(p q^j)) (Lemma 2, used in the proof of Thm. 2),
     the identity that lets each digit's second floor divide r directly."""
     rng = np.random.default_rng(5)
     for p, q in [(7, 1176), (5, 10), (3, 8), (251, 251)]:
@@ -187,8 +187,8 @@ def test_qd_is_inverse_of_power_matrix():
         assert (prod == np.eye(d + 1, dtype=object)).all()
 
 
-def test_example4_matrix_form(orc):
-    ex = EX["example4"]
+def test_example3_matrix_form(orc):
+    ex = EX["example3"]
     mu = (qd_matrix(3, ex["q"], ex["p"]) @ np.array(ex["u"])) % ex["p"]
     assert mu.tolist() == ex["mu"]
 
