@@ -394,6 +394,9 @@ def bench_redq(args, torch, q, W, count=None, steps=10):
             "value": 5.0 * count / (pms * 1e-3), "unit": "residues/s", "ms": pms,
             "roofline": {"bound": "hbm", "achieved": pgbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
                          "frac": pgbs / pk["hbm_gbs"], "traffic": None}}
+        if not int_floor:
+            # the Lemma 1 form is bound by the FP64 pipe: 4 round-up multiplies a word
+            pq["lemma1"]["fp64_pipe"] = fp64_pipe(4.0 * count, pms)
     del dq
     return None, out, {"value": 5.0 * count / (ms * 1e-3), "unit": "residues/s", "best": key,
                        "ms": ms, "words": count,
@@ -401,6 +404,19 @@ def bench_redq(args, torch, q, W, count=None, steps=10):
                                     "unit": "GB/s", "frac": gbs / pk["hbm_gbs"], "traffic": None},
                        "variants": res,
                        "q_multiple_of_p": {"p": 7, "q": PQ_Q, "digits": 5, **pq}}
+
+
+# FP64 multiplies (or FMAs) per second measured on this GPU: DFMA 1.01
+# TFLOP/s counts two flops per instruction.
+FP64_OPS_PEAK = 0.505e12
+
+
+def fp64_pipe(ops, ms):
+    """Second roofline for a kernel whose FP64 instructions are the limit."""
+    rate = ops / (ms * 1e-3)
+    return {"bound": "alu (FP64 pipe)", "ops_per_launch": ops, "achieved_Tops": rate / 1e12,
+            "peak_Tops": FP64_OPS_PEAK / 1e12, "frac": rate / FP64_OPS_PEAK,
+            "peak_source": "measured DFMA rate 1.01 TFLOP/s / 2 flops per instruction"}
 
 
 def bench_polymul(args, torch, q, W, count=65536, steps=50):
@@ -442,6 +458,7 @@ def bench_polymul(args, torch, q, W, count=65536, steps=50):
                            "roofline": {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"],
                                         "unit": "GB/s", "frac": gbs / pk["hbm_gbs"],
                                         "traffic": None, "bytes_per_pair": 15},
+                           "fp64_pipe": fp64_pipe(2.0 * big, msb),
                            "int64_words": {"value": big / (msi * 1e-3), "ms": msi,
                                            "GB/s": gbi, "frac": gbi / pk["hbm_gbs"]}}}
 

@@ -245,9 +245,10 @@ int qadic_redq(uint32_t p, uint32_t log2_q, uint32_t ndigits, const double *in, 
  * REDQ (Alg. 2) for q a multiple of p, the other choice of q that the
  * paper's conclusion leaves to compare (q = 10^4, p = 5 in Ex. 2).  Since
  * -q = 0 mod p the corrections of Alg. 2 vanish and mu_j = u_j (Thm. 2): no
- * table.  Each division by q^j (no longer a shift) is a Lemma 1 floor by
- * 1/q^j rounded upward, or with QADIC_REDQ_INT_FLOOR an integer
- * multiply-high, and floor(rop/q^j) = floor(r/(p q^j)).
+ * table.  The divisions by q^j (no longer shifts) are taken as a chain
+ * t_{j+1} = floor(t_j / q) (Lemma 2), each a Lemma 1 floor by 1/q rounded
+ * upward, or with QADIC_REDQ_INT_FLOOR an integer multiply-high; then
+ * u_j = t_j mod p = (t_j - q t_{j+1}) mod p since p | q.
  * in[i] = sum_{j<=d} mu~_j q^j with 0 <= mu~_j < q, d = ndigits-1, an exact
  * integer held in a double; out[i] = rho = sum_j (mu~_j mod p) q^j (exact).
  * Requires p prime <= 251, q >= p with p | q, q^ndigits <= 2^51 (else

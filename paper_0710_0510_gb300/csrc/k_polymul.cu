@@ -28,19 +28,67 @@ __device__ __forceinline__ int64_t f64_to_i64_exact(double x) {
     return x < 0.0 ? -mag : mag;
 }
 
+// The K coefficient bytes of pair idx, byte j at bits 8j: one vector load
+// for K = 1, 2, 4, 8 (when the base is aligned), byte loads otherwise.
+template <int K>
+__device__ __forceinline__ uint64_t load_pair(const uint8_t *__restrict__ base, int64_t idx,
+                                              bool aligned) {
+    if (K == 1) return __ldg(base + idx);
+    if (K == 2 && aligned) return __ldg(reinterpret_cast<const uint16_t *>(base) + idx);
+    if (K == 4 && aligned) return __ldg(reinterpret_cast<const uint32_t *>(base) + idx);
+    if (K == 8 && aligned)
+        return (uint64_t)__ldg(reinterpret_cast<const unsigned long long *>(base) + idx);
+    uint64_t v = 0;
+#pragma unroll
+    for (int j = 0; j < K; ++j) v |= (uint64_t)__ldg(base + idx * K + j) << (8 * j);
+    return v;
+}
+
+// DQT of one operand (Alg. 1, packing with a power-of-two q): each
+// coefficient byte taken mod p, then placed at bit s j.  The shifts are
+// multiplies by 2^(s j) (pw[j]) so that each coefficient costs one
+// multiply-add into the word.
+template <int K>
+__device__ __forceinline__ uint64_t pack_word(uint64_t bytes, uint32_t p, uint32_t m32,
+                                              const uint64_t (&pw)[K]) {
+    uint64_t w = 0;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const uint32_t c = mod_small((uint32_t)(bytes >> (8 * j)) & 0xffu, p, m32);
+        w += (uint64_t)c * pw[j];
+    }
+    return w;
+}
+
+// Same, when the packed word fits 32 bits (K s <= 32).
+template <int K>
+__device__ __forceinline__ uint32_t pack_word32(uint64_t bytes, uint32_t p, uint32_t m32,
+                                                const uint64_t (&pw)[K]) {
+    uint32_t w = 0;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const uint32_t c = mod_small((uint32_t)(bytes >> (8 * j)) & 0xffu, p, m32);
+        w += c * (uint32_t)pw[j];
+    }
+    return w;
+}
+
 // MODE 0: FP64 product made exact as hi + lo (lo = fma(a, b, -hi));
 // MODE 1: single-rounded FP64 product (Eq. 2 with m = 53 must hold);
 // MODE 2: 64-bit integer words, r = a~ b~ exactly (Sec. 2 allows m = 64).
 // The conversions between the packed integers and doubles are done on the
 // bit patterns, so the FP64 pipe only sees the multiply (and the FMA).
-template <int MODE, int kPairs>
+// K (the number of coefficients of an operand) is a template argument so
+// that every loop over coefficients unrolls and every shift amount is a
+// register computed once per thread.
+template <int MODE, int K, int kPairs>
 __global__ void __launch_bounds__(kThreads)
 polymul_kernel(const uint8_t *__restrict__ a, const uint8_t *__restrict__ b,
-               uint8_t *__restrict__ out, int64_t count, uint32_t p, uint32_t k, uint32_t s,
+               uint8_t *__restrict__ out, int64_t count, uint32_t p, uint32_t s,
                uint32_t qneg_mod_p, Div64 divp) {
     extern __shared__ __align__(16) uint8_t smem[];
     constexpr int kChunk = kThreads * kPairs;
-    const uint32_t D = 2 * k - 1;
+    constexpr int D = 2 * K - 1;
     uint8_t *corr = smem;                           // p*p entries
     uint8_t *stage = smem + ((p * p + 15) & ~15u);  // kChunk * D bytes (16-byte aligned)
 
@@ -51,45 +99,40 @@ polymul_kernel(const uint8_t *__restrict__ a, const uint8_t *__restrict__ b,
     }
     __syncthreads();
 
+    uint64_t pw[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) pw[j] = 1ull << (s * j);
+    const bool narrow = s * K <= 32;   // packed operands fit 32 bits
+    const bool aligned = ((((uintptr_t)a | (uintptr_t)b) & (K == 8 ? 7 : K == 4 ? 3 : 1)) == 0);
+
     // Grid-stride over chunks of kPairs * kThreads pairs (the table is built
     // once).  Each thread issues the operand loads of its kPairs pairs first,
     // so several loads are in flight, then reduces them; the chunk's output
     // bytes leave through shared memory as 16-byte stores.
-    const bool vec4 = k == 4 && ((((uintptr_t)a | (uintptr_t)b) & 3) == 0);
     for (int64_t base = (int64_t)blockIdx.x * kChunk; base < count;
          base += (int64_t)gridDim.x * kChunk) {
-        uint32_t wa[kPairs] = {}, wb[kPairs] = {};
-        if (vec4) {
+        uint64_t va[kPairs], vb[kPairs];
 #pragma unroll
-            for (int j = 0; j < kPairs; ++j) {
-                const int64_t idx = base + j * kThreads + threadIdx.x;
-                if (idx < count) {
-                    wa[j] = __ldg(reinterpret_cast<const uint32_t *>(a) + idx);
-                    wb[j] = __ldg(reinterpret_cast<const uint32_t *>(b) + idx);
-                }
-            }
+        for (int j = 0; j < kPairs; ++j) {
+            const int64_t idx = base + j * kThreads + threadIdx.x;
+            va[j] = idx < count ? load_pair<K>(a, idx, aligned) : 0;
+            vb[j] = idx < count ? load_pair<K>(b, idx, aligned) : 0;
         }
 #pragma unroll
         for (int j = 0; j < kPairs; ++j) {
             const int64_t idx = base + j * kThreads + threadIdx.x;
             if (idx >= count) break;
-            uint64_t aw = 0, bw = 0;
-            if (vec4) {
-#pragma unroll
-                for (uint32_t i = 0; i < 4; ++i) {
-                    aw |= (uint64_t)mod_small((wa[j] >> (8 * i)) & 0xff, p, m32) << (s * i);
-                    bw |= (uint64_t)mod_small((wb[j] >> (8 * i)) & 0xff, p, m32) << (s * i);
-                }
-            } else {
-                for (uint32_t i = 0; i < k; ++i) {   // coefficients taken mod p
-                    aw |= (uint64_t)mod_small(__ldg(a + idx * k + i), p, m32) << (s * i);
-                    bw |= (uint64_t)mod_small(__ldg(b + idx * k + i), p, m32) << (s * i);
-                }
-            }
             uint64_t r;
             if (MODE == 2) {
-                r = aw * bw;   // < 2^((2k-1) s) <= 2^63: exact in 64 bits
+                if (narrow) {
+                    r = (uint64_t)pack_word32<K>(va[j], p, m32, pw) *
+                        pack_word32<K>(vb[j], p, m32, pw);
+                } else {
+                    r = pack_word<K>(va[j], p, m32, pw) * pack_word<K>(vb[j], p, m32, pw);
+                }   // < 2^((2k-1) s) <= 2^63: exact in 64 bits
             } else {
+                const uint64_t aw = pack_word<K>(va[j], p, m32, pw);
+                const uint64_t bw = pack_word<K>(vb[j], p, m32, pw);
                 const double ad = u64_to_f64_exact(aw), bd = u64_to_f64_exact(bw);   // < 2^53
                 const double hi = ad * bd;
                 if (MODE == 1) {
@@ -104,12 +147,16 @@ polymul_kernel(const uint8_t *__restrict__ a, const uint8_t *__restrict__ b,
                     r = hi_u + (uint64_t)f64_to_i64_exact(lo);
                 }
             }
+            // REDQ (Alg. 2): rop = floor(r/p); u_i = floor(r/q^i) - p floor(rop/q^i)
+            // needs only the low 32 bits of each shifted word (u_i < p).
             const uint64_t rop = div64(r, divp);
-            uint32_t u_next = 0;
             uint8_t *dst = stage + (j * kThreads + threadIdx.x) * D;
-            for (int i = (int)D - 1; i >= 0; --i) {
-                const uint32_t ui = (uint32_t)((r >> (s * i)) - (uint64_t)p * (rop >> (s * i)));
-                dst[i] = (i == (int)D - 1) ? (uint8_t)ui : corr[ui * p + u_next];
+            uint32_t u_next = 0;
+#pragma unroll
+            for (int i = D - 1; i >= 0; --i) {
+                const uint32_t sh = s * i;
+                const uint32_t ui = (uint32_t)(r >> sh) - p * (uint32_t)(rop >> sh);
+                dst[i] = (i == D - 1) ? (uint8_t)ui : corr[ui * p + u_next];
                 u_next = ui;
             }
         }
@@ -129,6 +176,33 @@ polymul_kernel(const uint8_t *__restrict__ a, const uint8_t *__restrict__ b,
     }
 }
 
+template <int MODE, int K>
+auto pick_kernel(int pairs) {
+    return pairs == kMaxPairs ? polymul_kernel<MODE, K, kMaxPairs> : polymul_kernel<MODE, K, 1>;
+}
+
+template <int K>
+auto pick_kernel(int mode, int pairs) {
+    return mode == 2 ? pick_kernel<2, K>(pairs)
+                     : mode == 1 ? pick_kernel<1, K>(pairs) : pick_kernel<0, K>(pairs);
+}
+
+using PolymulKernel = void (*)(const uint8_t *, const uint8_t *, uint8_t *, int64_t, uint32_t,
+                               uint32_t, uint32_t, Div64);
+
+PolymulKernel select_kernel(uint32_t k, int mode, int pairs) {
+    switch (k) {
+        case 1: return pick_kernel<1>(mode, pairs);
+        case 2: return pick_kernel<2>(mode, pairs);
+        case 3: return pick_kernel<3>(mode, pairs);
+        case 4: return pick_kernel<4>(mode, pairs);
+        case 5: return pick_kernel<5>(mode, pairs);
+        case 6: return pick_kernel<6>(mode, pairs);
+        case 7: return pick_kernel<7>(mode, pairs);
+        default: return pick_kernel<8>(mode, pairs);
+    }
+}
+
 }  // namespace
 
 int launch_polymul(uint32_t p, uint32_t k, uint32_t log2_q, int mode, const uint8_t *a,
@@ -142,11 +216,7 @@ int launch_polymul(uint32_t p, uint32_t k, uint32_t log2_q, int mode, const uint
     const int pairs = count >= (int64_t)sms * kThreads * kMaxPairs * 2 ? kMaxPairs : 1;
     const int64_t chunk = (int64_t)kThreads * pairs;
     const size_t smem = ((p * p + 15) & ~15u) + (size_t)chunk * (2 * k - 1);
-    auto kern = pairs == kMaxPairs
-                    ? (mode == 2 ? polymul_kernel<2, kMaxPairs>
-                                 : mode == 1 ? polymul_kernel<1, kMaxPairs> : polymul_kernel<0, kMaxPairs>)
-                    : (mode == 2 ? polymul_kernel<2, 1>
-                                 : mode == 1 ? polymul_kernel<1, 1> : polymul_kernel<0, 1>);
+    const PolymulKernel kern = select_kernel(k, mode, pairs);
     if (smem > 48 * 1024) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
@@ -155,7 +225,7 @@ int launch_polymul(uint32_t p, uint32_t k, uint32_t log2_q, int mode, const uint
     }
     int64_t blocks = (count + chunk - 1) / chunk;
     blocks = std::min<int64_t>(blocks, resident_blocks(kern, kThreads, smem));
-    kern<<<(unsigned)blocks, kThreads, smem, stream>>>(a, b, out, count, p, k, log2_q, qneg,
+    kern<<<(unsigned)blocks, kThreads, smem, stream>>>(a, b, out, count, p, log2_q, qneg,
                                                        make_div64(p));
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(QADIC_E_CUDA, "polymul launch: %s", cudaGetErrorString(e));

@@ -219,37 +219,49 @@ redq_kernel(const double *__restrict__ in, double *__restrict__ out, int64_t cou
 // ---------------------------------------------------------------------------
 // REDQ with q a multiple of p.  Then -q = 0 mod p, so Alg. 2's corrections
 // vanish (mu_j = u_j, Thm. 2) and no table is needed; the price is that the
-// divisions by q^j are no longer shifts.  Each is a Lemma 1 floor by a
-// precomputed 1/q^j rounded up (or an integer multiply-high), and
-// floor(rop/q^j) = floor(r/(p q^j)) (nested floors, Lemma 2; used in the proof of
-// Thm. 2) makes every digit independent of the others:
-//   u_j = floor(r/q^j) - p floor(r/(p q^j)),   rho = sum_j u_j q^j.
+// divisions by q^j are no longer shifts.  They are taken as a chain:
+// t_{j+1} = floor(t_j / q) with t_0 = r gives t_j = floor(r/q^j) (nested
+// floors, Lemma 2), each step a Lemma 1 floor by 1/q rounded up (or an
+// integer multiply-high).  Lemma 2 also gives floor(rop/q^j) =
+// floor(t_j / p), so u_j = t_j - p floor(t_j/p) = t_j mod p, and as p | q,
+// t_j mod p = (t_j - q t_{j+1}) mod p: the mod p of r's base-q digit, a
+// number below q, by one small multiply-high.  d floors by q per word in all
+// (instead of 2d+1 floors by q^j and p q^j).
 constexpr int kMaxPqDigits = 51;
 
 struct RedqPqParams {
     uint32_t p, d;
+    uint32_t m32;                      // ceil(2^32 / p)
+    uint64_t q, small_lim;             // small_lim = floor(2^32 / p)
+    double inv_q_up;                   // 1/q rounded toward +infinity
+    Div64 div_q, div_p;
     uint64_t qpow[kMaxPqDigits];       // q^j
-    double inv_q_up[kMaxPqDigits];     // 1/q^j rounded toward +infinity
-    double inv_pq_up[kMaxPqDigits];    // 1/(p q^j) rounded toward +infinity
-    Div64 div_q[kMaxPqDigits], div_pq[kMaxPqDigits];
 };
+
+// x mod p for any 64-bit x: one 32-bit multiply-high below 2^32 / p (where
+// the rounded-up reciprocal is exact), a 64-bit one above.
+__device__ __forceinline__ uint32_t mod_p_any(uint64_t x, const RedqPqParams &P) {
+    if (x < P.small_lim) return mod_small((uint32_t)x, P.p, P.m32);
+    return (uint32_t)(x - P.p * div64(x, P.div_p));
+}
 
 template <bool INT_FLOOR>
 __device__ __forceinline__ double redq_pq_word(double x, const RedqPqParams &P) {
-    const uint64_t r = f64_to_u64_exact(x);
+    uint64_t t = f64_to_u64_exact(x);
+    double tx = x;
     uint64_t rho = 0;
-    for (uint32_t j = 0; j <= P.d; ++j) {
-        uint64_t a, b;   // floor(r / q^j), floor(r / (p q^j))
+    for (uint32_t j = 0; j < P.d; ++j) {
+        uint64_t tn;   // floor(r / q^(j+1))
         if (INT_FLOOR) {
-            a = j == 0 ? r : div64(r, P.div_q[j]);
-            b = div64(r, P.div_pq[j]);
+            tn = div64(t, P.div_q);
         } else {
-            a = j == 0 ? r : f64_to_u64_exact(__dmul_ru(x, P.inv_q_up[j]));
-            b = f64_to_u64_exact(__dmul_ru(x, P.inv_pq_up[j]));
+            tn = f64_to_u64_exact(__dmul_ru(tx, P.inv_q_up));
+            tx = u64_to_f64_exact(tn);
         }
-        const uint32_t u = (uint32_t)a - P.p * (uint32_t)b;
-        rho += (uint64_t)u * P.qpow[j];
+        rho += (uint64_t)mod_p_any(t - P.q * tn, P) * P.qpow[j];
+        t = tn;
     }
+    rho += (uint64_t)mod_p_any(t, P) * P.qpow[P.d];   // t_d < q for words below q^(d+1)
     return u64_to_f64_exact(rho);
 }
 
@@ -389,13 +401,15 @@ int launch_redq_pq(uint32_t p, uint64_t q, uint32_t ndigits, const double *in, d
     RedqPqParams P{};
     P.p = p;
     P.d = ndigits - 1;
+    P.m32 = make_mod_small(p);
+    P.small_lim = ((uint64_t)1 << 32) / p;
+    P.q = q;
+    P.inv_q_up = inv_up(q);
+    P.div_q = make_div64(q);
+    P.div_p = make_div64(p);
     uint64_t qj = 1;
     for (uint32_t j = 0; j < ndigits; ++j) {
         P.qpow[j] = qj;
-        P.inv_q_up[j] = inv_up(qj);
-        P.inv_pq_up[j] = inv_up(qj * p);
-        P.div_q[j] = make_div64(qj);
-        P.div_pq[j] = make_div64(qj * p);
         qj *= q;
     }
     if (int_floor) return launch_stream(redq_pq_kernel<true>, in, out, count, P, 0, stream, "redq_pq");
