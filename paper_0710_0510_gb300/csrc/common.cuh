@@ -40,6 +40,29 @@ __device__ __forceinline__ uint64_t div64(uint64_t n, const Div64 &d) {
     return (t + ((n - t) >> d.sh1)) >> d.sh2;
 }
 
+// The same for 32-bit n and 1 <= d < 2^32 (l = ceil(log2 d),
+// m = floor(2^32 (2^l - d) / d) + 1).
+struct Div32 {
+    uint32_t m;
+    uint32_t sh1, sh2;
+};
+
+inline Div32 make_div32(uint32_t d) {
+    uint32_t l = 0;
+    while (((uint64_t)1 << l) < d) ++l;
+    const uint64_t num = ((uint64_t)1 << 32) * ((((uint64_t)1) << l) - d);
+    Div32 r;
+    r.m = (uint32_t)(num / d + 1);
+    r.sh1 = l < 1 ? l : 1;
+    r.sh2 = l >= 1 ? l - 1 : 0;
+    return r;
+}
+
+__device__ __forceinline__ uint32_t div32(uint32_t n, const Div32 &d) {
+    const uint32_t t = __umulhi(d.m, n);
+    return (t + ((n - t) >> d.sh1)) >> d.sh2;
+}
+
 // x mod d for 0 <= x < 2^16 and d < 256: floor(x/d) = mulhi(x, ceil(2^32/d))
 // (the round-up error (m d - 2^32) x / 2^32 < d x / 2^32 stays below 1/d).
 __device__ __forceinline__ uint32_t mod_small(uint32_t x, uint32_t d, uint32_t m32) {

@@ -232,9 +232,12 @@ constexpr int kMaxPqDigits = 51;
 struct RedqPqParams {
     uint32_t p, d;
     uint32_t m32;                      // ceil(2^32 / p)
+    uint32_t small_q;                  // q <= 2^32 / p: a digit's mod p is one 32-bit multiply-high
+    uint32_t j32;                      // t_j < q^(d+1-j) <= 2^32 from this j on
     uint64_t q, small_lim;             // small_lim = floor(2^32 / p)
     double inv_q_up;                   // 1/q rounded toward +infinity
     Div64 div_q, div_p;
+    Div32 div_q32;                     // floor(t / q) for t < 2^32 (q < 2^32)
     uint64_t qpow[kMaxPqDigits];       // q^j
 };
 
@@ -245,6 +248,12 @@ __device__ __forceinline__ uint32_t mod_p_any(uint64_t x, const RedqPqParams &P)
     return (uint32_t)(x - P.p * div64(x, P.div_p));
 }
 
+// mod p of a base-q digit (< q for words below q^(d+1)).
+__device__ __forceinline__ uint32_t mod_p_digit(uint64_t x, const RedqPqParams &P) {
+    return P.small_q ? mod_small((uint32_t)x, P.p, P.m32) : mod_p_any(x, P);
+}
+
+// Any number of digits (loop over j, q^j from the parameter block).
 template <bool INT_FLOOR>
 __device__ __forceinline__ double redq_pq_word(double x, const RedqPqParams &P) {
     uint64_t t = f64_to_u64_exact(x);
@@ -265,7 +274,41 @@ __device__ __forceinline__ double redq_pq_word(double x, const RedqPqParams &P) 
     return u64_to_f64_exact(rho);
 }
 
-template <bool INT_FLOOR>
+// ND = d + 1 digits known at compile time: the chain unrolls, the integer
+// floors drop to 32 bits once t_j < 2^32 (j >= j32), and rho is assembled
+// by Horner's rule from the top digit.
+template <bool INT_FLOOR, int ND>
+__device__ __forceinline__ double redq_pq_word_nd(double x, const RedqPqParams &P) {
+    uint64_t t = f64_to_u64_exact(x);
+    double tx = x;
+    uint32_t u[ND];
+#pragma unroll
+    for (int j = 0; j < ND - 1; ++j) {
+        if (INT_FLOOR && j >= (int)P.j32) {
+            const uint32_t t32 = (uint32_t)t;
+            const uint32_t tn = div32(t32, P.div_q32);
+            u[j] = mod_p_digit(t32 - (uint32_t)P.q * tn, P);
+            t = tn;
+        } else {
+            uint64_t tn;
+            if (INT_FLOOR) {
+                tn = div64(t, P.div_q);
+            } else {
+                tn = f64_to_u64_exact(__dmul_ru(tx, P.inv_q_up));
+                tx = u64_to_f64_exact(tn);
+            }
+            u[j] = mod_p_digit(t - P.q * tn, P);
+            t = tn;
+        }
+    }
+    u[ND - 1] = ND == 1 ? mod_p_any(t, P) : mod_p_digit(t, P);
+    uint64_t rho = u[ND - 1];
+#pragma unroll
+    for (int j = ND - 2; j >= 0; --j) rho = rho * (uint32_t)P.q + u[j];   // q < 2^26 when ND >= 2
+    return u64_to_f64_exact(rho);
+}
+
+template <bool INT_FLOOR, int ND>
 __global__ void __launch_bounds__(kThreads)
 redq_pq_kernel(const double *__restrict__ in, double *__restrict__ out, int64_t count,
                const __grid_constant__ RedqPqParams P) {
@@ -273,6 +316,10 @@ redq_pq_kernel(const double *__restrict__ in, double *__restrict__ out, int64_t 
     const double2 *in2 = reinterpret_cast<const double2 *>(in);
     double2 *out2 = reinterpret_cast<double2 *>(out);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    auto word = [&](double v) {
+        if constexpr (ND > 0) return redq_pq_word_nd<INT_FLOOR, ND>(v, P);
+        else return redq_pq_word<INT_FLOOR>(v, P);
+    };
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < npairs;
          b += kUnroll * stride) {
         double2 w[kUnroll];
@@ -286,14 +333,13 @@ redq_pq_kernel(const double *__restrict__ in, double *__restrict__ out, int64_t 
             const int64_t i = b + s * stride;
             if (i < npairs) {
                 double2 o;
-                o.x = redq_pq_word<INT_FLOOR>(w[s].x, P);
-                o.y = redq_pq_word<INT_FLOOR>(w[s].y, P);
+                o.x = word(w[s].x);
+                o.y = word(w[s].y);
                 __stcs(out2 + i, o);
             }
         }
     }
-    if ((count & 1) && blockIdx.x == 0 && threadIdx.x == 0)
-        out[count - 1] = redq_pq_word<INT_FLOOR>(in[count - 1], P);
+    if ((count & 1) && blockIdx.x == 0 && threadIdx.x == 0) out[count - 1] = word(in[count - 1]);
 }
 
 template <typename Kern, typename Params>
@@ -412,8 +458,29 @@ int launch_redq_pq(uint32_t p, uint64_t q, uint32_t ndigits, const double *in, d
         P.qpow[j] = qj;
         qj *= q;
     }
-    if (int_floor) return launch_stream(redq_pq_kernel<true>, in, out, count, P, 0, stream, "redq_pq");
-    return launch_stream(redq_pq_kernel<false>, in, out, count, P, 0, stream, "redq_pq");
+    P.small_q = q <= P.small_lim;
+    P.div_q32 = make_div32(q < ((uint64_t)1 << 32) ? (uint32_t)q : 1u);
+    // first j with q^(ndigits - j) <= 2^32 (then t_j < 2^32); ndigits if none
+    P.j32 = ndigits;
+    for (uint32_t j = 0; j < ndigits; ++j) {
+        unsigned __int128 bound = 1;
+        for (uint32_t i = j; i < ndigits; ++i) bound *= q;
+        if (bound <= ((unsigned __int128)1 << 32)) {
+            P.j32 = j;
+            break;
+        }
+    }
+    switch (int_floor ? ndigits : ndigits + 100) {
+#define QADIC_PQ_CASE(N)                                                                            \
+    case N: return launch_stream(redq_pq_kernel<true, N>, in, out, count, P, 0, stream, "redq_pq"); \
+    case N + 100: return launch_stream(redq_pq_kernel<false, N>, in, out, count, P, 0, stream, "redq_pq");
+        QADIC_PQ_CASE(1) QADIC_PQ_CASE(2) QADIC_PQ_CASE(3) QADIC_PQ_CASE(4)
+        QADIC_PQ_CASE(5) QADIC_PQ_CASE(6) QADIC_PQ_CASE(7) QADIC_PQ_CASE(8)
+#undef QADIC_PQ_CASE
+        default: break;
+    }
+    if (int_floor) return launch_stream(redq_pq_kernel<true, 0>, in, out, count, P, 0, stream, "redq_pq");
+    return launch_stream(redq_pq_kernel<false, 0>, in, out, count, P, 0, stream, "redq_pq");
 }
 
 }  // namespace qadic
