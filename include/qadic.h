@@ -313,9 +313,17 @@ int qadic_polymul_batched(uint32_t p, uint32_t k, const uint8_t *a, const uint8_
 /* -------------------------------------------------------- batched_gemm --
  * `count` independent products descs[i] over fields[descs[i].field] in ONE
  * persistent launch (tiles of all products on a device work list).
- * Requires 1 <= m, n, K <= 4096 per product, k <= 8.  `workspace` must hold
- * qadic_batched_workspace_size(count, descs) bytes (device); the host packs
- * the work list into it.  With QADIC_BATCHED_GRAPH the launch is captured in
+ * Requires 1 <= m, n, K <= 4096 per product, k <= 8.  `workspace` (device,
+ * 256-byte aligned) must hold at least qadic_batched_workspace_size(descs,
+ * count) bytes: the host packs the work list into it, and the operand bytes
+ * are staged through registers tile by tile.  With at least
+ * qadic_batched_workspace_size_fields(fields, nfields, descs, count) bytes
+ * the faster path runs instead: one launch converts every operand once to
+ * centred 16-bit planes in the workspace (bf16; f16 for GF(2^8), whose 0/1
+ * planes keep every partial sum exact in f16 accumulators over chunks of
+ * 2047/k), and the persistent launch copies tiles of them with cp.async.
+ * Both paths give the same bytes.  The size query with fields returns 0 for
+ * invalid arguments.  With QADIC_BATCHED_GRAPH the launch is captured in
  * a CUDA graph keyed by (descs, count, workspace) and replayed on later calls
  * with the same key (and the same tile configurations); a replay first
  * re-uploads its own work list if another call wrote a different one into
@@ -325,6 +333,8 @@ int qadic_polymul_batched(uint32_t p, uint32_t k, const uint8_t *a, const uint8_
  * small), QADIC_E_OVERFLOW (exact FP32 chunk of a field below 32). */
 #define QADIC_BATCHED_GRAPH 0x1u
 size_t qadic_batched_workspace_size(const qadic_gemm_desc *descs, int64_t count);
+size_t qadic_batched_workspace_size_fields(const qadic_field *const *fields, int32_t nfields,
+                                           const qadic_gemm_desc *descs, int64_t count);
 int qadic_batched_gemm(const qadic_field *const *fields, int32_t nfields,
                        const qadic_gemm_desc *descs, int64_t count, void *workspace,
                        size_t ws_bytes, uint32_t flags, void *stream);

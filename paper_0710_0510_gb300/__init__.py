@@ -126,6 +126,8 @@ _SIGS = {
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                              ctypes.c_uint32, ctypes.c_void_p]),
     "qadic_batched_workspace_size": (ctypes.c_size_t, [ctypes.POINTER(GemmDesc), ctypes.c_int64]),
+    "qadic_batched_workspace_size_fields": (ctypes.c_size_t, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32,
+                                                              ctypes.POINTER(GemmDesc), ctypes.c_int64]),
     "qadic_batched_gemm": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32,
                                           ctypes.POINTER(GemmDesc), ctypes.c_int64,
                                           ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32,
@@ -367,9 +369,19 @@ def polymul_batched(p: int, k: int, a, b, out=None, plain_f64: bool = False,
     return out
 
 
-def batched_workspace_size(descs) -> int:
+def batched_workspace_size(descs, fields=None) -> int:
+    """Workspace bytes of ``batched_gemm``: with ``fields``, room for the
+    converted operands too (``qadic_batched_workspace_size_fields``, the
+    faster path); without, the work list alone (operands staged through
+    registers)."""
     arr = (GemmDesc * len(descs))(*descs)
-    return int(lib().qadic_batched_workspace_size(arr, len(descs)))
+    if fields is None:
+        return int(lib().qadic_batched_workspace_size(arr, len(descs)))
+    hs = (ctypes.c_void_p * len(fields))(*[f.handle for f in fields])
+    n = int(lib().qadic_batched_workspace_size_fields(hs, len(fields), arr, len(descs)))
+    if n == 0:
+        raise QadicError(1, "batched_workspace_size: invalid fields or descriptors")
+    return n
 
 
 def batched_gemm(fields, descs, workspace, graph: bool = False, stream=None):

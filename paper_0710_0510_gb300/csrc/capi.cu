@@ -1,6 +1,7 @@
 // C ABI entry points of libqadic (declared in include/qadic.h): argument
 // and bound checks on the host, field lifetime, dispatch to the kernels.
 #include <algorithm>
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -121,6 +122,8 @@ int qadic_field_init(qadic_field **out, uint32_t p, uint32_t k, const uint32_t *
         delete h;
         return st;
     }
+    static std::atomic<uint64_t> next_uid{1};
+    h->f.uid = next_uid.fetch_add(1);
     if (flags & QADIC_FIELD_HOST_ONLY) {
         h->f.device = -1;
         *out = h;
@@ -674,6 +677,17 @@ extern "C" {
 
 size_t qadic_batched_workspace_size(const qadic_gemm_desc *descs, int64_t count) {
     return batched_workspace_size(descs, count);
+}
+
+size_t qadic_batched_workspace_size_fields(const qadic_field *const *fields, int32_t nfields,
+                                           const qadic_gemm_desc *descs, int64_t count) {
+    if (!fields || nfields < 1 || nfields > 64) return 0;
+    const Field *fs[64];
+    for (int32_t i = 0; i < nfields; ++i) {
+        if (!fields[i]) return 0;
+        fs[i] = &fields[i]->f;
+    }
+    return batched_workspace_size_fields(fs, nfields, descs, count);
 }
 
 int qadic_batched_gemm(const qadic_field *const *fields, int32_t nfields,

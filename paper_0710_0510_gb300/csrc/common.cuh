@@ -58,6 +58,16 @@ inline Div32 make_div32(uint32_t d) {
     return r;
 }
 
+__device__ __forceinline__ Div32 make_div32_device(uint32_t d) {
+    const uint32_t l = d > 1 ? 32 - __clz(d - 1) : 0;   // ceil(log2 d)
+    const uint64_t num = ((uint64_t)1 << 32) * ((((uint64_t)1) << l) - d);
+    Div32 r;
+    r.m = (uint32_t)(num / d + 1);
+    r.sh1 = l < 1 ? l : 1;
+    r.sh2 = l >= 1 ? l - 1 : 0;
+    return r;
+}
+
 __device__ __forceinline__ uint32_t div32(uint32_t n, const Div32 &d) {
     const uint32_t t = __umulhi(d.m, n);
     return (t + ((n - t) >> d.sh1)) >> d.sh2;

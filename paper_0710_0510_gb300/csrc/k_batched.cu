@@ -19,122 +19,19 @@
 // list of candidates whose 2k-1 accumulator sets fit in registers: index 0
 // by default, or whichever qadic_batched_autotune measured fastest on the
 // caller's own batch (qadic_batched_select_tiles sets one by hand).
-#include <cuda_bf16.h>
-
 #include <algorithm>
 #include <cstring>
 #include <map>
 #include <mutex>
 #include <vector>
 
-#include "common.cuh"
+#include "batched_tile.cuh"
 
 namespace qadic {
 
 namespace {
 
-constexpr int kThreads = 128;
-constexpr int kMinBK = 32;        // K-block of every configuration 0 (the fallback): a field's
-                                  // exact FP32 chunk must cover at least this much
-constexpr int kMaxFields = 64;
-
-struct BFieldParams {
-    uint32_t p, k, h, m32;
-    float pf, inv_pf;
-    int32_t chunk_k;               // K elements per exact FP32 chunk (capped)
-    int32_t pad;
-    uint8_t fold[kMaxK * kMaxK];   // X^(k+t) mod P, row t (k coefficients)
-};
-
-struct BProd {
-    const uint8_t *A;
-    const uint8_t *B;
-    uint8_t *C;
-    int32_t m, n, K, lda, ldb, ldc;
-    int32_t field, cfg;            // field index, tile configuration index
-};
-
-struct BTile {
-    int32_t prod;
-    int16_t tm, tn;
-};
-
-struct BHeader {
-    uint32_t counter;
-    int32_t ntiles;
-    int32_t nprod;
-    int32_t nfields;
-    uint32_t fields_off, prods_off, tiles_off, pad;
-};
-
-constexpr size_t kHeaderBytes = 256;
-
-template <int KP, int BM_, int BN_, int BK_>
-struct TileCfg {
-    static constexpr int BM = BM_, BN = BN_, BK = BK_;
-    static constexpr int WM = BM / 2, WN = BN / 2;   // 2 x 2 warps
-    static constexpr int MT = WM / 16, NT = WN / 8;
-    static constexpr int NACC = 2 * KP - 1;
-    static constexpr int LDA = BK + 8;               // bf16 elements per A_s row
-    static constexpr int LDB = BN + 8;               // bf16 elements per B_s row
-    static constexpr int SMEM = (KP * BM * LDA + KP * BK * LDB) * 2;
-    static_assert(MT >= 1 && NT >= 1 && BK % 16 == 0, "tile shape");
-};
-
-// Candidate (BM, BN, BK) per k; index 0 is the default.  Every candidate is
-// at least 32 x 16 (the work-list bound); configuration 0 is kMinBK deep.
-struct TileShape {
-    int bm, bn, bk;
-};
-constexpr int kMaxCfg = 5;
-constexpr TileShape kShapesK2[kMaxCfg] = {{64, 32, 32}, {64, 64, 32}, {32, 32, 32}, {64, 32, 64},
-                                          {32, 32, 16}};
-constexpr TileShape kShapesK4[kMaxCfg] = {{32, 32, 32}, {64, 32, 32}, {32, 16, 32}, {32, 32, 64},
-                                          {32, 16, 16}};
-// (k >= 5: the 16-deep K-block halves the staged operand registers, which
-// the 15 accumulator sets of k = 8 otherwise push into spills)
-constexpr TileShape kShapesK8[kMaxCfg] = {{32, 16, 32}, {32, 32, 32}, {32, 16, 64}, {32, 16, 16},
-                                          {32, 16, 16}};
-
-__host__ __device__ constexpr int num_cfgs(uint32_t k) { return k <= 4 ? 5 : 4; }
-
-inline TileShape tile_shape_of(uint32_t k, int cfg) {
-    if (cfg < 0 || cfg >= num_cfgs(k)) cfg = 0;
-    return k <= 2 ? kShapesK2[cfg] : k <= 4 ? kShapesK4[cfg] : kShapesK8[cfg];
-}
-
-inline size_t tile_smem_bytes(uint32_t k, int cfg) {
-    const TileShape t = tile_shape_of(k, cfg);
-    return (size_t)(k * t.bm * (t.bk + 8) + k * t.bk * (t.bn + 8)) * 2;
-}
-
-__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2,
-                                        uint32_t &r3) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(addr));
-}
-
-__device__ __forceinline__ void ldsm_x2_trans(uint32_t addr, uint32_t &r0, uint32_t &r1) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];"
-                 : "=r"(r0), "=r"(r1)
-                 : "r"(addr));
-}
-
-__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4],
-                                               const uint32_t (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-__device__ __forceinline__ __nv_bfloat16 centred_bf16(uint32_t c, const BFieldParams &F) {
-    const uint32_t r = mod_small(c, F.p, F.m32);
-    const int v = (F.p > 2 && r > F.h) ? (int)r - (int)F.p : (int)r;
-    return __int2bfloat16_rn(v);
-}
+using namespace bt;
 
 // 16 consecutive bytes of a row starting at `src` (any alignment); only the
 // first `valid` (<= 16) are read, the others are zero.  In the full case the
@@ -193,8 +90,7 @@ struct Stager {
     }
 
     // bytes -> centred bf16 through the 256-entry table, 32-byte stores
-    __device__ __forceinline__ void store(__nv_bfloat16 *As, __nv_bfloat16 *Bs,
-                                          const uint16_t *tab) const {
+    __device__ __forceinline__ void store(uint16_t *As, uint16_t *Bs, const uint16_t *tab) const {
 #pragma unroll
         for (int s = 0; s < PER_THREAD; ++s) {
             const int c = threadIdx.x + s * kThreads;
@@ -205,7 +101,7 @@ struct Stager {
                 o[2 * q] = (uint32_t)tab[w & 0xff] | ((uint32_t)tab[(w >> 8) & 0xff] << 16);
                 o[2 * q + 1] = (uint32_t)tab[(w >> 16) & 0xff] | ((uint32_t)tab[w >> 24] << 16);
             }
-            __nv_bfloat16 *dst = nullptr;
+            uint16_t *dst = nullptr;
             if (c < A_CH) {
                 const int part = c % (BK / 16), r = (c / (BK / 16)) % T::BM,
                           i = c / ((BK / 16) * T::BM);
@@ -229,22 +125,14 @@ template <int KP, int BM, int BN, int BK>
 __device__ __forceinline__ void run_tile(const BProd &P, const BFieldParams &F, int tm, int tn,
                                       uint8_t *smem, const uint16_t *tab) {
     using T = TileCfg<KP, BM, BN, BK>;
-    __nv_bfloat16 *As = reinterpret_cast<__nv_bfloat16 *>(smem);   // [KP][BM][LDA]
-    __nv_bfloat16 *Bs = As + KP * T::BM * T::LDA;                   // [KP][BK][LDB]
+    uint16_t *As = reinterpret_cast<uint16_t *>(smem);   // [KP][BM][LDA]
+    uint16_t *Bs = As + KP * T::BM * T::LDA;             // [KP][BK][LDB]
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int wm = warp / 2, wn = warp % 2;
     const int row0 = tm * T::BM, col0 = tn * T::BN;
 
-    float acc[T::NACC][T::MT][T::NT][4];
-#pragma unroll
-    for (int t = 0; t < T::NACC; ++t)
-#pragma unroll
-        for (int a = 0; a < T::MT; ++a)
-#pragma unroll
-            for (int b = 0; b < T::NT; ++b)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) acc[t][a][b][e] = 0.f;
-
+    AccArray<T, false> acc;
+    acc_zero<T, false>(acc);
     const int nkb = (P.K + BK - 1) / BK;
     const int chunk_blocks = max(1, F.chunk_k / BK);
     Stager<KP, T> stage;
@@ -255,81 +143,10 @@ __device__ __forceinline__ void run_tile(const BProd &P, const BFieldParams &F, 
         __syncthreads();
         if (kb + 1 < nkb) stage.load(P, row0, col0, (kb + 1) * BK);   // in flight during the MMAs
 #pragma unroll 1
-        for (int ks = 0; ks < BK / 16; ++ks) {
-            uint32_t bfr[KP][T::NT][2];
-#pragma unroll
-            for (int j = 0; j < KP; ++j)
-#pragma unroll
-                for (int nt = 0; nt < T::NT; ++nt) {
-                    const __nv_bfloat16 *src =
-                        Bs + (j * BK + ks * 16 + (lane % 16)) * T::LDB + wn * T::WN + nt * 8;
-                    ldsm_x2_trans((uint32_t)__cvta_generic_to_shared(src), bfr[j][nt][0],
-                                  bfr[j][nt][1]);
-                }
-#pragma unroll
-            for (int i = 0; i < KP; ++i) {
-                uint32_t afr[T::MT][4];
-#pragma unroll
-                for (int mt = 0; mt < T::MT; ++mt) {
-                    const __nv_bfloat16 *src = As + (i * T::BM + wm * T::WM + mt * 16 + (lane % 16)) *
-                                                        T::LDA + ks * 16 + (lane / 16) * 8;
-                    ldsm_x4((uint32_t)__cvta_generic_to_shared(src), afr[mt][0], afr[mt][1],
-                            afr[mt][2], afr[mt][3]);
-                }
-#pragma unroll
-                for (int j = 0; j < KP; ++j)
-#pragma unroll
-                    for (int mt = 0; mt < T::MT; ++mt)
-#pragma unroll
-                        for (int nt = 0; nt < T::NT; ++nt)
-                            mma_bf16_16816(acc[i + j][mt][nt], afr[mt], bfr[j][nt]);
-            }
-        }
-        if ((kb + 1) % chunk_blocks == 0 && kb + 1 < nkb) {
-            // exact-chunk boundary: bring every accumulator back to |x| <= 1.5 p
-#pragma unroll
-            for (int t = 0; t < T::NACC; ++t)
-#pragma unroll
-                for (int a = 0; a < T::MT; ++a)
-#pragma unroll
-                    for (int b = 0; b < T::NT; ++b)
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const float x = acc[t][a][b][e];
-                            acc[t][a][b][e] = fmaf(-F.pf, rintf(x * F.inv_pf), x);
-                        }
-        }
+        for (int ks = 0; ks < BK / 16; ++ks) tile_mma_step<KP, T, false>(acc, As, Bs, ks, wm, wn, lane);
+        if ((kb + 1) % chunk_blocks == 0 && kb + 1 < nkb) tile_chunk_reduce<T, false>(acc, F);
     }
-
-    // epilogue: exact mod p, fold mod P, uint8 planes
-#pragma unroll
-    for (int mt = 0; mt < T::MT; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < T::NT; ++nt)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int row = row0 + wm * T::WM + mt * 16 + (lane / 4) + (e >= 2 ? 8 : 0);
-                const int col = col0 + wn * T::WN + nt * 8 + 2 * (lane % 4) + (e & 1);
-                uint32_t mu[T::NACC];
-#pragma unroll
-                for (int t = 0; t < T::NACC; ++t) {
-                    const float x = acc[t][mt][nt][e];
-                    float r = fmaf(-F.pf, floorf(x * F.inv_pf), x);
-                    if (r < 0.f) r += F.pf;
-                    if (r >= F.pf) r -= F.pf;
-                    mu[t] = (uint32_t)r;
-                }
-                if (row < P.m && col < P.n) {
-#pragma unroll
-                    for (int i = 0; i < KP; ++i) {
-                        uint32_t o = mu[i];
-#pragma unroll
-                        for (int t = KP; t < T::NACC; ++t)
-                            o = mod_small(o + mu[t] * F.fold[(t - KP) * KP + i], F.p, F.m32);
-                        P.C[((int64_t)i * P.m + row) * P.ldc + col] = (uint8_t)o;
-                    }
-                }
-            }
+    tile_epilogue<KP, T, false>(acc, P, F, row0, col0, wm, wn, lane);
 }
 
 // Not inlined: each k is register-allocated on its own (its configurations
@@ -382,7 +199,7 @@ __global__ void __launch_bounds__(kThreads, 5) batched_kernel(uint8_t *ws) {
         const BFieldParams &F = fields[P.field];
         if (P.field != cur_field) {   // block-uniform
             for (int b = threadIdx.x; b < 256; b += kThreads)
-                tab[b] = __bfloat16_as_ushort(centred_bf16((uint32_t)b, F));
+                tab[b] = bf16_bits((uint32_t)b, F);
             if (threadIdx.x == 0) s_field = P.field;
             // run_tile's first __syncthreads orders these writes before any use
         }
@@ -418,6 +235,13 @@ void field_params(const Field &f, BFieldParams &F) {
     F.pf = (float)f.p;
     F.inv_pf = 1.0f / (float)f.p;
     F.chunk_k = (int32_t)std::min<int64_t>(f.k_chunk_f32, 1 << 30);
+    // GF(2^8) in the converted-operand kernel: f16 operands and accumulators.
+    // The planes hold 0 and 1, so a chunk adds at most k per K element to an
+    // accumulator (at most k plane products meet in one C_t), and after a
+    // chunk reduction |x| <= 1: 1 + k chunk <= 2048 keeps every partial sum
+    // an integer that f16 holds exactly, in whatever order it is added.
+    F.f16 = f.p == 2 && f.k == 8;
+    F.chunk_k16 = F.f16 ? (int32_t)(2047 / f.k) : F.chunk_k;
     for (uint32_t t = 0; t + 1 < f.k; ++t)
         for (uint32_t c = 0; c < f.k; ++c) F.fold[t * f.k + c] = f.fold[t * f.k + c];
 }
@@ -459,16 +283,28 @@ int64_t grid_for(int dev, size_t smem, int64_t ntiles) {
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
-    size_t fields_off, prods_off, tiles_off, total;
+    size_t fields_off, prods_off, tiles_off, order_off, conv_off, total;
 };
 
-Layout layout_for(int64_t count, int64_t ntiles) {
+// Work list (header, fields, products, tiles), then, for the converted-
+// operand kernels, conv_bytes of 16-bit operands.
+Layout layout_for(int64_t count, int64_t ntiles, size_t conv_bytes = 0) {
     Layout L;
     L.fields_off = kHeaderBytes;
     L.prods_off = align_up(L.fields_off + kMaxFields * sizeof(BFieldParams), 256);
     L.tiles_off = align_up(L.prods_off + count * sizeof(BProd), 256);
-    L.total = align_up(L.tiles_off + ntiles * sizeof(BTile), 256);
+    L.order_off = align_up(L.tiles_off + ntiles * sizeof(BTile), 256);
+    L.conv_off = align_up(L.order_off + (conv_bytes ? 2 * count * sizeof(uint32_t) : 0), 256);
+    L.total = L.conv_off + conv_bytes;
     return L;
+}
+
+int32_t round8(int32_t x) { return (x + 7) / 8 * 8; }
+
+// Bytes of product d's converted operands: k planes of m x round8(K) and of
+// K x round8(n) 16-bit elements, each operand starting on a 256-byte boundary.
+size_t conv_bytes_of(const qadic_gemm_desc &d, uint32_t k) {
+    return align_up((size_t)k * d.m * round8(d.K) * 2, 256) + align_up((size_t)k * d.K * round8(d.n) * 2, 256);
 }
 
 int64_t max_tiles(const qadic_gemm_desc *descs, int64_t count) {
@@ -478,9 +314,9 @@ int64_t max_tiles(const qadic_gemm_desc *descs, int64_t count) {
     return t;
 }
 
-// Cached CUDA graphs of {counter reset, persistent kernel}, keyed by the
-// call's exact arguments (descriptors, fields, workspace, stream, tile
-// configurations).  A graph replays whatever work list its workspace holds,
+// Cached CUDA graphs of {counter reset, [operand conversion,] persistent
+// kernel}, keyed by the call's exact arguments (descriptors, field ids,
+// workspace, stream, tile configurations, path).  A graph replays whatever work list its workspace holds,
 // so each entry keeps the list it was built with, and a hit re-uploads it
 // when another list was written to the same workspace in between.
 struct GraphEntry {
@@ -515,6 +351,19 @@ size_t batched_workspace_size(const qadic_gemm_desc *descs, int64_t count) {
     return layout_for(count, max_tiles(descs, count)).total;
 }
 
+size_t batched_workspace_size_fields(const Field *const *fields, int32_t nfields,
+                                     const qadic_gemm_desc *descs, int64_t count) {
+    if (!descs || !fields || count <= 0 || nfields < 1) return 0;
+    size_t conv = 0;
+    for (int64_t i = 0; i < count; ++i) {
+        const qadic_gemm_desc &d = descs[i];
+        if (d.field < 0 || d.field >= nfields || !fields[d.field] || d.m < 1 || d.n < 1 || d.K < 1)
+            return 0;
+        conv += conv_bytes_of(d, fields[d.field]->k);
+    }
+    return layout_for(count, max_tiles(descs, count), conv).total;
+}
+
 int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm_desc *descs,
                    int64_t count, void *workspace, size_t ws_bytes, bool use_graph,
                    cudaStream_t stream) {
@@ -543,32 +392,44 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
             return set_error(QADIC_E_OVERFLOW, "exact FP32 chunk below one K-block (p=%u k=%u)",
                              f.p, f.k);
     }
+    const int64_t tile_bound = max_tiles(descs, count);
+    size_t conv = 0;
+    for (int64_t i = 0; i < count; ++i) conv += conv_bytes_of(descs[i], fields[descs[i].field]->k);
+    // converted operands when the workspace holds them, else bytes staged through registers
+    const Layout L_conv = layout_for(count, tile_bound, conv);
+    const Layout L_list = layout_for(count, tile_bound);
+    if (!workspace || ws_bytes < L_list.total)
+        return set_error(QADIC_E_NOMEM, "workspace %zu < %zu bytes", ws_bytes, L_list.total);
+    if (((uintptr_t)workspace) & 255) return set_error(QADIC_E_INVALID, "workspace must be 256-byte aligned");
+    const bool converted = ws_bytes >= L_conv.total;
+    const Layout L = converted ? L_conv : L_list;
     int cfgs[kMaxFields];
     size_t smem = 0;
     for (int32_t i = 0; i < nfields; ++i) {
         cfgs[i] = field_cfg(*fields[i]);
-        smem = std::max(smem, tile_smem_bytes(fields[i]->k, cfgs[i]));
+        smem = std::max(smem, converted ? async_smem_bytes(fields[i]->k, cfgs[i])
+                                        : tile_smem_bytes(fields[i]->k, cfgs[i]));
     }
-    int st = prepare_kernel(smem);
+    int st = converted ? prepare_async_kernel() : prepare_kernel(smem);
     if (st != QADIC_OK) return st;
-    const int64_t tile_bound = max_tiles(descs, count);
-    const Layout L = layout_for(count, tile_bound);
-    if (!workspace || ws_bytes < L.total)
-        return set_error(QADIC_E_NOMEM, "workspace %zu < %zu bytes", ws_bytes, L.total);
-    if (((uintptr_t)workspace) & 255) return set_error(QADIC_E_INVALID, "workspace must be 256-byte aligned");
 
     // graph cache lookup
     std::vector<uint8_t> key;
     if (use_graph) {
-        key.resize(sizeof(int64_t) + count * sizeof(qadic_gemm_desc) + nfields * sizeof(void *) +
-                   2 * sizeof(void *) + nfields * sizeof(int));
+        key.resize(sizeof(int64_t) + count * sizeof(qadic_gemm_desc) + nfields * sizeof(uint64_t) +
+                   2 * sizeof(void *) + nfields * sizeof(int) + 1);
         uint8_t *kp = key.data();
+        *kp++ = converted ? 1 : 0;
         std::memcpy(kp, &count, sizeof(int64_t));
         kp += sizeof(int64_t);
         std::memcpy(kp, descs, count * sizeof(qadic_gemm_desc));
         kp += count * sizeof(qadic_gemm_desc);
-        std::memcpy(kp, fields, nfields * sizeof(void *));
-        kp += nfields * sizeof(void *);
+        // fields by their never-reused ids: a destroyed field's address may
+        // come back for another field, whose graph must not be replayed
+        for (int32_t i = 0; i < nfields; ++i) {
+            std::memcpy(kp, &fields[i]->uid, sizeof(uint64_t));
+            kp += sizeof(uint64_t);
+        }
         std::memcpy(kp, &workspace, sizeof(void *));
         kp += sizeof(void *);
         std::memcpy(kp, &stream, sizeof(void *));
@@ -593,13 +454,14 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
     }
 
     // host-built work list
-    std::vector<uint8_t> host(L.total, 0);
+    std::vector<uint8_t> host(L.conv_off, 0);
     std::vector<BTile> tiles;
     std::vector<uint64_t> cost;
     tiles.reserve(tile_bound);
     BFieldParams *fp = reinterpret_cast<BFieldParams *>(host.data() + L.fields_off);
     for (int32_t i = 0; i < nfields; ++i) field_params(*fields[i], fp[i]);
     BProd *pp = reinterpret_cast<BProd *>(host.data() + L.prods_off);
+    size_t conv_at = L.conv_off;
     for (int64_t i = 0; i < count; ++i) {
         const qadic_gemm_desc &d = descs[i];
         BProd &P = pp[i];
@@ -615,6 +477,14 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
         P.field = d.field;
         P.cfg = cfgs[d.field];
         const uint32_t k = fields[d.field]->k;
+        if (converted) {
+            P.kp = round8(d.K);
+            P.np = round8(d.n);
+            P.A16 = reinterpret_cast<const uint16_t *>((uint8_t *)workspace + conv_at);
+            conv_at += align_up((size_t)k * d.m * P.kp * 2, 256);
+            P.B16 = reinterpret_cast<const uint16_t *>((uint8_t *)workspace + conv_at);
+            conv_at += align_up((size_t)k * d.K * P.np * 2, 256);
+        }
         const TileShape ts = tile_shape_of(k, P.cfg);
         const uint64_t c = tile_cost(d, k, P.cfg);
         for (int tm = 0; tm * ts.bm < d.m; ++tm)
@@ -637,7 +507,25 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
     hdr->fields_off = (uint32_t)L.fields_off;
     hdr->prods_off = (uint32_t)L.prods_off;
     hdr->tiles_off = (uint32_t)L.tiles_off;
-    const size_t used = L.tiles_off + tiles.size() * sizeof(BTile);
+    hdr->order_off = (uint32_t)L.order_off;
+    size_t used = L.tiles_off + tiles.size() * sizeof(BTile);
+    if (converted) {
+        // conversion blocks by decreasing operand size (elements incl. padding)
+        std::vector<uint32_t> items(2 * count);
+        std::vector<uint64_t> size(2 * count);
+        for (int64_t i = 0; i < count; ++i) {
+            const BProd &P = pp[i];
+            const uint64_t k = fields[descs[i].field]->k;
+            size[2 * i] = k * (uint64_t)P.m * P.kp;
+            size[2 * i + 1] = k * (uint64_t)P.K * P.np;
+            items[2 * i] = (uint32_t)(2 * i);
+            items[2 * i + 1] = (uint32_t)(2 * i + 1);
+        }
+        std::stable_sort(items.begin(), items.end(),
+                         [&](uint32_t a, uint32_t b) { return size[a] > size[b]; });
+        std::memcpy(host.data() + L.order_off, items.data(), items.size() * sizeof(uint32_t));
+        used = L.order_off + items.size() * sizeof(uint32_t);
+    }
     if (cudaMemcpyAsync(workspace, host.data(), used, cudaMemcpyHostToDevice, stream) != cudaSuccess)
         return set_error(QADIC_E_CUDA, "work list upload: %s", cudaGetErrorString(cudaGetLastError()));
     {
@@ -645,14 +533,22 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
         g_ws_list[workspace] = 0;   // an uncached list: no cached graph owns this workspace
     }
 
-    const int64_t grid = grid_for(dev, smem, (int64_t)tiles.size());
-
-    if (!use_graph) {
-        batched_kernel<<<(unsigned)grid, kThreads, smem, stream>>>((uint8_t *)workspace);
+    const int64_t grid = converted ? async_grid(smem, (int64_t)tiles.size())
+                                   : grid_for(dev, smem, (int64_t)tiles.size());
+    // {convert, products} or {products}; the tile counter starts at zero
+    auto enqueue = [&](cudaStream_t s) -> int {
+        if (converted) {
+            const int cs = launch_convert((const uint8_t *)workspace, count, s);
+            if (cs != QADIC_OK) return cs;
+            return launch_async((uint8_t *)workspace, grid, smem, s);
+        }
+        batched_kernel<<<(unsigned)grid, kThreads, smem, s>>>((uint8_t *)workspace);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return set_error(QADIC_E_CUDA, "batched launch: %s", cudaGetErrorString(e));
         return QADIC_OK;
-    }
+    };
+
+    if (!use_graph) return enqueue(stream);
     // Capture {counter reset, kernel} on a private stream (the caller's may
     // be the legacy default stream, which cannot be captured; capturing runs
     // nothing), then launch the graph on the caller's stream.  The work list
@@ -664,11 +560,12 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
     if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return set_error(QADIC_E_CUDA, "begin capture: %s", cudaGetErrorString(cudaGetLastError()));
     cudaMemsetAsync(workspace, 0, sizeof(uint32_t), cap);
-    batched_kernel<<<(unsigned)grid, kThreads, smem, cap>>>((uint8_t *)workspace);
+    const int qs = enqueue(cap);
     const cudaError_t le = cudaGetLastError();
     const cudaError_t ce = cudaStreamEndCapture(cap, &graph);
-    if (le != cudaSuccess || ce != cudaSuccess) {
+    if (qs != QADIC_OK || le != cudaSuccess || ce != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
+        if (qs != QADIC_OK) return qs;
         return set_error(QADIC_E_CUDA, "capture: %s", cudaGetErrorString(le != cudaSuccess ? le : ce));
     }
     const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);

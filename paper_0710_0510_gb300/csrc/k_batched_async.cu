@@ -1,0 +1,280 @@
+// Batched GF(p^k) products from operands converted once: the path that
+// qadic_batched_gemm takes when its workspace has room for the converted
+// operands (qadic_batched_workspace_size_fields).
+//
+// Launch 1 (convert_kernel, one block per product operand, largest first): the uint8
+// coefficient planes become centred 16-bit operands (bf16; f16 for GF(2^8),
+// see below) in the workspace, rows padded with zeros to a multiple of 8
+// elements so that every 16-byte piece of a row is aligned.  Each element is
+// converted once, where staging bytes through registers converts an A tile
+// again for every column tile of its product and a B tile for every row tile.
+//
+// Launch 2 (async_kernel, persistent, tiles pulled with one atomicAdd each):
+// operand tiles go from the converted planes to shared memory with
+// cp.async (16 bytes each, zero-filled past the edges), double-buffered so
+// that the copies of K-block kb+1 run under the MMAs of K-block kb; the
+// products, exact-chunk reductions and the epilogue are those of the
+// register-staged kernel (batched_tile.cuh).
+//
+// GF(2^8) (p = 2, k = 8) runs on f16 operands and f16 accumulators: its planes
+// hold 0 and 1, a K element adds at most k = 8 to an accumulator, and a chunk
+// of at most 2047 / k elements (after which every accumulator is reduced to
+// |x| <= 1) keeps each partial sum an integer of magnitude <= 2048, exact in
+// f16 in any order of addition.  Half the accumulator registers of FP32.
+#include "batched_tile.cuh"
+
+namespace qadic {
+namespace bt {
+
+namespace {
+
+constexpr int kConvThreads = 256;   // one thread per table entry when the table is built
+
+// 8 consecutive bytes of a row at `src` (any alignment); only the first
+// `valid` are read (none when valid <= 0), the others are zero.  In the full
+// case the bytes come from aligned 32-bit loads joined by funnel shifts; every
+// word loaded holds at least one of the 8 bytes, so no load leaves the buffer.
+__device__ __forceinline__ void load8(const uint8_t *src, int valid, uint32_t (&w)[2]) {
+    if (valid >= 8) {
+        const uint32_t a = (uint32_t)((uintptr_t)src & 3);
+        const uint32_t *base = reinterpret_cast<const uint32_t *>(src - a);
+        if (a == 0) {
+            w[0] = __ldg(base);
+            w[1] = __ldg(base + 1);
+        } else {
+            const uint32_t x0 = __ldg(base), x1 = __ldg(base + 1), x2 = __ldg(base + 2);
+            w[0] = __funnelshift_r(x0, x1, 8 * a);
+            w[1] = __funnelshift_r(x1, x2, 8 * a);
+        }
+    } else {
+        w[0] = w[1] = 0;
+        for (int b = 0; b < valid; ++b) w[b >> 2] |= (uint32_t)__ldg(src + b) << (8 * (b & 3));
+    }
+}
+
+__global__ void __launch_bounds__(kConvThreads) convert_kernel(const uint8_t *ws) {
+    const BHeader *hdr = reinterpret_cast<const BHeader *>(ws);
+    if ((int64_t)blockIdx.x >= 2 * (int64_t)hdr->nprod) return;
+    // largest operands first, so that the small ones fill the end of the launch
+    const uint32_t item = reinterpret_cast<const uint32_t *>(ws + hdr->order_off)[blockIdx.x];
+    const int64_t prod = item >> 1;
+    const bool isB = item & 1;
+    const BFieldParams *fields = reinterpret_cast<const BFieldParams *>(ws + hdr->fields_off);
+    const BProd &P = reinterpret_cast<const BProd *>(ws + hdr->prods_off)[prod];
+    const BFieldParams &F = fields[P.field];
+    __shared__ uint16_t tab[256];   // byte -> centred operand bits (kConvThreads == 256)
+    tab[threadIdx.x] = F.f16 ? f16_bits(threadIdx.x, F) : bf16_bits(threadIdx.x, F);
+    __syncthreads();
+    const int cols = isB ? P.n : P.K;
+    const int64_t rows = (int64_t)F.k * (isB ? P.K : P.m);   // all k planes, one after the other
+    const int ld_in = isB ? P.ldb : P.lda, ld_out = isB ? P.np : P.kp;
+    const uint8_t *src = isB ? P.B : P.A;
+    uint16_t *dst = const_cast<uint16_t *>(isB ? P.B16 : P.A16);
+    const uint32_t per_row = (uint32_t)ld_out / 8;
+    const uint32_t total = (uint32_t)rows * per_row;   // <= 8 * 4096 * 512
+    const Div32 div_row = make_div32_device(per_row);
+    // kUnrollConv chunks per thread per round: all their loads are issued
+    // before any of them is converted and stored
+    constexpr int kUnrollConv = 4;
+    for (uint32_t c0 = threadIdx.x; c0 < total; c0 += kConvThreads * kUnrollConv) {
+        uint32_t w[kUnrollConv][2];
+#pragma unroll
+        for (int u = 0; u < kUnrollConv; ++u) {
+            const uint32_t c = c0 + u * kConvThreads;
+            const uint32_t r = div32(c, div_row);
+            const int col = (int)(c - r * per_row) * 8;
+            // past the row (or past the last chunk): zeros, and tab[0] = 0
+            load8(src + (int64_t)r * ld_in + col, c < total ? cols - col : 0, w[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < kUnrollConv; ++u) {
+            const uint32_t c = c0 + u * kConvThreads;
+            if (c >= total) break;
+            const uint32_t r = div32(c, div_row);
+            const int col = (int)(c - r * per_row) * 8;
+            uint4 o;
+            o.x = (uint32_t)tab[w[u][0] & 0xff] | ((uint32_t)tab[(w[u][0] >> 8) & 0xff] << 16);
+            o.y = (uint32_t)tab[(w[u][0] >> 16) & 0xff] | ((uint32_t)tab[w[u][0] >> 24] << 16);
+            o.z = (uint32_t)tab[w[u][1] & 0xff] | ((uint32_t)tab[(w[u][1] >> 8) & 0xff] << 16);
+            o.w = (uint32_t)tab[(w[u][1] >> 16) & 0xff] | ((uint32_t)tab[w[u][1] >> 24] << 16);
+            *reinterpret_cast<uint4 *>(dst + (int64_t)r * ld_out + col) = o;
+        }
+    }
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+__device__ __forceinline__ void cp_async_wait_one() {
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
+
+// Copies of one K-block of operand tiles into a stage: A_s [KP][BM][LDA],
+// B_s [KP][BK][LDB], 16-byte pieces; a piece outside the product (rows past
+// m, K-rows past K, columns past the padded row) is zero-filled (source size
+// 0, the source pointer then only names the buffer's first element).
+template <int KP, typename T>
+__device__ __forceinline__ void issue_stage(const BProd &P, uint16_t *As, uint16_t *Bs, int row0,
+                                            int col0, int k0) {
+    constexpr int A_PER_ROW = T::BK / 8, B_PER_ROW = T::BN / 8;
+    constexpr int A_CH = KP * T::BM * A_PER_ROW;
+    constexpr int B_CH = KP * T::BK * B_PER_ROW;
+#pragma unroll
+    for (int s = 0; s < (A_CH + B_CH + kThreads - 1) / kThreads; ++s) {
+        const int c = threadIdx.x + s * kThreads;
+        if (c < A_CH) {
+            const int part = c % A_PER_ROW, r = (c / A_PER_ROW) % T::BM, i = c / (A_PER_ROW * T::BM);
+            const int gr = row0 + r, gk = k0 + part * 8;
+            const bool ok = gr < P.m && gk < P.kp;
+            const uint16_t *src = ok ? P.A16 + ((int64_t)i * P.m + gr) * P.kp + gk : P.A16;
+            cp_async16((uint32_t)__cvta_generic_to_shared(As + (i * T::BM + r) * T::LDA + part * 8),
+                       src, ok ? 16u : 0u);
+        } else if (c < A_CH + B_CH) {
+            const int cb = c - A_CH;
+            const int part = cb % B_PER_ROW, r = (cb / B_PER_ROW) % T::BK, j = cb / (B_PER_ROW * T::BK);
+            const int gk = k0 + r, gc = col0 + part * 8;
+            const bool ok = gk < P.K && gc < P.np;
+            const uint16_t *src = ok ? P.B16 + ((int64_t)j * P.K + gk) * P.np + gc : P.B16;
+            cp_async16((uint32_t)__cvta_generic_to_shared(Bs + (j * T::BK + r) * T::LDB + part * 8),
+                       src, ok ? 16u : 0u);
+        }
+    }
+}
+
+template <int KP, int BM, int BN, int BK, bool F16>
+__device__ __forceinline__ void run_tile_async(const BProd &P, const BFieldParams &F, int tm, int tn,
+                                               uint8_t *smem) {
+    using T = TileCfg<KP, BM, BN, BK>;
+    constexpr int kStage = T::SMEM / 2;               // 16-bit elements per stage
+    constexpr int kAElems = KP * T::BM * T::LDA;
+    uint16_t *S = reinterpret_cast<uint16_t *>(smem);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int wm = warp / 2, wn = warp % 2;
+    const int row0 = tm * T::BM, col0 = tn * T::BN;
+
+    AccArray<T, F16> acc;
+    acc_zero<T, F16>(acc);
+    const int nkb = (P.K + BK - 1) / BK;
+    const int chunk_blocks = max(1, (F16 ? F.chunk_k16 : F.chunk_k) / BK);
+    __syncthreads();   // the previous tile's reads of both stages are done
+    issue_stage<KP, T>(P, S, S + kAElems, row0, col0, 0);
+    cp_async_commit();
+    for (int kb = 0; kb < nkb; ++kb) {
+        uint16_t *As = S + (kb & 1) * kStage;
+        if (kb + 1 < nkb) {
+            uint16_t *An = S + ((kb + 1) & 1) * kStage;
+            issue_stage<KP, T>(P, An, An + kAElems, row0, col0, (kb + 1) * BK);
+        }
+        cp_async_commit();       // (empty on the last K-block: keeps the group count uniform)
+        cp_async_wait_one();     // everything but the newest group: stage kb has landed
+        __syncthreads();
+#pragma unroll 1
+        for (int ks = 0; ks < BK / 16; ++ks)
+            tile_mma_step<KP, T, F16>(acc, As, As + kAElems, ks, wm, wn, lane);
+        if ((kb + 1) % chunk_blocks == 0 && kb + 1 < nkb) tile_chunk_reduce<T, F16>(acc, F);
+        __syncthreads();         // stage kb read by every warp before it is refilled
+    }
+    tile_epilogue<KP, T, F16>(acc, P, F, row0, col0, wm, wn, lane);
+}
+
+// Not inlined: each (k, F16) is register-allocated on its own.
+template <int KP, bool F16>
+__device__ __noinline__ void run_tile_async_cfg(int cfg, const BProd &P, const BFieldParams &F,
+                                                int tm, int tn, uint8_t *smem) {
+    constexpr bool kSmall = KP <= 2, kMid = KP > 2 && KP <= 4;
+    constexpr TileShape c0 = kSmall ? kShapesK2[0] : kMid ? kShapesK4[0] : kShapesK8[0];
+    constexpr TileShape c1 = kSmall ? kShapesK2[1] : kMid ? kShapesK4[1] : kShapesK8[1];
+    constexpr TileShape c2 = kSmall ? kShapesK2[2] : kMid ? kShapesK4[2] : kShapesK8[2];
+    constexpr TileShape c3 = kSmall ? kShapesK2[3] : kMid ? kShapesK4[3] : kShapesK8[3];
+    constexpr TileShape c4 = kSmall ? kShapesK2[4] : kMid ? kShapesK4[4] : kShapesK8[4];
+    switch (cfg) {
+        case 1: run_tile_async<KP, c1.bm, c1.bn, c1.bk, F16>(P, F, tm, tn, smem); break;
+        case 2: run_tile_async<KP, c2.bm, c2.bn, c2.bk, F16>(P, F, tm, tn, smem); break;
+        case 3: run_tile_async<KP, c3.bm, c3.bn, c3.bk, F16>(P, F, tm, tn, smem); break;
+        case 4:
+            if constexpr (num_cfgs(KP) > 4) {
+                run_tile_async<KP, c4.bm, c4.bn, c4.bk, F16>(P, F, tm, tn, smem);
+                break;
+            }
+            [[fallthrough]];
+        default: run_tile_async<KP, c0.bm, c0.bn, c0.bk, F16>(P, F, tm, tn, smem); break;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 5) async_kernel(uint8_t *ws) {
+    extern __shared__ __align__(128) uint8_t smem[];   // two stages of the largest tile in the list
+    __shared__ int s_tile;
+    BHeader *hdr = reinterpret_cast<BHeader *>(ws);
+    const BFieldParams *fields = reinterpret_cast<const BFieldParams *>(ws + hdr->fields_off);
+    const BProd *prods = reinterpret_cast<const BProd *>(ws + hdr->prods_off);
+    const BTile *tiles = reinterpret_cast<const BTile *>(ws + hdr->tiles_off);
+    const int ntiles = hdr->ntiles;
+    while (true) {
+        if (threadIdx.x == 0) s_tile = (int)atomicAdd(&hdr->counter, 1u);
+        __syncthreads();
+        const int t = s_tile;
+        __syncthreads();
+        if (t >= ntiles) break;
+        const BTile tile = tiles[t];
+        const BProd &P = prods[tile.prod];
+        const BFieldParams &F = fields[P.field];
+        switch (F.k) {
+            case 1: run_tile_async_cfg<1, false>(P.cfg, P, F, tile.tm, tile.tn, smem); break;
+            case 2: run_tile_async_cfg<2, false>(P.cfg, P, F, tile.tm, tile.tn, smem); break;
+            case 3: run_tile_async_cfg<3, false>(P.cfg, P, F, tile.tm, tile.tn, smem); break;
+            case 4: run_tile_async_cfg<4, false>(P.cfg, P, F, tile.tm, tile.tn, smem); break;
+            case 5: run_tile_async_cfg<5, false>(P.cfg, P, F, tile.tm, tile.tn, smem); break;
+            case 6: run_tile_async_cfg<6, false>(P.cfg, P, F, tile.tm, tile.tn, smem); break;
+            case 7: run_tile_async_cfg<7, false>(P.cfg, P, F, tile.tm, tile.tn, smem); break;
+            default:
+                if (F.f16) run_tile_async_cfg<8, true>(P.cfg, P, F, tile.tm, tile.tn, smem);
+                else run_tile_async_cfg<8, false>(P.cfg, P, F, tile.tm, tile.tn, smem);
+                break;
+        }
+    }
+}
+
+}  // namespace
+
+size_t async_smem_bytes(uint32_t k, int cfg) { return 2 * tile_smem_bytes(k, cfg); }
+
+int prepare_async_kernel() {
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] {
+        size_t most = 0;
+        for (uint32_t k = 1; k <= kMaxK; ++k)
+            for (int c = 0; c < num_cfgs(k); ++c) most = std::max(most, async_smem_bytes(k, c));
+        err = cudaFuncSetAttribute(async_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+    });
+    if (err != cudaSuccess)
+        return set_error(QADIC_E_CUDA, "batched smem attribute: %s", cudaGetErrorString(err));
+    return QADIC_OK;
+}
+
+int64_t async_grid(size_t smem, int64_t ntiles) {
+    int64_t grid = resident_blocks(async_kernel, kThreads, smem);
+    if (ntiles < grid) grid = std::max<int64_t>(1, ntiles);
+    return grid;
+}
+
+int launch_convert(const uint8_t *ws, int64_t nprod, cudaStream_t stream) {
+    convert_kernel<<<(unsigned)(2 * nprod), kConvThreads, 0, stream>>>(ws);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(QADIC_E_CUDA, "batched convert launch: %s", cudaGetErrorString(e));
+    return QADIC_OK;
+}
+
+int launch_async(uint8_t *ws, int64_t grid, size_t smem, cudaStream_t stream) {
+    async_kernel<<<(unsigned)grid, kThreads, smem, stream>>>(ws);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(QADIC_E_CUDA, "batched launch: %s", cudaGetErrorString(e));
+    return QADIC_OK;
+}
+
+}  // namespace bt
+}  // namespace qadic

@@ -25,6 +25,7 @@ struct Field {
     int64_t k_max_int32 = 0;                // Eq. 3, 32-bit signed accumulator
     int64_t k_chunk_f32 = 0;                // exact FP32 accumulation chunk
     int device = 0;
+    uint64_t uid = 0;                       // process-unique, never reused (keys of cached graphs)
 
     // Host tables.
     std::vector<uint8_t> antilog;           // order x k coefficients; row order-1 = zero
@@ -115,6 +116,8 @@ int launch_gemm_fold_tc(const Field &f, int64_t m, int64_t n, int64_t K, const v
                         cudaStream_t stream);
 
 size_t batched_workspace_size(const qadic_gemm_desc *descs, int64_t count);
+size_t batched_workspace_size_fields(const Field *const *fields, int32_t nfields,
+                                     const qadic_gemm_desc *descs, int64_t count);
 
 int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm_desc *descs,
                    int64_t count, void *workspace, size_t ws_bytes, bool use_graph,

@@ -19,7 +19,7 @@ def torch():
 class Batch:
     """Products laid out in three flat device buffers (A, B, C)."""
 
-    def __init__(self, torch, fields, shapes, fidx, seed):
+    def __init__(self, torch, fields, shapes, fidx, seed, converted=True):
         rng = np.random.default_rng(seed)
         self.fields, self.shapes, self.fidx = fields, shapes, fidx
         self.A, self.B, offs = [], [], []
@@ -42,7 +42,9 @@ class Batch:
             self.descs.append(q.GemmDesc(fi, m, n, K, self.dA.data_ptr() + a,
                                          self.dB.data_ptr() + b, self.dC.data_ptr() + c,
                                          K, n, n, 0))
-        ws = q.batched_workspace_size(self.descs)
+        # with the fields: room for converted operands (the cp.async path);
+        # without: the work list only (operand bytes staged through registers)
+        ws = q.batched_workspace_size(self.descs, fields if converted else None)
         self.ws = torch.empty(ws, dtype=torch.uint8, device="cuda")
 
     def run(self, graph=False):
@@ -65,16 +67,40 @@ def mixed_fields():
     return [q.Field(2, 8), q.Field(7, 4), q.Field(31, 2)]
 
 
-def test_batched_mixed_fields(torch, orc):
+@pytest.mark.parametrize("converted", [True, False])
+def test_batched_mixed_fields(torch, orc, converted):
     fields = mixed_fields()
     dims, fidx = W.batched_shapes(60, salt=1)
     shapes = [tuple(int(x) for x in d) for d in dims]
     shapes[:5] = [(1, 1, 1), (16, 16, 16), (256, 256, 256), (65, 17, 33), (3, 200, 7)]
-    bt = Batch(torch, fields, shapes, [int(x) for x in fidx], seed=5)
+    bt = Batch(torch, fields, shapes, [int(x) for x in fidx], seed=5, converted=converted)
     bt.run()
     q.sync_status()
     for i in range(len(shapes)):
         assert np.array_equal(bt.result(i), bt.expected(orc, i)), (i, shapes[i], fidx[i])
+
+
+def test_batched_paths_agree_and_sizes(torch, orc):
+    """The converted-operand path and the register-staged path give the same
+    bytes; the size query with fields covers the converted operands (2 bytes
+    per element, rows padded to 8) on top of the work list."""
+    fields = mixed_fields()
+    dims, fidx = W.batched_shapes(30, salt=7)
+    shapes = [tuple(int(x) for x in d) for d in dims]
+    fi = [int(x) for x in fidx]
+    a = Batch(torch, fields, shapes, fi, seed=6, converted=True)
+    b = Batch(torch, fields, shapes, fi, seed=6, converted=False)
+    a.run(graph=True)
+    b.run(graph=True)
+    for i in range(len(shapes)):
+        assert np.array_equal(a.result(i), b.result(i)), i
+    small = q.batched_workspace_size(a.descs)
+    big = q.batched_workspace_size(a.descs, fields)
+    r8 = lambda x: (x + 7) // 8 * 8
+    conv = sum(fields[f].k * (m * r8(K) + K * r8(n)) * 2 for (m, n, K), f in zip(shapes, fi))
+    assert big >= small + conv
+    # + 256-byte alignment of each operand, + the conversion order (4 bytes per operand)
+    assert big <= small + conv + 2 * 256 * len(shapes) + 8 * len(shapes) + 512
 
 
 @pytest.mark.parametrize("pk", [(3, 3), (5, 5), (2, 6), (101, 2), (3, 7), (13, 3), (2, 1)])
@@ -165,27 +191,30 @@ def restore_tiles():
         q.batched_select_tiles(k, -1)
 
 
-@pytest.mark.parametrize("pk", [(101, 1), (31, 2), (3, 3), (7, 4), (5, 5), (2, 6), (2, 8)])
-def test_batched_every_tile_configuration(torch, orc, restore_tiles, pk):
+@pytest.mark.parametrize("converted", [True, False])
+@pytest.mark.parametrize("pk", [(101, 1), (31, 2), (3, 3), (7, 4), (5, 5), (2, 6), (2, 8), (3, 8)])
+def test_batched_every_tile_configuration(torch, orc, restore_tiles, pk, converted):
     """Each (BM, BN, BK) candidate of the autotuner computes the same exact
-    products: ragged shapes, K across exact-chunk boundaries."""
+    products on both paths: ragged shapes, K across exact-chunk boundaries."""
     f = q.Field(*pk)
     shapes = [(1, 1, 1), (33, 47, 95), (64, 64, 64), (100, 3, 250), (1, 70, 129), (77, 65, 640)]
     for c in range(len(q.batched_tile_configs(f.k))):
         q.batched_select_tiles(f.k, c)
-        bt = Batch(torch, [f], shapes, [0] * len(shapes), seed=pk[0] + c)
+        bt = Batch(torch, [f], shapes, [0] * len(shapes), seed=pk[0] + c, converted=converted)
         bt.run(graph=bool(c % 2))
         for i in range(len(shapes)):
             assert np.array_equal(bt.result(i), bt.expected(orc, i)), (pk, c, shapes[i])
 
 
-def test_batched_p251_chunks_every_configuration(torch, orc, restore_tiles):
+@pytest.mark.parametrize("converted", [True, False])
+def test_batched_p251_chunks_every_configuration(torch, orc, restore_tiles, converted):
     """GF(251^2) (exact chunk 536 = 16 blocks of 32 or 8 of 64), all-max
     inputs, K = 2000, under every configuration for k = 2."""
     f = q.Field(251, 2)
     for c in range(len(q.batched_tile_configs(2))):
         q.batched_select_tiles(2, c)
-        bt = Batch(torch, [f], [(64, 64, 2000), (50, 70, 1100)], [0, 0], seed=2)
+        bt = Batch(torch, [f], [(64, 64, 2000), (50, 70, 1100)], [0, 0], seed=2,
+                   converted=converted)
         bt.A[0][:] = 126
         bt.B[0][:] = 126
         bt.dA[: bt.A[0].size] = torch.from_numpy(bt.A[0].ravel()).cuda()
@@ -193,6 +222,47 @@ def test_batched_p251_chunks_every_configuration(torch, orc, restore_tiles):
         bt.run()
         for i in range(2):
             assert np.array_equal(bt.result(i), bt.expected(orc, i)), c
+
+
+@pytest.mark.parametrize("converted", [True, False])
+def test_batched_gf256_chunks_every_configuration(torch, orc, restore_tiles, converted):
+    """GF(2^8), whose converted path runs on f16 operands and accumulators:
+    all-one planes (every plane product is 1, the largest sums), K across the
+    f16 chunk of 2047/8 = 255 elements, every configuration for k = 8."""
+    f = q.Field(2, 8)
+    shapes = [(64, 64, 2000), (50, 70, 1100), (33, 16, 255), (32, 16, 256), (17, 9, 257)]
+    for c in range(len(q.batched_tile_configs(8))):
+        q.batched_select_tiles(8, c)
+        bt = Batch(torch, [f], shapes, [0] * len(shapes), seed=3, converted=converted)
+        for i in range(len(shapes)):
+            bt.A[i][:] = 1
+            bt.B[i][:] = 1
+        bt.dA[:] = torch.from_numpy(np.concatenate([x.ravel() for x in bt.A])).cuda()
+        bt.dB[:] = torch.from_numpy(np.concatenate([x.ravel() for x in bt.B])).cuda()
+        bt.run(graph=bool(c % 2))
+        for i in range(len(shapes)):
+            assert np.array_equal(bt.result(i), bt.expected(orc, i)), (c, shapes[i])
+
+
+@pytest.mark.parametrize("converted", [True, False])
+def test_graph_cache_after_field_destroyed(torch, orc, converted):
+    """A graph cached for a destroyed field is not replayed for a new field
+    (its handle may reuse the old address) with the same descriptors and
+    workspace."""
+    shapes = [(40, 24, 70), (1, 1, 1)]
+    f1 = q.Field(2, 8)
+    bt = Batch(torch, [f1], shapes, [0, 0], seed=12, converted=converted)
+    bt.run(graph=True)
+    for i in range(len(shapes)):
+        assert np.array_equal(bt.result(i), bt.expected(orc, i))
+    f1.close()
+    f2 = q.Field(3, 8)
+    bt.fields = [f2]
+    descs = bt.descs
+    q.batched_gemm([f2], descs, bt.ws, graph=True)
+    torch.cuda.synchronize()
+    for i in range(len(shapes)):
+        assert np.array_equal(bt.result(i), bt.expected(orc, i)), i
 
 
 def test_graph_replay_after_another_list_in_the_same_workspace(torch, orc):
