@@ -52,8 +52,16 @@ struct BHeader {
     int32_t nprod;
     int32_t nfields;
     uint32_t fields_off, prods_off, tiles_off;
-    uint32_t order_off;            // conversion order: 2 x nprod items (product 2i + operand), largest first
+    uint32_t order_off;            // conversion items (ConvItem), largest first
+    uint32_t nconv;                // number of conversion items
 };
+
+// One block of the conversion launch: 8-element chunks [begin, begin +
+// kConvItemChunks) of operand `op` (product op / 2, A if op is even, else B).
+struct ConvItem {
+    uint32_t op, begin;
+};
+constexpr uint32_t kConvItemChunks = 4096;
 
 constexpr size_t kHeaderBytes = 256;
 
@@ -272,7 +280,7 @@ __device__ __forceinline__ void tile_epilogue(const AccArray<T, F16> &acc, const
 int prepare_async_kernel();
 int64_t async_grid(size_t smem, int64_t ntiles);
 size_t async_smem_bytes(uint32_t k, int cfg);
-int launch_convert(const uint8_t *ws, int64_t nprod, cudaStream_t stream);
+int launch_convert(const uint8_t *ws, int64_t nitems, cudaStream_t stream);
 int launch_async(uint8_t *ws, int64_t grid, size_t smem, cudaStream_t stream);
 
 }  // namespace bt

@@ -288,13 +288,13 @@ struct Layout {
 
 // Work list (header, fields, products, tiles), then, for the converted-
 // operand kernels, conv_bytes of 16-bit operands.
-Layout layout_for(int64_t count, int64_t ntiles, size_t conv_bytes = 0) {
+Layout layout_for(int64_t count, int64_t ntiles, size_t conv_bytes = 0, int64_t conv_items = 0) {
     Layout L;
     L.fields_off = kHeaderBytes;
     L.prods_off = align_up(L.fields_off + kMaxFields * sizeof(BFieldParams), 256);
     L.tiles_off = align_up(L.prods_off + count * sizeof(BProd), 256);
     L.order_off = align_up(L.tiles_off + ntiles * sizeof(BTile), 256);
-    L.conv_off = align_up(L.order_off + (conv_bytes ? 2 * count * sizeof(uint32_t) : 0), 256);
+    L.conv_off = align_up(L.order_off + conv_items * sizeof(ConvItem), 256);
     L.total = L.conv_off + conv_bytes;
     return L;
 }
@@ -305,6 +305,14 @@ int32_t round8(int32_t x) { return (x + 7) / 8 * 8; }
 // K x round8(n) 16-bit elements, each operand starting on a 256-byte boundary.
 size_t conv_bytes_of(const qadic_gemm_desc &d, uint32_t k) {
     return align_up((size_t)k * d.m * round8(d.K) * 2, 256) + align_up((size_t)k * d.K * round8(d.n) * 2, 256);
+}
+
+// 8-element chunks of product d's operands (A, B) and the conversion items they make.
+uint64_t chunks_a(const qadic_gemm_desc &d, uint32_t k) { return (uint64_t)k * d.m * (round8(d.K) / 8); }
+uint64_t chunks_b(const qadic_gemm_desc &d, uint32_t k) { return (uint64_t)k * d.K * (round8(d.n) / 8); }
+int64_t conv_items_of(const qadic_gemm_desc &d, uint32_t k) {
+    return (int64_t)((chunks_a(d, k) + kConvItemChunks - 1) / kConvItemChunks +
+                     (chunks_b(d, k) + kConvItemChunks - 1) / kConvItemChunks);
 }
 
 int64_t max_tiles(const qadic_gemm_desc *descs, int64_t count) {
@@ -355,13 +363,15 @@ size_t batched_workspace_size_fields(const Field *const *fields, int32_t nfields
                                      const qadic_gemm_desc *descs, int64_t count) {
     if (!descs || !fields || count <= 0 || nfields < 1) return 0;
     size_t conv = 0;
+    int64_t items = 0;
     for (int64_t i = 0; i < count; ++i) {
         const qadic_gemm_desc &d = descs[i];
         if (d.field < 0 || d.field >= nfields || !fields[d.field] || d.m < 1 || d.n < 1 || d.K < 1)
             return 0;
         conv += conv_bytes_of(d, fields[d.field]->k);
+        items += conv_items_of(d, fields[d.field]->k);
     }
-    return layout_for(count, max_tiles(descs, count), conv).total;
+    return layout_for(count, max_tiles(descs, count), conv, items).total;
 }
 
 int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm_desc *descs,
@@ -394,9 +404,13 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
     }
     const int64_t tile_bound = max_tiles(descs, count);
     size_t conv = 0;
-    for (int64_t i = 0; i < count; ++i) conv += conv_bytes_of(descs[i], fields[descs[i].field]->k);
+    int64_t conv_items = 0;
+    for (int64_t i = 0; i < count; ++i) {
+        conv += conv_bytes_of(descs[i], fields[descs[i].field]->k);
+        conv_items += conv_items_of(descs[i], fields[descs[i].field]->k);
+    }
     // converted operands when the workspace holds them, else bytes staged through registers
-    const Layout L_conv = layout_for(count, tile_bound, conv);
+    const Layout L_conv = layout_for(count, tile_bound, conv, conv_items);
     const Layout L_list = layout_for(count, tile_bound);
     if (!workspace || ws_bytes < L_list.total)
         return set_error(QADIC_E_NOMEM, "workspace %zu < %zu bytes", ws_bytes, L_list.total);
@@ -510,21 +524,27 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
     hdr->order_off = (uint32_t)L.order_off;
     size_t used = L.tiles_off + tiles.size() * sizeof(BTile);
     if (converted) {
-        // conversion blocks by decreasing operand size (elements incl. padding)
-        std::vector<uint32_t> items(2 * count);
-        std::vector<uint64_t> size(2 * count);
+        // conversion items of at most kConvItemChunks chunks, by decreasing size
+        std::vector<ConvItem> items;
+        std::vector<uint32_t> size;
+        items.reserve(conv_items);
+        size.reserve(conv_items);
         for (int64_t i = 0; i < count; ++i) {
-            const BProd &P = pp[i];
-            const uint64_t k = fields[descs[i].field]->k;
-            size[2 * i] = k * (uint64_t)P.m * P.kp;
-            size[2 * i + 1] = k * (uint64_t)P.K * P.np;
-            items[2 * i] = (uint32_t)(2 * i);
-            items[2 * i + 1] = (uint32_t)(2 * i + 1);
+            const uint32_t k = fields[descs[i].field]->k;
+            const uint64_t n_ops[2] = {chunks_a(descs[i], k), chunks_b(descs[i], k)};
+            for (int op = 0; op < 2; ++op)
+                for (uint64_t b = 0; b < n_ops[op]; b += kConvItemChunks) {
+                    items.push_back(ConvItem{(uint32_t)(2 * i + op), (uint32_t)b});
+                    size.push_back((uint32_t)std::min<uint64_t>(kConvItemChunks, n_ops[op] - b));
+                }
         }
-        std::stable_sort(items.begin(), items.end(),
-                         [&](uint32_t a, uint32_t b) { return size[a] > size[b]; });
-        std::memcpy(host.data() + L.order_off, items.data(), items.size() * sizeof(uint32_t));
-        used = L.order_off + items.size() * sizeof(uint32_t);
+        std::vector<int64_t> ord(items.size());
+        for (size_t i = 0; i < ord.size(); ++i) ord[i] = (int64_t)i;
+        std::stable_sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) { return size[a] > size[b]; });
+        ConvItem *ip = reinterpret_cast<ConvItem *>(host.data() + L.order_off);
+        for (size_t i = 0; i < ord.size(); ++i) ip[i] = items[ord[i]];
+        hdr->nconv = (uint32_t)items.size();
+        used = L.order_off + items.size() * sizeof(ConvItem);
     }
     if (cudaMemcpyAsync(workspace, host.data(), used, cudaMemcpyHostToDevice, stream) != cudaSuccess)
         return set_error(QADIC_E_CUDA, "work list upload: %s", cudaGetErrorString(cudaGetLastError()));
@@ -538,7 +558,7 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
     // {convert, products} or {products}; the tile counter starts at zero
     auto enqueue = [&](cudaStream_t s) -> int {
         if (converted) {
-            const int cs = launch_convert((const uint8_t *)workspace, count, s);
+            const int cs = launch_convert((const uint8_t *)workspace, conv_items, s);
             if (cs != QADIC_OK) return cs;
             return launch_async((uint8_t *)workspace, grid, smem, s);
         }

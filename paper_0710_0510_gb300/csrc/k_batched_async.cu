@@ -2,7 +2,8 @@
 // qadic_batched_gemm takes when its workspace has room for the converted
 // operands (qadic_batched_workspace_size_fields).
 //
-// Launch 1 (convert_kernel, one block per product operand, largest first): the uint8
+// Launch 1 (convert_kernel, one block per piece of at most 4096 x 8 elements
+// of a product operand, largest first): the uint8
 // coefficient planes become centred 16-bit operands (bf16; f16 for GF(2^8),
 // see below) in the workspace, rows padded with zeros to a multiple of 8
 // elements so that every 16-byte piece of a row is aligned.  Each element is
@@ -47,18 +48,21 @@ __device__ __forceinline__ void load8(const uint8_t *src, int valid, uint32_t (&
             w[1] = __funnelshift_r(x1, x2, 8 * a);
         }
     } else {
-        w[0] = w[1] = 0;
-        for (int b = 0; b < valid; ++b) w[b >> 2] |= (uint32_t)__ldg(src + b) << (8 * (b & 3));
+        uint64_t v = 0;   // (a register: indexing w here would move it to local memory)
+        for (int b = 0; b < valid; ++b) v |= (uint64_t)__ldg(src + b) << (8 * b);
+        w[0] = (uint32_t)v;
+        w[1] = (uint32_t)(v >> 32);
     }
 }
 
 __global__ void __launch_bounds__(kConvThreads) convert_kernel(const uint8_t *ws) {
     const BHeader *hdr = reinterpret_cast<const BHeader *>(ws);
-    if ((int64_t)blockIdx.x >= 2 * (int64_t)hdr->nprod) return;
-    // largest operands first, so that the small ones fill the end of the launch
-    const uint32_t item = reinterpret_cast<const uint32_t *>(ws + hdr->order_off)[blockIdx.x];
-    const int64_t prod = item >> 1;
-    const bool isB = item & 1;
+    if (blockIdx.x >= hdr->nconv) return;
+    // items of at most kConvItemChunks chunks, largest first, so that the
+    // blocks are even and the small ones fill the end of the launch
+    const ConvItem item = reinterpret_cast<const ConvItem *>(ws + hdr->order_off)[blockIdx.x];
+    const int64_t prod = item.op >> 1;
+    const bool isB = item.op & 1;
     const BFieldParams *fields = reinterpret_cast<const BFieldParams *>(ws + hdr->fields_off);
     const BProd &P = reinterpret_cast<const BProd *>(ws + hdr->prods_off)[prod];
     const BFieldParams &F = fields[P.field];
@@ -71,12 +75,12 @@ __global__ void __launch_bounds__(kConvThreads) convert_kernel(const uint8_t *ws
     const uint8_t *src = isB ? P.B : P.A;
     uint16_t *dst = const_cast<uint16_t *>(isB ? P.B16 : P.A16);
     const uint32_t per_row = (uint32_t)ld_out / 8;
-    const uint32_t total = (uint32_t)rows * per_row;   // <= 8 * 4096 * 512
+    const uint32_t end = min((uint32_t)rows * per_row, item.begin + kConvItemChunks);   // <= 8 * 4096 * 512
     const Div32 div_row = make_div32_device(per_row);
     // kUnrollConv chunks per thread per round: all their loads are issued
     // before any of them is converted and stored
     constexpr int kUnrollConv = 4;
-    for (uint32_t c0 = threadIdx.x; c0 < total; c0 += kConvThreads * kUnrollConv) {
+    for (uint32_t c0 = item.begin + threadIdx.x; c0 < end; c0 += kConvThreads * kUnrollConv) {
         uint32_t w[kUnrollConv][2];
 #pragma unroll
         for (int u = 0; u < kUnrollConv; ++u) {
@@ -84,12 +88,12 @@ __global__ void __launch_bounds__(kConvThreads) convert_kernel(const uint8_t *ws
             const uint32_t r = div32(c, div_row);
             const int col = (int)(c - r * per_row) * 8;
             // past the row (or past the last chunk): zeros, and tab[0] = 0
-            load8(src + (int64_t)r * ld_in + col, c < total ? cols - col : 0, w[u]);
+            load8(src + (int64_t)r * ld_in + col, c < end ? cols - col : 0, w[u]);
         }
 #pragma unroll
         for (int u = 0; u < kUnrollConv; ++u) {
             const uint32_t c = c0 + u * kConvThreads;
-            if (c >= total) break;
+            if (c >= end) break;
             const uint32_t r = div32(c, div_row);
             const int col = (int)(c - r * per_row) * 8;
             uint4 o;
@@ -262,8 +266,8 @@ int64_t async_grid(size_t smem, int64_t ntiles) {
     return grid;
 }
 
-int launch_convert(const uint8_t *ws, int64_t nprod, cudaStream_t stream) {
-    convert_kernel<<<(unsigned)(2 * nprod), kConvThreads, 0, stream>>>(ws);
+int launch_convert(const uint8_t *ws, int64_t nitems, cudaStream_t stream) {
+    convert_kernel<<<(unsigned)nitems, kConvThreads, 0, stream>>>(ws);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(QADIC_E_CUDA, "batched convert launch: %s", cudaGetErrorString(e));
     return QADIC_OK;

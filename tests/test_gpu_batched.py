@@ -99,8 +99,12 @@ def test_batched_paths_agree_and_sizes(torch, orc):
     r8 = lambda x: (x + 7) // 8 * 8
     conv = sum(fields[f].k * (m * r8(K) + K * r8(n)) * 2 for (m, n, K), f in zip(shapes, fi))
     assert big >= small + conv
-    # + 256-byte alignment of each operand, + the conversion order (4 bytes per operand)
-    assert big <= small + conv + 2 * 256 * len(shapes) + 8 * len(shapes) + 512
+    # + 256-byte alignment of each operand, + the conversion items (8 bytes for
+    # every 4096 chunks of 8 elements of an operand)
+    cdiv = lambda a, b: -(-a // b)
+    items = sum(cdiv(fields[f].k * m * (r8(K) // 8), 4096) + cdiv(fields[f].k * K * (r8(n) // 8), 4096)
+                for (m, n, K), f in zip(shapes, fi))
+    assert big <= small + conv + 2 * 256 * len(shapes) + 8 * items + 512
 
 
 @pytest.mark.parametrize("pk", [(3, 3), (5, 5), (2, 6), (101, 2), (3, 7), (13, 3), (2, 1)])
