@@ -545,9 +545,10 @@ def make_batched(torch, q, W, count=4096, salt=0):
 
 def bench_batched(args, torch, q, W):
     fields, dims, fidx, offs, hA, hB, dC, descs, ws = make_batched(torch, q, W)
+    darr = q.desc_array(descs)   # built once: the host stays ahead of the GPU
 
     def step(kev):
-        q.batched_gemm(fields, descs, ws, graph=True)
+        q.batched_gemm(fields, darr, ws, graph=True)
 
     # default tiles, then the autotuner's choice on this batch (tuning is
     # setup, outside the timed region)
@@ -559,7 +560,7 @@ def bench_batched(args, torch, q, W):
     ws_list = torch.empty(q.batched_workspace_size(descs), dtype=torch.uint8, device="cuda")
 
     def step_reg(kev):
-        q.batched_gemm(fields, descs, ws_list, graph=True)
+        q.batched_gemm(fields, darr, ws_list, graph=True)
 
     tot_r, _ = time_steps(torch, step_reg, args.steps, args.warmup, None)
     ms_register = tot_r / args.steps

@@ -74,8 +74,15 @@ struct TileCfg {
     static constexpr int LDA = BK + 8;               // 16-bit elements per A_s row
     static constexpr int LDB = BN + 8;               // 16-bit elements per B_s row
     static constexpr int SMEM = (KP * BM * LDA + KP * BK * LDB) * 2;
+    // cp.async stages of the converted-operand kernel: more where a stage is
+    // small (little MMA work per K-block to hide a copy behind)
+    static constexpr int NSTAGE = SMEM <= 8192 ? 4 : SMEM <= 16384 ? 3 : 2;
     static_assert(MT >= 1 && NT >= 1 && BK % 16 == 0, "tile shape");
 };
+
+inline int async_stages(size_t stage_bytes) {
+    return stage_bytes <= 8192 ? 4 : stage_bytes <= 16384 ? 3 : 2;
+}
 
 // Candidate (BM, BN, BK) per k; index 0 is the default.  Every candidate is
 // at least 32 x 16 (the work-list bound); configuration 0 is kMinBK deep.

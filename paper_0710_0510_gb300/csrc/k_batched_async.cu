@@ -12,8 +12,9 @@
 //
 // Launch 2 (async_kernel, persistent, tiles pulled with one atomicAdd each):
 // operand tiles go from the converted planes to shared memory with
-// cp.async (16 bytes each, zero-filled past the edges), double-buffered so
-// that the copies of K-block kb+1 run under the MMAs of K-block kb; the
+// cp.async (16 bytes each, zero-filled past the edges) through 2-4 stages
+// (more for the smaller tiles), so that the copies of the next K-blocks run
+// under the MMAs of this one; the
 // products, exact-chunk reductions and the epilogue are those of the
 // register-staged kernel (batched_tile.cuh).
 //
@@ -113,8 +114,9 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 
-__device__ __forceinline__ void cp_async_wait_one() {
-    asm volatile("cp.async.wait_group 1;" ::: "memory");
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 // Copies of one K-block of operand tiles into a stage: A_s [KP][BM][LDA],
@@ -153,6 +155,7 @@ template <int KP, int BM, int BN, int BK, bool F16>
 __device__ __forceinline__ void run_tile_async(const BProd &P, const BFieldParams &F, int tm, int tn,
                                                uint8_t *smem) {
     using T = TileCfg<KP, BM, BN, BK>;
+    constexpr int NS = T::NSTAGE;
     constexpr int kStage = T::SMEM / 2;               // 16-bit elements per stage
     constexpr int kAElems = KP * T::BM * T::LDA;
     uint16_t *S = reinterpret_cast<uint16_t *>(smem);
@@ -164,17 +167,21 @@ __device__ __forceinline__ void run_tile_async(const BProd &P, const BFieldParam
     acc_zero<T, F16>(acc);
     const int nkb = (P.K + BK - 1) / BK;
     const int chunk_blocks = max(1, (F16 ? F.chunk_k16 : F.chunk_k) / BK);
-    __syncthreads();   // the previous tile's reads of both stages are done
-    issue_stage<KP, T>(P, S, S + kAElems, row0, col0, 0);
-    cp_async_commit();
+    __syncthreads();   // the previous tile's reads of every stage are done
+#pragma unroll
+    for (int s = 0; s < NS - 1; ++s) {   // K-blocks 0 .. NS-2 in flight
+        if (s < nkb) issue_stage<KP, T>(P, S + s * kStage, S + s * kStage + kAElems, row0, col0, s * BK);
+        cp_async_commit();
+    }
     for (int kb = 0; kb < nkb; ++kb) {
-        uint16_t *As = S + (kb & 1) * kStage;
-        if (kb + 1 < nkb) {
-            uint16_t *An = S + ((kb + 1) & 1) * kStage;
-            issue_stage<KP, T>(P, An, An + kAElems, row0, col0, (kb + 1) * BK);
+        uint16_t *As = S + (kb % NS) * kStage;
+        const int nxt = kb + NS - 1;   // refills the stage read in iteration kb - 1
+        if (nxt < nkb) {
+            uint16_t *An = S + (nxt % NS) * kStage;
+            issue_stage<KP, T>(P, An, An + kAElems, row0, col0, nxt * BK);
         }
-        cp_async_commit();       // (empty on the last K-block: keeps the group count uniform)
-        cp_async_wait_one();     // everything but the newest group: stage kb has landed
+        cp_async_commit();       // (empty near the end: keeps the group count uniform)
+        cp_async_wait<NS - 1>(); // all but the NS - 1 newest groups: stage kb has landed
         __syncthreads();
 #pragma unroll 1
         for (int ks = 0; ks < BK / 16; ++ks)
@@ -210,7 +217,7 @@ __device__ __noinline__ void run_tile_async_cfg(int cfg, const BProd &P, const B
 }
 
 __global__ void __launch_bounds__(kThreads, 5) async_kernel(uint8_t *ws) {
-    extern __shared__ __align__(128) uint8_t smem[];   // two stages of the largest tile in the list
+    extern __shared__ __align__(128) uint8_t smem[];   // the stages of the largest tile in the list
     __shared__ int s_tile;
     BHeader *hdr = reinterpret_cast<BHeader *>(ws);
     const BFieldParams *fields = reinterpret_cast<const BFieldParams *>(ws + hdr->fields_off);
@@ -244,7 +251,10 @@ __global__ void __launch_bounds__(kThreads, 5) async_kernel(uint8_t *ws) {
 
 }  // namespace
 
-size_t async_smem_bytes(uint32_t k, int cfg) { return 2 * tile_smem_bytes(k, cfg); }
+size_t async_smem_bytes(uint32_t k, int cfg) {
+    const size_t stage = tile_smem_bytes(k, cfg);
+    return async_stages(stage) * stage;
+}
 
 int prepare_async_kernel() {
     static std::once_flag once;

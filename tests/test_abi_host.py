@@ -246,3 +246,12 @@ def test_zero_counts_are_noops():
     L = q.lib()
     assert L.qadic_redq(7, 10, 5, None, None, 0, 3, None) == q.OK
     assert L.qadic_polymul_batched(7, 4, None, None, None, 0, 0, None) == q.OK
+
+
+def test_desc_array_is_built_once():
+    """A prebuilt descriptor array passes through unchanged; a list becomes
+    an array of the same descriptors."""
+    d = [q.GemmDesc(0, 3, 4, 5, 16, 32, 48, 5, 4, 4, 0), q.GemmDesc(1, 7, 8, 9, 0, 0, 0, 9, 8, 8, 0)]
+    arr = q.desc_array(d)
+    assert len(arr) == 2 and arr[1].m == 7 and arr[0].ldb == 4
+    assert q.desc_array(arr) is arr
