@@ -441,7 +441,9 @@ gemm_planes_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
 // side.  The pack step writes the operand as k planes (index i), plane i
 // being the k blocks M_i0, ..., M_i,k-1 (n_pad rows each, K-major), so a
 // K-block of plane i of A meets the same K-block of plane i of the operand.
-// The K loop runs over (plane i, K-block) pairs, one tile of each per stage;
+// The K loop runs over (K-block, plane i) pairs, one tile of each per stage
+// (all planes of a K-block before the next, so that CTAs on nearby tiles
+// read the same operand K-slices at about the same time and meet in L2);
 // each plane has its own accumulator (one product per K step, so the exact
 // FP32 chunk is (2^24 - 2p) / h^2), and the epilogue adds the k
 // accumulators and reduces mod p -- no fold, no 2k-1 plane sums.
@@ -529,7 +531,7 @@ gemm_fold_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
 
     if (warp == 0) {
         if (lane == 0) {
-            // ---------------- TMA producer: (plane, K-block) pairs ----------------
+            // ---------------- TMA producer: (K-block, plane) pairs ----------------
             ptx::prefetch_tmap(&tmA);
             ptx::prefetch_tmap(&tmB);
             int64_t it = 0;
@@ -538,8 +540,8 @@ gemm_fold_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
                 int um, tn;
                 unit_coords(unit, P, um, tn);
                 const int tm = um * CM + rank;
-                for (int i = 0; i < KP && ok; ++i)
-                    for (int kb = 0; kb < nkbp; ++kb, ++it) {
+                for (int kb = 0; kb < nkbp && ok; ++kb)
+                    for (int i = 0; i < KP; ++i, ++it) {
                         const int stage = (int)(it % CF::STAGES);
                         if (it >= CF::STAGES) {
                             if (*abort_flag ||
@@ -581,8 +583,8 @@ gemm_fold_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
                     }
                     ptx::tc_fence_after();
                 }
-                for (int i = 0; i < KP && ok; ++i)
-                    for (int kb = 0; kb < nkbp; ++kb, ++it) {
+                for (int kb = 0; kb < nkbp && ok; ++kb) {
+                    for (int i = 0; i < KP; ++i, ++it) {
                         const int stage = (int)(it % CF::STAGES);
                         if (*abort_flag ||
                             !ptx::mbar_wait(&full[stage], (uint32_t)(it / CF::STAGES) & 1)) {
@@ -598,16 +600,18 @@ gemm_fold_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
                                           (kb == 0 && kk == 0) ? 0u : 1u);
                         if (CM == 1) ptx::mma_commit(&empty[stage]);
                         else ptx::mma_commit_multicast(&empty[stage], kAllCtas);
-                        if ((kb + 1) % P.chunk_kb == 0 && kb + 1 < nkbp) {
-                            ptx::mma_commit(acc_full);
-                            if (!ptx::mbar_wait(acc_empty, (uint32_t)drain & 1)) {
-                                ok = false;
-                                break;
-                            }
-                            ptx::tc_fence_after();
-                            ++drain;
-                        }
                     }
+                    if (ok && (kb + 1) % P.chunk_kb == 0 && kb + 1 < nkbp) {
+                        // exact-chunk boundary of every accumulator at once
+                        ptx::mma_commit(acc_full);
+                        if (!ptx::mbar_wait(acc_empty, (uint32_t)drain & 1)) {
+                            ok = false;
+                            break;
+                        }
+                        ptx::tc_fence_after();
+                        ++drain;
+                    }
+                }
                 if (ok) ptx::mma_commit(acc_full);   // tile complete
             }
             if (!ok) {
@@ -621,7 +625,7 @@ gemm_fold_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
         // ---------------- epilogue (warps 2..5) ----------------
         const int quarter = warp & 3;
         const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16);
-        const int ndrain = nkbp > 0 ? KP * ((nkbp - 1) / P.chunk_kb) : 0;
+        const int ndrain = nkbp > 0 ? (nkbp - 1) / P.chunk_kb : 0;
         int phase = 0;
         bool ok = true;
         for (int unit = unit0; unit < P.nunits && ok; unit += unit_step) {
@@ -629,9 +633,7 @@ gemm_fold_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
             unit_coords(unit, P, um, tn);
             const int tm = um * CM + rank;
             for (int d = 0; d < ndrain; ++d, ++phase) {
-                // in-place reduction of every accumulator (the ones of planes
-                // not started yet hold stale values that the plane's first
-                // MMA overwrites)
+                // in-place reduction of every accumulator
                 if (!ptx::mbar_wait(acc_full, (uint32_t)phase & 1) || *abort_flag) {
                     ok = false;
                     break;
