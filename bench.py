@@ -51,8 +51,8 @@ def headline_config(n):
 MEASURED_TRAFFIC = {
     "gemm_planes_tc_kernel<2,128,2>": {
         "file": "paper_0710_0510_gb300/csrc/k_gemm_tc.cu",
-        "code_sha256": "e6b5523dd5fd45285468e70a4a4903717ea47855a6767a6ad1a50bef2068fbd8",
-        "bytes": 420781056 + 31405824, "n": 4096},
+        "code_sha256": "1e120ae908475f8808e92023bf97839ae115f42850807e3cda19be9ed67e9300",
+        "bytes": 453916416 + 31216640, "n": 4096},
 }
 
 

@@ -323,20 +323,28 @@ gemm_planes_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                     break;
                 }
                 ptx::tc_fence_after();
+                // NB 32-column loads in flight per wait: the tensor-memory load
+                // latency is paid NACC * CH / NB times per drain, not NACC * CH
+                constexpr int NB = CF::CH < 4 ? CF::CH : 4;
+                static_assert(CF::CH % NB == 0, "drain batches");
 #pragma unroll 1
                 for (int t = 0; t < CF::NACC; ++t)
 #pragma unroll 1
-                    for (int c = 0; c < CF::HALF; c += 32) {
-                        uint32_t v[32];
-                        ptx::tmem_ld32(tbase + t * BN + c, v);
+                    for (int c = 0; c < CF::HALF; c += 32 * NB) {
+                        uint32_t v[NB][32];
+#pragma unroll
+                        for (int b = 0; b < NB; ++b) ptx::tmem_ld32(tbase + t * BN + c + 32 * b, v[b]);
                         ptx::tmem_wait_ld();
 #pragma unroll
-                        for (int e = 0; e < 32; ++e) {
-                            const float x = __uint_as_float(v[e]);
-                            const float nq = rintf(x * P.inv_pf);
-                            v[e] = __float_as_uint(fmaf(-P.pf, nq, x));   // |.| <= 1.5 p, exact
+                        for (int b = 0; b < NB; ++b) {
+#pragma unroll
+                            for (int e = 0; e < 32; ++e) {
+                                const float x = __uint_as_float(v[b][e]);
+                                const float nq = rintf(x * P.inv_pf);
+                                v[b][e] = __float_as_uint(fmaf(-P.pf, nq, x));   // |.| <= 1.5 p, exact
+                            }
+                            ptx::tmem_st32(tbase + t * BN + c + 32 * b, v[b]);
                         }
-                        ptx::tmem_st32(tbase + t * BN + c, v);
                     }
                 ptx::tmem_wait_st();
                 ptx::tc_fence_before();
