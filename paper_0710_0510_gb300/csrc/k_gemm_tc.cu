@@ -30,7 +30,7 @@
 //   warp 0      TMA producer, streaming K-blocks of consecutive tiles into a
 //               STAGES-deep ring without a break between tiles
 //   warp 1      allocates tensor memory; one thread issues tcgen05.mma
-//   warps 2-5   epilogue, one warp per 32-lane quarter: in-place drains; at
+//   warps 2-9   epilogue, two warps per 32-lane quarter: in-place drains; at
 //               the end of a tile they read the accumulators 16 columns at
 //               a time, release tensor memory to the next tile's MMAs after
 //               the last read, and reduce mod p, fold mod P and store while
@@ -58,11 +58,13 @@ __device__ __forceinline__ uint64_t operand_desc(const void *tile) {
     else return ptx::smem_desc_sw64(tile);
 }
 constexpr int kGroupM = 16;
-// Four epilogue warps, one per 32-lane quarter of tensor memory.  (Warps are
-// spread over the SM's four sub-partitions, each with its own register
-// file: more epilogue warps would add no issue slots and would cap the
-// registers per thread.)
-constexpr int kEpiWarps = 4;
+// Eight epilogue warps, two per 32-lane quarter of tensor memory, each taking
+// half of the quarter's columns.  The epilogue is latency-bound (tensor-
+// memory loads, then dependent reduce/fold chains), and tensor memory goes to
+// the next tile's MMAs only when the last columns have been read, so two
+// warps per sub-partition shorten that wait (register cap 204 per thread at
+// 320 threads; no kernel spills).
+constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kSmemBudget = 227 * 1024;
 
@@ -302,10 +304,10 @@ gemm_planes_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
             if (!ptx::mbar_wait(mma_done, 0)) *abort_flag = 1;
         }
     } else {
-        // ---------------- epilogue (warps 2..5) ----------------
+        // ---------------- epilogue (warps 2..9) ----------------
         const int ew = warp - 2;
         const int quarter = warp & 3;           // TMEM lanes 32*quarter.. (warp % 4 rule)
-        const int col_base = (ew / 4) * CF::HALF;   // 0 with four epilogue warps
+        const int col_base = (ew / 4) * CF::HALF;   // which half of the quarter's columns
         const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + col_base;
         const int ndrain = nkb > 0 ? (nkb - 1) / P.chunk_kb : 0;
         float foldf[(KP - 1) * KP + 1];
@@ -630,9 +632,14 @@ gemm_fold_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
             if (!ptx::mbar_wait(mma_done, 0)) *abort_flag = 1;
         }
     } else {
-        // ---------------- epilogue (warps 2..5) ----------------
-        const int quarter = warp & 3;
+        // ---------------- epilogue (warps 2 ..) ----------------
+        // kEpiWarps / 4 warps share each 32-lane quarter, splitting its columns
+        constexpr int kPerQuarter = kEpiWarps / 4;
+        const int quarter = warp & 3, part = (warp - 2) / 4;
         const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16);
+        constexpr int kDrainCols = CF::ACC_COLS / kPerQuarter;   // accumulator columns reduced per warp
+        constexpr int kOutCols = BN / kPerQuarter;               // output columns per warp
+        static_assert(kDrainCols % 32 == 0 && kOutCols % 16 == 0, "epilogue column split");
         const int ndrain = nkbp > 0 ? (nkbp - 1) / P.chunk_kb : 0;
         int phase = 0;
         bool ok = true;
@@ -648,7 +655,7 @@ gemm_fold_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
                 }
                 ptx::tc_fence_after();
 #pragma unroll 1
-                for (int c = 0; c < CF::ACC_COLS; c += 32) {
+                for (int c = part * kDrainCols; c < (part + 1) * kDrainCols; c += 32) {
                     uint32_t v[32];
                     ptx::tmem_ld32(tbase + c, v);
                     ptx::tmem_wait_ld();
@@ -671,16 +678,17 @@ gemm_fold_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
             ++phase;
             ptx::tc_fence_after();
             const int64_t row = (int64_t)tm * BM + quarter * 32 + lane;
+            const int c_begin = part * kOutCols, c_end = c_begin + kOutCols;
             if constexpr (EPI == EPI_KARATSUBA) {
 #pragma unroll 1
-                for (int c = 0; c < BN; c += 16) {
+                for (int c = c_begin; c < c_end; c += 16) {
                     float r[3][16];
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         uint32_t v[16];
                         ptx::tmem_ld16(tbase + a * BN + c, v);
                         ptx::tmem_wait_ld();
-                        if (c + 16 >= BN && a == 2) {
+                        if (c + 16 >= c_end && a == 2) {
                             ptx::tc_fence_before();
                             ptx::mbar_arrive(tmem_free);
                         }
@@ -725,7 +733,7 @@ gemm_fold_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
                 continue;
             }
 #pragma unroll 1
-            for (int c = 0; c < BN; c += 16) {
+            for (int c = c_begin; c < c_end; c += 16) {
                 float s[16];
 #pragma unroll
                 for (int e = 0; e < 16; ++e) s[e] = 0.f;
@@ -734,7 +742,7 @@ gemm_fold_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
                     uint32_t v[16];
                     ptx::tmem_ld16(tbase + a * BN + c, v);
                     ptx::tmem_wait_ld();
-                    if (c + 16 >= BN && a == KP - 1) {
+                    if (c + 16 >= c_end && a == KP - 1) {
                         ptx::tc_fence_before();
                         ptx::mbar_arrive(tmem_free);
                     }
