@@ -73,6 +73,39 @@ __device__ __forceinline__ uint32_t pack_word32(uint64_t bytes, uint32_t p, uint
     return w;
 }
 
+// Packed word of one operand: the bytes taken mod p and spaced by s bits.
+// When every byte is already below p (checked four at a time) the reduction
+// is skipped, and with s = 8 the loaded bytes are the packed word as they
+// stand.  Same value either way.
+template <int K>
+__device__ __forceinline__ uint64_t operand_word(uint64_t bytes, uint32_t p, uint32_t m32,
+                                                 uint32_t p4, uint32_t s, const uint64_t (&pw)[K]) {
+    const bool canon = (__vcmpgeu4((uint32_t)bytes, p4) | __vcmpgeu4((uint32_t)(bytes >> 32), p4)) == 0;
+    if (canon) {
+        if (s == 8) return bytes;
+        uint64_t w = 0;
+#pragma unroll
+        for (int j = 0; j < K; ++j) w += ((bytes >> (8 * j)) & 0xffu) * pw[j];
+        return w;
+    }
+    return pack_word<K>(bytes, p, m32, pw);
+}
+
+template <int K>
+__device__ __forceinline__ uint32_t operand_word32(uint64_t bytes, uint32_t p, uint32_t m32,
+                                                   uint32_t p4, uint32_t s, const uint64_t (&pw)[K]) {
+    const uint32_t lo = (uint32_t)bytes;   // with s = 8 and K s <= 32 all K <= 4 bytes are here
+    const bool canon = (__vcmpgeu4(lo, p4) | __vcmpgeu4((uint32_t)(bytes >> 32), p4)) == 0;
+    if (canon) {
+        if (s == 8) return lo;
+        uint32_t w = 0;
+#pragma unroll
+        for (int j = 0; j < K; ++j) w += ((uint32_t)(bytes >> (8 * j)) & 0xffu) * (uint32_t)pw[j];
+        return w;
+    }
+    return pack_word32<K>(bytes, p, m32, pw);
+}
+
 // MODE 0: FP64 product made exact as hi + lo (lo = fma(a, b, -hi));
 // MODE 1: single-rounded FP64 product (Eq. 2 with m = 53 must hold);
 // MODE 2: 64-bit integer words, r = a~ b~ exactly (Sec. 2 allows m = 64).
@@ -93,6 +126,7 @@ polymul_kernel(const uint8_t *__restrict__ a, const uint8_t *__restrict__ b,
     uint8_t *stage = smem + ((p * p + 15) & ~15u);  // kChunk * D bytes (16-byte aligned)
 
     const uint32_t m32 = (uint32_t)((((uint64_t)1 << 32) + p - 1) / p);
+    const uint32_t p4 = p * 0x01010101u;   // p in every byte (p <= 251)
     for (uint32_t i = threadIdx.x; i < p * p; i += blockDim.x) {
         const uint32_t x = i / p, y = i % p;      // table index x*p + y -> (x + (-q) y) mod p
         corr[i] = (uint8_t)mod_small(x + qneg_mod_p * y, p, m32);
@@ -125,14 +159,14 @@ polymul_kernel(const uint8_t *__restrict__ a, const uint8_t *__restrict__ b,
             uint64_t r;
             if (MODE == 2) {
                 if (narrow) {
-                    r = (uint64_t)pack_word32<K>(va[j], p, m32, pw) *
-                        pack_word32<K>(vb[j], p, m32, pw);
+                    r = (uint64_t)operand_word32<K>(va[j], p, m32, p4, s, pw) *
+                        operand_word32<K>(vb[j], p, m32, p4, s, pw);
                 } else {
-                    r = pack_word<K>(va[j], p, m32, pw) * pack_word<K>(vb[j], p, m32, pw);
+                    r = operand_word<K>(va[j], p, m32, p4, s, pw) * operand_word<K>(vb[j], p, m32, p4, s, pw);
                 }   // < 2^((2k-1) s) <= 2^63: exact in 64 bits
             } else {
-                const uint64_t aw = pack_word<K>(va[j], p, m32, pw);
-                const uint64_t bw = pack_word<K>(vb[j], p, m32, pw);
+                const uint64_t aw = operand_word<K>(va[j], p, m32, p4, s, pw);
+                const uint64_t bw = operand_word<K>(vb[j], p, m32, p4, s, pw);
                 const double ad = u64_to_f64_exact(aw), bd = u64_to_f64_exact(bw);   // < 2^53
                 const double hi = ad * bd;
                 if (MODE == 1) {

@@ -67,6 +67,22 @@ def test_polymul_other_rings(torch, orc, p, k):
         assert np.array_equal(host(out), orc.polymul(p, a, b))
 
 
+@pytest.mark.parametrize("p,k", [(7, 4), (3, 3), (2, 8), (251, 2), (5, 5)])
+def test_polymul_unreduced_bytes(torch, orc, p, k):
+    """Coefficient bytes at or above p are taken mod p; pairs with such bytes
+    sit between canonical ones in the same warps (every third pair canonical),
+    so both packing paths run side by side."""
+    rng = np.random.default_rng(p * 7 + k)
+    a = rng.integers(0, 256, (4099, k), dtype=np.uint8)
+    b = rng.integers(0, 256, (4099, k), dtype=np.uint8)
+    a[::3] %= p
+    b[::3] %= p
+    b[1::3] %= p                      # some pairs with one canonical operand only
+    for int_words in (False, True):
+        out = q.polymul_batched(p, k, dev(torch, a), dev(torch, b), int_words=int_words)
+        assert np.array_equal(host(out), orc.polymul(p, a, b)), int_words
+
+
 def test_polymul_all_max(torch, orc):
     a = np.full((1000, 4), 6, np.uint8)
     for int_words in (False, True):
