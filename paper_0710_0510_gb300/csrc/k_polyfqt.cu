@@ -60,16 +60,35 @@ struct FqtParams {
     Div64 divp;
 };
 
+// q = 2^s is fixed by d and the word: the largest s with (2d+1) s within
+// the word (64 bits, or 51 for Lemma 1 on binary64) and, for integer words,
+// (d+1) s <= 32 (32-bit operands).  The host derives it the same way.
+__host__ __device__ constexpr uint32_t fqt_log2_q(uint32_t d, bool int_words) {
+    return int_words ? (64 / (2 * d + 1) < 32 / (d + 1) ? 64 / (2 * d + 1) : 32 / (d + 1))
+                     : 51 / (2 * d + 1);
+}
+
+// DT >= 0: the kernel is specialised for d = DT (every digit shift a
+// constant, every loop over digits unrolled); DT = -1 reads d from P.
+template <int DT>
+__device__ __forceinline__ uint32_t fqt_d(const FqtParams &P) { return DT >= 0 ? (uint32_t)DT : P.d; }
+
+template <bool INT, int DT>
+__device__ __forceinline__ uint32_t fqt_s(const FqtParams &P) {
+    return DT >= 0 ? fqt_log2_q((uint32_t)DT, INT) : P.s;
+}
+
 // REDQ_{2d+1} of an accumulator (Alg. 2): rop = floor(r/p), u_j from the
 // shifted words, mu_j = (u_j - q u_{j+1}) mod p; returns rho = sum_j mu_j q^j.
-template <bool INT>
+template <bool INT, int DT>
 __device__ __forceinline__ uint64_t redq_rho(uint64_t r, double rd, const FqtParams &P) {
     uint64_t rop;
     if constexpr (INT) rop = div64(r, P.divp);
     else rop = f64_to_u64_exact(__dmul_ru(rd, P.inv_p_up));
-    const uint32_t p = P.p, s = P.s, top = 2 * P.d;
+    const uint32_t p = P.p, s = fqt_s<INT, DT>(P), top = 2 * fqt_d<DT>(P);
     uint64_t rho = 0;
     uint32_t u_next = 0;
+#pragma unroll
     for (int j = (int)top; j >= 0; --j) {
         const uint32_t sh = s * (uint32_t)j;
         const uint32_t u = (uint32_t)(r >> sh) - p * (uint32_t)(rop >> sh);
@@ -80,15 +99,16 @@ __device__ __forceinline__ uint64_t redq_rho(uint64_t r, double rd, const FqtPar
     return rho;
 }
 
-template <bool INT>
+template <bool INT, int DT>
 __global__ void __launch_bounds__(kFqtThreads)
 polymul_fqt_kernel(const uint8_t *__restrict__ a, const uint8_t *__restrict__ b,
                    uint8_t *__restrict__ out, int64_t count, const FqtParams P) {
     using Word = typename std::conditional<INT, uint32_t, double>::type;
     using Acc = typename std::conditional<INT, uint64_t, double>::type;
     extern __shared__ __align__(16) uint8_t smem[];
-    const uint32_t p = P.p, N = P.N, Dq = P.Dq, nw = Dq + 1, d1 = P.d + 1, D = 2 * P.d + 1;
-    const uint32_t s_bits = P.s;
+    const uint32_t dd = fqt_d<DT>(P);
+    const uint32_t p = P.p, N = P.N, Dq = P.Dq, nw = Dq + 1, d1 = dd + 1, D = 2 * dd + 1;
+    const uint32_t s_bits = fqt_s<INT, DT>(P);
     Word *Pw = reinterpret_cast<Word *>(smem);                 // nw words
     Word *Qw = Pw + nw;                                        // Q_j at Qw[kPad + j]
     uint32_t *R = reinterpret_cast<uint32_t *>(Qw + nw + 2 * kPad);   // (2 Dq + 1) x D
@@ -101,6 +121,7 @@ polymul_fqt_kernel(const uint8_t *__restrict__ a, const uint8_t *__restrict__ b,
         // DQT pack by shifts (q = 2^s), inputs reduced mod p.
         for (uint32_t i = threadIdx.x; i < nw; i += blockDim.x) {
             uint64_t wa = 0, wb = 0;
+#pragma unroll
             for (uint32_t j = 0; j < d1; ++j) {
                 const uint32_t c = i * d1 + j;
                 if (c <= N) {
@@ -156,8 +177,8 @@ polymul_fqt_kernel(const uint8_t *__restrict__ a, const uint8_t *__restrict__ b,
                 // reduce and feed the reduced word back (digits < p)
 #pragma unroll
                 for (int tt = 0; tt < kTB; ++tt) {
-                    if constexpr (INT) acc[tt] = redq_rho<true>(acc[tt], 0.0, P);
-                    else acc[tt] = u64_to_f64_exact(redq_rho<false>(f64_to_u64_exact(acc[tt]), acc[tt], P));
+                    if constexpr (INT) acc[tt] = redq_rho<true, DT>(acc[tt], 0.0, P);
+                    else acc[tt] = u64_to_f64_exact(redq_rho<false, DT>(f64_to_u64_exact(acc[tt]), acc[tt], P));
                 }
             }
 #pragma unroll
@@ -167,6 +188,7 @@ polymul_fqt_kernel(const uint8_t *__restrict__ a, const uint8_t *__restrict__ b,
                 uint64_t rho;
                 if constexpr (INT) rho = acc[tt];
                 else rho = f64_to_u64_exact(acc[tt]);
+#pragma unroll
                 for (uint32_t j = 0; j < D; ++j) {
                     const uint32_t mu = (uint32_t)((rho >> (s_bits * j)) & dmask);
                     if (mu) atomicAdd(&R[t * D + j], mu);
@@ -181,7 +203,7 @@ polymul_fqt_kernel(const uint8_t *__restrict__ a, const uint8_t *__restrict__ b,
         for (uint32_t c = threadIdx.x; c <= 2 * N; c += blockDim.x) {
             const uint32_t t = c / d1, j = c - t * d1;
             uint32_t v = t <= 2 * Dq ? R[t * D + j] : 0;
-            if (t >= 1 && j < P.d) v += R[(t - 1) * D + j + d1];
+            if (t >= 1 && j < dd) v += R[(t - 1) * D + j + d1];
             o[c] = (uint8_t)(v % p);
         }
         __syncthreads();
@@ -194,7 +216,8 @@ int fqt_parameters(uint32_t p, uint32_t N, uint32_t d, bool int_words, qadic_fqt
     if (!is_prime(p) || p > 251) return set_error(QADIC_E_INVALID, "p must be a prime <= 251");
     if (d > 24) return set_error(QADIC_E_INVALID, "d outside [0, 24]");
     const uint32_t D = 2 * d + 1;
-    uint32_t s = int_words ? std::min(64 / D, 32 / (d + 1)) : 51 / D;
+    uint32_t s = fqt_log2_q(d, int_words);
+    (void)D;
     if (s < 1) return set_error(QADIC_E_OVERFLOW, "no q = 2^s fits %u digits", D);
     const uint64_t q = 1ull << s;
     const uint64_t unit = (uint64_t)(d + 1) * (p - 1) * (p - 1);
@@ -248,7 +271,16 @@ int launch_polymul_fqt(uint32_t p, uint32_t N, uint32_t d, bool int_words, const
     P.divp = make_div64(p);
     P.inv_p_up = inv_up(p);
 
-    auto kern = int_words ? polymul_fqt_kernel<true> : polymul_fqt_kernel<false>;
+    using Kern = void (*)(const uint8_t *, const uint8_t *, uint8_t *, int64_t, const FqtParams);
+    Kern kern;
+    switch (d) {   // the degrees of the bench's sweep and around it; others read d at run time
+#define QADIC_FQT_CASE(D_) \
+    case D_: kern = int_words ? polymul_fqt_kernel<true, D_> : polymul_fqt_kernel<false, D_>; break;
+        QADIC_FQT_CASE(0) QADIC_FQT_CASE(1) QADIC_FQT_CASE(2) QADIC_FQT_CASE(3)
+        QADIC_FQT_CASE(4) QADIC_FQT_CASE(5) QADIC_FQT_CASE(6)
+#undef QADIC_FQT_CASE
+        default: kern = int_words ? polymul_fqt_kernel<true, -1> : polymul_fqt_kernel<false, -1>; break;
+    }
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
