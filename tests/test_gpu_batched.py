@@ -249,6 +249,27 @@ def test_batched_gf256_chunks_every_configuration(torch, orc, restore_tiles, con
 
 
 @pytest.mark.parametrize("converted", [True, False])
+def test_batched_maximum_sizes(torch, orc, converted):
+    """The largest product the batched entry point takes (m = n = K = 4096)
+    beside small ones, GF(31^2) and GF(2^8): sampled entries and whole edge
+    rows and columns against the oracle."""
+    f31, f2 = q.Field(31, 2), q.Field(2, 8)
+    shapes = [(4096, 4096, 4096), (1, 4096, 4096), (4096, 1, 7), (17, 33, 4096)]
+    fidx = [0, 1, 0, 1]
+    bt = Batch(torch, [f31, f2], shapes, fidx, seed=21, converted=converted)
+    bt.run()
+    rng = np.random.default_rng(22)
+    for i, (m, n, K) in enumerate(shapes):
+        f = bt.fields[fidx[i]]
+        C = bt.result(i)
+        ii = np.concatenate([rng.integers(0, m, 64), np.full(min(n, 64), m - 1), np.arange(min(m, 64))])
+        jj = np.concatenate([rng.integers(0, n, 64), np.arange(min(n, 64)), np.full(min(m, 64), n - 1)])
+        want = orc.gemm_entries(f.p, f.poly, np.transpose(bt.A[i], (1, 2, 0)),
+                                np.transpose(bt.B[i], (1, 2, 0)), ii, jj)
+        assert np.array_equal(C[:, ii, jj].T, want), (i, shapes[i])
+
+
+@pytest.mark.parametrize("converted", [True, False])
 def test_graph_cache_after_field_destroyed(torch, orc, converted):
     """A graph cached for a destroyed field is not replayed for a new field
     (its handle may reuse the old address) with the same descriptors and
