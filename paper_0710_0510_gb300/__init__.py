@@ -166,11 +166,17 @@ def _check(status: int):
         raise QadicError(status, msg)
 
 
+_TORCH_CUDA = None   # torch, once a CUDA device has been seen (checked once per process)
+
+
 def _torch():
-    import torch
-    if not torch.cuda.is_available():
-        raise RuntimeError("a CUDA device is required: libqadic has no CPU path")
-    return torch
+    global _TORCH_CUDA
+    if _TORCH_CUDA is None:
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required: libqadic has no CPU path")
+        _TORCH_CUDA = torch
+    return _TORCH_CUDA
 
 
 def _stream(stream=None):

@@ -243,9 +243,14 @@ int launch_polymul(uint32_t p, uint32_t k, uint32_t log2_q, int mode, const uint
                    const uint8_t *b, uint8_t *out, int64_t count, cudaStream_t stream) {
     const uint64_t q = 1ull << log2_q;
     const uint32_t qneg = (uint32_t)((p - q % p) % p);
-    int dev = 0, sms = 0;
+    int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    static int sms_of[64] = {0};   // SM count per device, queried once
+    int sms = dev >= 0 && dev < 64 ? sms_of[dev] : 0;
+    if (sms == 0) {
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (dev >= 0 && dev < 64) sms_of[dev] = sms;
+    }
     // four pairs per thread once the batch fills every SM twice over with them
     const int pairs = count >= (int64_t)sms * kThreads * kMaxPairs * 2 ? kMaxPairs : 1;
     const int64_t chunk = (int64_t)kThreads * pairs;
