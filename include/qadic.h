@@ -319,9 +319,10 @@ int qadic_polymul_batched(uint32_t p, uint32_t k, const uint8_t *a, const uint8_
  * are staged through registers tile by tile.  With at least
  * qadic_batched_workspace_size_fields(fields, nfields, descs, count) bytes
  * the faster path runs instead: one launch converts every operand once to
- * centred 16-bit planes in the workspace (bf16; f16 for GF(2^8), whose 0/1
- * planes keep every partial sum exact in f16 accumulators over chunks of
- * 2047/k), and the persistent launch copies tiles of them with cp.async.
+ * centred planes in the workspace -- fp8 e4m3 for p <= 31 (exact: |c| <= 15),
+ * B transposed, products by m16n8k32 fp8 MMAs (f16 accumulators for GF(2^8),
+ * whose 0/1 planes keep every partial sum exact over chunks of 2047/k);
+ * bf16 for larger p -- and the persistent launch copies tiles with cp.async.
  * Both paths give the same bytes.  The size query with fields returns 0 for
  * invalid arguments.  With QADIC_BATCHED_GRAPH the launch is captured in
  * a CUDA graph keyed by (descs, count, workspace) and replayed on later calls

@@ -7,6 +7,7 @@
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include <type_traits>
 
@@ -25,8 +26,8 @@ struct BFieldParams {
     float pf, inv_pf;
     int32_t chunk_k;               // K elements per exact FP32 chunk (capped)
     int32_t chunk_k16;             // the same for f16 accumulators (GF(2^8) only)
-    int32_t f16;                   // GF(2^8): the converted operands are f16 (see below)
-    int32_t pad;
+    int32_t f16;                   // GF(2^8): f16 accumulators (see the converted-operand kernel)
+    int32_t fp8;                   // p <= 31: operands converted to fp8 e4m3 (|centred| <= 15, exact)
     uint8_t fold[kMaxK * kMaxK];   // X^(k+t) mod P, row t (k coefficients)
 };
 
@@ -34,10 +35,10 @@ struct BProd {
     const uint8_t *A;
     const uint8_t *B;
     uint8_t *C;
-    const uint16_t *A16;           // converted operands (bf16 or f16 bits), or null
-    const uint16_t *B16;
+    const uint16_t *A16;           // converted operands, or null: 16-bit A [k][m][kp] and
+    const uint16_t *B16;           // B [k][K][np]; fp8 fields: bytes, A [k][m][kp], B^T [k][n][kp]
     int32_t m, n, K, lda, ldb, ldc;
-    int32_t kp, np;                // row lengths of A16 (K rounded up to 8) and B16 (n up to 8)
+    int32_t kp, np;                // row lengths: 16-bit K up to 8 and n up to 8; fp8: K up to 16
     int32_t field, cfg;            // field index, tile configuration index
 };
 
@@ -159,6 +160,55 @@ __device__ __forceinline__ uint16_t f16_bits(uint32_t c, const BFieldParams &F) 
     return __half_as_ushort(__int2half_rn(centred_int(c, F)));
 }
 
+// e4m3 holds every integer of magnitude <= 16 exactly, so the centred
+// coefficients of any p <= 31 (and the 0/1 of p = 2) convert without loss.
+__device__ __forceinline__ uint8_t fp8_bits(uint32_t c, const BFieldParams &F) {
+    return (uint8_t)__nv_cvt_float_to_fp8((float)centred_int(c, F), __NV_SATFINITE, __NV_E4M3);
+}
+
+inline bool fp8_field(uint32_t p) { return p <= 31; }
+
+// m16n8k32 with fp8 e4m3 operands (four per register), FP32 or f16
+// accumulators.  On GB300 the legacy path runs these at about 3.6x the
+// bf16 m16n8k16 rate (2177 against 600 TFLOP/s, measured).
+__device__ __forceinline__ void mma_e4m3_f32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k32.row.col.f32.e4m3.e4m3.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ void mma_e4m3_f16(uint32_t (&d)[2], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k32.row.col.f16.e4m3.e4m3.f16 {%0,%1}, {%2,%3,%4,%5}, {%6,%7}, "
+        "{%0,%1};"
+        : "+r"(d[0]), "+r"(d[1])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// fp8 tiles: K-blocks of at least 32 (one m16n8k32 step), rows of BK + 16
+// bytes (A [KP][BM], B^T [KP][BN], both K-major) so that ldmatrix rows fall
+// in distinct banks.
+constexpr int fp8_bk(int bk) { return bk < 32 ? 32 : bk; }
+
+template <int KP, int BM_, int BN_, int BK_>
+struct TileCfg8 {
+    using W = TileCfg<KP, BM_, BN_, 32>;   // warp layout and accumulators as the 16-bit tiles
+    static constexpr int BM = BM_, BN = BN_, BK = fp8_bk(BK_);
+    static constexpr int WM = W::WM, WN = W::WN, MT = W::MT, NT = W::NT, NACC = W::NACC;
+    static constexpr int LDA = BK + 16, LDB = BK + 16;   // bytes
+    static constexpr int SMEM = KP * BM * LDA + KP * BN * LDB;
+    static constexpr int NSTAGE = SMEM <= 8192 ? 4 : SMEM <= 16384 ? 3 : 2;
+};
+
+inline size_t tile_smem_bytes8(uint32_t k, int cfg) {
+    const TileShape t = tile_shape_of(k, cfg);
+    const int bk = fp8_bk(t.bk);
+    return (size_t)k * t.bm * (bk + 16) + (size_t)k * t.bn * (bk + 16);
+}
+
+
 // Accumulators of one warp: 2k-1 sets of MT x NT m16n8 fragments, FP32 (four
 // registers each) or, with F16, f16 pairs (two registers each).
 template <typename T, bool F16>
@@ -210,6 +260,46 @@ __device__ __forceinline__ void tile_mma_step(AccArray<T, F16> &acc, const uint1
                         mma_f16_16816(acc[i + j][mt][nt], afr[mt], bfr[j][nt]);
                     else
                         mma_bf16_16816(acc[i + j][mt][nt], afr[mt], bfr[j][nt]);
+                }
+    }
+}
+
+// One 32-deep step of the k^2 plane products on fp8 tiles (bytes).
+template <int KP, typename T8, bool F16>
+__device__ __forceinline__ void tile_mma_step8(AccArray<typename T8::W, F16> &acc, const uint8_t *As,
+                                               const uint8_t *Bs, int ks, int wm, int wn, int lane) {
+    using T = T8;
+    uint32_t bfr[KP][T::NT][2];
+#pragma unroll
+    for (int j = 0; j < KP; ++j)
+#pragma unroll
+        for (int nt = 0; nt < T::NT; ++nt) {
+            // B^T rows (output columns) n, bytes k: matrix 0 = k 0-15, matrix 1 = k 16-31
+            const uint8_t *src = Bs + (j * T::BN + wn * T::WN + nt * 8 + (lane % 8)) * T::LDB + ks * 32 +
+                                 ((lane / 8) % 2) * 16;
+            asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];"
+                         : "=r"(bfr[j][nt][0]), "=r"(bfr[j][nt][1])
+                         : "r"((uint32_t)__cvta_generic_to_shared(src)));
+        }
+#pragma unroll
+    for (int i = 0; i < KP; ++i) {
+        uint32_t afr[T::MT][4];
+#pragma unroll
+        for (int mt = 0; mt < T::MT; ++mt) {
+            const uint8_t *src =
+                As + (i * T::BM + wm * T::WM + mt * 16 + (lane % 16)) * T::LDA + ks * 32 + (lane / 16) * 16;
+            ldsm_x4((uint32_t)__cvta_generic_to_shared(src), afr[mt][0], afr[mt][1], afr[mt][2], afr[mt][3]);
+        }
+#pragma unroll
+        for (int j = 0; j < KP; ++j)
+#pragma unroll
+            for (int mt = 0; mt < T::MT; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < T::NT; ++nt) {
+                    if constexpr (F16)
+                        mma_e4m3_f16(acc[i + j][mt][nt], afr[mt], bfr[j][nt]);
+                    else
+                        mma_e4m3_f32(acc[i + j][mt][nt], afr[mt], bfr[j][nt]);
                 }
     }
 }
@@ -286,7 +376,7 @@ __device__ __forceinline__ void tile_epilogue(const AccArray<T, F16> &acc, const
 // Launch helpers of the converted-operand kernels (k_batched_async.cu).
 int prepare_async_kernel();
 int64_t async_grid(size_t smem, int64_t ntiles);
-size_t async_smem_bytes(uint32_t k, int cfg);
+size_t async_smem_bytes(uint32_t k, int cfg, bool fp8);
 int launch_convert(const uint8_t *ws, int64_t nitems, cudaStream_t stream);
 int launch_async(uint8_t *ws, int64_t grid, size_t smem, cudaStream_t stream);
 

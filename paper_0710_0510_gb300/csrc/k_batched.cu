@@ -235,12 +235,14 @@ void field_params(const Field &f, BFieldParams &F) {
     F.pf = (float)f.p;
     F.inv_pf = 1.0f / (float)f.p;
     F.chunk_k = (int32_t)std::min<int64_t>(f.k_chunk_f32, 1 << 30);
-    // GF(2^8) in the converted-operand kernel: f16 operands and accumulators.
+    // Converted-operand kernel: p <= 31 runs on fp8 e4m3 operands (exact for
+    // |centred| <= 15), the rest on bf16.  GF(2^8) also uses f16 accumulators.
     // The planes hold 0 and 1, so a chunk adds at most k per K element to an
     // accumulator (at most k plane products meet in one C_t), and after a
     // chunk reduction |x| <= 1: 1 + k chunk <= 2048 keeps every partial sum
     // an integer that f16 holds exactly, in whatever order it is added.
     F.f16 = f.p == 2 && f.k == 8;
+    F.fp8 = fp8_field(f.p);
     F.chunk_k16 = F.f16 ? (int32_t)(2047 / f.k) : F.chunk_k;
     for (uint32_t t = 0; t + 1 < f.k; ++t)
         for (uint32_t c = 0; c < f.k; ++c) F.fold[t * f.k + c] = f.fold[t * f.k + c];
@@ -300,19 +302,29 @@ Layout layout_for(int64_t count, int64_t ntiles, size_t conv_bytes = 0, int64_t 
 }
 
 int32_t round8(int32_t x) { return (x + 7) / 8 * 8; }
+int32_t round16(int32_t x) { return (x + 15) / 16 * 16; }
 
-// Bytes of product d's converted operands: k planes of m x round8(K) and of
-// K x round8(n) 16-bit elements, each operand starting on a 256-byte boundary.
-size_t conv_bytes_of(const qadic_gemm_desc &d, uint32_t k) {
-    return align_up((size_t)k * d.m * round8(d.K) * 2, 256) + align_up((size_t)k * d.K * round8(d.n) * 2, 256);
+// Bytes of product d's converted operands, each operand starting on a
+// 256-byte boundary: 16-bit planes, A m x round8(K) and B K x round8(n); fp8
+// fields (p <= 31) bytes, A m x round16(K) and B^T n x round16(K).
+size_t conv_bytes_of(const qadic_gemm_desc &d, const Field &f) {
+    const size_t k = f.k;
+    if (fp8_field(f.p))
+        return align_up(k * d.m * round16(d.K), 256) + align_up(k * d.n * round16(d.K), 256);
+    return align_up(k * d.m * round8(d.K) * 2, 256) + align_up(k * d.K * round8(d.n) * 2, 256);
 }
 
-// 8-element chunks of product d's operands (A, B) and the conversion items they make.
-uint64_t chunks_a(const qadic_gemm_desc &d, uint32_t k) { return (uint64_t)k * d.m * (round8(d.K) / 8); }
-uint64_t chunks_b(const qadic_gemm_desc &d, uint32_t k) { return (uint64_t)k * d.K * (round8(d.n) / 8); }
-int64_t conv_items_of(const qadic_gemm_desc &d, uint32_t k) {
-    return (int64_t)((chunks_a(d, k) + kConvItemChunks - 1) / kConvItemChunks +
-                     (chunks_b(d, k) + kConvItemChunks - 1) / kConvItemChunks);
+// 16-byte output chunks of product d's operands (A, B) and the conversion
+// items they make.
+uint64_t chunks_a(const qadic_gemm_desc &d, const Field &f) {
+    return fp8_field(f.p) ? (uint64_t)f.k * d.m * (round16(d.K) / 16) : (uint64_t)f.k * d.m * (round8(d.K) / 8);
+}
+uint64_t chunks_b(const qadic_gemm_desc &d, const Field &f) {
+    return fp8_field(f.p) ? (uint64_t)f.k * d.n * (round16(d.K) / 16) : (uint64_t)f.k * d.K * (round8(d.n) / 8);
+}
+int64_t conv_items_of(const qadic_gemm_desc &d, const Field &f) {
+    return (int64_t)((chunks_a(d, f) + kConvItemChunks - 1) / kConvItemChunks +
+                     (chunks_b(d, f) + kConvItemChunks - 1) / kConvItemChunks);
 }
 
 int64_t max_tiles(const qadic_gemm_desc *descs, int64_t count) {
@@ -368,8 +380,8 @@ size_t batched_workspace_size_fields(const Field *const *fields, int32_t nfields
         const qadic_gemm_desc &d = descs[i];
         if (d.field < 0 || d.field >= nfields || !fields[d.field] || d.m < 1 || d.n < 1 || d.K < 1)
             return 0;
-        conv += conv_bytes_of(d, fields[d.field]->k);
-        items += conv_items_of(d, fields[d.field]->k);
+        conv += conv_bytes_of(d, *fields[d.field]);
+        items += conv_items_of(d, *fields[d.field]);
     }
     return layout_for(count, max_tiles(descs, count), conv, items).total;
 }
@@ -406,8 +418,8 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
     size_t conv = 0;
     int64_t conv_items = 0;
     for (int64_t i = 0; i < count; ++i) {
-        conv += conv_bytes_of(descs[i], fields[descs[i].field]->k);
-        conv_items += conv_items_of(descs[i], fields[descs[i].field]->k);
+        conv += conv_bytes_of(descs[i], *fields[descs[i].field]);
+        conv_items += conv_items_of(descs[i], *fields[descs[i].field]);
     }
     // converted operands when the workspace holds them, else bytes staged through registers
     const Layout L_conv = layout_for(count, tile_bound, conv, conv_items);
@@ -421,7 +433,7 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
     size_t smem = 0;
     for (int32_t i = 0; i < nfields; ++i) {
         cfgs[i] = field_cfg(*fields[i]);
-        smem = std::max(smem, converted ? async_smem_bytes(fields[i]->k, cfgs[i])
+        smem = std::max(smem, converted ? async_smem_bytes(fields[i]->k, cfgs[i], fp8_field(fields[i]->p))
                                         : tile_smem_bytes(fields[i]->k, cfgs[i]));
     }
     int st = converted ? prepare_async_kernel() : prepare_kernel(smem);
@@ -491,7 +503,13 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
         P.field = d.field;
         P.cfg = cfgs[d.field];
         const uint32_t k = fields[d.field]->k;
-        if (converted) {
+        if (converted && fp8_field(fields[d.field]->p)) {
+            P.kp = P.np = round16(d.K);   // A [k][m][kp], B^T [k][n][kp] bytes
+            P.A16 = reinterpret_cast<const uint16_t *>((uint8_t *)workspace + conv_at);
+            conv_at += align_up((size_t)k * d.m * P.kp, 256);
+            P.B16 = reinterpret_cast<const uint16_t *>((uint8_t *)workspace + conv_at);
+            conv_at += align_up((size_t)k * d.n * P.kp, 256);
+        } else if (converted) {
             P.kp = round8(d.K);
             P.np = round8(d.n);
             P.A16 = reinterpret_cast<const uint16_t *>((uint8_t *)workspace + conv_at);
@@ -530,8 +548,8 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
         items.reserve(conv_items);
         size.reserve(conv_items);
         for (int64_t i = 0; i < count; ++i) {
-            const uint32_t k = fields[descs[i].field]->k;
-            const uint64_t n_ops[2] = {chunks_a(descs[i], k), chunks_b(descs[i], k)};
+            const Field &fi = *fields[descs[i].field];
+            const uint64_t n_ops[2] = {chunks_a(descs[i], fi), chunks_b(descs[i], fi)};
             for (int op = 0; op < 2; ++op)
                 for (uint64_t b = 0; b < n_ops[op]; b += kConvItemChunks) {
                     items.push_back(ConvItem{(uint32_t)(2 * i + op), (uint32_t)b});

@@ -56,6 +56,59 @@ __device__ __forceinline__ void load8(const uint8_t *src, int valid, uint32_t (&
     }
 }
 
+// fp8 fields: 16-byte output chunks of e4m3 bytes.  A: rows of A as they
+// are (K-major, kp bytes).  B: transposed to B^T [k][n][kp] (K-major too,
+// as the m16n8k32 B fragment wants); chunk (plane, K-block of 16, column)
+// with the column fastest, so that a warp's byte loads of one K row are
+// consecutive.
+__device__ __noinline__ void convert_fp8(const BProd &P, const BFieldParams &F, bool isB, uint32_t begin) {
+    __shared__ uint8_t tab8[256];
+    tab8[threadIdx.x] = fp8_bits(threadIdx.x, F);
+    __syncthreads();
+    const uint32_t kc = (uint32_t)P.kp / 16;   // 16-byte chunks per row of K
+    uint8_t *dst = const_cast<uint8_t *>(reinterpret_cast<const uint8_t *>(isB ? P.B16 : P.A16));
+    if (!isB) {
+        const uint32_t total = (uint32_t)F.k * (uint32_t)P.m * kc;
+        const uint32_t end = min(total, begin + kConvItemChunks);
+        const Div32 div_row = make_div32_device(kc);
+        for (uint32_t c = begin + threadIdx.x; c < end; c += kConvThreads) {
+            const uint32_t r = div32(c, div_row);            // plane * m + row
+            const int col = (int)(c - r * kc) * 16;
+            uint32_t w[4];
+            load8(P.A + (int64_t)r * P.lda + col, P.K - col, *reinterpret_cast<uint32_t(*)[2]>(&w[0]));
+            load8(P.A + (int64_t)r * P.lda + col + 8, P.K - col - 8, *reinterpret_cast<uint32_t(*)[2]>(&w[2]));
+            uint4 o;
+            uint32_t *ow = &o.x;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                ow[q] = (uint32_t)tab8[w[q] & 0xff] | ((uint32_t)tab8[(w[q] >> 8) & 0xff] << 8) |
+                        ((uint32_t)tab8[(w[q] >> 16) & 0xff] << 16) | ((uint32_t)tab8[w[q] >> 24] << 24);
+            *reinterpret_cast<uint4 *>(dst + (int64_t)r * P.kp + col) = o;
+        }
+    } else {
+        const uint32_t per_plane = kc * (uint32_t)P.n;
+        const uint32_t total = (uint32_t)F.k * per_plane;
+        const uint32_t end = min(total, begin + kConvItemChunks);
+        const Div32 div_plane = make_div32_device(per_plane), div_n = make_div32_device((uint32_t)P.n);
+        for (uint32_t c = begin + threadIdx.x; c < end; c += kConvThreads) {
+            const uint32_t plane = div32(c, div_plane);
+            const uint32_t rem = c - plane * per_plane;
+            const uint32_t kb = div32(rem, div_n);
+            const uint32_t col = rem - kb * (uint32_t)P.n;
+            const int k0 = (int)kb * 16;
+            const uint8_t *src = P.B + ((int64_t)plane * P.K + k0) * P.ldb + col;
+            uint32_t ow[4] = {0, 0, 0, 0};
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const uint32_t v = k0 + i < P.K ? tab8[__ldg(src + (int64_t)i * P.ldb)] : 0u;
+                ow[i / 4] |= v << (8 * (i % 4));
+            }
+            *reinterpret_cast<uint4 *>(dst + ((int64_t)plane * P.n + col) * P.kp + k0) =
+                make_uint4(ow[0], ow[1], ow[2], ow[3]);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kConvThreads) convert_kernel(const uint8_t *ws) {
     const BHeader *hdr = reinterpret_cast<const BHeader *>(ws);
     if (blockIdx.x >= hdr->nconv) return;
@@ -67,8 +120,12 @@ __global__ void __launch_bounds__(kConvThreads) convert_kernel(const uint8_t *ws
     const BFieldParams *fields = reinterpret_cast<const BFieldParams *>(ws + hdr->fields_off);
     const BProd &P = reinterpret_cast<const BProd *>(ws + hdr->prods_off)[prod];
     const BFieldParams &F = fields[P.field];
+    if (F.fp8) {
+        convert_fp8(P, F, isB, item.begin);
+        return;
+    }
     __shared__ uint16_t tab[256];   // byte -> centred operand bits (kConvThreads == 256)
-    tab[threadIdx.x] = F.f16 ? f16_bits(threadIdx.x, F) : bf16_bits(threadIdx.x, F);
+    tab[threadIdx.x] = bf16_bits(threadIdx.x, F);
     __syncthreads();
     const int cols = isB ? P.n : P.K;
     const int64_t rows = (int64_t)F.k * (isB ? P.K : P.m);   // all k planes, one after the other
@@ -192,6 +249,102 @@ __device__ __forceinline__ void run_tile_async(const BProd &P, const BFieldParam
     tile_epilogue<KP, T, F16>(acc, P, F, row0, col0, wm, wn, lane);
 }
 
+// fp8 operand tiles: A [KP][BM][LDA] and B^T [KP][BN][LDB] bytes, 16-byte
+// pieces, zero-filled outside the product.
+template <int KP, typename T8>
+__device__ __forceinline__ void issue_stage8(const BProd &P, uint8_t *As, uint8_t *Bs, int row0, int col0,
+                                             int k0) {
+    constexpr int PER_ROW = T8::BK / 16;
+    constexpr int A_CH = KP * T8::BM * PER_ROW;
+    constexpr int B_CH = KP * T8::BN * PER_ROW;
+    const uint8_t *A8 = reinterpret_cast<const uint8_t *>(P.A16);
+    const uint8_t *B8 = reinterpret_cast<const uint8_t *>(P.B16);
+#pragma unroll
+    for (int s = 0; s < (A_CH + B_CH + kThreads - 1) / kThreads; ++s) {
+        const int c = threadIdx.x + s * kThreads;
+        if (c < A_CH) {
+            const int part = c % PER_ROW, r = (c / PER_ROW) % T8::BM, i = c / (PER_ROW * T8::BM);
+            const int gr = row0 + r, gk = k0 + part * 16;
+            const bool ok = gr < P.m && gk < P.kp;
+            const uint8_t *src = ok ? A8 + ((int64_t)i * P.m + gr) * P.kp + gk : A8;
+            cp_async16((uint32_t)__cvta_generic_to_shared(As + (i * T8::BM + r) * T8::LDA + part * 16), src,
+                       ok ? 16u : 0u);
+        } else if (c < A_CH + B_CH) {
+            const int cb = c - A_CH;
+            const int part = cb % PER_ROW, r = (cb / PER_ROW) % T8::BN, j = cb / (PER_ROW * T8::BN);
+            const int gn = col0 + r, gk = k0 + part * 16;
+            const bool ok = gn < P.n && gk < P.kp;
+            const uint8_t *src = ok ? B8 + ((int64_t)j * P.n + gn) * P.kp + gk : B8;
+            cp_async16((uint32_t)__cvta_generic_to_shared(Bs + (j * T8::BN + r) * T8::LDB + part * 16), src,
+                       ok ? 16u : 0u);
+        }
+    }
+}
+
+template <int KP, int BM, int BN, int BK, bool F16>
+__device__ __forceinline__ void run_tile_async8(const BProd &P, const BFieldParams &F, int tm, int tn,
+                                                uint8_t *smem) {
+    using T8 = TileCfg8<KP, BM, BN, BK>;
+    using T = typename T8::W;
+    constexpr int NS = T8::NSTAGE;
+    constexpr int kStage = T8::SMEM;
+    constexpr int kABytes = KP * T8::BM * T8::LDA;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int wm = warp / 2, wn = warp % 2;
+    const int row0 = tm * T8::BM, col0 = tn * T8::BN;
+
+    AccArray<T, F16> acc;
+    acc_zero<T, F16>(acc);
+    const int nkb = (P.K + T8::BK - 1) / T8::BK;
+    const int chunk_blocks = max(1, (F16 ? F.chunk_k16 : F.chunk_k) / T8::BK);
+    __syncthreads();   // the previous tile's reads of every stage are done
+#pragma unroll
+    for (int s = 0; s < NS - 1; ++s) {
+        if (s < nkb) issue_stage8<KP, T8>(P, smem + s * kStage, smem + s * kStage + kABytes, row0, col0, s * T8::BK);
+        cp_async_commit();
+    }
+    for (int kb = 0; kb < nkb; ++kb) {
+        uint8_t *As = smem + (kb % NS) * kStage;
+        const int nxt = kb + NS - 1;
+        if (nxt < nkb) {
+            uint8_t *An = smem + (nxt % NS) * kStage;
+            issue_stage8<KP, T8>(P, An, An + kABytes, row0, col0, nxt * T8::BK);
+        }
+        cp_async_commit();
+        cp_async_wait<NS - 1>();
+        __syncthreads();
+#pragma unroll 1
+        for (int ks = 0; ks < T8::BK / 32; ++ks)
+            tile_mma_step8<KP, T8, F16>(acc, As, As + kABytes, ks, wm, wn, lane);
+        if ((kb + 1) % chunk_blocks == 0 && kb + 1 < nkb) tile_chunk_reduce<T, F16>(acc, F);
+        __syncthreads();
+    }
+    tile_epilogue<KP, T, F16>(acc, P, F, row0, col0, wm, wn, lane);
+}
+
+template <int KP, bool F16>
+__device__ __noinline__ void run_tile_async8_cfg(int cfg, const BProd &P, const BFieldParams &F, int tm,
+                                                 int tn, uint8_t *smem) {
+    constexpr bool kSmall = KP <= 2, kMid = KP > 2 && KP <= 4;
+    constexpr TileShape c0 = kSmall ? kShapesK2[0] : kMid ? kShapesK4[0] : kShapesK8[0];
+    constexpr TileShape c1 = kSmall ? kShapesK2[1] : kMid ? kShapesK4[1] : kShapesK8[1];
+    constexpr TileShape c2 = kSmall ? kShapesK2[2] : kMid ? kShapesK4[2] : kShapesK8[2];
+    constexpr TileShape c3 = kSmall ? kShapesK2[3] : kMid ? kShapesK4[3] : kShapesK8[3];
+    constexpr TileShape c4 = kSmall ? kShapesK2[4] : kMid ? kShapesK4[4] : kShapesK8[4];
+    switch (cfg) {
+        case 1: run_tile_async8<KP, c1.bm, c1.bn, c1.bk, F16>(P, F, tm, tn, smem); break;
+        case 2: run_tile_async8<KP, c2.bm, c2.bn, c2.bk, F16>(P, F, tm, tn, smem); break;
+        case 3: run_tile_async8<KP, c3.bm, c3.bn, c3.bk, F16>(P, F, tm, tn, smem); break;
+        case 4:
+            if constexpr (num_cfgs(KP) > 4) {
+                run_tile_async8<KP, c4.bm, c4.bn, c4.bk, F16>(P, F, tm, tn, smem);
+                break;
+            }
+            [[fallthrough]];
+        default: run_tile_async8<KP, c0.bm, c0.bn, c0.bk, F16>(P, F, tm, tn, smem); break;
+    }
+}
+
 // Not inlined: each (k, F16) is register-allocated on its own.
 template <int KP, bool F16>
 __device__ __noinline__ void run_tile_async_cfg(int cfg, const BProd &P, const BFieldParams &F,
@@ -233,6 +386,22 @@ __global__ void __launch_bounds__(kThreads, 5) async_kernel(uint8_t *ws) {
         const BTile tile = tiles[t];
         const BProd &P = prods[tile.prod];
         const BFieldParams &F = fields[P.field];
+        if (F.fp8) {
+            switch (F.k) {
+                case 1: run_tile_async8_cfg<1, false>(P.cfg, P, F, tile.tm, tile.tn, smem); break;
+                case 2: run_tile_async8_cfg<2, false>(P.cfg, P, F, tile.tm, tile.tn, smem); break;
+                case 3: run_tile_async8_cfg<3, false>(P.cfg, P, F, tile.tm, tile.tn, smem); break;
+                case 4: run_tile_async8_cfg<4, false>(P.cfg, P, F, tile.tm, tile.tn, smem); break;
+                case 5: run_tile_async8_cfg<5, false>(P.cfg, P, F, tile.tm, tile.tn, smem); break;
+                case 6: run_tile_async8_cfg<6, false>(P.cfg, P, F, tile.tm, tile.tn, smem); break;
+                case 7: run_tile_async8_cfg<7, false>(P.cfg, P, F, tile.tm, tile.tn, smem); break;
+                default:
+                    if (F.f16) run_tile_async8_cfg<8, true>(P.cfg, P, F, tile.tm, tile.tn, smem);
+                    else run_tile_async8_cfg<8, false>(P.cfg, P, F, tile.tm, tile.tn, smem);
+                    break;
+            }
+            continue;
+        }
         switch (F.k) {
             case 1: run_tile_async_cfg<1, false>(P.cfg, P, F, tile.tm, tile.tn, smem); break;
             case 2: run_tile_async_cfg<2, false>(P.cfg, P, F, tile.tm, tile.tn, smem); break;
@@ -241,18 +410,15 @@ __global__ void __launch_bounds__(kThreads, 5) async_kernel(uint8_t *ws) {
             case 5: run_tile_async_cfg<5, false>(P.cfg, P, F, tile.tm, tile.tn, smem); break;
             case 6: run_tile_async_cfg<6, false>(P.cfg, P, F, tile.tm, tile.tn, smem); break;
             case 7: run_tile_async_cfg<7, false>(P.cfg, P, F, tile.tm, tile.tn, smem); break;
-            default:
-                if (F.f16) run_tile_async_cfg<8, true>(P.cfg, P, F, tile.tm, tile.tn, smem);
-                else run_tile_async_cfg<8, false>(P.cfg, P, F, tile.tm, tile.tn, smem);
-                break;
+            default: run_tile_async_cfg<8, false>(P.cfg, P, F, tile.tm, tile.tn, smem); break;
         }
     }
 }
 
 }  // namespace
 
-size_t async_smem_bytes(uint32_t k, int cfg) {
-    const size_t stage = tile_smem_bytes(k, cfg);
+size_t async_smem_bytes(uint32_t k, int cfg, bool fp8) {
+    const size_t stage = fp8 ? tile_smem_bytes8(k, cfg) : tile_smem_bytes(k, cfg);
     return async_stages(stage) * stage;
 }
 
@@ -262,7 +428,8 @@ int prepare_async_kernel() {
     std::call_once(once, [] {
         size_t most = 0;
         for (uint32_t k = 1; k <= kMaxK; ++k)
-            for (int c = 0; c < num_cfgs(k); ++c) most = std::max(most, async_smem_bytes(k, c));
+            for (int c = 0; c < num_cfgs(k); ++c)
+                most = std::max(most, std::max(async_smem_bytes(k, c, false), async_smem_bytes(k, c, true)));
         err = cudaFuncSetAttribute(async_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
     });
     if (err != cudaSuccess)

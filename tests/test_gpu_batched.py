@@ -97,13 +97,19 @@ def test_batched_paths_agree_and_sizes(torch, orc):
     small = q.batched_workspace_size(a.descs)
     big = q.batched_workspace_size(a.descs, fields)
     r8 = lambda x: (x + 7) // 8 * 8
-    conv = sum(fields[f].k * (m * r8(K) + K * r8(n)) * 2 for (m, n, K), f in zip(shapes, fi))
-    assert big >= small + conv
-    # + 256-byte alignment of each operand, + the conversion items (8 bytes for
-    # every 4096 chunks of 8 elements of an operand)
+    r16 = lambda x: (x + 15) // 16 * 16
     cdiv = lambda a, b: -(-a // b)
-    items = sum(cdiv(fields[f].k * m * (r8(K) // 8), 4096) + cdiv(fields[f].k * K * (r8(n) // 8), 4096)
-                for (m, n, K), f in zip(shapes, fi))
+    conv = items = 0
+    for (m, n, K), f in zip(shapes, fi):
+        k = fields[f].k
+        if fields[f].p <= 31:   # fp8 bytes: A m x r16(K), B^T n x r16(K); 16-byte chunks
+            conv += k * (m + n) * r16(K)
+            items += cdiv(k * m * (r16(K) // 16), 4096) + cdiv(k * n * (r16(K) // 16), 4096)
+        else:                   # bf16: A m x r8(K), B K x r8(n); 8-element chunks
+            conv += 2 * k * (m * r8(K) + K * r8(n))
+            items += cdiv(k * m * (r8(K) // 8), 4096) + cdiv(k * K * (r8(n) // 8), 4096)
+    assert big >= small + conv
+    # + 256-byte alignment of each operand, + the conversion items (8 bytes each)
     assert big <= small + conv + 2 * 256 * len(shapes) + 8 * items + 512
 
 
