@@ -29,6 +29,7 @@ struct BFieldParams {
     int32_t f16;                   // GF(2^8): f16 accumulators (see the converted-operand kernel)
     int32_t fp8;                   // p <= 31: operands converted to fp8 e4m3 (|centred| <= 15, exact)
     uint8_t fold[kMaxK * kMaxK];   // X^(k+t) mod P, row t (k coefficients)
+    uint8_t fold2[kMaxK];          // p = 2: row t of `fold` as a bit mask (coefficient i at bit i)
 };
 
 struct BProd {
@@ -332,10 +333,49 @@ __device__ __forceinline__ void tile_chunk_reduce(AccArray<T, F16> &acc, const B
 // Epilogue: each C_t exactly mod p, then the fold mod P (Alg. 4, fold step,
 // in coefficient form: out_i = mu_i + sum_{t >= k} mu_t (X^t mod P)_i), and
 // the k output planes written as bytes.
+// Value of accumulator element e of fragment (t, mt, nt).
+template <typename T, bool F16>
+__device__ __forceinline__ float acc_value(const AccArray<T, F16> &acc, int t, int mt, int nt, int e) {
+    if constexpr (F16) {
+        const __half2 h = *reinterpret_cast<const __half2 *>(&acc[t][mt][nt][e >> 1]);
+        return (e & 1) ? __high2float(h) : __low2float(h);
+    } else {
+        return acc[t][mt][nt][e];
+    }
+}
+
 template <int KP, typename T, bool F16>
 __device__ __forceinline__ void tile_epilogue(const AccArray<T, F16> &acc, const BProd &P,
                                               const BFieldParams &F, int row0, int col0, int wm,
                                               int wn, int lane) {
+    if (F.p == 2) {
+        // GF(2^k): the 2k-1 plane sums mod 2 as the bits of one word (the low
+        // bit of x + 1.5 * 2^23 is the parity of an integer-valued float of
+        // magnitude < 2^22), the fold mod P as XORs of the rows X^t mod P, and
+        // output plane i as bit i.
+#pragma unroll
+        for (int mt = 0; mt < T::MT; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < T::NT; ++nt)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int row = row0 + wm * T::WM + mt * 16 + (lane / 4) + (e >= 2 ? 8 : 0);
+                    const int col = col0 + wn * T::WN + nt * 8 + 2 * (lane % 4) + (e & 1);
+                    uint32_t bits = 0;
+#pragma unroll
+                    for (int t = 0; t < T::NACC; ++t)
+                        bits |= (__float_as_uint(acc_value<T, F16>(acc, t, mt, nt, e) + 12582912.0f) & 1u) << t;
+                    uint32_t out = bits & ((1u << KP) - 1u);
+#pragma unroll
+                    for (int t = 0; t < T::NACC - KP; ++t) out ^= (0u - ((bits >> (KP + t)) & 1u)) & F.fold2[t];
+                    if (row < P.m && col < P.n) {
+#pragma unroll
+                        for (int i = 0; i < KP; ++i)
+                            P.C[((int64_t)i * P.m + row) * P.ldc + col] = (uint8_t)((out >> i) & 1u);
+                    }
+                }
+        return;
+    }
 #pragma unroll
     for (int mt = 0; mt < T::MT; ++mt)
 #pragma unroll

@@ -244,8 +244,13 @@ void field_params(const Field &f, BFieldParams &F) {
     F.f16 = f.p == 2 && f.k == 8;
     F.fp8 = fp8_field(f.p);
     F.chunk_k16 = F.f16 ? (int32_t)(2047 / f.k) : F.chunk_k;
-    for (uint32_t t = 0; t + 1 < f.k; ++t)
-        for (uint32_t c = 0; c < f.k; ++c) F.fold[t * f.k + c] = f.fold[t * f.k + c];
+    for (uint32_t t = 0; t + 1 < f.k; ++t) {
+        F.fold2[t] = 0;
+        for (uint32_t c = 0; c < f.k; ++c) {
+            F.fold[t * f.k + c] = f.fold[t * f.k + c];
+            F.fold2[t] |= (uint8_t)((f.fold[t * f.k + c] & 1u) << c);
+        }
+    }
 }
 
 int field_cfg(const Field &f) {
