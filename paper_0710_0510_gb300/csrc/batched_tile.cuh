@@ -353,25 +353,41 @@ __device__ __forceinline__ void tile_epilogue(const AccArray<T, F16> &acc, const
         // bit of x + 1.5 * 2^23 is the parity of an integer-valued float of
         // magnitude < 2^22), the fold mod P as XORs of the rows X^t mod P, and
         // output plane i as bit i.
+        // The two adjacent columns of a fragment row go together: their
+        // parities at bits 0.. and 16.. of one word, folded by the same XORs.
+        constexpr uint32_t kLow = (1u << KP) - 1u;
 #pragma unroll
         for (int mt = 0; mt < T::MT; ++mt)
 #pragma unroll
             for (int nt = 0; nt < T::NT; ++nt)
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int row = row0 + wm * T::WM + mt * 16 + (lane / 4) + (e >= 2 ? 8 : 0);
-                    const int col = col0 + wn * T::WN + nt * 8 + 2 * (lane % 4) + (e & 1);
+                for (int eh = 0; eh < 2; ++eh) {
+                    const int row = row0 + wm * T::WM + mt * 16 + (lane / 4) + 8 * eh;
+                    const int col = col0 + wn * T::WN + nt * 8 + 2 * (lane % 4);   // and col + 1
                     uint32_t bits = 0;
 #pragma unroll
-                    for (int t = 0; t < T::NACC; ++t)
-                        bits |= (__float_as_uint(acc_value<T, F16>(acc, t, mt, nt, e) + 12582912.0f) & 1u) << t;
-                    uint32_t out = bits & ((1u << KP) - 1u);
+                    for (int t = 0; t < T::NACC; ++t) {
+                        const uint32_t b0 = __float_as_uint(acc_value<T, F16>(acc, t, mt, nt, 2 * eh) + 12582912.0f);
+                        const uint32_t b1 = __float_as_uint(acc_value<T, F16>(acc, t, mt, nt, 2 * eh + 1) + 12582912.0f);
+                        bits |= ((b0 & 1u) | ((b1 & 1u) << 16)) << t;
+                    }
+                    uint32_t out = bits & (kLow | (kLow << 16));
 #pragma unroll
-                    for (int t = 0; t < T::NACC - KP; ++t) out ^= (0u - ((bits >> (KP + t)) & 1u)) & F.fold2[t];
+                    for (int t = 0; t < T::NACC - KP; ++t)
+                        out ^= ((bits >> (KP + t)) & 0x00010001u) * F.fold2[t];   // row t at both halves
                     if (row < P.m && col < P.n) {
+                        const bool pair = col + 1 < P.n;
 #pragma unroll
-                        for (int i = 0; i < KP; ++i)
-                            P.C[((int64_t)i * P.m + row) * P.ldc + col] = (uint8_t)((out >> i) & 1u);
+                        for (int i = 0; i < KP; ++i) {
+                            uint8_t *dst = P.C + ((int64_t)i * P.m + row) * P.ldc + col;
+                            const uint32_t lo = (out >> i) & 1u, hi = (out >> (16 + i)) & 1u;
+                            if (pair && (((uintptr_t)dst & 1) == 0)) {
+                                *reinterpret_cast<uint16_t *>(dst) = (uint16_t)(lo | (hi << 8));
+                            } else {
+                                dst[0] = (uint8_t)lo;
+                                if (pair) dst[1] = (uint8_t)hi;
+                            }
+                        }
                     }
                 }
         return;
