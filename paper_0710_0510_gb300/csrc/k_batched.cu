@@ -530,10 +530,26 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
                 cost.push_back(c);
             }
     }
+    // Tiles field by field (the field with the most work first), decreasing
+    // cost within a field: all SMs then run one field's code at a time
+    // (tiles of different fields interleaved kept the instruction cache
+    // missing), and the cheapest tiles of the smallest field fill the end.
+    std::vector<double> field_work(nfields, 0.0);
+    for (size_t i = 0; i < tiles.size(); ++i) field_work[pp[tiles[i].prod].field] += (double)cost[i];
+    std::vector<int> field_rank(nfields);
+    {
+        std::vector<int> fo(nfields);
+        for (int32_t i = 0; i < nfields; ++i) fo[i] = i;
+        std::stable_sort(fo.begin(), fo.end(), [&](int a, int b) { return field_work[a] > field_work[b]; });
+        for (int32_t r = 0; r < nfields; ++r) field_rank[fo[r]] = r;
+    }
     std::vector<int64_t> order(tiles.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = (int64_t)i;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int64_t a, int64_t b) { return cost[a] > cost[b]; });
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+        const int fa = field_rank[pp[tiles[a].prod].field], fb = field_rank[pp[tiles[b].prod].field];
+        if (fa != fb) return fa < fb;
+        return cost[a] > cost[b];
+    });
     BTile *tp = reinterpret_cast<BTile *>(host.data() + L.tiles_off);
     for (size_t i = 0; i < order.size(); ++i) tp[i] = tiles[order[i]];
     BHeader *hdr = reinterpret_cast<BHeader *>(host.data());
