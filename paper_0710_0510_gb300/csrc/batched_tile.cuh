@@ -157,10 +157,6 @@ __device__ __forceinline__ uint16_t bf16_bits(uint32_t c, const BFieldParams &F)
     return __bfloat16_as_ushort(__int2bfloat16_rn(centred_int(c, F)));
 }
 
-__device__ __forceinline__ uint16_t f16_bits(uint32_t c, const BFieldParams &F) {
-    return __half_as_ushort(__int2half_rn(centred_int(c, F)));
-}
-
 // e4m3 holds every integer of magnitude <= 16 exactly, so the centred
 // coefficients of any p <= 31 (and the 0/1 of p = 2) convert without loss.
 __device__ __forceinline__ uint8_t fp8_bits(uint32_t c, const BFieldParams &F) {

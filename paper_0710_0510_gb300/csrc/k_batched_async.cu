@@ -2,27 +2,28 @@
 // qadic_batched_gemm takes when its workspace has room for the converted
 // operands (qadic_batched_workspace_size_fields).
 //
-// Launch 1 (convert_kernel, one block per piece of at most 4096 x 8 elements
-// of a product operand, largest first): the uint8
-// coefficient planes become centred 16-bit operands (bf16; f16 for GF(2^8),
-// see below) in the workspace, rows padded with zeros to a multiple of 8
-// elements so that every 16-byte piece of a row is aligned.  Each element is
-// converted once, where staging bytes through registers converts an A tile
-// again for every column tile of its product and a B tile for every row tile.
+// Launch 1 (convert_kernel, one block per piece of at most 4096 chunks of a
+// product operand, largest first): the uint8 coefficient planes become
+// centred operands in the workspace, each element converted once (staging
+// bytes through registers converts an A tile again for every column tile of
+// its product and a B tile for every row tile).  Fields with p <= 31 get fp8
+// e4m3 (exact for |c| <= 15): A as K-major rows padded to 16 bytes, B
+// transposed to n x K (the m16n8k32 B fragment wants K-contiguous columns).
+// Larger p get bf16: A K-major, B as it is, rows padded to 8 elements.
 //
 // Launch 2 (async_kernel, persistent, tiles pulled with one atomicAdd each):
 // operand tiles go from the converted planes to shared memory with
 // cp.async (16 bytes each, zero-filled past the edges) through 2-4 stages
 // (more for the smaller tiles), so that the copies of the next K-blocks run
-// under the MMAs of this one; the
-// products, exact-chunk reductions and the epilogue are those of the
-// register-staged kernel (batched_tile.cuh).
+// under the MMAs of this one; fp8 tiles take m16n8k32 e4m3 MMAs, bf16 tiles
+// m16n8k16, and the exact-chunk reductions and the epilogue are those of
+// the register-staged kernel (batched_tile.cuh).
 //
-// GF(2^8) (p = 2, k = 8) runs on f16 operands and f16 accumulators: its planes
-// hold 0 and 1, a K element adds at most k = 8 to an accumulator, and a chunk
-// of at most 2047 / k elements (after which every accumulator is reduced to
-// |x| <= 1) keeps each partial sum an integer of magnitude <= 2048, exact in
-// f16 in any order of addition.  Half the accumulator registers of FP32.
+// GF(2^8) (p = 2, k = 8) accumulates in f16: its planes hold 0 and 1, a K
+// element adds at most k = 8 to an accumulator, and a chunk of at most
+// 2047 / k elements (after which every accumulator is reduced to |x| <= 1)
+// keeps each partial sum an integer of magnitude <= 2048, exact in f16 in
+// any order of addition.  Half the accumulator registers of FP32.
 #include "batched_tile.cuh"
 
 namespace qadic {
