@@ -47,3 +47,24 @@ def test_single_process_has_no_group():
     os.environ.pop("WORLD_SIZE", None)
     assert bench.dist_setup() == (0, 1, None)
     assert bench.reduce_max(3.5, None) == 3.5
+
+
+def test_clock_regime_picks_the_peak_and_scales_fp8():
+    import bench
+    pk = {"hbm_gbs": 6800.0, "bf16": 2000.0, "bf16_sustained": 1600.0, "source": "measured"}
+    obj = {"plane": {"roofline": {"bound": "tensor", "unit": "TFLOP/s", "achieved": 1000.0}},
+           "extras": {"b": {"roofline": {"bound": "tensor", "unit": "TFLOP/s",
+                                         "achieved": 400.0, "peak_scale": 2.0}}},
+           "redq": {"roofline": {"bound": "hbm", "unit": "GB/s", "achieved": 6000.0,
+                                 "peak": 6800.0}}}
+    bench.apply_clock_regime(obj, {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []}, pk)
+    assert obj["plane"]["roofline"]["peak"] == 2000.0
+    assert obj["plane"]["roofline"]["frac"] == 0.5
+    assert obj["extras"]["b"]["roofline"]["peak"] == 4000.0
+    assert obj["extras"]["b"]["roofline"]["frac"] == 0.1
+    assert obj["redq"]["roofline"]["peak"] == 6800.0 and "frac_of_burst" not in obj["redq"]["roofline"]
+    # power-capped (or below the maximum clock): the sustained figure
+    bench.apply_clock_regime(obj, {"sm_mhz": 1800.0, "sm_max_mhz": 2070.0,
+                                   "reasons": ["sw_power_cap"]}, pk)
+    assert obj["plane"]["roofline"]["peak"] == 1600.0
+    assert obj["extras"]["b"]["roofline"]["frac_of_sustained"] == 400.0 / 3200.0
