@@ -425,8 +425,11 @@ def bench_redq(args, torch, q, W, count=None, steps=10):
             "roofline": {"bound": "hbm", "achieved": pgbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
                          "frac": pgbs / pk["hbm_gbs"], "traffic": None}}
         if not int_floor:
-            # the Lemma 1 form is bound by the FP64 pipe: 4 round-up multiplies a word
-            pq["lemma1"]["fp64_pipe"] = fp64_pipe(4.0 * count, pms)
+            # the Lemma 1 form takes one round-up multiply a word (the floor
+            # by q^2 = 1,382,976 < 2^32; the floors below 2^32 are 32-bit
+            # integer ones): far from the FP64 pipe's limit, which the
+            # chain of four multiplies a word reached
+            pq["lemma1"]["fp64_pipe"] = fp64_pipe(1.0 * count, pms)
     del dq
     return None, out, {"value": 5.0 * count / (ms * 1e-3), "unit": "residues/s", "best": key,
                        "ms": ms, "words": count,

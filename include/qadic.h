@@ -248,7 +248,10 @@ int qadic_redq(uint32_t p, uint32_t log2_q, uint32_t ndigits, const double *in, 
  * table.  The divisions by q^j (no longer shifts) are taken as a chain
  * t_{j+1} = floor(t_j / q) (Lemma 2), each a Lemma 1 floor by 1/q rounded
  * upward, or with QADIC_REDQ_INT_FLOOR an integer multiply-high; then
- * u_j = t_j mod p = (t_j - q t_{j+1}) mod p since p | q.
+ * u_j = t_j mod p = (t_j - q t_{j+1}) mod p since p | q.  Where q^s < 2^32
+ * for the first s with q^(ndigits-s) <= 2^32, the chain starts with one such
+ * floor by q^s, and the floors of r mod q^s and of t_s below 2^32 are 32-bit
+ * integer ones (exact, so the flag then only picks the floor by q^s).
  * in[i] = sum_{j<=d} mu~_j q^j with 0 <= mu~_j < q, d = ndigits-1, an exact
  * integer held in a double; out[i] = rho = sum_j (mu~_j mod p) q^j (exact).
  * Requires p prime <= 251, q >= p with p | q, q^ndigits <= 2^51 (else

@@ -61,7 +61,11 @@ __device__ __forceinline__ void load8(const uint8_t *src, int valid, uint32_t (&
 // are (K-major, kp bytes).  B: transposed to B^T [k][n][kp] (K-major too,
 // as the m16n8k32 B fragment wants); chunk (plane, K-block of 16, column)
 // with the column fastest, so that a warp's byte loads of one K row are
-// consecutive.
+// consecutive.  Each thread takes kUnroll8 chunks per round and issues all
+// their loads before it converts any: the launch is bound by the latency
+// of those loads, so the bytes in flight per thread set its speed.
+constexpr int kUnroll8 = 2;
+
 __device__ __noinline__ void convert_fp8(const BProd &P, const BFieldParams &F, bool isB, uint32_t begin) {
     __shared__ uint8_t tab8[256];
     tab8[threadIdx.x] = fp8_bits(threadIdx.x, F);
@@ -72,40 +76,73 @@ __device__ __noinline__ void convert_fp8(const BProd &P, const BFieldParams &F, 
         const uint32_t total = (uint32_t)F.k * (uint32_t)P.m * kc;
         const uint32_t end = min(total, begin + kConvItemChunks);
         const Div32 div_row = make_div32_device(kc);
-        for (uint32_t c = begin + threadIdx.x; c < end; c += kConvThreads) {
-            const uint32_t r = div32(c, div_row);            // plane * m + row
-            const int col = (int)(c - r * kc) * 16;
-            uint32_t w[4];
-            load8(P.A + (int64_t)r * P.lda + col, P.K - col, *reinterpret_cast<uint32_t(*)[2]>(&w[0]));
-            load8(P.A + (int64_t)r * P.lda + col + 8, P.K - col - 8, *reinterpret_cast<uint32_t(*)[2]>(&w[2]));
-            uint4 o;
-            uint32_t *ow = &o.x;
+        for (uint32_t c0 = begin + threadIdx.x; c0 < end; c0 += kConvThreads * kUnroll8) {
+            uint32_t w[kUnroll8][4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                ow[q] = (uint32_t)tab8[w[q] & 0xff] | ((uint32_t)tab8[(w[q] >> 8) & 0xff] << 8) |
-                        ((uint32_t)tab8[(w[q] >> 16) & 0xff] << 16) | ((uint32_t)tab8[w[q] >> 24] << 24);
-            *reinterpret_cast<uint4 *>(dst + (int64_t)r * P.kp + col) = o;
+            for (int u = 0; u < kUnroll8; ++u) {
+                const uint32_t c = c0 + u * kConvThreads;
+                const uint32_t r = div32(c, div_row);            // plane * m + row
+                const int col = (int)(c - r * kc) * 16;
+                // past the last chunk: no loads (valid <= 0), zeros
+                const int valid = c < end ? P.K - col : 0;
+                load8(P.A + (int64_t)r * P.lda + col, valid, *reinterpret_cast<uint32_t(*)[2]>(&w[u][0]));
+                load8(P.A + (int64_t)r * P.lda + col + 8, valid - 8, *reinterpret_cast<uint32_t(*)[2]>(&w[u][2]));
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll8; ++u) {
+                const uint32_t c = c0 + u * kConvThreads;
+                if (c >= end) break;
+                const uint32_t r = div32(c, div_row);
+                const int col = (int)(c - r * kc) * 16;
+                uint4 o;
+                uint32_t *ow = &o.x;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    ow[q] = (uint32_t)tab8[w[u][q] & 0xff] | ((uint32_t)tab8[(w[u][q] >> 8) & 0xff] << 8) |
+                            ((uint32_t)tab8[(w[u][q] >> 16) & 0xff] << 16) | ((uint32_t)tab8[w[u][q] >> 24] << 24);
+                *reinterpret_cast<uint4 *>(dst + (int64_t)r * P.kp + col) = o;
+            }
         }
     } else {
         const uint32_t per_plane = kc * (uint32_t)P.n;
         const uint32_t total = (uint32_t)F.k * per_plane;
         const uint32_t end = min(total, begin + kConvItemChunks);
         const Div32 div_plane = make_div32_device(per_plane), div_n = make_div32_device((uint32_t)P.n);
-        for (uint32_t c = begin + threadIdx.x; c < end; c += kConvThreads) {
-            const uint32_t plane = div32(c, div_plane);
-            const uint32_t rem = c - plane * per_plane;
-            const uint32_t kb = div32(rem, div_n);
-            const uint32_t col = rem - kb * (uint32_t)P.n;
-            const int k0 = (int)kb * 16;
-            const uint8_t *src = P.B + ((int64_t)plane * P.K + k0) * P.ldb + col;
-            uint32_t ow[4] = {0, 0, 0, 0};
+        for (uint32_t c0 = begin + threadIdx.x; c0 < end; c0 += kConvThreads * kUnroll8) {
+            uint32_t raw[kUnroll8][16];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const uint32_t v = k0 + i < P.K ? tab8[__ldg(src + (int64_t)i * P.ldb)] : 0u;
-                ow[i / 4] |= v << (8 * (i % 4));
+            for (int u = 0; u < kUnroll8; ++u) {
+                const uint32_t c = c0 + u * kConvThreads;
+                const uint32_t plane = div32(c, div_plane);
+                const uint32_t rem = c - plane * per_plane;
+                const uint32_t kb = div32(rem, div_n);
+                const uint32_t col = rem - kb * (uint32_t)P.n;
+                const int k0 = (int)kb * 16;
+                // rows past K, and every row of a chunk past the last: not read
+                const int rows = c < end ? min(16, P.K - k0) : 0;
+                const uint8_t *src = P.B + ((int64_t)plane * P.K + k0) * P.ldb + col;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) raw[u][i] = i < rows ? __ldg(src + (int64_t)i * P.ldb) : 0u;
             }
-            *reinterpret_cast<uint4 *>(dst + ((int64_t)plane * P.n + col) * P.kp + k0) =
-                make_uint4(ow[0], ow[1], ow[2], ow[3]);
+#pragma unroll
+            for (int u = 0; u < kUnroll8; ++u) {
+                const uint32_t c = c0 + u * kConvThreads;
+                if (c >= end) break;
+                const uint32_t plane = div32(c, div_plane);
+                const uint32_t rem = c - plane * per_plane;
+                const uint32_t kb = div32(rem, div_n);
+                const uint32_t col = rem - kb * (uint32_t)P.n;
+                const int k0 = (int)kb * 16;
+                const int rows = min(16, P.K - k0);
+                uint32_t ow[4] = {0, 0, 0, 0};
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const uint32_t v = i < rows ? (uint32_t)tab8[raw[u][i]] : 0u;
+                    ow[i / 4] |= v << (8 * (i % 4));
+                }
+                *reinterpret_cast<uint4 *>(dst + ((int64_t)plane * P.n + col) * P.kp + k0) =
+                    make_uint4(ow[0], ow[1], ow[2], ow[3]);
+            }
         }
     }
 }

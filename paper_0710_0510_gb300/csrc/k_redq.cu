@@ -238,6 +238,10 @@ struct RedqPqParams {
     double inv_q_up;                   // 1/q rounded toward +infinity
     Div64 div_q, div_p;
     Div32 div_q32;                     // floor(t / q) for t < 2^32 (q < 2^32)
+    uint32_t split;                    // 1 <= j32 < d + 1 and q^j32 < 2^32 (see redq_pq_word_split)
+    uint32_t qs;                       // q^j32 when split
+    Div64 div_qs;                      // floor(r / q^j32)
+    double inv_qs_up;                  // 1/q^j32 rounded toward +infinity
     uint64_t qpow[kMaxPqDigits];       // q^j
 };
 
@@ -277,6 +281,42 @@ __device__ __forceinline__ double redq_pq_word(double x, const RedqPqParams &P) 
 // ND = d + 1 digits known at compile time: the chain unrolls, the integer
 // floors drop to 32 bits once t_j < 2^32 (j >= j32), and rho is assembled
 // by Horner's rule from the top digit.
+// When q^S < 2^32 for S = j32: one floor by q^S (64-bit integer, or
+// Lemma 1 on the binary64 word) splits the word into t_S = floor(r / q^S)
+// < 2^32 and r mod q^S < 2^32 (Lemma 2: the floors of t_S by q continue the
+// chain), so every other floor is an exact 32-bit integer one and the two
+// chains are independent, and rho = (Horner of the high digits) q^S +
+// (Horner of the low digits), both sums below 2^32.
+template <bool INT_FLOOR, int ND, int S>
+__device__ __forceinline__ double redq_pq_word_split(double x, const RedqPqParams &P) {
+    static_assert(S >= 1 && S < ND, "split point");
+    const uint64_t t = f64_to_u64_exact(x);
+    const uint64_t ts = INT_FLOOR ? div64(t, P.div_qs) : f64_to_u64_exact(__dmul_ru(x, P.inv_qs_up));
+    uint32_t lo = (uint32_t)(t - (uint64_t)P.qs * ts), hi = (uint32_t)ts;
+    const uint32_t q = (uint32_t)P.q;
+    uint32_t u[ND];
+#pragma unroll
+    for (int j = 0; j < S - 1; ++j) {
+        const uint32_t tn = div32(lo, P.div_q32);
+        u[j] = mod_p_digit(lo - q * tn, P);
+        lo = tn;
+    }
+    u[S - 1] = mod_p_digit(lo, P);   // lo < q now
+#pragma unroll
+    for (int j = S; j < ND - 1; ++j) {
+        const uint32_t tn = div32(hi, P.div_q32);
+        u[j] = mod_p_digit(hi - q * tn, P);
+        hi = tn;
+    }
+    u[ND - 1] = mod_p_digit(hi, P);  // t_d < q
+    uint32_t rh = u[ND - 1], rl = u[S - 1];
+#pragma unroll
+    for (int j = ND - 2; j >= S; --j) rh = rh * q + u[j];
+#pragma unroll
+    for (int j = S - 2; j >= 0; --j) rl = rl * q + u[j];
+    return u64_to_f64_exact((uint64_t)rh * P.qs + rl);
+}
+
 template <bool INT_FLOOR, int ND>
 __device__ __forceinline__ double redq_pq_word_nd(double x, const RedqPqParams &P) {
     uint64_t t = f64_to_u64_exact(x);
@@ -308,7 +348,8 @@ __device__ __forceinline__ double redq_pq_word_nd(double x, const RedqPqParams &
     return u64_to_f64_exact(rho);
 }
 
-template <bool INT_FLOOR, int ND>
+// S > 0: the integer floors split at q^S (redq_pq_word_split).
+template <bool INT_FLOOR, int ND, int S = 0>
 __global__ void __launch_bounds__(kThreads)
 redq_pq_kernel(const double *__restrict__ in, double *__restrict__ out, int64_t count,
                const __grid_constant__ RedqPqParams P) {
@@ -317,7 +358,8 @@ redq_pq_kernel(const double *__restrict__ in, double *__restrict__ out, int64_t 
     double2 *out2 = reinterpret_cast<double2 *>(out);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     auto word = [&](double v) {
-        if constexpr (ND > 0) return redq_pq_word_nd<INT_FLOOR, ND>(v, P);
+        if constexpr (S > 0) return redq_pq_word_split<INT_FLOOR, ND, S>(v, P);
+        else if constexpr (ND > 0) return redq_pq_word_nd<INT_FLOOR, ND>(v, P);
         else return redq_pq_word<INT_FLOOR>(v, P);
     };
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < npairs;
@@ -468,6 +510,33 @@ int launch_redq_pq(uint32_t p, uint64_t q, uint32_t ndigits, const double *in, d
         if (bound <= ((unsigned __int128)1 << 32)) {
             P.j32 = j;
             break;
+        }
+    }
+    if (P.j32 >= 1 && P.j32 < ndigits && P.qpow[P.j32] < ((uint64_t)1 << 32)) {
+        P.split = 1;
+        P.qs = (uint32_t)P.qpow[P.j32];
+        P.div_qs = make_div64(P.qpow[P.j32]);
+        P.inv_qs_up = inv_up(P.qpow[P.j32]);
+    }
+    if (P.split) {
+        switch ((int_floor ? 256 : 0) + ndigits * 16 + P.j32) {
+#define QADIC_PQ_SPLIT(N, S)                                                                    \
+    case 256 + N * 16 + S:                                                                      \
+        return launch_stream(redq_pq_kernel<true, N, S>, in, out, count, P, 0, stream, "redq_pq"); \
+    case N * 16 + S:                                                                            \
+        return launch_stream(redq_pq_kernel<false, N, S>, in, out, count, P, 0, stream, "redq_pq");
+            QADIC_PQ_SPLIT(2, 1)
+            QADIC_PQ_SPLIT(3, 1) QADIC_PQ_SPLIT(3, 2)
+            QADIC_PQ_SPLIT(4, 1) QADIC_PQ_SPLIT(4, 2) QADIC_PQ_SPLIT(4, 3)
+            QADIC_PQ_SPLIT(5, 1) QADIC_PQ_SPLIT(5, 2) QADIC_PQ_SPLIT(5, 3) QADIC_PQ_SPLIT(5, 4)
+            QADIC_PQ_SPLIT(6, 1) QADIC_PQ_SPLIT(6, 2) QADIC_PQ_SPLIT(6, 3) QADIC_PQ_SPLIT(6, 4)
+            QADIC_PQ_SPLIT(6, 5)
+            QADIC_PQ_SPLIT(7, 1) QADIC_PQ_SPLIT(7, 2) QADIC_PQ_SPLIT(7, 3) QADIC_PQ_SPLIT(7, 4)
+            QADIC_PQ_SPLIT(7, 5) QADIC_PQ_SPLIT(7, 6)
+            QADIC_PQ_SPLIT(8, 1) QADIC_PQ_SPLIT(8, 2) QADIC_PQ_SPLIT(8, 3) QADIC_PQ_SPLIT(8, 4)
+            QADIC_PQ_SPLIT(8, 5) QADIC_PQ_SPLIT(8, 6) QADIC_PQ_SPLIT(8, 7)
+#undef QADIC_PQ_SPLIT
+            default: break;   // more digits: the chain below
         }
     }
     switch (int_floor ? ndigits : ndigits + 100) {

@@ -136,7 +136,8 @@ def test_redq_adversarial_words(torch, orc):
                                      (251, 251, 6), (2, 1024, 5), (3, 3 * 2 ** 14, 3),
                                      (101, 101 * 64, 3), (13, 13, 1), (7, 7 * 2 ** 20, 2),
                                      (3, 3 * 2 ** 9, 4), (2, 128, 7), (5, 80, 8),
-                                     (251, 251 * 2 ** 17, 2), (13, 13 * 2 ** 30, 1)])
+                                     (251, 251 * 2 ** 17, 2), (13, 13 * 2 ** 30, 1),
+                                     (2, 2 ** 16, 3), (3, 3 * 2 ** 15, 3)])
 def test_redq_pq_parameters(torch, orc, p, q_, nd):
     w = W.redq_words_q(30001, nd, q_, salt=p)   # odd count: ragged tail
     want = orc.redq(p, q_, nd - 1, w)
