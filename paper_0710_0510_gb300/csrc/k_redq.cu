@@ -278,9 +278,6 @@ __device__ __forceinline__ double redq_pq_word(double x, const RedqPqParams &P) 
     return u64_to_f64_exact(rho);
 }
 
-// ND = d + 1 digits known at compile time: the chain unrolls, the integer
-// floors drop to 32 bits once t_j < 2^32 (j >= j32), and rho is assembled
-// by Horner's rule from the top digit.
 // When q^S < 2^32 for S = j32: one floor by q^S (64-bit integer, or
 // Lemma 1 on the binary64 word) splits the word into t_S = floor(r / q^S)
 // < 2^32 and r mod q^S < 2^32 (Lemma 2: the floors of t_S by q continue the
@@ -317,6 +314,9 @@ __device__ __forceinline__ double redq_pq_word_split(double x, const RedqPqParam
     return u64_to_f64_exact((uint64_t)rh * P.qs + rl);
 }
 
+// ND = d + 1 digits known at compile time: the chain unrolls, the integer
+// floors drop to 32 bits once t_j < 2^32 (j >= j32), and rho is assembled
+// by Horner's rule from the top digit.
 template <bool INT_FLOOR, int ND>
 __device__ __forceinline__ double redq_pq_word_nd(double x, const RedqPqParams &P) {
     uint64_t t = f64_to_u64_exact(x);
@@ -348,7 +348,7 @@ __device__ __forceinline__ double redq_pq_word_nd(double x, const RedqPqParams &
     return u64_to_f64_exact(rho);
 }
 
-// S > 0: the integer floors split at q^S (redq_pq_word_split).
+// S > 0: each word splits at q^S (redq_pq_word_split).
 template <bool INT_FLOOR, int ND, int S = 0>
 __global__ void __launch_bounds__(kThreads)
 redq_pq_kernel(const double *__restrict__ in, double *__restrict__ out, int64_t count,
