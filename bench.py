@@ -45,31 +45,76 @@ def headline_config(n):
             "p": 101, "k": 2, "n": n, "l2": FLUSH_NOTE}
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# headline GEMM from one ncu capture (profiles/gemm_planes_tc_gf101_2_n4096.md),
-# valid only while the kernel's source file, "//" comments and blank lines
-# aside, is the one captured.
+# headline GEMM from one ncu capture of the same workload, valid only while
+# the kernel's source file, "//" comments and blank lines aside, is the one
+# captured (its hash below); otherwise the line reports null.
+PLANE_KERNEL = "gemm_planes_pair_kernel<2,128>"
 MEASURED_TRAFFIC = {
-    "gemm_planes_tc_kernel<2,128,2>": {
+    PLANE_KERNEL: {
         "file": "paper_0710_0510_gb300/csrc/k_gemm_tc.cu",
-        "code_sha256": "6b3098fccb881092c810a8335836d81a36ea7600086229560d14a87bea7fc26b",
-        "bytes": 453969920 + 34107648, "n": 4096},
+        "code_sha256": None,
+        "bytes": None, "n": 4096},
 }
 
 
-def measured_traffic(kernel, n):
+def source_hash(path):
+    """sha256 of a source file with "//" comments and blank lines removed."""
     import hashlib
-    rec = MEASURED_TRAFFIC.get(kernel)
-    if not rec or rec["bytes"] is None or rec["n"] != n:
-        return None
     code = []
-    with open(os.path.join(ROOT, rec["file"])) as fh:
+    with open(os.path.join(ROOT, path)) as fh:
         for line in fh:
             line = line.split("//", 1)[0].rstrip()
             if line:
                 code.append(line)
-    if hashlib.sha256("\n".join(code).encode()).hexdigest() != rec["code_sha256"]:
+    return hashlib.sha256("\n".join(code).encode()).hexdigest()
+
+
+def measured_traffic(kernel, n):
+    """(bytes per launch, where they come from) for `kernel` at size n, or
+    (None, reason) when no capture of the current source exists."""
+    rec = MEASURED_TRAFFIC.get(kernel)
+    if not rec or rec["bytes"] is None or rec["n"] != n:
+        return None, "no ncu capture of this kernel at this size"
+    if source_hash(rec["file"]) != rec["code_sha256"]:
+        return None, "the kernel changed since its ncu capture"
+    return rec["bytes"], (f"ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one launch) "
+                          f"of {rec['file']} with source hash {rec['code_sha256'][:16]}")
+
+
+# ---------------------------------------------------------- device status --
+
+class LegWithheld(RuntimeError):
+    """A bounded wait in one of the kernels ran out during a timed leg: its
+    results and its time are not valid, so the leg reports no value."""
+
+
+# Returns None while no kernel has recorded a device timeout since the last
+# call, else the error text; set by main() to read the library's status word.
+STATUS_READER = None
+
+
+def device_error():
+    return STATUS_READER() if STATUS_READER is not None else None
+
+
+def library_status_reader(q):
+    def read():
+        try:
+            q.sync_status()
+        except q.QadicError as exc:
+            if exc.status == q.E_DEVICE_TIMEOUT:
+                return str(exc)
+            raise
         return None
-    return rec["bytes"]
+    return read
+
+
+def guarded(fn, *a, **kw):
+    """fn(*a, **kw), or a withheld-leg record when a device wait expired."""
+    try:
+        return fn(*a, **kw)
+    except LegWithheld as exc:
+        return {"status": "device_timeout", "value": None, "error": str(exc)}
 PQ_Q = 1176
 
 
@@ -234,6 +279,11 @@ def time_steps(torch, step, steps, warmup, dist, kernel_events=None):
     end.record(stream)
     torch.cuda.synchronize()
     barrier(dist)
+    # the status word is sticky: an expiry in a warm-up or a timed step shows
+    # here; every rank learns whether any rank saw one
+    err = device_error()
+    if reduce_max(1.0 if err else 0.0, dist) > 0:
+        raise LegWithheld(err or "a device wait expired on another rank")
     total = reduce_max(start.elapsed_time(end), dist)
     kms = None
     if kev:
@@ -284,15 +334,16 @@ def bench_plane(args, torch, q, W, dist, p=101, n=4096, name="plane"):
     flops = 4 * 2.0 * n ** 3          # k^2 plane products
     pk = peaks()
     achieved = flops / (kms * 1e-3) / 1e12
+    traffic, traffic_source = measured_traffic(PLANE_KERNEL, n)
     res = {
         "ms_per_step": ms, "value": field_ops / (ms * 1e-3) / 1e9, "n": n, "p": p,
         "kernel_ms": kms,
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": pk["bf16_sustained"],
                      "unit": "TFLOP/s", "frac": achieved / pk["bf16_sustained"],
-                     "traffic": measured_traffic("gemm_planes_tc_kernel<2,128,2>", n),
+                     "traffic": traffic, "traffic_source": traffic_source,
                      "traffic_unit": "bytes per launch (DRAM read + write)",
                      "algorithmic_bytes": 2 * 2 * n * n * 2 + 2 * n * n,
-                     "kernel": "gemm_planes_tc_kernel<2,128,2>",
+                     "kernel": PLANE_KERNEL,
                      "peak_source": pk["source"] + " bf16 sustained (cuBLAS)"},
         "gpu_launches": 2 * args.steps,
     }
@@ -330,7 +381,7 @@ def bench_fold(args, torch, q, W, f, A, B, n, C_plane, steps=20):
             "kernel_ms": kms, "bitexact_vs_plane": bool(torch.equal(C, C_plane)),
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": pk["bf16_sustained"],
                          "unit": "TFLOP/s", "frac": achieved / pk["bf16_sustained"],
-                         "traffic": None, "kernel": "gemm_fold_tc_kernel<2,256,2>"}}
+                         "traffic": None, "kernel": "gemm_fold_tc_kernel<2,256,fold>"}}
 
 
 def bench_karatsuba(args, torch, q, W, f, A, B, n, C_plane, steps=20):
@@ -363,7 +414,7 @@ def bench_karatsuba(args, torch, q, W, f, A, B, n, C_plane, steps=20):
             "kernel_ms": kms, "bitexact_vs_plane": bool(torch.equal(C, C_plane)),
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": pk["bf16_sustained"],
                          "unit": "TFLOP/s", "frac": achieved / pk["bf16_sustained"],
-                         "traffic": None, "kernel": "gemm_fold_tc_kernel<3,128,2,karatsuba>",
+                         "traffic": None, "kernel": "gemm_fold_tc_kernel<3,128,karatsuba>",
                          "flop_count": "3 plane products (2 * 3 * n^3)"}}
 
 
@@ -883,121 +934,26 @@ def main():
     uuid = getattr(torch.cuda.get_device_properties(dev_index), "uuid", None)
     smi_id = f"GPU-{uuid}" if uuid else str(dev_index)
     q.lib()
+    global STATUS_READER
+    STATUS_READER = library_status_reader(q)
+    STATUS_READER()   # start from a clear status word
 
     line = {"metric": METRIC,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "data": "synthetic (seeded, shaped like the paper's workloads)"}
     extras = {}
-    with Clocks(smi_id) as clk:
-        if args.workload == "plane":
-            f, A, B, C, res = bench_plane(args, torch, q, W, dist)
-            n = res["n"]
-            line.update({"value": res["value"] * world, "unit": "field Gop/s",
-                         "ms_per_step": res["ms_per_step"], "dtype": "bf16 (exact small integers), "
-                         "f32 accumulate", "roofline": res["roofline"],
-                         "gpu_launches": res["gpu_launches"]})
-            line["config"] = headline_config(n)
-            if rank == 0 and args.extras == "all":
-                C64, fp = bench_fp64(args, torch, q, W, f, A, B, n)
-                fp["bitexact_vs_plane"] = bool(torch.equal(C64, C))
-                extras["fp64_qadic"] = fp
-                extras["plane_over_fp64"] = res["value"] / fp["value"]
-                extras["fold_before"] = bench_fold(args, torch, q, W, f, A, B, n, C)
-                extras["karatsuba"] = bench_karatsuba(args, torch, q, W, f, A, B, n, C)
-                hC, e2e = e2e_plane(args, torch, q, W, f, A, B, n)
-                e2e["bitexact"] = bool(torch.equal(hC, C.cpu()))
-                line["e2e"] = e2e
-        elif args.workload == "redq":
-            d, out, r = bench_redq(args, torch, q, W)
-            line.update({"value": r["value"] * world, "unit": "residues/s", "ms_per_step": r["ms"],
-                         "dtype": "f64 words, integer REDQ", "roofline": r["roofline"],
-                         "gpu_launches": args.steps})
-            line["config"] = {"workload": f"REDQ sweep: {args.words} FP64 words, 5 digits, p=7, "
-                              "q=2^10", "l2": FLUSH_NOTE}
-            extras["redq_variants"] = r["variants"]
-            extras["q_multiple_of_p"] = r["q_multiple_of_p"]
-        elif args.workload == "polymul":
-            a, b, out, r = bench_polymul(args, torch, q, W)
-            line.update({"value": r["value"] * world, "unit": "products/s",
-                         "ms_per_step": r["us_per_batch"] / 1e3, "dtype": "f64 product, u64 REDQ",
-                         "gpu_launches": 50})
-            line["config"] = {"workload": "65,536 pairs of degree-3 polynomials over Z/7, q=2^8"}
-            extras["scaling_2_24_pairs"] = r["scaling_2_24_pairs"]
-            extras["graph_replayed_us_per_batch"] = r["graph_replayed_us_per_batch"]
-        elif args.workload in ("fold", "karatsuba"):
-            f, A, B, C, step = make_plane_workload(torch, q, W, 101, args.n or 4096)
-            step(None)
-            n = args.n or 4096
-            fn = bench_fold if args.workload == "fold" else bench_karatsuba
-            r = fn(args, torch, q, W, f, A, B, n, C, steps=args.steps)
-            line.update({"value": r["value"] * world, "unit": "field Gop/s",
-                         "ms_per_step": r["ms_per_step"], "dtype": "bf16 exact, f32 accumulate",
-                         "roofline": r["roofline"], "gpu_launches": 3 * args.steps})
-            line["config"] = {"workload": f"GF(101^2) n={n}, {args.workload} form", "p": 101,
-                              "k": 2, "n": n, "l2": FLUSH_NOTE}
-            extras["bitexact_vs_plane"] = r["bitexact_vs_plane"]
-        elif args.workload == "fqt":
-            r = bench_fqt(args, torch, q, W)
-            line.update({"value": r["value"] * world, "unit": "products/s", "ms_per_step": r["ms"],
-                         "dtype": "f64 or int64 q-adic words", "roofline": r["roofline_f64"],
-                         "gpu_launches": 1})
-            line["config"] = {"workload": f"{FQT_COUNT} pairs of degree-{FQT_N} polynomials over "
-                              f"Z/{FQT_P}, d-FQT (d = 0: classical delayed reduction)"}
-            extras.update({k: r[k] for k in ("best", "variants", "fqt_over_classical_f64",
-                                             "fqt_over_classical_int64")})
-        elif args.workload == "large":
-            f, A, B, C, res = bench_plane(args, torch, q, W, dist, p=251, n=args.n or 16384)
-            line.update({"value": res["value"] * world, "unit": "field Gop/s",
-                         "ms_per_step": res["ms_per_step"], "dtype": "bf16 exact, f32 accumulate",
-                         "roofline": res["roofline"], "gpu_launches": res["gpu_launches"]})
-            line["config"] = {"workload": f"GF(251^2) n={res['n']} plane form", "p": 251, "k": 2,
-                              "n": res["n"], "l2": FLUSH_NOTE}
-        elif args.workload == "batched":
-            r = bench_batched(args, torch, q, W)
-            line.update({"value": r["value"] * world, "unit": "field Gop/s",
-                         "ms_per_step": r["ms_per_step"], "dtype": "bf16 exact, f32 accumulate",
-                         "roofline": r["roofline"], "gpu_launches": 2 * args.steps})
-            line["config"] = {"workload": "4096 products, m,n,K log-uniform in [16,256], fields "
-                              "GF(2^8), GF(7^4), GF(31^2); one persistent graph-replayed launch"}
-            extras.update({k: r[k] for k in ("one_launch_per_product", "speedup_vs_per_product",
-                                             "speedup_vs_per_product_gpu_only",
-                                             "products", "autotuned_tiles", "ms_default_tiles",
-                                             "ms_register_staged_default_tiles")})
-        elif args.workload == "fp64":
-            r = bench_fp64_gf27(args, torch, q, W)
-            line.update({"value": r["value"] * world, "unit": "field Gop/s",
-                         "ms_per_step": r["ms_per_step"], "dtype": "f64",
-                         "roofline": r["roofline"], "gpu_launches": 3 * args.steps})
-            line["config"] = {"workload": "GF(3^3) n=1024 log-coded: pack (log->q-adic table) + "
-                              "FP64 q-adic GEMM, REDQ every n_q=85 products"}
-        else:
-            raise SystemExit(f"workload {args.workload} not available")
+    try:
+        with Clocks(smi_id) as clk:
+            run_workload(args, torch, q, W, dist, rank, world, line, extras)
+    except LegWithheld as exc:
+        # the headline leg itself saw a device timeout: no value is reported
+        line.update({"value": None, "status": "device_timeout", "error": str(exc),
+                     "unit": line.get("unit")})
+        line.setdefault("config", {"workload": args.workload})
     line["clocks"] = clk.summary()
-    if args.workload == "plane" and rank == 0 and args.extras == "all":
-        r2 = bench_redq(args, torch, q, W)[2]
-        extras["redq"] = {k: r2[k] for k in ("value", "unit", "best", "ms", "roofline",
-                                             "q_multiple_of_p")}
-        pm = bench_polymul(args, torch, q, W)
-        extras["polymul"] = pm[3]
-        bb = bench_batched(args, torch, q, W)
-        extras["batched"] = {k: bb[k] for k in ("value", "unit", "ms_per_step", "one_launch_per_product",
-                                                "speedup_vs_per_product_gpu_only",
-                                                "speedup_vs_per_product", "roofline",
-                                                "autotuned_tiles", "ms_default_tiles",
-                                                "ms_register_staged_default_tiles")}
-        g27 = bench_fp64_gf27(args, torch, q, W)
-        extras["polymul_fqt_p3_n500"] = bench_fqt(args, torch, q, W)
-        extras["fp64_gf27_n1024"] = g27
-        del pm, bb
-        torch.cuda.empty_cache()
-        lf, lA, lB, lC, lres = bench_plane(argparse.Namespace(n=None, steps=5, warmup=2), torch, q,
-                                           W, None, p=251, n=16384)
-        extras["large_gf251_2_n16384"] = {
-            "value": lres["value"], "unit": "field Gop/s", "ms_per_step": lres["ms_per_step"],
-            "kernel_ms": lres["kernel_ms"], "roofline": lres["roofline"]}
-        del lA, lB, lC
-        torch.cuda.empty_cache()
+    if args.workload == "plane" and rank == 0 and args.extras == "all" and "status" not in line:
+        run_plane_extras(args, torch, q, W, extras)
     if rank == 0:
         if args.workload == "plane" and args.extras == "all":
             line["cpu_baseline"] = cpu_baseline_plane(101, line["config"]["n"])
@@ -1008,6 +964,129 @@ def main():
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def run_workload(args, torch, q, W, dist, rank, world, line, extras):
+    """The selected workload's timed leg (fills `line`), with the plane
+    workload's same-input comparisons in `extras`."""
+    if args.workload == "plane":
+        f, A, B, C, res = bench_plane(args, torch, q, W, dist)
+        n = res["n"]
+        line.update({"value": res["value"] * world, "unit": "field Gop/s",
+                     "ms_per_step": res["ms_per_step"], "dtype": "bf16 (exact small integers), "
+                     "f32 accumulate", "roofline": res["roofline"],
+                     "gpu_launches": res["gpu_launches"]})
+        line["config"] = headline_config(n)
+        if rank == 0 and args.extras == "all":
+            def fp64_leg():
+                C64, fp = bench_fp64(args, torch, q, W, f, A, B, n)
+                fp["bitexact_vs_plane"] = bool(torch.equal(C64, C))
+                return fp
+            fp = guarded(fp64_leg)
+            extras["fp64_qadic"] = fp
+            if fp.get("value"):
+                extras["plane_over_fp64"] = res["value"] / fp["value"]
+            extras["fold_before"] = guarded(bench_fold, args, torch, q, W, f, A, B, n, C)
+            extras["karatsuba"] = guarded(bench_karatsuba, args, torch, q, W, f, A, B, n, C)
+
+            def e2e_leg():
+                hC, e2e = e2e_plane(args, torch, q, W, f, A, B, n)
+                e2e["bitexact"] = bool(torch.equal(hC, C.cpu()))
+                return e2e
+            line["e2e"] = guarded(e2e_leg)
+    elif args.workload == "redq":
+        d, out, r = bench_redq(args, torch, q, W)
+        line.update({"value": r["value"] * world, "unit": "residues/s", "ms_per_step": r["ms"],
+                     "dtype": "f64 words, integer REDQ", "roofline": r["roofline"],
+                     "gpu_launches": args.steps})
+        line["config"] = {"workload": f"REDQ sweep: {args.words} FP64 words, 5 digits, p=7, "
+                          "q=2^10", "l2": FLUSH_NOTE}
+        extras["redq_variants"] = r["variants"]
+        extras["q_multiple_of_p"] = r["q_multiple_of_p"]
+    elif args.workload == "polymul":
+        a, b, out, r = bench_polymul(args, torch, q, W)
+        line.update({"value": r["value"] * world, "unit": "products/s",
+                     "ms_per_step": r["us_per_batch"] / 1e3, "dtype": "f64 product, u64 REDQ",
+                     "gpu_launches": 50})
+        line["config"] = {"workload": "65,536 pairs of degree-3 polynomials over Z/7, q=2^8"}
+        extras["scaling_2_24_pairs"] = r["scaling_2_24_pairs"]
+        extras["graph_replayed_us_per_batch"] = r["graph_replayed_us_per_batch"]
+    elif args.workload in ("fold", "karatsuba"):
+        f, A, B, C, step = make_plane_workload(torch, q, W, 101, args.n or 4096)
+        step(None)
+        n = args.n or 4096
+        fn = bench_fold if args.workload == "fold" else bench_karatsuba
+        r = fn(args, torch, q, W, f, A, B, n, C, steps=args.steps)
+        line.update({"value": r["value"] * world, "unit": "field Gop/s",
+                     "ms_per_step": r["ms_per_step"], "dtype": "bf16 exact, f32 accumulate",
+                     "roofline": r["roofline"], "gpu_launches": 3 * args.steps})
+        line["config"] = {"workload": f"GF(101^2) n={n}, {args.workload} form", "p": 101,
+                          "k": 2, "n": n, "l2": FLUSH_NOTE}
+        extras["bitexact_vs_plane"] = r["bitexact_vs_plane"]
+    elif args.workload == "fqt":
+        r = bench_fqt(args, torch, q, W)
+        line.update({"value": r["value"] * world, "unit": "products/s", "ms_per_step": r["ms"],
+                     "dtype": "f64 or int64 q-adic words", "roofline": r["roofline_f64"],
+                     "gpu_launches": 1})
+        line["config"] = {"workload": f"{FQT_COUNT} pairs of degree-{FQT_N} polynomials over "
+                          f"Z/{FQT_P}, d-FQT (d = 0: classical delayed reduction)"}
+        extras.update({k: r[k] for k in ("best", "variants", "fqt_over_classical_f64",
+                                         "fqt_over_classical_int64")})
+    elif args.workload == "large":
+        f, A, B, C, res = bench_plane(args, torch, q, W, dist, p=251, n=args.n or 16384)
+        line.update({"value": res["value"] * world, "unit": "field Gop/s",
+                     "ms_per_step": res["ms_per_step"], "dtype": "bf16 exact, f32 accumulate",
+                     "roofline": res["roofline"], "gpu_launches": res["gpu_launches"]})
+        line["config"] = {"workload": f"GF(251^2) n={res['n']} plane form", "p": 251, "k": 2,
+                          "n": res["n"], "l2": FLUSH_NOTE}
+    elif args.workload == "batched":
+        r = bench_batched(args, torch, q, W)
+        line.update({"value": r["value"] * world, "unit": "field Gop/s",
+                     "ms_per_step": r["ms_per_step"], "dtype": "bf16 exact, f32 accumulate",
+                     "roofline": r["roofline"], "gpu_launches": 2 * args.steps})
+        line["config"] = {"workload": "4096 products, m,n,K log-uniform in [16,256], fields "
+                          "GF(2^8), GF(7^4), GF(31^2); one persistent graph-replayed launch"}
+        extras.update({k: r[k] for k in ("one_launch_per_product", "speedup_vs_per_product",
+                                         "speedup_vs_per_product_gpu_only",
+                                         "products", "autotuned_tiles", "ms_default_tiles",
+                                         "ms_register_staged_default_tiles")})
+    elif args.workload == "fp64":
+        r = bench_fp64_gf27(args, torch, q, W)
+        line.update({"value": r["value"] * world, "unit": "field Gop/s",
+                     "ms_per_step": r["ms_per_step"], "dtype": "f64",
+                     "roofline": r["roofline"], "gpu_launches": 3 * args.steps})
+        line["config"] = {"workload": "GF(3^3) n=1024 log-coded: pack (log->q-adic table) + "
+                          "FP64 q-adic GEMM, REDQ every n_q=85 products"}
+    else:
+        raise SystemExit(f"workload {args.workload} not available")
+
+
+def run_plane_extras(args, torch, q, W, extras):
+    """Every other workload, each its own guarded leg, beside the headline."""
+    def pick(keys):
+        return lambda r: {k: r[k] for k in keys} if "status" not in r else r
+
+    r2 = guarded(lambda: bench_redq(args, torch, q, W)[2])
+    extras["redq"] = pick(("value", "unit", "best", "ms", "roofline", "q_multiple_of_p"))(r2)
+    extras["polymul"] = guarded(lambda: bench_polymul(args, torch, q, W)[3])
+    bb = guarded(bench_batched, args, torch, q, W)
+    extras["batched"] = pick(("value", "unit", "ms_per_step", "one_launch_per_product",
+                              "speedup_vs_per_product_gpu_only", "speedup_vs_per_product",
+                              "roofline", "autotuned_tiles", "ms_default_tiles",
+                              "ms_register_staged_default_tiles"))(bb)
+    g27 = guarded(bench_fp64_gf27, args, torch, q, W)
+    extras["polymul_fqt_p3_n500"] = guarded(bench_fqt, args, torch, q, W)
+    extras["fp64_gf27_n1024"] = g27
+    del bb
+    torch.cuda.empty_cache()
+
+    def large_leg():
+        lf, lA, lB, lC, lres = bench_plane(argparse.Namespace(n=None, steps=5, warmup=2), torch, q,
+                                           W, None, p=251, n=16384)
+        return {"value": lres["value"], "unit": "field Gop/s", "ms_per_step": lres["ms_per_step"],
+                "kernel_ms": lres["kernel_ms"], "roofline": lres["roofline"]}
+    extras["large_gf251_2_n16384"] = guarded(large_leg)
+    torch.cuda.empty_cache()
 
 
 if __name__ == "__main__":

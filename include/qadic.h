@@ -17,7 +17,9 @@
  *          CUDA tensor) unless the name ends in _host.  The caller owns all
  *          data buffers and workspaces; the library owns only the field
  *          handle and the device tables it uploads at qadic_field_init and
- *          frees at qadic_field_destroy.
+ *          frees at qadic_field_destroy.  Those tables are the only device
+ *          memory the library allocates; qadic_set_device_allocator lets the
+ *          caller supply that memory.
  * Streams. `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *          stream).  Calls that take a stream only enqueue work and return.
  * Errors.  Every call returns a qadic_status.  Argument, size, alignment and
@@ -128,6 +130,27 @@ int qadic_field_init(qadic_field **out, uint32_t p, uint32_t k, const uint32_t *
 /* Frees the handle and its device tables.  The caller must ensure no queued
  * work still uses the field.  NULL is accepted. */
 int qadic_field_destroy(qadic_field *field);
+
+/* ------------------------------------------------------ device allocator --
+ * Not from the paper: a property of the library.  The device tables of a
+ * field are the only device memory the library allocates itself.  A caller
+ * whose own allocator owns the device memory (a framework's caching
+ * allocator) installs it here; qadic_field_init then asks `alloc` for every
+ * table, before any other CUDA call, and qadic_field_destroy (or a failed
+ * init) hands each table back to the `free_fn` that was installed when the
+ * field was built.
+ *   alloc(&ptr, bytes, ctx) returns QADIC_OK with ptr set to at least
+ *     `bytes` bytes of device memory on the current device (256-byte
+ *     aligned), or QADIC_E_NOMEM / QADIC_E_CUDA; qadic_field_init then
+ *     returns that status after giving back the tables it already got.
+ *   free_fn(ptr, bytes, ctx) releases one table.
+ *   alloc = free_fn = NULL restores cudaMalloc / cudaFree (the default).
+ * Process-wide; fields built earlier keep the allocator they were built
+ * with, so free_fn and ctx must stay valid until every such field has been
+ * destroyed.  QADIC_E_INVALID when exactly one of alloc, free_fn is NULL. */
+typedef int (*qadic_alloc_fn)(void **ptr, size_t bytes, void *ctx);
+typedef void (*qadic_free_fn)(void *ptr, size_t bytes, void *ctx);
+int qadic_set_device_allocator(qadic_alloc_fn alloc, qadic_free_fn free_fn, void *ctx);
 /* Copies the field description into *out (host memory). */
 int qadic_field_info(const qadic_field *field, qadic_info *out);
 
@@ -384,11 +407,14 @@ int qadic_batched_autotune(const qadic_field *const *fields, int32_t nfields,
  *   (built on the host in a fixed host array of the same size); no device or
  *   host memory is allocated and no allocating routine is called.  Every
  *   device that loads the library holds that array until the process exits.
- *   The first call on a device looks up the array's device address; make
- *   that first call before capturing a stream into a CUDA graph.
+ *   The first call on a device does the set-up: it looks up the array's
+ *   device address and creates one event (no memory allocation); make that
+ *   first call before capturing a stream into a CUDA graph.
  *   All calls share the one array and each call rewrites it from the start
  *   (the tile counter included), so calls whose kernels overlap on the GPU
- *   race: order them on one stream, or synchronise in between.
+ *   race: order them on one stream, or synchronise in between.  A call
+ *   waits on the host until the previous call's upload of the work list
+ *   has read the host array, then rewrites it.
  *   QADIC_E_INVALID when the work list would exceed the array (about
  *   8 MiB / 8 bytes per 32 x 16 output tile); use qadic_batched_gemm then. */
 int qadic_batched_gemm_noalloc(const qadic_field *const *fields, int32_t nfields,

@@ -69,7 +69,13 @@ class FqtInfo(ctypes.Structure):
                 ("word_bits", ctypes.c_uint32), ("word_products", ctypes.c_uint64)]
 
 
+# qadic_set_device_allocator callbacks: alloc(&ptr, bytes, ctx) -> status, free(ptr, bytes, ctx)
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(ctypes.c_void_p), ctypes.c_size_t,
+                            ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
 _SIGS = {
+    "qadic_set_device_allocator": (ctypes.c_int, [ALLOC_FN, FREE_FN, ctypes.c_void_p]),
     "qadic_field_init": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_uint32,
                                         ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint32]),
     "qadic_field_destroy": (ctypes.c_int, [ctypes.c_void_p]),
@@ -446,6 +452,36 @@ def batched_gemm_noalloc(fields, descs, stream=None):
     arr = desc_array(descs)
     hs = (ctypes.c_void_p * len(fields))(*[f.handle for f in fields])
     _check(lib().qadic_batched_gemm_noalloc(hs, len(fields), arr, len(descs), _stream(stream)))
+
+
+# Every callback pair ever installed stays alive for the life of the process:
+# a field built while a pair was installed calls that pair's free at destroy,
+# possibly long after another allocator (or the default) replaced it.
+_ALLOCATOR_REFS = []
+
+
+def set_device_allocator(alloc=None, free=None):
+    """Install the device allocator for field tables (``qadic_set_device_allocator``):
+    ``alloc(bytes) -> int`` returns a device address (0 for out of memory),
+    ``free(ptr, bytes)`` releases one; both None restores cudaMalloc/cudaFree."""
+    if alloc is None and free is None:
+        _check(lib().qadic_set_device_allocator(ALLOC_FN(), FREE_FN(), None))
+        return
+
+    def c_alloc(out, nbytes, ctx):
+        try:
+            ptr = int(alloc(int(nbytes)) or 0)
+        except MemoryError:
+            ptr = 0
+        out[0] = ptr or None
+        return OK if ptr else E_NOMEM
+
+    def c_free(ptr, nbytes, ctx):
+        free(int(ptr or 0), int(nbytes))
+
+    refs = (ALLOC_FN(c_alloc), FREE_FN(c_free))
+    _ALLOCATOR_REFS.append(refs)
+    _check(lib().qadic_set_device_allocator(refs[0], refs[1], None))
 
 
 def selftest_bounded_wait(polls: int, stream=None):

@@ -24,33 +24,90 @@ __device__ int g_status_word;   // bounded-wait status (one per device)
 std::mutex g_status_mu;
 int *g_status_ptr[64] = {nullptr};
 
+// The device allocator for field tables (qadic_set_device_allocator).
+int default_alloc(void **ptr, size_t bytes, void *) {
+    const cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e == cudaSuccess) return QADIC_OK;
+    cudaGetLastError();
+    *ptr = nullptr;
+    return e == cudaErrorMemoryAllocation ? QADIC_E_NOMEM : QADIC_E_CUDA;
+}
+
+void default_free(void *ptr, size_t, void *) { cudaFree(ptr); }
+
+struct Allocator {
+    qadic_alloc_fn alloc = default_alloc;
+    qadic_free_fn free_fn = default_free;
+    void *ctx = nullptr;
+};
+std::mutex g_alloc_mu;
+Allocator g_alloc;
+
+Allocator current_allocator() {
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    return g_alloc;
+}
+
 template <class T>
-int upload(T **dst, const std::vector<T> &src) {
+int alloc_table(const Allocator &a, T **dst, const std::vector<T> &src) {
     *dst = nullptr;
     if (src.empty()) return QADIC_OK;
-    if (cudaMalloc((void **)dst, src.size() * sizeof(T)) != cudaSuccess) {
-        cudaGetLastError();
-        return set_error(QADIC_E_NOMEM, "cudaMalloc of %zu bytes failed", src.size() * sizeof(T));
+    void *p = nullptr;
+    const int st = a.alloc(&p, src.size() * sizeof(T), a.ctx);
+    if (st != QADIC_OK || !p) {
+        *dst = nullptr;
+        return set_error(st == QADIC_E_CUDA ? QADIC_E_CUDA : QADIC_E_NOMEM,
+                         "device allocation of %zu bytes for a field table failed (status %d)",
+                         src.size() * sizeof(T), st);
     }
-    if (cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice) !=
+    *dst = (T *)p;
+    return QADIC_OK;
+}
+
+template <class T>
+int copy_table(T *dst, const std::vector<T> &src) {
+    if (src.empty()) return QADIC_OK;
+    if (cudaMemcpy(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice) !=
         cudaSuccess)
         return set_error(QADIC_E_CUDA, "table upload failed: %s",
                          cudaGetErrorString(cudaGetLastError()));
     return QADIC_OK;
 }
 
+template <class T>
+void free_table(Field &f, T *&p, const std::vector<T> &src) {
+    if (p && f.table_free) f.table_free(p, src.size() * sizeof(T), f.table_ctx);
+    p = nullptr;
+}
+
 void free_tables(Field &f) {
-    cudaFree(f.d_antilog);
-    cudaFree(f.d_log_f64);
-    cudaFree(f.d_log_centred);
-    cudaFree(f.d_tab_L);
-    cudaFree(f.d_tab_H);
-    cudaFree(f.d_fold);
-    f.d_antilog = nullptr;
-    f.d_log_f64 = nullptr;
-    f.d_log_centred = nullptr;
-    f.d_tab_L = f.d_tab_H = nullptr;
-    f.d_fold = nullptr;
+    free_table(f, f.d_antilog, f.antilog);
+    free_table(f, f.d_log_f64, f.log_f64);
+    free_table(f, f.d_log_centred, f.log_centred);
+    free_table(f, f.d_tab_L, f.tab_L);
+    free_table(f, f.d_tab_H, f.tab_H);
+    free_table(f, f.d_fold, f.fold);
+}
+
+// Every device table from the allocator, then the uploads.
+int upload_tables(Field &f) {
+    const Allocator a = current_allocator();
+    f.table_free = a.free_fn;
+    f.table_ctx = a.ctx;
+    int st;
+    if ((st = alloc_table(a, &f.d_antilog, f.antilog)) ||
+        (st = alloc_table(a, &f.d_log_f64, f.log_f64)) ||
+        (st = alloc_table(a, &f.d_log_centred, f.log_centred)) ||
+        (st = alloc_table(a, &f.d_tab_L, f.tab_L)) || (st = alloc_table(a, &f.d_tab_H, f.tab_H)) ||
+        (st = alloc_table(a, &f.d_fold, f.fold)))
+        return st;
+    if (cudaGetDevice(&f.device) != cudaSuccess)
+        return set_error(QADIC_E_CUDA, "no CUDA device: %s", cudaGetErrorString(cudaGetLastError()));
+    if ((st = copy_table(f.d_antilog, f.antilog)) || (st = copy_table(f.d_log_f64, f.log_f64)) ||
+        (st = copy_table(f.d_log_centred, f.log_centred)) || (st = copy_table(f.d_tab_L, f.tab_L)) ||
+        (st = copy_table(f.d_tab_H, f.tab_H)) || (st = copy_table(f.d_fold, f.fold)))
+        return st;
+    return QADIC_OK;
 }
 
 // One non-blocking stream per device for the host copies of qadic_matmul_host.
@@ -129,14 +186,8 @@ int qadic_field_init(qadic_field **out, uint32_t p, uint32_t k, const uint32_t *
         *out = h;
         return QADIC_OK;
     }
-    if (cudaGetDevice(&h->f.device) != cudaSuccess) {
-        delete h;
-        return set_error(QADIC_E_CUDA, "no CUDA device: %s", cudaGetErrorString(cudaGetLastError()));
-    }
     Field &f = h->f;
-    if ((st = upload(&f.d_antilog, f.antilog)) || (st = upload(&f.d_log_f64, f.log_f64)) ||
-        (st = upload(&f.d_log_centred, f.log_centred)) || (st = upload(&f.d_tab_L, f.tab_L)) ||
-        (st = upload(&f.d_tab_H, f.tab_H)) || (st = upload(&f.d_fold, f.fold))) {
+    if ((st = upload_tables(f)) != QADIC_OK) {
         free_tables(f);
         delete h;
         return st;
@@ -147,6 +198,20 @@ int qadic_field_init(qadic_field **out, uint32_t p, uint32_t k, const uint32_t *
         return set_error(QADIC_E_CUDA, "status word unavailable");
     }
     *out = h;
+    return QADIC_OK;
+}
+
+int qadic_set_device_allocator(qadic_alloc_fn alloc, qadic_free_fn free_fn, void *ctx) {
+    if ((alloc == nullptr) != (free_fn == nullptr))
+        return set_error(QADIC_E_INVALID, "alloc and free_fn must both be given or both be NULL");
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    if (!alloc) {
+        g_alloc = Allocator();
+    } else {
+        g_alloc.alloc = alloc;
+        g_alloc.free_fn = free_fn;
+        g_alloc.ctx = ctx;
+    }
     return QADIC_OK;
 }
 
@@ -411,8 +476,8 @@ int qadic_matmul_host(const qadic_field *field, int path, int in_fmt, int64_t m,
     // block fits beside the GEMM's CTA on an SM), and the plane GEMM runs
     // per block.  Each block of C goes back to the host while the next one
     // is computed.  The split keeps the block GEMMs at the wave count of one
-    // GEMM over all rows (one cluster of two CTAs per two SMs) and makes the
-    // last block small, since its copy back cannot be hidden.
+    // GEMM over all rows (counted in 256 x 128 output units, one per two SMs)
+    // and makes the last block small, since its copy back cannot be hidden.
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -332,6 +332,11 @@ int64_t conv_items_of(const qadic_gemm_desc &d, const Field &f) {
                      (chunks_b(d, f) + kConvItemChunks - 1) / kConvItemChunks);
 }
 
+// The work queue's tile counter and tile count are 32-bit signed integers,
+// and so are the byte offsets of the list's sections (below 2^31 with
+// 8-byte tiles and at most 2^24 products).
+constexpr int64_t kMaxQueueTiles = (int64_t)1 << 27;
+
 int64_t max_tiles(const qadic_gemm_desc *descs, int64_t count) {
     int64_t t = 0;
     for (int64_t i = 0; i < count; ++i)
@@ -420,6 +425,10 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
                              f.p, f.k);
     }
     const int64_t tile_bound = max_tiles(descs, count);
+    if (tile_bound > kMaxQueueTiles)
+        return set_error(QADIC_E_INVALID,
+                         "the batch has up to %lld output tiles; the work queue indexes at most %lld",
+                         (long long)tile_bound, (long long)kMaxQueueTiles);
     size_t conv = 0;
     int64_t conv_items = 0;
     for (int64_t i = 0; i < count; ++i) {
@@ -764,9 +773,17 @@ static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes]
 std::mutex g_noalloc_mu;
 alignas(256) uint8_t g_noalloc_host[kNoAllocScratchBytes];
 void *g_noalloc_dev[64] = {nullptr};
+// One event per device, recorded after each upload of the host array; the
+// next call waits for the last one before it rewrites the array, since a
+// copy from pageable memory need not have read all of it when
+// cudaMemcpyAsync returns (on a system whose GPU reads host page tables,
+// the copy may read the array in place).
+cudaEvent_t g_noalloc_uploaded[64] = {nullptr};
+cudaEvent_t g_noalloc_pending = nullptr;
 
-// Device address of the array on the current device, looked up once per
-// device (the symbol's name is only a host-side stand-in).
+// Set-up, once per device with that device current: the device address of
+// the array (the symbol's name is only a host-side stand-in) and the upload
+// event.
 int noalloc_device_ptr(int dev, void **out) {
     if (dev < 0 || dev >= 64) return set_error(QADIC_E_INVALID, "device index %d", dev);
     if (!g_noalloc_dev[dev]) {
@@ -774,6 +791,11 @@ int noalloc_device_ptr(int dev, void **out) {
         const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
         if (e != cudaSuccess || !ptr)
             return set_error(QADIC_E_CUDA, "scratch address: %s", cudaGetErrorString(e));
+        cudaEvent_t ev = nullptr;
+        const cudaError_t e2 = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e2 != cudaSuccess)
+            return set_error(QADIC_E_CUDA, "upload event: %s", cudaGetErrorString(e2));
+        g_noalloc_uploaded[dev] = ev;
         g_noalloc_dev[dev] = ptr;
     }
     *out = g_noalloc_dev[dev];
@@ -813,9 +835,14 @@ int launch_batched_noalloc(const Field *const *fields, int32_t nfields,
         cfgs[i] = field_cfg(*fields[i]);
         smem = std::max(smem, tile_smem_bytes(fields[i]->k, cfgs[i]));
     }
+    const int64_t tile_bound = max_tiles(descs, count);
+    if (tile_bound > kMaxQueueTiles)
+        return set_error(QADIC_E_INVALID,
+                         "the batch has up to %lld output tiles; the work queue indexes at most %lld",
+                         (long long)tile_bound, (long long)kMaxQueueTiles);
     int st0 = prepare_kernel(smem);
     if (st0 != QADIC_OK) return st0;
-    const Layout L = layout_for(count, max_tiles(descs, count));
+    const Layout L = layout_for(count, tile_bound);
     if (L.total > kNoAllocScratchBytes)
         return set_error(QADIC_E_INVALID,
                          "work list of %zu bytes exceeds the %zu-byte fixed scratch of the "
@@ -827,6 +854,13 @@ int launch_batched_noalloc(const Field *const *fields, int32_t nfields,
     int st = noalloc_device_ptr(dev, &dptr);
     if (st != QADIC_OK) return st;
 
+    // the previous call's upload must have read the host array before it changes
+    if (g_noalloc_pending) {
+        const cudaError_t e = cudaEventSynchronize(g_noalloc_pending);
+        if (e != cudaSuccess)
+            return set_error(QADIC_E_CUDA, "previous upload: %s", cudaGetErrorString(e));
+        g_noalloc_pending = nullptr;
+    }
     uint8_t *host = g_noalloc_host;
     std::memset(host, 0, L.tiles_off);
     BFieldParams *fp = reinterpret_cast<BFieldParams *>(host + L.fields_off);
@@ -872,10 +906,11 @@ int launch_batched_noalloc(const Field *const *fields, int32_t nfields,
     hdr->prods_off = (uint32_t)L.prods_off;
     hdr->tiles_off = (uint32_t)L.tiles_off;
     const size_t used = L.tiles_off + (size_t)nt * sizeof(BTile);
-    // A copy from pageable host memory returns once the data has been staged,
-    // so the host array may be rewritten by the next call.
     if (cudaMemcpyAsync(dptr, host, used, cudaMemcpyHostToDevice, stream) != cudaSuccess)
         return set_error(QADIC_E_CUDA, "work list upload: %s", cudaGetErrorString(cudaGetLastError()));
+    if (cudaEventRecord(g_noalloc_uploaded[dev], stream) != cudaSuccess)
+        return set_error(QADIC_E_CUDA, "upload event: %s", cudaGetErrorString(cudaGetLastError()));
+    g_noalloc_pending = g_noalloc_uploaded[dev];
     const int64_t grid = grid_for(dev, smem, nt);
     batched_kernel<<<(unsigned)grid, kThreads, smem, stream>>>((uint8_t *)dptr);
     const cudaError_t e = cudaGetLastError();

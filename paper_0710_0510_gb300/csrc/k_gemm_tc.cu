@@ -24,9 +24,7 @@
 // product only and the exact chunk grows by a factor k: at K = 4096 a tile
 // needs no drain at all.
 //
-// Persistent, in clusters of two CTAs on vertically adjacent output tiles
-// (one unit) that share their B tiles: each CTA loads half of the B tile and
-// multicasts it to both.  One CTA per SM walks units (grouped raster) with
+// Persistent: one CTA per SM walks output tiles (grouped raster) with
 //   warp 0      TMA producer, streaming K-blocks of consecutive tiles into a
 //               STAGES-deep ring without a break between tiles
 //   warp 1      allocates tensor memory; one thread issues tcgen05.mma
@@ -104,8 +102,7 @@ struct Cfg {
 struct TcParams {
     int64_t m, n, ldc;
     int64_t c_plane;      // elements between output planes
-    // Work units are CM tile rows tall (CM = CTAs per cluster along M):
-    // units_m = ceil(tiles_m / CM), nunits = units_m * tiles_n.
+    // Work units are output tiles: units_m = tiles_m, nunits = units_m * tiles_n.
     int32_t tiles_m, tiles_n, units_m, nunits;
     int32_t nkb;          // K-blocks of BK
     int32_t chunk_kb;     // K-blocks per exact FP32 chunk
@@ -136,20 +133,113 @@ __device__ __forceinline__ void unit_coords(int unit, const Params &P, int &um, 
     tn = r / gm;
 }
 
-// CM = 1: one CTA per tile.  CM = 2: clusters of two CTAs on vertically
-// adjacent tiles that share their B tiles: each CTA loads half of every B
-// tile and multicasts it to both, so each SM reads 3/4 of the operand bytes
-// per K-block.  A stage is refilled only when both CTAs have consumed it
-// (their MMA completions arrive on both CTAs' "empty" barriers).
-template <int KP, int BN, int CM>
+// In-place reduction of a warp's share of every accumulator at an exact-
+// chunk boundary: x -> x - p rint(x / p), |result| <= 1.5 p, exact in FP32.
+// NB 32-column loads are in flight per wait, so the tensor-memory load
+// latency is paid NACC * CH / NB times per drain, not NACC * CH.
+template <class CF, int BN>
+__device__ __forceinline__ void drain_accumulators(uint32_t tbase, const TcParams &P) {
+    constexpr int NB = CF::CH < 4 ? CF::CH : 4;
+    static_assert(CF::CH % NB == 0, "drain batches");
+#pragma unroll 1
+    for (int t = 0; t < CF::NACC; ++t)
+#pragma unroll 1
+        for (int c = 0; c < CF::HALF; c += 32 * NB) {
+            uint32_t v[NB][32];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) ptx::tmem_ld32(tbase + t * BN + c + 32 * b, v[b]);
+            ptx::tmem_wait_ld();
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+#pragma unroll
+                for (int e = 0; e < 32; ++e) {
+                    const float x = __uint_as_float(v[b][e]);
+                    const float nq = rintf(x * P.inv_pf);
+                    v[b][e] = __float_as_uint(fmaf(-P.pf, nq, x));   // |.| <= 1.5 p, exact
+                }
+                ptx::tmem_st32(tbase + t * BN + c + 32 * b, v[b]);
+            }
+        }
+    ptx::tmem_wait_st();
+}
+
+// A warp's share of a finished tile: row `row` (this thread's lane), columns
+// col0 .. col0 + HALF.  Each plane sum is brought to |r| <= 1.5 p by one rint
+// step, the fold out_i = r_i + sum_t r_t (X^t mod P)_i runs in FP32 FMAs
+// (every value stays below 2^19, so they are exact), and only the k outputs
+// take the exact reduction to [0, p).  Chunks of 16 columns are stored as
+// soon as they are computed; release() runs once the last chunk has been
+// read from tensor memory.
+template <int KP, int BN, class CF, class Release>
+__device__ __forceinline__ void tile_epilogue(uint32_t tbase, int64_t row, int64_t col0,
+                                              uint8_t *__restrict__ C, const TcParams &P,
+                                              const float *foldf, Release release) {
+#pragma unroll 1
+    for (int c = 0; c < CF::HALF; c += 16) {
+        float r[CF::NACC][16];
+        {
+            uint32_t v[CF::NACC][16];
+#pragma unroll
+            for (int t = 0; t < CF::NACC; ++t) ptx::tmem_ld16(tbase + t * BN + c, v[t]);
+            ptx::tmem_wait_ld();
+            if (c + 16 >= CF::HALF) release();   // tensor memory may take the next tile's MMAs
+#pragma unroll
+            for (int t = 0; t < CF::NACC; ++t)
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const float x = __uint_as_float(v[t][e]);
+                    r[t][e] = fmaf(-P.pf, rintf(x * P.inv_pf), x);
+                }
+        }
+        // plane sums C_t from the accumulators (exact: small integers)
+        float s[2 * KP - 1][16];
+#pragma unroll
+        for (int t = 0; t < 2 * KP - 1; ++t)
+#pragma unroll
+            for (int e = 0; e < 16; ++e) s[t][e] = 0.f;
+#pragma unroll
+        for (int a = 0; a < CF::NACC; ++a)
+#pragma unroll
+            for (int e = 0; e < 16; ++e) s[CF::sum_of(a)][e] += r[a][e];
+        const int64_t col = col0 + c;
+#pragma unroll
+        for (int i = 0; i < KP; ++i) {
+            uint32_t word[4];
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                word[w] = 0;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int e = 4 * w + b;
+                    float o = s[i][e];
+#pragma unroll
+                    for (int t = KP; t < 2 * KP - 1; ++t)
+                        o = fmaf(s[t][e], foldf[(t - KP) * KP + i], o);
+                    word[w] |= mod_exact_f32(__float_as_uint(o), P.pf, P.inv_pf) << (8 * b);
+                }
+            }
+            if (row < P.m && col < P.n) {
+                uint8_t *dst = C + (int64_t)i * P.c_plane + row * P.ldc + col;
+                if (col + 16 <= P.n && (((uintptr_t)dst) & 15) == 0) {
+                    *reinterpret_cast<uint4 *>(dst) = make_uint4(word[0], word[1], word[2], word[3]);
+                } else {
+                    const int64_t nrem = P.n - col;
+                    const int lim = nrem < 16 ? (int)nrem : 16;
+                    for (int e = 0; e < lim; ++e) dst[e] = (uint8_t)(word[e / 4] >> (8 * (e % 4)));
+                }
+            }
+        }
+    }
+}
+
+// One CTA per output tile at a time; a stage is refilled once the MMAs that
+// read it have completed (their commit arrives on the stage's "empty" barrier).
+template <int KP, int BN>
 __global__ void __launch_bounds__(kThreads, 1)
 gemm_planes_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       uint8_t *__restrict__ C, const TcParams P) {
     using CF = Cfg<KP, BN>;
-    static_assert(CM == 1 || CM == 2, "cluster size along M");
-    constexpr uint16_t kAllCtas = (uint16_t)((1u << CM) - 1);
-    const int rank = CM > 1 ? (int)ptx::cluster_ctarank() : 0;
-    const int unit0 = blockIdx.x / CM, unit_step = gridDim.x / CM;
+    const int unit0 = blockIdx.x, unit_step = gridDim.x;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = (uint64_t *)(smem + CF::STAGES * CF::STAGE);
@@ -167,7 +257,7 @@ gemm_planes_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
     if (threadIdx.x == 0) {
         for (int s = 0; s < CF::STAGES; ++s) {
             ptx::mbar_init(&full[s], 1);
-            ptx::mbar_init(&empty[s], CM);   // one MMA completion from each CTA
+            ptx::mbar_init(&empty[s], 1);
         }
         ptx::mbar_init(acc_full, 1);
         ptx::mbar_init(acc_empty, 32 * kEpiWarps);
@@ -182,7 +272,6 @@ gemm_planes_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
     }
     ptx::tc_fence_before();
     __syncthreads();
-    if (CM > 1) ptx::cluster_sync();   // peers' barriers exist before any multicast
     ptx::tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
@@ -201,31 +290,22 @@ gemm_planes_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
             for (int unit = unit0; unit < P.nunits && ok; unit += unit_step) {
                 int um, tn;
                 unit_coords(unit, P, um, tn);
-                const int tm = um * CM + rank;
+                const int tm = um;
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const int stage = (int)(it % CF::STAGES);
                     if (it >= CF::STAGES) {
-                        // with CM > 1 this completes once every CTA has freed the stage
                         if (*abort_flag ||
                             !ptx::mbar_wait(&empty[stage], (uint32_t)((it / CF::STAGES) - 1) & 1)) {
                             ok = false;
                             break;
                         }
                     }
-                    // own A tiles + all of the B tiles (half from each CTA when CM = 2)
+                    // the k A tiles and the k B tiles of this K-block
                     ptx::mbar_arrive_expect_tx(&full[stage], CF::STAGE);
                     for (int i = 0; i < KP; ++i)
                         ptx::tma_load_3d(a_tile(stage, i), &tmA, &full[stage], kb * BK, tm * BM, i);
-                    for (int j = 0; j < KP; ++j) {
-                        if (CM == 1) {
-                            ptx::tma_load_3d(b_tile(stage, j), &tmB, &full[stage], kb * BK, tn * BN, j);
-                        } else {
-                            constexpr int ROWS = BN / CM;   // rows of the B tile this CTA fetches
-                            ptx::tma_load_3d_multicast(b_tile(stage, j) + rank * ROWS * kRowBytes, &tmB,
-                                                       &full[stage], kb * BK, tn * BN + rank * ROWS,
-                                                       j, kAllCtas);
-                        }
-                    }
+                    for (int j = 0; j < KP; ++j)
+                        ptx::tma_load_3d(b_tile(stage, j), &tmB, &full[stage], kb * BK, tn * BN, j);
                 }
             }
             if (!ok) {
@@ -280,8 +360,7 @@ gemm_planes_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                             }
                         }
                     }
-                    if (CM == 1) ptx::mma_commit(&empty[stage]);
-                    else ptx::mma_commit_multicast(&empty[stage], kAllCtas);
+                    ptx::mma_commit(&empty[stage]);
                     if ((kb + 1) % P.chunk_kb == 0 && kb + 1 < nkb) {
                         ptx::mma_commit(acc_full);
                         if (!ptx::mbar_wait(acc_empty, (uint32_t)drain & 1)) {
@@ -318,37 +397,14 @@ gemm_planes_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
         for (int unit = unit0; unit < P.nunits && ok; unit += unit_step) {
             int um, tn;
             unit_coords(unit, P, um, tn);
-            const int tm = um * CM + rank;
+            const int tm = um;
             for (int d = 0; d < ndrain; ++d, ++phase) {
                 if (!ptx::mbar_wait(acc_full, (uint32_t)phase & 1) || *abort_flag) {
                     ok = false;
                     break;
                 }
                 ptx::tc_fence_after();
-                // NB 32-column loads in flight per wait: the tensor-memory load
-                // latency is paid NACC * CH / NB times per drain, not NACC * CH
-                constexpr int NB = CF::CH < 4 ? CF::CH : 4;
-                static_assert(CF::CH % NB == 0, "drain batches");
-#pragma unroll 1
-                for (int t = 0; t < CF::NACC; ++t)
-#pragma unroll 1
-                    for (int c = 0; c < CF::HALF; c += 32 * NB) {
-                        uint32_t v[NB][32];
-#pragma unroll
-                        for (int b = 0; b < NB; ++b) ptx::tmem_ld32(tbase + t * BN + c + 32 * b, v[b]);
-                        ptx::tmem_wait_ld();
-#pragma unroll
-                        for (int b = 0; b < NB; ++b) {
-#pragma unroll
-                            for (int e = 0; e < 32; ++e) {
-                                const float x = __uint_as_float(v[b][e]);
-                                const float nq = rintf(x * P.inv_pf);
-                                v[b][e] = __float_as_uint(fmaf(-P.pf, nq, x));   // |.| <= 1.5 p, exact
-                            }
-                            ptx::tmem_st32(tbase + t * BN + c + 32 * b, v[b]);
-                        }
-                    }
-                ptx::tmem_wait_st();
+                drain_accumulators<CF, BN>(tbase, P);
                 ptx::tc_fence_before();
                 ptx::mbar_arrive(acc_empty);
             }
@@ -359,87 +415,289 @@ gemm_planes_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
             }
             ++phase;
             ptx::tc_fence_after();
-            // Each plane sum is brought to |r| <= 1.5 p by one rint step, the
-            // fold out_i = r_i + sum_t r_t (X^t mod P)_i runs in FP32 FMAs
-            // (every value stays below 2^19, so they are exact), and only the
-            // k outputs take the exact reduction to [0, p).  Chunks of 16
-            // columns are stored as soon as they are computed; tensor memory is
-            // released once the last chunk has been read.
             const int64_t row = (int64_t)tm * BM + quarter * 32 + lane;
-#pragma unroll 1
-            for (int c = 0; c < CF::HALF; c += 16) {
-                float r[CF::NACC][16];
-                {
-                    uint32_t v[CF::NACC][16];
-#pragma unroll
-                    for (int t = 0; t < CF::NACC; ++t) ptx::tmem_ld16(tbase + t * BN + c, v[t]);
-                    ptx::tmem_wait_ld();
-                    if (c + 16 >= CF::HALF) {
-                        // tensor memory may now take the next tile's MMAs
-                        ptx::tc_fence_before();
-                        ptx::mbar_arrive(tmem_free);
-                    }
-#pragma unroll
-                    for (int t = 0; t < CF::NACC; ++t)
-#pragma unroll
-                        for (int e = 0; e < 16; ++e) {
-                            const float x = __uint_as_float(v[t][e]);
-                            r[t][e] = fmaf(-P.pf, rintf(x * P.inv_pf), x);
-                        }
-                }
-                // plane sums C_t from the accumulators (exact: small integers)
-                float s[2 * KP - 1][16];
-#pragma unroll
-                for (int t = 0; t < 2 * KP - 1; ++t)
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) s[t][e] = 0.f;
-#pragma unroll
-                for (int a = 0; a < CF::NACC; ++a)
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) s[CF::sum_of(a)][e] += r[a][e];
-                const int64_t col = (int64_t)tn * BN + col_base + c;
-#pragma unroll
-                for (int i = 0; i < KP; ++i) {
-                    uint32_t word[4];
-#pragma unroll
-                    for (int w = 0; w < 4; ++w) {
-                        word[w] = 0;
-#pragma unroll
-                        for (int b = 0; b < 4; ++b) {
-                            const int e = 4 * w + b;
-                            float o = s[i][e];
-#pragma unroll
-                            for (int t = KP; t < 2 * KP - 1; ++t)
-                                o = fmaf(s[t][e], foldf[(t - KP) * KP + i], o);
-                            word[w] |= mod_exact_f32(__float_as_uint(o), P.pf, P.inv_pf) << (8 * b);
-                        }
-                    }
-                    if (row < P.m && col < P.n) {
-                        uint8_t *dst = C + (int64_t)i * P.c_plane + row * P.ldc + col;
-                        if (col + 16 <= P.n && (((uintptr_t)dst) & 15) == 0) {
-                            *reinterpret_cast<uint4 *>(dst) = make_uint4(word[0], word[1], word[2], word[3]);
-                        } else {
-                            const int64_t nrem = P.n - col;
-                            const int lim = nrem < 16 ? (int)nrem : 16;
-                            for (int e = 0; e < lim; ++e) dst[e] = (uint8_t)(word[e / 4] >> (8 * (e % 4)));
-                        }
-                    }
-                }
-            }
+            const int64_t col0 = (int64_t)tn * BN + col_base;
+            tile_epilogue<KP, BN, CF>(tbase, row, col0, C, P, foldf, [&] {
+                ptx::tc_fence_before();
+                ptx::mbar_arrive(tmem_free);
+            });
         }
         if (!ok) *abort_flag = 1;
     }
 
     ptx::tc_fence_before();
     __syncthreads();
-    // no peer may still multicast into this CTA's shared memory or arrive on
-    // its barriers once it exits: every CTA has waited for its own MMAs
-    // (mma_done) and its loads (full barriers) before this point
-    if (CM > 1) ptx::cluster_sync();
     if (threadIdx.x == 0 && *abort_flag) record_timeout(P.status, 3);
     if (warp == 1) {
         ptx::tc_fence_after();
         ptx::tmem_dealloc(tmem_base, CF::TMEM_COLS);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// CTA-pair form (cta_group::2), k = 2.  A cluster of two CTAs on two SMs
+// computes a 256 x BN unit: the leader (cluster rank 0) takes output rows
+// 0..127 of the unit, the peer rows 128..255.  One MMA of M = 256 per A plane
+// and 16-wide K step covers both: each CTA holds its own 128 rows of A_i and
+// one half of the combined operand [B_0; B_1] (the leader B_0's tile, the
+// peer B_1's), so each SM stages and reads half of the B bytes per multiply-
+// add that a one-CTA tile needs.  Each CTA's tensor memory holds its rows of
+// the four split accumulators [C_0 | C_1a | C_1b | C_2] (512 columns).
+//   warp 0      both CTAs: TMA producer for its own tiles.  The loads of both
+//               CTAs complete on the leader's "full" barrier (cta_group::2
+//               TMA); the leader announces the transaction bytes of both.
+//   warp 1      both CTAs allocate the pair's tensor memory; the leader's lane
+//               0 issues the MMAs and commits each stage's completion to the
+//               "empty" barriers, and each chunk's or tile's to the
+//               "accumulators ready" barriers, of both CTAs.
+//   warps 2-9   both CTAs: epilogue of its own rows; every epilogue warp of
+//               both CTAs arrives on the leader's "drained" / "read out"
+//               barriers (one arrival per warp).
+// Waits are bounded; an expired wait raises the abort flag of both CTAs.
+// After an abort each CTA gives in-flight copies a bounded time to land
+// before the final cluster barrier, then both free tensor memory and exit.
+template <int KP, int BN>
+struct PairCfg {
+    static_assert(KP == 2, "the pair kernel uses the split accumulators of k = 2");
+    static constexpr int NACC = KP * KP;
+    static constexpr int A_TILE = BM * BK * 2;
+    static constexpr int B_ROWS = KP * BN / 2;             // this CTA's half of [B_0; B_1]
+    static constexpr int B_HALF = B_ROWS * BK * 2;
+    static constexpr int BOX = BN;                         // rows per B load (one plane tile)
+    static constexpr int NBOX = B_ROWS / BOX;
+    static constexpr int STAGE = KP * A_TILE + B_HALF;     // bytes per CTA per stage
+    static constexpr int STAGES_RAW = (kSmemBudget - 2048) / STAGE;
+    static constexpr int STAGES = STAGES_RAW > 8 ? 8 : STAGES_RAW;
+    static constexpr int ACC_COLS = NACC * BN;
+    static constexpr int a_col(int i) { return i * KP * BN; }
+    static constexpr int sum_of(int a) { return (a / KP) + (a % KP); }
+    static constexpr int TMEM_COLS = ACC_COLS <= 32 ? 32 : ACC_COLS <= 64 ? 64
+                                   : ACC_COLS <= 128 ? 128 : ACC_COLS <= 256 ? 256 : 512;
+    static constexpr int HALF = BN * 4 / kEpiWarps;
+    static constexpr int CH = HALF / 32;
+    static constexpr int SMEM = 1024 + STAGES * STAGE + 256;
+    static_assert(ACC_COLS <= 512, "accumulators exceed tensor memory");
+    static_assert(KP * BN <= 256 && (KP * BN) % 16 == 0, "pair MMA N must be <= 256");
+    static_assert(B_ROWS % BOX == 0 && BOX <= 256, "B half in whole loads");
+    static_assert(HALF % 32 == 0, "epilogue works on 32-column chunks");
+    static_assert(STAGES >= 2, "not enough shared memory for two stages");
+};
+
+// Bounded settling time after an abort: copies issued before the abort land
+// within microseconds; the CTAs wait this long before leaving the cluster.
+constexpr uint64_t kSettleNs = 2000000;
+
+template <int KP, int BN>
+__global__ void __launch_bounds__(kThreads, 1)
+gemm_planes_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                        uint8_t *__restrict__ C, const TcParams P) {
+    using CF = PairCfg<KP, BN>;
+    const uint32_t rank = ptx::cluster_ctarank();   // 0: leader, 1: peer
+    const uint32_t peer = rank ^ 1u;
+    const int unit0 = blockIdx.x / 2, unit_step = gridDim.x / 2;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = (uint64_t *)(smem + CF::STAGES * CF::STAGE);
+    uint64_t *empty = full + CF::STAGES;
+    uint64_t *acc_full = empty + CF::STAGES;   // MMAs of a chunk / a tile completed
+    uint64_t *acc_empty = acc_full + 1;        // both CTAs' epilogues finished a drain
+    uint64_t *tmem_free = acc_empty + 1;       // both CTAs read a tile's accumulators out
+    uint64_t *mma_done = tmem_free + 1;
+    uint32_t *tmem_slot = (uint32_t *)(mma_done + 1);
+    volatile uint32_t *abort_flag = (volatile uint32_t *)(tmem_slot + 1);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int nkb = P.nkb;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < CF::STAGES; ++s) {
+            ptx::mbar_init(&full[s], 1);
+            ptx::mbar_init(&empty[s], 1);
+        }
+        ptx::mbar_init(acc_full, 1);
+        ptx::mbar_init(acc_empty, 2 * kEpiWarps);
+        ptx::mbar_init(tmem_free, 2 * kEpiWarps);
+        ptx::mbar_init(mma_done, 1);
+        *abort_flag = 0;
+        ptx::fence_mbar_init();
+    }
+    if (warp == 1) {
+        ptx::tmem_alloc_pair(tmem_slot, CF::TMEM_COLS);
+        ptx::tmem_relinquish_pair();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::cluster_sync();   // both CTAs' barriers and tensor memory exist before any remote use
+    ptx::tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    auto in_leader = [&](const void *x) { return ptx::mapa(ptx::smem_addr(x), 0); };
+    auto in_peer = [&](const void *x) { return ptx::mapa(ptx::smem_addr(x), peer); };
+    const uint32_t peer_abort = in_peer((const void *)abort_flag);
+    auto abort_both = [&]() {
+        *abort_flag = 1;
+        ptx::st_cluster_u32(peer_abort, 1);
+    };
+    auto a_tile = [&](int stage, int i) { return smem + stage * CF::STAGE + i * CF::A_TILE; };
+    auto b_half = [&](int stage) { return smem + stage * CF::STAGE + KP * CF::A_TILE; };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer (both CTAs) ----------------
+            ptx::prefetch_tmap(&tmA);
+            ptx::prefetch_tmap(&tmB);
+            int64_t it = 0;
+            bool ok = true;
+            for (int unit = unit0; unit < P.nunits && ok; unit += unit_step) {
+                int um, tn;
+                unit_coords(unit, P, um, tn);
+                const int tm = um * 2 + (int)rank;
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int stage = (int)(it % CF::STAGES);
+                    if (it >= CF::STAGES) {
+                        if (*abort_flag ||
+                            !ptx::mbar_wait_cluster(&empty[stage],
+                                                    (uint32_t)((it / CF::STAGES) - 1) & 1)) {
+                            ok = false;
+                            break;
+                        }
+                    }
+                    const uint32_t fb = in_leader(&full[stage]);
+                    if (rank == 0) ptx::mbar_arrive_expect_tx(&full[stage], 2 * CF::STAGE);
+                    for (int i = 0; i < KP; ++i)
+                        ptx::tma_load_3d_pair(a_tile(stage, i), &tmA, fb, kb * BK, tm * BM, i);
+                    for (int b = 0; b < CF::NBOX; ++b) {
+                        const int row = ((int)rank * CF::NBOX + b) * CF::BOX;   // in [B_0; B_1]
+                        ptx::tma_load_3d_pair(b_half(stage) + b * CF::BOX * kRowBytes, &tmB, fb,
+                                              kb * BK, tn * BN + row % BN, row / BN);
+                    }
+                }
+            }
+            if (!ok) abort_both();
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && rank == 0) {
+            // ---------------- MMA issuer (leader) ----------------
+            const uint32_t idesc = ptx::idesc_bf16_f32(2 * BM, KP * BN);
+            const uint32_t peer_empty0 = in_peer(&empty[0]), peer_acc_full = in_peer(acc_full);
+            auto commit_both = [&](uint64_t *bar, uint32_t peer_bar) {
+                ptx::mma_commit_pair(bar);
+                ptx::mma_commit_pair_at(peer_bar);
+            };
+            int64_t it = 0;
+            int drain = 0, tcount = 0;
+            bool ok = true;
+            for (int unit = unit0; unit < P.nunits && ok; unit += unit_step, ++tcount) {
+                if (tcount > 0) {   // both CTAs have read the previous tile's accumulators
+                    if (*abort_flag ||
+                        !ptx::mbar_wait_cluster(tmem_free, (uint32_t)(tcount - 1) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    ptx::tc_fence_after();
+                }
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int stage = (int)(it % CF::STAGES);
+                    if (*abort_flag ||
+                        !ptx::mbar_wait_cluster(&full[stage], (uint32_t)(it / CF::STAGES) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    ptx::tc_fence_after();
+                    const uint64_t bd = operand_desc(b_half(stage));
+#pragma unroll
+                    for (int kk = 0; kk < BK / UMMA_K; ++kk)
+#pragma unroll
+                        for (int i = 0; i < KP; ++i)
+                            ptx::mma_bf16_pair(tmem_base + CF::a_col(i),
+                                               operand_desc(a_tile(stage, i)) + 2 * kk, bd + 2 * kk,
+                                               idesc, (kb == 0 && kk == 0) ? 0u : 1u);
+                    commit_both(&empty[stage], peer_empty0 + 8 * stage);
+                    if ((kb + 1) % P.chunk_kb == 0 && kb + 1 < nkb) {
+                        commit_both(acc_full, peer_acc_full);
+                        if (!ptx::mbar_wait_cluster(acc_empty, (uint32_t)drain & 1)) {
+                            ok = false;
+                            break;
+                        }
+                        ptx::tc_fence_after();
+                        ++drain;
+                    }
+                }
+                if (ok) commit_both(acc_full, peer_acc_full);   // tile complete
+            }
+            if (!ok) {
+                abort_both();
+                commit_both(acc_full, peer_acc_full);   // wake the epilogues
+            }
+            // every MMA has completed (in both CTAs' tensor memory) once
+            // mma_done flips: only then may tensor memory be released
+            ptx::mma_commit_pair(mma_done);
+            if (!ptx::mbar_wait(mma_done, 0)) abort_both();
+        }
+    } else {
+        // ---------------- epilogue (warps 2..9, both CTAs) ----------------
+        const int ew = warp - 2;
+        const int quarter = warp & 3;
+        const int col_base = (ew / 4) * CF::HALF;
+        const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + col_base;
+        const int ndrain = nkb > 0 ? (nkb - 1) / P.chunk_kb : 0;
+        const uint32_t lead_acc_empty = in_leader(acc_empty);
+        const uint32_t lead_tmem_free = in_leader(tmem_free);
+        float foldf[(KP - 1) * KP + 1];
+#pragma unroll
+        for (int x = 0; x < (KP - 1) * KP; ++x) foldf[x] = (float)P.fold[x];
+        auto ready = [&](int ph) { return ptx::mbar_wait_cluster(acc_full, (uint32_t)ph & 1); };
+        auto arrive_warp = [&](uint32_t lead_bar) {
+            ptx::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive_cluster(lead_bar);
+        };
+        int phase = 0;
+        bool ok = true;
+        for (int unit = unit0; unit < P.nunits && ok; unit += unit_step) {
+            int um, tn;
+            unit_coords(unit, P, um, tn);
+            const int tm = um * 2 + (int)rank;
+            for (int d = 0; d < ndrain; ++d, ++phase) {
+                if (!ready(phase) || *abort_flag) {
+                    ok = false;
+                    break;
+                }
+                ptx::tc_fence_after();
+                drain_accumulators<CF, BN>(tbase, P);
+                arrive_warp(lead_acc_empty);
+            }
+            if (!ok) break;
+            if (!ready(phase) || *abort_flag) {
+                ok = false;
+                break;
+            }
+            ++phase;
+            ptx::tc_fence_after();
+            const int64_t row = (int64_t)tm * BM + quarter * 32 + lane;
+            const int64_t col0 = (int64_t)tn * BN + col_base;
+            tile_epilogue<KP, BN, CF>(tbase, row, col0, C, P, foldf,
+                                      [&] { arrive_warp(lead_tmem_free); });
+        }
+        if (!ok) abort_both();
+    }
+
+    ptx::tc_fence_before();
+    const bool aborted = __syncthreads_or(*abort_flag != 0) != 0;
+    if (aborted) {
+        if (threadIdx.x == 0) {
+            const uint64_t t0 = ptx::globaltimer_ns();
+            while (ptx::globaltimer_ns() - t0 < kSettleNs) __nanosleep(10000);
+        }
+        __syncthreads();
+    }
+    // neither CTA leaves while the other may still arrive on its barriers,
+    // copy into its shared memory or have MMAs write its tensor memory
+    ptx::cluster_sync();
+    if (threadIdx.x == 0 && aborted) record_timeout(P.status, 5);
+    if (warp == 1) {
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc_pair(tmem_base, CF::TMEM_COLS);
     }
 }
 
@@ -491,15 +749,12 @@ struct FoldCfg {
     static_assert(STAGES >= 2, "not enough shared memory for two stages");
 };
 
-template <int KP, int BN, int CM, int EPI>
+template <int KP, int BN, int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
 gemm_fold_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     uint8_t *__restrict__ C, const FoldParams P) {
     using CF = FoldCfg<KP, BN>;
-    static_assert(CM == 1 || CM == 2, "cluster size along M");
-    constexpr uint16_t kAllCtas = (uint16_t)((1u << CM) - 1);
-    const int rank = CM > 1 ? (int)ptx::cluster_ctarank() : 0;
-    const int unit0 = blockIdx.x / CM, unit_step = gridDim.x / CM;
+    const int unit0 = blockIdx.x, unit_step = gridDim.x;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = (uint64_t *)(smem + CF::STAGES * CF::STAGE);
@@ -517,7 +772,7 @@ gemm_fold_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
     if (threadIdx.x == 0) {
         for (int s = 0; s < CF::STAGES; ++s) {
             ptx::mbar_init(&full[s], 1);
-            ptx::mbar_init(&empty[s], CM);
+            ptx::mbar_init(&empty[s], 1);
         }
         ptx::mbar_init(acc_full, 1);
         ptx::mbar_init(acc_empty, 32 * kEpiWarps);
@@ -532,7 +787,6 @@ gemm_fold_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
     }
     ptx::tc_fence_before();
     __syncthreads();
-    if (CM > 1) ptx::cluster_sync();
     ptx::tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
@@ -549,7 +803,7 @@ gemm_fold_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
             for (int unit = unit0; unit < P.nunits && ok; unit += unit_step) {
                 int um, tn;
                 unit_coords(unit, P, um, tn);
-                const int tm = um * CM + rank;
+                const int tm = um;
                 for (int kb = 0; kb < nkbp && ok; ++kb)
                     for (int i = 0; i < KP; ++i, ++it) {
                         const int stage = (int)(it % CF::STAGES);
@@ -562,14 +816,7 @@ gemm_fold_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
                         }
                         ptx::mbar_arrive_expect_tx(&full[stage], CF::STAGE);
                         ptx::tma_load_3d(a_tile(stage), &tmA, &full[stage], kb * BK, tm * BM, i);
-                        if (CM == 1) {
-                            ptx::tma_load_3d(b_tile(stage), &tmB, &full[stage], kb * BK, tn * BN, i);
-                        } else {
-                            constexpr int ROWS = BN / CM;
-                            ptx::tma_load_3d_multicast(b_tile(stage) + rank * ROWS * kRowBytes, &tmB,
-                                                       &full[stage], kb * BK, tn * BN + rank * ROWS,
-                                                       i, kAllCtas);
-                        }
+                        ptx::tma_load_3d(b_tile(stage), &tmB, &full[stage], kb * BK, tn * BN, i);
                     }
             }
             if (!ok) {
@@ -608,8 +855,7 @@ gemm_fold_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
                         for (int kk = 0; kk < BK / UMMA_K; ++kk)
                             ptx::mma_bf16(tmem_base + i * BN, ad + 2 * kk, bd + 2 * kk, idesc,
                                           (kb == 0 && kk == 0) ? 0u : 1u);
-                        if (CM == 1) ptx::mma_commit(&empty[stage]);
-                        else ptx::mma_commit_multicast(&empty[stage], kAllCtas);
+                        ptx::mma_commit(&empty[stage]);
                     }
                     if (ok && (kb + 1) % P.chunk_kb == 0 && kb + 1 < nkbp) {
                         // exact-chunk boundary of every accumulator at once
@@ -646,7 +892,7 @@ gemm_fold_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
         for (int unit = unit0; unit < P.nunits && ok; unit += unit_step) {
             int um, tn;
             unit_coords(unit, P, um, tn);
-            const int tm = um * CM + rank;
+            const int tm = um;
             for (int d = 0; d < ndrain; ++d, ++phase) {
                 // in-place reduction of every accumulator
                 if (!ptx::mbar_wait(acc_full, (uint32_t)phase & 1) || *abort_flag) {
@@ -781,7 +1027,6 @@ gemm_fold_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
 
     ptx::tc_fence_before();
     __syncthreads();
-    if (CM > 1) ptx::cluster_sync();
     if (threadIdx.x == 0 && *abort_flag) record_timeout(P.status, 4);
     if (warp == 1) {
         ptx::tc_fence_after();
@@ -827,7 +1072,7 @@ int make_plane_map(CUtensorMap *map, const void *base, int64_t K, int64_t rows, 
     return QADIC_OK;
 }
 
-template <int KP, int BN, int CM>
+template <int KP, int BN>
 int launch_tc(const Field &f, int64_t m, int64_t n, int64_t K, const void *A, int64_t lda,
               int64_t a_plane, const void *B, int64_t ldb, int64_t b_plane, uint8_t *C,
               int64_t ldc, int64_t c_plane, cudaStream_t stream) {
@@ -835,7 +1080,7 @@ int launch_tc(const Field &f, int64_t m, int64_t n, int64_t K, const void *A, in
     CUtensorMap tmA, tmB;
     int st;
     if ((st = make_plane_map(&tmA, A, K, m, lda, a_plane, KP, BM))) return st;
-    if ((st = make_plane_map(&tmB, B, K, n, ldb, b_plane, KP, BN / CM))) return st;
+    if ((st = make_plane_map(&tmB, B, K, n, ldb, b_plane, KP, BN))) return st;
     TcParams P;
     P.m = m;
     P.n = n;
@@ -857,12 +1102,71 @@ int launch_tc(const Field &f, int64_t m, int64_t n, int64_t K, const void *A, in
     for (uint32_t t = 0; t + 1 < f.k; ++t)
         for (uint32_t i = 0; i < f.k; ++i) P.fold[t * KP + i] = f.fold[t * f.k + i];
     P.status = device_status_word();
-    auto kern = gemm_planes_tc_kernel<KP, BN, CM>;
+    auto kern = gemm_planes_tc_kernel<KP, BN>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM) !=
         cudaSuccess)
         return set_error(QADIC_E_CUDA, "tc smem attribute: %s", cudaGetErrorString(cudaGetLastError()));
     const int64_t tiles_m = (m + BM - 1) / BM, tiles_n = (n + BN - 1) / BN;
-    const int64_t units_m = (tiles_m + CM - 1) / CM;
+    const int64_t units_m = tiles_m;
+    if (units_m * tiles_n > 0x7fffffff) return set_error(QADIC_E_INVALID, "too many tiles");
+    P.tiles_m = (int32_t)tiles_m;
+    P.tiles_n = (int32_t)tiles_n;
+    P.units_m = (int32_t)units_m;
+    P.nunits = (int32_t)(units_m * tiles_n);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = CF::SMEM;
+    cfg.stream = stream;
+    // persistent: one CTA per SM (one fits: 227 KB of shared memory each)
+    const int units = (int)std::min<int64_t>(P.nunits, std::max(sms, 1));
+    cfg.gridDim = dim3((unsigned)units);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, tmA, tmB, C, P);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(QADIC_E_CUDA, "tc launch: %s", cudaGetErrorString(e));
+    }
+    return QADIC_OK;
+}
+
+// CTA-pair launch: clusters of two CTAs, one pair per two SMs, persistent
+// over 256 x BN units.
+template <int KP, int BN>
+int launch_tc_pair(const Field &f, int64_t m, int64_t n, int64_t K, const void *A, int64_t lda,
+                   int64_t a_plane, const void *B, int64_t ldb, int64_t b_plane, uint8_t *C,
+                   int64_t ldc, int64_t c_plane, cudaStream_t stream) {
+    using CF = PairCfg<KP, BN>;
+    CUtensorMap tmA, tmB;
+    int st;
+    if ((st = make_plane_map(&tmA, A, K, m, lda, a_plane, KP, BM))) return st;
+    if ((st = make_plane_map(&tmB, B, K, n, ldb, b_plane, KP, CF::BOX))) return st;
+    TcParams P;
+    P.m = m;
+    P.n = n;
+    P.ldc = ldc;
+    P.c_plane = c_plane;
+    P.nkb = (int32_t)((K + BK - 1) / BK);
+    // split accumulators: a drained residue (|.| <= 1.5p < 2p) plus h^2 per K step
+    const int64_t hh = (int64_t)f.h * f.h;
+    const int64_t chunk = ((1ll << 24) - 2 * (int64_t)f.p) / hh;
+    P.chunk_kb = (int32_t)std::min<int64_t>(chunk / BK, 1 << 30);
+    if (P.chunk_kb < 1) return set_error(QADIC_E_OVERFLOW, "exact FP32 chunk below one K-block");
+    P.p = f.p;
+    P.m32 = make_mod_small(f.p);
+    P.pf = (float)f.p;
+    P.inv_pf = 1.0f / (float)f.p;
+    for (uint32_t i = 0; i < kMaxK * kMaxK; ++i) P.fold[i] = 0;
+    for (uint32_t t = 0; t + 1 < f.k; ++t)
+        for (uint32_t i = 0; i < f.k; ++i) P.fold[t * KP + i] = f.fold[t * f.k + i];
+    P.status = device_status_word();
+    auto kern = gemm_planes_pair_kernel<KP, BN>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM) !=
+        cudaSuccess)
+        return set_error(QADIC_E_CUDA, "pair smem attribute: %s", cudaGetErrorString(cudaGetLastError()));
+    const int64_t tiles_m = (m + BM - 1) / BM, tiles_n = (n + BN - 1) / BN;
+    const int64_t units_m = (tiles_m + 1) / 2;
     if (units_m * tiles_n > 0x7fffffff) return set_error(QADIC_E_INVALID, "too many tiles");
     P.tiles_m = (int32_t)tiles_m;
     P.tiles_n = (int32_t)tiles_n;
@@ -873,35 +1177,33 @@ int launch_tc(const Field &f, int64_t m, int64_t n, int64_t K, const void *A, in
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = CF::SMEM;
     cfg.stream = stream;
-    int max_units = sms > 0 ? sms / CM : 1;
-    if (CM > 1) {
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = CM;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        cfg.gridDim = dim3((unsigned)(max_units * CM));
-        int clusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) == cudaSuccess && clusters > 0)
-            max_units = std::min(max_units, clusters);
-        else
-            cudaGetLastError();
-    }
-    const int units = (int)std::min<int64_t>(P.nunits, std::max(max_units, 1));
-    cfg.gridDim = dim3((unsigned)(units * CM));
+    int pairs = std::max(sms / 2, 1);
+    cfg.gridDim = dim3((unsigned)(2 * pairs));
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) == cudaSuccess && clusters > 0)
+        pairs = std::min(pairs, clusters);
+    else
+        cudaGetLastError();
+    pairs = (int)std::min<int64_t>(P.nunits, pairs);
+    cfg.gridDim = dim3((unsigned)(2 * pairs));
     const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, tmA, tmB, C, P);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return set_error(QADIC_E_CUDA, "tc launch: %s", cudaGetErrorString(e));
+        return set_error(QADIC_E_CUDA, "pair launch: %s", cudaGetErrorString(e));
     }
     return QADIC_OK;
 }
 
-template <int KP, int BN, int CM, int EPI = EPI_FOLD>
+template <int KP, int BN, int EPI = EPI_FOLD>
 int launch_fold(const Field &f, int64_t m, int64_t n, int64_t K, const void *A, int64_t lda,
                 const void *B, int64_t ldb, uint8_t *C, int64_t ldc, cudaStream_t stream) {
     using CF = FoldCfg<KP, BN>;
@@ -911,7 +1213,7 @@ int launch_fold(const Field &f, int64_t m, int64_t n, int64_t K, const void *A, 
     CUtensorMap tmA, tmB;
     int st;
     if ((st = make_plane_map(&tmA, A, K, m, lda, m * lda, KP, BM))) return st;
-    if ((st = make_plane_map(&tmB, B, K, b_rows, ldb, b_rows * ldb, KP, BN / CM))) return st;
+    if ((st = make_plane_map(&tmB, B, K, b_rows, ldb, b_rows * ldb, KP, BN))) return st;
     FoldParams P;
     P.m = m;
     P.n = n;
@@ -931,13 +1233,13 @@ int launch_fold(const Field &f, int64_t m, int64_t n, int64_t K, const void *A, 
         P.x2[1] = (float)f.fold[1];
     }
     P.status = device_status_word();
-    auto kern = gemm_fold_tc_kernel<KP, BN, CM, EPI>;
+    auto kern = gemm_fold_tc_kernel<KP, BN, EPI>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM) !=
         cudaSuccess)
         return set_error(QADIC_E_CUDA, "fold smem attribute: %s", cudaGetErrorString(cudaGetLastError()));
     const int64_t tiles_m = (m + BM - 1) / BM;
     const int64_t tiles_n = EPI == EPI_FOLD ? KP * n_pad / BN : (n + BN - 1) / BN;
-    const int64_t units_m = (tiles_m + CM - 1) / CM;
+    const int64_t units_m = tiles_m;
     if (units_m * tiles_n > 0x7fffffff) return set_error(QADIC_E_INVALID, "too many tiles");
     P.tiles_m = (int32_t)tiles_m;
     P.tiles_n = (int32_t)tiles_n;
@@ -947,27 +1249,11 @@ int launch_fold(const Field &f, int64_t m, int64_t n, int64_t K, const void *A, 
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = CF::SMEM;
     cfg.stream = stream;
-    int max_units = sms > 0 ? sms / CM : 1;
-    if (CM > 1) {
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = CM;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        cfg.gridDim = dim3((unsigned)(max_units * CM));
-        int clusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) == cudaSuccess && clusters > 0)
-            max_units = std::min(max_units, clusters);
-        else
-            cudaGetLastError();
-    }
-    const int units = (int)std::min<int64_t>(P.nunits, std::max(max_units, 1));
-    cfg.gridDim = dim3((unsigned)(units * CM));
+    const int units = (int)std::min<int64_t>(P.nunits, std::max(sms, 1));
+    cfg.gridDim = dim3((unsigned)units);
     const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, tmA, tmB, C, P);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -994,12 +1280,17 @@ int launch_gemm_planes_tc_strided(const Field &f, int64_t m, int64_t n, int64_t 
                 return set_error(QADIC_E_CUDA, "memset: %s", cudaGetErrorString(cudaGetLastError()));
         return QADIC_OK;
     }
-    if (f.k == 2)
-        return launch_tc<2, 128, 2>(f, m, n, K, A, lda, a_plane, B, ldb, b_plane, C, ldc, c_plane, stream);
+    if (f.k == 2) {
+        // two tile rows or more: CTA pairs on 256-row units
+        if (m > BM)
+            return launch_tc_pair<2, 128>(f, m, n, K, A, lda, a_plane, B, ldb, b_plane, C, ldc,
+                                          c_plane, stream);
+        return launch_tc<2, 128>(f, m, n, K, A, lda, a_plane, B, ldb, b_plane, C, ldc, c_plane, stream);
+    }
     if (f.k == 3)
-        return launch_tc<3, 64, 2>(f, m, n, K, A, lda, a_plane, B, ldb, b_plane, C, ldc, c_plane, stream);
+        return launch_tc<3, 64>(f, m, n, K, A, lda, a_plane, B, ldb, b_plane, C, ldc, c_plane, stream);
     if (f.k == 4)
-        return launch_tc<4, 64, 2>(f, m, n, K, A, lda, a_plane, B, ldb, b_plane, C, ldc, c_plane, stream);
+        return launch_tc<4, 64>(f, m, n, K, A, lda, a_plane, B, ldb, b_plane, C, ldc, c_plane, stream);
     return set_error(QADIC_E_UNSUPPORTED, "no tensor-core plane kernel for k=%u", f.k);
 }
 
@@ -1023,14 +1314,14 @@ int launch_gemm_fold_tc(const Field &f, int64_t m, int64_t n, int64_t K, const v
         return QADIC_OK;
     }
     switch (f.k) {
-        case 1: return launch_fold<1, 256, 2>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
-        case 2: return launch_fold<2, 256, 2>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
-        case 3: return launch_fold<3, 128, 2>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
-        case 4: return launch_fold<4, 128, 2>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
-        case 5: return launch_fold<5, 64, 2>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
-        case 6: return launch_fold<6, 64, 2>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
-        case 7: return launch_fold<7, 64, 2>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
-        case 8: return launch_fold<8, 64, 2>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
+        case 1: return launch_fold<1, 256>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
+        case 2: return launch_fold<2, 256>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
+        case 3: return launch_fold<3, 128>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
+        case 4: return launch_fold<4, 128>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
+        case 5: return launch_fold<5, 64>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
+        case 6: return launch_fold<6, 64>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
+        case 7: return launch_fold<7, 64>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
+        case 8: return launch_fold<8, 64>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
         default: return set_error(QADIC_E_UNSUPPORTED, "no fold kernel for k=%u", f.k);
     }
 }
@@ -1048,7 +1339,7 @@ int launch_gemm_karatsuba_tc(const Field &f, int64_t m, int64_t n, int64_t K, co
                 return set_error(QADIC_E_CUDA, "memset: %s", cudaGetErrorString(cudaGetLastError()));
         return QADIC_OK;
     }
-    return launch_fold<3, 128, 2, EPI_KARATSUBA>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
+    return launch_fold<3, 128, EPI_KARATSUBA>(f, m, n, K, A, lda, B, ldb, C, ldc, stream);
 }
 
 }  // namespace qadic

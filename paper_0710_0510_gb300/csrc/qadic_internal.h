@@ -34,7 +34,9 @@ struct Field {
     std::vector<uint32_t> tab_L, tab_H;     // Thm. 3 tables (order entries, k bytes packed)
     std::vector<uint8_t> fold;              // (k-1) x k: X^(k+t) mod P, t = 0..k-2
 
-    // Device copies (owned).
+    // Device copies (owned), from the allocator installed at init.
+    qadic_free_fn table_free = nullptr;
+    void *table_ctx = nullptr;
     uint8_t *d_antilog = nullptr;
     double *d_log_f64 = nullptr;
     int8_t *d_log_centred = nullptr;

@@ -1,8 +1,10 @@
 """GPU parity at the benchmark's full sizes, in the launch configuration that
 bench.py times (its own workload builders): outputs against the oracle,
-entry by entry where the oracle can compute them in seconds, and otherwise
-sampled entries plus Freivalds checks (C x = A (B x) for random field
-vectors x), which hold at any size."""
+entry by entry where the oracle computes them within a minute (GF(3^3)
+n = 1024, GF(101^2) n = 4096, all 4096 batched products, both REDQ sweeps),
+and for GF(251^2) n = 16384 sampled entries, whole rows and columns, plus
+Freivalds checks (C x = A (B x) for random field vectors x), which hold at
+any size."""
 import numpy as np
 import pytest
 
@@ -45,18 +47,17 @@ def freivalds(orc, f, A, B, C, vectors=2, seed=0):
 
 
 def test_plane_gf101_2_n4096_and_fp64_form(torch, orc):
-    """Headline workload: pack + tcgen05 plane GEMM at n = 4096, and the FP64
-    q-adic form on the same inputs."""
+    """Headline workload: pack + tcgen05 plane GEMM at n = 4096, every entry
+    against the oracle (2.7e11 schoolbook multiply-adds on the host cores),
+    and the FP64 q-adic form and the end-to-end host path on the same inputs."""
     n = 4096
     f, A, B, C, step = bench.make_plane_workload(torch, q, W, 101, n)
     step(None)
     torch.cuda.synchronize()
     Ch = C.cpu().numpy()
-    rng = np.random.default_rng(11)
-    ii = np.concatenate([rng.integers(0, n, 512), np.full(n, 17), np.arange(n)])
-    jj = np.concatenate([rng.integers(0, n, 512), np.arange(n), np.full(n, n - 1)])
-    assert sampled_entries_agree(orc, f, A, B, Ch, ii, jj)
-    assert freivalds(orc, f, planes_to_mkk(A), planes_to_mkk(B), planes_to_mkk(Ch))
+    want = orc.gemm(f.p, f.poly, planes_to_mkk(A), planes_to_mkk(B))
+    assert np.array_equal(planes_to_mkk(Ch), want)
+    del want
     C64, _ = bench.bench_fp64(None, torch, q, W, f, A, B, n, reps=1)
     assert torch.equal(C64, C)
     # end to end from pinned host buffers, as timed
@@ -75,8 +76,9 @@ def test_plane_gf101_2_n4096_and_fp64_form(torch, orc):
 
 
 def test_plane_gf251_2_n16384(torch, orc):
-    """The n = 16384 GF(251^2) product: 256 sampled entries, one full row and
-    two Freivalds vectors."""
+    """The n = 16384 GF(251^2) product: 4096 sampled entries, two whole rows
+    (one in a leader CTA's half of a 256-row unit, one in a peer's) and two
+    whole columns, and Freivalds checks with 4 random vectors."""
     n = 16384
     f, A, B, C, step = bench.make_plane_workload(torch, q, W, 251, n)
     step(None)
@@ -85,10 +87,13 @@ def test_plane_gf251_2_n16384(torch, orc):
     del C
     torch.cuda.empty_cache()
     rng = np.random.default_rng(12)
-    ii = np.concatenate([rng.integers(0, n, 256), np.full(n, n - 1)])
-    jj = np.concatenate([rng.integers(0, n, 256), np.arange(n)])
+    rows, cols = [5, n - 1], [0, n - 77]
+    ii = np.concatenate([rng.integers(0, n, 4096)] + [np.full(n, r) for r in rows] +
+                        [np.arange(n) for _ in cols])
+    jj = np.concatenate([rng.integers(0, n, 4096)] + [np.arange(n) for _ in rows] +
+                        [np.full(n, c) for c in cols])
     assert sampled_entries_agree(orc, f, A, B, Ch, ii, jj)
-    assert freivalds(orc, f, planes_to_mkk(A), planes_to_mkk(B), planes_to_mkk(Ch))
+    assert freivalds(orc, f, planes_to_mkk(A), planes_to_mkk(B), planes_to_mkk(Ch), vectors=4)
 
 
 def test_fp64_gf27_n1024_full(torch, orc):
@@ -131,8 +136,7 @@ def test_redq_sweep_2_28_words(torch, orc):
 
 def test_batched_4096_products(torch, orc):
     """4096 uneven products over GF(2^8), GF(7^4), GF(31^2) in one
-    graph-replayed launch: 48 products in full, every product by a
-    Freivalds vector."""
+    graph-replayed launch: every product in full against the oracle."""
     fields, dims, fidx, offs, hA, hB, dC, descs, ws = bench.make_batched(torch, q, W)
     q.batched_gemm(fields, descs, ws, graph=True)
     torch.cuda.synchronize()
@@ -147,12 +151,9 @@ def test_batched_4096_products(torch, orc):
         C = planes_to_mkk(Ch[c:c + f.k * m * n].reshape(f.k, m, n))
         return f, A, B, C
 
-    for i in np.random.default_rng(5).choice(len(descs), 48, replace=False):
-        f, A, B, C = operands(i)
-        assert np.array_equal(C, orc.gemm(f.p, f.poly, A, B)), i
     for i in range(len(descs)):
         f, A, B, C = operands(i)
-        assert freivalds(orc, f, A, B, C, vectors=1, seed=i), i
+        assert np.array_equal(C, orc.gemm(f.p, f.poly, A, B)), i
 
 
 def test_fold_and_karatsuba_forms_n4096(torch, orc):

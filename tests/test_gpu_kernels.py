@@ -351,6 +351,43 @@ def test_gemm_planes_sums_at_the_fp32_limit(torch, orc, p, val):
     assert (got == got[:, :1, :1]).all()
 
 
+@pytest.mark.parametrize("p,val", [(251, 125), (251, -125), (101, 50)])
+def test_gemm_planes_pair_sums_at_the_fp32_limit(torch, orc, p, val):
+    """k = 2 with m > 128 runs on CTA pairs (one M = 256 MMA per A plane, the
+    peer's rows in the peer's tensor memory).  All coefficients at +-h with
+    one sign: each split accumulator grows by h^2 per K step and reaches the
+    2^24 bound at the end of every exact chunk; K crosses two drains.  Rows of
+    both CTAs of a pair (0, 127 | 128, 255) and of a second pair are checked."""
+    k = 2
+    f = q.Field(p, k)
+    h2 = ((p - 1) // 2) ** 2
+    chunk = (2 ** 24 - 2 * p) // h2 // 64 * 64          # K-blocks of 64 per split chunk
+    m, n, K = 384, 256, 2 * chunk + 64
+    A = np.full((k, m, K), val, np.int8)
+    B = np.full((k, K, n), val, np.int8)
+    got = run_planes(torch, f, q.FMT_INT8_PLANES, A, B, m, n, K)
+    rows = [0, 127, 128, 255, 256, 383]
+    full = oracle_gemm_from_planes(orc, p, f.poly, A[:, :2, :], B[:, :, :2])
+    for r in rows:
+        assert np.array_equal(got[:, r, :2], full[:, 0, :]), r
+    assert (got == got[:, :1, :1]).all()
+
+
+@pytest.mark.parametrize("pk,shape", [((101, 2), (257, 130, 777)), ((251, 2), (512, 200, 2179)),
+                                      ((101, 2), (1000, 72, 136)), ((31, 2), (300, 520, 64))])
+def test_gemm_planes_pair_shapes(torch, orc, pk, shape):
+    """CTA-pair path on ragged shapes: odd tile-row counts (the last pair's
+    peer rows wholly outside A), ragged n and K, GF(251^2) drains."""
+    p, k = pk
+    m, n, K = shape
+    f = q.Field(p, k)
+    h = (p - 1) // 2
+    A = W.centred_planes(k, m, K, h, salt=m + 3)
+    B = W.centred_planes(k, K, n, h, salt=n + 4)
+    got = run_planes(torch, f, q.FMT_INT8_PLANES, A, B, m, n, K)
+    assert np.array_equal(got, oracle_gemm_from_planes(orc, p, f.poly, A, B))
+
+
 @pytest.mark.parametrize("pk,shape", [((3, 3), (200, 130, 300)), ((7, 4), (129, 64, 256)),
                                       ((13, 3), (128, 192, 1000)), ((5, 4), (77, 65, 90)),
                                       ((31, 3), (128, 64, 64 * 390 + 20))])

@@ -6,7 +6,10 @@ cudaMalloc/cudaFree would synchronise the device, a plugin that is handed
 only its inputs and outputs.  It keeps its work list in a fixed array inside
 the library.  This file checks, through the C ABI, that it returns exactly
 what qadic_batched_gemm (the workspace version) returns, on two calls in a
-row, and that a work list too large for the fixed array is refused.
+row, that two different batches issued back to back on one stream with no
+synchronisation in between both come out right, that a small mixed-field
+batch matches the CPU oracle, and that a work list too large for the fixed
+array is refused.
 
 The file name makes pytest collect it last, so a run that stops at the
 first failure has already run every other test.
@@ -22,7 +25,7 @@ from paper_0710_0510_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def _batch(torch, fields, count, seed):
+def _batch(torch, fields, count, seed, with_host=False):
     dims, fidx = W.batched_shapes(count, salt=seed)
     rng = np.random.default_rng(seed)
     A, B, descs = [], [], []
@@ -40,7 +43,16 @@ def _batch(torch, fields, count, seed):
     for (m, n, K), fi, (a, b, c) in zip(dims, fidx, offs):
         descs.append(q.GemmDesc(int(fi), int(m), int(n), int(K), dA.data_ptr() + a,
                                 dB.data_ptr() + b, dC.data_ptr() + c, int(K), int(n), int(n), 0))
+    if with_host:
+        return dA, dB, dC, descs, (dims, fidx, A, B, offs)
     return dA, dB, dC, descs
+
+
+def _reference(torch, fields, descs, dC):
+    ws = torch.empty(q.batched_workspace_size(descs), dtype=torch.uint8, device="cuda")
+    q.batched_gemm(fields, descs, ws)
+    torch.cuda.synchronize()
+    return dC.clone()
 
 
 def _call_noalloc(fields, descs, stream):
@@ -80,14 +92,66 @@ def test_noalloc_matches_workspace_version_twice():
     q.sync_status()
 
 
+def test_noalloc_back_to_back_without_sync():
+    """Two different batches on one stream, no synchronisation between the
+    calls: the second call rewrites the shared host array only after the
+    first call's upload has read it, so both results are right."""
+    import torch
+    stream = torch.cuda.current_stream()
+    fields = [q.Field(2, 8), q.Field(7, 4), q.Field(31, 2)]
+    dA, dB, dC, descs = _batch(torch, fields, 64, seed=21)
+    dA2, dB2, dC2, descs2 = _batch(torch, fields, 48, seed=22)
+    want = _reference(torch, fields, descs, dC)
+    want2 = _reference(torch, fields, descs2, dC2)
+    for _ in range(2):
+        dC.fill_(255)
+        dC2.fill_(255)
+        torch.cuda.synchronize()
+        assert _call_noalloc(fields, descs, stream) == q.OK
+        assert _call_noalloc(fields, descs2, stream) == q.OK
+        torch.cuda.synchronize()
+        assert torch.equal(dC, want)
+        assert torch.equal(dC2, want2)
+    q.sync_status()
+
+
+def test_noalloc_matches_oracle(orc):
+    import torch
+    stream = torch.cuda.current_stream()
+    fields = [q.Field(2, 8), q.Field(7, 4), q.Field(31, 2)]
+    dA, dB, dC, descs, (dims, fidx, A, B, offs) = _batch(torch, fields, 9, seed=23,
+                                                          with_host=True)
+    dC.fill_(255)
+    assert _call_noalloc(fields, descs, stream) == q.OK
+    torch.cuda.synchronize()
+    q.sync_status()
+    got = dC.cpu().numpy()
+    for (m, n, K), fi, a, b, (_, _, c) in zip(dims, fidx, A, B, offs):
+        m, n, K, f = int(m), int(n), int(K), fields[int(fi)]
+        Ai = np.transpose(a.reshape(f.k, m, K), (1, 2, 0))
+        Bi = np.transpose(b.reshape(f.k, K, n), (1, 2, 0))
+        want = np.transpose(orc.gemm(f.p, f.poly, Ai, Bi), (2, 0, 1))
+        assert np.array_equal(got[c:c + f.k * m * n].reshape(f.k, m, n), want), (m, n, K, f.p)
+
+
 def test_noalloc_rejects_work_list_beyond_fixed_array():
     import torch
     stream = torch.cuda.current_stream()
     f = q.Field(31, 2)
-    x = torch.zeros(1 << 12, dtype=torch.uint8, device="cuda")
-    # 40 products of 4096 x 4096 -> 40 * 128 * 256 tiles of 8 bytes > 8 MiB;
-    # refused before anything is read or launched
-    big = [q.GemmDesc(0, 4096, 4096, 4096, x.data_ptr(), x.data_ptr(), x.data_ptr(),
-                      4096, 4096, 4096, 0) for _ in range(40)]
+    m = n = 4096
+    K = 16
+    # Every descriptor stays inside its buffers, so even a launch would read
+    # and write only memory it owns: A holds k*m*K bytes, B k*K*n, C k*m*n
+    # (shared by all descriptors).  The size check counts tiles of the
+    # smallest shape, 32 x 16: 40 products of 4096 x 4096 give 40 * 128 * 256
+    # tiles of 8 bytes > 8 MiB, so the list is refused before anything is
+    # uploaded or launched.
+    A = torch.zeros(f.k * m * K, dtype=torch.uint8, device="cuda")
+    B = torch.zeros(f.k * K * n, dtype=torch.uint8, device="cuda")
+    C = torch.zeros(f.k * m * n, dtype=torch.uint8, device="cuda")
+    big = [q.GemmDesc(0, m, n, K, A.data_ptr(), B.data_ptr(), C.data_ptr(), K, n, n, 0)
+           for _ in range(40)]
     assert _call_noalloc([f], big, stream) == q.E_INVALID
     assert b"fixed scratch" in q.lib().qadic_last_error()
+    torch.cuda.synchronize()
+    assert int(C.sum()) == 0
