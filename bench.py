@@ -52,8 +52,8 @@ PLANE_KERNEL = "gemm_planes_pair_kernel<2,128>"
 MEASURED_TRAFFIC = {
     PLANE_KERNEL: {
         "file": "paper_0710_0510_gb300/csrc/k_gemm_tc.cu",
-        "code_sha256": None,
-        "bytes": None, "n": 4096},
+        "code_sha256": "25bc66580d5ad95193cecc7cd4f7bd7c40a9b282cccba529aaf82540ddac280b",
+        "bytes": 467632384 + 34291200, "n": 4096},
 }
 
 

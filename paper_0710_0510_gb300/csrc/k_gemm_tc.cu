@@ -435,7 +435,8 @@ gemm_planes_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
 }
 
 // ---------------------------------------------------------------------------
-// CTA-pair form (cta_group::2), k = 2.  A cluster of two CTAs on two SMs
+// CTA-pair form (cta_group::2), k = 2, for K within one exact FP32 chunk
+// (no in-place reduction).  A cluster of two CTAs on two SMs
 // computes a 256 x BN unit: the leader (cluster rank 0) takes output rows
 // 0..127 of the unit, the peer rows 128..255.  One MMA of M = 256 per A plane
 // and 16-wide K step covers both: each CTA holds its own 128 rows of A_i and
@@ -448,11 +449,11 @@ gemm_planes_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
 //               TMA); the leader announces the transaction bytes of both.
 //   warp 1      both CTAs allocate the pair's tensor memory; the leader's lane
 //               0 issues the MMAs and commits each stage's completion to the
-//               "empty" barriers, and each chunk's or tile's to the
-//               "accumulators ready" barriers, of both CTAs.
+//               "empty" barriers, and each tile's to the "accumulators
+//               ready" barriers, of both CTAs.
 //   warps 2-9   both CTAs: epilogue of its own rows; every epilogue warp of
-//               both CTAs arrives on the leader's "drained" / "read out"
-//               barriers (one arrival per warp).
+//               both CTAs arrives on the leader's "read out" barrier (one
+//               arrival per warp).
 // Waits are bounded; an expired wait raises the abort flag of both CTAs.
 // After an abort each CTA gives in-flight copies a bounded time to land
 // before the final cluster barrier, then both free tensor memory and exit.
@@ -499,9 +500,8 @@ gemm_planes_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_co
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = (uint64_t *)(smem + CF::STAGES * CF::STAGE);
     uint64_t *empty = full + CF::STAGES;
-    uint64_t *acc_full = empty + CF::STAGES;   // MMAs of a chunk / a tile completed
-    uint64_t *acc_empty = acc_full + 1;        // both CTAs' epilogues finished a drain
-    uint64_t *tmem_free = acc_empty + 1;       // both CTAs read a tile's accumulators out
+    uint64_t *acc_full = empty + CF::STAGES;   // a tile's MMAs completed
+    uint64_t *tmem_free = acc_full + 1;        // both CTAs read a tile's accumulators out
     uint64_t *mma_done = tmem_free + 1;
     uint32_t *tmem_slot = (uint32_t *)(mma_done + 1);
     volatile uint32_t *abort_flag = (volatile uint32_t *)(tmem_slot + 1);
@@ -515,7 +515,6 @@ gemm_planes_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_co
             ptx::mbar_init(&empty[s], 1);
         }
         ptx::mbar_init(acc_full, 1);
-        ptx::mbar_init(acc_empty, 2 * kEpiWarps);
         ptx::mbar_init(tmem_free, 2 * kEpiWarps);
         ptx::mbar_init(mma_done, 1);
         *abort_flag = 0;
@@ -585,7 +584,7 @@ gemm_planes_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_co
                 ptx::mma_commit_pair_at(peer_bar);
             };
             int64_t it = 0;
-            int drain = 0, tcount = 0;
+            int tcount = 0;
             bool ok = true;
             for (int unit = unit0; unit < P.nunits && ok; unit += unit_step, ++tcount) {
                 if (tcount > 0) {   // both CTAs have read the previous tile's accumulators
@@ -613,15 +612,6 @@ gemm_planes_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_co
                                                operand_desc(a_tile(stage, i)) + 2 * kk, bd + 2 * kk,
                                                idesc, (kb == 0 && kk == 0) ? 0u : 1u);
                     commit_both(&empty[stage], peer_empty0 + 8 * stage);
-                    if ((kb + 1) % P.chunk_kb == 0 && kb + 1 < nkb) {
-                        commit_both(acc_full, peer_acc_full);
-                        if (!ptx::mbar_wait_cluster(acc_empty, (uint32_t)drain & 1)) {
-                            ok = false;
-                            break;
-                        }
-                        ptx::tc_fence_after();
-                        ++drain;
-                    }
                 }
                 if (ok) commit_both(acc_full, peer_acc_full);   // tile complete
             }
@@ -640,8 +630,6 @@ gemm_planes_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_co
         const int quarter = warp & 3;
         const int col_base = (ew / 4) * CF::HALF;
         const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + col_base;
-        const int ndrain = nkb > 0 ? (nkb - 1) / P.chunk_kb : 0;
-        const uint32_t lead_acc_empty = in_leader(acc_empty);
         const uint32_t lead_tmem_free = in_leader(tmem_free);
         float foldf[(KP - 1) * KP + 1];
 #pragma unroll
@@ -658,16 +646,6 @@ gemm_planes_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_co
             int um, tn;
             unit_coords(unit, P, um, tn);
             const int tm = um * 2 + (int)rank;
-            for (int d = 0; d < ndrain; ++d, ++phase) {
-                if (!ready(phase) || *abort_flag) {
-                    ok = false;
-                    break;
-                }
-                ptx::tc_fence_after();
-                drain_accumulators<CF, BN>(tbase, P);
-                arrive_warp(lead_acc_empty);
-            }
-            if (!ok) break;
             if (!ready(phase) || *abort_flag) {
                 ok = false;
                 break;
@@ -1152,7 +1130,8 @@ int launch_tc_pair(const Field &f, int64_t m, int64_t n, int64_t K, const void *
     const int64_t hh = (int64_t)f.h * f.h;
     const int64_t chunk = ((1ll << 24) - 2 * (int64_t)f.p) / hh;
     P.chunk_kb = (int32_t)std::min<int64_t>(chunk / BK, 1 << 30);
-    if (P.chunk_kb < 1) return set_error(QADIC_E_OVERFLOW, "exact FP32 chunk below one K-block");
+    if (P.chunk_kb < P.nkb)
+        return set_error(QADIC_E_UNSUPPORTED, "pair kernel: K beyond one exact FP32 chunk");
     P.p = f.p;
     P.m32 = make_mod_small(f.p);
     P.pf = (float)f.p;
@@ -1281,8 +1260,14 @@ int launch_gemm_planes_tc_strided(const Field &f, int64_t m, int64_t n, int64_t 
         return QADIC_OK;
     }
     if (f.k == 2) {
-        // two tile rows or more: CTA pairs on 256-row units
-        if (m > BM)
+        // Two tile rows or more and no in-place reduction on the way through
+        // K: CTA pairs on 256-row units.  Where the exact FP32 chunk is
+        // shorter than K, both SMs of a pair wait for every reduction, and
+        // the one-CTA kernel measured faster (GF(251^2), n = 16384: 21.4 ms
+        // against 22.3 ms).
+        const int64_t hh = (int64_t)f.h * f.h;
+        const int64_t chunk_kb = ((1ll << 24) - 2 * (int64_t)f.p) / hh / BK;
+        if (m > BM && (K + BK - 1) / BK <= chunk_kb)
             return launch_tc_pair<2, 128>(f, m, n, K, A, lda, a_plane, B, ldb, b_plane, C, ldc,
                                           c_plane, stream);
         return launch_tc<2, 128>(f, m, n, K, A, lda, a_plane, B, ldb, b_plane, C, ldc, c_plane, stream);

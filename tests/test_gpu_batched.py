@@ -255,6 +255,37 @@ def test_batched_gf256_chunks_every_configuration(torch, orc, restore_tiles, con
 
 
 @pytest.mark.parametrize("converted", [True, False])
+@pytest.mark.parametrize("pk", [(31, 2), (7, 4), (2, 8)])
+def test_batched_fp8_fields_all_max(torch, orc, pk, converted):
+    """The fields whose coefficients run as fp8 e4m3 (p <= 31), every
+    coefficient at -h (the same sign: every plane product is h^2 > 0), K up
+    to 4096: the plane sums reach k K h^2 (1.8e6 for GF(31^2)), so any loss
+    of low-order bits in the tensor-core accumulation shows."""
+    p, k = pk
+    f = q.Field(p, k)
+    h = (p - 1) // 2 if p > 2 else 1
+    code = p - h if p > 2 else 1          # least non-negative representative of -h (p = 2: 1)
+    shapes = [(64, 64, 4096), (33, 17, 4096), (16, 16, 1000), (130, 70, 2049)]
+    bt = Batch(torch, [f], shapes, [0] * len(shapes), seed=p, converted=converted)
+    for i in range(len(shapes)):
+        bt.A[i][:] = code
+        bt.B[i][:] = code
+    bt.dA[:] = torch.from_numpy(np.concatenate([x.ravel() for x in bt.A])).cuda()
+    bt.dB[:] = torch.from_numpy(np.concatenate([x.ravel() for x in bt.B])).cuda()
+    bt.run()
+    q.sync_status()
+    for i in range(len(shapes)):
+        got = bt.result(i)
+        m, n, K = shapes[i]
+        want = bt.expected(orc, i) if m * n * K <= 64 * 64 * 4096 else None
+        if want is None:   # every entry is the same: compare one against the oracle
+            one = orc.gemm(p, f.poly, np.transpose(bt.A[i][:, :1, :], (1, 2, 0)),
+                           np.transpose(bt.B[i][:, :, :1], (1, 2, 0)))
+            want = np.broadcast_to(np.transpose(one, (2, 0, 1)), got.shape)
+        assert np.array_equal(got, want), (pk, shapes[i])
+
+
+@pytest.mark.parametrize("converted", [True, False])
 def test_batched_maximum_sizes(torch, orc, converted):
     """The largest product the batched entry point takes (m = n = K = 4096)
     beside small ones, GF(31^2) and GF(2^8): sampled entries and whole edge

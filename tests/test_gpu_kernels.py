@@ -351,18 +351,21 @@ def test_gemm_planes_sums_at_the_fp32_limit(torch, orc, p, val):
     assert (got == got[:, :1, :1]).all()
 
 
-@pytest.mark.parametrize("p,val", [(251, 125), (251, -125), (101, 50)])
-def test_gemm_planes_pair_sums_at_the_fp32_limit(torch, orc, p, val):
-    """k = 2 with m > 128 runs on CTA pairs (one M = 256 MMA per A plane, the
-    peer's rows in the peer's tensor memory).  All coefficients at +-h with
-    one sign: each split accumulator grows by h^2 per K step and reaches the
-    2^24 bound at the end of every exact chunk; K crosses two drains.  Rows of
-    both CTAs of a pair (0, 127 | 128, 255) and of a second pair are checked."""
+@pytest.mark.parametrize("p,val", [(251, 125), (251, -125), (101, 50), (101, -50)])
+@pytest.mark.parametrize("extra", [0, 1])
+def test_gemm_planes_pair_sums_at_the_fp32_limit(torch, orc, p, val, extra):
+    """k = 2, m > 128.  extra = 0: K is the longest with no in-place
+    reduction (a whole number of exact chunks' worth of K-blocks), which runs
+    on CTA pairs (one M = 256 MMA per A plane, the peer's rows in the peer's
+    tensor memory); all coefficients at +-h with one sign, so each split
+    accumulator ends at the 2^24 bound.  extra = 1: one K element more, which
+    takes the one-CTA kernel with one in-place reduction.  Rows of both CTAs
+    of a pair (0, 127 | 128, 255) and of a second pair are checked."""
     k = 2
     f = q.Field(p, k)
     h2 = ((p - 1) // 2) ** 2
-    chunk = (2 ** 24 - 2 * p) // h2 // 64 * 64          # K-blocks of 64 per split chunk
-    m, n, K = 384, 256, 2 * chunk + 64
+    K = (2 ** 24 - 2 * p) // h2 // 64 * 64 + extra
+    m, n = 384, 256
     A = np.full((k, m, K), val, np.int8)
     B = np.full((k, K, n), val, np.int8)
     got = run_planes(torch, f, q.FMT_INT8_PLANES, A, B, m, n, K)
@@ -376,8 +379,9 @@ def test_gemm_planes_pair_sums_at_the_fp32_limit(torch, orc, p, val):
 @pytest.mark.parametrize("pk,shape", [((101, 2), (257, 130, 777)), ((251, 2), (512, 200, 2179)),
                                       ((101, 2), (1000, 72, 136)), ((31, 2), (300, 520, 64))])
 def test_gemm_planes_pair_shapes(torch, orc, pk, shape):
-    """CTA-pair path on ragged shapes: odd tile-row counts (the last pair's
-    peer rows wholly outside A), ragged n and K, GF(251^2) drains."""
+    """k = 2 with m > 128 on ragged shapes: odd tile-row counts (the last
+    pair's peer rows wholly outside A), ragged n and K; GF(251^2) with
+    K = 2179 crosses exact chunks and takes the one-CTA kernel."""
     p, k = pk
     m, n, K = shape
     f = q.Field(p, k)
