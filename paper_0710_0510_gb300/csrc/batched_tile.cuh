@@ -1,8 +1,8 @@
-// Shared pieces of the two batched GF(p^k) product kernels (k_batched.cu:
-// operand bytes staged through registers; k_batched_async.cu: operands
-// converted once, tiles copied with cp.async): the work-list layout, the
-// tile shapes, the warp-level MMA step, the exact-chunk reduction and the
-// mod p / mod P epilogue.
+// Shared pieces of the batched GF(p^k) product kernels: the work-list layout
+// (both), and for the register-staged kernel (k_batched.cu) the tile
+// shapes, the warp-level MMA step, the exact-chunk reduction and the mod p /
+// mod P epilogue; the tensor-core path (k_batched_tc.cu) adds its tile
+// records and launch helpers.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -25,9 +25,8 @@ struct BFieldParams {
     uint32_t p, k, h, m32;
     float pf, inv_pf;
     int32_t chunk_k;               // K elements per exact FP32 chunk (capped)
-    int32_t chunk_k16;             // the same for f16 accumulators (GF(2^8) only)
-    int32_t f16;                   // GF(2^8): f16 accumulators (see the converted-operand kernel)
-    int32_t fp8;                   // p <= 31: operands converted to fp8 e4m3 (|centred| <= 15, exact)
+    int32_t fp8;                   // p <= 31: tensor-core operands fp8 e4m3 (|centred| <= 15, exact)
+    int32_t tc_chunk_ks;           // tensor-core path: 32-byte K-blocks per exact FP32 chunk
     uint8_t fold[kMaxK * kMaxK];   // X^(k+t) mod P, row t (k coefficients)
     uint8_t fold2[kMaxK];          // p = 2: row t of `fold` as a bit mask (coefficient i at bit i)
 };
@@ -36,10 +35,10 @@ struct BProd {
     const uint8_t *A;
     const uint8_t *B;
     uint8_t *C;
-    const uint16_t *A16;           // converted operands, or null: 16-bit A [k][m][kp] and
-    const uint16_t *B16;           // B [k][K][np]; fp8 fields: bytes, A [k][m][kp], B^T [k][n][kp]
+    const uint16_t *A16;           // tensor-core path: the converted operands in their blocked
+    const uint16_t *B16;           // layout (k_batched_tc.cu); null on the register-staged path
     int32_t m, n, K, lda, ldb, ldc;
-    int32_t kp, np;                // row lengths: 16-bit K up to 8 and n up to 8; fp8: K up to 16
+    int32_t kp, np;                // tensor-core path: 32-byte K-blocks, output columns per tile
     int32_t field, cfg;            // field index, tile configuration index
 };
 
@@ -47,6 +46,22 @@ struct BTile {
     int32_t prod;
     int16_t tm, tn;
 };
+
+// One tile of the tensor-core path's work list, complete in itself (the
+// roles of the product kernel read it with independent loads, one tile
+// ahead, instead of a chain tile -> product -> field).
+struct TcRec {
+    const uint8_t *a;    // the tile's A blocks: K-blocks of k planes x rows8 x 32 bytes
+    const uint8_t *b;    // the tile's B blocks: K-blocks of k planes x BN x 32 bytes
+    uint8_t *c;          // output byte (row tm*128, column tn*BN) of plane 0
+    int64_t c_plane;     // bytes between output planes (m * ldc)
+    int32_t ldc;
+    int16_t rows, cols;  // valid rows (<= 128) and columns (<= BN) of the tile
+    int16_t ks;          // 32-byte K-blocks
+    int16_t rows8;       // rows rounded up to 8
+    int16_t field, k;
+};
+static_assert(sizeof(TcRec) == 48, "TcRec layout");
 
 struct BHeader {
     uint32_t counter;
@@ -76,15 +91,8 @@ struct TileCfg {
     static constexpr int LDA = BK + 8;               // 16-bit elements per A_s row
     static constexpr int LDB = BN + 8;               // 16-bit elements per B_s row
     static constexpr int SMEM = (KP * BM * LDA + KP * BK * LDB) * 2;
-    // cp.async stages of the converted-operand kernel: more where a stage is
-    // small (little MMA work per K-block to hide a copy behind)
-    static constexpr int NSTAGE = SMEM <= 8192 ? 4 : SMEM <= 16384 ? 3 : 2;
     static_assert(MT >= 1 && NT >= 1 && BK % 16 == 0, "tile shape");
 };
-
-inline int async_stages(size_t stage_bytes) {
-    return stage_bytes <= 8192 ? 4 : stage_bytes <= 16384 ? 3 : 2;
-}
 
 // Candidate (BM, BN, BK) per k; index 0 is the default.  Every candidate is
 // at least 32 x 16 (the work-list bound); configuration 0 is kMinBK deep.
@@ -136,16 +144,6 @@ __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-// m16n8k16 with f16 operands and f16 accumulators (two half2 registers).
-__device__ __forceinline__ void mma_f16_16816(uint32_t (&d)[2], const uint32_t (&a)[4],
-                                              const uint32_t (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f16.f16.f16.f16 {%0,%1}, {%2,%3,%4,%5}, {%6,%7}, "
-        "{%0,%1};"
-        : "+r"(d[0]), "+r"(d[1])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
 // Centred representative of a coefficient byte: c mod p in [-(p-1)/2, (p-1)/2]
 // (Eq. 3's centred representation), {0, 1} for p = 2.
 __device__ __forceinline__ int centred_int(uint32_t c, const BFieldParams &F) {
@@ -165,54 +163,12 @@ __device__ __forceinline__ uint8_t fp8_bits(uint32_t c, const BFieldParams &F) {
 
 inline bool fp8_field(uint32_t p) { return p <= 31; }
 
-// m16n8k32 with fp8 e4m3 operands (four per register), FP32 or f16
-// accumulators.  On GB300 the legacy path runs these at about 3.6x the
-// bf16 m16n8k16 rate (2177 against 600 TFLOP/s, measured).
-__device__ __forceinline__ void mma_e4m3_f32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k32.row.col.f32.e4m3.e4m3.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
+// Accumulators of one warp: 2k-1 sets of MT x NT m16n8 FP32 fragments.
+template <typename T>
+using AccArray = float[T::NACC][T::MT][T::NT][4];
 
-__device__ __forceinline__ void mma_e4m3_f16(uint32_t (&d)[2], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k32.row.col.f16.e4m3.e4m3.f16 {%0,%1}, {%2,%3,%4,%5}, {%6,%7}, "
-        "{%0,%1};"
-        : "+r"(d[0]), "+r"(d[1])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-// fp8 tiles: K-blocks of at least 32 (one m16n8k32 step), rows of BK + 16
-// bytes (A [KP][BM], B^T [KP][BN], both K-major) so that ldmatrix rows fall
-// in distinct banks.
-constexpr int fp8_bk(int bk) { return bk < 32 ? 32 : bk; }
-
-template <int KP, int BM_, int BN_, int BK_>
-struct TileCfg8 {
-    using W = TileCfg<KP, BM_, BN_, 32>;   // warp layout and accumulators as the 16-bit tiles
-    static constexpr int BM = BM_, BN = BN_, BK = fp8_bk(BK_);
-    static constexpr int WM = W::WM, WN = W::WN, MT = W::MT, NT = W::NT, NACC = W::NACC;
-    static constexpr int LDA = BK + 16, LDB = BK + 16;   // bytes
-    static constexpr int SMEM = KP * BM * LDA + KP * BN * LDB;
-    static constexpr int NSTAGE = SMEM <= 8192 ? 4 : SMEM <= 16384 ? 3 : 2;
-};
-
-inline size_t tile_smem_bytes8(uint32_t k, int cfg) {
-    const TileShape t = tile_shape_of(k, cfg);
-    const int bk = fp8_bk(t.bk);
-    return (size_t)k * t.bm * (bk + 16) + (size_t)k * t.bn * (bk + 16);
-}
-
-
-// Accumulators of one warp: 2k-1 sets of MT x NT m16n8 fragments, FP32 (four
-// registers each) or, with F16, f16 pairs (two registers each).
-template <typename T, bool F16>
-using AccArray = std::conditional_t<F16, uint32_t, float>[T::NACC][T::MT][T::NT][F16 ? 2 : 4];
-
-template <typename T, bool F16>
-__device__ __forceinline__ void acc_zero(AccArray<T, F16> &acc) {
+template <typename T>
+__device__ __forceinline__ void acc_zero(AccArray<T> &acc) {
 #pragma unroll
     for (int t = 0; t < T::NACC; ++t)
 #pragma unroll
@@ -220,13 +176,13 @@ __device__ __forceinline__ void acc_zero(AccArray<T, F16> &acc) {
 #pragma unroll
             for (int b = 0; b < T::NT; ++b)
 #pragma unroll
-                for (int e = 0; e < (F16 ? 2 : 4); ++e) acc[t][a][b][e] = 0;
+                for (int e = 0; e < 4; ++e) acc[t][a][b][e] = 0.f;
 }
 
 // One 16-deep step of the k^2 plane products: plane i of A times plane j of
 // B accumulates into C_{i+j}.  As is [KP][BM][LDA], Bs is [KP][BK][LDB].
-template <int KP, typename T, bool F16>
-__device__ __forceinline__ void tile_mma_step(AccArray<T, F16> &acc, const uint16_t *As,
+template <int KP, typename T>
+__device__ __forceinline__ void tile_mma_step(AccArray<T> &acc, const uint16_t *As,
                                               const uint16_t *Bs, int ks, int wm, int wn,
                                               int lane) {
     uint32_t bfr[KP][T::NT][2];
@@ -252,59 +208,14 @@ __device__ __forceinline__ void tile_mma_step(AccArray<T, F16> &acc, const uint1
 #pragma unroll
             for (int mt = 0; mt < T::MT; ++mt)
 #pragma unroll
-                for (int nt = 0; nt < T::NT; ++nt) {
-                    if constexpr (F16)
-                        mma_f16_16816(acc[i + j][mt][nt], afr[mt], bfr[j][nt]);
-                    else
-                        mma_bf16_16816(acc[i + j][mt][nt], afr[mt], bfr[j][nt]);
-                }
-    }
-}
-
-// One 32-deep step of the k^2 plane products on fp8 tiles (bytes).
-template <int KP, typename T8, bool F16>
-__device__ __forceinline__ void tile_mma_step8(AccArray<typename T8::W, F16> &acc, const uint8_t *As,
-                                               const uint8_t *Bs, int ks, int wm, int wn, int lane) {
-    using T = T8;
-    uint32_t bfr[KP][T::NT][2];
-#pragma unroll
-    for (int j = 0; j < KP; ++j)
-#pragma unroll
-        for (int nt = 0; nt < T::NT; ++nt) {
-            // B^T rows (output columns) n, bytes k: matrix 0 = k 0-15, matrix 1 = k 16-31
-            const uint8_t *src = Bs + (j * T::BN + wn * T::WN + nt * 8 + (lane % 8)) * T::LDB + ks * 32 +
-                                 ((lane / 8) % 2) * 16;
-            asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];"
-                         : "=r"(bfr[j][nt][0]), "=r"(bfr[j][nt][1])
-                         : "r"((uint32_t)__cvta_generic_to_shared(src)));
-        }
-#pragma unroll
-    for (int i = 0; i < KP; ++i) {
-        uint32_t afr[T::MT][4];
-#pragma unroll
-        for (int mt = 0; mt < T::MT; ++mt) {
-            const uint8_t *src =
-                As + (i * T::BM + wm * T::WM + mt * 16 + (lane % 16)) * T::LDA + ks * 32 + (lane / 16) * 16;
-            ldsm_x4((uint32_t)__cvta_generic_to_shared(src), afr[mt][0], afr[mt][1], afr[mt][2], afr[mt][3]);
-        }
-#pragma unroll
-        for (int j = 0; j < KP; ++j)
-#pragma unroll
-            for (int mt = 0; mt < T::MT; ++mt)
-#pragma unroll
-                for (int nt = 0; nt < T::NT; ++nt) {
-                    if constexpr (F16)
-                        mma_e4m3_f16(acc[i + j][mt][nt], afr[mt], bfr[j][nt]);
-                    else
-                        mma_e4m3_f32(acc[i + j][mt][nt], afr[mt], bfr[j][nt]);
-                }
+                for (int nt = 0; nt < T::NT; ++nt) mma_bf16_16816(acc[i + j][mt][nt], afr[mt], bfr[j][nt]);
     }
 }
 
 // Exact-chunk boundary: every accumulator x becomes x - p rint(x / p), an
 // integer of magnitude <= p / 2 congruent to x.
-template <typename T, bool F16>
-__device__ __forceinline__ void tile_chunk_reduce(AccArray<T, F16> &acc, const BFieldParams &F) {
+template <typename T>
+__device__ __forceinline__ void tile_chunk_reduce(AccArray<T> &acc, const BFieldParams &F) {
 #pragma unroll
     for (int t = 0; t < T::NACC; ++t)
 #pragma unroll
@@ -312,36 +223,17 @@ __device__ __forceinline__ void tile_chunk_reduce(AccArray<T, F16> &acc, const B
 #pragma unroll
             for (int b = 0; b < T::NT; ++b)
 #pragma unroll
-                for (int e = 0; e < (F16 ? 2 : 4); ++e) {
-                    if constexpr (F16) {
-                        float2 x = __half22float2(*reinterpret_cast<__half2 *>(&acc[t][a][b][e]));
-                        x.x = fmaf(-F.pf, rintf(x.x * F.inv_pf), x.x);
-                        x.y = fmaf(-F.pf, rintf(x.y * F.inv_pf), x.y);
-                        const __half2 h = __floats2half2_rn(x.x, x.y);
-                        acc[t][a][b][e] = *reinterpret_cast<const uint32_t *>(&h);
-                    } else {
-                        const float x = acc[t][a][b][e];
-                        acc[t][a][b][e] = fmaf(-F.pf, rintf(x * F.inv_pf), x);
-                    }
+                for (int e = 0; e < 4; ++e) {
+                    const float x = acc[t][a][b][e];
+                    acc[t][a][b][e] = fmaf(-F.pf, rintf(x * F.inv_pf), x);
                 }
 }
 
 // Epilogue: each C_t exactly mod p, then the fold mod P (Alg. 4, fold step,
 // in coefficient form: out_i = mu_i + sum_{t >= k} mu_t (X^t mod P)_i), and
 // the k output planes written as bytes.
-// Value of accumulator element e of fragment (t, mt, nt).
-template <typename T, bool F16>
-__device__ __forceinline__ float acc_value(const AccArray<T, F16> &acc, int t, int mt, int nt, int e) {
-    if constexpr (F16) {
-        const __half2 h = *reinterpret_cast<const __half2 *>(&acc[t][mt][nt][e >> 1]);
-        return (e & 1) ? __high2float(h) : __low2float(h);
-    } else {
-        return acc[t][mt][nt][e];
-    }
-}
-
-template <int KP, typename T, bool F16>
-__device__ __forceinline__ void tile_epilogue(const AccArray<T, F16> &acc, const BProd &P,
+template <int KP, typename T>
+__device__ __forceinline__ void tile_epilogue(const AccArray<T> &acc, const BProd &P,
                                               const BFieldParams &F, int row0, int col0, int wm,
                                               int wn, int lane) {
     if (F.p == 2) {
@@ -363,8 +255,8 @@ __device__ __forceinline__ void tile_epilogue(const AccArray<T, F16> &acc, const
                     uint32_t bits = 0;
 #pragma unroll
                     for (int t = 0; t < T::NACC; ++t) {
-                        const uint32_t b0 = __float_as_uint(acc_value<T, F16>(acc, t, mt, nt, 2 * eh) + 12582912.0f);
-                        const uint32_t b1 = __float_as_uint(acc_value<T, F16>(acc, t, mt, nt, 2 * eh + 1) + 12582912.0f);
+                        const uint32_t b0 = __float_as_uint(acc[t][mt][nt][2 * eh] + 12582912.0f);
+                        const uint32_t b1 = __float_as_uint(acc[t][mt][nt][2 * eh + 1] + 12582912.0f);
                         bits |= ((b0 & 1u) | ((b1 & 1u) << 16)) << t;
                     }
                     uint32_t out = bits & (kLow | (kLow << 16));
@@ -399,13 +291,7 @@ __device__ __forceinline__ void tile_epilogue(const AccArray<T, F16> &acc, const
                 uint32_t mu[T::NACC];
 #pragma unroll
                 for (int t = 0; t < T::NACC; ++t) {
-                    float x;
-                    if constexpr (F16) {
-                        const __half2 h = *reinterpret_cast<const __half2 *>(&acc[t][mt][nt][e >> 1]);
-                        x = (e & 1) ? __high2float(h) : __low2float(h);
-                    } else {
-                        x = acc[t][mt][nt][e];
-                    }
+                    const float x = acc[t][mt][nt][e];
                     float r = fmaf(-F.pf, floorf(x * F.inv_pf), x);
                     if (r < 0.f) r += F.pf;
                     if (r >= F.pf) r -= F.pf;
@@ -425,12 +311,21 @@ __device__ __forceinline__ void tile_epilogue(const AccArray<T, F16> &acc, const
             }
 }
 
-// Launch helpers of the converted-operand kernels (k_batched_async.cu).
-int prepare_async_kernel();
-int64_t async_grid(size_t smem, int64_t ntiles);
-size_t async_smem_bytes(uint32_t k, int cfg, bool fp8);
-int launch_convert(const uint8_t *ws, int64_t nitems, cudaStream_t stream);
-int launch_async(uint8_t *ws, int64_t grid, size_t smem, cudaStream_t stream);
+// Output columns per tile on the tensor-core path (k_batched_tc.cu): the
+// MMA N = k BN is 128 (80-112 for k = 3, 5, 6, 7) and the 2k-1 accumulators
+// (four split ones for k = 2) fit in 256 tensor-memory columns, so two
+// tiles' accumulators fit at once.
+__host__ __device__ constexpr int tc_bn(uint32_t k) {
+    return k <= 1 ? 128 : k == 2 ? 64 : k <= 4 ? 32 : 16;
+}
+
+// Launch helpers of the tensor-core path (k_batched_tc.cu).
+int tc_stage_layout(uint32_t kmax, int *slot_bytes, int *a_bytes, int *stages);
+int prepare_tc_kernel();
+int64_t tc_grid(int64_t ntiles);
+int launch_tc_convert(const uint8_t *ws, int64_t nitems, cudaStream_t stream);
+int launch_tc_products(const uint8_t *ws, int64_t grid, int slot_bytes, int a_bytes, int stages,
+                       int *status, cudaStream_t stream);
 
 }  // namespace bt
 }  // namespace qadic

@@ -4,21 +4,26 @@
 // sums C_t = sum_{i+j=t} A_i B_j, reduced mod p and folded mod P with
 // X^t mod P.  The host lays a work list into the caller's workspace: field
 // parameters, product descriptors and one entry per output tile, sorted by
-// decreasing work.  A grid of (SMs x resident blocks) CTAs pulls tiles with
-// one atomicAdd each (no waits of any kind), so thousands of uneven products
-// (m, n, K in [16, 256], three different fields) share one launch.
+// field and decreasing work, so thousands of uneven products (m, n, K in
+// [16, 256], several fields) share one launch.  Two kernels run it:
 //
-// Per tile: uint8 coefficient tiles are staged in shared memory as centred
-// bf16 (exact small integers), multiplied with warp-level mma.sync
-// (m16n8k16, bf16 -> f32; the tiles are too small for 128-row tcgen05
-// MMAs), accumulated exactly in FP32 registers (every partial sum stays
-// within 2^24; at each exact chunk the accumulators are reduced mod p in
-// place), then reduced mod p, folded and written as uint8 planes.
+//   * with room in the workspace for converted operands, the tensor-core
+//     path of k_batched_tc.cu: one conversion launch, then a persistent
+//     tcgen05 kernel over 128-row tiles (fp8 or bf16 operands, FP32
+//     accumulators in tensor memory);
+//   * with the work list alone (and in the allocation-free entry point), the
+//     register-staged kernel below: uint8 coefficient tiles staged in shared
+//     memory as centred bf16 (exact small integers), multiplied with
+//     warp-level mma.sync (m16n8k16, bf16 -> f32), accumulated exactly in
+//     FP32 registers (at each exact chunk the accumulators are reduced mod p
+//     in place), then reduced mod p, folded and written as uint8 planes; a
+//     grid of (SMs x resident blocks) CTAs pulls tiles with one atomicAdd each.
 //
-// Tile shape (BM x BN) and K-block size BK are picked per k from a short
-// list of candidates whose 2k-1 accumulator sets fit in registers: index 0
-// by default, or whichever qadic_batched_autotune measured fastest on the
-// caller's own batch (qadic_batched_select_tiles sets one by hand).
+// The register-staged kernel's tile shape (BM x BN) and K-block size BK are
+// picked per k from a short list of candidates whose 2k-1 accumulator sets
+// fit in registers: index 0 by default, or whichever qadic_batched_autotune
+// measured fastest on the caller's own batch (qadic_batched_select_tiles
+// sets one by hand).
 #include <algorithm>
 #include <cstring>
 #include <map>
@@ -131,8 +136,8 @@ __device__ __forceinline__ void run_tile(const BProd &P, const BFieldParams &F, 
     const int wm = warp / 2, wn = warp % 2;
     const int row0 = tm * T::BM, col0 = tn * T::BN;
 
-    AccArray<T, false> acc;
-    acc_zero<T, false>(acc);
+    AccArray<T> acc;
+    acc_zero<T>(acc);
     const int nkb = (P.K + BK - 1) / BK;
     const int chunk_blocks = max(1, F.chunk_k / BK);
     Stager<KP, T> stage;
@@ -143,10 +148,10 @@ __device__ __forceinline__ void run_tile(const BProd &P, const BFieldParams &F, 
         __syncthreads();
         if (kb + 1 < nkb) stage.load(P, row0, col0, (kb + 1) * BK);   // in flight during the MMAs
 #pragma unroll 1
-        for (int ks = 0; ks < BK / 16; ++ks) tile_mma_step<KP, T, false>(acc, As, Bs, ks, wm, wn, lane);
-        if ((kb + 1) % chunk_blocks == 0 && kb + 1 < nkb) tile_chunk_reduce<T, false>(acc, F);
+        for (int ks = 0; ks < BK / 16; ++ks) tile_mma_step<KP, T>(acc, As, Bs, ks, wm, wn, lane);
+        if ((kb + 1) % chunk_blocks == 0 && kb + 1 < nkb) tile_chunk_reduce<T>(acc, F);
     }
-    tile_epilogue<KP, T, false>(acc, P, F, row0, col0, wm, wn, lane);
+    tile_epilogue<KP, T>(acc, P, F, row0, col0, wm, wn, lane);
 }
 
 // Not inlined: each k is register-allocated on its own (its configurations
@@ -235,15 +240,19 @@ void field_params(const Field &f, BFieldParams &F) {
     F.pf = (float)f.p;
     F.inv_pf = 1.0f / (float)f.p;
     F.chunk_k = (int32_t)std::min<int64_t>(f.k_chunk_f32, 1 << 30);
-    // Converted-operand kernel: p <= 31 runs on fp8 e4m3 operands (exact for
-    // |centred| <= 15), the rest on bf16.  GF(2^8) also uses f16 accumulators.
-    // The planes hold 0 and 1, so a chunk adds at most k per K element to an
-    // accumulator (at most k plane products meet in one C_t), and after a
-    // chunk reduction |x| <= 1: 1 + k chunk <= 2048 keeps every partial sum
-    // an integer that f16 holds exactly, in whatever order it is added.
-    F.f16 = f.p == 2 && f.k == 8;
+    // Tensor-core path: p <= 31 runs on fp8 e4m3 operands (exact for
+    // |centred| <= 15), the rest on bf16.
     F.fp8 = fp8_field(f.p);
-    F.chunk_k16 = F.f16 ? (int32_t)(2047 / f.k) : F.chunk_k;
+    // Tensor-core path: FP32 accumulators exact while |sum| <= 2^24; a drained
+    // residue is below 2p and a K element adds at most h^2 to an accumulator
+    // of k = 1 or of the split k = 2 layout, k h^2 with shared accumulators
+    // (p = 2: the planes hold 0 and 1, h = 1).
+    {
+        const int64_t hh = (int64_t)f.h * f.h;
+        const int64_t growth = (f.k <= 2 ? 1 : (int64_t)f.k) * hh;
+        const int64_t elems = ((1ll << 24) - 2 * (int64_t)f.p) / growth;
+        F.tc_chunk_ks = (int32_t)std::min<int64_t>(elems / (F.fp8 ? 32 : 16), 1 << 30);
+    }
     for (uint32_t t = 0; t + 1 < f.k; ++t) {
         F.fold2[t] = 0;
         for (uint32_t c = 0; c < f.k; ++c) {
@@ -295,12 +304,13 @@ struct Layout {
 
 // Work list (header, fields, products, tiles), then, for the converted-
 // operand kernels, conv_bytes of 16-bit operands.
-Layout layout_for(int64_t count, int64_t ntiles, size_t conv_bytes = 0, int64_t conv_items = 0) {
+Layout layout_for(int64_t count, int64_t ntiles, size_t conv_bytes = 0, int64_t conv_items = 0,
+                  size_t tile_bytes = sizeof(BTile)) {
     Layout L;
     L.fields_off = kHeaderBytes;
     L.prods_off = align_up(L.fields_off + kMaxFields * sizeof(BFieldParams), 256);
     L.tiles_off = align_up(L.prods_off + count * sizeof(BProd), 256);
-    L.order_off = align_up(L.tiles_off + ntiles * sizeof(BTile), 256);
+    L.order_off = align_up(L.tiles_off + ntiles * tile_bytes, 256);
     L.conv_off = align_up(L.order_off + conv_items * sizeof(ConvItem), 256);
     L.total = L.conv_off + conv_bytes;
     return L;
@@ -309,23 +319,34 @@ Layout layout_for(int64_t count, int64_t ntiles, size_t conv_bytes = 0, int64_t 
 int32_t round8(int32_t x) { return (x + 7) / 8 * 8; }
 int32_t round16(int32_t x) { return (x + 15) / 16 * 16; }
 
-// Bytes of product d's converted operands, each operand starting on a
-// 256-byte boundary: 16-bit planes, A m x round8(K) and B K x round8(n); fp8
-// fields (p <= 31) bytes, A m x round16(K) and B^T n x round16(K).
+// The tensor-core path's converted operands (k_batched_tc.cu): per product,
+// 32-byte K-blocks (32 fp8 or 16 bf16 elements); A as k planes of 128-row
+// tiles (rows rounded up to 8), B^T as k planes of BN-column tiles, each
+// operand starting on a 256-byte boundary.
+int32_t tc_kblocks(const qadic_gemm_desc &d, const Field &f) {
+    const int32_t e = fp8_field(f.p) ? 32 : 16;
+    return (d.K + e - 1) / e;
+}
+size_t tc_a_bytes(const qadic_gemm_desc &d, const Field &f) {
+    return (size_t)f.k * round8(d.m) * 32 * tc_kblocks(d, f);
+}
+size_t tc_b_bytes(const qadic_gemm_desc &d, const Field &f) {
+    const int32_t bn = tc_bn(f.k);
+    return (size_t)f.k * bn * 32 * tc_kblocks(d, f) * ((d.n + bn - 1) / bn);
+}
 size_t conv_bytes_of(const qadic_gemm_desc &d, const Field &f) {
-    const size_t k = f.k;
-    if (fp8_field(f.p))
-        return align_up(k * d.m * round16(d.K), 256) + align_up(k * d.n * round16(d.K), 256);
-    return align_up(k * d.m * round8(d.K) * 2, 256) + align_up(k * d.K * round8(d.n) * 2, 256);
+    return align_up(tc_a_bytes(d, f), 256) + align_up(tc_b_bytes(d, f), 256);
 }
 
-// 16-byte output chunks of product d's operands (A, B) and the conversion
-// items they make.
-uint64_t chunks_a(const qadic_gemm_desc &d, const Field &f) {
-    return fp8_field(f.p) ? (uint64_t)f.k * d.m * (round16(d.K) / 16) : (uint64_t)f.k * d.m * (round8(d.K) / 8);
-}
+// 16-byte output chunks the conversion writes for product d's operands (A:
+// all of its blocks; B: the valid columns only) and the items they make.
+uint64_t chunks_a(const qadic_gemm_desc &d, const Field &f) { return tc_a_bytes(d, f) / 16; }
 uint64_t chunks_b(const qadic_gemm_desc &d, const Field &f) {
-    return fp8_field(f.p) ? (uint64_t)f.k * d.n * (round16(d.K) / 16) : (uint64_t)f.k * d.K * (round8(d.n) / 8);
+    return (uint64_t)f.k * tc_kblocks(d, f) * 2 * d.n;
+}
+int64_t tc_tiles_of(const qadic_gemm_desc &d, const Field &f) {
+    const int32_t bn = tc_bn(f.k);
+    return (int64_t)((d.m + 127) / 128) * ((d.n + bn - 1) / bn);
 }
 int64_t conv_items_of(const qadic_gemm_desc &d, const Field &f) {
     return (int64_t)((chunks_a(d, f) + kConvItemChunks - 1) / kConvItemChunks +
@@ -385,15 +406,16 @@ size_t batched_workspace_size_fields(const Field *const *fields, int32_t nfields
                                      const qadic_gemm_desc *descs, int64_t count) {
     if (!descs || !fields || count <= 0 || nfields < 1) return 0;
     size_t conv = 0;
-    int64_t items = 0;
+    int64_t items = 0, tc_tiles = 0;
     for (int64_t i = 0; i < count; ++i) {
         const qadic_gemm_desc &d = descs[i];
         if (d.field < 0 || d.field >= nfields || !fields[d.field] || d.m < 1 || d.n < 1 || d.K < 1)
             return 0;
         conv += conv_bytes_of(d, *fields[d.field]);
         items += conv_items_of(d, *fields[d.field]);
+        tc_tiles += tc_tiles_of(d, *fields[d.field]);
     }
-    return layout_for(count, max_tiles(descs, count), conv, items).total;
+    return layout_for(count, tc_tiles, conv, items, sizeof(TcRec)).total;
 }
 
 int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm_desc *descs,
@@ -430,13 +452,14 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
                          "the batch has up to %lld output tiles; the work queue indexes at most %lld",
                          (long long)tile_bound, (long long)kMaxQueueTiles);
     size_t conv = 0;
-    int64_t conv_items = 0;
+    int64_t conv_items = 0, tc_tiles = 0;
     for (int64_t i = 0; i < count; ++i) {
         conv += conv_bytes_of(descs[i], *fields[descs[i].field]);
         conv_items += conv_items_of(descs[i], *fields[descs[i].field]);
+        tc_tiles += tc_tiles_of(descs[i], *fields[descs[i].field]);
     }
     // converted operands when the workspace holds them, else bytes staged through registers
-    const Layout L_conv = layout_for(count, tile_bound, conv, conv_items);
+    const Layout L_conv = layout_for(count, tc_tiles, conv, conv_items, sizeof(TcRec));
     const Layout L_list = layout_for(count, tile_bound);
     if (!workspace || ws_bytes < L_list.total)
         return set_error(QADIC_E_NOMEM, "workspace %zu < %zu bytes", ws_bytes, L_list.total);
@@ -445,12 +468,20 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
     const Layout L = converted ? L_conv : L_list;
     int cfgs[kMaxFields];
     size_t smem = 0;
+    uint32_t kmax = 1;
     for (int32_t i = 0; i < nfields; ++i) {
         cfgs[i] = field_cfg(*fields[i]);
-        smem = std::max(smem, converted ? async_smem_bytes(fields[i]->k, cfgs[i], fp8_field(fields[i]->p))
-                                        : tile_smem_bytes(fields[i]->k, cfgs[i]));
+        smem = std::max(smem, tile_smem_bytes(fields[i]->k, cfgs[i]));
     }
-    int st = converted ? prepare_async_kernel() : prepare_kernel(smem);
+    for (int64_t i = 0; i < count; ++i) kmax = std::max(kmax, fields[descs[i].field]->k);
+    int tc_slot = 0, tc_a = 0, tc_stages = 0;
+    int st = QADIC_OK;
+    if (converted) {
+        if ((st = tc_stage_layout(kmax, &tc_slot, &tc_a, &tc_stages)) != QADIC_OK) return st;
+        st = prepare_tc_kernel();
+    } else {
+        st = prepare_kernel(smem);
+    }
     if (st != QADIC_OK) return st;
 
     // graph cache lookup
@@ -517,22 +548,21 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
         P.field = d.field;
         P.cfg = cfgs[d.field];
         const uint32_t k = fields[d.field]->k;
-        if (converted && fp8_field(fields[d.field]->p)) {
-            P.kp = P.np = round16(d.K);   // A [k][m][kp], B^T [k][n][kp] bytes
+        TileShape ts = tile_shape_of(k, P.cfg);
+        uint64_t c = tile_cost(d, k, P.cfg);
+        if (converted) {
+            // tensor-core path: kp = 32-byte K-blocks; A16 / B16 = the
+            // operands in the blocked layout of k_batched_tc.cu
+            const Field &f = *fields[d.field];
+            P.kp = tc_kblocks(d, f);
+            P.np = tc_bn(k);
             P.A16 = reinterpret_cast<const uint16_t *>((uint8_t *)workspace + conv_at);
-            conv_at += align_up((size_t)k * d.m * P.kp, 256);
+            conv_at += align_up(tc_a_bytes(d, f), 256);
             P.B16 = reinterpret_cast<const uint16_t *>((uint8_t *)workspace + conv_at);
-            conv_at += align_up((size_t)k * d.n * P.kp, 256);
-        } else if (converted) {
-            P.kp = round8(d.K);
-            P.np = round8(d.n);
-            P.A16 = reinterpret_cast<const uint16_t *>((uint8_t *)workspace + conv_at);
-            conv_at += align_up((size_t)k * d.m * P.kp * 2, 256);
-            P.B16 = reinterpret_cast<const uint16_t *>((uint8_t *)workspace + conv_at);
-            conv_at += align_up((size_t)k * d.K * P.np * 2, 256);
+            conv_at += align_up(tc_b_bytes(d, f), 256);
+            ts = TileShape{128, tc_bn(k), 32};
+            c = (uint64_t)k * k * 128 * tc_bn(k) * 32 * P.kp;   // MMA work of a tile
         }
-        const TileShape ts = tile_shape_of(k, P.cfg);
-        const uint64_t c = tile_cost(d, k, P.cfg);
         for (int tm = 0; tm * ts.bm < d.m; ++tm)
             for (int tn = 0; tn * ts.bn < d.n; ++tn) {
                 tiles.push_back(BTile{(int32_t)i, (int16_t)tm, (int16_t)tn});
@@ -559,8 +589,32 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
         if (fa != fb) return fa < fb;
         return cost[a] > cost[b];
     });
-    BTile *tp = reinterpret_cast<BTile *>(host.data() + L.tiles_off);
-    for (size_t i = 0; i < order.size(); ++i) tp[i] = tiles[order[i]];
+    if (converted) {
+        TcRec *rp = reinterpret_cast<TcRec *>(host.data() + L.tiles_off);
+        for (size_t i = 0; i < order.size(); ++i) {
+            const BTile &t = tiles[order[i]];
+            const BProd &P = pp[t.prod];
+            const uint32_t k = fields[P.field]->k;
+            const int32_t bn = tc_bn(k);
+            const int32_t rows = std::min(128, P.m - 128 * t.tm);
+            TcRec r;
+            r.a = reinterpret_cast<const uint8_t *>(P.A16) + (size_t)t.tm * P.kp * k * 4096;
+            r.b = reinterpret_cast<const uint8_t *>(P.B16) + (size_t)t.tn * P.kp * k * bn * 32;
+            r.c = P.C + (int64_t)t.tm * 128 * P.ldc + (int64_t)t.tn * bn;
+            r.c_plane = (int64_t)P.m * P.ldc;
+            r.ldc = P.ldc;
+            r.rows = (int16_t)rows;
+            r.cols = (int16_t)std::min(bn, P.n - bn * t.tn);
+            r.ks = (int16_t)P.kp;
+            r.rows8 = (int16_t)((rows + 7) / 8 * 8);
+            r.field = (int16_t)P.field;
+            r.k = (int16_t)k;
+            rp[i] = r;
+        }
+    } else {
+        BTile *tp = reinterpret_cast<BTile *>(host.data() + L.tiles_off);
+        for (size_t i = 0; i < order.size(); ++i) tp[i] = tiles[order[i]];
+    }
     BHeader *hdr = reinterpret_cast<BHeader *>(host.data());
     hdr->counter = 0;
     hdr->ntiles = (int32_t)tiles.size();
@@ -570,7 +624,7 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
     hdr->prods_off = (uint32_t)L.prods_off;
     hdr->tiles_off = (uint32_t)L.tiles_off;
     hdr->order_off = (uint32_t)L.order_off;
-    size_t used = L.tiles_off + tiles.size() * sizeof(BTile);
+    size_t used = L.tiles_off + tiles.size() * (converted ? sizeof(TcRec) : sizeof(BTile));
     if (converted) {
         // conversion items of at most kConvItemChunks chunks, by decreasing size
         std::vector<ConvItem> items;
@@ -601,14 +655,16 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
         g_ws_list[workspace] = 0;   // an uncached list: no cached graph owns this workspace
     }
 
-    const int64_t grid = converted ? async_grid(smem, (int64_t)tiles.size())
+    const int64_t grid = converted ? tc_grid((int64_t)tiles.size())
                                    : grid_for(dev, smem, (int64_t)tiles.size());
+    int *status = device_status_word();
     // {convert, products} or {products}; the tile counter starts at zero
     auto enqueue = [&](cudaStream_t s) -> int {
         if (converted) {
-            const int cs = launch_convert((const uint8_t *)workspace, conv_items, s);
+            const int cs = launch_tc_convert((const uint8_t *)workspace, conv_items, s);
             if (cs != QADIC_OK) return cs;
-            return launch_async((uint8_t *)workspace, grid, smem, s);
+            return launch_tc_products((const uint8_t *)workspace, grid, tc_slot, tc_a, tc_stages,
+                                      status, s);
         }
         batched_kernel<<<(unsigned)grid, kThreads, smem, s>>>((uint8_t *)workspace);
         const cudaError_t e = cudaGetLastError();

@@ -81,9 +81,9 @@ def test_batched_mixed_fields(torch, orc, converted):
 
 
 def test_batched_paths_agree_and_sizes(torch, orc):
-    """The converted-operand path and the register-staged path give the same
-    bytes; the size query with fields covers the converted operands (2 bytes
-    per element, rows padded to 8) on top of the work list."""
+    """The tensor-core path (converted operands) and the register-staged path
+    give the same bytes; the size query with fields covers the converted
+    operands in their blocked layout on top of the work list."""
     fields = mixed_fields()
     dims, fidx = W.batched_shapes(30, salt=7)
     shapes = [tuple(int(x) for x in d) for d in dims]
@@ -97,20 +97,27 @@ def test_batched_paths_agree_and_sizes(torch, orc):
     small = q.batched_workspace_size(a.descs)
     big = q.batched_workspace_size(a.descs, fields)
     r8 = lambda x: (x + 7) // 8 * 8
-    r16 = lambda x: (x + 15) // 16 * 16
     cdiv = lambda a, b: -(-a // b)
-    conv = items = 0
+    conv = items = tiles = 0
     for (m, n, K), f in zip(shapes, fi):
         k = fields[f].k
-        if fields[f].p <= 31:   # fp8 bytes: A m x r16(K), B^T n x r16(K); 16-byte chunks
-            conv += k * (m + n) * r16(K)
-            items += cdiv(k * m * (r16(K) // 16), 4096) + cdiv(k * n * (r16(K) // 16), 4096)
-        else:                   # bf16: A m x r8(K), B K x r8(n); 8-element chunks
-            conv += 2 * k * (m * r8(K) + K * r8(n))
-            items += cdiv(k * m * (r8(K) // 8), 4096) + cdiv(k * K * (r8(n) // 8), 4096)
-    assert big >= small + conv
-    # + 256-byte alignment of each operand, + the conversion items (8 bytes each)
-    assert big <= small + conv + 2 * 256 * len(shapes) + 8 * items + 512
+        # tensor-core blocks: 32-byte K-blocks of 32 fp8 (p <= 31) or 16 bf16
+        # elements; A as k planes of m rounded up to 8 rows, B^T as k planes
+        # of BN-column tiles (BN = 128, 64, 32, 32, 16, ... for k = 1, 2, 3, 4, 5..)
+        ks = cdiv(K, 32 if fields[f].p <= 31 else 16)
+        bn = 128 if k == 1 else 64 if k == 2 else 32 if k <= 4 else 16
+        a_bytes = k * r8(m) * 32 * ks
+        b_bytes = k * bn * 32 * ks * cdiv(n, bn)
+        conv += a_bytes + b_bytes
+        items += cdiv(a_bytes // 16, 4096) + cdiv(k * ks * 2 * n, 4096)
+        tiles += cdiv(m, 128) * cdiv(n, bn)
+    # the work list holds 48-byte tile records on this path (8-byte ones with
+    # the smallest tile shape in the work-list-only size)
+    small_tiles = sum(cdiv(m, 32) * cdiv(n, 16) for m, n, K in shapes)
+    header = small - 8 * small_tiles
+    assert big >= header - 512 + 48 * tiles + conv
+    # + 256-byte alignment of each operand and section, + the conversion items (8 bytes each)
+    assert big <= header + 48 * tiles + conv + 2 * 256 * len(shapes) + 8 * items + 1024
 
 
 @pytest.mark.parametrize("pk", [(3, 3), (5, 5), (2, 6), (101, 2), (3, 7), (13, 3), (2, 1)])
