@@ -57,6 +57,18 @@ MEASURED_TRAFFIC = {
 }
 
 
+def plane_kernel(p, n):
+    """Name of the kernel the k = 2 plane GEMM dispatches to for an n x n x n
+    product over GF(p^2): CTA pairs when there are two tile rows or more and
+    K fits one exact FP32 chunk of 64-wide K-blocks, one CTA per tile
+    otherwise (the same rule as the launcher in k_gemm_tc.cu)."""
+    h = (p - 1) // 2
+    chunk_kb = ((1 << 24) - 2 * p) // (h * h) // 64
+    if n > 128 and (n + 63) // 64 <= chunk_kb:
+        return PLANE_KERNEL
+    return "gemm_planes_tc_kernel<2,128>"
+
+
 def source_hash(path):
     """sha256 of a source file with "//" comments and blank lines removed."""
     import hashlib
@@ -309,18 +321,24 @@ def make_plane_workload(torch, q, W, p, n, salt=0):
     opB = torch.empty((k, n, n), dtype=torch.bfloat16, device="cuda")
     C = torch.empty((k, n, n), dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
+    pack_events = []
 
     def step(kev):
         # both operands packed by one launch, then the plane GEMM
-        f.pack_operands(q.FMT_INT8_PLANES, dA, dB, n, n, n, opA, opB)
         if kev is not None:
             a, b = ev_pair(torch)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        f.pack_operands(q.FMT_INT8_PLANES, dA, dB, n, n, n, opA, opB)
+        if kev is not None:
             a.record(stream)
         f.gemm(q.PATH_PLANES, opA, opB, n, n, n, C=C)
         if kev is not None:
             b.record(stream)
             kev.append((a, b))
+            pack_events.append((e0, a))
 
+    step.pack_events = pack_events
     return f, A, B, C, step
 
 
@@ -330,11 +348,14 @@ def bench_plane(args, torch, q, W, dist, p=101, n=4096, name="plane"):
     f, A, B, C, step = make_plane_workload(torch, q, W, p, n)
     total, kms = time_steps(torch, step, args.steps, args.warmup, dist, kernel_events=True)
     ms = total / args.steps
+    pev = step.pack_events[-args.steps:]
+    pack_ms = sum(e0.elapsed_time(e1) for e0, e1 in pev) / len(pev)
     field_ops = 2.0 * n ** 3
     flops = 4 * 2.0 * n ** 3          # k^2 plane products
     pk = peaks()
     achieved = flops / (kms * 1e-3) / 1e12
-    traffic, traffic_source = measured_traffic(PLANE_KERNEL, n)
+    kernel = plane_kernel(p, n)
+    traffic, traffic_source = measured_traffic(kernel, n)
     res = {
         "ms_per_step": ms, "value": field_ops / (ms * 1e-3) / 1e9, "n": n, "p": p,
         "kernel_ms": kms,
@@ -343,10 +364,16 @@ def bench_plane(args, torch, q, W, dist, p=101, n=4096, name="plane"):
                      "traffic": traffic, "traffic_source": traffic_source,
                      "traffic_unit": "bytes per launch (DRAM read + write)",
                      "algorithmic_bytes": 2 * 2 * n * n * 2 + 2 * n * n,
-                     "kernel": PLANE_KERNEL,
+                     "kernel": kernel,
                      "peak_source": pk["source"] + " bf16 sustained (cuBLAS)"},
         "gpu_launches": 2 * args.steps,
     }
+    # the pack launch on its own: k int8 planes of A and B read, k bf16
+    # planes of each written
+    pack_bytes = 2 * (2 * n * n * 1 + 2 * n * n * 2)
+    res["pack"] = {"kernel": "pack_vec_ab", "ms": pack_ms, "algorithmic_bytes": pack_bytes,
+                   "achieved_gbs": pack_bytes / (pack_ms * 1e-3) / 1e9,
+                   "frac_of_hbm": pack_bytes / (pack_ms * 1e-3) / 1e9 / pk["hbm_gbs"]}
     return f, A, B, C, res
 
 
@@ -465,17 +492,18 @@ def bench_redq(args, torch, q, W, count=None, steps=10):
     del d
     dq = torch.from_numpy(W.redq_words_q(count, 5, PQ_Q)).cuda()
     pq = {}
-    for int_floor in (False, True):
+    for form in ("lemma1", "int", "f32_digits"):
         def step(kev):
-            q.redq_pq(7, PQ_Q, 5, dq, out=out, int_floor=int_floor)
+            q.redq_pq(7, PQ_Q, 5, dq, out=out, int_floor=form == "int",
+                      f32_digits=form == "f32_digits")
         total, _ = time_steps(torch, step, steps, 3, None)
         pms = total / steps
         pgbs = 16.0 * count / (pms * 1e-3) / 1e9
-        pq["int" if int_floor else "lemma1"] = {
+        pq[form] = {
             "value": 5.0 * count / (pms * 1e-3), "unit": "residues/s", "ms": pms,
             "roofline": {"bound": "hbm", "achieved": pgbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
                          "frac": pgbs / pk["hbm_gbs"], "traffic": None}}
-        if not int_floor:
+        if form == "lemma1":
             # the Lemma 1 form takes one round-up multiply a word (the floor
             # by q^2 = 1,382,976 < 2^32; the floors below 2^32 are 32-bit
             # integer ones): far from the FP64 pipe's limit, which the
@@ -647,7 +675,7 @@ def make_batched(torch, q, W, count=4096, salt=0):
     for (m, n, K), fi, (a, b, c) in zip(dims, fidx, offs):
         descs.append(q.GemmDesc(int(fi), int(m), int(n), int(K), dA.data_ptr() + a,
                                 dB.data_ptr() + b, dC.data_ptr() + c, int(K), int(n), int(n), 0))
-    # room for the converted operands: the convert + cp.async path
+    # room for the converted operands: the tensor-core path
     ws = torch.empty(q.batched_workspace_size(descs, fields), dtype=torch.uint8, device="cuda")
     return fields, dims, fidx, offs, hA, hB, dC, descs, ws
 
@@ -659,27 +687,45 @@ def bench_batched(args, torch, q, W):
     def step(kev):
         q.batched_gemm(fields, darr, ws, graph=True)
 
-    # default tiles, then the autotuner's choice on this batch (tuning is
-    # setup, outside the timed region)
-    for k in range(1, 9):
-        q.batched_select_tiles(k, -1)
-    total0, _ = time_steps(torch, step, args.steps, args.warmup, None)
-    ms_default = total0 / args.steps
-    # the register-staged path (work-list-only workspace), default tiles
-    ws_list = torch.empty(q.batched_workspace_size(descs), dtype=torch.uint8, device="cuda")
-
-    def step_reg(kev):
-        q.batched_gemm(fields, darr, ws_list, graph=True)
-
-    tot_r, _ = time_steps(torch, step_reg, args.steps, args.warmup, None)
-    ms_register = tot_r / args.steps
-    del ws_list
-    chosen = q.batched_autotune(fields, descs, ws, reps=3)
+    # the tensor-core path (the workspace holds the converted operands)
     total, _ = time_steps(torch, step, args.steps, args.warmup, None)
     ms = total / args.steps
     ops = float(sum(2 * int(m) * int(n) * int(K) for m, n, K in dims))
     flops = float(sum(2 * fields[fi].k ** 2 * int(m) * int(n) * int(K)
                       for (m, n, K), fi in zip(dims, fidx)))
+    pk = peaks()
+    achieved = flops / (ms * 1e-3) / 1e12
+    # all three fields have p <= 31: the products run on fp8 e4m3 operands,
+    # so the peak is the bf16 one times the nominal fp8 / bf16 ratio (4.5 /
+    # 2.25 PFLOP/s dense)
+    roofline = {"bound": "tensor", "achieved": achieved,
+                "peak": 2.0 * pk["bf16_sustained"], "unit": "TFLOP/s",
+                "frac": achieved / (2.0 * pk["bf16_sustained"]), "traffic": None,
+                "operand_dtype": "fp8 e4m3", "peak_scale": 2.0,
+                "kernel": "tc_convert_kernel + tc_products_kernel (tcgen05 kind::f8f6f4, "
+                          "FP32 accumulators in tensor memory)",
+                "note": "plane flops 2 k^2 m n K of the products over the time of both "
+                        "launches (the conversion included)"}
+    out = {"value": ops / (ms * 1e-3) / 1e9, "unit": "field Gop/s", "ms_per_step": ms,
+           "products": len(descs), "field_ops": ops, "plane_flops": flops, "roofline": roofline}
+    if args.extras == "none":
+        return out
+    # the register-staged path (work-list-only workspace): default tiles,
+    # then the autotuner's choice on this batch (tuning is setup, outside
+    # the timed region)
+    ws_list = torch.empty(q.batched_workspace_size(descs), dtype=torch.uint8, device="cuda")
+
+    def step_reg(kev):
+        q.batched_gemm(fields, darr, ws_list, graph=True)
+
+    for k in range(1, 9):
+        q.batched_select_tiles(k, -1)
+    tot_r, _ = time_steps(torch, step_reg, args.steps, args.warmup, None)
+    ms_register = tot_r / args.steps
+    chosen = q.batched_autotune(fields, descs, ws_list, reps=3)
+    tot_rt, _ = time_steps(torch, step_reg, args.steps, args.warmup, None)
+    ms_register_tuned = tot_rt / args.steps
+    del ws_list
     # one launch per product through the same entry point (no graph)
     single_ws = torch.empty(max(q.batched_workspace_size([d], fields) for d in descs),
                             dtype=torch.uint8, device="cuda")
@@ -700,10 +746,7 @@ def bench_batched(args, torch, q, W):
         e1.record(stream)
     torch.cuda.synchronize()
     ms1_gpu = sum(e0.elapsed_time(e1) for e0, e1 in evs)
-    pk = peaks()
-    achieved = flops / (ms * 1e-3) / 1e12
-    return {"value": ops / (ms * 1e-3) / 1e9, "unit": "field Gop/s", "ms_per_step": ms,
-            "products": len(descs), "field_ops": ops, "plane_flops": flops,
+    out.update({
             "one_launch_per_product": {"value": ops / (ms1 * 1e-3) / 1e9, "ms": ms1,
                                        "ms_gpu_only": ms1_gpu,
                                        "note": "ms: wall time of 4096 API calls (host builds a "
@@ -711,23 +754,14 @@ def bench_batched(args, torch, q, W):
                                                "time of the 4096 launches"},
             "speedup_vs_per_product_gpu_only": ms1_gpu / ms,
             "speedup_vs_per_product": ms1 / ms,
-            "autotuned_tiles": {str(k): dict(zip(("bm", "bn", "bk"),
-                                                 q.batched_tile_configs(k)[c][:3]))
-                                for k, c in chosen.items()},
-            "ms_default_tiles": ms_default,
-            "ms_register_staged_default_tiles": ms_register,
-            # all three fields have p <= 31: the products run on fp8 e4m3
-            # operands, so the peak is the bf16 one times the nominal fp8 /
-            # bf16 ratio (4.5 / 2.25 PFLOP/s dense)
-            "roofline": {"bound": "tensor", "achieved": achieved,
-                         "peak": 2.0 * pk["bf16_sustained"], "unit": "TFLOP/s",
-                         "frac": achieved / (2.0 * pk["bf16_sustained"]), "traffic": None,
-                         "operand_dtype": "fp8 e4m3", "peak_scale": 2.0,
-                         "kernel": "convert_kernel + async_kernel (cp.async, mma.sync fp8 e4m3 "
-                                   "m16n8k32; f16 accumulators for GF(2^8))",
-                         "note": "legacy mma.sync measured on this GPU at 606 TFLOP/s (bf16) and "
-                                 "2177 TFLOP/s (fp8 e4m3, operands resident); time includes the "
-                                 "operand conversion launch"}}
+            "register_staged": {"ms_default_tiles": ms_register,
+                                "ms_autotuned": ms_register_tuned,
+                                "autotuned_tiles": {str(k): dict(zip(("bm", "bn", "bk"),
+                                                                     q.batched_tile_configs(k)[c][:3]))
+                                                    for k, c in chosen.items()},
+                                "note": "work-list-only workspace (and the allocation-free "
+                                        "call): operands staged through registers, mma.sync"}})
+    return out
 
 
 def bench_fp64_gf27(args, torch, q, W, n=1024):
@@ -977,6 +1011,7 @@ def run_workload(args, torch, q, W, dist, rank, world, line, extras):
                      "f32 accumulate", "roofline": res["roofline"],
                      "gpu_launches": res["gpu_launches"]})
         line["config"] = headline_config(n)
+        extras["pack"] = res["pack"]
         if rank == 0 and args.extras == "all":
             def fp64_leg():
                 C64, fp = bench_fp64(args, torch, q, W, f, A, B, n)
@@ -1042,14 +1077,14 @@ def run_workload(args, torch, q, W, dist, rank, world, line, extras):
     elif args.workload == "batched":
         r = bench_batched(args, torch, q, W)
         line.update({"value": r["value"] * world, "unit": "field Gop/s",
-                     "ms_per_step": r["ms_per_step"], "dtype": "bf16 exact, f32 accumulate",
+                     "ms_per_step": r["ms_per_step"], "dtype": "fp8 e4m3 exact, f32 accumulate",
                      "roofline": r["roofline"], "gpu_launches": 2 * args.steps})
         line["config"] = {"workload": "4096 products, m,n,K log-uniform in [16,256], fields "
-                          "GF(2^8), GF(7^4), GF(31^2); one persistent graph-replayed launch"}
+                          "GF(2^8), GF(7^4), GF(31^2); conversion + one persistent tcgen05 "
+                          "launch, graph-replayed"}
         extras.update({k: r[k] for k in ("one_launch_per_product", "speedup_vs_per_product",
                                          "speedup_vs_per_product_gpu_only",
-                                         "products", "autotuned_tiles", "ms_default_tiles",
-                                         "ms_register_staged_default_tiles")})
+                                         "products", "register_staged") if k in r})
     elif args.workload == "fp64":
         r = bench_fp64_gf27(args, torch, q, W)
         line.update({"value": r["value"] * world, "unit": "field Gop/s",
@@ -1072,8 +1107,7 @@ def run_plane_extras(args, torch, q, W, extras):
     bb = guarded(bench_batched, args, torch, q, W)
     extras["batched"] = pick(("value", "unit", "ms_per_step", "one_launch_per_product",
                               "speedup_vs_per_product_gpu_only", "speedup_vs_per_product",
-                              "roofline", "autotuned_tiles", "ms_default_tiles",
-                              "ms_register_staged_default_tiles"))(bb)
+                              "roofline", "register_staged"))(bb)
     g27 = guarded(bench_fp64_gf27, args, torch, q, W)
     extras["polymul_fqt_p3_n500"] = guarded(bench_fqt, args, torch, q, W)
     extras["fp64_gf27_n1024"] = g27

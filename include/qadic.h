@@ -275,12 +275,18 @@ int qadic_redq(uint32_t p, uint32_t log2_q, uint32_t ndigits, const double *in, 
  * for the first s with q^(ndigits-s) <= 2^32, the chain starts with one such
  * floor by q^s, and the floors of r mod q^s and of t_s below 2^32 are 32-bit
  * integer ones (exact, so the flag then only picks the floor by q^s).
+ * With QADIC_REDQ_F32_DIGITS (q^2 < 2^21, at most 8 digits, else
+ * QADIC_E_UNSUPPORTED) the word is cut into chunks of two base-q digits by
+ * integer floors by q^2, and the floors by q and by p inside a chunk
+ * (below 2^21) are exact FP32 ones: the same rho, with no FP64 arithmetic.
  * in[i] = sum_{j<=d} mu~_j q^j with 0 <= mu~_j < q, d = ndigits-1, an exact
  * integer held in a double; out[i] = rho = sum_j (mu~_j mod p) q^j (exact).
  * Requires p prime <= 251, q >= p with p | q, q^ndigits <= 2^51 (else
- * QADIC_E_OVERFLOW: Lemma 1's limit), flags 0 or QADIC_REDQ_INT_FLOOR,
- * in/out 16-byte aligned device pointers (may alias).  Words at or above
- * q^ndigits give unspecified values without faulting. */
+ * QADIC_E_OVERFLOW: Lemma 1's limit), flags 0, QADIC_REDQ_INT_FLOOR or
+ * QADIC_REDQ_F32_DIGITS (one of them), in/out 16-byte aligned device
+ * pointers (may alias).  Words at or above q^ndigits give unspecified values
+ * without faulting. */
+#define QADIC_REDQ_F32_DIGITS 0x200u
 int qadic_redq_pq(uint32_t p, uint64_t q, uint32_t ndigits, const double *in, double *out,
                   int64_t count, uint32_t flags, void *stream);
 
@@ -342,22 +348,26 @@ int qadic_polymul_batched(uint32_t p, uint32_t k, const uint8_t *a, const uint8_
  * Requires 1 <= m, n, K <= 4096 per product, k <= 8.  `workspace` (device,
  * 256-byte aligned) must hold at least qadic_batched_workspace_size(descs,
  * count) bytes: the host packs the work list into it, and the operand bytes
- * are staged through registers tile by tile.  With at least
- * qadic_batched_workspace_size_fields(fields, nfields, descs, count) bytes
- * the faster path runs instead: one launch converts every operand once to
- * centred planes in the workspace -- fp8 e4m3 for p <= 31 (exact: |c| <= 15),
- * B transposed, products by m16n8k32 fp8 MMAs (f16 accumulators for GF(2^8),
- * whose 0/1 planes keep every partial sum exact over chunks of 2047/k);
- * bf16 for larger p -- and the persistent launch copies tiles with cp.async.
+ * are staged through registers tile by tile (warp-level bf16 MMAs).  With
+ * at least qadic_batched_workspace_size_fields(fields, nfields, descs, count)
+ * bytes the tensor-core path runs instead: one launch converts every operand
+ * once to centred planes in the workspace -- fp8 e4m3 for p <= 31 (exact:
+ * |c| <= 15), bf16 for larger p -- cut into the blocks the MMAs read (B
+ * transposed), and a persistent tcgen05 kernel copies them into shared
+ * memory and accumulates the plane sums in FP32 in tensor memory (128-row
+ * tiles, 128 / k output columns per tile, rounded to the sizes in tc_bn of
+ * the implementation), reducing them in place at every exact chunk.
  * Both paths give the same bytes.  The size query with fields returns 0 for
  * invalid arguments.  With QADIC_BATCHED_GRAPH the launch is captured in
  * a CUDA graph keyed by (descs, count, workspace) and replayed on later calls
  * with the same key (and the same tile configurations); a replay first
  * re-uploads its own work list if another call wrote a different one into
- * the same workspace.  Tiles: for each field the configuration selected for
- * its k (qadic_batched_select_tiles / qadic_batched_autotune below), or
- * configuration 0.  Errors: QADIC_E_INVALID, QADIC_E_NOMEM (workspace too
- * small), QADIC_E_OVERFLOW (exact FP32 chunk of a field below 32). */
+ * the same workspace.  Tiles of the register-staged path: for each field the
+ * configuration selected for its k (qadic_batched_select_tiles /
+ * qadic_batched_autotune below), or configuration 0.  Errors:
+ * QADIC_E_INVALID (including a list of more tiles than the work queue
+ * indexes), QADIC_E_NOMEM (workspace too small), QADIC_E_OVERFLOW (exact
+ * FP32 chunk of a field below 32). */
 #define QADIC_BATCHED_GRAPH 0x1u
 size_t qadic_batched_workspace_size(const qadic_gemm_desc *descs, int64_t count);
 size_t qadic_batched_workspace_size_fields(const qadic_field *const *fields, int32_t nfields,
@@ -367,11 +377,14 @@ int qadic_batched_gemm(const qadic_field *const *fields, int32_t nfields,
                        size_t ws_bytes, uint32_t flags, void *stream);
 
 /* ----------------------------------------------- batched tile autotuning --
- * The batched kernel can run each product with one of a few tile
- * configurations per field degree k (the shapes whose 2k-1 accumulator sets
- * fit in registers): output tile bm x bn, K-block bk, and the shared memory
- * it needs.  Configuration 0 is the default.  No counterpart in the paper
- * (it concerns the GPU schedule, not the arithmetic).
+ * The register-staged batched kernel (the path of work-list-only workspaces
+ * and of qadic_batched_gemm_noalloc) can run each product with one of a few
+ * tile configurations per field degree k (the shapes whose 2k-1 accumulator
+ * sets fit in registers): output tile bm x bn, K-block bk, and the shared
+ * memory it needs.  Configuration 0 is the default.  No counterpart in the
+ * paper (it concerns the GPU schedule, not the arithmetic).  The autotuner
+ * always times that kernel (it offers the batch the work-list part of the
+ * workspace only).
  * qadic_batched_tile_configs: writes min(capacity, n) entries of the table
  *   for k and sets *count = n.
  * qadic_batched_select_tiles: process-wide choice for fields with k

@@ -22,6 +22,7 @@ FMT_LOG, FMT_COEFF_U8, FMT_INT8_PLANES, FMT_QADIC_F64, FMT_OPERAND_A, FMT_OPERAN
 # qadic_path
 PATH_FP64_QADIC, PATH_PLANES, PATH_FOLD, PATH_KARATSUBA = 0, 1, 2, 3
 REDQ_INT_FLOOR = 0x100
+REDQ_F32_DIGITS = 0x200
 POLYMUL_PLAIN_F64 = 0x1
 POLYMUL_INT_WORDS = 0x2
 BATCHED_GRAPH = 0x1
@@ -338,13 +339,15 @@ def redq(p: int, log2_q: int, ndigits: int, words, out=None, table_mode: int = 3
 
 
 def redq_pq(p: int, q: int, ndigits: int, words, out=None, int_floor: bool = False,
-            stream=None):
-    """REDQ for q a multiple of p, no correction step (``qadic_redq_pq``)."""
+            stream=None, f32_digits: bool = False):
+    """REDQ for q a multiple of p, no correction step (``qadic_redq_pq``);
+    ``f32_digits`` selects QADIC_REDQ_F32_DIGITS."""
     torch = _torch()
     if out is None:
         out = torch.empty_like(words)
+    flags = (REDQ_INT_FLOOR if int_floor else 0) | (REDQ_F32_DIGITS if f32_digits else 0)
     _check(lib().qadic_redq_pq(p, q, ndigits, _ptr(words), _ptr(out), words.numel(),
-                               REDQ_INT_FLOOR if int_floor else 0, _stream(stream)))
+                               flags, _stream(stream)))
     return out
 
 

@@ -59,7 +59,8 @@ struct TcRec {
     int16_t rows, cols;  // valid rows (<= 128) and columns (<= BN) of the tile
     int16_t ks;          // 32-byte K-blocks
     int16_t rows8;       // rows rounded up to 8
-    int16_t field, k;
+    int16_t ndrain;      // in-place reductions on the way through K
+    uint8_t field, k;
 };
 static_assert(sizeof(TcRec) == 48, "TcRec layout");
 

@@ -644,14 +644,18 @@ int qadic_redq_pq(uint32_t p, uint64_t q, uint32_t ndigits, const double *in, do
     if (qd > ((unsigned __int128)1 << 51))
         return set_error(QADIC_E_OVERFLOW,
                          "q^ndigits exceeds 2^51 (Lemma 1 limit for binary64)");
-    if (flags & ~QADIC_REDQ_INT_FLOOR) return set_error(QADIC_E_INVALID, "flags 0x%x", flags);
+    if ((flags & ~(QADIC_REDQ_INT_FLOOR | QADIC_REDQ_F32_DIGITS)) ||
+        flags == (QADIC_REDQ_INT_FLOOR | QADIC_REDQ_F32_DIGITS))
+        return set_error(QADIC_E_INVALID, "flags 0x%x", flags);
+    if ((flags & QADIC_REDQ_F32_DIGITS) && (q > 1448 || ndigits > 8))   // 1448^2 < 2^21 < 1449^2
+        return set_error(QADIC_E_UNSUPPORTED, "FP32 digits need q^2 < 2^21 and at most 8 digits");
     if (count < 0) return set_error(QADIC_E_INVALID, "negative count");
     if (count == 0) return QADIC_OK;
     if (!in || !out) return set_error(QADIC_E_INVALID, "NULL pointer");
     if (((uintptr_t)in & 15) || ((uintptr_t)out & 15))
         return set_error(QADIC_E_INVALID, "in/out must be 16-byte aligned");
     return launch_redq_pq(p, q, ndigits, in, out, count, (flags & QADIC_REDQ_INT_FLOOR) != 0,
-                          (cudaStream_t)stream);
+                          (flags & QADIC_REDQ_F32_DIGITS) != 0, (cudaStream_t)stream);
 }
 
 int qadic_polymul_fqt_info(uint32_t p, uint32_t N, uint32_t d, uint32_t flags,

@@ -591,6 +591,8 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
     });
     if (converted) {
         TcRec *rp = reinterpret_cast<TcRec *>(host.data() + L.tiles_off);
+        int32_t chunk_ks[kMaxFields];
+        for (int32_t i = 0; i < nfields; ++i) chunk_ks[i] = fp[i].tc_chunk_ks;
         for (size_t i = 0; i < order.size(); ++i) {
             const BTile &t = tiles[order[i]];
             const BProd &P = pp[t.prod];
@@ -607,8 +609,9 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
             r.cols = (int16_t)std::min(bn, P.n - bn * t.tn);
             r.ks = (int16_t)P.kp;
             r.rows8 = (int16_t)((rows + 7) / 8 * 8);
-            r.field = (int16_t)P.field;
-            r.k = (int16_t)k;
+            r.ndrain = (int16_t)((P.kp - 1) / chunk_ks[P.field]);
+            r.field = (uint8_t)P.field;
+            r.k = (uint8_t)k;
             rp[i] = r;
         }
     } else {
@@ -744,10 +747,16 @@ int batched_selected_tiles(uint32_t k, int32_t *index) {
 // For each k present (largest total work first), time every candidate on
 // this batch -- one graph capture as warm-up, then `reps` graph replays
 // between CUDA events -- and keep the fastest before tuning the next k.
+// The candidates are the register-staged kernel's tile shapes: tuning runs
+// that kernel (the workspace is offered with its work-list size only), which
+// the batched call uses when the workspace holds no converted operands and
+// the allocation-free call always; the tensor-core path's tiles follow from
+// the tensor-memory budget per k (tc_bn).
 int autotune_batched(const Field *const *fields, int32_t nfields, const qadic_gemm_desc *descs,
                      int64_t count, void *workspace, size_t ws_bytes, int32_t reps,
                      int32_t *chosen, cudaStream_t stream) {
     if (reps < 1 || reps > 1000) return set_error(QADIC_E_INVALID, "reps outside [1, 1000]");
+    ws_bytes = std::min(ws_bytes, batched_workspace_size(descs, count));
     if (nfields < 1 || nfields > kMaxFields)
         return set_error(QADIC_E_INVALID, "nfields must be in [1, %d]", kMaxFields);
     double work[kMaxK + 1] = {0};

@@ -26,10 +26,12 @@
 //               [B_0; ...; B_{k-1}], so C_t sits at column t BN of the buffer
 //               (k = 2: split sums [C_0 | C_1a | C_1b | C_2], one product per
 //               accumulator per K step)
-//   warps 2-9   epilogue, two warps per 32-lane quarter of tensor memory:
+//   warps 2-9   epilogue in two groups of four warps (one per 32-lane quarter
+//               of tensor memory), group g taking the tiles of buffer g:
 //               in-place reductions at exact-chunk boundaries, then the
 //               tile's plane sums mod p, the fold and the byte stores, while
-//               the next tile's MMAs fill the other buffer.
+//               the other group works on the previous tile and the MMAs fill
+//               the buffer it released.
 // Waits are bounded; on expiry the kernel records QADIC_E_DEVICE_TIMEOUT,
 // lets its copies land and frees tensor memory.
 #include "batched_tile.cuh"
@@ -543,8 +545,8 @@ tc_products_kernel(const uint8_t *__restrict__ ws, int slot_bytes, int a_bytes, 
         }
         for (int b = 0; b < 2; ++b) {
             ptx::mbar_init(&acc_full[b], 1);
-            ptx::mbar_init(&acc_empty[b], 32 * kTcEpiWarps);
-            ptx::mbar_init(&tmem_free[b], 32 * kTcEpiWarps);
+            ptx::mbar_init(&acc_empty[b], 16 * kTcEpiWarps);
+            ptx::mbar_init(&tmem_free[b], 16 * kTcEpiWarps);
         }
         ptx::mbar_init(mma_done, 1);
         *abort_flag = 0;
@@ -655,29 +657,28 @@ tc_products_kernel(const uint8_t *__restrict__ ws, int slot_bytes, int a_bytes, 
     } else {
         // ---------------- epilogue (warps 2..9) ----------------
         const int ew = warp - 2;
-        const int quarter = warp & 3, part = ew / 4;
+        const int quarter = warp & 3, part = ew / 4;   // part: the group, and its buffer
         {
-            // both accumulator buffers start at zero: every MMA accumulates
+            // the group's buffer starts at zero: every MMA accumulates
             const uint32_t tz = tmem_base + ((uint32_t)(quarter * 32) << 16) + 256u * part;
             for (int c = 0; c < 256; c += 8) tmem_zero8(tz + c);
             ptx::tmem_wait_st();
             ptx::tc_fence_before();
-            ptx::mbar_arrive(&tmem_free[0]);
-            ptx::mbar_arrive(&tmem_free[1]);
+            ptx::mbar_arrive(&tmem_free[part]);
         }
         int phase0 = 0, phase1 = 0;
-        int tcount = 0;
+        int tcount = part;
         bool ok = true;
-        TcRec T = tc_rec(ws, hdr, t0, ntiles);
-        for (int t = t0; t < ntiles && ok; t += tstep, ++tcount) {
-            const TcRec Tn = tc_rec(ws, hdr, t + tstep, ntiles);
+        TcRec T = tc_rec(ws, hdr, t0 + part * tstep, ntiles);
+        for (int t = t0 + part * tstep; t < ntiles && ok; t += 2 * tstep, tcount += 2) {
+            const TcRec Tn = tc_rec(ws, hdr, t + 2 * tstep, ntiles);
             const int b = tcount & 1;
             const uint32_t tacc = tmem_base + 256u * b + ((uint32_t)(quarter * 32) << 16);
             const BFieldParams &F = sF[T.field];
             const int bn = tc_bn(T.k);
-            const int w = bn / 2, c0 = part * w;
+            const int w = bn, c0 = 0;
             const int nacc = T.k == 2 ? 4 : 2 * T.k - 1;
-            const int ndrain = (T.ks - 1) / F.tc_chunk_ks;
+            const int ndrain = T.ndrain;
             auto ready = [&]() {
                 const bool r = ptx::mbar_wait(&acc_full[b], (uint32_t)(b ? phase1 : phase0) & 1);
                 if (b) ++phase1;

@@ -35,6 +35,7 @@ struct PackParams {
     int64_t rows, cols, ld_in, ld_out;
     uint32_t p, k, s, order, h;
     uint32_t m32;                 // ceil(2^32/p)
+    float inv_p;                  // 1/p rounded to FP32
     const double *log_f64;        // global tables
     const int8_t *log_centred;
     const uint8_t *antilog;
@@ -255,9 +256,44 @@ __device__ __forceinline__ uint32_t centre_pair(uint32_t b0, uint32_t b1, const 
     return (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
 }
 
+// Odd p, in FP32 on the full-rate pipes (no integer-to-float or bf16
+// conversion instructions): a byte b placed under the exponent of 2^23 gives
+// the float 2^23 + b, so one subtraction yields the coefficient v exactly
+// (int8 input: b ^ 0x80 = v + 128).  r = the integer nearest v/p, by adding
+// and subtracting 1.5 * 2^23 after the multiply; v/p is never within 1/(2p)
+// of a half-integer for odd p, far more than the FP32 error of v * (1/p)
+// for |v| <= 255, so r is exact and c = v - p r is the centred residue in
+// [-(p-1)/2, (p-1)/2] (the same value, with the same +0 for zero, as
+// reducing into [0, p) and centring).  |c| < 2^8 needs at most 8 significant
+// bits, so its bf16 is the upper half of its FP32 bits.
+template <int IN>
+__device__ __forceinline__ uint32_t centre_pair_odd(uint32_t w, uint32_t sel0, uint32_t sel1,
+                                                    const PackParams &P) {
+    constexpr float kBias = IN == IN_I8 ? 8388608.0f + 128.0f : 8388608.0f;
+    constexpr float kRound = 12582912.0f;   // 1.5 * 2^23
+    const float pf = (float)P.p;
+    const float v0 = __uint_as_float(__byte_perm(w, 0x4B000000u, sel0)) - kBias;
+    const float v1 = __uint_as_float(__byte_perm(w, 0x4B000000u, sel1)) - kBias;
+    const float r0 = __fmaf_rn(v0, P.inv_p, kRound) - kRound;
+    const float r1 = __fmaf_rn(v1, P.inv_p, kRound) - kRound;
+    const float c0 = __fmaf_rn(-pf, r0, v0);
+    const float c1 = __fmaf_rn(-pf, r1, v1);
+    return __byte_perm(__float_as_uint(c0), __float_as_uint(c1), 0x7632);
+}
+
 template <int IN>
 __device__ __forceinline__ void convert16(uint4 w, const PackParams &P, uint32_t (&o)[8]) {
     const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+    if (P.p & 1) {
+        // byte j of the word to byte 0 under 0x4B (bytes 4-7 of the pair)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t x = IN == IN_I8 ? words[q] ^ 0x80808080u : words[q];
+            o[2 * q] = centre_pair_odd<IN>(x, 0x7440, 0x7441, P);
+            o[2 * q + 1] = centre_pair_odd<IN>(x, 0x7442, 0x7443, P);
+        }
+        return;
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         o[2 * q] = centre_pair<IN>(words[q] & 0xff, (words[q] >> 8) & 0xff, P);
@@ -484,6 +520,7 @@ int launch_pack(const Field &f, int in_fmt, const void *in, int64_t rows, int64_
     P.order = f.order;
     P.h = f.h;
     P.m32 = make_mod_small(f.p);
+    P.inv_p = 1.0f / (float)f.p;
     P.log_f64 = f.d_log_f64;
     P.log_centred = f.d_log_centred;
     P.antilog = f.d_antilog;
@@ -527,6 +564,7 @@ PackParams pack_params(const Field &f, int64_t rows, int64_t cols, int64_t ld_in
     P.order = f.order;
     P.h = f.h;
     P.m32 = make_mod_small(f.p);
+    P.inv_p = 1.0f / (float)f.p;
     P.log_f64 = f.d_log_f64;
     P.log_centred = f.d_log_centred;
     P.antilog = f.d_antilog;

@@ -24,8 +24,9 @@ constexpr int kMaxPairs = 4;   // pairs per thread per chunk: 1 for small batche
 // Signed integer value of a double holding an exact integer of magnitude
 // < 2^53, from its bit pattern (integer instructions only).
 __device__ __forceinline__ int64_t f64_to_i64_exact(double x) {
-    const int64_t mag = (int64_t)f64_to_u64_exact(fabs(x));
-    return x < 0.0 ? -mag : mag;
+    const int64_t bits = __double_as_longlong(x);
+    const int64_t mag = (int64_t)f64_to_u64_exact(__longlong_as_double(bits & INT64_MAX));
+    return bits < 0 ? -mag : mag;   // the sign bit, not an FP64 compare
 }
 
 // The K coefficient bytes of pair idx, byte j at bits 8j: one vector load
@@ -113,12 +114,17 @@ __device__ __forceinline__ uint32_t operand_word32(uint64_t bytes, uint32_t p, u
 // bit patterns, so the FP64 pipe only sees the multiply (and the FMA).
 // K (the number of coefficients of an operand) is a template argument so
 // that every loop over coefficients unrolls and every shift amount is a
-// register computed once per thread.
-template <int MODE, int K, int kPairs>
+// register computed once per thread.  Q8: q = 2^8 and K <= 4, so r < 2^56
+// and its base-q digits are its bytes; REDQ then runs on the two 32-bit
+// halves of r separately (each half is a q-adic word of its own, since no
+// digit carries into the next), with one 32-bit floor by p per half and
+// constant byte shifts.
+template <int MODE, int K, int kPairs, bool Q8>
 __global__ void __launch_bounds__(kThreads)
 polymul_kernel(const uint8_t *__restrict__ a, const uint8_t *__restrict__ b,
                uint8_t *__restrict__ out, int64_t count, uint32_t p, uint32_t s,
-               uint32_t qneg_mod_p, Div64 divp) {
+               uint32_t qneg_mod_p, Div64 divp, Div32 divp32) {
+    static_assert(!Q8 || K <= 4, "q = 2^8 halves hold four digits each");
     extern __shared__ __align__(16) uint8_t smem[];
     constexpr int kChunk = kThreads * kPairs;
     constexpr int D = 2 * K - 1;
@@ -181,17 +187,40 @@ polymul_kernel(const uint8_t *__restrict__ a, const uint8_t *__restrict__ b,
                     r = hi_u + (uint64_t)f64_to_i64_exact(lo);
                 }
             }
-            // REDQ (Alg. 2): rop = floor(r/p); u_i = floor(r/q^i) - p floor(rop/q^i)
-            // needs only the low 32 bits of each shifted word (u_i < p).
-            const uint64_t rop = div64(r, divp);
             uint8_t *dst = stage + (j * kThreads + threadIdx.x) * D;
-            uint32_t u_next = 0;
+            if constexpr (Q8) {
+                // REDQ (Alg. 2) per 32-bit half x: o = floor(x/p), u_i =
+                // floor(x/q^i) - p floor(o/q^i), mu_i = (u_i - q u_{i+1}) mod p
+                // through the p^2 table, the half's top digit mu = u
+                const uint32_t x[2] = {(uint32_t)r, (uint32_t)(r >> 32)};
 #pragma unroll
-            for (int i = D - 1; i >= 0; --i) {
-                const uint32_t sh = s * i;
-                const uint32_t ui = (uint32_t)(r >> sh) - p * (uint32_t)(rop >> sh);
-                dst[i] = (i == D - 1) ? (uint8_t)ui : corr[ui * p + u_next];
-                u_next = ui;
+                for (int hf = 0; hf < 2; ++hf) {
+                    constexpr int kLo[2] = {0, 4};
+                    const int nd = D - kLo[hf] < 4 ? D - kLo[hf] : 4;
+                    if (nd <= 0) break;
+                    const uint32_t o = div32(x[hf], divp32);
+                    uint32_t u_next = 0;
+#pragma unroll
+                    for (int i = 3; i >= 0; --i) {
+                        if (i >= nd) continue;
+                        const uint32_t ui = (x[hf] >> (8 * i)) - p * (o >> (8 * i));
+                        dst[kLo[hf] + i] = (i == nd - 1) ? (uint8_t)ui : corr[ui * p + u_next];
+                        u_next = ui;
+                    }
+                }
+            } else {
+                // REDQ (Alg. 2): rop = floor(r/p); u_i = floor(r/q^i) - p
+                // floor(rop/q^i) needs only the low 32 bits of each shifted
+                // word (u_i < p).
+                const uint64_t rop = div64(r, divp);
+                uint32_t u_next = 0;
+#pragma unroll
+                for (int i = D - 1; i >= 0; --i) {
+                    const uint32_t sh = s * i;
+                    const uint32_t ui = (uint32_t)(r >> sh) - p * (uint32_t)(rop >> sh);
+                    dst[i] = (i == D - 1) ? (uint8_t)ui : corr[ui * p + u_next];
+                    u_next = ui;
+                }
             }
         }
         __syncthreads();
@@ -210,30 +239,36 @@ polymul_kernel(const uint8_t *__restrict__ a, const uint8_t *__restrict__ b,
     }
 }
 
+using PolymulKernel = void (*)(const uint8_t *, const uint8_t *, uint8_t *, int64_t, uint32_t,
+                               uint32_t, uint32_t, Div64, Div32);
+
 template <int MODE, int K>
-auto pick_kernel(int pairs) {
-    return pairs == kMaxPairs ? polymul_kernel<MODE, K, kMaxPairs> : polymul_kernel<MODE, K, 1>;
+PolymulKernel pick_kernel(int pairs, bool q8) {
+    if constexpr (K <= 4) {
+        if (q8)
+            return pairs == kMaxPairs ? polymul_kernel<MODE, K, kMaxPairs, true>
+                                      : polymul_kernel<MODE, K, 1, true>;
+    }
+    return pairs == kMaxPairs ? polymul_kernel<MODE, K, kMaxPairs, false>
+                              : polymul_kernel<MODE, K, 1, false>;
 }
 
 template <int K>
-auto pick_kernel(int mode, int pairs) {
-    return mode == 2 ? pick_kernel<2, K>(pairs)
-                     : mode == 1 ? pick_kernel<1, K>(pairs) : pick_kernel<0, K>(pairs);
+PolymulKernel pick_kernel(int mode, int pairs, bool q8) {
+    return mode == 2 ? pick_kernel<2, K>(pairs, q8)
+                     : mode == 1 ? pick_kernel<1, K>(pairs, q8) : pick_kernel<0, K>(pairs, q8);
 }
 
-using PolymulKernel = void (*)(const uint8_t *, const uint8_t *, uint8_t *, int64_t, uint32_t,
-                               uint32_t, uint32_t, Div64);
-
-PolymulKernel select_kernel(uint32_t k, int mode, int pairs) {
+PolymulKernel select_kernel(uint32_t k, int mode, int pairs, bool q8) {
     switch (k) {
-        case 1: return pick_kernel<1>(mode, pairs);
-        case 2: return pick_kernel<2>(mode, pairs);
-        case 3: return pick_kernel<3>(mode, pairs);
-        case 4: return pick_kernel<4>(mode, pairs);
-        case 5: return pick_kernel<5>(mode, pairs);
-        case 6: return pick_kernel<6>(mode, pairs);
-        case 7: return pick_kernel<7>(mode, pairs);
-        default: return pick_kernel<8>(mode, pairs);
+        case 1: return pick_kernel<1>(mode, pairs, q8);
+        case 2: return pick_kernel<2>(mode, pairs, q8);
+        case 3: return pick_kernel<3>(mode, pairs, q8);
+        case 4: return pick_kernel<4>(mode, pairs, q8);
+        case 5: return pick_kernel<5>(mode, pairs, q8);
+        case 6: return pick_kernel<6>(mode, pairs, q8);
+        case 7: return pick_kernel<7>(mode, pairs, q8);
+        default: return pick_kernel<8>(mode, pairs, q8);
     }
 }
 
@@ -255,7 +290,7 @@ int launch_polymul(uint32_t p, uint32_t k, uint32_t log2_q, int mode, const uint
     const int pairs = count >= (int64_t)sms * kThreads * kMaxPairs * 2 ? kMaxPairs : 1;
     const int64_t chunk = (int64_t)kThreads * pairs;
     const size_t smem = ((p * p + 15) & ~15u) + (size_t)chunk * (2 * k - 1);
-    const PolymulKernel kern = select_kernel(k, mode, pairs);
+    const PolymulKernel kern = select_kernel(k, mode, pairs, log2_q == 8 && k <= 4);
     if (smem > 48 * 1024) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
@@ -265,7 +300,7 @@ int launch_polymul(uint32_t p, uint32_t k, uint32_t log2_q, int mode, const uint
     int64_t blocks = (count + chunk - 1) / chunk;
     blocks = std::min<int64_t>(blocks, resident_blocks(kern, kThreads, smem));
     kern<<<(unsigned)blocks, kThreads, smem, stream>>>(a, b, out, count, p, log2_q, qneg,
-                                                       make_div64(p));
+                                                       make_div64(p), make_div32(p));
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(QADIC_E_CUDA, "polymul launch: %s", cudaGetErrorString(e));
     return QADIC_OK;

@@ -242,6 +242,13 @@ struct RedqPqParams {
     uint32_t qs;                       // q^j32 when split
     Div64 div_qs;                      // floor(r / q^j32)
     double inv_qs_up;                  // 1/q^j32 rounded toward +infinity
+    // digits in FP32 (QADIC_REDQ_F32_DIGITS, q^2 < 2^21)
+    uint32_t Q;                        // q^2
+    uint32_t k64;                      // leading floors by q^2 whose dividend may reach 2^32
+    Div64 div_Q;
+    Div32 div_Q32;
+    float fq, inv_q, c_q;              // q, RN(1/q), RN(1/(2q) - 1/2)
+    float fp, inv_p, c_p;              // the same for p
     uint64_t qpow[kMaxPqDigits];       // q^j
 };
 
@@ -348,7 +355,70 @@ __device__ __forceinline__ double redq_pq_word_nd(double x, const RedqPqParams &
     return u64_to_f64_exact(rho);
 }
 
-// S > 0: each word splits at q^S (redq_pq_word_split).
+// floor(X / m) for an integer-valued float 0 <= X < 2^21 and an integer m
+// >= 2: Y = (X + 1/2) / m - 1/2 lies within 1/2 - 1/(2m) of floor(X / m), so
+// its nearest integer is the floor; computed as fma(X, RN(1/m), RN(1/(2m) -
+// 1/2)), whose error is below (2X/m + 3/4) 2^-24 < 1/(2m) for X < 2^21, and
+// rounded to an integer by adding and subtracting 1.5 * 2^23.
+__device__ __forceinline__ float floor_div_f32(float X, float inv_m, float c_m) {
+    constexpr float kRound = 12582912.0f;
+    return __fadd_rn(__fadd_rn(__fmaf_rn(X, inv_m, c_m), kRound), -kRound);
+}
+
+// v < 2^23 as a float (placed under the exponent of 2^23), and back.
+__device__ __forceinline__ float u32_to_f32_small(uint32_t v) {
+    return __fadd_rn(__uint_as_float(0x4B000000u | v), -8388608.0f);
+}
+__device__ __forceinline__ uint32_t f32_small_to_u32(float f) {
+    return __float_as_uint(__fadd_rn(f, 8388608.0f)) & 0x7FFFFFu;
+}
+
+// ND digits, q^2 < 2^21: the word is cut into chunks of two base-q digits
+// by integer floors by q^2 (64-bit while the dividend may reach 2^32, then
+// 32-bit); within a chunk X = hi q + lo (< 2^21, exact in FP32) the floors
+// by q and by p are FP32 ones (floor_div_f32), all on the full-rate FP32
+// pipe: u = digit mod p, and rho's chunk u_hi q + u_lo < q^2.  The chunks
+// of rho are joined by Horner's rule in q^2.
+template <int ND>
+__device__ __forceinline__ double redq_pq_word_f32(double x, const RedqPqParams &P) {
+    constexpr int NC = (ND + 1) / 2;   // the top chunk holds one digit when ND is odd
+    uint64_t t = f64_to_u64_exact(x);
+    uint32_t c[NC];
+#pragma unroll
+    for (int i = 0; i < NC - 1; ++i) {
+        if (i < (int)P.k64) {
+            const uint64_t tn = div64(t, P.div_Q);
+            c[i] = (uint32_t)t - P.Q * (uint32_t)tn;
+            t = tn;
+        } else {
+            const uint32_t t32 = (uint32_t)t;
+            const uint32_t tn = div32(t32, P.div_Q32);
+            c[i] = t32 - P.Q * tn;
+            t = tn;
+        }
+    }
+    c[NC - 1] = (uint32_t)t;   // below q^(ND - 2 (NC - 1)) for words below q^ND
+    uint64_t rho = 0;
+#pragma unroll
+    for (int i = NC - 1; i >= 0; --i) {
+        const float X = u32_to_f32_small(c[i]);
+        float r;
+        if (2 * i + 1 < ND) {
+            const float hi = floor_div_f32(X, P.inv_q, P.c_q);
+            const float lo = __fmaf_rn(-P.fq, hi, X);
+            const float uhi = __fmaf_rn(-P.fp, floor_div_f32(hi, P.inv_p, P.c_p), hi);
+            const float ulo = __fmaf_rn(-P.fp, floor_div_f32(lo, P.inv_p, P.c_p), lo);
+            r = __fmaf_rn(P.fq, uhi, ulo);
+        } else {
+            r = __fmaf_rn(-P.fp, floor_div_f32(X, P.inv_p, P.c_p), X);
+        }
+        rho = rho * P.Q + f32_small_to_u32(r);
+    }
+    return u64_to_f64_exact(rho);
+}
+
+// S > 0: each word splits at q^S (redq_pq_word_split); S < 0: digits in
+// FP32 (redq_pq_word_f32).
 template <bool INT_FLOOR, int ND, int S = 0>
 __global__ void __launch_bounds__(kThreads)
 redq_pq_kernel(const double *__restrict__ in, double *__restrict__ out, int64_t count,
@@ -358,7 +428,8 @@ redq_pq_kernel(const double *__restrict__ in, double *__restrict__ out, int64_t 
     double2 *out2 = reinterpret_cast<double2 *>(out);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     auto word = [&](double v) {
-        if constexpr (S > 0) return redq_pq_word_split<INT_FLOOR, ND, S>(v, P);
+        if constexpr (S < 0) return redq_pq_word_f32<ND>(v, P);
+        else if constexpr (S > 0) return redq_pq_word_split<INT_FLOOR, ND, S>(v, P);
         else if constexpr (ND > 0) return redq_pq_word_nd<INT_FLOOR, ND>(v, P);
         else return redq_pq_word<INT_FLOOR>(v, P);
     };
@@ -483,9 +554,13 @@ int launch_redq(uint32_t p, uint32_t log2_q, uint32_t ndigits, const double *in,
 }
 
 int launch_redq_pq(uint32_t p, uint64_t q, uint32_t ndigits, const double *in, double *out,
-                   int64_t count, bool int_floor, cudaStream_t stream) {
+                   int64_t count, bool int_floor, bool f32_digits, cudaStream_t stream) {
     if (ndigits < 1 || ndigits > (uint32_t)kMaxPqDigits)
         return set_error(QADIC_E_INVALID, "ndigits outside [1, %d]", kMaxPqDigits);
+    if (f32_digits && (q > 1448 || ndigits > 8))   // q^2 < 2^21
+        return set_error(QADIC_E_UNSUPPORTED,
+                         "FP32 digits need q^2 < 2^21 and at most 8 digits (q = %llu, %u digits)",
+                         (unsigned long long)q, ndigits);
     RedqPqParams P{};
     P.p = p;
     P.d = ndigits - 1;
@@ -517,6 +592,32 @@ int launch_redq_pq(uint32_t p, uint64_t q, uint32_t ndigits, const double *in, d
         P.qs = (uint32_t)P.qpow[P.j32];
         P.div_qs = make_div64(P.qpow[P.j32]);
         P.inv_qs_up = inv_up(P.qpow[P.j32]);
+    }
+    if (f32_digits) {
+        P.Q = (uint32_t)(q * q);
+        P.div_Q = make_div64(P.Q);
+        P.div_Q32 = make_div32(P.Q);
+        // the dividend of floor i is below q^(ndigits - 2i)
+        P.k64 = 0;
+        for (uint32_t i = 0; 2 * i + 2 <= ndigits; ++i) {
+            unsigned __int128 bound = 1;
+            for (uint32_t j = 2 * i; j < ndigits; ++j) bound *= q;
+            if (bound > ((unsigned __int128)1 << 32)) P.k64 = i + 1;
+        }
+        P.fq = (float)q;
+        P.inv_q = 1.0f / (float)q;
+        P.c_q = (float)(0.5 / (double)q - 0.5);
+        P.fp = (float)p;
+        P.inv_p = 1.0f / (float)p;
+        P.c_p = (float)(0.5 / (double)p - 0.5);
+        switch (ndigits) {
+#define QADIC_PQ_F32(N) \
+    case N: return launch_stream(redq_pq_kernel<true, N, -1>, in, out, count, P, 0, stream, "redq_pq");
+            QADIC_PQ_F32(1) QADIC_PQ_F32(2) QADIC_PQ_F32(3) QADIC_PQ_F32(4)
+            QADIC_PQ_F32(5) QADIC_PQ_F32(6) QADIC_PQ_F32(7) QADIC_PQ_F32(8)
+#undef QADIC_PQ_F32
+            default: break;
+        }
     }
     if (P.split) {
         switch ((int_floor ? 256 : 0) + ndigits * 16 + P.j32) {

@@ -81,7 +81,7 @@ int launch_polymul_fqt(uint32_t p, uint32_t N, uint32_t d, bool int_words, const
 
 // REDQ with q a multiple of p (q^ndigits <= 2^51): no correction step.
 int launch_redq_pq(uint32_t p, uint64_t q, uint32_t ndigits, const double *in, double *out,
-                   int64_t count, bool int_floor, cudaStream_t stream);
+                   int64_t count, bool int_floor, bool f32_digits, cudaStream_t stream);
 
 int launch_pack(const Field &f, int in_fmt, const void *in, int64_t rows, int64_t cols,
                 int64_t ld_in, int out_fmt, void *out, int64_t ld_out, cudaStream_t stream);

@@ -149,6 +149,14 @@ def test_redq_pq_rejections():
     assert L.qadic_redq_pq(7, 1176, 5, ctypes.c_void_p(8), b, 10, 0, None) == q.E_INVALID
     assert L.qadic_redq_pq(9, 18, 5, a, b, 10, 0, None) == q.E_INVALID
     assert L.qadic_redq_pq(7, 1176, 5, None, None, 0, 0, None) == q.OK
+    # FP32 digits: one floor flag at most, q^2 < 2^21 (q <= 1448), <= 8 digits
+    F32 = q.REDQ_F32_DIGITS
+    assert L.qadic_redq_pq(7, 1176, 5, a, b, 10, F32 | q.REDQ_INT_FLOOR, None) == q.E_INVALID
+    assert L.qadic_redq_pq(3, 1449, 4, a, b, 10, F32, None) == q.E_UNSUPPORTED
+    assert L.qadic_redq_pq(2, 2 ** 32, 1, a, b, 10, F32, None) == q.E_UNSUPPORTED
+    assert L.qadic_redq_pq(3, 3, 9, a, b, 10, F32, None) == q.E_UNSUPPORTED
+    assert L.qadic_redq_pq(181, 1448, 4, None, None, 0, F32, None) == q.OK
+    assert L.qadic_redq_pq(3, 3, 8, None, None, 0, F32, None) == q.OK
 
 
 @pytest.mark.parametrize("p", [2, 3, 7, 31, 101, 251])

@@ -126,10 +126,10 @@ def test_redq_sweep_2_28_words(torch, orc):
     want = torch.from_numpy(orc.redq(7, bench.PQ_Q, 4, wq)).cuda()
     d = torch.from_numpy(wq).cuda()
     del wq
-    for int_floor in (False, True):
+    for kw in (dict(int_floor=False), dict(int_floor=True), dict(f32_digits=True)):
         out.zero_()
-        q.redq_pq(7, bench.PQ_Q, 5, d, out=out, int_floor=int_floor)
-        assert torch.equal(out, want), int_floor
+        q.redq_pq(7, bench.PQ_Q, 5, d, out=out, **kw)
+        assert torch.equal(out, want), kw
     del d, want, out
     torch.cuda.empty_cache()
 

@@ -144,6 +144,25 @@ def test_redq_pq_parameters(torch, orc, p, q_, nd):
     for int_floor in (False, True):
         out = q.redq_pq(p, q_, nd, dev(torch, w), int_floor=int_floor)
         assert np.array_equal(host(out), want), int_floor
+    if q_ <= 1448 and nd <= 8:      # q^2 < 2^21: the FP32-digit form applies
+        out = q.redq_pq(p, q_, nd, dev(torch, w), f32_digits=True)
+        assert np.array_equal(host(out), want), "f32 digits"
+    else:
+        with pytest.raises(q.QadicError):
+            q.redq_pq(p, q_, nd, dev(torch, w), f32_digits=True)
+
+
+@pytest.mark.parametrize("p,q_,nd", [(2, 1448, 4), (181, 1448, 4), (3, 1401, 4), (2, 2, 8),
+                                     (5, 5, 1), (7, 1176, 1), (7, 1176, 2), (7, 1176, 3),
+                                     (251, 1255, 4), (5, 1445, 4)])
+def test_redq_pq_f32_digits_limits(torch, orc, p, q_, nd):
+    """The FP32-digit form at its largest q (1448^2 < 2^21), one to eight
+    digits, chunks with and without a lone top digit."""
+    w = W.redq_words_q(20001, nd, q_, salt=p + nd)
+    top = float(q_ ** nd - 1)
+    w = np.concatenate([w, [top, 0.0, float(q_ - 1), float(q_)]])
+    out = q.redq_pq(p, q_, nd, dev(torch, w), f32_digits=True)
+    assert np.array_equal(host(out), orc.redq(p, q_, nd - 1, w))
 
 
 def test_redq_pq_adversarial_words(torch, orc):
@@ -154,10 +173,10 @@ def test_redq_pq_adversarial_words(torch, orc):
     words = np.array([sum(d * q_ ** i for i, d in enumerate(x)) for x in digs] * 3 + [1.0],
                      dtype=np.float64)
     assert words.max() == q_ ** nd - 1
-    for int_floor in (False, True):
-        out = q.redq_pq(p, q_, nd, dev(torch, words), int_floor=int_floor)
+    for kw in (dict(int_floor=False), dict(int_floor=True), dict(f32_digits=True)):
+        out = q.redq_pq(p, q_, nd, dev(torch, words), **kw)
         assert np.array_equal(host(out), orc.redq(p, q_, nd - 1, words))
-        one = q.redq_pq(p, q_, nd, dev(torch, words[:1]), int_floor=int_floor)
+        one = q.redq_pq(p, q_, nd, dev(torch, words[:1]), **kw)
         assert np.array_equal(host(one), orc.redq(p, q_, nd - 1, words[:1]))
 
 
@@ -165,6 +184,9 @@ def test_redq_pq_in_place(torch, orc):
     w = W.redq_words_q(4096, 5, 1176, salt=9)
     x = dev(torch, w)
     q.redq_pq(7, 1176, 5, x, out=x)
+    assert np.array_equal(host(x), orc.redq(7, 1176, 4, w))
+    x = dev(torch, w)
+    q.redq_pq(7, 1176, 5, x, out=x, f32_digits=True)
     assert np.array_equal(host(x), orc.redq(7, 1176, 4, w))
 
 
