@@ -213,10 +213,37 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
                  : "r"(taddr));
 }
 
+// 32 lanes x 4 columns.
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&v)[4]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+                 : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_zero4(uint32_t taddr) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%1,%1,%1};" ::"r"(taddr), "r"(0u)
+                 : "memory");
+}
+
+template <int CW>
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, uint32_t (&v)[CW]) {
+    if constexpr (CW == 8) tmem_ld8(taddr, v);
+    else tmem_ld4(taddr, v);
+}
+
+template <int CW>
+__device__ __forceinline__ void tmem_zero_cols(uint32_t taddr);
+
 __device__ __forceinline__ void tmem_zero8(uint32_t taddr) {
     asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
                  "r"(0u)
                  : "memory");
+}
+
+template <int CW>
+__device__ __forceinline__ void tmem_zero_cols(uint32_t taddr) {
+    if constexpr (CW == 8) tmem_zero8(taddr);
+    else tmem_zero4(taddr);
 }
 
 __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8]) {
@@ -259,30 +286,41 @@ __device__ __forceinline__ void tc_drain(uint32_t tacc, int nacc, int bn, int c0
     ptx::tmem_wait_st();
 }
 
+// o mod p for an integer-valued float |o| < 2^23 and 3 <= p < 256, on the
+// full-rate FP32 pipe: t = o / p rounded to an integer by adding and
+// subtracting 1.5 * 2^23 (|o / p| < 2^22), possibly one off, r = o - p t
+// exact and within (-2p, 2p), one correction each way, and the integer r
+// read off the bits of r + 2^23.
 __device__ __forceinline__ uint32_t tc_mod(float o, float pf, float inv_pf) {
-    float r = fmaf(-pf, floorf(o * inv_pf), o);   // exact: an integer of magnitude < 2p
+    const float t = __fadd_rn(__fmaf_rn(o, inv_pf, 12582912.0f), -12582912.0f);
+    float r = __fmaf_rn(-pf, t, o);
     if (r < 0.f) r += pf;
     if (r >= pf) r -= pf;
-    return (uint32_t)r;
+    return __float_as_uint(r + 8388608.0f) & 0xffu;
 }
 
 // Stores 8 columns of one output plane for the warp's 32 rows: lane r holds
-// row r's 8 bytes in (lo, hi).  The rows go through a 256-byte staging area
-// of the warp in shared memory, so that each store instruction writes 8
-// consecutive bytes of each of 4 rows (the rows of a plane start at any byte,
-// so the stores are bytes; with one row per lane each instruction would
-// touch 32 rows).  p0 = the lane's byte of row (lane / 8) in this plane.
-__device__ __forceinline__ void store_rows8(uint8_t *stage, const uint8_t *p0, int64_t step4,
-                                            int rows_left, bool col_ok, uint32_t lo, uint32_t hi,
-                                            int lane) {
-    __syncwarp();
-    reinterpret_cast<uint2 *>(stage)[lane] = make_uint2(lo, hi);
-    __syncwarp();
+// row r's 8 bytes in (lo, hi).  Store j writes byte lane % 8 of row
+// lane / 8 + 4 j, taken from that row's lane by two shuffles, so that each
+// store instruction covers 8 consecutive bytes of each of 4 rows (the rows
+// of a plane start at any byte, so the stores are bytes; with one row per
+// lane each instruction would touch 32 rows).  Shuffles, not a shared-memory
+// exchange: a warp barrier between exchange steps would also wait for this
+// warp's global stores already in flight.  p0 = the lane's byte of row
+// (lane / 8) in this plane; rows_left, cols_left: valid rows and columns
+// from the first of these.
+__device__ __forceinline__ void store_rows8(const uint8_t *p0, int64_t step4, int rows_left,
+                                            int cols_left, uint32_t lo, uint32_t hi, int lane) {
     uint8_t *p = const_cast<uint8_t *>(p0);
+    const uint32_t sh = 8u * (lane & 3);
+    const bool col_ok = (lane & 7) < cols_left;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        const uint8_t v = stage[lane + 32 * j];   // row lane / 8 + 4 j, byte lane % 8
-        if (col_ok && (lane >> 3) + 4 * j < rows_left) *p = v;
+        const int src = (lane >> 3) + 4 * j;   // the row this store writes
+        const uint32_t wl = __shfl_sync(0xffffffffu, lo, src);
+        const uint32_t wh = __shfl_sync(0xffffffffu, hi, src);
+        const uint8_t v = (uint8_t)(((lane & 4) ? wh : wl) >> sh);
+        if (col_ok && src < rows_left) *p = v;
         p += step4;
     }
 }
@@ -297,7 +335,7 @@ __device__ __forceinline__ uint32_t spread4(uint32_t x) { return ((x & 0xFu) * 0
 template <int KP, bool P2, class Release>
 __device__ __forceinline__ void tc_epilogue(uint32_t tacc, const TcRec &T,
                                             const BFieldParams &F, int row0, int c0, int w,
-                                            uint8_t *stage, Release release) {
+                                            Release release) {
     constexpr int NACC = KP == 2 ? 4 : 2 * KP - 1;
     constexpr int BN = tc_bn(KP);
     // tile-relative coordinates: rows [0, T.rows), columns [0, T.cols)
@@ -345,14 +383,14 @@ __device__ __forceinline__ void tc_epilogue(uint32_t tacc, const TcRec &T,
                 }
             }
             if (rows_left <= 0 || c >= T.cols) continue;   // the same for the whole warp
-            const bool col_ok = c + (lane & 7) < T.cols;
+            const int cols_left = T.cols - c;
 #pragma unroll
             for (int i = 0; i < KP; ++i) {
                 uint32_t o = mt[i];
 #pragma unroll
                 for (int t = KP; t < 2 * KP - 1; ++t)
                     o ^= mt[t] & (0u - ((fold2[t - KP] >> i) & 1u));
-                store_rows8(stage, lane_base + (int64_t)i * c_plane + c, step4, rows_left, col_ok,
+                store_rows8(lane_base + (int64_t)i * c_plane + c, step4, rows_left, cols_left,
                             spread4(o), spread4(o >> 4), lane);
             }
         }
@@ -373,82 +411,97 @@ __device__ __forceinline__ void tc_epilogue(uint32_t tacc, const TcRec &T,
         const double kel = (double)T.ks * (F.fp8 ? 32 : 16);
         const double hh = (double)F.h * F.h;
         const bool direct = kel * hh * (KP == 2 ? 2 : KP) * (1.0 + (KP - 1) * (double)(F.p - 1)) < 8388608.0;
+        // columns per tensor-memory read: 4 for k >= 4 (up to 15
+        // accumulators, then their sums, live at once), else 8
+        constexpr int CW = KP >= 5 ? 4 : 8;
         for (int c = c0; c < c0 + w; c += 8) {
-            float s[2 * KP - 1][8];
+            const bool active = rows_left > 0 && c < T.cols;   // the same for the whole warp
+            uint32_t lo[KP], hi[KP];
 #pragma unroll
-            for (int t = 0; t < 2 * KP - 1; ++t)
+            for (int i = 0; i < KP; ++i) lo[i] = hi[i] = 0;
 #pragma unroll
-                for (int e = 0; e < 8; ++e) s[t][e] = 0.f;
-            {
-                uint32_t v[NACC][8];
+            for (int h = 0; h < 8 / CW; ++h) {
+                const int cc = c + h * CW;
+                // plane sums C_t of these columns (k = 2: C_1 = C_1a + C_1b),
+                // each accumulator reduced first unless the fold is exact on
+                // the raw sums
+                float sum[2 * KP - 1][CW];
+                {
+                    uint32_t v[NACC][CW];
 #pragma unroll
-                for (int a = 0; a < NACC; ++a) tmem_ld8(tacc + a * BN + c, v[a]);
-                ptx::tmem_wait_ld();
+                    for (int a = 0; a < NACC; ++a) tmem_ld_cols<CW>(tacc + a * BN + cc, v[a]);
+                    ptx::tmem_wait_ld();
 #pragma unroll
-                for (int a = 0; a < NACC; ++a) tmem_zero8(tacc + a * BN + c);
-                if (c + 8 >= c0 + w) release();
+                    for (int a = 0; a < NACC; ++a) tmem_zero_cols<CW>(tacc + a * BN + cc);
+                    if (h + 1 == 8 / CW && c + 8 >= c0 + w) release();
 #pragma unroll
-                for (int a = 0; a < NACC; ++a) {
-                    const int t = KP == 2 ? (a / 2) + (a % 2) : a;
+                    for (int a = 0; a < NACC; ++a) {
+                        const int t = KP == 2 ? (a / 2) + (a % 2) : a;
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const float x = __uint_as_float(v[a][e]);
-                        s[t][e] += direct ? x : fmaf(-pf, rintf(x * inv_pf), x);
+                        for (int e = 0; e < CW; ++e) {
+                            const float x = __uint_as_float(v[a][e]);
+                            const float y = direct ? x : fmaf(-pf, rintf(x * inv_pf), x);
+                            if (KP == 2 && a == 2) sum[t][e] += y;
+                            else sum[t][e] = y;
+                        }
+                    }
+                }
+                if (!active) continue;
+#pragma unroll
+                for (int i = 0; i < KP; ++i) {
+#pragma unroll
+                    for (int e = 0; e < CW; ++e) {
+                        float o = sum[i][e];
+#pragma unroll
+                        for (int t = KP; t < 2 * KP - 1; ++t) {
+                            const float fv = KP <= 4 ? foldf[(KP <= 4 ? (t - KP) * KP + i : 0)]
+                                                     : (float)F.fold[(t - KP) * KP + i];
+                            o = fmaf(sum[t][e], fv, o);
+                        }
+                        const uint32_t b = tc_mod(o, pf, inv_pf);
+                        const int pos = h * CW + e;
+                        if (pos < 4) lo[i] |= b << (8 * pos);
+                        else hi[i] |= b << (8 * (pos - 4));
                     }
                 }
             }
-            if (rows_left <= 0 || c >= T.cols) continue;   // the same for the whole warp
-            const bool col_ok = c + (lane & 7) < T.cols;
+            if (!active) continue;
+            const int cols_left = T.cols - c;
 #pragma unroll
-            for (int i = 0; i < KP; ++i) {
-                uint32_t lo = 0, hi = 0;
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    float o = s[i][e];
-#pragma unroll
-                    for (int t = KP; t < 2 * KP - 1; ++t) {
-                        const float fv = KP <= 4 ? foldf[(KP <= 4 ? (t - KP) * KP + i : 0)]
-                                                 : (float)F.fold[(t - KP) * KP + i];
-                        o = fmaf(s[t][e], fv, o);
-                    }
-                    const uint32_t b = tc_mod(o, pf, inv_pf);
-                    if (e < 4) lo |= b << (8 * e);
-                    else hi |= b << (8 * (e - 4));
-                }
-                store_rows8(stage, lane_base + (int64_t)i * c_plane + c, step4, rows_left, col_ok, lo,
-                            hi, lane);
-            }
+            for (int i = 0; i < KP; ++i)
+                store_rows8(lane_base + (int64_t)i * c_plane + c, step4, rows_left, cols_left, lo[i],
+                            hi[i], lane);
         }
     }
 }
 
 template <class Release>
 __device__ __forceinline__ void tc_epilogue_k(uint32_t tacc, const TcRec &T, const BFieldParams &F,
-                                           int row, int c0, int w, uint8_t *stage, Release release) {
+                                           int row, int c0, int w, Release release) {
     // GF(2^k) (the parity path) and the other fields (FP32 reductions) are
     // separate functions, each with its own register allocation
     if (F.p == 2) {
         switch (T.k) {
-            case 1: tc_epilogue<1, true>(tacc, T, F, row, c0, w, stage, release); break;
-            case 2: tc_epilogue<2, true>(tacc, T, F, row, c0, w, stage, release); break;
-            case 3: tc_epilogue<3, true>(tacc, T, F, row, c0, w, stage, release); break;
-            case 4: tc_epilogue<4, true>(tacc, T, F, row, c0, w, stage, release); break;
-            case 5: tc_epilogue<5, true>(tacc, T, F, row, c0, w, stage, release); break;
-            case 6: tc_epilogue<6, true>(tacc, T, F, row, c0, w, stage, release); break;
-            case 7: tc_epilogue<7, true>(tacc, T, F, row, c0, w, stage, release); break;
-            default: tc_epilogue<8, true>(tacc, T, F, row, c0, w, stage, release); break;
+            case 1: tc_epilogue<1, true>(tacc, T, F, row, c0, w, release); break;
+            case 2: tc_epilogue<2, true>(tacc, T, F, row, c0, w, release); break;
+            case 3: tc_epilogue<3, true>(tacc, T, F, row, c0, w, release); break;
+            case 4: tc_epilogue<4, true>(tacc, T, F, row, c0, w, release); break;
+            case 5: tc_epilogue<5, true>(tacc, T, F, row, c0, w, release); break;
+            case 6: tc_epilogue<6, true>(tacc, T, F, row, c0, w, release); break;
+            case 7: tc_epilogue<7, true>(tacc, T, F, row, c0, w, release); break;
+            default: tc_epilogue<8, true>(tacc, T, F, row, c0, w, release); break;
         }
         return;
     }
     switch (T.k) {
-        case 1: tc_epilogue<1, false>(tacc, T, F, row, c0, w, stage, release); break;
-        case 2: tc_epilogue<2, false>(tacc, T, F, row, c0, w, stage, release); break;
-        case 3: tc_epilogue<3, false>(tacc, T, F, row, c0, w, stage, release); break;
-        case 4: tc_epilogue<4, false>(tacc, T, F, row, c0, w, stage, release); break;
-        case 5: tc_epilogue<5, false>(tacc, T, F, row, c0, w, stage, release); break;
-        case 6: tc_epilogue<6, false>(tacc, T, F, row, c0, w, stage, release); break;
-        case 7: tc_epilogue<7, false>(tacc, T, F, row, c0, w, stage, release); break;
-        default: tc_epilogue<8, false>(tacc, T, F, row, c0, w, stage, release); break;
+        case 1: tc_epilogue<1, false>(tacc, T, F, row, c0, w, release); break;
+        case 2: tc_epilogue<2, false>(tacc, T, F, row, c0, w, release); break;
+        case 3: tc_epilogue<3, false>(tacc, T, F, row, c0, w, release); break;
+        case 4: tc_epilogue<4, false>(tacc, T, F, row, c0, w, release); break;
+        case 5: tc_epilogue<5, false>(tacc, T, F, row, c0, w, release); break;
+        case 6: tc_epilogue<6, false>(tacc, T, F, row, c0, w, release); break;
+        case 7: tc_epilogue<7, false>(tacc, T, F, row, c0, w, release); break;
+        default: tc_epilogue<8, false>(tacc, T, F, row, c0, w, release); break;
     }
 }
 
@@ -527,8 +580,6 @@ tc_products_kernel(const uint8_t *__restrict__ ws, int slot_bytes, int a_bytes, 
     uint32_t *tmem_slot = (uint32_t *)(mma_done + 1);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
     BFieldParams *sF = reinterpret_cast<BFieldParams *>(smem + (size_t)stages * slot_bytes + 256);
-    // 256 bytes per epilogue warp for transposing its stores
-    uint8_t *store_stage = reinterpret_cast<uint8_t *>(sF + kMaxFields);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
 
     {
@@ -657,10 +708,12 @@ tc_products_kernel(const uint8_t *__restrict__ ws, int slot_bytes, int a_bytes, 
     } else {
         // ---------------- epilogue (warps 2..9) ----------------
         const int ew = warp - 2;
-        const int quarter = warp & 3, part = ew / 4;   // part: the group, and its buffer
+        // part: the group, and its buffer; half: which half of the tile's
+        // columns this warp takes in its 32-lane quarter of tensor memory
+        const int quarter = warp & 3, part = ew / 4, half = 0;
         {
             // the group's buffer starts at zero: every MMA accumulates
-            const uint32_t tz = tmem_base + ((uint32_t)(quarter * 32) << 16) + 256u * part;
+            const uint32_t tz = tmem_base + ((uint32_t)(quarter * 32) << 16) + 256u * part + 128u * half;
             for (int c = 0; c < 256; c += 8) tmem_zero8(tz + c);
             ptx::tmem_wait_st();
             ptx::tc_fence_before();
@@ -701,8 +754,7 @@ tc_products_kernel(const uint8_t *__restrict__ ws, int slot_bytes, int a_bytes, 
                 break;
             }
             ptx::tc_fence_after();
-            tc_epilogue_k(tacc, T, F, quarter * 32, c0, w, store_stage + 256 * ew,
-                          Releaser{&tmem_free[b]});
+            tc_epilogue_k(tacc, T, F, quarter * 32, c0, w, Releaser{&tmem_free[b]});
             T = Tn;
         }
         if (!ok) *abort_flag = 1;
@@ -724,7 +776,7 @@ tc_products_kernel(const uint8_t *__restrict__ ws, int slot_bytes, int a_bytes, 
 int tc_stage_layout(uint32_t kmax, int *slot_bytes, int *a_bytes, int *stages) {
     *a_bytes = (int)kmax * 4096;
     *slot_bytes = *a_bytes + 4096;
-    const int reserve = 256 + kMaxFields * (int)sizeof(BFieldParams) + 256 * kTcEpiWarps;
+    const int reserve = 256 + kMaxFields * (int)sizeof(BFieldParams);
     int s = (kTcSmemBudget - reserve - 128) / *slot_bytes;
     if (s > kTcMaxStages) s = kTcMaxStages;
     if (s < 2) return set_error(QADIC_E_UNSUPPORTED, "batched tcgen05 stages do not fit");
@@ -736,8 +788,7 @@ int tc_stage_layout(uint32_t kmax, int *slot_bytes, int *a_bytes, int *stages) {
 // least half of the SM's shared memory, so that no two CTAs share an SM
 // (each allocates all 512 tensor-memory columns).
 size_t tc_smem_bytes(int slot_bytes, int stages) {
-    const size_t need = 128 + (size_t)stages * slot_bytes + 256 + kMaxFields * sizeof(BFieldParams) +
-                        256 * kTcEpiWarps;
+    const size_t need = 128 + (size_t)stages * slot_bytes + 256 + kMaxFields * sizeof(BFieldParams);
     return std::max<size_t>(need, kTcSmemBudget / 2 + 1024);
 }
 
