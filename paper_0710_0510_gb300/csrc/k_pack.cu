@@ -356,60 +356,68 @@ __global__ void __launch_bounds__(256) pack_vec_a(const uint8_t *__restrict__ in
     vec_a_body<IN>(in, out, P, blockIdx.x, gridDim.x);
 }
 
-// Transposed operand: a 64 x 64 input tile per block, every plane of it;
-// the k 16-byte loads of a thread are issued together, then each plane goes
-// through the shared-memory transpose and leaves as 16-byte stores along the
-// output rows.
-template <int IN>
+// Transposed operand: RT stacked 64 x 64 input tiles per block (input rows
+// RT by .. RT by + 64 RT - 1), every plane of them; the 16-byte loads of a
+// thread for two planes of all RT tiles are issued together, then each tile
+// and plane goes through the shared-memory transpose and leaves as 16-byte
+// stores along the output rows.
+template <int IN, int RT>
 __device__ __forceinline__ void vec_b_body(const uint8_t *__restrict__ in,
                                            __nv_bfloat16 *__restrict__ out, const PackParams &P,
                                            int64_t bx, int64_t by, uint16_t (*tile)[64 + 2]) {
-    const int64_t r0 = by * 64, c0 = bx * 64;
+    const int64_t c0 = bx * 64;
     const int rr = threadIdx.x / 4, cc = (threadIdx.x % 4) * 16;
-    const int64_t r = r0 + rr;
-    // planes in groups of two: both loads of a group are in flight together
+    // planes in groups of two: the loads of a group are in flight together
 #pragma unroll 1
     for (int g = 0; g < (int)P.k; g += 2) {
-        uint4 w[2];
+        uint4 w[RT][2];
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            w[e] = make_uint4(0, 0, 0, 0);
-            if (g + e < (int)P.k && r < P.rows)
-                w[e] = __ldcs(reinterpret_cast<const uint4 *>(
-                    in + ((int64_t)(g + e) * P.rows + r) * P.ld_in + c0 + cc));
-        }
+        for (int t = 0; t < RT; ++t)
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const int plane = g + e;
-            if (plane >= (int)P.k) break;   // block-uniform
-            uint32_t o[8];
-            convert16<IN>(w[e], P, o);
-#pragma unroll
-            for (int x = 0; x < 8; ++x) {
-                tile[rr][cc + 2 * x] = (uint16_t)o[x];
-                tile[rr][cc + 2 * x + 1] = (uint16_t)(o[x] >> 16);
+            for (int e = 0; e < 2; ++e) {
+                const int64_t r = (by * RT + t) * 64 + rr;
+                w[t][e] = make_uint4(0, 0, 0, 0);
+                if (g + e < (int)P.k && r < P.rows)
+                    w[t][e] = __ldcs(reinterpret_cast<const uint4 *>(
+                        in + ((int64_t)(g + e) * P.rows + r) * P.ld_in + c0 + cc));
             }
-            __syncthreads();
-            // output row (input column) oc, 8 consecutive input rows per chunk
 #pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                const int idx = threadIdx.x + 256 * s;        // 64 output rows x 8 chunks
-                const int oc = idx / 8, ch = (idx % 8) * 8;
-                uint32_t v[4];
+        for (int t = 0; t < RT; ++t) {
+            const int64_t r0 = (by * RT + t) * 64;
+            if (r0 >= P.rows) break;   // block-uniform
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    v[q] = (uint32_t)tile[ch + 2 * q][oc] | ((uint32_t)tile[ch + 2 * q + 1][oc] << 16);
-                const int64_t orow = c0 + oc, ocol = r0 + ch;
-                if (ocol + 8 <= P.rows) {
-                    *reinterpret_cast<uint4 *>(out + ((int64_t)plane * P.cols + orow) * P.ld_out +
-                                               ocol) = make_uint4(v[0], v[1], v[2], v[3]);
-                } else {
-                    for (int x = 0; x < 8 && ocol + x < P.rows; ++x)
-                        out[((int64_t)plane * P.cols + orow) * P.ld_out + ocol + x] =
-                            __ushort_as_bfloat16((uint16_t)(v[x / 2] >> (16 * (x % 2))));
+            for (int e = 0; e < 2; ++e) {
+                const int plane = g + e;
+                if (plane >= (int)P.k) break;   // block-uniform
+                uint32_t o[8];
+                convert16<IN>(w[t][e], P, o);
+#pragma unroll
+                for (int x = 0; x < 8; ++x) {
+                    tile[rr][cc + 2 * x] = (uint16_t)o[x];
+                    tile[rr][cc + 2 * x + 1] = (uint16_t)(o[x] >> 16);
                 }
+                __syncthreads();
+                // output row (input column) oc, 8 consecutive input rows per chunk
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    const int idx = threadIdx.x + 256 * s;        // 64 output rows x 8 chunks
+                    const int oc = idx / 8, ch = (idx % 8) * 8;
+                    uint32_t v[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        v[q] = (uint32_t)tile[ch + 2 * q][oc] | ((uint32_t)tile[ch + 2 * q + 1][oc] << 16);
+                    const int64_t orow = c0 + oc, ocol = r0 + ch;
+                    if (ocol + 8 <= P.rows) {
+                        *reinterpret_cast<uint4 *>(out + ((int64_t)plane * P.cols + orow) * P.ld_out +
+                                                   ocol) = make_uint4(v[0], v[1], v[2], v[3]);
+                    } else {
+                        for (int x = 0; x < 8 && ocol + x < P.rows; ++x)
+                            out[((int64_t)plane * P.cols + orow) * P.ld_out + ocol + x] =
+                                __ushort_as_bfloat16((uint16_t)(v[x / 2] >> (16 * (x % 2))));
+                    }
+                }
+                __syncthreads();   // the tile is rewritten next
             }
-            __syncthreads();   // the tile is rewritten by the next plane
         }
     }
 }
@@ -418,12 +426,13 @@ template <int IN>
 __global__ void __launch_bounds__(256) pack_vec_b(const uint8_t *__restrict__ in,
                                                   __nv_bfloat16 *__restrict__ out, PackParams P) {
     __shared__ uint16_t tile[64][64 + 2];
-    vec_b_body<IN>(in, out, P, blockIdx.x, blockIdx.y, tile);
+    vec_b_body<IN, 1>(in, out, P, blockIdx.x, blockIdx.y, tile);
 }
 
 // Both operands of a plane GEMM in one launch: blocks [0, na) convert A
-// (same layout), the others transpose B in 64 x 64 tiles -- one ramp-up and
-// one tail instead of two for these short HBM-bound passes.
+// (same layout), the others transpose B, two 64 x 64 tiles stacked down K
+// per block -- one ramp-up and one tail instead of two for these short
+// HBM-bound passes.
 template <int IN>
 __global__ void __launch_bounds__(256) pack_vec_ab(const uint8_t *__restrict__ a,
                                                    __nv_bfloat16 *__restrict__ oa, PackParams PA,
@@ -436,7 +445,7 @@ __global__ void __launch_bounds__(256) pack_vec_ab(const uint8_t *__restrict__ a
     } else {
         const int64_t t = (int64_t)blockIdx.x - na;
         const int64_t nbx = PB.cols / 64;
-        vec_b_body<IN>(b, ob, PB, t % nbx, t / nbx, tile);
+        vec_b_body<IN, 2>(b, ob, PB, t % nbx, t / nbx, tile);
     }
 }
 
@@ -597,7 +606,7 @@ int launch_pack_pair(const Field &f, int in_fmt, const void *A, int64_t m, int64
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t units_a = (int64_t)f.k * m * (K / 16);
     // A blocks in proportion to A's share of the bytes; B blocks one per tile
-    const int64_t nb = (int64_t)(n / 64) * ((K + 63) / 64);
+    const int64_t nb = (int64_t)(n / 64) * ((K + 127) / 128);
     const int64_t na = std::max<int64_t>(1, std::min<int64_t>((units_a + 1023) / 1024, (int64_t)sms * 8));
     if (na + nb > 0x7fffffff) return set_error(QADIC_E_INVALID, "too many pack blocks");
     if (in_fmt == QADIC_FMT_INT8_PLANES)

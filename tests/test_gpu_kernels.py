@@ -743,6 +743,40 @@ def test_pack_operands_equals_two_packs(torch, fmt, shape):
     assert torch.equal(oa, ra) and torch.equal(ob, rb)
 
 
+@pytest.mark.parametrize("pk", [(101, 2), (7, 4), (2, 8), (3, 3), (251, 2)])
+@pytest.mark.parametrize("fmt", [q.FMT_INT8_PLANES, q.FMT_COEFF_U8])
+@pytest.mark.parametrize("shape", [(100, 48, 128), (1, 16, 64), (257, 80, 192), (64, 64, 64),
+                                   (65, 4096, 64), (130, 144, 128), (130, 40, 70)])
+def test_pack_operands_ragged(torch, pk, fmt, shape):
+    """The fused launch (K a multiple of 16, n of 64): B tiles stacked two
+    deep down K, cut by the edge of K, ragged m for A, full-range int8 and
+    uint8 bytes (reduced mod p on the way), against the two single-operand
+    packs; the last shape takes two launches."""
+    p, k = pk
+    m, K, n = shape
+    f = q.Field(p, k)
+    rng = np.random.default_rng(p * 1000 + m + K + n)
+    if fmt == q.FMT_INT8_PLANES:
+        A = rng.integers(-128, 128, (k, m, K), dtype=np.int8)
+        B = rng.integers(-128, 128, (k, K, n), dtype=np.int8)
+    else:
+        A = rng.integers(0, 256, (k, m, K), dtype=np.uint8)
+        B = rng.integers(0, 256, (k, K, n), dtype=np.uint8)
+    ld = (K + 7) // 8 * 8
+    oa = torch.full((k, m, ld), 7.0, dtype=torch.bfloat16, device="cuda")
+    ob = torch.full((k, n, ld), 7.0, dtype=torch.bfloat16, device="cuda")
+    f.pack_operands(fmt, dev(torch, A), dev(torch, B), m, n, K, oa, ob)
+    ra = f.pack(fmt, dev(torch, A), m, K, q.FMT_OPERAND_A,
+                out=torch.full((k, m, ld), 7.0, dtype=torch.bfloat16, device="cuda"), ld_out=ld)
+    rb = f.pack(fmt, dev(torch, B), K, n, q.FMT_OPERAND_B,
+                out=torch.full((k, n, ld), 7.0, dtype=torch.bfloat16, device="cuda"), ld_out=ld)
+    torch.cuda.synchronize()
+    q.sync_status()
+    assert torch.equal(oa[:, :, :K], ra[:, :, :K]) and torch.equal(ob[:, :, :K], rb[:, :, :K])
+    # nothing written past K in the padded rows
+    assert bool((oa[:, :, K:] == 7.0).all()) and bool((ob[:, :, K:] == 7.0).all())
+
+
 @pytest.mark.parametrize("path", [q.PATH_PLANES, q.PATH_FP64_QADIC, q.PATH_FOLD,
                                   q.PATH_KARATSUBA])
 @pytest.mark.parametrize("fmt", [q.FMT_INT8_PLANES, q.FMT_LOG])
