@@ -321,11 +321,11 @@ __host__ __device__ constexpr int tc_bn(uint32_t k) {
 }
 
 // Launch helpers of the tensor-core path (k_batched_tc.cu).
-int tc_stage_layout(uint32_t kmax, int *slot_bytes, int *a_bytes, int *stages);
+int tc_stage_layout(uint32_t kmax, int *slot_bytes, int *stages);
 int prepare_tc_kernel();
 int64_t tc_grid(int64_t ntiles);
 int launch_tc_convert(const uint8_t *ws, int64_t nitems, cudaStream_t stream);
-int launch_tc_products(const uint8_t *ws, int64_t grid, int slot_bytes, int a_bytes, int stages,
+int launch_tc_products(const uint8_t *ws, int64_t grid, int slot_bytes, int stages,
                        int *status, cudaStream_t stream);
 
 }  // namespace bt

@@ -474,10 +474,10 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
         smem = std::max(smem, tile_smem_bytes(fields[i]->k, cfgs[i]));
     }
     for (int64_t i = 0; i < count; ++i) kmax = std::max(kmax, fields[descs[i].field]->k);
-    int tc_slot = 0, tc_a = 0, tc_stages = 0;
+    int tc_slot = 0, tc_stages = 0;
     int st = QADIC_OK;
     if (converted) {
-        if ((st = tc_stage_layout(kmax, &tc_slot, &tc_a, &tc_stages)) != QADIC_OK) return st;
+        if ((st = tc_stage_layout(kmax, &tc_slot, &tc_stages)) != QADIC_OK) return st;
         st = prepare_tc_kernel();
     } else {
         st = prepare_kernel(smem);
@@ -666,7 +666,7 @@ int launch_batched(const Field *const *fields, int32_t nfields, const qadic_gemm
         if (converted) {
             const int cs = launch_tc_convert((const uint8_t *)workspace, conv_items, s);
             if (cs != QADIC_OK) return cs;
-            return launch_tc_products((const uint8_t *)workspace, grid, tc_slot, tc_a, tc_stages,
+            return launch_tc_products((const uint8_t *)workspace, grid, tc_slot, tc_stages,
                                       status, s);
         }
         batched_kernel<<<(unsigned)grid, kThreads, smem, s>>>((uint8_t *)workspace);

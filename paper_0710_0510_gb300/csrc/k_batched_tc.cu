@@ -205,6 +205,16 @@ __device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t b
         : "memory");
 }
 
+// The same in pieces of at most 32 KB (sizes and addresses stay multiples
+// of 16 bytes).
+__device__ __forceinline__ void bulk_copy_split(void *dst, const void *src, uint32_t bytes,
+                                                uint64_t *bar) {
+    constexpr uint32_t kPiece = 32768;
+    for (uint32_t off = 0; off < bytes; off += kPiece)
+        bulk_copy(static_cast<uint8_t *>(dst) + off, static_cast<const uint8_t *>(src) + off,
+                  bytes - off < kPiece ? bytes - off : kPiece, bar);
+}
+
 // 32 lanes x 8 columns of 32-bit data.
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -505,33 +515,56 @@ __device__ __forceinline__ void tc_epilogue_k(uint32_t tacc, const TcRec &T, con
     }
 }
 
+// K-blocks of a tile per ring stage: as many as one slot holds (the
+// converted blocks of consecutive K-blocks are contiguous, so a stage is one
+// bulk copy per operand: nkb A blocks, then nkb B blocks).
+__device__ __forceinline__ int tc_stage_kblocks(int slot_bytes, uint32_t ab, uint32_t bb) {
+    const int c = slot_bytes / (int)(ab + bb);
+    return c > 1 ? c : 1;
+}
+
 // The K loop of one tile on the MMA thread: per K-block one MMA per A
 // plane, A_i against [B_0; ...; B_{k-1}] into the accumulators at column
 // a_col(i) of the buffer, which the epilogue zeroed after reading the tile
 // before last (every MMA accumulates).  The ring position (s, round) and the
 // drain count of the buffer advance here.
 template <int KP, bool FP8>
-__device__ __noinline__ bool tc_mma_tile(uint32_t d0, uint8_t *smem, int slot_bytes, int a_bytes,
-                                         int stages, int &s, uint32_t &round, int rows8, int ks_n,
-                                         int chunk, uint64_t *full, uint64_t *empty,
-                                         uint64_t *acc_full_b, uint64_t *acc_empty_b, int &drains,
+__device__ __noinline__ bool tc_mma_tile(uint32_t d0, uint8_t *smem, int slot_bytes, int stages,
+                                         int &s, uint32_t &round, int rows8, int ks_n, int chunk,
+                                         uint64_t *full, uint64_t *empty, uint64_t *acc_full_b,
+                                         uint64_t *acc_empty_b, int &drains,
                                          volatile int *abort_flag) {
     constexpr int BN = tc_bn(KP);
     const uint32_t idesc = FP8 ? idesc_e4m3_f32(128, KP * BN) : ptx::idesc_bf16_f32(128, KP * BN);
+    const uint32_t ab = (uint32_t)(KP * rows8 * 32), bb = (uint32_t)(KP * BN * 32);
     const uint64_t astep = (uint64_t)((uint32_t)rows8 * 32) >> 4;   // descriptor units of 16 bytes
+    const int cap = tc_stage_kblocks(slot_bytes, ab, bb);
     uint32_t sa = ptx::smem_addr(smem + (size_t)s * slot_bytes);
     const uint32_t slot_u = (uint32_t)slot_bytes;
     const uint32_t sa0 = ptx::smem_addr(smem);
     int to_drain = chunk;
-    for (int ks = 0; ks < ks_n; ++ks) {
+    for (int kb = 0; kb < ks_n;) {
+        const int nkb = ks_n - kb < cap ? ks_n - kb : cap;
         if (*abort_flag || !ptx::mbar_wait(&full[s], round & 1)) return false;
         ptx::tc_fence_after();
-        const uint64_t ad = desc_kmajor(sa), bd = desc_kmajor(sa + (uint32_t)a_bytes);
+        const uint32_t sb = sa + (uint32_t)nkb * ab;
+        for (int j = 0; j < nkb; ++j, ++kb) {
+            const uint64_t ad = desc_kmajor(sa + (uint32_t)j * ab), bd = desc_kmajor(sb + (uint32_t)j * bb);
 #pragma unroll
-        for (int i = 0; i < KP; ++i) {
-            const uint32_t col = KP <= 2 ? (uint32_t)(i * KP * BN) : (uint32_t)(i * BN);
-            if constexpr (FP8) mma_e4m3(d0 + col, ad + i * astep, bd, idesc, 1u);
-            else ptx::mma_bf16(d0 + col, ad + i * astep, bd, idesc, 1u);
+            for (int i = 0; i < KP; ++i) {
+                const uint32_t col = KP <= 2 ? (uint32_t)(i * KP * BN) : (uint32_t)(i * BN);
+                if constexpr (FP8) mma_e4m3(d0 + col, ad + i * astep, bd, idesc, 1u);
+                else ptx::mma_bf16(d0 + col, ad + i * astep, bd, idesc, 1u);
+            }
+            if (--to_drain == 0 && kb + 1 < ks_n) {
+                // an exact chunk ends inside or at the end of this stage: the
+                // epilogue reduces in place before the next K-block's MMAs
+                to_drain = chunk;
+                ptx::mma_commit(acc_full_b);
+                if (!ptx::mbar_wait(acc_empty_b, (uint32_t)drains & 1)) return false;
+                ++drains;
+                ptx::tc_fence_after();
+            }
         }
         ptx::mma_commit(&empty[s]);
         if (++s == stages) {
@@ -541,31 +574,26 @@ __device__ __noinline__ bool tc_mma_tile(uint32_t d0, uint8_t *smem, int slot_by
         } else {
             sa += slot_u;
         }
-        if (--to_drain == 0 && ks + 1 < ks_n) {
-            to_drain = chunk;
-            ptx::mma_commit(acc_full_b);
-            if (!ptx::mbar_wait(acc_empty_b, (uint32_t)drains & 1)) return false;
-            ++drains;
-            ptx::tc_fence_after();
-        }
     }
     return true;
 }
 
 // Called once the warp's last accumulator columns of the tile have been
 // read (and zeroed, tmem_zero8): the zeros land, then the buffer goes back
-// to the MMAs.
+// to the MMAs.  The tensor-memory waits are warp-collective, so after them
+// one lane speaks for the warp (one arrival per warp: per-lane arrivals on
+// one barrier serialise).
 struct Releaser {
     uint64_t *bar;
     __device__ void operator()() const {
         ptx::tmem_wait_st();
         ptx::tc_fence_before();
-        ptx::mbar_arrive(bar);
+        if ((threadIdx.x & 31) == 0) ptx::mbar_arrive(bar);
     }
 };
 
 __global__ void __launch_bounds__(kTcThreads, 1)
-tc_products_kernel(const uint8_t *__restrict__ ws, int slot_bytes, int a_bytes, int stages,
+tc_products_kernel(const uint8_t *__restrict__ ws, int slot_bytes, int stages,
                    int *status) {
     const BHeader *hdr = reinterpret_cast<const BHeader *>(ws);
     const int ntiles = hdr->ntiles, nfields = hdr->nfields;
@@ -596,8 +624,8 @@ tc_products_kernel(const uint8_t *__restrict__ ws, int slot_bytes, int a_bytes, 
         }
         for (int b = 0; b < 2; ++b) {
             ptx::mbar_init(&acc_full[b], 1);
-            ptx::mbar_init(&acc_empty[b], 16 * kTcEpiWarps);
-            ptx::mbar_init(&tmem_free[b], 16 * kTcEpiWarps);
+            ptx::mbar_init(&acc_empty[b], kTcEpiWarps / 2);   // one arrival per warp of a group
+            ptx::mbar_init(&tmem_free[b], kTcEpiWarps / 2);
         }
         ptx::mbar_init(mma_done, 1);
         *abort_flag = 0;
@@ -611,8 +639,7 @@ tc_products_kernel(const uint8_t *__restrict__ ws, int slot_bytes, int a_bytes, 
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-    auto slot_a = [&](int s) { return smem + (size_t)s * slot_bytes; };
-    auto slot_b = [&](int s) { return smem + (size_t)s * slot_bytes + a_bytes; };
+    auto slot_at = [&](int s) { return smem + (size_t)s * slot_bytes; };
     const int t0 = blockIdx.x, tstep = gridDim.x;
 
     if (warp == 0) {
@@ -628,18 +655,22 @@ tc_products_kernel(const uint8_t *__restrict__ ws, int slot_bytes, int a_bytes, 
             for (int t = t0; t < ntiles && ok; t += tstep) {
                 const TcRec Tn = tc_rec(ws, hdr, t + tstep, ntiles);   // in flight meanwhile
                 const uint32_t ab = (uint32_t)(T.k * T.rows8 * 32), bb = (uint32_t)(T.k * tc_bn(T.k) * 32);
+                const int cap = tc_stage_kblocks(slot_bytes, ab, bb);
                 const uint8_t *a0 = T.a;
                 const uint8_t *b0 = T.b;
-                for (int ks = 0; ks < T.ks; ++ks, ++it) {
+                for (int kb = 0; kb < T.ks; ++it) {
+                    const int nkb = T.ks - kb < cap ? T.ks - kb : cap;
                     if (round > 0) {
                         if (*abort_flag || !ptx::mbar_wait(&empty[s], (round - 1) & 1)) {
                             ok = false;
                             break;
                         }
                     }
-                    ptx::mbar_arrive_expect_tx(&full[s], ab + bb);
-                    bulk_copy(slot_a(s), a0 + (size_t)ks * ab, ab, &full[s]);
-                    bulk_copy(slot_b(s), b0 + (size_t)ks * bb, bb, &full[s]);
+                    ptx::mbar_arrive_expect_tx(&full[s], (uint32_t)nkb * (ab + bb));
+                    bulk_copy_split(slot_at(s), a0 + (size_t)kb * ab, (uint32_t)nkb * ab, &full[s]);
+                    bulk_copy_split(slot_at(s) + (size_t)nkb * ab, b0 + (size_t)kb * bb,
+                                    (uint32_t)nkb * bb, &full[s]);
+                    kb += nkb;
                     if (++s == stages) {
                         s = 0;
                         ++round;
@@ -677,10 +708,10 @@ tc_products_kernel(const uint8_t *__restrict__ ws, int slot_bytes, int a_bytes, 
                 const int chunk = sF[T.field].tc_chunk_ks;
                 int &drains = b ? drains1 : drains0;
 #define QADIC_TC_MMA(KP_)                                                                         \
-    ok = fp8 ? tc_mma_tile<KP_, true>(d0, smem, slot_bytes, a_bytes, stages, s, round, T.rows8,      \
+    ok = fp8 ? tc_mma_tile<KP_, true>(d0, smem, slot_bytes, stages, s, round, T.rows8,                \
                                       T.ks, chunk, full, empty, &acc_full[b], &acc_empty[b],        \
                                       drains, abort_flag)                                           \
-             : tc_mma_tile<KP_, false>(d0, smem, slot_bytes, a_bytes, stages, s, round, T.rows8,     \
+             : tc_mma_tile<KP_, false>(d0, smem, slot_bytes, stages, s, round, T.rows8,               \
                                        T.ks, chunk, full, empty, &acc_full[b], &acc_empty[b],       \
                                        drains, abort_flag)
                 switch (T.k) {
@@ -708,16 +739,14 @@ tc_products_kernel(const uint8_t *__restrict__ ws, int slot_bytes, int a_bytes, 
     } else {
         // ---------------- epilogue (warps 2..9) ----------------
         const int ew = warp - 2;
-        // part: the group, and its buffer; half: which half of the tile's
-        // columns this warp takes in its 32-lane quarter of tensor memory
-        const int quarter = warp & 3, part = ew / 4, half = 0;
+        const int quarter = warp & 3, part = ew / 4;   // part: the group, and its buffer
         {
             // the group's buffer starts at zero: every MMA accumulates
-            const uint32_t tz = tmem_base + ((uint32_t)(quarter * 32) << 16) + 256u * part + 128u * half;
+            const uint32_t tz = tmem_base + ((uint32_t)(quarter * 32) << 16) + 256u * part;
             for (int c = 0; c < 256; c += 8) tmem_zero8(tz + c);
             ptx::tmem_wait_st();
             ptx::tc_fence_before();
-            ptx::mbar_arrive(&tmem_free[part]);
+            if (lane == 0) ptx::mbar_arrive(&tmem_free[part]);
         }
         int phase0 = 0, phase1 = 0;
         int tcount = part;
@@ -746,7 +775,7 @@ tc_products_kernel(const uint8_t *__restrict__ ws, int slot_bytes, int a_bytes, 
                 ptx::tc_fence_after();
                 tc_drain(tacc, nacc, bn, c0, w, F.pf, F.inv_pf);
                 ptx::tc_fence_before();
-                ptx::mbar_arrive(&acc_empty[b]);
+                if (lane == 0) ptx::mbar_arrive(&acc_empty[b]);
             }
             if (!ok) break;
             if (!ready()) {
@@ -773,13 +802,17 @@ tc_products_kernel(const uint8_t *__restrict__ ws, int slot_bytes, int a_bytes, 
 
 // Stage layout for the fields of a launch: every stage holds the A planes of
 // the largest k (k x 128 rows x 32 bytes) and one B tile (k BN = 128 rows).
-int tc_stage_layout(uint32_t kmax, int *slot_bytes, int *a_bytes, int *stages) {
-    *a_bytes = (int)kmax * 4096;
-    *slot_bytes = *a_bytes + 4096;
+// Ring stages for the widest field degree present: three when a K-block of
+// A takes 20 KB or more (k >= 5), else four; each slot as large as the
+// budget allows (several K-blocks of the smaller degrees per stage), and at
+// least one K-block of the widest degree.
+int tc_stage_layout(uint32_t kmax, int *slot_bytes, int *stages) {
+    const int one = (int)kmax * 4096 + 4096;
     const int reserve = 256 + kMaxFields * (int)sizeof(BFieldParams);
-    int s = (kTcSmemBudget - reserve - 128) / *slot_bytes;
-    if (s > kTcMaxStages) s = kTcMaxStages;
-    if (s < 2) return set_error(QADIC_E_UNSUPPORTED, "batched tcgen05 stages do not fit");
+    const int s = kmax >= 5 ? 3 : 4;
+    const int slot = (kTcSmemBudget - reserve - 128) / s / 256 * 256;
+    if (slot < one) return set_error(QADIC_E_UNSUPPORTED, "batched tcgen05 stages do not fit");
+    *slot_bytes = slot;
     *stages = s;
     return QADIC_OK;
 }
@@ -819,10 +852,10 @@ int launch_tc_convert(const uint8_t *ws, int64_t nitems, cudaStream_t stream) {
     return QADIC_OK;
 }
 
-int launch_tc_products(const uint8_t *ws, int64_t grid, int slot_bytes, int a_bytes, int stages,
+int launch_tc_products(const uint8_t *ws, int64_t grid, int slot_bytes, int stages,
                        int *status, cudaStream_t stream) {
     tc_products_kernel<<<(unsigned)grid, kTcThreads, tc_smem_bytes(slot_bytes, stages), stream>>>(
-        ws, slot_bytes, a_bytes, stages, status);
+        ws, slot_bytes, stages, status);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(QADIC_E_CUDA, "tc products launch: %s", cudaGetErrorString(e));
     return QADIC_OK;
