@@ -94,7 +94,8 @@ typedef struct {
 
 /* One product of qadic_batched_gemm: C = A * B over fields[field].
  * A: k-plane COEFF_U8 m x K (ld = lda), B: k-plane COEFF_U8 K x n (ld = ldb),
- * C: k-plane COEFF_U8 m x n (ld = ldc).  All device pointers. */
+ * C: k-plane COEFF_U8 m x n (ld = ldc).  All device pointers.  Input bytes
+ * at or above p are taken mod p; C holds coefficients in [0, p). */
 typedef struct {
     int32_t field;            /* index into the fields array */
     int32_t m, n, K;

@@ -369,3 +369,29 @@ def test_autotune_selects_measured_configurations(torch, orc, restore_tiles):
     bt.run(graph=True)
     for i in range(0, len(shapes), 7):
         assert np.array_equal(bt.result(i), bt.expected(orc, i)), i
+
+
+@pytest.mark.parametrize("converted", [True, False])
+def test_batched_unreduced_bytes(torch, orc, converted):
+    """Operand bytes anywhere in [0, 255] are taken mod p (canonical and
+    unreduced bytes side by side in the same rows and columns), on both
+    paths."""
+    fields = mixed_fields()
+    shapes = [(70, 96, 64), (33, 130, 48), (128, 64, 100), (5, 257, 17), (64, 64, 64), (90, 32, 40)]
+    fidx = [0, 1, 2, 0, 1, 0]
+    bt = Batch(torch, fields, shapes, fidx, seed=9, converted=converted)
+    rng = np.random.default_rng(10)
+    for i, (m, n, K) in enumerate(shapes):
+        f = fields[fidx[i]]
+        a = rng.integers(0, 256, (f.k, m, K), dtype=np.uint8)
+        b = rng.integers(0, 256, (f.k, K, n), dtype=np.uint8)
+        a[:, ::2] %= f.p             # every other row canonical
+        b[:, :, ::3] %= f.p          # every third column canonical
+        oa, ob, _ = bt.offs[i]
+        bt.dA[oa:oa + a.size] = torch.from_numpy(a.ravel()).cuda()
+        bt.dB[ob:ob + b.size] = torch.from_numpy(b.ravel()).cuda()
+        bt.A[i], bt.B[i] = a % f.p, b % f.p
+    bt.run()
+    q.sync_status()
+    for i in range(len(shapes)):
+        assert np.array_equal(bt.result(i), bt.expected(orc, i)), (i, shapes[i])
