@@ -241,6 +241,8 @@ struct RedqPqParams {
     uint32_t split;                    // 1 <= j32 < d + 1 and q^j32 < 2^32 (see redq_pq_word_split)
     uint32_t qs;                       // q^j32 when split
     Div64 div_qs;                      // floor(r / q^j32)
+    uint64_t qs_m;                     // floor(r / q^j32) = mulhi(r, qs_m) >> qs_s for r < 2^52
+    uint32_t qs_s;
     double inv_qs_up;                  // 1/q^j32 rounded toward +infinity
     // digits in FP32 (QADIC_REDQ_F32_DIGITS, q^2 < 2^21)
     uint32_t Q;                        // q^2
@@ -285,6 +287,12 @@ __device__ __forceinline__ double redq_pq_word(double x, const RedqPqParams &P) 
     return u64_to_f64_exact(rho);
 }
 
+// v < 2^52 as a double: the bits of 2^52 + v, less 2^52 (one FP64 add on
+// a pipe the integer forms leave idle, instead of normalising the integer).
+__device__ __forceinline__ double u52_to_f64(uint64_t v) {
+    return __longlong_as_double((long long)(0x4330000000000000ull | v)) - 4503599627370496.0;
+}
+
 // When q^S < 2^32 for S = j32: one floor by q^S (64-bit integer, or
 // Lemma 1 on the binary64 word) splits the word into t_S = floor(r / q^S)
 // < 2^32 and r mod q^S < 2^32 (Lemma 2: the floors of t_S by q continue the
@@ -295,7 +303,8 @@ template <bool INT_FLOOR, int ND, int S>
 __device__ __forceinline__ double redq_pq_word_split(double x, const RedqPqParams &P) {
     static_assert(S >= 1 && S < ND, "split point");
     const uint64_t t = f64_to_u64_exact(x);
-    const uint64_t ts = INT_FLOOR ? div64(t, P.div_qs) : f64_to_u64_exact(__dmul_ru(x, P.inv_qs_up));
+    const uint64_t ts = INT_FLOOR ? __umul64hi(t, P.qs_m) >> P.qs_s
+                                  : f64_to_u64_exact(__dmul_ru(x, P.inv_qs_up));
     uint32_t lo = (uint32_t)(t - (uint64_t)P.qs * ts), hi = (uint32_t)ts;
     const uint32_t q = (uint32_t)P.q;
     uint32_t u[ND];
@@ -318,7 +327,7 @@ __device__ __forceinline__ double redq_pq_word_split(double x, const RedqPqParam
     for (int j = ND - 2; j >= S; --j) rh = rh * q + u[j];
 #pragma unroll
     for (int j = S - 2; j >= 0; --j) rl = rl * q + u[j];
-    return u64_to_f64_exact((uint64_t)rh * P.qs + rl);
+    return u52_to_f64((uint64_t)rh * P.qs + rl);
 }
 
 // ND = d + 1 digits known at compile time: the chain unrolls, the integer
@@ -591,6 +600,16 @@ int launch_redq_pq(uint32_t p, uint64_t q, uint32_t ndigits, const double *in, d
         P.split = 1;
         P.qs = (uint32_t)P.qpow[P.j32];
         P.div_qs = make_div64(P.qpow[P.j32]);
+        // round-up reciprocal with 2^s < q^S <= 2^(s+1): its error e < q^S
+        // times r < 2^52 stays below 2^(64+s), so the floor is exact
+        {
+            const uint64_t d = P.qpow[P.j32];
+            uint32_t sh = 0;
+            while (((uint64_t)2 << sh) < d) ++sh;   // 2^sh < d <= 2^(sh+1)
+            const unsigned __int128 two = (unsigned __int128)1 << (64 + sh);
+            P.qs_m = (uint64_t)((two + d - 1) / d);
+            P.qs_s = sh;
+        }
         P.inv_qs_up = inv_up(P.qpow[P.j32]);
     }
     if (f32_digits) {
