@@ -115,8 +115,8 @@ int upload_tables(Field &f) {
 // of later row blocks in qadic_matmul_host).
 cudaStream_t side_stream(int dev, int which = 0) {
     static std::mutex mu;
-    static cudaStream_t streams[64][2] = {};
-    if (dev < 0 || dev >= 64 || which < 0 || which > 1) return nullptr;
+    static cudaStream_t streams[64][3] = {};
+    if (dev < 0 || dev >= 64 || which < 0 || which > 2) return nullptr;
     std::lock_guard<std::mutex> lock(mu);
     cudaStream_t &st = streams[dev][which];
     if (!st && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
@@ -474,50 +474,32 @@ int qadic_matmul_host(const qadic_field *field, int path, int in_fmt, int64_t m,
     // then A in row blocks; B and the first block are packed on `stream`,
     // later blocks on a second side stream as soon as they land (a pack
     // block fits beside the GEMM's CTA on an SM), and the plane GEMM runs
-    // per block.  Each block of C goes back to the host while the next one
-    // is computed.  The split keeps the block GEMMs at the wave count of one
-    // GEMM over all rows (counted in 256 x 128 output units, one per two SMs)
-    // and makes the last block small, since its copy back cannot be hidden.
+    // per block.  Each block of C goes back to the host on a third stream
+    // while the next one is computed (the link carries both directions at
+    // once).  A block is as many 256-row unit rows as one round of 256 x 128
+    // output units on the SM pairs takes, so the GEMMs can start on the
+    // first small block and follow the copies, at most kMaxBlocks blocks.
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaStream_t side = side_stream(dev, 0), side2 = side_stream(dev, 1);
-    if (!side || !side2) return set_error(QADIC_E_CUDA, "no side stream");
-    constexpr int kMaxBlocks = 3;
-    int64_t rows[kMaxBlocks] = {m, 0, 0};
+    cudaStream_t side = side_stream(dev, 0), side2 = side_stream(dev, 1), d2h = side_stream(dev, 2);
+    if (!side || !side2 || !d2h) return set_error(QADIC_E_CUDA, "no side stream");
+    constexpr int kMaxBlocks = 8;
+    int64_t rows[kMaxBlocks] = {m};
     int nblk = 1;
     if (path == QADIC_PATH_PLANES && m >= 512) {
         const int64_t unit_rows = 256, um = (m + unit_rows - 1) / unit_rows;
         const int64_t tn = (n + 127) / 128, cl = std::max(1, sms / 2);
-        auto rounds = [&](int64_t u) { return (u * tn + cl - 1) / cl; };
-        int64_t best[3] = {0, 0, 0}, best_cost = -1;
-        for (int64_t u1 = 1; u1 < um - 1; ++u1)
-            for (int64_t u3 = 1; u1 + u3 < um; ++u3) {
-                const int64_t u2 = um - u1 - u3;
-                const int64_t cost = rounds(u1) + rounds(u2) + rounds(u3);
-                // fewest rounds, then the smallest last block, then the smallest first
-                const bool better = best_cost < 0 || cost < best_cost ||
-                                    (cost == best_cost && (u3 < best[2] ||
-                                                           (u3 == best[2] && u1 < best[0])));
-                if (better) {
-                    best_cost = cost;
-                    best[0] = u1;
-                    best[1] = u2;
-                    best[2] = u3;
-                }
-            }
-        if (best_cost > 0 && best_cost <= rounds(um)) {
-            rows[0] = best[0] * unit_rows;
-            rows[1] = best[1] * unit_rows;
-            rows[2] = m - rows[0] - rows[1];
-            nblk = 3;
-        } else if (m >= 512) {   // two blocks
-            rows[0] = std::min<int64_t>(m, (um / 2 + 1) * unit_rows);
-            rows[1] = m - rows[0];
-            nblk = rows[1] > 0 ? 2 : 1;
+        int64_t ub = std::max<int64_t>(1, cl / tn);          // unit rows per block: one round
+        if ((um + ub - 1) / ub > kMaxBlocks) ub = (um + kMaxBlocks - 1) / kMaxBlocks;
+        const int64_t nb = (um + ub - 1) / ub;
+        if (nb >= 2) {
+            nblk = (int)nb;
+            for (int b = 0; b < nblk; ++b)
+                rows[b] = std::min<int64_t>(ub * unit_rows, m - (int64_t)b * ub * unit_rows);
         }
     }
-    constexpr int kEvents = 2 + 3 * kMaxBlocks + 1;
+    constexpr int kEvents = 2 + 3 * kMaxBlocks + 2;
     cudaEvent_t ev[kEvents] = {};
     for (auto &e : ev)
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
@@ -525,7 +507,7 @@ int qadic_matmul_host(const qadic_field *field, int path, int in_fmt, int64_t m,
                 if (x) cudaEventDestroy(x);
             return set_error(QADIC_E_CUDA, "event: %s", cudaGetErrorString(cudaGetLastError()));
         }
-    cudaEvent_t &ev_start = ev[0], &ev_b = ev[1], &ev_join = ev[kEvents - 1];
+    cudaEvent_t &ev_start = ev[0], &ev_b = ev[1], &ev_join = ev[kEvents - 2], &ev_d2h = ev[kEvents - 1];
     cudaEvent_t *ev_copied = ev + 2, *ev_packed = ev + 2 + kMaxBlocks, *ev_gemm = ev + 2 + 2 * kMaxBlocks;
     auto cleanup = [&](int status) {
         for (auto &x : ev) cudaEventDestroy(x);   // released once their work completes
@@ -541,7 +523,8 @@ int qadic_matmul_host(const qadic_field *field, int path, int in_fmt, int64_t m,
     const uint32_t planes = planar ? f.k : 1;
     const size_t esz = planar ? 1 : eb;
     const size_t pa_elem = path == QADIC_PATH_FP64_QADIC ? 8 : 2 * (size_t)f.k;
-    int64_t r0[kMaxBlocks] = {0, rows[0], rows[0] + rows[1]};
+    int64_t r0[kMaxBlocks] = {0};
+    for (int b = 1; b < nblk; ++b) r0[b] = r0[b - 1] + rows[b - 1];
     auto dA_blk = [&](int b) { return dA + (size_t)planes * r0[b] * K * esz; };
     auto pA_blk = [&](int b) { return pA + pa_elem * r0[b] * K; };
     auto copy_rows = [&](char *dst, int64_t first, int64_t nrows) -> cudaError_t {
@@ -590,11 +573,11 @@ int qadic_matmul_host(const qadic_field *field, int path, int in_fmt, int64_t m,
                                                     dC + r0[b] * n, n, (int64_t)c_plane, s)))
                 return cleanup(st);
             if (b + 1 < nblk) {   // this block's C goes back while the next one is computed
-                if (cudaEventRecord(ev_gemm[b], s) || cudaStreamWaitEvent(side, ev_gemm[b], 0))
+                if (cudaEventRecord(ev_gemm[b], s) || cudaStreamWaitEvent(d2h, ev_gemm[b], 0))
                     return cuda_fail("event");
                 for (uint32_t i = 0; i < f.k; ++i)
                     if (cudaMemcpyAsync(C_host + i * c_plane + r0[b] * n, dC + i * c_plane + r0[b] * n,
-                                        (size_t)rows[b] * n, cudaMemcpyDeviceToHost, side))
+                                        (size_t)rows[b] * n, cudaMemcpyDeviceToHost, d2h))
                         return cuda_fail("D2H copy");
             }
         }
@@ -609,7 +592,9 @@ int qadic_matmul_host(const qadic_field *field, int path, int in_fmt, int64_t m,
         return cuda_fail("D2H copy");
     }
     // join: `stream` also waits for the side streams' copies
-    if (cudaEventRecord(ev_join, side) || cudaStreamWaitEvent(s, ev_join, 0)) return cuda_fail("join");
+    if (cudaEventRecord(ev_join, side) || cudaStreamWaitEvent(s, ev_join, 0) ||
+        cudaEventRecord(ev_d2h, d2h) || cudaStreamWaitEvent(s, ev_d2h, 0))
+        return cuda_fail("join");
     return cleanup(QADIC_OK);
 }
 

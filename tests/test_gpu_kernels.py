@@ -522,11 +522,12 @@ def test_matmul_host_log_codes_split(torch, orc, pk, shape):
     assert np.array_equal(np.transpose(hC.numpy(), (1, 2, 0)), want)
 
 
-def test_matmul_host_three_blocks(torch, orc):
-    """m = 2048, n = 4096: the host pipeline splits A into three row blocks
-    (512, 1024, 512 rows: the block GEMMs keep the single GEMM's four
-    rounds); rows of every block against the oracle, and the whole result
-    against the device path."""
+def test_matmul_host_row_blocks(torch, orc):
+    """m = 2048, n = 4096: the host pipeline splits A into four row blocks of
+    512 rows (each block's GEMM one round of 64 output units of 256 x 128 on
+    the SM pairs), C going back block by block on its own stream; rows of
+    every block against the oracle, and the whole result against the device
+    path."""
     p, k, m, n, K = 101, 2, 2048, 4096, 64
     f = q.Field(p, k)
     A = W.centred_planes(k, m, K, 50, salt=71)
@@ -541,7 +542,7 @@ def test_matmul_host_three_blocks(torch, orc):
     b = f.pack(q.FMT_INT8_PLANES, dev(torch, B), K, n, q.FMT_OPERAND_B)
     C = f.gemm(q.PATH_PLANES, a, b, m, n, K).cpu().numpy()
     assert np.array_equal(hC.numpy(), C)
-    rows = np.array([0, 511, 512, 1535, 1536, 2047])
+    rows = np.array([0, 511, 512, 1023, 1024, 1535, 1536, 2047])
     want = orc.gemm(p, f.poly, np.transpose(A[:, rows], (1, 2, 0)), np.transpose(B, (1, 2, 0)))
     assert np.array_equal(np.transpose(C[:, rows], (1, 2, 0)), want)
 
