@@ -441,6 +441,136 @@ size_t qadic_matmul_workspace_size(const qadic_field *field, int path, int in_fm
     return ws;
 }
 
+namespace {
+
+// The plane path's host pipeline with B cut into four column blocks as well
+// as A into row blocks (n a multiple of 512 and at least 1024, m >= 512):
+// the first GEMM needs one quarter of B and the first rows of A, so it
+// starts after about a fifth of the inputs have crossed the link instead of
+// all of B.  Copies in on `side` (B_0, A_0, then the other blocks of B, then
+// those of A), packs on `side2` as each block lands, the block GEMMs on `s`
+// (each one round of 256 x 128 output units on the SM pairs), each block of
+// C back on `d2h` while the next is computed, the last on `s`.
+int matmul_host_blocked(const qadic_field *field, const Field &f, int in_fmt, int64_t m, int64_t n,
+                        int64_t K, const void *A_host, const void *B_host, uint8_t *C_host, char *dA,
+                        char *dB, uint8_t *dC, char *pA, char *pB, uint32_t planes, size_t esz,
+                        cudaStream_t s, cudaStream_t side, cudaStream_t side2, cudaStream_t d2h,
+                        int sms) {
+    constexpr int NCB = 4, kMaxRows = 4;
+    const int64_t nc = n / NCB;
+    const int64_t unit_rows = 256, um = (m + unit_rows - 1) / unit_rows;
+    const int64_t tn = (nc + 127) / 128, cl = std::max(1, sms / 2);
+    int64_t ub = std::max<int64_t>(1, cl / tn);
+    if ((um + ub - 1) / ub > kMaxRows) ub = (um + kMaxRows - 1) / kMaxRows;
+    const int nrb = (int)((um + ub - 1) / ub);
+    int64_t rows[kMaxRows] = {0}, r0[kMaxRows] = {0};
+    for (int i = 0; i < nrb; ++i) {
+        r0[i] = (int64_t)i * ub * unit_rows;
+        rows[i] = std::min<int64_t>(ub * unit_rows, m - r0[i]);
+    }
+    constexpr int kEvents = 1 + 2 * NCB + 2 * kMaxRows + kMaxRows * NCB + 2;
+    cudaEvent_t ev[kEvents] = {};
+    for (auto &e : ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            for (auto &x : ev)
+                if (x) cudaEventDestroy(x);
+            return set_error(QADIC_E_CUDA, "event: %s", cudaGetErrorString(cudaGetLastError()));
+        }
+    cudaEvent_t *ev_bc = ev + 1, *ev_bp = ev + 1 + NCB, *ev_ac = ev + 1 + 2 * NCB,
+                *ev_ap = ev + 1 + 2 * NCB + kMaxRows, *ev_g = ev + 1 + 2 * NCB + 2 * kMaxRows;
+    cudaEvent_t &ev_start = ev[0], &ev_join = ev[kEvents - 2], &ev_d2h = ev[kEvents - 1];
+    auto cleanup = [&](int status) {
+        for (auto &x : ev) cudaEventDestroy(x);   // released once their work completes
+        return status;
+    };
+    auto cuda_fail = [&](const char *what) {
+        return cleanup(set_error(QADIC_E_CUDA, "%s: %s", what, cudaGetErrorString(cudaGetLastError())));
+    };
+    const size_t c_plane = (size_t)m * n;
+    auto dA_blk = [&](int i) { return dA + (size_t)planes * r0[i] * K * esz; };
+    auto pA_blk = [&](int i) { return pA + 2 * (size_t)f.k * r0[i] * K; };
+    auto pB_blk = [&](int j) { return pB + 2 * (size_t)f.k * nc * K * j; };
+    auto copy_b = [&](int j) -> cudaError_t {   // columns j nc .. j nc + nc - 1 of every plane
+        for (uint32_t i = 0; i < planes; ++i) {
+            const size_t off = ((size_t)i * K * n + (size_t)j * nc) * esz;
+            const cudaError_t e = cudaMemcpy2DAsync(dB + off, n * esz, (const char *)B_host + off,
+                                                    n * esz, nc * esz, K, cudaMemcpyHostToDevice, side);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaEventRecord(ev_bc[j], side);
+    };
+    auto copy_a = [&](int b) -> cudaError_t {   // rows r0[b] .., each plane a block of its own
+        for (uint32_t i = 0; i < planes; ++i) {
+            const cudaError_t e = cudaMemcpyAsync(
+                dA_blk(b) + (size_t)i * rows[b] * K * esz,
+                (const char *)A_host + ((size_t)i * m + r0[b]) * K * esz, (size_t)rows[b] * K * esz,
+                cudaMemcpyHostToDevice, side);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaEventRecord(ev_ac[b], side);
+    };
+    // every side stream starts after the work already queued on `stream`
+    if (cudaEventRecord(ev_start, s) || cudaStreamWaitEvent(side, ev_start, 0) ||
+        cudaStreamWaitEvent(side2, ev_start, 0) || cudaStreamWaitEvent(d2h, ev_start, 0))
+        return cuda_fail("stream order");
+    if (copy_b(0) || copy_a(0)) return cuda_fail("H2D copy");
+    for (int j = 1; j < NCB; ++j)
+        if (copy_b(j)) return cuda_fail("H2D copy");
+    for (int b = 1; b < nrb; ++b)
+        if (copy_a(b)) return cuda_fail("H2D copy");
+    // packs in the order the blocks land
+    auto pack_b = [&](int j) -> int {
+        if (cudaStreamWaitEvent(side2, ev_bc[j], 0)) return cuda_fail("wait");
+        const int st = qadic_pack(field, in_fmt, dB + (size_t)j * nc * esz, K, nc, n,
+                                  QADIC_FMT_OPERAND_B, pB_blk(j), K, side2);
+        if (st != QADIC_OK) return cleanup(st);
+        return cudaEventRecord(ev_bp[j], side2) ? cuda_fail("event") : QADIC_OK;
+    };
+    auto pack_a = [&](int b) -> int {
+        if (cudaStreamWaitEvent(side2, ev_ac[b], 0)) return cuda_fail("wait");
+        const int st = qadic_pack(field, in_fmt, dA_blk(b), rows[b], K, K, QADIC_FMT_OPERAND_A,
+                                  pA_blk(b), K, side2);
+        if (st != QADIC_OK) return cleanup(st);
+        return cudaEventRecord(ev_ap[b], side2) ? cuda_fail("event") : QADIC_OK;
+    };
+    int st;
+    if ((st = pack_b(0)) != QADIC_OK || (st = pack_a(0)) != QADIC_OK) return st;
+    for (int j = 1; j < NCB; ++j)
+        if ((st = pack_b(j)) != QADIC_OK) return st;
+    for (int b = 1; b < nrb; ++b)
+        if ((st = pack_a(b)) != QADIC_OK) return st;
+    // block GEMMs; each block of C goes back while the next is computed
+    for (int b = 0; b < nrb; ++b)
+        for (int j = 0; j < NCB; ++j) {
+            const bool last = b + 1 == nrb && j + 1 == NCB;
+            if ((j == 0 && cudaStreamWaitEvent(s, ev_ap[b], 0)) ||
+                (b == 0 && cudaStreamWaitEvent(s, ev_bp[j], 0)))
+                return cuda_fail("wait");
+            if ((st = launch_gemm_planes_tc_strided(f, rows[b], nc, K, pA_blk(b), K,
+                                                    (int64_t)rows[b] * K, pB_blk(j), K,
+                                                    (int64_t)nc * K, dC + r0[b] * n + (int64_t)j * nc,
+                                                    n, (int64_t)c_plane, s)) != QADIC_OK)
+                return cleanup(st);
+            cudaStream_t cs = last ? s : d2h;
+            if (!last && (cudaEventRecord(ev_g[b * NCB + j], s) ||
+                          cudaStreamWaitEvent(d2h, ev_g[b * NCB + j], 0)))
+                return cuda_fail("event");
+            for (uint32_t i = 0; i < f.k; ++i) {
+                const size_t off = i * c_plane + (size_t)r0[b] * n + (size_t)j * nc;
+                if (cudaMemcpy2DAsync(C_host + off, n, dC + off, n, nc, rows[b],
+                                      cudaMemcpyDeviceToHost, cs))
+                    return cuda_fail("D2H copy");
+            }
+        }
+    // join: `stream` also waits for the side streams' copies
+    if (cudaEventRecord(ev_join, side) || cudaStreamWaitEvent(s, ev_join, 0) ||
+        cudaEventRecord(ev_d2h, d2h) || cudaStreamWaitEvent(s, ev_d2h, 0))
+        return cuda_fail("join");
+    return cleanup(QADIC_OK);
+}
+
+}  // namespace
+
 int qadic_matmul_host(const qadic_field *field, int path, int in_fmt, int64_t m, int64_t n,
                       int64_t K, const void *A_host, const void *B_host, uint8_t *C_host,
                       void *workspace, size_t ws_bytes, void *stream) {
@@ -484,6 +614,12 @@ int qadic_matmul_host(const qadic_field *field, int path, int in_fmt, int64_t m,
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaStream_t side = side_stream(dev, 0), side2 = side_stream(dev, 1), d2h = side_stream(dev, 2);
     if (!side || !side2 || !d2h) return set_error(QADIC_E_CUDA, "no side stream");
+    if (path == QADIC_PATH_PLANES && m >= 512 && n >= 1024 && n % 512 == 0) {
+        const bool planar_in = in_fmt != QADIC_FMT_LOG;
+        return matmul_host_blocked(field, f, in_fmt, m, n, K, A_host, B_host, C_host, dA, dB, dC, pA,
+                                   pB, planar_in ? f.k : 1, planar_in ? 1 : eb, s, side, side2, d2h,
+                                   sms);
+    }
     constexpr int kMaxBlocks = 8;
     int64_t rows[kMaxBlocks] = {m};
     int nblk = 1;

@@ -522,12 +522,12 @@ def test_matmul_host_log_codes_split(torch, orc, pk, shape):
     assert np.array_equal(np.transpose(hC.numpy(), (1, 2, 0)), want)
 
 
-def test_matmul_host_row_blocks(torch, orc):
-    """m = 2048, n = 4096: the host pipeline splits A into four row blocks of
-    512 rows (each block's GEMM one round of 64 output units of 256 x 128 on
-    the SM pairs), C going back block by block on its own stream; rows of
-    every block against the oracle, and the whole result against the device
-    path."""
+def test_matmul_host_blocks(torch, orc):
+    """m = 2048, n = 4096: the host pipeline cuts B into four column blocks
+    and A into row blocks (each block GEMM one round of 256 x 128 output
+    units on the SM pairs), C going back block by block on its own stream;
+    rows of every block against the oracle, and the whole result against the
+    device path."""
     p, k, m, n, K = 101, 2, 2048, 4096, 64
     f = q.Field(p, k)
     A = W.centred_planes(k, m, K, 50, salt=71)
@@ -544,6 +544,46 @@ def test_matmul_host_row_blocks(torch, orc):
     assert np.array_equal(hC.numpy(), C)
     rows = np.array([0, 511, 512, 1023, 1024, 1535, 1536, 2047])
     want = orc.gemm(p, f.poly, np.transpose(A[:, rows], (1, 2, 0)), np.transpose(B, (1, 2, 0)))
+    assert np.array_equal(np.transpose(C[:, rows], (1, 2, 0)), want)
+
+
+@pytest.mark.parametrize("fmt", [q.FMT_INT8_PLANES, q.FMT_COEFF_U8, q.FMT_LOG])
+@pytest.mark.parametrize("shape", [(1100, 1024, 72), (520, 1536, 40), (2304, 2048, 16)])
+def test_matmul_host_column_blocks(torch, orc, fmt, shape):
+    """n a multiple of 512 (>= 1024) and m >= 512: B crosses the link in four
+    column blocks and A in row blocks (ragged last block), one GEMM per
+    block pair, C back in 2-D block copies, twice in a row on the same
+    workspace; the whole result against the device path, sampled rows of
+    every row block against the oracle."""
+    m, n, K = shape
+    p, k = 101, 2
+    f = q.Field(p, k)
+    if fmt == q.FMT_LOG:
+        A, B = W.log_matrix(m, K, f.order, salt=81), W.log_matrix(K, n, f.order, salt=82)
+    elif fmt == q.FMT_INT8_PLANES:
+        A, B = W.centred_planes(k, m, K, 50, salt=81), W.centred_planes(k, K, n, 50, salt=82)
+    else:
+        A, B = W.coeff_planes(k, m, K, p, salt=81), W.coeff_planes(k, K, n, p, salt=82)
+    hA, hB = torch.from_numpy(A).pin_memory(), torch.from_numpy(B).pin_memory()
+    hC = torch.full((k, m, n), 255, dtype=torch.uint8).pin_memory()
+    ws = torch.empty(f.matmul_workspace_size(q.PATH_PLANES, fmt, m, n, K), dtype=torch.uint8,
+                     device="cuda")
+    a = f.pack(fmt, dev(torch, A), m, K, q.FMT_OPERAND_A)
+    b = f.pack(fmt, dev(torch, B), K, n, q.FMT_OPERAND_B)
+    C = f.gemm(q.PATH_PLANES, a, b, m, n, K).cpu().numpy()
+    for _ in range(2):
+        hC.fill_(255)
+        f.matmul_host(q.PATH_PLANES, fmt, hA, hB, hC, m, n, K, ws)
+        torch.cuda.synchronize()
+        q.sync_status()
+        assert np.array_equal(hC.numpy(), C)
+    rows = np.unique(np.clip(np.array([0, 255, 256, 511, 512, 1023, 1024, m // 2, m - 1]), 0, m - 1))
+    if fmt == q.FMT_LOG:
+        T = orc.antilog(p, f.poly)
+        want = orc.gemm(p, f.poly, T[A[rows].astype(np.int64)], T[B.astype(np.int64)])
+    else:
+        want = orc.gemm(p, f.poly, np.transpose(A[:, rows].astype(np.int64) % p, (1, 2, 0)),
+                        np.transpose(B.astype(np.int64) % p, (1, 2, 0)))
     assert np.array_equal(np.transpose(C[:, rows], (1, 2, 0)), want)
 
 
