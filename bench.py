@@ -48,12 +48,16 @@ def headline_config(n):
 # headline GEMM from one ncu capture of the same workload, valid only while
 # the kernel's source file, "//" comments and blank lines aside, is the one
 # captured (its hash below); otherwise the line reports null.
-PLANE_KERNEL = "gemm_planes_pair_kernel<2,128>"
+PLANE_KERNEL = "gemm_planes_pair_kernel<2,128,false>"
 MEASURED_TRAFFIC = {
     PLANE_KERNEL: {
         "file": "paper_0710_0510_gb300/csrc/k_gemm_tc.cu",
-        "code_sha256": "25bc66580d5ad95193cecc7cd4f7bd7c40a9b282cccba529aaf82540ddac280b",
-        "bytes": 467632384 + 34291200, "n": 4096},
+        "code_sha256": "12cbc6ee979769f4b0f115a28ca3ac34291e9d1a2dec379642ca84213096d298",
+        "bytes": 431406080 + 30127616, "n": 4096},
+    "gemm_planes_pair_kernel<2,128,true>": {
+        "file": "paper_0710_0510_gb300/csrc/k_gemm_tc.cu",
+        "code_sha256": "12cbc6ee979769f4b0f115a28ca3ac34291e9d1a2dec379642ca84213096d298",
+        "bytes": 68489984 + 16238336, "n": 4096},
 }
 
 
@@ -66,7 +70,7 @@ def plane_kernel(p, n):
     chunk_kb = ((1 << 24) - 2 * p) // (h * h) // 64
     if n > 128 and (n + 63) // 64 <= chunk_kb:
         return PLANE_KERNEL
-    return "gemm_planes_tc_kernel<2,128>"
+    return "gemm_planes_tc_kernel<2,128,false>"
 
 
 def source_hash(path):
@@ -138,7 +142,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="plane",
                     choices=["plane", "fp64", "redq", "polymul", "large", "batched", "fqt", "fold",
-                             "karatsuba"])
+                             "karatsuba", "e4m3"])
     ap.add_argument("--n", type=int, default=None, help="override the matrix size")
     ap.add_argument("--words", type=int, default=1 << 28, help="REDQ sweep size (words)")
     ap.add_argument("--extras", default="all", choices=["all", "none"],
@@ -443,6 +447,65 @@ def bench_karatsuba(args, torch, q, W, f, A, B, n, C_plane, steps=20):
                          "unit": "TFLOP/s", "frac": achieved / pk["bf16_sustained"],
                          "traffic": None, "kernel": "gemm_fold_tc_kernel<3,128,karatsuba>",
                          "flop_count": "3 plane products (2 * 3 * n^3)"}}
+
+
+def bench_e4m3(args, torch, q, W, p=31, n=4096, steps=20):
+    """GF(p^2) with p <= 31 on both plane paths, same inputs: the bf16 plane
+    path (one-launch pack + kind::f16 GEMM) and the e4m3 one (two pack
+    launches + kind::f8f6f4 GEMM, half the operand bytes, twice the tensor
+    rate); bit-exact against each other."""
+    k = 2
+    h = (p - 1) // 2
+    f = q.Field(p, k)
+    dA = torch.from_numpy(W.centred_planes(k, n, n, h, index=2, salt=31)).cuda()
+    dB = torch.from_numpy(W.centred_planes(k, n, n, h, index=2, salt=32)).cuda()
+    stream = torch.cuda.current_stream()
+    out = {}
+    Cs = {}
+    pk = peaks()
+    for name, dt in (("bf16", torch.bfloat16), ("e4m3", torch.uint8)):
+        opA = torch.empty((k, n, n), dtype=dt, device="cuda")
+        opB = torch.empty((k, n, n), dtype=dt, device="cuda")
+        C = torch.empty((k, n, n), dtype=torch.uint8, device="cuda")
+
+        def step(kev, name=name, opA=opA, opB=opB, C=C):
+            if name == "bf16":
+                f.pack_operands(q.FMT_INT8_PLANES, dA, dB, n, n, n, opA, opB)
+            else:
+                f.pack(q.FMT_INT8_PLANES, dA, n, n, q.FMT_OPERAND_A_E4M3, out=opA)
+                f.pack(q.FMT_INT8_PLANES, dB, n, n, q.FMT_OPERAND_B_E4M3, out=opB)
+            if kev is not None:
+                a, b = ev_pair(torch)
+                a.record(stream)
+            f.gemm(q.PATH_PLANES if name == "bf16" else q.PATH_PLANES_E4M3, opA, opB, n, n, n, C=C)
+            if kev is not None:
+                b.record(stream)
+                kev.append((a, b))
+
+        total, kms = time_steps(torch, step, steps, 3, None, kernel_events=True)
+        ms = total / steps
+        achieved = 4 * 2.0 * n ** 3 / (kms * 1e-3) / 1e12
+        kernel = ("gemm_planes_pair_kernel<2,128,false>" if name == "bf16"
+                  else "gemm_planes_pair_kernel<2,128,true>")
+        traffic, traffic_source = measured_traffic(kernel, n)
+        scale = 2.0 if name == "e4m3" else 1.0
+        peak = pk["bf16_sustained"] * scale
+        out[name] = {"value": 2.0 * n ** 3 / (ms * 1e-3) / 1e9, "unit": "field Gop/s",
+                     "ms_per_step": ms, "kernel_ms": kms,
+                     "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak,
+                                  "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                                  "traffic_source": traffic_source,
+                                  "algorithmic_bytes": 2 * 2 * n * n * (2 if name == "bf16" else 1)
+                                  + 2 * n * n,
+                                  "peak_scale": scale, "kernel": kernel,
+                                  "peak_source": pk["source"] + " bf16 sustained (cuBLAS)" +
+                                  (" x 2, the nominal fp8/bf16 dense ratio" if name == "e4m3"
+                                   else "")}}
+        Cs[name] = C
+    out["bitexact_e4m3_vs_bf16"] = bool(torch.equal(Cs["bf16"], Cs["e4m3"]))
+    out["kernel_speedup_e4m3"] = out["bf16"]["kernel_ms"] / out["e4m3"]["kernel_ms"]
+    out["workload"] = f"GF({p}^2) n={n}, int8 centred planes resident"
+    return out
 
 
 def bench_fp64(args, torch, q, W, f, A, B, n, reps=2):
@@ -1058,6 +1121,17 @@ def run_workload(args, torch, q, W, dist, rank, world, line, extras):
         line["config"] = {"workload": f"GF(101^2) n={n}, {args.workload} form", "p": 101,
                           "k": 2, "n": n, "l2": FLUSH_NOTE}
         extras["bitexact_vs_plane"] = r["bitexact_vs_plane"]
+    elif args.workload == "e4m3":
+        n = args.n or 4096
+        r = bench_e4m3(args, torch, q, W, n=n, steps=args.steps)
+        e = r["e4m3"]
+        line.update({"value": e["value"] * world, "unit": "field Gop/s",
+                     "ms_per_step": e["ms_per_step"], "dtype": "fp8 e4m3 exact, f32 accumulate",
+                     "roofline": e["roofline"], "gpu_launches": 3 * args.steps})
+        line["config"] = {"workload": f"GF(31^2) n={n}: pack A, B to e4m3 planes + tcgen05 "
+                          "kind::f8f6f4 plane GEMM + fused epilogue", "p": 31, "k": 2, "n": n,
+                          "l2": "each step writes and reads more than L2 (129 MB)"}
+        extras.update({k_: r[k_] for k_ in ("bf16", "bitexact_e4m3_vs_bf16", "kernel_speedup_e4m3")})
     elif args.workload == "fqt":
         r = bench_fqt(args, torch, q, W)
         line.update({"value": r["value"] * world, "unit": "products/s", "ms_per_step": r["ms"],
@@ -1120,6 +1194,8 @@ def run_plane_extras(args, torch, q, W, extras):
         return {"value": lres["value"], "unit": "field Gop/s", "ms_per_step": lres["ms_per_step"],
                 "kernel_ms": lres["kernel_ms"], "roofline": lres["roofline"]}
     extras["large_gf251_2_n16384"] = guarded(large_leg)
+    torch.cuda.empty_cache()
+    extras["e4m3_gf31_2_n4096"] = guarded(bench_e4m3, args, torch, q, W)
     torch.cuda.empty_cache()
 
 

@@ -66,7 +66,10 @@ typedef enum {
     QADIC_FMT_OPERAND_B_FOLD = 6,/* k planes i, each k blocks j of n_pad rows: plane j of B X^i mod P,
                                     TRANSPOSED (K contiguous); n_pad = cols rounded up to 256 */
     QADIC_FMT_OPERAND_A_KARA = 7,/* k = 2: 3 bf16 planes c_0, c_1, (c_0 + c_1) mod p, centred, rows x cols */
-    QADIC_FMT_OPERAND_B_KARA = 8 /* k = 2: the same 3 planes, TRANSPOSED: cols x rows */
+    QADIC_FMT_OPERAND_B_KARA = 8,/* k = 2: the same 3 planes, TRANSPOSED: cols x rows */
+    QADIC_FMT_OPERAND_A_E4M3 = 9,/* p <= 31: k planes of fp8 e4m3 centred coefficients (one byte
+                                    each; |c| <= 15 is exact), rows x cols (K contiguous) */
+    QADIC_FMT_OPERAND_B_E4M3 = 10/* p <= 31: the same, TRANSPOSED: cols x rows */
 } qadic_format;
 
 /* Contraction forms of qadic_gemm. */
@@ -74,7 +77,8 @@ typedef enum {
     QADIC_PATH_FP64_QADIC = 0, /* FP64 q-adic GEMM, REDQ after every n_q-product K-block (Alg. 4) */
     QADIC_PATH_PLANES = 1,     /* k x k coefficient-plane tensor-core GEMMs + fused mod-p / mod-P epilogue */
     QADIC_PATH_FOLD = 2,       /* fold-before: B's multiplication matrices, one prime-field tensor-core GEMM */
-    QADIC_PATH_KARATSUBA = 3   /* k = 2: three plane products (Karatsuba) on the tensor cores */
+    QADIC_PATH_KARATSUBA = 3,  /* k = 2: three plane products (Karatsuba) on the tensor cores */
+    QADIC_PATH_PLANES_E4M3 = 4 /* p <= 31: the plane path on fp8 e4m3 operands (kind::f8f6f4) */
 } qadic_path;
 
 /* Field description returned by qadic_field_info. */
@@ -176,7 +180,8 @@ int qadic_field_info(const qadic_field *field, qadic_info *out);
  * OPERAND_B_KARA.
  * Errors: QADIC_E_INVALID (format pair, ld < cols, NULL), QADIC_E_OVERFLOW
  * (QADIC_F64 requested but Eq. 2 has no q with n_q >= 1).
- * OPERAND formats need ld_out a multiple of 8 and 16-byte aligned bases. */
+ * OPERAND formats need ld_out a multiple of 8 (of 16 for the E4M3 ones) and
+ * 16-byte aligned bases; the E4M3 ones need p <= 31 (QADIC_E_UNSUPPORTED). */
 int qadic_pack(const qadic_field *field, int in_fmt, const void *in, int64_t rows, int64_t cols,
                int64_t ld_in, int out_fmt, void *out, int64_t ld_out, void *stream);
 
@@ -192,6 +197,11 @@ int qadic_pack(const qadic_field *field, int in_fmt, const void *in, int64_t row
  *   (Eq. 1 coefficientwise) are accumulated exactly on the tensor cores in
  *   K-chunks of at most k_chunk_f32, reduced mod p, and folded mod P with
  *   X^t mod P in the epilogue.  lda, ldb multiples of 8.
+ * QADIC_PATH_PLANES_E4M3 (p <= 31): the same contraction on A in
+ *   OPERAND_A_E4M3 and B in OPERAND_B_E4M3 (one byte per coefficient;
+ *   |c| <= 15 is exact in e4m3), through tcgen05 kind::f8f6f4 MMAs with FP32
+ *   accumulators: half the operand bytes of the bf16 planes and twice the
+ *   tensor rate.  lda, ldb multiples of 16; QADIC_E_UNSUPPORTED for p > 31.
  * QADIC_PATH_FOLD: A is OPERAND_A, B is OPERAND_B_FOLD (ldb >= K, multiple
  *   of 8).  out_j = sum_i A_i M_ij(B) with M_ij(B) plane j of B X^i mod P:
  *   the reduction mod P happens before the contraction (the same map Thm. 3
@@ -228,7 +238,7 @@ int qadic_pack_operands(const qadic_field *field, int in_fmt, const void *A, int
  * planes of a plane format `rows * ld` elements apart), packed into
  * `workspace` (device, 256-byte aligned, at least
  * qadic_matmul_device_workspace_size bytes) and multiplied with `path`
- * (any of the four); C: k planes of uint8, m x n (ldc).  For the plane path
+ * (any of the five); C: k planes of uint8, m x n (ldc).  For the plane path
  * with plane inputs both operands are packed by one launch.  Errors as for
  * qadic_pack and qadic_gemm, QADIC_E_NOMEM for a short workspace. */
 size_t qadic_matmul_device_workspace_size(const qadic_field *field, int path, int64_t m,
@@ -242,7 +252,8 @@ int qadic_matmul(const qadic_field *field, int path, int in_fmt, int64_t m, int6
  * INT8_PLANES) in HOST memory (pinned for asynchrony), C (k planes of uint8,
  * m x n) in HOST memory.  Copies the inputs into `workspace` (device, at
  * least qadic_matmul_workspace_size bytes), packs, multiplies with `path`,
- * and copies C back, all enqueued on `stream`.  Dense leading dimensions. */
+ * and copies C back, all enqueued on `stream`.  Dense leading dimensions.
+ * path: QADIC_PATH_FP64_QADIC or QADIC_PATH_PLANES (K % 8 == 0). */
 size_t qadic_matmul_workspace_size(const qadic_field *field, int path, int in_fmt, int64_t m,
                                    int64_t n, int64_t K);
 int qadic_matmul_host(const qadic_field *field, int path, int in_fmt, int64_t m, int64_t n,

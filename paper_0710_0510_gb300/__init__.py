@@ -18,9 +18,10 @@ OK, E_INVALID, E_NOT_PRIME, E_REDUCIBLE, E_OVERFLOW, E_UNSUPPORTED, E_CUDA, E_DE
     E_NOMEM = range(9)
 # qadic_format
 FMT_LOG, FMT_COEFF_U8, FMT_INT8_PLANES, FMT_QADIC_F64, FMT_OPERAND_A, FMT_OPERAND_B, \
-    FMT_OPERAND_B_FOLD, FMT_OPERAND_A_KARA, FMT_OPERAND_B_KARA = range(9)
+    FMT_OPERAND_B_FOLD, FMT_OPERAND_A_KARA, FMT_OPERAND_B_KARA, FMT_OPERAND_A_E4M3, \
+    FMT_OPERAND_B_E4M3 = range(11)
 # qadic_path
-PATH_FP64_QADIC, PATH_PLANES, PATH_FOLD, PATH_KARATSUBA = 0, 1, 2, 3
+PATH_FP64_QADIC, PATH_PLANES, PATH_FOLD, PATH_KARATSUBA, PATH_PLANES_E4M3 = 0, 1, 2, 3, 4
 REDQ_INT_FLOOR = 0x100
 REDQ_F32_DIGITS = 0x200
 POLYMUL_PLAIN_F64 = 0x1
@@ -257,6 +258,10 @@ class Field:
                 out = torch.empty((3, rows, cols), dtype=torch.bfloat16, device=x.device)
             elif out_fmt == FMT_OPERAND_B_KARA:
                 out = torch.empty((3, cols, rows), dtype=torch.bfloat16, device=x.device)
+            elif out_fmt == FMT_OPERAND_A_E4M3:
+                out = torch.empty((self.k, rows, cols), dtype=torch.uint8, device=x.device)
+            elif out_fmt == FMT_OPERAND_B_E4M3:
+                out = torch.empty((self.k, cols, rows), dtype=torch.uint8, device=x.device)
             elif out_fmt == FMT_OPERAND_B_FOLD:
                 out = torch.empty((self.k, self.k * fold_n_pad(cols), (rows + 7) // 8 * 8),
                                   dtype=torch.bfloat16, device=x.device)
@@ -268,7 +273,8 @@ class Field:
             if out_fmt == FMT_OPERAND_B_FOLD:
                 ld_out = out.shape[-1]
             else:
-                ld_out = rows if out_fmt in (FMT_OPERAND_B, FMT_OPERAND_B_KARA) else cols
+                ld_out = rows if out_fmt in (FMT_OPERAND_B, FMT_OPERAND_B_KARA,
+                                             FMT_OPERAND_B_E4M3) else cols
         _check(lib().qadic_pack(self._h, in_fmt, _ptr(x), rows, cols, ld_in, out_fmt, _ptr(out),
                                 ld_out, _stream(stream)))
         return out

@@ -259,7 +259,7 @@ int qadic_pack(const qadic_field *field, int in_fmt, const void *in, int64_t row
     if (ld_in < cols) return set_error(QADIC_E_INVALID, "ld_in < cols");
     const int64_t out_minor =
         (out_fmt == QADIC_FMT_OPERAND_B || out_fmt == QADIC_FMT_OPERAND_B_FOLD ||
-         out_fmt == QADIC_FMT_OPERAND_B_KARA) ? rows : cols;
+         out_fmt == QADIC_FMT_OPERAND_B_KARA || out_fmt == QADIC_FMT_OPERAND_B_E4M3) ? rows : cols;
     if (ld_out < out_minor) return set_error(QADIC_E_INVALID, "ld_out too small");
     if (out_fmt == QADIC_FMT_QADIC_F64 && f.n_q == 0)
         return set_error(QADIC_E_OVERFLOW, "Eq. 2 admits no q-adic block for p=%u k=%u", f.p, f.k);
@@ -268,6 +268,10 @@ int qadic_pack(const qadic_field *field, int in_fmt, const void *in, int64_t row
         out_fmt == QADIC_FMT_OPERAND_B_KARA) {
         if (ld_out % 8 != 0 || ((uintptr_t)out & 15) != 0)
             return set_error(QADIC_E_INVALID, "operand output needs ld %% 8 == 0 and 16B alignment");
+    }
+    if (out_fmt == QADIC_FMT_OPERAND_A_E4M3 || out_fmt == QADIC_FMT_OPERAND_B_E4M3) {
+        if (ld_out % 16 != 0 || ((uintptr_t)out & 15) != 0)
+            return set_error(QADIC_E_INVALID, "e4m3 operand output needs ld %% 16 == 0 and 16B alignment");
     }
     return launch_pack(f, in_fmt, in, rows, cols, ld_in, out_fmt, out, ld_out,
                        (cudaStream_t)stream);
@@ -296,11 +300,12 @@ int qadic_gemm(const qadic_field *field, int path, int64_t m, int64_t n, int64_t
         return launch_gemm_f64(f, m, n, K, (const double *)A, lda, (const double *)B, ldb, C, ldc,
                                s);
     }
-    if (path == QADIC_PATH_PLANES) {
+    if (path == QADIC_PATH_PLANES || path == QADIC_PATH_PLANES_E4M3) {
         if (lda < K || ldb < K) return set_error(QADIC_E_INVALID, "lda or ldb < K");
         if (!gemm_planes_tc_supported(f))
             return set_error(QADIC_E_UNSUPPORTED, "no tensor-core plane kernel for k=%u", f.k);
-        return launch_gemm_planes_tc(f, m, n, K, A, lda, B, ldb, C, ldc, s);
+        return launch_gemm_planes_tc(f, m, n, K, A, lda, B, ldb, C, ldc, s,
+                                     path == QADIC_PATH_PLANES_E4M3);
     }
     if (path == QADIC_PATH_FOLD) {
         if (lda < K || ldb < K) return set_error(QADIC_E_INVALID, "lda or ldb < K");
@@ -331,6 +336,12 @@ static size_t packed_bytes(const Field &f, int path, int64_t m, int64_t n, int64
             b = 2 * (size_t)f.k * f.k * (size_t)fold_n_pad(n) * K8;
             break;
         case QADIC_PATH_KARATSUBA: a = 6 * (size_t)m * K8; b = 6 * (size_t)n * K8; break;
+        case QADIC_PATH_PLANES_E4M3: {   // one byte per element, rows padded to 16
+            const size_t K16 = (size_t)((K + 15) / 16 * 16);
+            a = (size_t)f.k * m * K16;
+            b = (size_t)f.k * n * K16;
+            break;
+        }
         default: return 0;
     }
     if (a_bytes) *a_bytes = align256_(a);
@@ -376,8 +387,10 @@ int qadic_matmul(const qadic_field *field, int path, int in_fmt, int64_t m, int6
     if (m < 0 || n < 0 || K < 0) return set_error(QADIC_E_INVALID, "negative size");
     if (in_fmt != QADIC_FMT_LOG && in_fmt != QADIC_FMT_COEFF_U8 && in_fmt != QADIC_FMT_INT8_PLANES)
         return set_error(QADIC_E_INVALID, "input format %d", in_fmt);
-    if (path < QADIC_PATH_FP64_QADIC || path > QADIC_PATH_KARATSUBA)
+    if (path < QADIC_PATH_FP64_QADIC || path > QADIC_PATH_PLANES_E4M3)
         return set_error(QADIC_E_INVALID, "unknown path %d", path);
+    if (path == QADIC_PATH_PLANES_E4M3 && f.p > 31)
+        return set_error(QADIC_E_UNSUPPORTED, "e4m3 operands need p <= 31 (|c| <= 15 exact)");
     size_t a_bytes = 0;
     const size_t need = packed_bytes(f, path, m, n, K, &a_bytes);
     if (m == 0 || n == 0) return QADIC_OK;
@@ -411,6 +424,13 @@ int qadic_matmul(const qadic_field *field, int path, int in_fmt, int64_t m, int6
     int64_t la, lb;
     switch (path) {
         case QADIC_PATH_FP64_QADIC: fa = fb = QADIC_FMT_QADIC_F64; la = K; lb = n; break;
+        case QADIC_PATH_PLANES_E4M3:
+            if (!gemm_planes_tc_supported(f))
+                return set_error(QADIC_E_UNSUPPORTED, "no tensor-core plane kernel for k=%u", f.k);
+            fa = QADIC_FMT_OPERAND_A_E4M3;
+            fb = QADIC_FMT_OPERAND_B_E4M3;
+            la = lb = (K + 15) / 16 * 16;
+            break;
         case QADIC_PATH_FOLD: fa = QADIC_FMT_OPERAND_A; fb = QADIC_FMT_OPERAND_B_FOLD; la = lb = K8; break;
         default: fa = QADIC_FMT_OPERAND_A_KARA; fb = QADIC_FMT_OPERAND_B_KARA; la = lb = K8; break;
     }

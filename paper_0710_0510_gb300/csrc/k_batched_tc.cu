@@ -182,21 +182,6 @@ __device__ __forceinline__ uint64_t desc_kmajor(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor, kind::f8f6f4 with e4m3 A and B (type code 0),
-// f32 D, both K-major.
-__device__ __forceinline__ uint32_t idesc_e4m3_f32(uint32_t M, uint32_t N) {
-    return (1u << 4) | ((N >> 3) << 17) | ((M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
 __device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -535,7 +520,7 @@ __device__ __noinline__ bool tc_mma_tile(uint32_t d0, uint8_t *smem, int slot_by
                                          uint64_t *acc_empty_b, int &drains,
                                          volatile int *abort_flag) {
     constexpr int BN = tc_bn(KP);
-    const uint32_t idesc = FP8 ? idesc_e4m3_f32(128, KP * BN) : ptx::idesc_bf16_f32(128, KP * BN);
+    const uint32_t idesc = FP8 ? ptx::idesc_e4m3_f32(128, KP * BN) : ptx::idesc_bf16_f32(128, KP * BN);
     const uint32_t ab = (uint32_t)(KP * rows8 * 32), bb = (uint32_t)(KP * BN * 32);
     const uint64_t astep = (uint64_t)((uint32_t)rows8 * 32) >> 4;   // descriptor units of 16 bytes
     const int cap = tc_stage_kblocks(slot_bytes, ab, bb);
@@ -553,7 +538,7 @@ __device__ __noinline__ bool tc_mma_tile(uint32_t d0, uint8_t *smem, int slot_by
 #pragma unroll
             for (int i = 0; i < KP; ++i) {
                 const uint32_t col = KP <= 2 ? (uint32_t)(i * KP * BN) : (uint32_t)(i * BN);
-                if constexpr (FP8) mma_e4m3(d0 + col, ad + i * astep, bd, idesc, 1u);
+                if constexpr (FP8) ptx::mma_e4m3(d0 + col, ad + i * astep, bd, idesc, 1u);
                 else ptx::mma_bf16(d0 + col, ad + i * astep, bd, idesc, 1u);
             }
             if (--to_drain == 0 && kb + 1 < ks_n) {

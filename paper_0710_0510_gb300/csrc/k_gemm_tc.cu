@@ -55,6 +55,27 @@ __device__ __forceinline__ uint64_t operand_desc(const void *tile) {
     if constexpr (kRowBytes == 128) return ptx::smem_desc_sw128(tile);
     else return ptx::smem_desc_sw64(tile);
 }
+// Operand element type of the plane GEMMs: bf16 (64 elements per 128-byte
+// K-block row, 16 per MMA) or fp8 e4m3 for p <= 31 (128 and 32: the same
+// bytes per row and per MMA, so the shared-memory layout, the descriptor
+// steps and the MMA count per K-block are the same; a K-block covers twice
+// the K and the MMAs run at the fp8 rate).
+template <bool FP8>
+struct OpT {
+    static constexpr int KE = FP8 ? 128 : 64;   // K elements per K-block
+    __device__ static uint32_t idesc(uint32_t M, uint32_t N) {
+        return FP8 ? ptx::idesc_e4m3_f32(M, N) : ptx::idesc_bf16_f32(M, N);
+    }
+    __device__ static void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+        if constexpr (FP8) ptx::mma_e4m3(d, a, b, idesc, acc);
+        else ptx::mma_bf16(d, a, b, idesc, acc);
+    }
+    __device__ static void mma_pair(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+        if constexpr (FP8) ptx::mma_e4m3_pair(d, a, b, idesc, acc);
+        else ptx::mma_bf16_pair(d, a, b, idesc, acc);
+    }
+};
+
 constexpr int kGroupM = 16;
 // Eight epilogue warps, two per 32-lane quarter of tensor memory, each taking
 // half of the quarter's columns.  The epilogue is latency-bound (tensor-
@@ -163,45 +184,75 @@ __device__ __forceinline__ void drain_accumulators(uint32_t tbase, const TcParam
     ptx::tmem_wait_st();
 }
 
+// Accumulators feeding plane sum t (two for C_1 with split accumulators).
+template <class CF>
+__host__ __device__ constexpr int feeders(int t) {
+    int c = 0;
+    for (int a = 0; a < CF::NACC; ++a) c += CF::sum_of(a) == t ? 1 : 0;
+    return c;
+}
+
+// A plane-sum residue |s| <= 127 as one byte, s + 128: the low byte of
+// s + (1.5 * 2^23 + 128), exact in FP32 (the spacing there is 1); and back.
+constexpr float kByteMagic = 12583040.f;   // 1.5 * 2^23 + 128
+__device__ __forceinline__ uint32_t byte_code(float s) { return __float_as_uint(s + kByteMagic); }
+__device__ __forceinline__ float byte_value(uint32_t word, int b) {
+    return __uint_as_float(0x4B400000u | ((word >> (8 * b)) & 0xFFu)) - kByteMagic;
+}
+
 // A warp's share of a finished tile: row `row` (this thread's lane), columns
-// col0 .. col0 + HALF.  Each plane sum is brought to |r| <= 1.5 p by one rint
-// step, the fold out_i = r_i + sum_t r_t (X^t mod P)_i runs in FP32 FMAs
-// (every value stays below 2^19, so they are exact), and only the k outputs
-// take the exact reduction to [0, p).  Chunks of 16 columns are stored as
-// soon as they are computed; release() runs once the last chunk has been
-// read from tensor memory.
+// col0 .. col0 + HALF.  Two passes, so that tensor memory goes back to the
+// MMAs as early as possible: the first reads every accumulator column of the
+// share and keeps each plane sum as a centred residue in one byte; release()
+// runs after its last load; the second folds and stores.  A residue is
+// x - p rint(x RN(1/p)): for |x| < 2^24 the product is within 2/p of x / p,
+// so rint is off by at most one and only where the centred residue exceeds
+// p/2 - 2, which leaves |r| < p/2 + 2 <= 127.5.  C_1 of the split
+// accumulators (the sum of two residues) takes one more such step (exact
+// there).  The fold out_i = s_i + sum_t s_t (X^t mod P)_i runs in FP32 FMAs
+// (every value below 2^17, exact) and only the k outputs take the exact
+// reduction to [0, p).
 template <int KP, int BN, class CF, class Release>
 __device__ __forceinline__ void tile_epilogue(uint32_t tbase, int64_t row, int64_t col0,
                                               uint8_t *__restrict__ C, const TcParams &P,
                                               const float *foldf, Release release) {
-#pragma unroll 1
-    for (int c = 0; c < CF::HALF; c += 16) {
-        float r[CF::NACC][16];
-        {
-            uint32_t v[CF::NACC][16];
+    constexpr int NS = 2 * KP - 1;
+    constexpr int NG = CF::HALF / 16;   // 16-column groups
+    uint32_t code[NG][NS][4];
 #pragma unroll
-            for (int t = 0; t < CF::NACC; ++t) ptx::tmem_ld16(tbase + t * BN + c, v[t]);
-            ptx::tmem_wait_ld();
-            if (c + 16 >= CF::HALF) release();   // tensor memory may take the next tile's MMAs
+    for (int g = 0; g < NG; ++g) {
+        uint32_t v[CF::NACC][16];
 #pragma unroll
-            for (int t = 0; t < CF::NACC; ++t)
+        for (int t = 0; t < CF::NACC; ++t) ptx::tmem_ld16(tbase + t * BN + 16 * g, v[t]);
+        ptx::tmem_wait_ld();
+        if (g == NG - 1) release();   // tensor memory may take the next tile's MMAs
+        float s[NS][16];
 #pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                    const float x = __uint_as_float(v[t][e]);
-                    r[t][e] = fmaf(-P.pf, rintf(x * P.inv_pf), x);
-                }
-        }
-        // plane sums C_t from the accumulators (exact: small integers)
-        float s[2 * KP - 1][16];
-#pragma unroll
-        for (int t = 0; t < 2 * KP - 1; ++t)
+        for (int t = 0; t < NS; ++t)
 #pragma unroll
             for (int e = 0; e < 16; ++e) s[t][e] = 0.f;
 #pragma unroll
         for (int a = 0; a < CF::NACC; ++a)
 #pragma unroll
-            for (int e = 0; e < 16; ++e) s[CF::sum_of(a)][e] += r[a][e];
-        const int64_t col = col0 + c;
+            for (int e = 0; e < 16; ++e) {
+                const float x = __uint_as_float(v[a][e]);
+                s[CF::sum_of(a)][e] += fmaf(-P.pf, rintf(x * P.inv_pf), x);
+            }
+#pragma unroll
+        for (int t = 0; t < NS; ++t) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e)
+                if (feeders<CF>(t) > 1) s[t][e] = fmaf(-P.pf, rintf(s[t][e] * P.inv_pf), s[t][e]);
+#pragma unroll
+            for (int w = 0; w < 4; ++w)
+                code[g][t][w] = __byte_perm(__byte_perm(byte_code(s[t][4 * w]), byte_code(s[t][4 * w + 1]), 0x0040),
+                                            __byte_perm(byte_code(s[t][4 * w + 2]), byte_code(s[t][4 * w + 3]), 0x0040),
+                                            0x5410);
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+        const int64_t col = col0 + 16 * g;
 #pragma unroll
         for (int i = 0; i < KP; ++i) {
             uint32_t word[4];
@@ -210,11 +261,10 @@ __device__ __forceinline__ void tile_epilogue(uint32_t tbase, int64_t row, int64
                 word[w] = 0;
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
-                    const int e = 4 * w + b;
-                    float o = s[i][e];
+                    float o = byte_value(code[g][i][w], b);
 #pragma unroll
-                    for (int t = KP; t < 2 * KP - 1; ++t)
-                        o = fmaf(s[t][e], foldf[(t - KP) * KP + i], o);
+                    for (int t = KP; t < NS; ++t)
+                        o = fmaf(byte_value(code[g][t][w], b), foldf[(t - KP) * KP + i], o);
                     word[w] |= mod_exact_f32(__float_as_uint(o), P.pf, P.inv_pf) << (8 * b);
                 }
             }
@@ -234,7 +284,7 @@ __device__ __forceinline__ void tile_epilogue(uint32_t tbase, int64_t row, int64
 
 // One CTA per output tile at a time; a stage is refilled once the MMAs that
 // read it have completed (their commit arrives on the stage's "empty" barrier).
-template <int KP, int BN>
+template <int KP, int BN, bool FP8>
 __global__ void __launch_bounds__(kThreads, 1)
 gemm_planes_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       uint8_t *__restrict__ C, const TcParams P) {
@@ -303,9 +353,9 @@ gemm_planes_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
                     // the k A tiles and the k B tiles of this K-block
                     ptx::mbar_arrive_expect_tx(&full[stage], CF::STAGE);
                     for (int i = 0; i < KP; ++i)
-                        ptx::tma_load_3d(a_tile(stage, i), &tmA, &full[stage], kb * BK, tm * BM, i);
+                        ptx::tma_load_3d(a_tile(stage, i), &tmA, &full[stage], kb * OpT<FP8>::KE, tm * BM, i);
                     for (int j = 0; j < KP; ++j)
-                        ptx::tma_load_3d(b_tile(stage, j), &tmB, &full[stage], kb * BK, tn * BN, j);
+                        ptx::tma_load_3d(b_tile(stage, j), &tmB, &full[stage], kb * OpT<FP8>::KE, tn * BN, j);
                 }
             }
             if (!ok) {
@@ -318,8 +368,8 @@ gemm_planes_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
-            const uint32_t idesc_all = ptx::idesc_bf16_f32(BM, KP * BN);
-            const uint32_t idesc_one = ptx::idesc_bf16_f32(BM, BN);
+            const uint32_t idesc_all = OpT<FP8>::idesc(BM, KP * BN);
+            const uint32_t idesc_one = OpT<FP8>::idesc(BM, BN);
             int64_t it = 0;
             int drain = 0, tcount = 0;
             bool ok = true;
@@ -351,11 +401,11 @@ gemm_planes_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
 #pragma unroll
                                 for (int j = 0; j < KP; ++j) {
                                     const uint64_t bd = operand_desc(b_tile(stage, j));
-                                    ptx::mma_bf16(tmem_base + (i + j) * BN, ad, bd, idesc_one,
+                                    OpT<FP8>::mma(tmem_base + (i + j) * BN, ad, bd, idesc_one,
                                                   j < KP - 1 ? 1u : 0u);
                                 }
                             } else {
-                                ptx::mma_bf16(tmem_base + CF::a_col(i), ad, bd0 + 2 * kk, idesc_all,
+                                OpT<FP8>::mma(tmem_base + CF::a_col(i), ad, bd0 + 2 * kk, idesc_all,
                                               (kb == 0 && kk == 0) ? 0u : 1u);
                             }
                         }
@@ -488,7 +538,7 @@ struct PairCfg {
 // within microseconds; the CTAs wait this long before leaving the cluster.
 constexpr uint64_t kSettleNs = 2000000;
 
-template <int KP, int BN>
+template <int KP, int BN, bool FP8>
 __global__ void __launch_bounds__(kThreads, 1)
 gemm_planes_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                         uint8_t *__restrict__ C, const TcParams P) {
@@ -564,11 +614,11 @@ gemm_planes_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_co
                     const uint32_t fb = in_leader(&full[stage]);
                     if (rank == 0) ptx::mbar_arrive_expect_tx(&full[stage], 2 * CF::STAGE);
                     for (int i = 0; i < KP; ++i)
-                        ptx::tma_load_3d_pair(a_tile(stage, i), &tmA, fb, kb * BK, tm * BM, i);
+                        ptx::tma_load_3d_pair(a_tile(stage, i), &tmA, fb, kb * OpT<FP8>::KE, tm * BM, i);
                     for (int b = 0; b < CF::NBOX; ++b) {
                         const int row = ((int)rank * CF::NBOX + b) * CF::BOX;   // in [B_0; B_1]
                         ptx::tma_load_3d_pair(b_half(stage) + b * CF::BOX * kRowBytes, &tmB, fb,
-                                              kb * BK, tn * BN + row % BN, row / BN);
+                                              kb * OpT<FP8>::KE, tn * BN + row % BN, row / BN);
                     }
                 }
             }
@@ -577,7 +627,7 @@ gemm_planes_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_co
     } else if (warp == 1) {
         if (lane == 0 && rank == 0) {
             // ---------------- MMA issuer (leader) ----------------
-            const uint32_t idesc = ptx::idesc_bf16_f32(2 * BM, KP * BN);
+            const uint32_t idesc = OpT<FP8>::idesc(2 * BM, KP * BN);
             const uint32_t peer_empty0 = in_peer(&empty[0]), peer_acc_full = in_peer(acc_full);
             auto commit_both = [&](uint64_t *bar, uint32_t peer_bar) {
                 ptx::mma_commit_pair(bar);
@@ -608,7 +658,7 @@ gemm_planes_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_co
                     for (int kk = 0; kk < BK / UMMA_K; ++kk)
 #pragma unroll
                         for (int i = 0; i < KP; ++i)
-                            ptx::mma_bf16_pair(tmem_base + CF::a_col(i),
+                            OpT<FP8>::mma_pair(tmem_base + CF::a_col(i),
                                                operand_desc(a_tile(stage, i)) + 2 * kk, bd + 2 * kk,
                                                idesc, (kb == 0 && kk == 0) ? 0u : 1u);
                     commit_both(&empty[stage], peer_empty0 + 8 * stage);
@@ -1032,16 +1082,20 @@ EncodeTiledFn get_encode_fn() {
     return fn;
 }
 
-// 3-D map over (K, rows, planes) of a k-plane bf16 operand, box (64, box_rows, 1).
+// 3-D map over (K, rows, planes) of a k-plane operand, box (one 128-byte
+// K-block row, box_rows, 1): bf16 (64 elements) or, with fp8, e4m3 bytes
+// (128 elements).
 int make_plane_map(CUtensorMap *map, const void *base, int64_t K, int64_t rows, int64_t ld,
-                   int64_t plane_stride, uint32_t planes, uint32_t box_rows) {
+                   int64_t plane_stride, uint32_t planes, uint32_t box_rows, bool fp8 = false) {
     EncodeTiledFn enc = get_encode_fn();
     if (!enc) return set_error(QADIC_E_CUDA, "cuTensorMapEncodeTiled unavailable");
+    const int64_t esz = fp8 ? 1 : 2;
     const cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)planes};
-    const cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)(plane_stride * 2)};
-    const cuuint32_t box[3] = {(cuuint32_t)BK, box_rows, 1};
+    const cuuint64_t strides[2] = {(cuuint64_t)(ld * esz), (cuuint64_t)(plane_stride * esz)};
+    const cuuint32_t box[3] = {(cuuint32_t)(kRowBytes / esz), box_rows, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
-    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims,
+    const CUresult r = enc(map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                           3, const_cast<void *>(base), dims,
                            strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                            kRowBytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -1050,27 +1104,28 @@ int make_plane_map(CUtensorMap *map, const void *base, int64_t K, int64_t rows, 
     return QADIC_OK;
 }
 
-template <int KP, int BN>
+template <int KP, int BN, bool FP8 = false>
 int launch_tc(const Field &f, int64_t m, int64_t n, int64_t K, const void *A, int64_t lda,
               int64_t a_plane, const void *B, int64_t ldb, int64_t b_plane, uint8_t *C,
               int64_t ldc, int64_t c_plane, cudaStream_t stream) {
     using CF = Cfg<KP, BN>;
     CUtensorMap tmA, tmB;
     int st;
-    if ((st = make_plane_map(&tmA, A, K, m, lda, a_plane, KP, BM))) return st;
-    if ((st = make_plane_map(&tmB, B, K, n, ldb, b_plane, KP, BN))) return st;
+    if ((st = make_plane_map(&tmA, A, K, m, lda, a_plane, KP, BM, FP8))) return st;
+    if ((st = make_plane_map(&tmB, B, K, n, ldb, b_plane, KP, BN, FP8))) return st;
+    constexpr int KE = OpT<FP8>::KE;
     TcParams P;
     P.m = m;
     P.n = n;
     P.ldc = ldc;
     P.c_plane = c_plane;
-    P.nkb = (int32_t)((K + BK - 1) / BK);
+    P.nkb = (int32_t)((K + KE - 1) / KE);
     // exact FP32 chunk: a drained residue (|.| <= 1.5p < 2p) plus the growth
     // per K step (k h^2 with shared accumulators, h^2 with split ones) must
     // stay within 2^24
     const int64_t hh = (int64_t)f.h * f.h;
     const int64_t chunk = CF::SPLIT ? ((1ll << 24) - 2 * (int64_t)f.p) / hh : f.k_chunk_f32;
-    P.chunk_kb = (int32_t)std::min<int64_t>(chunk / BK, 1 << 30);
+    P.chunk_kb = (int32_t)std::min<int64_t>(chunk / KE, 1 << 30);
     if (P.chunk_kb < 1) return set_error(QADIC_E_OVERFLOW, "exact FP32 chunk below one K-block");
     P.p = f.p;
     P.m32 = make_mod_small(f.p);
@@ -1080,7 +1135,7 @@ int launch_tc(const Field &f, int64_t m, int64_t n, int64_t K, const void *A, in
     for (uint32_t t = 0; t + 1 < f.k; ++t)
         for (uint32_t i = 0; i < f.k; ++i) P.fold[t * KP + i] = f.fold[t * f.k + i];
     P.status = device_status_word();
-    auto kern = gemm_planes_tc_kernel<KP, BN>;
+    auto kern = gemm_planes_tc_kernel<KP, BN, FP8>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM) !=
         cudaSuccess)
         return set_error(QADIC_E_CUDA, "tc smem attribute: %s", cudaGetErrorString(cudaGetLastError()));
@@ -1111,25 +1166,26 @@ int launch_tc(const Field &f, int64_t m, int64_t n, int64_t K, const void *A, in
 
 // CTA-pair launch: clusters of two CTAs, one pair per two SMs, persistent
 // over 256 x BN units.
-template <int KP, int BN>
+template <int KP, int BN, bool FP8 = false>
 int launch_tc_pair(const Field &f, int64_t m, int64_t n, int64_t K, const void *A, int64_t lda,
                    int64_t a_plane, const void *B, int64_t ldb, int64_t b_plane, uint8_t *C,
                    int64_t ldc, int64_t c_plane, cudaStream_t stream) {
     using CF = PairCfg<KP, BN>;
     CUtensorMap tmA, tmB;
     int st;
-    if ((st = make_plane_map(&tmA, A, K, m, lda, a_plane, KP, BM))) return st;
-    if ((st = make_plane_map(&tmB, B, K, n, ldb, b_plane, KP, CF::BOX))) return st;
+    if ((st = make_plane_map(&tmA, A, K, m, lda, a_plane, KP, BM, FP8))) return st;
+    if ((st = make_plane_map(&tmB, B, K, n, ldb, b_plane, KP, CF::BOX, FP8))) return st;
+    constexpr int KE = OpT<FP8>::KE;
     TcParams P;
     P.m = m;
     P.n = n;
     P.ldc = ldc;
     P.c_plane = c_plane;
-    P.nkb = (int32_t)((K + BK - 1) / BK);
+    P.nkb = (int32_t)((K + KE - 1) / KE);
     // split accumulators: a drained residue (|.| <= 1.5p < 2p) plus h^2 per K step
     const int64_t hh = (int64_t)f.h * f.h;
     const int64_t chunk = ((1ll << 24) - 2 * (int64_t)f.p) / hh;
-    P.chunk_kb = (int32_t)std::min<int64_t>(chunk / BK, 1 << 30);
+    P.chunk_kb = (int32_t)std::min<int64_t>(chunk / KE, 1 << 30);
     if (P.chunk_kb < P.nkb)
         return set_error(QADIC_E_UNSUPPORTED, "pair kernel: K beyond one exact FP32 chunk");
     P.p = f.p;
@@ -1140,7 +1196,7 @@ int launch_tc_pair(const Field &f, int64_t m, int64_t n, int64_t K, const void *
     for (uint32_t t = 0; t + 1 < f.k; ++t)
         for (uint32_t i = 0; i < f.k; ++i) P.fold[t * KP + i] = f.fold[t * f.k + i];
     P.status = device_status_word();
-    auto kern = gemm_planes_pair_kernel<KP, BN>;
+    auto kern = gemm_planes_pair_kernel<KP, BN, FP8>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM) !=
         cudaSuccess)
         return set_error(QADIC_E_CUDA, "pair smem attribute: %s", cudaGetErrorString(cudaGetLastError()));
@@ -1248,10 +1304,15 @@ bool gemm_planes_tc_supported(const Field &f) { return f.k >= 2 && f.k <= 4; }
 int launch_gemm_planes_tc_strided(const Field &f, int64_t m, int64_t n, int64_t K,
                                   const void *A, int64_t lda, int64_t a_plane, const void *B,
                                   int64_t ldb, int64_t b_plane, uint8_t *C, int64_t ldc,
-                                  int64_t c_plane, cudaStream_t stream) {
-    if (lda % 8 || ldb % 8 || a_plane % 8 || b_plane % 8 || ((uintptr_t)A & 15) ||
+                                  int64_t c_plane, cudaStream_t stream, bool fp8) {
+    // TMA: 16-byte aligned bases and row / plane strides of whole 16 bytes
+    const int64_t e16 = fp8 ? 16 : 8;   // elements per 16 bytes
+    if (lda % e16 || ldb % e16 || a_plane % e16 || b_plane % e16 || ((uintptr_t)A & 15) ||
         ((uintptr_t)B & 15))
-        return set_error(QADIC_E_INVALID, "plane operands need ld %% 8 == 0 and 16-byte alignment");
+        return set_error(QADIC_E_INVALID, "plane operands need ld %% %d == 0 and 16-byte alignment",
+                         (int)e16);
+    if (fp8 && f.p > 31)
+        return set_error(QADIC_E_UNSUPPORTED, "e4m3 operands need p <= 31 (|c| <= 15 exact)");
     if (K == 0) {
         for (uint32_t i = 0; i < f.k; ++i)
             if (cudaMemset2DAsync(C + (size_t)i * c_plane, (size_t)ldc, 0, (size_t)n, (size_t)m,
@@ -1259,31 +1320,38 @@ int launch_gemm_planes_tc_strided(const Field &f, int64_t m, int64_t n, int64_t 
                 return set_error(QADIC_E_CUDA, "memset: %s", cudaGetErrorString(cudaGetLastError()));
         return QADIC_OK;
     }
+#define QADIC_TC(KP_, BN_)                                                                            \
+    (fp8 ? launch_tc<KP_, BN_, true>(f, m, n, K, A, lda, a_plane, B, ldb, b_plane, C, ldc, c_plane,    \
+                                     stream)                                                          \
+         : launch_tc<KP_, BN_, false>(f, m, n, K, A, lda, a_plane, B, ldb, b_plane, C, ldc, c_plane,   \
+                                      stream))
     if (f.k == 2) {
         // Two tile rows or more and no in-place reduction on the way through
         // K: CTA pairs on 256-row units.  Where the exact FP32 chunk is
         // shorter than K, both SMs of a pair wait for every reduction, and
         // the one-CTA kernel measured faster (GF(251^2), n = 16384: 21.4 ms
         // against 22.3 ms).
+        const int64_t ke = fp8 ? 128 : 64;   // K elements per K-block
         const int64_t hh = (int64_t)f.h * f.h;
-        const int64_t chunk_kb = ((1ll << 24) - 2 * (int64_t)f.p) / hh / BK;
-        if (m > BM && (K + BK - 1) / BK <= chunk_kb)
-            return launch_tc_pair<2, 128>(f, m, n, K, A, lda, a_plane, B, ldb, b_plane, C, ldc,
-                                          c_plane, stream);
-        return launch_tc<2, 128>(f, m, n, K, A, lda, a_plane, B, ldb, b_plane, C, ldc, c_plane, stream);
+        const int64_t chunk_kb = ((1ll << 24) - 2 * (int64_t)f.p) / hh / ke;
+        if (m > BM && (K + ke - 1) / ke <= chunk_kb)
+            return fp8 ? launch_tc_pair<2, 128, true>(f, m, n, K, A, lda, a_plane, B, ldb, b_plane, C,
+                                                      ldc, c_plane, stream)
+                       : launch_tc_pair<2, 128, false>(f, m, n, K, A, lda, a_plane, B, ldb, b_plane,
+                                                       C, ldc, c_plane, stream);
+        return QADIC_TC(2, 128);
     }
-    if (f.k == 3)
-        return launch_tc<3, 64>(f, m, n, K, A, lda, a_plane, B, ldb, b_plane, C, ldc, c_plane, stream);
-    if (f.k == 4)
-        return launch_tc<4, 64>(f, m, n, K, A, lda, a_plane, B, ldb, b_plane, C, ldc, c_plane, stream);
+    if (f.k == 3) return QADIC_TC(3, 64);
+    if (f.k == 4) return QADIC_TC(4, 64);
+#undef QADIC_TC
     return set_error(QADIC_E_UNSUPPORTED, "no tensor-core plane kernel for k=%u", f.k);
 }
 
 int launch_gemm_planes_tc(const Field &f, int64_t m, int64_t n, int64_t K, const void *A,
                           int64_t lda, const void *B, int64_t ldb, uint8_t *C, int64_t ldc,
-                          cudaStream_t stream) {
+                          cudaStream_t stream, bool fp8) {
     return launch_gemm_planes_tc_strided(f, m, n, K, A, lda, m * lda, B, ldb, n * ldb, C, ldc,
-                                         m * ldc, stream);
+                                         m * ldc, stream, fp8);
 }
 
 int launch_gemm_fold_tc(const Field &f, int64_t m, int64_t n, int64_t K, const void *A,

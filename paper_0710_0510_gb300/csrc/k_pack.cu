@@ -16,6 +16,7 @@
 // HBM-bound elementwise work; the transposing variant stages 32 x 32 tiles
 // in shared memory so both the reads and the writes are coalesced.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 
@@ -26,7 +27,18 @@ namespace qadic {
 namespace {
 
 enum InKind { IN_LOG8 = 0, IN_LOG16 = 1, IN_U8 = 2, IN_I8 = 3 };
-enum OutKind { OUT_F64 = 0, OUT_OPA = 1, OUT_OPB = 2, OUT_COEFF = 3 };
+enum OutKind { OUT_F64 = 0, OUT_OPA = 1, OUT_OPB = 2, OUT_COEFF = 3, OUT_OPA8 = 4 };
+
+// e4m3 code of a centred coefficient (|c| <= 15 for p <= 31: exact).
+__device__ __forceinline__ uint8_t e4m3_of(int c) {
+    return (uint8_t)__nv_cvt_float_to_fp8((float)c, __NV_SATFINITE, __NV_E4M3);
+}
+
+// Two bf16 small integers (low element first) -> their two e4m3 codes.
+__device__ __forceinline__ uint32_t e4m3x2_of_bf16x2(uint32_t w) {
+    const float2 f = make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+    return (uint32_t)__nv_cvt_float2_to_fp8x2(f, __NV_SATFINITE, __NV_E4M3);
+}
 
 constexpr int kTile = 32;
 constexpr int kSmemTableBytes = 96 * 1024;
@@ -101,6 +113,9 @@ __global__ void __launch_bounds__(256) pack_elementwise(const void *__restrict__
             for (uint32_t i = 0; i < P.k; ++i)
                 ((__nv_bfloat16 *)out)[((int64_t)i * P.rows + r) * P.ld_out + c] =
                     __int2bfloat16_rn(tcen[code * P.k + i]);
+        } else if (OUT == OUT_OPA8) {
+            for (uint32_t i = 0; i < P.k; ++i)
+                ((uint8_t *)out)[((int64_t)i * P.rows + r) * P.ld_out + c] = e4m3_of(tcen[code * P.k + i]);
         } else {
             for (uint32_t i = 0; i < P.k; ++i)
                 ((uint8_t *)out)[((int64_t)i * P.rows + r) * P.ld_out + c] =
@@ -111,6 +126,10 @@ __global__ void __launch_bounds__(256) pack_elementwise(const void *__restrict__
             uint64_t w = 0;
             for (uint32_t i = 0; i < P.k; ++i) w |= (uint64_t)coeff_canon<IN>(in, P, r, c, i) << (P.s * i);
             ((double *)out)[r * P.ld_out + c] = (double)w;   // exact: w < 2^53
+        } else if (OUT == OUT_OPA8) {
+            for (uint32_t i = 0; i < P.k; ++i)
+                ((uint8_t *)out)[((int64_t)i * P.rows + r) * P.ld_out + c] =
+                    e4m3_of(centre(coeff_canon<IN>(in, P, r, c, i), P));
         } else {
             for (uint32_t i = 0; i < P.k; ++i)
                 ((__nv_bfloat16 *)out)[((int64_t)i * P.rows + r) * P.ld_out + c] =
@@ -119,10 +138,11 @@ __global__ void __launch_bounds__(256) pack_elementwise(const void *__restrict__
     }
 }
 
-// Transposed operand (OPERAND_B): out plane i is cols x rows.
-template <int IN>
+// Transposed operand (OPERAND_B, or with OUT8 OPERAND_B_E4M3): out plane i
+// is cols x rows.
+template <int IN, bool OUT8 = false>
 __global__ void __launch_bounds__(kTile * 8) pack_transpose(const void *__restrict__ in,
-                                                           __nv_bfloat16 *__restrict__ out,
+                                                           void *__restrict__ out_v,
                                                            PackParams P) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ int16_t tile[kMaxK][kTile][kTile + 1];
@@ -152,8 +172,11 @@ __global__ void __launch_bounds__(kTile * 8) pack_transpose(const void *__restri
     for (int yy = ty; yy < kTile; yy += 8) {
         const int64_t oc = c0 + yy, orow = r0 + tx;   // output row = input col
         if (oc < P.cols && orow < P.rows)
-            for (uint32_t i = 0; i < P.k; ++i)
-                out[((int64_t)i * P.cols + oc) * P.ld_out + orow] = __int2bfloat16_rn(tile[i][tx][yy]);
+            for (uint32_t i = 0; i < P.k; ++i) {
+                const int64_t o = ((int64_t)i * P.cols + oc) * P.ld_out + orow;
+                if constexpr (OUT8) static_cast<uint8_t *>(out_v)[o] = e4m3_of(tile[i][tx][yy]);
+                else static_cast<__nv_bfloat16 *>(out_v)[o] = __int2bfloat16_rn(tile[i][tx][yy]);
+            }
     }
 }
 
@@ -361,10 +384,12 @@ __global__ void __launch_bounds__(256) pack_vec_a(const uint8_t *__restrict__ in
 // thread for two planes of all RT tiles are issued together, then each tile
 // and plane goes through the shared-memory transpose and leaves as 16-byte
 // stores along the output rows.
-template <int IN, int RT>
-__device__ __forceinline__ void vec_b_body(const uint8_t *__restrict__ in,
-                                           __nv_bfloat16 *__restrict__ out, const PackParams &P,
-                                           int64_t bx, int64_t by, uint16_t (*tile)[64 + 2]) {
+template <int IN, int RT, bool OUT8 = false>
+__device__ __forceinline__ void vec_b_body(const uint8_t *__restrict__ in, void *__restrict__ out_v,
+                                           const PackParams &P, int64_t bx, int64_t by,
+                                           uint16_t (*tile)[64 + 2]) {
+    __nv_bfloat16 *out = static_cast<__nv_bfloat16 *>(out_v);
+    uint8_t *out8 = static_cast<uint8_t *>(out_v);
     const int64_t c0 = bx * 64;
     const int rr = threadIdx.x / 4, cc = (threadIdx.x % 4) * 16;
     // planes in groups of two: the loads of a group are in flight together
@@ -407,7 +432,18 @@ __device__ __forceinline__ void vec_b_body(const uint8_t *__restrict__ in,
                     for (int q = 0; q < 4; ++q)
                         v[q] = (uint32_t)tile[ch + 2 * q][oc] | ((uint32_t)tile[ch + 2 * q + 1][oc] << 16);
                     const int64_t orow = c0 + oc, ocol = r0 + ch;
-                    if (ocol + 8 <= P.rows) {
+                    if (OUT8) {
+                        // e4m3 codes: 8 bytes per chunk (8-byte aligned: ld_out % 16 == 0)
+                        uint8_t *dst = out8 + ((int64_t)plane * P.cols + orow) * P.ld_out + ocol;
+                        const uint32_t lo = e4m3x2_of_bf16x2(v[0]) | (e4m3x2_of_bf16x2(v[1]) << 16);
+                        const uint32_t hi = e4m3x2_of_bf16x2(v[2]) | (e4m3x2_of_bf16x2(v[3]) << 16);
+                        if (ocol + 8 <= P.rows) {
+                            *reinterpret_cast<uint2 *>(dst) = make_uint2(lo, hi);
+                        } else {
+                            for (int x = 0; x < 8 && ocol + x < P.rows; ++x)
+                                dst[x] = (uint8_t)((x < 4 ? lo : hi) >> (8 * (x % 4)));
+                        }
+                    } else if (ocol + 8 <= P.rows) {
                         *reinterpret_cast<uint4 *>(out + ((int64_t)plane * P.cols + orow) * P.ld_out +
                                                    ocol) = make_uint4(v[0], v[1], v[2], v[3]);
                     } else {
@@ -427,6 +463,36 @@ __global__ void __launch_bounds__(256) pack_vec_b(const uint8_t *__restrict__ in
                                                   __nv_bfloat16 *__restrict__ out, PackParams P) {
     __shared__ uint16_t tile[64][64 + 2];
     vec_b_body<IN, 1>(in, out, P, blockIdx.x, blockIdx.y, tile);
+}
+
+// OPERAND_B_E4M3 from aligned planes: the same 64 x 64 transpose.
+template <int IN>
+__global__ void __launch_bounds__(256) pack_vec_b8(const uint8_t *__restrict__ in,
+                                                   uint8_t *__restrict__ out, PackParams P) {
+    __shared__ uint16_t tile[64][64 + 2];
+    vec_b_body<IN, 1, true>(in, out, P, blockIdx.x, blockIdx.y, tile);
+}
+
+// OPERAND_A_E4M3 from aligned planes: 16 coefficients per thread, one
+// 16-byte load and one 16-byte store of their codes.
+template <int IN>
+__global__ void __launch_bounds__(256) pack_vec_a8(const uint8_t *__restrict__ in,
+                                                   uint8_t *__restrict__ out, PackParams P) {
+    const int64_t per_row = P.cols / 16;
+    const int64_t units = (int64_t)P.k * P.rows * per_row;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < units;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t pr = u / per_row, c16 = u - pr * per_row;   // pr = plane * rows + row
+        const uint4 w = __ldcs(reinterpret_cast<const uint4 *>(in + pr * P.ld_in + c16 * 16));
+        uint32_t o[8];
+        convert16<IN>(w, P, o);
+        uint4 r;
+        r.x = e4m3x2_of_bf16x2(o[0]) | (e4m3x2_of_bf16x2(o[1]) << 16);
+        r.y = e4m3x2_of_bf16x2(o[2]) | (e4m3x2_of_bf16x2(o[3]) << 16);
+        r.z = e4m3x2_of_bf16x2(o[4]) | (e4m3x2_of_bf16x2(o[5]) << 16);
+        r.w = e4m3x2_of_bf16x2(o[6]) | (e4m3x2_of_bf16x2(o[7]) << 16);
+        *reinterpret_cast<uint4 *>(out + pr * P.ld_out + c16 * 16) = r;
+    }
 }
 
 // Both operands of a plane GEMM in one launch: blocks [0, na) convert A
@@ -476,6 +542,36 @@ int dispatch_out(int out_fmt, const void *in, void *out, const PackParams &P0, c
                (P.rows + 63) / 64 <= 65535) {
         const dim3 grid((unsigned)(P.cols / 64), (unsigned)((P.rows + 63) / 64), 1);
         pack_vec_b<IN><<<grid, 256, 0, stream>>>((const uint8_t *)in, (__nv_bfloat16 *)out, P);
+    } else if (out_fmt == QADIC_FMT_OPERAND_A_E4M3 || out_fmt == QADIC_FMT_OPERAND_B_E4M3) {
+        const bool fast = planes_in && P.cols % 16 == 0 && P.ld_in % 16 == 0 &&
+                          ((uintptr_t)in & 15) == 0 && P.ld_out % 16 == 0 && ((uintptr_t)out & 15) == 0;
+        if (out_fmt == QADIC_FMT_OPERAND_A_E4M3 && fast) {
+            int dev = 0, sms = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            const int64_t units = (int64_t)P.k * P.rows * (P.cols / 16);
+            const int64_t blocks = std::min<int64_t>((units + 255) / 256, (int64_t)sms * 8);
+            pack_vec_a8<IN><<<(unsigned)blocks, 256, 0, stream>>>((const uint8_t *)in, (uint8_t *)out, P);
+        } else if (out_fmt == QADIC_FMT_OPERAND_B_E4M3 && fast && P.cols % 64 == 0 &&
+                   (P.rows + 63) / 64 <= 65535) {
+            const dim3 grid((unsigned)(P.cols / 64), (unsigned)((P.rows + 63) / 64), 1);
+            pack_vec_b8<IN><<<grid, 256, 0, stream>>>((const uint8_t *)in, (uint8_t *)out, P);
+        } else if (out_fmt == QADIC_FMT_OPERAND_B_E4M3) {
+            auto kern = pack_transpose<IN, true>;
+            if (smem > 48 * 1024)
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            const dim3 grid((unsigned)((P.cols + kTile - 1) / kTile), (unsigned)((P.rows + kTile - 1) / kTile));
+            if (grid.y > 65535) return set_error(QADIC_E_INVALID, "too many rows for the transpose pack");
+            kern<<<grid, kTile * 8, smem, stream>>>(in, out, P);
+        } else {
+            auto kern = pack_elementwise<IN, OUT_OPA8>;
+            if (smem > 48 * 1024)
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            const int64_t gy = std::min<int64_t>(P.rows, 65535);
+            const int64_t gz = (P.rows + gy - 1) / gy;
+            const dim3 grid((unsigned)((P.cols + 255) / 256), (unsigned)gy, (unsigned)gz);
+            kern<<<grid, 256, smem, stream>>>(in, out, P);
+        }
     } else if (out_fmt == QADIC_FMT_OPERAND_A_KARA || out_fmt == QADIC_FMT_OPERAND_B_KARA) {
         if (P.k != 2) return set_error(QADIC_E_UNSUPPORTED, "Karatsuba operands are for k = 2");
         const dim3 grid((unsigned)((P.cols + kTile - 1) / kTile), (unsigned)((P.rows + kTile - 1) / kTile));
@@ -540,9 +636,11 @@ int launch_pack(const Field &f, int in_fmt, const void *in, int64_t rows, int64_
     for (uint32_t t = 0; t < f.k; ++t) P.xpow[t][t] = 1;
     for (uint32_t t = 0; t + 1 < f.k; ++t)
         for (uint32_t j = 0; j < f.k; ++j) P.xpow[f.k + t][j] = f.fold[t * f.k + j];
-    if (out_fmt < QADIC_FMT_COEFF_U8 || out_fmt > QADIC_FMT_OPERAND_B_KARA ||
+    if (out_fmt < QADIC_FMT_COEFF_U8 || out_fmt > QADIC_FMT_OPERAND_B_E4M3 ||
         out_fmt == QADIC_FMT_INT8_PLANES)
         return set_error(QADIC_E_INVALID, "unsupported output format %d", out_fmt);
+    if ((out_fmt == QADIC_FMT_OPERAND_A_E4M3 || out_fmt == QADIC_FMT_OPERAND_B_E4M3) && f.p > 31)
+        return set_error(QADIC_E_UNSUPPORTED, "e4m3 operands need p <= 31 (|c| <= 15 exact)");
     switch (in_fmt) {
         case QADIC_FMT_LOG:
             return f.order <= 256 ? dispatch_out<IN_LOG8>(out_fmt, in, out, P, stream)

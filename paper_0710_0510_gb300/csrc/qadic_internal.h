@@ -95,14 +95,14 @@ int launch_gemm_f64(const Field &f, int64_t m, int64_t n, int64_t K, const doubl
 
 int launch_gemm_planes_tc(const Field &f, int64_t m, int64_t n, int64_t K, const void *A,
                           int64_t lda, const void *B, int64_t ldb, uint8_t *C, int64_t ldc,
-                          cudaStream_t stream);
+                          cudaStream_t stream, bool fp8 = false);
 
 // Same, with explicit element strides between the k planes of A, B and C
 // (row ranges of k-plane matrices).
 int launch_gemm_planes_tc_strided(const Field &f, int64_t m, int64_t n, int64_t K,
                                   const void *A, int64_t lda, int64_t a_plane, const void *B,
                                   int64_t ldb, int64_t b_plane, uint8_t *C, int64_t ldc,
-                                  int64_t c_plane, cudaStream_t stream);
+                                  int64_t c_plane, cudaStream_t stream, bool fp8 = false);
 
 bool gemm_planes_tc_supported(const Field &f);
 

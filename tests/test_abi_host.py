@@ -242,6 +242,23 @@ def test_fold_format_and_path_constants_match_header():
     assert re.search(r"QADIC_FMT_OPERAND_A_KARA = 7", h) and q.FMT_OPERAND_A_KARA == 7
     assert re.search(r"QADIC_FMT_OPERAND_B_KARA = 8", h) and q.FMT_OPERAND_B_KARA == 8
     assert re.search(r"QADIC_PATH_KARATSUBA = 3", h) and q.PATH_KARATSUBA == 3
+    assert re.search(r"QADIC_FMT_OPERAND_A_E4M3 = 9", h) and q.FMT_OPERAND_A_E4M3 == 9
+    assert re.search(r"QADIC_FMT_OPERAND_B_E4M3 = 10", h) and q.FMT_OPERAND_B_E4M3 == 10
+    assert re.search(r"QADIC_PATH_PLANES_E4M3 = 4", h) and q.PATH_PLANES_E4M3 == 4
+
+
+def test_e4m3_workspace_is_one_byte_per_element_padded_to_16():
+    """Packed e4m3 operands: k planes of m x K16 and n x K16 bytes, each
+    block 256-byte aligned; half the bf16 planes' bytes when K % 16 == 0."""
+    f = q.Field(31, 2, host_only=True)
+    L = q.lib()
+    a256 = lambda x: (x + 255) // 256 * 256
+    for m, n, K in ((64, 64, 64), (7, 9, 17), (300, 200, 333)):
+        K16 = (K + 15) // 16 * 16
+        want = a256(2 * m * K16) + a256(2 * n * K16)
+        assert L.qadic_matmul_device_workspace_size(f.handle, q.PATH_PLANES_E4M3, m, n, K) == want
+    assert L.qadic_matmul_device_workspace_size(f.handle, q.PATH_PLANES_E4M3, 128, 128, 128) * 2 == \
+        L.qadic_matmul_device_workspace_size(f.handle, q.PATH_PLANES, 128, 128, 128)
 
 
 def test_selftest_rejects_bad_poll_counts():

@@ -101,8 +101,8 @@ def test_plane_kernel_label_follows_the_dispatch_rule():
     """The roofline names the kernel that runs: CTA pairs for GF(101^2) at
     n = 4096 (K = 4096 within one exact chunk of 6656), one CTA per tile for
     GF(251^2) at n = 16384 (chunk of 1073 K elements) and for one tile row."""
-    assert bench.plane_kernel(101, 4096) == "gemm_planes_pair_kernel<2,128>"
-    assert bench.plane_kernel(251, 16384) == "gemm_planes_tc_kernel<2,128>"
-    assert bench.plane_kernel(101, 128) == "gemm_planes_tc_kernel<2,128>"
-    assert bench.plane_kernel(101, 6656) == "gemm_planes_pair_kernel<2,128>"
-    assert bench.plane_kernel(101, 6657) == "gemm_planes_tc_kernel<2,128>"
+    assert bench.plane_kernel(101, 4096) == "gemm_planes_pair_kernel<2,128,false>"
+    assert bench.plane_kernel(251, 16384) == "gemm_planes_tc_kernel<2,128,false>"
+    assert bench.plane_kernel(101, 128) == "gemm_planes_tc_kernel<2,128,false>"
+    assert bench.plane_kernel(101, 6656) == "gemm_planes_pair_kernel<2,128,false>"
+    assert bench.plane_kernel(101, 6657) == "gemm_planes_tc_kernel<2,128,false>"
