@@ -395,3 +395,55 @@ def test_batched_unreduced_bytes(torch, orc, converted):
     q.sync_status()
     for i in range(len(shapes)):
         assert np.array_equal(bt.result(i), bt.expected(orc, i)), (i, shapes[i])
+
+
+@pytest.mark.parametrize("converted", [True, False])
+def test_batched_strided_unaligned_operands(torch, orc, converted):
+    """Row strides above the widths (odd ones among them) and operand bases
+    at every offset mod 4: the conversion's word loads of B columns (one or
+    two aligned words per K row, four columns per thread) and the ragged
+    last column group, on both paths."""
+    fields = mixed_fields()
+    shapes = [(70, 97, 64), (33, 130, 48), (128, 61, 100), (5, 257, 17), (64, 66, 64),
+              (90, 3, 40), (17, 1, 33), (129, 255, 255)]
+    fidx = [0, 1, 2, 0, 1, 2, 0, 1]
+    pads = [(3, 5), (1, 0), (0, 7), (2, 2), (5, 1), (0, 13), (1, 3), (4, 9)]
+    rng = np.random.default_rng(31)
+    As, Bs, descs, offs = [], [], [], []
+    ra = rb = rc = 0
+    layout = []
+    for (m, n, K), fi, (pa, pb) in zip(shapes, fidx, pads):
+        f = fields[fi]
+        lda, ldb = K + pa, n + pb
+        ra += 1 + (ra % 3)     # bases at varied offsets mod 4
+        rb += 1 + (rb % 3)
+        layout.append((ra, rb, rc, lda, ldb))
+        ra += f.k * m * lda
+        rb += f.k * K * ldb
+        rc += f.k * m * n
+        As.append(rng.integers(0, f.p, (f.k, m, K), dtype=np.uint8))
+        Bs.append(rng.integers(0, f.p, (f.k, K, n), dtype=np.uint8))
+    hA = np.full(ra + 64, 0xEE, np.uint8)
+    hB = np.full(rb + 64, 0xEE, np.uint8)
+    for (m, n, K), fi, A, B, (oa, ob, oc, lda, ldb) in zip(shapes, fidx, As, Bs, layout):
+        f = fields[fi]
+        va = hA[oa:oa + f.k * m * lda].reshape(f.k, m, lda)
+        va[:, :, :K] = A
+        vb = hB[ob:ob + f.k * K * ldb].reshape(f.k, K, ldb)
+        vb[:, :, :n] = B
+    dA = torch.from_numpy(hA).cuda()
+    dB = torch.from_numpy(hB).cuda()
+    dC = torch.zeros(rc, dtype=torch.uint8, device="cuda")
+    for (m, n, K), fi, (oa, ob, oc, lda, ldb) in zip(shapes, fidx, layout):
+        descs.append(q.GemmDesc(fi, m, n, K, dA.data_ptr() + oa, dB.data_ptr() + ob,
+                                dC.data_ptr() + oc, lda, ldb, n, 0))
+    ws = torch.empty(q.batched_workspace_size(descs, fields if converted else None),
+                     dtype=torch.uint8, device="cuda")
+    q.batched_gemm(fields, descs, ws)
+    torch.cuda.synchronize()
+    q.sync_status()
+    for (m, n, K), fi, A, B, (oa, ob, oc, lda, ldb) in zip(shapes, fidx, As, Bs, layout):
+        f = fields[fi]
+        got = dC[oc:oc + f.k * m * n].cpu().numpy().reshape(f.k, m, n)
+        want = orc.gemm(f.p, f.poly, np.transpose(A, (1, 2, 0)), np.transpose(B, (1, 2, 0)))
+        assert np.array_equal(got, np.transpose(want, (2, 0, 1))), (m, n, K, fi)
