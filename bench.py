@@ -449,16 +449,23 @@ def bench_karatsuba(args, torch, q, W, f, A, B, n, C_plane, steps=20):
                          "flop_count": "3 plane products (2 * 3 * n^3)"}}
 
 
+def make_e4m3_inputs(q, W, p=31, n=4096):
+    """GF(p^2) field and the two n x n operands (int8 centred planes) of the
+    e4m3 comparison."""
+    k, h = 2, (p - 1) // 2
+    return (q.Field(p, k), W.centred_planes(k, n, n, h, index=2, salt=31),
+            W.centred_planes(k, n, n, h, index=2, salt=32))
+
+
 def bench_e4m3(args, torch, q, W, p=31, n=4096, steps=20):
     """GF(p^2) with p <= 31 on both plane paths, same inputs: the bf16 plane
     path (one-launch pack + kind::f16 GEMM) and the e4m3 one (two pack
     launches + kind::f8f6f4 GEMM, half the operand bytes, twice the tensor
     rate); bit-exact against each other."""
     k = 2
-    h = (p - 1) // 2
-    f = q.Field(p, k)
-    dA = torch.from_numpy(W.centred_planes(k, n, n, h, index=2, salt=31)).cuda()
-    dB = torch.from_numpy(W.centred_planes(k, n, n, h, index=2, salt=32)).cuda()
+    f, A, B = make_e4m3_inputs(q, W, p, n)
+    dA = torch.from_numpy(A).cuda()
+    dB = torch.from_numpy(B).cuda()
     stream = torch.cuda.current_stream()
     out = {}
     Cs = {}

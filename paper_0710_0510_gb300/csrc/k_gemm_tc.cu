@@ -324,6 +324,7 @@ gemm_planes_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_cons
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    ptx::griddep_wait();   // the set-up above overlaps the previous kernel's tail
 
     auto a_tile = [&](int stage, int i) { return smem + stage * CF::STAGE + i * CF::A_TILE; };
     auto b_tile = [&](int stage, int j) {
@@ -579,6 +580,7 @@ gemm_planes_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_co
     ptx::cluster_sync();   // both CTAs' barriers and tensor memory exist before any remote use
     ptx::tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    ptx::griddep_wait();   // the set-up above overlaps the previous kernel's tail
 
     auto in_leader = [&](const void *x) { return ptx::mapa(ptx::smem_addr(x), 0); };
     auto in_peer = [&](const void *x) { return ptx::mapa(ptx::smem_addr(x), peer); };
@@ -1150,6 +1152,11 @@ int launch_tc(const Field &f, int64_t m, int64_t n, int64_t K, const void *A, in
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = CF::SMEM;
     cfg.stream = stream;
@@ -1211,13 +1218,15 @@ int launch_tc_pair(const Field &f, int64_t m, int64_t n, int64_t K, const void *
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 2;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 1;   // the cluster shape alone for the occupancy query
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = CF::SMEM;
     cfg.stream = stream;
@@ -1230,6 +1239,7 @@ int launch_tc_pair(const Field &f, int64_t m, int64_t n, int64_t K, const void *
         cudaGetLastError();
     pairs = (int)std::min<int64_t>(P.nunits, pairs);
     cfg.gridDim = dim3((unsigned)(2 * pairs));
+    cfg.numAttrs = 2;   // and the launch may overlap the previous kernel's tail
     const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, tmA, tmB, C, P);
     if (e != cudaSuccess) {
         cudaGetLastError();

@@ -21,6 +21,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "tc_ptx.cuh"
 
 namespace qadic {
 
@@ -506,6 +507,7 @@ __global__ void __launch_bounds__(256) pack_vec_ab(const uint8_t *__restrict__ a
                                                    __nv_bfloat16 *__restrict__ ob, PackParams PB,
                                                    int64_t na) {
     __shared__ uint16_t tile[64][64 + 2];
+    ptx::griddep_wait();   // launched to overlap the previous kernel's tail
     if ((int64_t)blockIdx.x < na) {
         vec_a_body<IN>(a, oa, PA, blockIdx.x, na);
     } else {
@@ -707,16 +709,28 @@ int launch_pack_pair(const Field &f, int in_fmt, const void *A, int64_t m, int64
     const int64_t nb = (int64_t)(n / 64) * ((K + 127) / 128);
     const int64_t na = std::max<int64_t>(1, std::min<int64_t>((units_a + 1023) / 1024, (int64_t)sms * 8));
     if (na + nb > 0x7fffffff) return set_error(QADIC_E_INVALID, "too many pack blocks");
-    if (in_fmt == QADIC_FMT_INT8_PLANES)
-        pack_vec_ab<IN_I8><<<(unsigned)(na + nb), 256, 0, stream>>>(
-            (const uint8_t *)A, (__nv_bfloat16 *)outA, PA, (const uint8_t *)B,
-            (__nv_bfloat16 *)outB, PB, na);
-    else
-        pack_vec_ab<IN_U8><<<(unsigned)(na + nb), 256, 0, stream>>>(
-            (const uint8_t *)A, (__nv_bfloat16 *)outA, PA, (const uint8_t *)B,
-            (__nv_bfloat16 *)outB, PB, na);
-    const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return set_error(QADIC_E_CUDA, "pack launch: %s", cudaGetErrorString(e));
+    // programmatic stream serialization: the launch may begin while the
+    // previous kernel of the stream finishes (the kernel waits for it before
+    // touching memory)
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3((unsigned)(na + nb));
+    cfg.blockDim = dim3(256);
+    cfg.stream = stream;
+    const cudaError_t e =
+        in_fmt == QADIC_FMT_INT8_PLANES
+            ? cudaLaunchKernelEx(&cfg, pack_vec_ab<IN_I8>, (const uint8_t *)A, (__nv_bfloat16 *)outA,
+                                 PA, (const uint8_t *)B, (__nv_bfloat16 *)outB, PB, na)
+            : cudaLaunchKernelEx(&cfg, pack_vec_ab<IN_U8>, (const uint8_t *)A, (__nv_bfloat16 *)outA,
+                                 PA, (const uint8_t *)B, (__nv_bfloat16 *)outB, PB, na);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(QADIC_E_CUDA, "pack launch: %s", cudaGetErrorString(e));
+    }
     return QADIC_OK;
 }
 

@@ -75,6 +75,42 @@ def test_plane_gf101_2_n4096_and_fp64_form(torch, orc):
     torch.cuda.empty_cache()
 
 
+def test_plane_e4m3_gf31_2_n4096(torch, orc):
+    """The e4m3 comparison workload as bench.py times it (two e4m3 packs +
+    the kind::f8f6f4 plane GEMM, GF(31^2), n = 4096): 4096 sampled entries,
+    two whole rows (a leader CTA's and a peer's half of a 256-row unit) and
+    two whole columns against the oracle, every entry against the bf16 plane
+    path on the same inputs, and one Freivalds vector."""
+    n = 4096
+    f, A, B = bench.make_e4m3_inputs(q, W, 31, n)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    a8 = f.pack(q.FMT_INT8_PLANES, dA, n, n, q.FMT_OPERAND_A_E4M3)
+    b8 = f.pack(q.FMT_INT8_PLANES, dB, n, n, q.FMT_OPERAND_B_E4M3)
+    C8 = f.gemm(q.PATH_PLANES_E4M3, a8, b8, n, n, n)
+    a16 = torch.empty((2, n, n), dtype=torch.bfloat16, device="cuda")
+    b16 = torch.empty((2, n, n), dtype=torch.bfloat16, device="cuda")
+    f.pack_operands(q.FMT_INT8_PLANES, dA, dB, n, n, n, a16, b16)
+    C16 = f.gemm(q.PATH_PLANES, a16, b16, n, n, n)
+    torch.cuda.synchronize()
+    q.sync_status()
+    assert torch.equal(C8, C16)
+    Ch = C8.cpu().numpy()
+    rng = np.random.default_rng(77)
+    ii = rng.integers(0, n, 4096)
+    jj = rng.integers(0, n, 4096)
+    assert sampled_entries_agree(orc, f, A, B, Ch, ii, jj)
+    Am, Bm = planes_to_mkk(A), planes_to_mkk(B)
+    for r in (5, 128 + 77):
+        want = orc.gemm(f.p, f.poly, Am[r:r + 1], Bm)
+        assert np.array_equal(planes_to_mkk(Ch[:, r:r + 1, :]), want), r
+    for c in (0, n - 1):
+        want = orc.gemm(f.p, f.poly, Am, Bm[:, c:c + 1])
+        assert np.array_equal(planes_to_mkk(Ch[:, :, c:c + 1]), want), c
+    assert freivalds(orc, f, Am % f.p, Bm % f.p, planes_to_mkk(Ch), vectors=1, seed=5)
+    del a8, b8, C8, a16, b16, C16
+    torch.cuda.empty_cache()
+
+
 def test_plane_gf251_2_n16384(torch, orc):
     """The n = 16384 GF(251^2) product: 4096 sampled entries, two whole rows
     (one in a leader CTA's half of a 256-row unit, one in a peer's) and two
