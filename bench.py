@@ -52,14 +52,13 @@ PLANE_KERNEL = "gemm_planes_pair_kernel<2,128,false>"
 MEASURED_TRAFFIC = {
     PLANE_KERNEL: {
         "file": "paper_0710_0510_gb300/csrc/k_gemm_tc.cu",
-        "code_sha256": "12cbc6ee979769f4b0f115a28ca3ac34291e9d1a2dec379642ca84213096d298",
-        "bytes": 431406080 + 30127616, "n": 4096},
+        "code_sha256": "a7b0456e9cf491ed560a2a76356ba13dfd97780ae7206f98b3cbd1498f7f999e",
+        "bytes": 460768256 + 30390528, "n": 4096},
     "gemm_planes_pair_kernel<2,128,true>": {
         "file": "paper_0710_0510_gb300/csrc/k_gemm_tc.cu",
-        "code_sha256": "12cbc6ee979769f4b0f115a28ca3ac34291e9d1a2dec379642ca84213096d298",
-        "bytes": 68489984 + 16238336, "n": 4096},
+        "code_sha256": "a7b0456e9cf491ed560a2a76356ba13dfd97780ae7206f98b3cbd1498f7f999e",
+        "bytes": 68392448 + 12731392, "n": 4096},
 }
-
 
 def plane_kernel(p, n):
     """Name of the kernel the k = 2 plane GEMM dispatches to for an n x n x n

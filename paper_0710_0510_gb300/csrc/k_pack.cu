@@ -471,6 +471,7 @@ template <int IN>
 __global__ void __launch_bounds__(256) pack_vec_b8(const uint8_t *__restrict__ in,
                                                    uint8_t *__restrict__ out, PackParams P) {
     __shared__ uint16_t tile[64][64 + 2];
+    ptx::griddep_wait();   // launched to overlap the previous kernel's tail
     vec_b_body<IN, 1, true>(in, out, P, blockIdx.x, blockIdx.y, tile);
 }
 
@@ -481,6 +482,7 @@ __global__ void __launch_bounds__(256) pack_vec_a8(const uint8_t *__restrict__ i
                                                    uint8_t *__restrict__ out, PackParams P) {
     const int64_t per_row = P.cols / 16;
     const int64_t units = (int64_t)P.k * P.rows * per_row;
+    ptx::griddep_wait();   // launched to overlap the previous kernel's tail
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < units;
          u += (int64_t)gridDim.x * blockDim.x) {
         const int64_t pr = u / per_row, c16 = u - pr * per_row;   // pr = plane * rows + row
@@ -515,6 +517,23 @@ __global__ void __launch_bounds__(256) pack_vec_ab(const uint8_t *__restrict__ a
         const int64_t nbx = PB.cols / 64;
         vec_b_body<IN, 2>(b, ob, PB, t % nbx, t / nbx, tile);
     }
+}
+
+// A 256-thread launch with programmatic stream serialization: it may begin
+// while the previous kernel of the stream finishes (the kernel waits for it
+// before touching memory).
+template <class... Args>
+cudaError_t launch_pdl(void (*kern)(Args...), dim3 grid, cudaStream_t stream, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(256);
+    cfg.stream = stream;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
 template <int IN>
@@ -553,11 +572,12 @@ int dispatch_out(int out_fmt, const void *in, void *out, const PackParams &P0, c
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
             const int64_t units = (int64_t)P.k * P.rows * (P.cols / 16);
             const int64_t blocks = std::min<int64_t>((units + 255) / 256, (int64_t)sms * 8);
-            pack_vec_a8<IN><<<(unsigned)blocks, 256, 0, stream>>>((const uint8_t *)in, (uint8_t *)out, P);
+            e = launch_pdl(pack_vec_a8<IN>, dim3((unsigned)blocks), stream, (const uint8_t *)in,
+                           (uint8_t *)out, P);
         } else if (out_fmt == QADIC_FMT_OPERAND_B_E4M3 && fast && P.cols % 64 == 0 &&
                    (P.rows + 63) / 64 <= 65535) {
             const dim3 grid((unsigned)(P.cols / 64), (unsigned)((P.rows + 63) / 64), 1);
-            pack_vec_b8<IN><<<grid, 256, 0, stream>>>((const uint8_t *)in, (uint8_t *)out, P);
+            e = launch_pdl(pack_vec_b8<IN>, grid, stream, (const uint8_t *)in, (uint8_t *)out, P);
         } else if (out_fmt == QADIC_FMT_OPERAND_B_E4M3) {
             auto kern = pack_transpose<IN, true>;
             if (smem > 48 * 1024)
@@ -607,7 +627,8 @@ int dispatch_out(int out_fmt, const void *in, void *out, const PackParams &P0, c
         const dim3 grid((unsigned)((P.cols + 255) / 256), (unsigned)gy, (unsigned)gz);
         kern<<<grid, 256, smem, stream>>>(in, out, P);
     }
-    e = cudaGetLastError();
+    const cudaError_t le = cudaGetLastError();   // clears a launch error either way
+    if (e == cudaSuccess) e = le;
     if (e != cudaSuccess) return set_error(QADIC_E_CUDA, "pack launch: %s", cudaGetErrorString(e));
     return QADIC_OK;
 }
