@@ -433,8 +433,7 @@ int qadic_batched_autotune(const qadic_field *const *fields, int32_t nfields,
  *   host memory is allocated and no allocating routine is called.  Every
  *   device that loads the library holds that array until the process exits.
  *   The first call on a device does the set-up: it looks up the array's
- *   device address and creates one event (no memory allocation); make that
- *   first call before capturing a stream into a CUDA graph.
+ *   device address and creates one event (no memory allocation).
  *   All calls share the one array and each call rewrites it from the start
  *   (the tile counter included), so calls whose kernels overlap on the GPU
  *   race: order them on one stream, or synchronise in between.  A call
