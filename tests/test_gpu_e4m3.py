@@ -171,3 +171,64 @@ def test_gemm_e4m3_refuses_misaligned_and_large_p(torch):
     with pytest.raises(q.QadicError) as e:
         g.gemm(q.PATH_PLANES_E4M3, b, b, 64, 64, 64)
     assert e.value.status == q.E_UNSUPPORTED
+
+
+@pytest.mark.parametrize("path", [q.PATH_PLANES, q.PATH_PLANES_E4M3])
+def test_chained_packs_and_gemms_share_operand_buffers(torch, path):
+    """Packs and GEMMs launched back to back on one stream with no host
+    synchronisation, two input sets alternating through the same operand
+    buffers: each launch may begin while the previous one finishes
+    (programmatic dependent launch), so a pack that overwrote operands still
+    being read, or a GEMM that read operands not yet written, would change
+    some product.  Every product equals the one computed in isolation."""
+    p, k, n = 31, 2, 2048
+    f = q.Field(p, k)
+    X = [(dev(torch, W.centred_planes(k, n, n, 15, salt=40 + 2 * i)),
+          dev(torch, W.centred_planes(k, n, n, 15, salt=41 + 2 * i))) for i in range(2)]
+    e4 = path == q.PATH_PLANES_E4M3
+    dt = torch.uint8 if e4 else torch.bfloat16
+    opA = torch.empty((k, n, n), dtype=dt, device="cuda")
+    opB = torch.empty((k, n, n), dtype=dt, device="cuda")
+
+    def product(i, C):
+        a, b = X[i]
+        if e4:
+            f.pack(q.FMT_INT8_PLANES, a, n, n, q.FMT_OPERAND_A_E4M3, out=opA)
+            f.pack(q.FMT_INT8_PLANES, b, n, n, q.FMT_OPERAND_B_E4M3, out=opB)
+        else:
+            f.pack_operands(q.FMT_INT8_PLANES, a, b, n, n, n, opA, opB)
+        return f.gemm(path, opA, opB, n, n, n, C=C)
+
+    want = []
+    for i in range(2):
+        want.append(product(i, torch.empty((k, n, n), dtype=torch.uint8, device="cuda")))
+        torch.cuda.synchronize()
+    assert not torch.equal(want[0], want[1])
+    outs = [torch.empty((k, n, n), dtype=torch.uint8, device="cuda") for _ in range(12)]
+    for j, C in enumerate(outs):
+        product(j % 2, C)
+    torch.cuda.synchronize()
+    q.sync_status()
+    for j, C in enumerate(outs):
+        assert torch.equal(C, want[j % 2]), j
+
+
+def test_matmul_device_e4m3_strided_inputs(torch, orc):
+    """qadic_matmul on e4m3 with input rows longer than the widths (odd
+    strides, each plane rows x ld elements) against the oracle."""
+    p, k, m, n, K = 31, 2, 200, 150, 270
+    f = q.Field(p, k)
+    lda, ldb = K + 5, n + 3
+    A = W.centred_planes(k, m, K, 15, salt=61)
+    B = W.centred_planes(k, K, n, 15, salt=62)
+    Ap = np.full((k, m, lda), 99, np.int8)
+    Bp = np.full((k, K, ldb), -99, np.int8)
+    Ap[:, :, :K] = A
+    Bp[:, :, :n] = B
+    ws = torch.empty(max(f.matmul_device_workspace_size(q.PATH_PLANES_E4M3, m, n, K), 256),
+                     dtype=torch.uint8, device="cuda")
+    C = f.matmul(q.PATH_PLANES_E4M3, q.FMT_INT8_PLANES, dev(torch, Ap), dev(torch, Bp), m, n, K, ws,
+                 lda=lda, ldb=ldb)
+    torch.cuda.synchronize()
+    q.sync_status()
+    assert np.array_equal(C.cpu().numpy(), oracle_planes(orc, p, f.poly, A, B))
