@@ -232,6 +232,14 @@ int qadic_pack_operands(const qadic_field *field, int in_fmt, const void *A, int
                         int64_t lda_in, void *outA, int64_t lda_out, const void *B, int64_t n,
                         int64_t ldb_in, void *outB, int64_t ldb_out, void *stream);
 
+/* The same for the e4m3 plane path (p <= 31, else QADIC_E_UNSUPPORTED):
+ * A -> OPERAND_A_E4M3 and B -> OPERAND_B_E4M3, one launch under the same
+ * conditions; lda_out, ldb_out >= K, multiples of 16; 16-byte aligned
+ * outputs. */
+int qadic_pack_operands_e4m3(const qadic_field *field, int in_fmt, const void *A, int64_t m,
+                             int64_t K, int64_t lda_in, void *outA, int64_t lda_out, const void *B,
+                             int64_t n, int64_t ldb_in, void *outB, int64_t ldb_out, void *stream);
+
 /* ----------------------------------------------------------------- matmul --
  * The whole path on device operands in one call: A (m x K) and B (K x n) in
  * in_fmt (LOG, COEFF_U8 or INT8_PLANES; lda, ldb element strides per row,

@@ -94,6 +94,11 @@ _SIGS = {
                                            ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                            ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
                                            ctypes.c_int64, ctypes.c_void_p]),
+    "qadic_pack_operands_e4m3": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                                ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                                ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                                ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
+                                                ctypes.c_int64, ctypes.c_void_p]),
     "qadic_matmul_device_workspace_size": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int,
                                                              ctypes.c_int64, ctypes.c_int64,
                                                              ctypes.c_int64]),
@@ -296,9 +301,12 @@ class Field:
         return C
 
     def pack_operands(self, in_fmt: int, A, B, m: int, n: int, K: int, outA, outB,
-                      lda_in=None, ldb_in=None, lda_out=None, ldb_out=None, stream=None):
-        """A -> OPERAND_A and B -> OPERAND_B in one call (``qadic_pack_operands``)."""
-        _check(lib().qadic_pack_operands(
+                      lda_in=None, ldb_in=None, lda_out=None, ldb_out=None, stream=None,
+                      e4m3: bool = False):
+        """A -> OPERAND_A and B -> OPERAND_B in one call (``qadic_pack_operands``);
+        with e4m3, the E4M3 operand formats (``qadic_pack_operands_e4m3``)."""
+        fn = lib().qadic_pack_operands_e4m3 if e4m3 else lib().qadic_pack_operands
+        _check(fn(
             self._h, in_fmt, _ptr(A), m, K, K if lda_in is None else lda_in, _ptr(outA),
             outA.shape[-1] if lda_out is None else lda_out, _ptr(B), n,
             n if ldb_in is None else ldb_in, _ptr(outB),

@@ -348,28 +348,49 @@ static size_t packed_bytes(const Field &f, int path, int64_t m, int64_t n, int64
     return align256_(a) + align256_(b);
 }
 
-int qadic_pack_operands(const qadic_field *field, int in_fmt, const void *A, int64_t m, int64_t K,
-                        int64_t lda_in, void *outA, int64_t lda_out, const void *B, int64_t n,
-                        int64_t ldb_in, void *outB, int64_t ldb_out, void *stream) {
+// Both operands in one call; e4m3 selects the fp8 operand formats.
+static int pack_operands(const qadic_field *field, int in_fmt, const void *A, int64_t m, int64_t K,
+                         int64_t lda_in, void *outA, int64_t lda_out, const void *B, int64_t n,
+                         int64_t ldb_in, void *outB, int64_t ldb_out, void *stream, bool e4m3) {
     if (!field) return set_error(QADIC_E_INVALID, "field is NULL");
     const Field &f = field->f;
     if (!on_device(f)) return set_error(QADIC_E_INVALID, "field lives on another device");
     if (m < 0 || n < 0 || K < 0) return set_error(QADIC_E_INVALID, "negative size");
+    if (e4m3 && f.p > 31)
+        return set_error(QADIC_E_UNSUPPORTED, "e4m3 operands need p <= 31 (|c| <= 15 exact)");
     if (m == 0 || n == 0 || K == 0) return QADIC_OK;
     if (!A || !B || !outA || !outB) return set_error(QADIC_E_INVALID, "NULL data pointer");
     if (lda_in < K || ldb_in < n) return set_error(QADIC_E_INVALID, "ld_in too small");
-    if (lda_out < K || ldb_out < K || lda_out % 8 || ldb_out % 8 || ((uintptr_t)outA & 15) ||
+    const int64_t lo = e4m3 ? 16 : 8;
+    if (lda_out < K || ldb_out < K || lda_out % lo || ldb_out % lo || ((uintptr_t)outA & 15) ||
         ((uintptr_t)outB & 15))
-        return set_error(QADIC_E_INVALID, "operand outputs need ld >= K, ld %% 8 == 0, 16B alignment");
+        return set_error(QADIC_E_INVALID, "operand outputs need ld >= K, ld %% %d == 0, 16B alignment",
+                         (int)lo);
+    const int fa = e4m3 ? QADIC_FMT_OPERAND_A_E4M3 : QADIC_FMT_OPERAND_A;
+    const int fb = e4m3 ? QADIC_FMT_OPERAND_B_E4M3 : QADIC_FMT_OPERAND_B;
     if (in_fmt == QADIC_FMT_LOG) {
-        int st = qadic_pack(field, in_fmt, A, m, K, lda_in, QADIC_FMT_OPERAND_A, outA, lda_out, stream);
+        int st = qadic_pack(field, in_fmt, A, m, K, lda_in, fa, outA, lda_out, stream);
         if (st != QADIC_OK) return st;
-        return qadic_pack(field, in_fmt, B, K, n, ldb_in, QADIC_FMT_OPERAND_B, outB, ldb_out, stream);
+        return qadic_pack(field, in_fmt, B, K, n, ldb_in, fb, outB, ldb_out, stream);
     }
     if (in_fmt != QADIC_FMT_COEFF_U8 && in_fmt != QADIC_FMT_INT8_PLANES)
         return set_error(QADIC_E_INVALID, "input format %d", in_fmt);
     return launch_pack_pair(f, in_fmt, A, m, K, lda_in, outA, lda_out, B, n, ldb_in, outB, ldb_out,
-                            (cudaStream_t)stream);
+                            (cudaStream_t)stream, e4m3);
+}
+
+int qadic_pack_operands(const qadic_field *field, int in_fmt, const void *A, int64_t m, int64_t K,
+                        int64_t lda_in, void *outA, int64_t lda_out, const void *B, int64_t n,
+                        int64_t ldb_in, void *outB, int64_t ldb_out, void *stream) {
+    return pack_operands(field, in_fmt, A, m, K, lda_in, outA, lda_out, B, n, ldb_in, outB, ldb_out,
+                         stream, false);
+}
+
+int qadic_pack_operands_e4m3(const qadic_field *field, int in_fmt, const void *A, int64_t m,
+                             int64_t K, int64_t lda_in, void *outA, int64_t lda_out, const void *B,
+                             int64_t n, int64_t ldb_in, void *outB, int64_t ldb_out, void *stream) {
+    return pack_operands(field, in_fmt, A, m, K, lda_in, outA, lda_out, B, n, ldb_in, outB, ldb_out,
+                         stream, true);
 }
 
 size_t qadic_matmul_device_workspace_size(const qadic_field *field, int path, int64_t m, int64_t n,
@@ -424,13 +445,18 @@ int qadic_matmul(const qadic_field *field, int path, int in_fmt, int64_t m, int6
     int64_t la, lb;
     switch (path) {
         case QADIC_PATH_FP64_QADIC: fa = fb = QADIC_FMT_QADIC_F64; la = K; lb = n; break;
-        case QADIC_PATH_PLANES_E4M3:
+        case QADIC_PATH_PLANES_E4M3: {
+            // both operands by one launch where the inputs allow it
             if (!gemm_planes_tc_supported(f))
                 return set_error(QADIC_E_UNSUPPORTED, "no tensor-core plane kernel for k=%u", f.k);
-            fa = QADIC_FMT_OPERAND_A_E4M3;
-            fb = QADIC_FMT_OPERAND_B_E4M3;
-            la = lb = (K + 15) / 16 * 16;
-            break;
+            if (!A || !B) return set_error(QADIC_E_INVALID, "NULL operand");
+            if (lda < K || ldb < n) return set_error(QADIC_E_INVALID, "lda < K or ldb < n");
+            const int64_t K16 = (K + 15) / 16 * 16;
+            if ((st = qadic_pack_operands_e4m3(field, in_fmt, A, m, K, lda, pA, K16, B, n, ldb, pB,
+                                               K16, stream)))
+                return st;
+            return qadic_gemm(field, path, m, n, K, pA, K16, pB, K16, C, ldc, nullptr, 0, stream);
+        }
         case QADIC_PATH_FOLD: fa = QADIC_FMT_OPERAND_A; fb = QADIC_FMT_OPERAND_B_FOLD; la = lb = K8; break;
         default: fa = QADIC_FMT_OPERAND_A_KARA; fb = QADIC_FMT_OPERAND_B_KARA; la = lb = K8; break;
     }

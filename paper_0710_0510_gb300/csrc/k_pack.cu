@@ -476,15 +476,14 @@ __global__ void __launch_bounds__(256) pack_vec_b8(const uint8_t *__restrict__ i
 }
 
 // OPERAND_A_E4M3 from aligned planes: 16 coefficients per thread, one
-// 16-byte load and one 16-byte store of their codes.
+// 16-byte load and one 16-byte store of their codes; blocks `block` of
+// `nblocks` stride over the units.
 template <int IN>
-__global__ void __launch_bounds__(256) pack_vec_a8(const uint8_t *__restrict__ in,
-                                                   uint8_t *__restrict__ out, PackParams P) {
+__device__ __forceinline__ void vec_a8_body(const uint8_t *__restrict__ in, uint8_t *__restrict__ out,
+                                            const PackParams &P, int64_t block, int64_t nblocks) {
     const int64_t per_row = P.cols / 16;
     const int64_t units = (int64_t)P.k * P.rows * per_row;
-    ptx::griddep_wait();   // launched to overlap the previous kernel's tail
-    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < units;
-         u += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t u = block * blockDim.x + threadIdx.x; u < units; u += nblocks * blockDim.x) {
         const int64_t pr = u / per_row, c16 = u - pr * per_row;   // pr = plane * rows + row
         const uint4 w = __ldcs(reinterpret_cast<const uint4 *>(in + pr * P.ld_in + c16 * 16));
         uint32_t o[8];
@@ -498,24 +497,30 @@ __global__ void __launch_bounds__(256) pack_vec_a8(const uint8_t *__restrict__ i
     }
 }
 
+template <int IN>
+__global__ void __launch_bounds__(256) pack_vec_a8(const uint8_t *__restrict__ in,
+                                                   uint8_t *__restrict__ out, PackParams P) {
+    ptx::griddep_wait();   // launched to overlap the previous kernel's tail
+    vec_a8_body<IN>(in, out, P, blockIdx.x, gridDim.x);
+}
+
 // Both operands of a plane GEMM in one launch: blocks [0, na) convert A
 // (same layout), the others transpose B, two 64 x 64 tiles stacked down K
 // per block -- one ramp-up and one tail instead of two for these short
 // HBM-bound passes.
-template <int IN>
-__global__ void __launch_bounds__(256) pack_vec_ab(const uint8_t *__restrict__ a,
-                                                   __nv_bfloat16 *__restrict__ oa, PackParams PA,
-                                                   const uint8_t *__restrict__ b,
-                                                   __nv_bfloat16 *__restrict__ ob, PackParams PB,
-                                                   int64_t na) {
+template <int IN, bool OUT8>
+__global__ void __launch_bounds__(256) pack_vec_ab(const uint8_t *__restrict__ a, void *__restrict__ oa,
+                                                   PackParams PA, const uint8_t *__restrict__ b,
+                                                   void *__restrict__ ob, PackParams PB, int64_t na) {
     __shared__ uint16_t tile[64][64 + 2];
     ptx::griddep_wait();   // launched to overlap the previous kernel's tail
     if ((int64_t)blockIdx.x < na) {
-        vec_a_body<IN>(a, oa, PA, blockIdx.x, na);
+        if constexpr (OUT8) vec_a8_body<IN>(a, static_cast<uint8_t *>(oa), PA, blockIdx.x, na);
+        else vec_a_body<IN>(a, static_cast<__nv_bfloat16 *>(oa), PA, blockIdx.x, na);
     } else {
         const int64_t t = (int64_t)blockIdx.x - na;
         const int64_t nbx = PB.cols / 64;
-        vec_b_body<IN, 2>(b, ob, PB, t % nbx, t / nbx, tile);
+        vec_b_body<IN, 2, OUT8>(b, ob, PB, t % nbx, t / nbx, tile);
     }
 }
 
@@ -705,20 +710,24 @@ PackParams pack_params(const Field &f, int64_t rows, int64_t cols, int64_t ld_in
 
 }  // namespace
 
-// A (m x K) -> OPERAND_A and B (K x n) -> OPERAND_B from coefficient planes,
-// in one launch when both fit the vectorised paths, else two.
+// A (m x K) -> OPERAND_A and B (K x n) -> OPERAND_B from coefficient planes
+// (with e4m3: OPERAND_A_E4M3 and OPERAND_B_E4M3), in one launch when both
+// fit the vectorised paths, else two.
 int launch_pack_pair(const Field &f, int in_fmt, const void *A, int64_t m, int64_t K,
                      int64_t lda_in, void *outA, int64_t lda_out, const void *B, int64_t n,
-                     int64_t ldb_in, void *outB, int64_t ldb_out, cudaStream_t stream) {
+                     int64_t ldb_in, void *outB, int64_t ldb_out, cudaStream_t stream, bool e4m3) {
     const bool planes_in = in_fmt == QADIC_FMT_INT8_PLANES || in_fmt == QADIC_FMT_COEFF_U8;
+    const int64_t lo = e4m3 ? 16 : 8;   // output rows in whole 16-byte units
     const bool a_ok = K % 16 == 0 && lda_in % 16 == 0 && ((uintptr_t)A & 15) == 0 &&
-                      lda_out % 8 == 0 && ((uintptr_t)outA & 15) == 0;
+                      lda_out % lo == 0 && ((uintptr_t)outA & 15) == 0;
     const bool b_ok = n % 64 == 0 && ldb_in % 16 == 0 && ((uintptr_t)B & 15) == 0 &&
-                      ldb_out % 8 == 0 && ((uintptr_t)outB & 15) == 0 && (K + 63) / 64 <= 65535;
+                      ldb_out % lo == 0 && ((uintptr_t)outB & 15) == 0 && (K + 63) / 64 <= 65535;
     if (!planes_in || !a_ok || !b_ok) {
-        int st = launch_pack(f, in_fmt, A, m, K, lda_in, QADIC_FMT_OPERAND_A, outA, lda_out, stream);
+        int st = launch_pack(f, in_fmt, A, m, K, lda_in,
+                             e4m3 ? QADIC_FMT_OPERAND_A_E4M3 : QADIC_FMT_OPERAND_A, outA, lda_out, stream);
         if (st != QADIC_OK) return st;
-        return launch_pack(f, in_fmt, B, K, n, ldb_in, QADIC_FMT_OPERAND_B, outB, ldb_out, stream);
+        return launch_pack(f, in_fmt, B, K, n, ldb_in,
+                           e4m3 ? QADIC_FMT_OPERAND_B_E4M3 : QADIC_FMT_OPERAND_B, outB, ldb_out, stream);
     }
     const PackParams PA = pack_params(f, m, K, lda_in, lda_out);
     const PackParams PB = pack_params(f, K, n, ldb_in, ldb_out);
@@ -742,12 +751,11 @@ int launch_pack_pair(const Field &f, int in_fmt, const void *A, int64_t m, int64
     cfg.gridDim = dim3((unsigned)(na + nb));
     cfg.blockDim = dim3(256);
     cfg.stream = stream;
-    const cudaError_t e =
-        in_fmt == QADIC_FMT_INT8_PLANES
-            ? cudaLaunchKernelEx(&cfg, pack_vec_ab<IN_I8>, (const uint8_t *)A, (__nv_bfloat16 *)outA,
-                                 PA, (const uint8_t *)B, (__nv_bfloat16 *)outB, PB, na)
-            : cudaLaunchKernelEx(&cfg, pack_vec_ab<IN_U8>, (const uint8_t *)A, (__nv_bfloat16 *)outA,
-                                 PA, (const uint8_t *)B, (__nv_bfloat16 *)outB, PB, na);
+    auto kern = in_fmt == QADIC_FMT_INT8_PLANES
+                    ? (e4m3 ? pack_vec_ab<IN_I8, true> : pack_vec_ab<IN_I8, false>)
+                    : (e4m3 ? pack_vec_ab<IN_U8, true> : pack_vec_ab<IN_U8, false>);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, (const uint8_t *)A, outA, PA,
+                                             (const uint8_t *)B, outB, PB, na);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return set_error(QADIC_E_CUDA, "pack launch: %s", cudaGetErrorString(e));

@@ -88,7 +88,8 @@ int launch_pack(const Field &f, int in_fmt, const void *in, int64_t rows, int64_
 
 int launch_pack_pair(const Field &f, int in_fmt, const void *A, int64_t m, int64_t K,
                      int64_t lda_in, void *outA, int64_t lda_out, const void *B, int64_t n,
-                     int64_t ldb_in, void *outB, int64_t ldb_out, cudaStream_t stream);
+                     int64_t ldb_in, void *outB, int64_t ldb_out, cudaStream_t stream,
+                     bool e4m3 = false);
 
 int launch_gemm_f64(const Field &f, int64_t m, int64_t n, int64_t K, const double *A, int64_t lda,
                     const double *B, int64_t ldb, uint8_t *C, int64_t ldc, cudaStream_t stream);

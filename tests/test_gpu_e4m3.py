@@ -192,11 +192,7 @@ def test_chained_packs_and_gemms_share_operand_buffers(torch, path):
 
     def product(i, C):
         a, b = X[i]
-        if e4:
-            f.pack(q.FMT_INT8_PLANES, a, n, n, q.FMT_OPERAND_A_E4M3, out=opA)
-            f.pack(q.FMT_INT8_PLANES, b, n, n, q.FMT_OPERAND_B_E4M3, out=opB)
-        else:
-            f.pack_operands(q.FMT_INT8_PLANES, a, b, n, n, n, opA, opB)
+        f.pack_operands(q.FMT_INT8_PLANES, a, b, n, n, n, opA, opB, e4m3=e4)
         return f.gemm(path, opA, opB, n, n, n, C=C)
 
     want = []
@@ -232,3 +228,43 @@ def test_matmul_device_e4m3_strided_inputs(torch, orc):
     torch.cuda.synchronize()
     q.sync_status()
     assert np.array_equal(C.cpu().numpy(), oracle_planes(orc, p, f.poly, A, B))
+
+
+@pytest.mark.parametrize("fmt", [q.FMT_INT8_PLANES, q.FMT_COEFF_U8, q.FMT_LOG])
+@pytest.mark.parametrize("m,n,K", [(256, 256, 256), (130, 192, 96), (77, 100, 45), (64, 64, 4096)])
+def test_pack_operands_e4m3_equals_separate_packs(torch, fmt, m, n, K):
+    """qadic_pack_operands_e4m3 (one launch for aligned plane inputs with n a
+    multiple of 64, two otherwise) writes the bytes of the two single packs."""
+    p, k = 7, 4
+    f = q.Field(p, k)
+    if fmt == q.FMT_LOG:
+        A, B = W.log_matrix(m, K, f.order, salt=m), W.log_matrix(K, n, f.order, salt=n)
+    elif fmt == q.FMT_COEFF_U8:   # any byte: taken mod p
+        A = np.random.default_rng(m).integers(0, 256, (k, m, K), dtype=np.uint8)
+        B = np.random.default_rng(n).integers(0, 256, (k, K, n), dtype=np.uint8)
+    else:
+        A = np.random.default_rng(m).integers(-128, 128, (k, m, K), dtype=np.int8)
+        B = np.random.default_rng(n).integers(-128, 128, (k, K, n), dtype=np.int8)
+    dA, dB = dev(torch, A), dev(torch, B)
+    Kp = (K + 15) // 16 * 16
+    fused = [torch.full((k, r, Kp), 0x7F, dtype=torch.uint8, device="cuda") for r in (m, n)]
+    single = [torch.full((k, r, Kp), 0x7F, dtype=torch.uint8, device="cuda") for r in (m, n)]
+    f.pack_operands(fmt, dA, dB, m, n, K, fused[0], fused[1], e4m3=True)
+    f.pack(fmt, dA, m, K, q.FMT_OPERAND_A_E4M3, out=single[0], ld_out=Kp)
+    f.pack(fmt, dB, K, n, q.FMT_OPERAND_B_E4M3, out=single[1], ld_out=Kp)
+    torch.cuda.synchronize()
+    q.sync_status()
+    assert torch.equal(fused[0], single[0]) and torch.equal(fused[1], single[1])
+
+
+def test_pack_operands_e4m3_refusals(torch):
+    L = q.lib()
+    g = q.Field(37, 2)
+    z = torch.zeros(2 * 64 * 64, dtype=torch.uint8, device="cuda")
+    st = L.qadic_pack_operands_e4m3(g.handle, q.FMT_INT8_PLANES, q._ptr(z), 64, 64, 64, q._ptr(z), 64,
+                                    q._ptr(z), 64, 64, q._ptr(z), 64, None)
+    assert st == q.E_UNSUPPORTED
+    f = q.Field(31, 2)
+    st = L.qadic_pack_operands_e4m3(f.handle, q.FMT_INT8_PLANES, q._ptr(z), 64, 24, 24, q._ptr(z), 24,
+                                    q._ptr(z), 64, 64, q._ptr(z), 24, None)
+    assert st == q.E_INVALID   # ld_out 24 is not a multiple of 16

@@ -76,16 +76,17 @@ def test_plane_gf101_2_n4096_and_fp64_form(torch, orc):
 
 
 def test_plane_e4m3_gf31_2_n4096(torch, orc):
-    """The e4m3 comparison workload as bench.py times it (two e4m3 packs +
-    the kind::f8f6f4 plane GEMM, GF(31^2), n = 4096): 4096 sampled entries,
+    """The e4m3 comparison workload as bench.py times it (one-launch e4m3
+    pack + the kind::f8f6f4 plane GEMM, GF(31^2), n = 4096): 4096 sampled entries,
     two whole rows (a leader CTA's and a peer's half of a 256-row unit) and
     two whole columns against the oracle, every entry against the bf16 plane
     path on the same inputs, and one Freivalds vector."""
     n = 4096
     f, A, B = bench.make_e4m3_inputs(q, W, 31, n)
     dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
-    a8 = f.pack(q.FMT_INT8_PLANES, dA, n, n, q.FMT_OPERAND_A_E4M3)
-    b8 = f.pack(q.FMT_INT8_PLANES, dB, n, n, q.FMT_OPERAND_B_E4M3)
+    a8 = torch.empty((2, n, n), dtype=torch.uint8, device="cuda")
+    b8 = torch.empty((2, n, n), dtype=torch.uint8, device="cuda")
+    f.pack_operands(q.FMT_INT8_PLANES, dA, dB, n, n, n, a8, b8, e4m3=True)
     C8 = f.gemm(q.PATH_PLANES_E4M3, a8, b8, n, n, n)
     a16 = torch.empty((2, n, n), dtype=torch.bfloat16, device="cuda")
     b16 = torch.empty((2, n, n), dtype=torch.bfloat16, device="cuda")
