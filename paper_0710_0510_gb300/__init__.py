@@ -192,10 +192,24 @@ def _torch():
     return _TORCH_CUDA
 
 
+_RAW_STREAM = None
+
+
 def _stream(stream=None):
+    """The CUDA stream handle to pass: `stream`'s, else the current one (read
+    as a raw handle where torch exposes it, which skips building a Stream
+    object on every call)."""
+    global _RAW_STREAM
     torch = _torch()
-    s = stream if stream is not None else torch.cuda.current_stream()
-    return ctypes.c_void_p(s.cuda_stream)
+    if stream is not None:
+        return ctypes.c_void_p(stream.cuda_stream)
+    if _RAW_STREAM is None:
+        raw = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+        dev = getattr(torch._C, "_cuda_getDevice", None)
+        _RAW_STREAM = (lambda: raw(dev())) if raw is not None and dev is not None else False
+    if _RAW_STREAM:
+        return ctypes.c_void_p(_RAW_STREAM())
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
 def _ptr(t) -> ctypes.c_void_p:

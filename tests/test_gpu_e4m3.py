@@ -268,3 +268,13 @@ def test_pack_operands_e4m3_refusals(torch):
     st = L.qadic_pack_operands_e4m3(f.handle, q.FMT_INT8_PLANES, q._ptr(z), 64, 24, 24, q._ptr(z), 24,
                                     q._ptr(z), 64, 64, q._ptr(z), 24, None)
     assert st == q.E_INVALID   # ld_out 24 is not a multiple of 16
+
+
+def test_stream_handle_is_the_current_stream(torch):
+    """The binding passes the stream torch has current (a side stream inside
+    `torch.cuda.stream`, the default one outside)."""
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        assert (q._stream().value or 0) == s.cuda_stream
+    assert (q._stream().value or 0) == torch.cuda.current_stream().cuda_stream
+    assert (q._stream(s).value or 0) == s.cuda_stream
