@@ -275,10 +275,9 @@ polymul_q8_kernel(const uint8_t *__restrict__ a, const uint8_t *__restrict__ b,
     // a group's 4K bytes start on a 4K-byte boundary of each operand
     const bool vec = ((((uintptr_t)a | (uintptr_t)b) & (K == 3 ? 3 : 4 * K - 1)) == 0);
 
-    for (int64_t base = (int64_t)blockIdx.x * kChunk; base < count;
-         base += (int64_t)gridDim.x * kChunk) {
+    // the group's operand bytes (little-endian) of the chunk at `base`
+    auto load_group = [&](int64_t base, uint32_t (&wa)[K], uint32_t (&wb)[K]) {
         const int64_t pair0 = base + (int64_t)threadIdx.x * G;
-        uint32_t wa[K], wb[K];          // the group's operand bytes, little-endian
         if (vec && pair0 + G <= count) {
             const uint8_t *pa = a + pair0 * K, *pb = b + pair0 * K;
             if constexpr (K == 4) {
@@ -308,6 +307,18 @@ polymul_q8_kernel(const uint8_t *__restrict__ a, const uint8_t *__restrict__ b,
                     wb[x / 4] |= (uint32_t)__ldg(b + pair0 * K + x) << (8 * (x % 4));
                 }
         }
+    };
+    const int64_t step = (int64_t)gridDim.x * kChunk;
+    uint32_t na[K], nb[K];   // the next chunk's bytes, loaded while this one is worked on
+    if ((int64_t)blockIdx.x * kChunk < count) load_group((int64_t)blockIdx.x * kChunk, na, nb);
+    for (int64_t base = (int64_t)blockIdx.x * kChunk; base < count; base += step) {
+        uint32_t wa[K], wb[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            wa[j] = na[j];
+            wb[j] = nb[j];
+        }
+        if (base + step < count) load_group(base + step, na, nb);
         uint32_t any = 0;
 #pragma unroll
         for (int j = 0; j < K; ++j) any |= any_byte_ge(wa[j], ge.add, ge.p_low) | any_byte_ge(wb[j], ge.add, ge.p_low);
